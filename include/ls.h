@@ -1,0 +1,188 @@
+/*
+ * ls.h -- C ABI of the GB300 (sm_103a) two-level Lippmann-Schwinger solver.
+ *
+ * Method: Zepeda-Nunez & Zhao, "Fast alternating bi-directional preconditioner
+ * for the 2D high-frequency Lippmann-Schwinger equation".  Sections, equations
+ * and algorithms below refer to that paper.
+ *
+ * Conventions shared by every entry point
+ *   - Grid (Sec. 2): nodes x_{i,j} = (h i, h j), 1 <= i <= nx, 1 <= j <= nz.
+ *     A field is an array of nz*nx elements, x fastest: element (i, j) sits at
+ *     index (j-1)*nx + (i-1) (eq. global_ordering / eq. trace_ordering).
+ *   - Complex fields are interleaved (re, im): ls_c64 = two doubles,
+ *     ls_c32 = two floats.
+ *   - Unless an entry point says otherwise, every field pointer is a DEVICE
+ *     pointer on the handle's device; the caller owns it and must keep it
+ *     alive until the call's work on the handle's stream has finished.
+ *     Calls are stream-ordered on the stream given to ls_setup; the functions
+ *     that return iteration counts or residuals synchronise that stream.
+ *   - Return value: LS_OK (0) or a negative LS_E* code; ls_strerror() names it.
+ *     No entry point aborts the process, and none falls back to the CPU.
+ *   - A handle is used by one host thread at a time.
+ */
+#ifndef LS_H
+#define LS_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct { double re, im; } ls_c64;
+typedef struct { float re, im; } ls_c32;
+
+enum {
+    LS_OK = 0,
+    LS_EINVAL = -1,     /* bad size, option or null pointer                         */
+    LS_ENOMEM = -2,     /* device or host allocation failed                         */
+    LS_ECUDA = -3,      /* a CUDA runtime call or kernel launch failed              */
+    LS_ESINGULAR = -4,  /* zero pivot in a local factorisation                      */
+    LS_ENOCONV = -5,    /* iteration limit reached; output holds the best iterate   */
+    LS_ENAN = -6,       /* NaN or Inf in an input or a residual                     */
+    LS_ETIMEOUT = -7,   /* a bounded device-side wait ran out                       */
+    LS_ESTATE = -8      /* call out of order (e.g. solve before ls_factor)          */
+};
+
+enum { LS_FP64 = 0, LS_MIXED = 1 };
+
+typedef struct {
+    int nx, nz;       /* grid points per direction (this build requires nx == nz >= 8)      */
+    int layers;       /* L, number of layers per direction (Sec. 3.1); must divide nz       */
+    int ext;          /* extension rows on each side of a layer (Sec. 5: 10); >= 1          */
+    int precision;    /* LS_FP64: all FP64.  LS_MIXED: FP32 FFT convolution and local
+                         solves inside FP64 refinement; FP64 factorisation and Arnoldi     */
+} ls_grid;
+
+typedef struct {
+    double inner_tol;      /* Algorithm 3 inner GMRES tolerance (Sec. 4: 1e-3)             */
+    int inner_restart;     /* inner GMRES restart length (default 30)                       */
+    int inner_maxit;       /* inner GMRES iteration cap (default 200)                       */
+    int outer_restart;     /* outer flexible GMRES restart length (default 40)              */
+    int outer_maxit;       /* outer iteration cap (default 200)                             */
+    double shift;          /* complex-shift constant c: the cut-off region adds i c w to
+                              the w^2-weighted coefficient (Sec. 3.3; default 10)            */
+    int refine_maxit;      /* LS_MIXED: refinement steps cap (default 6)                    */
+    double refine_inner_tol; /* LS_MIXED: relative tolerance of each FP32 correction solve
+                                (default 1e-4)                                               */
+} ls_opts;
+
+typedef struct {
+    int outer_iters;         /* outer (flexible) GMRES iterations, all refinement steps     */
+    int inner_iters_total;   /* inner GMRES iterations summed over all preconditioner calls */
+    int inner_calls;         /* Algorithm 3 applications                                     */
+    int refine_steps;        /* LS_MIXED refinement steps (1 = no correction needed)         */
+    double true_rel_residual;/* ||f - H u|| / ||f|| with an FP64 apply of H                 */
+    double t_solve_s;        /* wall time of the call                                        */
+    double t_apply_ms;       /* total device time of LS-apply launches (if timing enabled)  */
+    int n_apply;             /* LS-apply launches counted in t_apply_ms                      */
+    double t_sweep_ms;       /* total device time of Algorithm 2 applications (if timing)   */
+    int n_sweep;             /* Algorithm 2 applications counted in t_sweep_ms               */
+    long long kernel_launches; /* kernels this library launched during the call            */
+} ls_stats;
+
+typedef struct ls_handle ls_handle;
+
+/* Defaults of ls_opts (the paper's values where it gives them). */
+void ls_default_opts(ls_opts* opts);
+
+/* ls_setup -- create a handle for the discrete problem of Sec. 2.
+ *   grid: sizes and precision (see ls_grid).  h: mesh step; omega: frequency.
+ *   m: DEVICE array nz*nx of the contrast m(x_{i,j}) (1/c^2 = 1 + m, Sec. 1);
+ *      copied, the caller keeps ownership.
+ *   opts: NULL for defaults.  stream: cudaStream_t (NULL = legacy default stream).
+ * Allocates the handle's device memory (medium, spectrum, stencil tables,
+ * workspaces).  Computes the quadrature weights G_w (Sec. 2), the spectrum of
+ * the circulant embedding, and the sparsifying stencils alpha, beta (Sec. 2).
+ * Errors: LS_EINVAL (sizes, L not dividing nz, null pointers), LS_ENOMEM, LS_ECUDA.
+ * On error *out is NULL and nothing is leaked. */
+int ls_setup(const ls_grid* grid, double h, double omega, const double* m,
+             const ls_opts* opts, void* stream, ls_handle** out);
+
+/* ls_factor -- off-line stage (Sec. 4.1): assemble the local matrices C^l of
+ * the L horizontal and the L vertical layers (Sec. 3.1, 3.3) and factor each
+ * by block cyclic reduction in FP64.  LS_ESINGULAR on a zero pivot. */
+int ls_factor(ls_handle* h);
+
+/* ls_apply -- y = H u = u + w^2 G (m u) (Sec. 2, eq. discrete_Lipmann-Schwinger),
+ * FP64, by the zero-padded FFT convolution.  u, y: device, nz*nx; may alias. */
+int ls_apply(ls_handle* h, const ls_c64* u, ls_c64* y);
+
+/* ls_apply_f32 -- the same operator with FP32 complex arithmetic and FP32 I/O. */
+int ls_apply_f32(ls_handle* h, const ls_c32* u, ls_c32* y);
+
+/* ls_incident_rhs -- f = -w^2 G (m u_I) with u_I = exp(i w (x cos theta + z sin theta))
+ * generated on the device (Sec. 2, f = -w^2 G D u_I).  f: device, nz*nx. */
+int ls_incident_rhs(ls_handle* h, double theta, ls_c64* f);
+
+/* ls_solve -- solve H u = f (Sec. 4): outer flexible GMRES preconditioned by
+ * Algorithm 3 (inner GMRES on C v = A r preconditioned by Algorithm 2).
+ *   tol: relative residual target ||f - H u|| / ||f||, checked with FP64 H.
+ *   u: in: initial guess if use_x0 != 0, else ignored; out: solution.
+ *   stats: may be NULL.
+ * Requires ls_factor.  LS_ENOCONV if the caps are reached (u = best iterate,
+ * stats filled); LS_ENAN on NaN/Inf in f or a residual.  f = 0 gives u = 0. */
+int ls_solve(ls_handle* h, const ls_c64* f, double tol, ls_c64* u, int use_x0, ls_stats* stats);
+
+/* ls_solve_host -- ls_solve with HOST arrays f and u (pageable or pinned); the
+ * host<->device copies run on the handle's stream inside the call. */
+int ls_solve_host(ls_handle* h, const ls_c64* f_host, double tol, ls_c64* u_host, ls_stats* stats);
+
+/* ls_solve_plane_wave -- f = ls_incident_rhs(theta) followed by ls_solve. */
+int ls_solve_plane_wave(ls_handle* h, double theta, double tol, ls_c64* u, ls_stats* stats);
+
+/* ---- operators of the inner level (Sec. 2-3), exposed for checking and reuse ---- */
+
+/* y = A r: sparsifying stencil (Sec. 2), 9-point with boundary types.  FP64. */
+int ls_apply_A(ls_handle* h, const ls_c64* r, ls_c64* y);
+
+/* y = C v: sparsified matrix C = A H kept on the 9-point pattern (Sec. 2). FP64. */
+int ls_apply_C(ls_handle* h, const ls_c64* v, ls_c64* y);
+
+/* v = Algorithm 1 (Gauss-Seidel polarized-traces preconditioner, Sec. 3.4) applied
+ * to g, on horizontal layers (dir = 0) or vertical layers (dir = 1).  Requires
+ * ls_factor.  Local solves in the handle's precision. */
+int ls_sweep(ls_handle* h, int dir, const ls_c64* g, ls_c64* v);
+
+/* v = Algorithm 2 (bi-directional preconditioner, Sec. 3.5) applied to g. */
+int ls_precond_bd(ls_handle* h, const ls_c64* g, ls_c64* v);
+
+/* Inner level of Algorithm 3: GMRES on C v = g preconditioned by Algorithm 2,
+ * from v = 0, to relative tolerance tol.  *iters receives the iteration count. */
+int ls_inner_solve(ls_handle* h, const ls_c64* g, double tol, ls_c64* v, int* iters);
+
+/* Local solve x = (C^l)^{-1} b on layer l of direction dir (Sec. 3.1): b and x are
+ * DEVICE arrays of q*nx elements, q = t + 2*ext rows of the extended layer,
+ * local row r <-> global row l*t - ext + r (rows outside Omega are identity
+ * rows), x fastest.  Uses the factors of ls_factor in the handle's precision. */
+int ls_local_solve(ls_handle* h, int dir, int layer, const ls_c64* b, ls_c64* x);
+
+/* ---- introspection (host copies of small tables) ---- */
+
+/* alpha, beta: host arrays of 81 ls_c64 each, index [type*9 + slot] with
+ * type = (bz+1)*3 + (bx+1) and slot = (dz+1)*3 + (dx+1) (Sec. 2 stencils;
+ * beta_d = sum_e alpha_e G_w(e - d)). Either may be NULL. */
+int ls_get_stencils(ls_handle* h, ls_c64* alpha, ls_c64* beta);
+
+/* Quadrant of the spectral factor Ghat = (w^2/P^2) FFT2(circulant embedding of G),
+ * (P/2+1)^2 elements, index [kx*(P/2+1) + kz] (the quadrant is symmetric, G being
+ * radial).  P = smallest power of two >= 2*nx - 1.  ghat: DEVICE array. *P_out = P. */
+int ls_get_spectrum(ls_handle* h, ls_c64* ghat, int* P_out);
+
+/* Diagonal quadrature weight G_w(0) (Sec. 2) as used by the handle. */
+int ls_get_diag_weight(ls_handle* h, ls_c64* w0);
+
+/* Local strip height q = t + 2*ext and t = nz / layers. */
+int ls_get_layout(ls_handle* h, int* t, int* q);
+
+/* Turn per-call CUDA-event timing of LS-apply and Algorithm 2 on (1) or off (0). */
+int ls_set_timing(ls_handle* h, int on);
+
+/* Number of kernels the library has launched on this handle since setup. */
+long long ls_kernel_count(ls_handle* h);
+
+void ls_destroy(ls_handle* h);
+const char* ls_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LS_H */

@@ -142,3 +142,19 @@ def dense_G(n: int, h: float, omega: float) -> np.ndarray:
     kz = jj.ravel()
     kx = ii.ravel()
     return W[(kz[:, None] - kz[None, :]) + n - 1, (kx[:, None] - kx[None, :]) + n - 1]
+
+
+def apply_H_points(u: np.ndarray, m: np.ndarray, h: float, omega: float, points) -> np.ndarray:
+    """(H u)_k at selected nodes k = (j, i) by the direct quadrature sum (Sec. 2), O(N) each."""
+    n = u.shape[0]
+    jj, ii = np.meshgrid(np.arange(n), np.arange(n), indexing="ij")
+    mu = m * u
+    out = []
+    for (j, i) in points:
+        r = h * np.sqrt((ii - i) ** 2.0 + (jj - j) ** 2.0)
+        W = np.empty(r.shape, dtype=np.complex128)
+        nz = r > 0
+        W[nz] = h * h * green(r[nz], omega)
+        W[~nz] = diagonal_weight(h, omega)
+        out.append(u[j, i] + omega * omega * np.sum(W * mu))
+    return np.array(out)

@@ -1,0 +1,277 @@
+"""Thin ctypes binding over libls.so (the C ABI in include/ls.h).
+
+Argument marshalling only: every function forwards torch tensor device pointers
+(or host pointers for `solve_host`) to the C entry point of the same name and
+raises `LSError` on a non-zero status.  No computation happens here, and there
+is no fallback: if libls.so is missing or no CUDA device is present, `load()`
+raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+_LIB = None
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libls.so")
+
+LS_FP64, LS_MIXED = 0, 1
+
+
+class LSError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        msg = _LIB.ls_strerror(code).decode() if _LIB is not None else str(code)
+        super().__init__("%s failed: %s (%d)" % (where, msg, code))
+        self.code = code
+
+
+class Grid(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("nz", ctypes.c_int), ("layers", ctypes.c_int),
+                ("ext", ctypes.c_int), ("precision", ctypes.c_int)]
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("inner_tol", ctypes.c_double), ("inner_restart", ctypes.c_int),
+                ("inner_maxit", ctypes.c_int), ("outer_restart", ctypes.c_int),
+                ("outer_maxit", ctypes.c_int), ("shift", ctypes.c_double),
+                ("refine_maxit", ctypes.c_int), ("refine_inner_tol", ctypes.c_double)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("outer_iters", ctypes.c_int), ("inner_iters_total", ctypes.c_int),
+                ("inner_calls", ctypes.c_int), ("refine_steps", ctypes.c_int),
+                ("true_rel_residual", ctypes.c_double), ("t_solve_s", ctypes.c_double),
+                ("t_apply_ms", ctypes.c_double), ("n_apply", ctypes.c_int),
+                ("t_sweep_ms", ctypes.c_double), ("n_sweep", ctypes.c_int),
+                ("kernel_launches", ctypes.c_longlong)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_P = ctypes.c_void_p
+_SIGS = {
+    "ls_default_opts": (None, [ctypes.POINTER(Opts)]),
+    "ls_setup": (ctypes.c_int, [ctypes.POINTER(Grid), ctypes.c_double, ctypes.c_double, _P,
+                                ctypes.POINTER(Opts), _P, ctypes.POINTER(_P)]),
+    "ls_factor": (ctypes.c_int, [_P]),
+    "ls_apply": (ctypes.c_int, [_P, _P, _P]),
+    "ls_apply_f32": (ctypes.c_int, [_P, _P, _P]),
+    "ls_incident_rhs": (ctypes.c_int, [_P, ctypes.c_double, _P]),
+    "ls_solve": (ctypes.c_int, [_P, _P, ctypes.c_double, _P, ctypes.c_int, ctypes.POINTER(Stats)]),
+    "ls_solve_host": (ctypes.c_int, [_P, _P, ctypes.c_double, _P, ctypes.POINTER(Stats)]),
+    "ls_solve_plane_wave": (ctypes.c_int, [_P, ctypes.c_double, ctypes.c_double, _P, ctypes.POINTER(Stats)]),
+    "ls_apply_A": (ctypes.c_int, [_P, _P, _P]),
+    "ls_apply_C": (ctypes.c_int, [_P, _P, _P]),
+    "ls_sweep": (ctypes.c_int, [_P, ctypes.c_int, _P, _P]),
+    "ls_precond_bd": (ctypes.c_int, [_P, _P, _P]),
+    "ls_inner_solve": (ctypes.c_int, [_P, _P, ctypes.c_double, _P, ctypes.POINTER(ctypes.c_int)]),
+    "ls_local_solve": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, _P, _P]),
+    "ls_get_stencils": (ctypes.c_int, [_P, _P, _P]),
+    "ls_get_spectrum": (ctypes.c_int, [_P, _P, ctypes.POINTER(ctypes.c_int)]),
+    "ls_get_diag_weight": (ctypes.c_int, [_P, _P]),
+    "ls_get_layout": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
+    "ls_set_timing": (ctypes.c_int, [_P, ctypes.c_int]),
+    "ls_kernel_count": (ctypes.c_longlong, [_P]),
+    "ls_destroy": (None, [_P]),
+    "ls_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+}
+
+EXPORTED = tuple(_SIGS)
+
+
+def load_library(path: str = LIB_PATH):
+    """dlopen libls.so and declare the prototypes (no GPU needed)."""
+    global _LIB
+    if _LIB is None:
+        if not os.path.exists(path):
+            raise RuntimeError("libls.so not built (run __graft_entry__.build()): %s" % path)
+        lib = ctypes.CDLL(path)
+        for name, (res, args) in _SIGS.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _LIB = lib
+    return _LIB
+
+
+def load():
+    """Load the library for GPU use; raises when no CUDA device is available."""
+    if not torch.cuda.is_available():
+        raise RuntimeError("no CUDA device: the Lippmann-Schwinger solver runs only on the GPU")
+    return load_library()
+
+
+def _ck(code: int, where: str):
+    if code != 0:
+        raise LSError(code, where)
+
+
+def _ptr(t: torch.Tensor):
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _c128(t: torch.Tensor, n: int, where: str):
+    if t.dtype != torch.complex128 or not t.is_cuda or not t.is_contiguous() or t.numel() != n:
+        raise ValueError("%s: expected a contiguous CUDA complex128 tensor with %d elements" % (where, n))
+    return _ptr(t)
+
+
+def default_opts() -> Opts:
+    o = Opts()
+    load_library().ls_default_opts(ctypes.byref(o))
+    return o
+
+
+class Solver:
+    """A handle of the C library: setup -> factor -> apply / solve."""
+
+    def __init__(self, m: torch.Tensor, omega: float, layers: int, ext: int = 10,
+                 precision: int = LS_FP64, h: float | None = None, opts: Opts | None = None,
+                 stream: torch.cuda.Stream | None = None):
+        lib = load()
+        if m.dim() != 2 or m.shape[0] != m.shape[1]:
+            raise ValueError("m must be a square (n_z, n_x) array")
+        self.n = int(m.shape[0])
+        self.N = self.n * self.n
+        md = m.to(device="cuda", dtype=torch.float64).contiguous()
+        self.omega = float(omega)
+        self.h = 1.0 / self.n if h is None else float(h)
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        g = Grid(self.n, self.n, int(layers), int(ext), int(precision))
+        handle = ctypes.c_void_p()
+        o = ctypes.byref(opts) if opts is not None else None
+        _ck(lib.ls_setup(ctypes.byref(g), self.h, self.omega, _ptr(md), o,
+                         ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(handle)), "ls_setup")
+        self._h = handle
+        self._lib = lib
+        self.precision = precision
+        t, q = ctypes.c_int(), ctypes.c_int()
+        _ck(lib.ls_get_layout(self._h, ctypes.byref(t), ctypes.byref(q)), "ls_get_layout")
+        self.t, self.q = t.value, q.value
+        self.layers = int(layers)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.ls_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ---- entry points (same names as the C ABI) ----
+    def ls_factor(self):
+        _ck(self._lib.ls_factor(self._h), "ls_factor")
+
+    def ls_apply(self, u, y=None):
+        y = torch.empty_like(u) if y is None else y
+        _ck(self._lib.ls_apply(self._h, _c128(u, self.N, "ls_apply"), _c128(y, self.N, "ls_apply")), "ls_apply")
+        return y
+
+    def ls_apply_f32(self, u, y=None):
+        y = torch.empty_like(u) if y is None else y
+        if u.dtype != torch.complex64 or y.dtype != torch.complex64:
+            raise ValueError("ls_apply_f32 takes complex64 tensors")
+        _ck(self._lib.ls_apply_f32(self._h, _ptr(u), _ptr(y)), "ls_apply_f32")
+        return y
+
+    def ls_incident_rhs(self, theta, f=None):
+        f = torch.empty((self.n, self.n), dtype=torch.complex128, device="cuda") if f is None else f
+        _ck(self._lib.ls_incident_rhs(self._h, float(theta), _c128(f, self.N, "ls_incident_rhs")), "ls_incident_rhs")
+        return f
+
+    def ls_solve(self, f, tol, u=None, x0=False, check=True):
+        u = torch.empty_like(f) if u is None else u
+        st = Stats()
+        rc = self._lib.ls_solve(self._h, _c128(f, self.N, "ls_solve"), float(tol), _c128(u, self.N, "ls_solve"),
+                                1 if x0 else 0, ctypes.byref(st))
+        if check:
+            _ck(rc, "ls_solve")
+        return u, st.as_dict(), rc
+
+    def ls_solve_host(self, f_host, tol, u_host):
+        """f_host, u_host: CPU complex128 tensors (pinned or pageable)."""
+        for t in (f_host, u_host):
+            if t.is_cuda or t.dtype != torch.complex128 or not t.is_contiguous() or t.numel() != self.N:
+                raise ValueError("ls_solve_host takes contiguous CPU complex128 tensors")
+        st = Stats()
+        rc = self._lib.ls_solve_host(self._h, _ptr(f_host), float(tol), _ptr(u_host), ctypes.byref(st))
+        _ck(rc, "ls_solve_host")
+        return st.as_dict()
+
+    def ls_solve_plane_wave(self, theta, tol, u=None):
+        u = torch.empty((self.n, self.n), dtype=torch.complex128, device="cuda") if u is None else u
+        st = Stats()
+        _ck(self._lib.ls_solve_plane_wave(self._h, float(theta), float(tol), _c128(u, self.N, "ls_solve_plane_wave"),
+                                          ctypes.byref(st)), "ls_solve_plane_wave")
+        return u, st.as_dict()
+
+    def ls_apply_A(self, r, y=None):
+        y = torch.empty_like(r) if y is None else y
+        _ck(self._lib.ls_apply_A(self._h, _c128(r, self.N, "ls_apply_A"), _c128(y, self.N, "ls_apply_A")), "ls_apply_A")
+        return y
+
+    def ls_apply_C(self, v, y=None):
+        y = torch.empty_like(v) if y is None else y
+        _ck(self._lib.ls_apply_C(self._h, _c128(v, self.N, "ls_apply_C"), _c128(y, self.N, "ls_apply_C")), "ls_apply_C")
+        return y
+
+    def ls_sweep(self, direction, g, v=None):
+        v = torch.empty_like(g) if v is None else v
+        _ck(self._lib.ls_sweep(self._h, int(direction), _c128(g, self.N, "ls_sweep"), _c128(v, self.N, "ls_sweep")),
+            "ls_sweep")
+        return v
+
+    def ls_precond_bd(self, g, v=None):
+        v = torch.empty_like(g) if v is None else v
+        _ck(self._lib.ls_precond_bd(self._h, _c128(g, self.N, "ls_precond_bd"), _c128(v, self.N, "ls_precond_bd")),
+            "ls_precond_bd")
+        return v
+
+    def ls_inner_solve(self, g, tol, v=None):
+        v = torch.empty_like(g) if v is None else v
+        it = ctypes.c_int()
+        _ck(self._lib.ls_inner_solve(self._h, _c128(g, self.N, "ls_inner_solve"), float(tol),
+                                     _c128(v, self.N, "ls_inner_solve"), ctypes.byref(it)), "ls_inner_solve")
+        return v, it.value
+
+    def ls_local_solve(self, direction, layer, b, x=None):
+        x = torch.empty_like(b) if x is None else x
+        cnt = self.q * self.n
+        _ck(self._lib.ls_local_solve(self._h, int(direction), int(layer), _c128(b, cnt, "ls_local_solve"),
+                                     _c128(x, cnt, "ls_local_solve")), "ls_local_solve")
+        return x
+
+    def ls_get_stencils(self):
+        a = (ctypes.c_double * 162)()
+        b = (ctypes.c_double * 162)()
+        _ck(self._lib.ls_get_stencils(self._h, a, b), "ls_get_stencils")
+        import numpy as np
+        A = np.frombuffer(a, dtype=np.complex128).copy().reshape(9, 9)
+        B = np.frombuffer(b, dtype=np.complex128).copy().reshape(9, 9)
+        return A, B
+
+    def ls_get_spectrum(self):
+        P = ctypes.c_int()
+        _ck(self._lib.ls_get_spectrum(self._h, None, ctypes.byref(P)), "ls_get_spectrum")
+        q1 = P.value // 2 + 1
+        g = torch.empty((q1, q1), dtype=torch.complex128, device="cuda")
+        _ck(self._lib.ls_get_spectrum(self._h, _ptr(g), ctypes.byref(P)), "ls_get_spectrum")
+        torch.cuda.synchronize()
+        return g, P.value
+
+    def ls_get_diag_weight(self):
+        w = (ctypes.c_double * 2)()
+        _ck(self._lib.ls_get_diag_weight(self._h, w), "ls_get_diag_weight")
+        return complex(w[0], w[1])
+
+    def ls_set_timing(self, on: bool):
+        _ck(self._lib.ls_set_timing(self._h, 1 if on else 0), "ls_set_timing")
+
+    def ls_kernel_count(self) -> int:
+        return int(self._lib.ls_kernel_count(self._h))

@@ -1,0 +1,358 @@
+// ls_api.cu -- the C ABI declared in include/ls.h: handle lifetime, argument
+// checks, status codes, timing and the host-buffer entry point.
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "ls_internal.cuh"
+
+int ls_transpose_real(ls_handle* h, const double* a, double* b);
+void ls_krylov_free(ls_handle* h);
+
+namespace {
+
+thread_local char g_last_cuda[256] = "";
+
+__global__ void k_real_to32(size_t n, const double* __restrict__ a, float* __restrict__ b) {
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        b[i] = (float)a[i];
+}
+
+struct HostBufs {
+    ls_handle* h = nullptr;
+    double2* f = nullptr;
+    double2* u = nullptr;
+};
+HostBufs g_hostbufs[64];
+
+HostBufs* host_bufs(ls_handle* h, bool create) {
+    for (auto& b : g_hostbufs)
+        if (b.h == h) return &b;
+    if (!create) return nullptr;
+    for (auto& b : g_hostbufs)
+        if (!b.h) {
+            b.h = h;
+            return &b;
+        }
+    return nullptr;
+}
+
+void release(ls_handle* h) {
+    if (!h) return;
+    cudaStreamSynchronize(h->stream);
+    ls_krylov_free(h);
+    ls_factor_free(h);
+    if (HostBufs* b = host_bufs(h, false)) {
+        cudaFree(b->f);
+        cudaFree(b->u);
+        *b = HostBufs{};
+    }
+    void* ptrs[] = {h->m64, h->m32, h->mT64, h->ghat64, h->ghat32, h->tw64, h->tw32, h->fftws, h->incx,
+                    h->incz, h->dtabs, h->srhs, h->ssol, h->vtmp, h->vtmp2, h->red};
+    for (void* p : ptrs) cudaFree(p);
+    if (h->red_host) cudaFreeHost(h->red_host);
+    if (h->ev0) cudaEventDestroy(h->ev0);
+    if (h->ev1) cudaEventDestroy(h->ev1);
+    delete h;
+}
+
+int next_pow2_log(int v) {
+    int l = 0;
+    while ((1 << l) < v) ++l;
+    return l;
+}
+
+}  // namespace
+
+int ls_cuda_fail(cudaError_t e) {
+    std::snprintf(g_last_cuda, sizeof(g_last_cuda), "%s", cudaGetErrorString(e));
+    cudaGetLastError();  // clear a non-sticky error
+    return LS_ECUDA;
+}
+
+int ls_timing_begin(ls_handle* h) {
+    if (!h->timing) return LS_OK;
+    LS_CUDA(cudaEventRecord(h->ev0, h->stream));
+    return LS_OK;
+}
+
+int ls_timing_end(ls_handle* h, int kind) {
+    if (!h->timing) return LS_OK;
+    LS_CUDA(cudaEventRecord(h->ev1, h->stream));
+    LS_CUDA(cudaEventSynchronize(h->ev1));
+    float ms = 0;
+    LS_CUDA(cudaEventElapsedTime(&ms, h->ev0, h->ev1));
+    if (kind == 0) {
+        h->t_apply_ms += ms;
+        h->n_apply++;
+    } else {
+        h->t_sweep_ms += ms;
+        h->n_sweep++;
+    }
+    return LS_OK;
+}
+
+extern "C" {
+
+void ls_default_opts(ls_opts* o) {
+    if (!o) return;
+    o->inner_tol = 1e-3;
+    o->inner_restart = 30;
+    o->inner_maxit = 200;
+    o->outer_restart = 40;
+    o->outer_maxit = 200;
+    o->shift = 10.0;
+    o->refine_maxit = 6;
+    o->refine_inner_tol = 1e-4;
+}
+
+const char* ls_strerror(int code) {
+    switch (code) {
+        case LS_OK: return "ok";
+        case LS_EINVAL: return "invalid argument (size, option or null pointer)";
+        case LS_ENOMEM: return "out of memory";
+        case LS_ECUDA: return g_last_cuda[0] ? g_last_cuda : "CUDA error";
+        case LS_ESINGULAR: return "zero pivot in a local factorisation";
+        case LS_ENOCONV: return "iteration limit reached before the tolerance";
+        case LS_ENAN: return "NaN or Inf in an input or a residual";
+        case LS_ETIMEOUT: return "a bounded device wait ran out";
+        case LS_ESTATE: return "call out of order (ls_factor required first)";
+        default: return "unknown status";
+    }
+}
+
+int ls_setup(const ls_grid* grid, double hstep, double omega, const double* m, const ls_opts* opts, void* stream,
+             ls_handle** out) {
+    if (!out) return LS_EINVAL;
+    *out = nullptr;
+    if (!grid || !m) return LS_EINVAL;
+    const int n = grid->nx;
+    if (grid->nx != grid->nz || n < 8 || grid->layers < 1 || grid->nz % grid->layers != 0 || grid->ext < 1)
+        return LS_EINVAL;
+    if (grid->precision != LS_FP64 && grid->precision != LS_MIXED) return LS_EINVAL;
+    if (!(hstep > 0) || !(omega > 0)) return LS_EINVAL;
+    const int lp = next_pow2_log(2 * n - 1);
+    if (lp > 12) return LS_EINVAL;  // FFT kernels are sized for P <= 4096 (n <= 2048)
+    const int t = n / grid->layers, q = t + 2 * grid->ext;
+    if (q > 112) return LS_EINVAL;  // local blocks are inverted in shared memory
+    ls_handle* h = new (std::nothrow) ls_handle();
+    if (!h) return LS_ENOMEM;
+    h->n = n;
+    h->L = grid->layers;
+    h->E = grid->ext;
+    h->t = t;
+    h->q = q;
+    h->lp = lp;
+    h->P = 1 << lp;
+    h->prec = grid->precision;
+    h->h = hstep;
+    h->omega = omega;
+    ls_default_opts(&h->opts);
+    if (opts) h->opts = *opts;
+    if (h->opts.outer_restart < 1 || h->opts.outer_restart > 63 || h->opts.inner_restart < 1 ||
+        h->opts.inner_restart > 63) {
+        delete h;
+        return LS_EINVAL;
+    }
+    h->stream = static_cast<cudaStream_t>(stream);
+    int rc = LS_OK;
+    do {
+        if (cudaGetDevice(&h->device) != cudaSuccess) { rc = LS_ECUDA; break; }
+        const size_t N = (size_t)n * n;
+        if (cudaMalloc(&h->m64, sizeof(double) * N) != cudaSuccess ||
+            cudaMalloc(&h->m32, sizeof(float) * N) != cudaSuccess ||
+            cudaMalloc(&h->mT64, sizeof(double) * N) != cudaSuccess) {
+            rc = LS_ENOMEM;
+            break;
+        }
+        if (cudaMemcpyAsync(h->m64, m, sizeof(double) * N, cudaMemcpyDefault, h->stream) != cudaSuccess) {
+            rc = LS_ECUDA;
+            break;
+        }
+        k_real_to32<<<608, 256, 0, h->stream>>>(N, h->m64, h->m32);
+        h->launches++;
+        if ((rc = ls_transpose_real(h, h->m64, h->mT64)) != LS_OK) break;
+        if ((rc = ls_fft_init(h)) != LS_OK) break;
+        double2* gtab = nullptr;
+        if ((rc = ls_green_table(h, &gtab)) != LS_OK) break;
+        rc = ls_spectrum_build(h, gtab);
+        if (rc == LS_OK) rc = ls_stencils_build(h, gtab);
+        cudaFree(gtab);
+        if (rc != LS_OK) break;
+        if ((rc = ls_sweep_alloc(h)) != LS_OK) break;
+        if (cudaEventCreate(&h->ev0) != cudaSuccess || cudaEventCreate(&h->ev1) != cudaSuccess) {
+            rc = LS_ECUDA;
+            break;
+        }
+        if (cudaStreamSynchronize(h->stream) != cudaSuccess) { rc = LS_ECUDA; break; }
+    } while (0);
+    if (rc != LS_OK) {
+        release(h);
+        return rc;
+    }
+    *out = h;
+    return LS_OK;
+}
+
+int ls_factor(ls_handle* h) {
+    if (!h) return LS_EINVAL;
+    ls_factor_free(h);
+    h->factored = false;
+    const int rc = ls_factor_all(h);
+    if (rc != LS_OK) {
+        ls_factor_free(h);
+        return rc;
+    }
+    h->factored = true;
+    return LS_OK;
+}
+
+int ls_apply(ls_handle* h, const ls_c64* u, ls_c64* y) {
+    if (!h || !u || !y) return LS_EINVAL;
+    return ls_apply64(h, reinterpret_cast<const double2*>(u), reinterpret_cast<double2*>(y));
+}
+
+int ls_apply_f32(ls_handle* h, const ls_c32* u, ls_c32* y) {
+    if (!h || !u || !y) return LS_EINVAL;
+    return ls_apply32(h, reinterpret_cast<const float2*>(u), reinterpret_cast<float2*>(y));
+}
+
+int ls_incident_rhs(ls_handle* h, double theta, ls_c64* f) {
+    if (!h || !f || !std::isfinite(theta)) return LS_EINVAL;
+    return ls_rhs64(h, theta, reinterpret_cast<double2*>(f));
+}
+
+int ls_solve(ls_handle* h, const ls_c64* f, double tol, ls_c64* u, int use_x0, ls_stats* st) {
+    if (!h || !f || !u || !(tol > 0)) return LS_EINVAL;
+    if (!h->factored) return LS_ESTATE;
+    ls_stats local{};
+    ls_stats* s = st ? st : &local;
+    std::memset(s, 0, sizeof(*s));
+    h->t_apply_ms = h->t_sweep_ms = 0;
+    h->n_apply = h->n_sweep = 0;
+    const long long l0 = h->launches;
+    const auto t0 = std::chrono::steady_clock::now();
+    int rc = ls_outer_solve(h, reinterpret_cast<const double2*>(f), tol, reinterpret_cast<double2*>(u), use_x0, s);
+    if (cudaStreamSynchronize(h->stream) != cudaSuccess && rc == LS_OK) rc = ls_cuda_fail(cudaGetLastError());
+    s->t_solve_s = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    s->t_apply_ms = h->t_apply_ms;
+    s->n_apply = h->n_apply;
+    s->t_sweep_ms = h->t_sweep_ms;
+    s->n_sweep = h->n_sweep;
+    s->kernel_launches = h->launches - l0;
+    return rc;
+}
+
+int ls_solve_plane_wave(ls_handle* h, double theta, double tol, ls_c64* u, ls_stats* st) {
+    if (!h || !u) return LS_EINVAL;
+    if (!h->factored) return LS_ESTATE;
+    HostBufs* b = host_bufs(h, true);
+    if (!b) return LS_ENOMEM;
+    const size_t N = (size_t)h->n * h->n;
+    if (!b->f) LS_CUDA(cudaMalloc(&b->f, sizeof(double2) * N));
+    const long long l0 = h->launches;
+    LS_TRY(ls_rhs64(h, theta, b->f));
+    const long long extra = h->launches - l0;
+    const int rc = ls_solve(h, reinterpret_cast<const ls_c64*>(b->f), tol, u, 0, st);
+    if (st) st->kernel_launches += extra;
+    return rc;
+}
+
+int ls_solve_host(ls_handle* h, const ls_c64* f_host, double tol, ls_c64* u_host, ls_stats* st) {
+    if (!h || !f_host || !u_host) return LS_EINVAL;
+    if (!h->factored) return LS_ESTATE;
+    HostBufs* b = host_bufs(h, true);
+    if (!b) return LS_ENOMEM;
+    const size_t N = (size_t)h->n * h->n;
+    if (!b->f) LS_CUDA(cudaMalloc(&b->f, sizeof(double2) * N));
+    if (!b->u) LS_CUDA(cudaMalloc(&b->u, sizeof(double2) * N));
+    LS_CUDA(cudaMemcpyAsync(b->f, f_host, sizeof(double2) * N, cudaMemcpyHostToDevice, h->stream));
+    const int rc = ls_solve(h, reinterpret_cast<const ls_c64*>(b->f), tol, reinterpret_cast<ls_c64*>(b->u), 0, st);
+    if (rc != LS_OK && rc != LS_ENOCONV) return rc;
+    LS_CUDA(cudaMemcpyAsync(u_host, b->u, sizeof(double2) * N, cudaMemcpyDeviceToHost, h->stream));
+    LS_CUDA(cudaStreamSynchronize(h->stream));
+    return rc;
+}
+
+int ls_apply_A(ls_handle* h, const ls_c64* r, ls_c64* y) {
+    if (!h || !r || !y) return LS_EINVAL;
+    return ls_stencil_apply(h, 0, 0, reinterpret_cast<const double2*>(r), nullptr, reinterpret_cast<double2*>(y));
+}
+
+int ls_apply_C(ls_handle* h, const ls_c64* v, ls_c64* y) {
+    if (!h || !v || !y) return LS_EINVAL;
+    return ls_stencil_apply(h, 0, 1, reinterpret_cast<const double2*>(v), nullptr, reinterpret_cast<double2*>(y));
+}
+
+int ls_sweep(ls_handle* h, int dir, const ls_c64* g, ls_c64* v) {
+    if (!h || !g || !v || (dir != 0 && dir != 1)) return LS_EINVAL;
+    if (!h->factored) return LS_ESTATE;
+    return ls_sweep_dir(h, dir, reinterpret_cast<const double2*>(g), reinterpret_cast<double2*>(v));
+}
+
+int ls_precond_bd(ls_handle* h, const ls_c64* g, ls_c64* v) {
+    if (!h || !g || !v) return LS_EINVAL;
+    if (!h->factored) return LS_ESTATE;
+    return ls_bd(h, reinterpret_cast<const double2*>(g), reinterpret_cast<double2*>(v));
+}
+
+int ls_inner_solve(ls_handle* h, const ls_c64* g, double tol, ls_c64* v, int* iters) {
+    if (!h || !g || !v || !(tol > 0)) return LS_EINVAL;
+    if (!h->factored) return LS_ESTATE;
+    const int rc = ls_inner_gmres(h, reinterpret_cast<const double2*>(g), tol, reinterpret_cast<double2*>(v), iters);
+    if (cudaStreamSynchronize(h->stream) != cudaSuccess && rc == LS_OK) return ls_cuda_fail(cudaGetLastError());
+    return rc;
+}
+
+int ls_local_solve(ls_handle* h, int dir, int layer, const ls_c64* b, ls_c64* x) {
+    if (!h || !b || !x || (dir != 0 && dir != 1) || layer < 0 || layer >= h->L) return LS_EINVAL;
+    if (!h->factored) return LS_ESTATE;
+    return ls_strip_solve(h, dir, layer, reinterpret_cast<const double2*>(b), reinterpret_cast<double2*>(x));
+}
+
+int ls_get_stencils(ls_handle* h, ls_c64* alpha, ls_c64* beta) {
+    if (!h) return LS_EINVAL;
+    const double w2 = h->omega * h->omega;
+    for (int i = 0; i < 81; ++i) {
+        if (alpha) alpha[i] = ls_c64{h->tabs[0].alpha[i].x, h->tabs[0].alpha[i].y};
+        if (beta) beta[i] = ls_c64{h->tabs[0].wbeta[i].x / w2, h->tabs[0].wbeta[i].y / w2};
+    }
+    return LS_OK;
+}
+
+int ls_get_spectrum(ls_handle* h, ls_c64* ghat, int* P_out) {
+    if (!h) return LS_EINVAL;
+    if (P_out) *P_out = h->P;
+    if (ghat) {
+        const size_t q1 = (size_t)(h->P / 2 + 1);
+        LS_CUDA(cudaMemcpyAsync(ghat, h->ghat64, sizeof(double2) * q1 * q1, cudaMemcpyDeviceToDevice, h->stream));
+    }
+    return LS_OK;
+}
+
+int ls_get_diag_weight(ls_handle* h, ls_c64* w0) {
+    if (!h || !w0) return LS_EINVAL;
+    *w0 = ls_c64{h->w0.x, h->w0.y};
+    return LS_OK;
+}
+
+int ls_get_layout(ls_handle* h, int* t, int* q) {
+    if (!h) return LS_EINVAL;
+    if (t) *t = h->t;
+    if (q) *q = h->q;
+    return LS_OK;
+}
+
+int ls_set_timing(ls_handle* h, int on) {
+    if (!h) return LS_EINVAL;
+    h->timing = on != 0;
+    return LS_OK;
+}
+
+long long ls_kernel_count(ls_handle* h) { return h ? h->launches : -1; }
+
+void ls_destroy(ls_handle* h) { release(h); }
+
+}  // extern "C"

@@ -1,0 +1,488 @@
+// ls_fft.cu -- zero-padded FFT convolution: the LS-apply y = u + w^2 G (m u).
+//
+// Sec. 2 of the paper: G is translation invariant on the uniform grid, so the
+// dense quadrature matrix is a two-level Toeplitz matrix; embedding it in a
+// circulant of size P x P (P >= 2n - 1) turns G v into a cyclic convolution,
+// applied by FFT in O(N log N).  With Ghat = (w^2/P^2) FFT2(Gpad):
+//     H u = u + IFFT2(Ghat .* FFT2(pad(m u)))[0:n, 0:n]        (unnormalised IFFT)
+//
+// Three HBM passes (the minimum for a 2-D transform that does not fit on chip):
+//   pass 1 (rows)    read u, m; form m u; zero-pad to P; FFT along x; write n x P.
+//   pass 2 (columns) for a tile of CW columns kx: FFT along z (input zero-padded,
+//                    rows >= n skipped), multiply by Ghat(kx, kz) in registers,
+//                    inverse FFT along z, keep rows z < n; write n x P in place.
+//   pass 3 (rows)    inverse FFT along x, keep x < n, add u; write y.
+// Each transform is a Stockham autosort FFT held in shared memory: a thread
+// owns E elements of a transform, every stage loads its radix-R butterflies
+// into registers, twiddles them, runs an in-register DFT and stores them back.
+// The first stage of a transform reads straight from global memory and the
+// last stage writes straight to global memory, so each pass touches HBM once.
+// Ghat is even in both indices (G_w is even), so only its (P/2+1)^2 quadrant is
+// stored and read.
+#include <cmath>
+
+#include "ls_internal.cuh"
+
+namespace {
+
+// ---------------------------------------------------------------- DFT in registers
+template <typename R>
+__device__ __forceinline__ R cos16(int i) {  // cos(2 pi i / 16), i in [0, 8]
+    return i == 0 ? R(1) : i == 1 ? R(0.92387953251128675613) : i == 2 ? R(0.70710678118654752440)
+         : i == 3 ? R(0.38268343236508977173) : i == 4 ? R(0) : i == 5 ? R(-0.38268343236508977173)
+         : i == 6 ? R(-0.70710678118654752440) : i == 7 ? R(-0.92387953251128675613) : R(-1);
+}
+
+// d * exp(-DIR * 2 pi i idx / 16); idx is a compile-time constant after unrolling.
+template <int DIR, typename C>
+__device__ __forceinline__ C rot16(C d, int idx) {
+    using R = typename real_of<C>::type;
+    if (idx == 0) return d;
+    if (idx == 4) return DIR > 0 ? mkc(d.y, -d.x) : mkc(-d.y, d.x);
+    const R c = cos16<R>(idx);
+    const R s = cos16<R>(idx <= 4 ? 4 - idx : idx - 4);  // sin(2 pi idx / 16) for idx in [0, 8)
+    if (DIR > 0) return mkc(d.x * c + d.y * s, d.y * c - d.x * s);
+    return mkc(d.x * c - d.y * s, d.y * c + d.x * s);
+}
+
+template <int R>
+__host__ __device__ constexpr int brev(int k) {
+    int r = 0;
+    for (int b = 1; b < R; b <<= 1) r = (r << 1) | ((k & b) ? 1 : 0);
+    return r;
+}
+template <int R>
+__host__ __device__ constexpr int ilog2c() {
+    return R == 2 ? 1 : R == 4 ? 2 : R == 8 ? 3 : 4;
+}
+
+// Natural-order DFT of length R (2, 4, 8, 16): radix-2 decimation in frequency,
+// then the bit-reversal permutation.  DIR = +1: exp(-2 pi i nk/R); -1: conjugate.
+template <int R, int DIR, typename C>
+__device__ __forceinline__ void dft_reg(C* v) {
+#pragma unroll
+    for (int half = R / 2; half >= 1; half >>= 1) {
+#pragma unroll
+        for (int s = 0; s < R; s += 2 * half) {
+#pragma unroll
+            for (int k = 0; k < half; ++k) {
+                const C a = v[s + k], b = v[s + k + half];
+                v[s + k] = a + b;
+                v[s + k + half] = rot16<DIR>(a - b, k * (16 / (2 * half)));
+            }
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < R; ++k) {
+        const int r = brev<R>(k);
+        if (r > k) {
+            const C t = v[k];
+            v[k] = v[r];
+            v[r] = t;
+        }
+    }
+}
+
+// One Stockham stage on the E/R butterflies a thread owns: twiddle by
+// exp(-DIR 2 pi i k r / (Ns R)), k = b mod Ns, then the radix-R DFT.
+template <int R, int DIR, int E, typename C>
+__device__ __forceinline__ void stage_compute(C (&v)[E], int j, int TPC, int ls, int lp,
+                                              const C* __restrict__ tw) {
+    constexpr int LR = ilog2c<R>();
+#pragma unroll
+    for (int e = 0; e < E / R; ++e) {
+        if (ls > 0) {
+            const int b = j + e * TPC;
+            const int k = b & ((1 << ls) - 1);
+            const int sh = lp - ls - LR;
+#pragma unroll
+            for (int r = 1; r < R; ++r) {
+                C w = __ldg(&tw[(k * r) << sh]);
+                if (DIR < 0) w.y = -w.y;
+                v[e * R + r] = v[e * R + r] * w;
+            }
+        }
+        dft_reg<R, DIR>(&v[e * R]);
+    }
+}
+
+// A full transform of length P = plan.P.  On entry v holds the first stage's
+// inputs (element j + e*TPC + r*P/R0 in v[e*R0 + r]); on exit v holds the last
+// stage's outputs in the same form for the last radix.  buf: CW interleaved
+// transforms of length P in shared memory (element idx of column c at idx*CW + c).
+// The inverse (DIR = -1) runs the plan's stages in reverse order.
+template <int E, int DIR, int CW, int MAXR = 16, typename C>
+__device__ __forceinline__ void fft_core(C (&v)[E], C* buf, const FftPlan& pl, int j, int TPC, int c,
+                                         const C* __restrict__ tw) {
+    int ls = 0;
+    for (int s = 0; s < pl.ns; ++s) {
+        const int lr = pl.lr[DIR > 0 ? s : pl.ns - 1 - s];
+        if (s > 0) {
+#pragma unroll
+            for (int qq = 0; qq < E; ++qq) {
+                const int e = qq >> lr, r = qq & ((1 << lr) - 1);
+                const int idx = j + e * TPC + (r << (pl.lp - lr));
+                v[qq] = buf[idx * CW + c];
+            }
+        }
+        switch (lr) {
+            case 1: stage_compute<2, DIR>(v, j, TPC, ls, pl.lp, tw); break;
+            case 2: stage_compute<4, DIR>(v, j, TPC, ls, pl.lp, tw); break;
+            case 3:
+                if constexpr (E >= 8) stage_compute<8, DIR>(v, j, TPC, ls, pl.lp, tw);
+                break;
+            default:
+                if constexpr (E >= 16 && MAXR >= 16) stage_compute<16, DIR>(v, j, TPC, ls, pl.lp, tw);
+                break;
+        }
+        if (s < pl.ns - 1) {
+            __syncthreads();
+#pragma unroll
+            for (int qq = 0; qq < E; ++qq) {
+                const int e = qq >> lr, r = qq & ((1 << lr) - 1);
+                const int b = j + e * TPC;
+                const int dst = ((b >> ls) << (ls + lr)) + (b & ((1 << ls) - 1)) + (r << ls);
+                buf[dst * CW + c] = v[qq];
+            }
+            __syncthreads();
+        }
+        ls += lr;
+    }
+}
+
+// ---------------------------------------------------------------- pass-1 sources
+template <typename T, typename UIn>
+struct SrcMU {  // m u  (Sec. 2: D u)
+    const T* m;
+    const UIn* u;
+    int n;
+    template <typename C>
+    __device__ __forceinline__ C load(int z, int x) const {
+        const size_t i = (size_t)z * n + x;
+        return m[i] * ccast<C>(__ldg(&u[i]));
+    }
+};
+
+template <typename T>
+struct SrcInc {  // m u_I, u_I = exp(i w x cos) exp(i w z sin)  (Sec. 2: D u_I)
+    const T* m;
+    const double2* ex;
+    const double2* ez;
+    int n;
+    template <typename C>
+    __device__ __forceinline__ C load(int z, int x) const {
+        const double2 ui = __ldg(&ex[x]) * __ldg(&ez[z]);
+        return m[(size_t)z * n + x] * ccast<C>(ui);
+    }
+};
+
+struct SrcGpad {  // circulant embedding of G_w on the P x P torus (offsets |d| <= n-1)
+    const double2* gtab;  // G_w on [-n, n]^2, row-major by dz
+    int n, P;
+    template <typename C>
+    __device__ __forceinline__ C load(int b, int a) const {
+        const int at = a < P / 2 ? a : a - P;
+        const int bt = b < P / 2 ? b : b - P;
+        if (at > n - 1 || at < -(n - 1) || bt > n - 1 || bt < -(n - 1)) return czero<C>();
+        return ccast<C>(gtab[(size_t)(bt + n) * (2 * n + 1) + (at + n)]);
+    }
+};
+
+// ---------------------------------------------------------------- pass-3 sinks
+template <typename UIO>
+struct DstApply {  // y = u + (G-term)
+    const UIO* u;
+    UIO* y;
+    int n;
+    template <typename C>
+    __device__ __forceinline__ void store(int z, int x, C v) const {
+        const size_t i = (size_t)z * n + x;
+        y[i] = u[i] + ccast<UIO>(v);
+    }
+};
+
+struct DstRhs {  // f = -(G-term)
+    double2* f;
+    int n;
+    template <typename C>
+    __device__ __forceinline__ void store(int z, int x, C v) const {
+        f[(size_t)z * n + x] = -ccast<double2>(v);
+    }
+};
+
+// ---------------------------------------------------------------- kernels
+template <typename T, int E, class Src>
+__global__ void k_rows_fwd(FftPlan pl, int nin, Src src, cpx_t<T>* __restrict__ out,
+                           const cpx_t<T>* __restrict__ tw) {
+    using C = cpx_t<T>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* buf = reinterpret_cast<C*>(smem_raw);
+    const int z = blockIdx.x;
+    const int j = threadIdx.x, TPC = blockDim.x;
+    C v[E];
+    const int lr0 = pl.lr[0];
+#pragma unroll
+    for (int qq = 0; qq < E; ++qq) {
+        const int e = qq >> lr0, r = qq & ((1 << lr0) - 1);
+        const int x = j + e * TPC + (r << (pl.lp - lr0));
+        v[qq] = x < nin ? src.template load<C>(z, x) : czero<C>();
+    }
+    fft_core<E, +1, 1>(v, buf, pl, j, TPC, 0, tw);
+    const int lrl = pl.lr[pl.ns - 1];
+    C* o = out + (size_t)z * pl.P;
+#pragma unroll
+    for (int qq = 0; qq < E; ++qq) {
+        const int e = qq >> lrl, r = qq & ((1 << lrl) - 1);
+        o[j + e * TPC + (r << (pl.lp - lrl))] = v[qq];
+    }
+}
+
+// MODE 0: forward z-FFT, times Ghat, inverse z-FFT, rows < nout written back in place.
+// MODE 1: forward z-FFT only; the (P/2+1)^2 quadrant of qscale * result is written.
+template <typename T, int E, int CW, int MODE>
+__global__ void __launch_bounds__(512, 1) k_cols(FftPlan pl, int nin, int nout, cpx_t<T>* __restrict__ X,
+                       const cpx_t<T>* __restrict__ ghat, cpx_t<T>* __restrict__ quad, T qscale,
+                       const cpx_t<T>* __restrict__ tw) {
+    using C = cpx_t<T>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* buf = reinterpret_cast<C*>(smem_raw);
+    const int P = pl.P, lp = pl.lp;
+    const int ntile = P / CW;
+    const int b = blockIdx.x;
+    // mirror tiles (kx and P - kx read the same Ghat rows) run back to back
+    const int tile = (b & 1) ? (ntile - 1 - (b >> 1)) : (b >> 1);
+    const int c = threadIdx.x % CW, j = threadIdx.x / CW, TPC = blockDim.x / CW;
+    const int kx = tile * CW + c;
+    C v[E];
+    const int lr0 = pl.lr[0];
+#pragma unroll
+    for (int qq = 0; qq < E; ++qq) {
+        const int e = qq >> lr0, r = qq & ((1 << lr0) - 1);
+        const int z = j + e * TPC + (r << (lp - lr0));
+        v[qq] = z < nin ? X[(size_t)z * P + kx] : czero<C>();
+    }
+    fft_core<E, +1, CW, 8>(v, buf, pl, j, TPC, c, tw);
+    const int lrl = pl.lr[pl.ns - 1];
+    if constexpr (MODE == 0) {
+        const int kxq = kx <= P / 2 ? kx : P - kx;
+        const C* g = ghat + (size_t)kxq * (P / 2 + 1);
+#pragma unroll
+        for (int qq = 0; qq < E; ++qq) {
+            const int e = qq >> lrl, r = qq & ((1 << lrl) - 1);
+            const int kz = j + e * TPC + (r << (lp - lrl));
+            const int kzq = kz <= P / 2 ? kz : P - kz;
+            v[qq] = v[qq] * __ldg(&g[kzq]);
+        }
+        fft_core<E, -1, CW, 8>(v, buf, pl, j, TPC, c, tw);
+#pragma unroll
+        for (int qq = 0; qq < E; ++qq) {
+            const int e = qq >> lr0, r = qq & ((1 << lr0) - 1);
+            const int z = j + e * TPC + (r << (lp - lr0));
+            if (z < nout) X[(size_t)z * P + kx] = v[qq];
+        }
+    } else {
+        if (kx <= P / 2) {
+#pragma unroll
+            for (int qq = 0; qq < E; ++qq) {
+                const int e = qq >> lrl, r = qq & ((1 << lrl) - 1);
+                const int kz = j + e * TPC + (r << (lp - lrl));
+                if (kz <= P / 2) quad[(size_t)kx * (P / 2 + 1) + kz] = qscale * v[qq];
+            }
+        }
+    }
+}
+
+template <typename T, int E, class Dst>
+__global__ void k_rows_inv(FftPlan pl, int n, const cpx_t<T>* __restrict__ X, Dst dst,
+                           const cpx_t<T>* __restrict__ tw) {
+    using C = cpx_t<T>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* buf = reinterpret_cast<C*>(smem_raw);
+    const int z = blockIdx.x;
+    const int j = threadIdx.x, TPC = blockDim.x;
+    C v[E];
+    const int lrl = pl.lr[pl.ns - 1];
+    const C* xr = X + (size_t)z * pl.P;
+#pragma unroll
+    for (int qq = 0; qq < E; ++qq) {
+        const int e = qq >> lrl, r = qq & ((1 << lrl) - 1);
+        v[qq] = xr[j + e * TPC + (r << (pl.lp - lrl))];
+    }
+    fft_core<E, -1, 1>(v, buf, pl, j, TPC, 0, tw);
+    const int lr0 = pl.lr[0];
+#pragma unroll
+    for (int qq = 0; qq < E; ++qq) {
+        const int e = qq >> lr0, r = qq & ((1 << lr0) - 1);
+        const int x = j + e * TPC + (r << (pl.lp - lr0));
+        if (x < n) dst.template store<C>(z, x, v[qq]);
+    }
+}
+
+__global__ void k_twiddles(int P, double2* tw64, float2* tw32) {
+    const int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= P) return;
+    double s, c;
+    sincospi(2.0 * (double)m / (double)P, &s, &c);
+    tw64[m] = make_double2(c, -s);
+    tw32[m] = make_float2((float)c, (float)-s);
+}
+
+__global__ void k_incident_factors(int n, double wh, double cth, double sth, double2* ex, double2* ez) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double s, c;
+    sincos(wh * (double)(i + 1) * cth, &s, &c);
+    ex[i] = make_double2(c, s);
+    sincos(wh * (double)(i + 1) * sth, &s, &c);
+    ez[i] = make_double2(c, s);
+}
+
+__global__ void k_quad_to32(size_t cnt, const double2* a, float2* b) {
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < cnt) b[i] = ccast<float2>(a[i]);
+}
+
+// Elements per thread: row passes FP64 8 / FP32 16; column pass FP64 16 / FP32 32
+// (a column tile is CW transforms, so fewer threads keep the register file within
+// one 64K-register SM).  Column tiles are 2 (FP64) or 4 (FP32) columns: 32-byte
+// row segments either way.
+constexpr int E64 = 8, EC64 = 16, CW64 = 2;
+constexpr int E32 = 16, EC32 = 32, CW32 = 4;
+
+FftPlan make_plan(int lp, int lrmax) {
+    FftPlan p{};
+    p.P = 1 << lp;
+    p.lp = lp;
+    int left = lp;
+    while (left > 0) {
+        const int lr = left >= lrmax ? lrmax : left;
+        p.lr[p.ns++] = lr;
+        left -= lr;
+    }
+    return p;
+}
+
+template <typename K>
+int allow_smem(K kern, size_t bytes) {
+    if (bytes > 48 * 1024) LS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+    return LS_OK;
+}
+
+}  // namespace
+
+int ls_fft_init(ls_handle* h) {
+    const int P = h->P;
+    h->plan64 = make_plan(h->lp, 3);
+    h->plan32 = make_plan(h->lp, 4);
+    h->planc64 = make_plan(h->lp, 3);
+    h->planc32 = make_plan(h->lp, 3);
+    LS_CUDA(cudaMalloc(&h->tw64, sizeof(double2) * P));
+    LS_CUDA(cudaMalloc(&h->tw32, sizeof(float2) * P));
+    LS_CUDA(cudaMalloc(&h->fftws, sizeof(double2) * (size_t)h->n * P));
+    LS_CUDA(cudaMalloc(&h->incx, sizeof(double2) * h->n));
+    LS_CUDA(cudaMalloc(&h->incz, sizeof(double2) * h->n));
+    LS_LAUNCH(h, k_twiddles, (P + 255) / 256, 256, 0, P, h->tw64, h->tw32);
+    LS_TRY(allow_smem(k_cols<double, EC64, CW64, 0>, sizeof(double2) * CW64 * P));
+    LS_TRY(allow_smem(k_cols<double, EC64, CW64, 1>, sizeof(double2) * CW64 * P));
+    LS_TRY(allow_smem(k_cols<float, EC32, CW32, 0>, sizeof(float2) * CW32 * P));
+    LS_TRY(allow_smem(k_rows_fwd<double, E64, SrcMU<double, double2>>, sizeof(double2) * P));
+    LS_TRY(allow_smem(k_rows_fwd<double, E64, SrcInc<double>>, sizeof(double2) * P));
+    LS_TRY(allow_smem(k_rows_fwd<double, E64, SrcGpad>, sizeof(double2) * P));
+    LS_TRY(allow_smem(k_rows_inv<double, E64, DstApply<double2>>, sizeof(double2) * P));
+    LS_TRY(allow_smem(k_rows_inv<double, E64, DstRhs>, sizeof(double2) * P));
+    LS_TRY(allow_smem(k_rows_fwd<float, E32, SrcMU<float, float2>>, sizeof(float2) * P));
+    LS_TRY(allow_smem(k_rows_fwd<float, E32, SrcMU<float, double2>>, sizeof(float2) * P));
+    LS_TRY(allow_smem(k_rows_inv<float, E32, DstApply<float2>>, sizeof(float2) * P));
+    LS_TRY(allow_smem(k_rows_inv<float, E32, DstApply<double2>>, sizeof(float2) * P));
+    return LS_OK;
+}
+
+int ls_spectrum_build(ls_handle* h, const double2* gtab) {
+    const int P = h->P, n = h->n;
+    const FftPlan& pl = h->plan64;
+    double2* work = nullptr;
+    const size_t q1 = (size_t)(P / 2 + 1);
+    LS_CUDA(cudaMalloc(&work, sizeof(double2) * (size_t)P * P));
+    LS_CUDA(cudaMalloc(&h->ghat64, sizeof(double2) * q1 * q1));
+    LS_CUDA(cudaMalloc(&h->ghat32, sizeof(float2) * q1 * q1));
+    int rc = LS_OK;
+    do {
+        SrcGpad src{gtab, n, P};
+        k_rows_fwd<double, E64, SrcGpad><<<P, P / E64, sizeof(double2) * P, h->stream>>>(pl, P, src, work, h->tw64);
+        h->launches++;
+        const double qscale = h->omega * h->omega / ((double)P * (double)P);
+        k_cols<double, EC64, CW64, 1><<<P / CW64, CW64 * (P / EC64), sizeof(double2) * CW64 * P, h->stream>>>(
+            h->planc64, P, P, work, nullptr, h->ghat64, qscale, h->tw64);
+        h->launches++;
+        const size_t cnt = q1 * q1;
+        k_quad_to32<<<(unsigned)((cnt + 255) / 256), 256, 0, h->stream>>>(cnt, h->ghat64, h->ghat32);
+        h->launches++;
+        cudaError_t e = cudaPeekAtLastError();
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+        if (e != cudaSuccess) rc = ls_cuda_fail(e);
+    } while (0);
+    cudaFree(work);
+    return rc;
+}
+
+int ls_apply64(ls_handle* h, const double2* u, double2* y) {
+    const int n = h->n, P = h->P;
+    const FftPlan& pl = h->plan64;
+    double2* X = static_cast<double2*>(h->fftws);
+    SrcMU<double, double2> src{h->m64, u, n};
+    LS_LAUNCH(h, (k_rows_fwd<double, E64, SrcMU<double, double2>>), n, P / E64, sizeof(double2) * P,
+              pl, n, src, X, h->tw64);
+    LS_LAUNCH(h, (k_cols<double, EC64, CW64, 0>), P / CW64, CW64 * (P / EC64), sizeof(double2) * CW64 * P,
+              h->planc64, n, n, X, h->ghat64, (double2*)nullptr, 0.0, h->tw64);
+    DstApply<double2> dst{u, y, n};
+    LS_LAUNCH(h, (k_rows_inv<double, E64, DstApply<double2>>), n, P / E64, sizeof(double2) * P,
+              pl, n, X, dst, h->tw64);
+    return LS_OK;
+}
+
+int ls_apply32(ls_handle* h, const float2* u, float2* y) {
+    const int n = h->n, P = h->P;
+    const FftPlan& pl = h->plan32;
+    float2* X = static_cast<float2*>(h->fftws);
+    SrcMU<float, float2> src{h->m32, u, n};
+    LS_LAUNCH(h, (k_rows_fwd<float, E32, SrcMU<float, float2>>), n, P / E32, sizeof(float2) * P,
+              pl, n, src, X, h->tw32);
+    LS_LAUNCH(h, (k_cols<float, EC32, CW32, 0>), P / CW32, CW32 * (P / EC32), sizeof(float2) * CW32 * P,
+              h->planc32, n, n, X, h->ghat32, (float2*)nullptr, 0.0f, h->tw32);
+    DstApply<float2> dst{u, y, n};
+    LS_LAUNCH(h, (k_rows_inv<float, E32, DstApply<float2>>), n, P / E32, sizeof(float2) * P,
+              pl, n, X, dst, h->tw32);
+    return LS_OK;
+}
+
+int ls_apply_mixed(ls_handle* h, const double2* u, double2* y) {
+    const int n = h->n, P = h->P;
+    const FftPlan& pl = h->plan32;
+    float2* X = static_cast<float2*>(h->fftws);
+    SrcMU<float, double2> src{h->m32, u, n};
+    LS_LAUNCH(h, (k_rows_fwd<float, E32, SrcMU<float, double2>>), n, P / E32, sizeof(float2) * P,
+              pl, n, src, X, h->tw32);
+    LS_LAUNCH(h, (k_cols<float, EC32, CW32, 0>), P / CW32, CW32 * (P / EC32), sizeof(float2) * CW32 * P,
+              h->planc32, n, n, X, h->ghat32, (float2*)nullptr, 0.0f, h->tw32);
+    DstApply<double2> dst{u, y, n};
+    LS_LAUNCH(h, (k_rows_inv<float, E32, DstApply<double2>>), n, P / E32, sizeof(float2) * P,
+              pl, n, X, dst, h->tw32);
+    return LS_OK;
+}
+
+int ls_rhs64(ls_handle* h, double theta, double2* f) {
+    const int n = h->n, P = h->P;
+    const FftPlan& pl = h->plan64;
+    double2* X = static_cast<double2*>(h->fftws);
+    LS_LAUNCH(h, k_incident_factors, (n + 255) / 256, 256, 0, n, h->omega * h->h, std::cos(theta),
+              std::sin(theta), h->incx, h->incz);
+    SrcInc<double> src{h->m64, h->incx, h->incz, n};
+    LS_LAUNCH(h, (k_rows_fwd<double, E64, SrcInc<double>>), n, P / E64, sizeof(double2) * P,
+              pl, n, src, X, h->tw64);
+    LS_LAUNCH(h, (k_cols<double, EC64, CW64, 0>), P / CW64, CW64 * (P / EC64), sizeof(double2) * CW64 * P,
+              h->planc64, n, n, X, h->ghat64, (double2*)nullptr, 0.0, h->tw64);
+    DstRhs dst{f, n};
+    LS_LAUNCH(h, (k_rows_inv<double, E64, DstRhs>), n, P / E64, sizeof(double2) * P, pl, n, X, dst, h->tw64);
+    return LS_OK;
+}
+

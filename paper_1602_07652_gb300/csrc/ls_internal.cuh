@@ -1,0 +1,220 @@
+// ls_internal.cuh -- shared definitions of the GB300 Lippmann-Schwinger library.
+//
+// Complex helpers, the handle, launch bookkeeping and the declarations that the
+// translation units (FFT convolution, stencils, factorisation, sweeps, Krylov,
+// C ABI) share.  Everything here is device code or plain host C++; no torch.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+#include <vector>
+
+#include "ls.h"
+
+// ------------------------------------------------------------------ complex
+template <typename T> struct cpx;
+template <> struct cpx<float> { using type = float2; };
+template <> struct cpx<double> { using type = double2; };
+template <typename T> using cpx_t = typename cpx<T>::type;
+
+template <typename C> struct real_of;
+template <> struct real_of<float2> { using type = float; };
+template <> struct real_of<double2> { using type = double; };
+
+__host__ __device__ __forceinline__ float2 mkc(float a, float b) { return make_float2(a, b); }
+__host__ __device__ __forceinline__ double2 mkc(double a, double b) { return make_double2(a, b); }
+template <typename C> __host__ __device__ __forceinline__ C czero();
+template <> __host__ __device__ __forceinline__ float2 czero<float2>() { return make_float2(0.f, 0.f); }
+template <> __host__ __device__ __forceinline__ double2 czero<double2>() { return make_double2(0.0, 0.0); }
+
+#define LS_CPX_OPS(C, R)                                                                          \
+    __host__ __device__ __forceinline__ C operator+(C a, C b) { return mkc(a.x + b.x, a.y + b.y); } \
+    __host__ __device__ __forceinline__ C operator-(C a, C b) { return mkc(a.x - b.x, a.y - b.y); } \
+    __host__ __device__ __forceinline__ C operator-(C a) { return mkc(-a.x, -a.y); }               \
+    __host__ __device__ __forceinline__ C operator*(C a, C b) {                                    \
+        return mkc(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);                                  \
+    }                                                                                              \
+    __host__ __device__ __forceinline__ C operator*(R s, C a) { return mkc(s * a.x, s * a.y); }     \
+    __host__ __device__ __forceinline__ C conj(C a) { return mkc(a.x, -a.y); }                     \
+    __host__ __device__ __forceinline__ R cabs2(C a) { return a.x * a.x + a.y * a.y; }             \
+    __host__ __device__ __forceinline__ C cfma(C a, C b, C c) { /* a*b + c */                      \
+        return mkc(fma(a.x, b.x, fma(-a.y, b.y, c.x)), fma(a.x, b.y, fma(a.y, b.x, c.y)));          \
+    }                                                                                              \
+    __host__ __device__ __forceinline__ C cfms(C a, C b, C c) { /* c - a*b */                      \
+        return mkc(fma(-a.x, b.x, fma(a.y, b.y, c.x)), fma(-a.x, b.y, fma(-a.y, b.x, c.y)));        \
+    }                                                                                              \
+    __host__ __device__ __forceinline__ C cconjmul_acc(C a, C b, C c) { /* conj(a)*b + c */        \
+        return mkc(fma(a.x, b.x, fma(a.y, b.y, c.x)), fma(a.x, b.y, fma(-a.y, b.x, c.y)));          \
+    }
+
+LS_CPX_OPS(float2, float)
+LS_CPX_OPS(double2, double)
+#undef LS_CPX_OPS
+
+template <typename D, typename S> __host__ __device__ __forceinline__ D ccast(S a);
+template <> __host__ __device__ __forceinline__ float2 ccast<float2, float2>(float2 a) { return a; }
+template <> __host__ __device__ __forceinline__ double2 ccast<double2, double2>(double2 a) { return a; }
+template <> __host__ __device__ __forceinline__ float2 ccast<float2, double2>(double2 a) {
+    return make_float2((float)a.x, (float)a.y);
+}
+template <> __host__ __device__ __forceinline__ double2 ccast<double2, float2>(float2 a) {
+    return make_double2((double)a.x, (double)a.y);
+}
+
+// ------------------------------------------------------------------ FFT plan
+// Stockham stages: log2 radix of each stage in forward order (inverse runs them reversed).
+struct FftPlan {
+    int P;       // transform length (power of two)
+    int lp;      // log2 P
+    int ns;      // number of stages
+    int lr[8];   // log2 radix per stage
+};
+
+// ------------------------------------------------------------------ stencils
+// 9 point types x 9 slots; type = (bz+1)*3 + (bx+1), slot = (dz+1)*3 + (dx+1).
+struct StencilTables {
+    double2 alpha[81];
+    double2 wbeta[81];   // w^2 * beta
+};
+
+// ------------------------------------------------------------------ CR factors
+// Block cyclic reduction of one direction's L strips.  Block tridiagonal along
+// the long axis (n blocks of q x q), levels k = 0..K-1 eliminate the odd blocks
+// j of level k (global block index i = j << k); level K holds one block.
+// All dense matrices are stored column-major (element (r, c) at c*q + r).
+struct CrLevel {
+    int nk;          // blocks at this level
+    int nodd;        // odd blocks: nk / 2
+    int neven;       // even blocks: (nk + 1) / 2
+    // offsets (in matrices of q*q elements) into the factor pool, per strip
+    size_t off_dinv;  // nodd matrices: D^{-1} of odd blocks
+    size_t off_p;     // k >= 1: nodd matrices P = D^{-1} W
+    size_t off_q;     // k >= 1: nodd matrices Q = D^{-1} E
+    size_t off_f;     // k >= 1: neven matrices F = W_j D^{-1}_{j-1} (zero if j == 0)
+    size_t off_g;     // k >= 1: neven matrices G = E_j D^{-1}_{j+1} (zero if j+1 == nk)
+};
+
+struct DirFactors {
+    int K = 0;                    // levels
+    std::vector<CrLevel> lev;     // K entries
+    size_t off_top = 0;           // D^{-1} of the single block of level K
+    size_t mats_per_strip = 0;    // matrices per strip in the pool
+    double2* pool64 = nullptr;    // L * mats_per_strip * q*q (FP64; freed in LS_MIXED)
+    float2* pool32 = nullptr;     // same layout in FP32 (LS_MIXED)
+    // problem of this direction (the vertical direction is the transposed grid)
+    const double* m = nullptr;    // medium of this direction's grid (n x n, long axis fastest)
+    StencilTables* tab = nullptr; // device copy of the tables of this direction
+    StencilTables host_tab;
+};
+
+// ------------------------------------------------------------------ handle
+struct ls_handle {
+    int n = 0, L = 0, E = 0, t = 0, q = 0, P = 0, lp = 0, prec = LS_FP64;
+    double h = 0, omega = 0;
+    ls_opts opts{};
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    long long launches = 0;
+    bool factored = false;
+    bool timing = false;
+
+    double* m64 = nullptr;     // medium, n*n
+    float* m32 = nullptr;
+    double* mT64 = nullptr;    // transposed medium
+
+    double2 w0{};              // diagonal weight G_w(0)
+    double2* ghat64 = nullptr; // spectral quadrant (P/2+1)^2
+    float2* ghat32 = nullptr;
+    double2* tw64 = nullptr;   // twiddles exp(-2 pi i m / P), m < P
+    float2* tw32 = nullptr;
+    FftPlan plan64{}, plan32{};    // row passes
+    FftPlan planc64{}, planc32{};  // column pass
+    void* fftws = nullptr;     // n*P complex (FP64 size)
+    double2* incx = nullptr;   // incident-wave factors exp(i w h (i+1) cos), exp(i w h (j+1) sin)
+    double2* incz = nullptr;
+
+    StencilTables tabs[2];     // host copies: [0] grid, [1] transposed grid
+    StencilTables* dtabs = nullptr;  // device copies (2)
+
+    DirFactors fac[2];
+    // sweep buffers per direction: rhs and solution of every strip (n*q each)
+    void* srhs = nullptr;
+    void* ssol = nullptr;
+    void* vtmp = nullptr;      // n*n complex scratch (FP64) for transposes
+    void* vtmp2 = nullptr;
+
+    // Krylov workspaces (FP64)
+    double2* kry = nullptr;    // pool of N-vectors
+    int kry_vectors = 0;
+    double* red = nullptr;     // reduction partials
+    double* red_host = nullptr;
+    size_t red_cap = 0;
+
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    double t_apply_ms = 0, t_sweep_ms = 0;
+    int n_apply = 0, n_sweep = 0;
+};
+
+// ------------------------------------------------------------------ errors
+#define LS_CUDA(call)                                    \
+    do {                                                 \
+        cudaError_t e_ = (call);                         \
+        if (e_ != cudaSuccess) return ls_cuda_fail(e_);  \
+    } while (0)
+
+#define LS_TRY(call)                     \
+    do {                                 \
+        int rc_ = (call);                \
+        if (rc_ != LS_OK) return rc_;    \
+    } while (0)
+
+int ls_cuda_fail(cudaError_t e);
+
+// launch + bookkeeping; returns LS_ECUDA from the enclosing function on failure
+#define LS_LAUNCH(hdl, kern, grid, block, smem, ...)                                   \
+    do {                                                                               \
+        kern<<<(grid), (block), (smem), (hdl)->stream>>>(__VA_ARGS__);                 \
+        (hdl)->launches++;                                                             \
+        cudaError_t e_ = cudaPeekAtLastError();                                        \
+        if (e_ != cudaSuccess) return ls_cuda_fail(e_);                                \
+    } while (0)
+
+// ------------------------------------------------------------------ internal API
+// FFT convolution (ls_fft.cu)
+int ls_fft_init(ls_handle* h);                                   // twiddles, plans, workspace
+int ls_spectrum_build(ls_handle* h, const double2* gtab);       // Ghat from the G_w table
+int ls_apply64(ls_handle* h, const double2* u, double2* y);     // y = H u (FP64)
+int ls_apply32(ls_handle* h, const float2* u, float2* y);       // y = H u (FP32)
+int ls_apply_mixed(ls_handle* h, const double2* u, double2* y); // FP64 I/O, FP32 arithmetic
+int ls_rhs64(ls_handle* h, double theta, double2* f);           // f = -w^2 G (m u_I)
+
+// setup (ls_setup_kernels.cu)
+int ls_green_table(ls_handle* h, double2** gtab_out);          // G_w on [-n, n]^2 (device)
+int ls_stencils_build(ls_handle* h, const double2* gtab);      // alpha, beta for both grids
+
+// stencils + vector kernels (ls_stencil.cu)
+int ls_stencil_apply(ls_handle* h, int dir, int withm, const double2* v, const double2* g, double2* y);
+int ls_transpose64(ls_handle* h, const double2* a, double2* b);
+int ls_vec_dots(ls_handle* h, int nvec, const double2* V, size_t ld, const double2* w, double2* out_host);
+int ls_vec_update(ls_handle* h, int nvec, const double2* V, size_t ld, const double2* coef_dev, double2* w);
+int ls_vec_norm(ls_handle* h, const double2* w, double* out_host);
+int ls_vec_axpby(ls_handle* h, double2 a, const double2* x, double2 b, double2* y);  // y = a x + b y
+int ls_vec_copy(ls_handle* h, const double2* x, double2* y);
+int ls_vec_zero(ls_handle* h, double2* y);
+int ls_vec_combine(ls_handle* h, int nvec, const double2* Z, size_t ld, const double2* coef_host, double2* x);
+
+// factorisation (ls_factor.cu)
+int ls_factor_all(ls_handle* h);
+void ls_factor_free(ls_handle* h);
+
+// sweeps (ls_sweep.cu)
+int ls_sweep_alloc(ls_handle* h);
+int ls_sweep_dir(ls_handle* h, int dir, const double2* g, double2* v);   // Algorithm 1
+int ls_bd(ls_handle* h, const double2* g, double2* v);                   // Algorithm 2
+int ls_strip_solve(ls_handle* h, int dir, int layer, const double2* b, double2* x);
+
+// Krylov (ls_krylov.cu)
+int ls_inner_gmres(ls_handle* h, const double2* g, double tol, double2* v, int* iters);
+int ls_outer_solve(ls_handle* h, const double2* f, double tol, double2* u, int use_x0, ls_stats* st);

@@ -1,0 +1,263 @@
+// ls_stencil.cu -- 9-point stencil applies (Sec. 2) and FP64 vector kernels.
+//
+//  * (A r)_k = sum_{d in mu(k)} alpha^{t(k)}_d r_{k+d}                   (sparsifying matrix)
+//  * (C v)_k = sum_{d in mu(k)} (alpha^{t(k)}_d + w^2 beta^{t(k)}_d m_{k+d}) v_{k+d}
+//    (A H kept on the pattern of A, Sec. 2); t(k) is the point type (interior,
+//    edge, corner) and mu(k) drops offsets that leave Omega.
+//  * e = g - C v is the iterative-refinement residual of Algorithm 2.
+// One thread per grid point, x fastest, so neighbour loads along x coalesce and
+// the z-neighbours come from L1/L2; the stencil tables sit in shared memory.
+//
+// Vector kernels for the Krylov levels (Sec. 4) accumulate in FP64 with a fixed
+// reduction order (block partials, then one block), so results are reproducible.
+#include "ls_internal.cuh"
+
+namespace {
+
+template <int MODE>  // 0: y = A v   1: y = C v   2: y = g - C v
+__global__ void k_stencil(int n, const StencilTables* __restrict__ tab, const double* __restrict__ m,
+                          const double2* __restrict__ v, const double2* __restrict__ g, double2* __restrict__ y) {
+    __shared__ double2 sa[81], sb[81];
+    for (int i = threadIdx.x; i < 81; i += blockDim.x) {
+        sa[i] = tab->alpha[i];
+        sb[i] = tab->wbeta[i];
+    }
+    __syncthreads();
+    const size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= (size_t)n * n) return;
+    const int i = (int)(k % n), j = (int)(k / n);
+    const int bx = i == 0 ? -1 : (i == n - 1 ? 1 : 0);
+    const int bz = j == 0 ? -1 : (j == n - 1 ? 1 : 0);
+    const int t = (bz + 1) * 3 + (bx + 1);
+    double2 acc = make_double2(0, 0);
+#pragma unroll
+    for (int dz = -1; dz <= 1; ++dz) {
+        if ((bz == -1 && dz == -1) || (bz == 1 && dz == 1)) continue;
+#pragma unroll
+        for (int dx = -1; dx <= 1; ++dx) {
+            if ((bx == -1 && dx == -1) || (bx == 1 && dx == 1)) continue;
+            const int s = (dz + 1) * 3 + (dx + 1);
+            const size_t p = k + (long long)dz * n + dx;
+            double2 c = sa[t * 9 + s];
+            if (MODE >= 1) {
+                const double mm = __ldg(&m[p]);
+                c = mkc(fma(mm, sb[t * 9 + s].x, c.x), fma(mm, sb[t * 9 + s].y, c.y));
+            }
+            acc = cfma(c, __ldg(&v[p]), acc);
+        }
+    }
+    if (MODE == 2) acc = __ldg(&g[k]) - acc;
+    y[k] = acc;
+}
+
+__global__ void k_transpose(int n, const double2* __restrict__ a, double2* __restrict__ b) {
+    __shared__ double2 tile[32][33];
+    const int x0 = blockIdx.x * 32, z0 = blockIdx.y * 32;
+    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+        const int z = z0 + r, x = x0 + threadIdx.x;
+        if (z < n && x < n) tile[r][threadIdx.x] = a[(size_t)z * n + x];
+    }
+    __syncthreads();
+    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+        const int x = x0 + r, z = z0 + threadIdx.x;
+        if (z < n && x < n) b[(size_t)x * n + z] = tile[threadIdx.x][r];
+    }
+}
+
+__global__ void k_transpose_real(int n, const double* __restrict__ a, double* __restrict__ b) {
+    __shared__ double tile[32][33];
+    const int x0 = blockIdx.x * 32, z0 = blockIdx.y * 32;
+    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+        const int z = z0 + r, x = x0 + threadIdx.x;
+        if (z < n && x < n) tile[r][threadIdx.x] = a[(size_t)z * n + x];
+    }
+    __syncthreads();
+    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+        const int x = x0 + r, z = z0 + threadIdx.x;
+        if (z < n && x < n) b[(size_t)x * n + z] = tile[threadIdx.x][r];
+    }
+}
+
+constexpr int RED_BLOCKS = 608;   // 4 x 152 SMs
+constexpr int RED_THREADS = 256;
+
+// partial[b * nvec + i] = sum over block b's elements of conj(V_i) w   (i < nvec)
+__global__ void k_dots(size_t N, int nvec, const double2* __restrict__ V, size_t ld,
+                       const double2* __restrict__ w, double2* __restrict__ partial) {
+    __shared__ double2 red[RED_THREADS];
+    for (int i = 0; i < nvec; ++i) {
+        const double2* vi = V + (size_t)i * ld;
+        double2 acc = make_double2(0, 0);
+        for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < N; k += (size_t)gridDim.x * blockDim.x)
+            acc = cconjmul_acc(__ldg(&vi[k]), __ldg(&w[k]), acc);
+        red[threadIdx.x] = acc;
+        __syncthreads();
+        for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+            if (threadIdx.x < s) red[threadIdx.x] = red[threadIdx.x] + red[threadIdx.x + s];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) partial[(size_t)blockIdx.x * nvec + i] = red[0];
+        __syncthreads();
+    }
+}
+
+// out[i] = sum_b partial[b * nvec + i]  (one block, fixed order)
+__global__ void k_dots_final(int nblk, int nvec, const double2* __restrict__ partial, double2* __restrict__ out) {
+    __shared__ double2 red[RED_THREADS];
+    for (int i = 0; i < nvec; ++i) {
+        double2 acc = make_double2(0, 0);
+        for (int b = threadIdx.x; b < nblk; b += blockDim.x) acc = acc + partial[(size_t)b * nvec + i];
+        red[threadIdx.x] = acc;
+        __syncthreads();
+        for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+            if (threadIdx.x < s) red[threadIdx.x] = red[threadIdx.x] + red[threadIdx.x + s];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) out[i] = red[0];
+        __syncthreads();
+    }
+}
+
+// w -= sum_i coef[i] V_i
+__global__ void k_update(size_t N, int nvec, const double2* __restrict__ V, size_t ld,
+                         const double2* __restrict__ coef, double2* __restrict__ w) {
+    __shared__ double2 sc[128];
+    for (int i = threadIdx.x; i < nvec; i += blockDim.x) sc[i] = coef[i];
+    __syncthreads();
+    for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < N; k += (size_t)gridDim.x * blockDim.x) {
+        double2 acc = w[k];
+        for (int i = 0; i < nvec; ++i) acc = cfms(sc[i], __ldg(&V[(size_t)i * ld + k]), acc);
+        w[k] = acc;
+    }
+}
+
+struct Coefs {
+    double2 c[64];
+};
+// x += sum_i c_i Z_i
+__global__ void k_combine(size_t N, int nvec, const double2* __restrict__ Z, size_t ld, Coefs cf,
+                          double2* __restrict__ x) {
+    for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < N; k += (size_t)gridDim.x * blockDim.x) {
+        double2 acc = x[k];
+        for (int i = 0; i < nvec; ++i) acc = cfma(cf.c[i], __ldg(&Z[(size_t)i * ld + k]), acc);
+        x[k] = acc;
+    }
+}
+
+__global__ void k_axpby(size_t N, double2 a, const double2* __restrict__ x, double2 b, double2* __restrict__ y) {
+    for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < N; k += (size_t)gridDim.x * blockDim.x)
+        y[k] = a * x[k] + b * y[k];
+}
+
+__global__ void k_copy(size_t N, const double2* __restrict__ x, double2* __restrict__ y) {
+    for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < N; k += (size_t)gridDim.x * blockDim.x)
+        y[k] = x[k];
+}
+
+__global__ void k_zero(size_t N, double2* __restrict__ y) {
+    for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < N; k += (size_t)gridDim.x * blockDim.x)
+        y[k] = make_double2(0, 0);
+}
+
+}  // namespace
+
+int ls_stencil_apply(ls_handle* h, int dir, int mode, const double2* v, const double2* g, double2* y) {
+    const int n = h->n;
+    const size_t N = (size_t)n * n;
+    const unsigned nb = (unsigned)((N + 255) / 256);
+    const double* m = dir == 0 ? h->m64 : h->mT64;
+    const StencilTables* tab = h->dtabs + dir;
+    if (mode == 0) LS_LAUNCH(h, k_stencil<0>, nb, 256, 0, n, tab, m, v, g, y);
+    else if (mode == 1) LS_LAUNCH(h, k_stencil<1>, nb, 256, 0, n, tab, m, v, g, y);
+    else LS_LAUNCH(h, k_stencil<2>, nb, 256, 0, n, tab, m, v, g, y);
+    return LS_OK;
+}
+
+int ls_transpose64(ls_handle* h, const double2* a, double2* b) {
+    const int n = h->n;
+    dim3 grid((n + 31) / 32, (n + 31) / 32), block(32, 8);
+    LS_LAUNCH(h, k_transpose, grid, block, 0, n, a, b);
+    return LS_OK;
+}
+
+int ls_transpose_real(ls_handle* h, const double* a, double* b) {
+    const int n = h->n;
+    dim3 grid((n + 31) / 32, (n + 31) / 32), block(32, 8);
+    LS_LAUNCH(h, k_transpose_real, grid, block, 0, n, a, b);
+    return LS_OK;
+}
+
+static int red_reserve(ls_handle* h, size_t cnt) {
+    if (h->red_cap >= cnt) return LS_OK;
+    if (h->red) cudaFree(h->red);
+    if (h->red_host) cudaFreeHost(h->red_host);
+    h->red = nullptr;
+    h->red_host = nullptr;
+    LS_CUDA(cudaMalloc(&h->red, cnt * sizeof(double2)));
+    LS_CUDA(cudaMallocHost(&h->red_host, cnt * sizeof(double2)));
+    h->red_cap = cnt;
+    return LS_OK;
+}
+
+// dots into device memory out_dev[0..nvec)
+int ls_vec_dots_dev(ls_handle* h, int nvec, const double2* V, size_t ld, const double2* w, double2* out_dev) {
+    const size_t N = (size_t)h->n * h->n;
+    LS_TRY(red_reserve(h, (size_t)RED_BLOCKS * 64 + 256));
+    double2* partial = reinterpret_cast<double2*>(h->red);
+    LS_LAUNCH(h, k_dots, RED_BLOCKS, RED_THREADS, 0, N, nvec, V, ld, w, partial);
+    LS_LAUNCH(h, k_dots_final, 1, RED_THREADS, 0, RED_BLOCKS, nvec, partial, out_dev);
+    return LS_OK;
+}
+
+int ls_vec_dots(ls_handle* h, int nvec, const double2* V, size_t ld, const double2* w, double2* out_host) {
+    LS_TRY(red_reserve(h, (size_t)RED_BLOCKS * 64 + 256));
+    double2* outd = reinterpret_cast<double2*>(h->red) + (size_t)RED_BLOCKS * 64;
+    LS_TRY(ls_vec_dots_dev(h, nvec, V, ld, w, outd));
+    LS_CUDA(cudaMemcpyAsync(h->red_host, outd, sizeof(double2) * nvec, cudaMemcpyDeviceToHost, h->stream));
+    LS_CUDA(cudaStreamSynchronize(h->stream));
+    const double2* hr = reinterpret_cast<const double2*>(h->red_host);
+    for (int i = 0; i < nvec; ++i) out_host[i] = hr[i];
+    return LS_OK;
+}
+
+int ls_vec_update(ls_handle* h, int nvec, const double2* V, size_t ld, const double2* coef_dev, double2* w) {
+    const size_t N = (size_t)h->n * h->n;
+    LS_LAUNCH(h, k_update, RED_BLOCKS, RED_THREADS, 0, N, nvec, V, ld, coef_dev, w);
+    return LS_OK;
+}
+
+int ls_vec_norm(ls_handle* h, const double2* w, double* out_host) {
+    double2 d;
+    LS_TRY(ls_vec_dots(h, 1, w, 0, w, &d));
+    *out_host = sqrt(d.x > 0 ? d.x : 0.0);
+    return LS_OK;
+}
+
+int ls_vec_combine(ls_handle* h, int nvec, const double2* Z, size_t ld, const double2* coef_host, double2* x) {
+    const size_t N = (size_t)h->n * h->n;
+    for (int base = 0; base < nvec; base += 64) {
+        Coefs cf;
+        const int cnt = nvec - base < 64 ? nvec - base : 64;
+        for (int i = 0; i < cnt; ++i) cf.c[i] = coef_host[base + i];
+        LS_LAUNCH(h, k_combine, RED_BLOCKS, RED_THREADS, 0, N, cnt, Z + (size_t)base * ld, ld, cf, x);
+    }
+    return LS_OK;
+}
+
+int ls_vec_axpby(ls_handle* h, double2 a, const double2* x, double2 b, double2* y) {
+    const size_t N = (size_t)h->n * h->n;
+    LS_LAUNCH(h, k_axpby, RED_BLOCKS, RED_THREADS, 0, N, a, x, b, y);
+    return LS_OK;
+}
+
+int ls_vec_copy(ls_handle* h, const double2* x, double2* y) {
+    const size_t N = (size_t)h->n * h->n;
+    LS_LAUNCH(h, k_copy, RED_BLOCKS, RED_THREADS, 0, N, x, y);
+    return LS_OK;
+}
+
+int ls_vec_zero(ls_handle* h, double2* y) {
+    const size_t N = (size_t)h->n * h->n;
+    LS_LAUNCH(h, k_zero, RED_BLOCKS, RED_THREADS, 0, N, y);
+    return LS_OK;
+}

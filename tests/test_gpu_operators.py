@@ -1,0 +1,181 @@
+"""GPU parity of the operators (LS-apply, spectrum, stencils, local solves, sweeps) vs the oracle.
+
+Every test runs the CUDA path through the C ABI (binding.Solver) and compares it
+element by element with the FP64 oracle on the same seeded inputs.
+Tolerances: FP64 arithmetic on both sides -> 1e-11 relative; stencil
+coefficients come from a Gram eigenproblem on the GPU and an SVD in the oracle,
+which agree to ~1e-10, so everything built from them is compared at 1e-7;
+FP32 paths at 2e-5 (single precision FFT of length <= 4096: eps_32 * log2 N * few).
+"""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+from oracle import greens, polarized, sparsify  # noqa: E402
+from paper_1602_07652_gb300 import binding, inputs  # noqa: E402
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / max(np.linalg.norm(np.asarray(b)), 1e-300))
+
+
+def cuda(x):
+    return torch.from_numpy(np.ascontiguousarray(x)).cuda()
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    from paper_1602_07652_gb300 import build_lib
+    build_lib.build()
+    binding.load()
+
+
+CASES = [(16, 2, 3, 6.0), (48, 3, 4, 8.0), (64, 4, 10, 8.0), (100, 5, 6, 10.0)]
+
+
+@pytest.mark.parametrize("n,L,E,ppw", CASES)
+def test_ls_apply_fp64_matches_oracle(n, L, E, ppw):
+    w = inputs.omega_for_ppw(n, ppw)
+    m = inputs.bump_medium(n, nbumps=6, seed=n)
+    s = binding.Solver(cuda(m), w, layers=L, ext=E)
+    u = inputs.random_field(n, n + 1)
+    y = s.ls_apply(cuda(u)).cpu().numpy()
+    assert rel(y, greens.apply_H(u, m, 1.0 / n, w)) < 1e-11
+    # the diagonal weight and the spectral quadrant are the oracle's
+    assert abs(s.ls_get_diag_weight() - greens.diagonal_weight(1.0 / n, w)) < 1e-15
+    g, P = s.ls_get_spectrum()
+    assert P == 1 << math.ceil(math.log2(2 * n - 1))
+    ref = greens.spectrum(n, 1.0 / n, w, P)[: P // 2 + 1, : P // 2 + 1]
+    assert rel(g.cpu().numpy(), ref) < 1e-11
+    # in-place apply (u and y alias)
+    ud = cuda(u)
+    s.ls_apply(ud, ud)
+    assert rel(ud.cpu().numpy(), y) < 1e-15
+    s.close()
+
+
+@pytest.mark.parametrize("n,L,E,ppw", CASES[1:3])
+def test_ls_apply_fp32_and_incident_rhs(n, L, E, ppw):
+    w = inputs.omega_for_ppw(n, ppw)
+    m = inputs.bump_medium(n, nbumps=6, seed=n + 5)
+    s = binding.Solver(cuda(m), w, layers=L, ext=E)
+    u = inputs.random_field(n, 9)
+    y32 = s.ls_apply_f32(cuda(u.astype(np.complex64))).cpu().numpy()
+    assert rel(y32, greens.apply_H(u, m, 1.0 / n, w)) < 2e-5
+    th = 0.37
+    f = s.ls_incident_rhs(th).cpu().numpy()
+    f_ref = greens.rhs(m, 1.0 / n, w, greens.incident_plane_wave(n, w, th))
+    assert rel(f, f_ref) < 1e-11
+    s.close()
+
+
+def test_zero_medium_apply_is_identity_and_rhs_zero():
+    n = 32
+    s = binding.Solver(cuda(np.zeros((n, n))), 2 * math.pi * 4, layers=2, ext=4)
+    u = inputs.random_field(n, 1)
+    assert np.array_equal(s.ls_apply(cuda(u)).cpu().numpy(), u)
+    assert not s.ls_incident_rhs(0.2).abs().max().item()
+    s.close()
+
+
+@pytest.mark.parametrize("n,L,E,ppw", CASES[:3])
+def test_stencils_and_C_match_oracle(n, L, E, ppw):
+    w = inputs.omega_for_ppw(n, ppw)
+    m = inputs.bump_medium(n, nbumps=6, seed=2 * n)
+    s = binding.Solver(cuda(m), w, layers=L, ext=E)
+    st = sparsify.Stencils(n, 1.0 / n, w)
+    A, B = s.ls_get_stencils()
+    assert np.max(np.abs(A - st.alpha.reshape(9, 9))) < 1e-8
+    assert np.max(np.abs(B - st.beta.reshape(9, 9))) < 1e-8 * np.max(np.abs(st.beta))
+    v = inputs.random_field(n, 4)
+    assert rel(s.ls_apply_A(cuda(v)).cpu().numpy(), sparsify.apply_A(v, st)) < 1e-7
+    assert rel(s.ls_apply_C(cuda(v)).cpu().numpy(), sparsify.apply_C(v, m, st, w)) < 1e-7
+    s.close()
+
+
+@pytest.mark.parametrize("prec,tol", [(binding.LS_FP64, 1e-7), (binding.LS_MIXED, 2e-4)])
+@pytest.mark.parametrize("n,L,E,ppw", CASES[1:3])
+def test_local_solves_match_oracle(n, L, E, ppw, prec, tol):
+    w = inputs.omega_for_ppw(n, ppw)
+    m = inputs.bump_medium(n, nbumps=6, seed=3 * n)
+    s = binding.Solver(cuda(m), w, layers=L, ext=E, precision=prec)
+    s.ls_factor()
+    st = sparsify.Stencils(n, 1.0 / n, w)
+    lay = polarized.Layering(m, st, w, L, E)
+    lay_t = polarized.Layering(m.T.copy(), st.transposed(), w, L, E)
+    for d, ly in ((0, lay), (1, lay_t)):
+        for l in range(L):
+            b = inputs.random_field(n, 100 + l, nz=lay.q)
+            x = s.ls_local_solve(d, l, cuda(b)).cpu().numpy()
+            assert rel(x, ly.solve_local(l, b)) < tol, (d, l)
+    s.close()
+
+
+@pytest.mark.parametrize("prec,tol", [(binding.LS_FP64, 1e-7), (binding.LS_MIXED, 2e-4)])
+@pytest.mark.parametrize("n,L,E,ppw", CASES[1:3])
+def test_sweeps_match_oracle(n, L, E, ppw, prec, tol):
+    w = inputs.omega_for_ppw(n, ppw)
+    m = inputs.bump_medium(n, nbumps=6, seed=4 * n)
+    s = binding.Solver(cuda(m), w, layers=L, ext=E, precision=prec)
+    s.ls_factor()
+    st = sparsify.Stencils(n, 1.0 / n, w)
+    bd = polarized.BiDirectional(m, st, w, L, E)
+    g = inputs.random_field(n, 21)
+    gd = cuda(g)
+    assert rel(s.ls_sweep(0, gd).cpu().numpy(), bd.precond_horizontal(g)) < tol
+    assert rel(s.ls_sweep(1, gd).cpu().numpy(), bd.precond_vertical(g)) < tol
+    assert rel(s.ls_precond_bd(gd).cpu().numpy(), bd(g)) < tol
+    s.close()
+
+
+def test_single_layer_sweep_inverts_C():
+    n, E = 40, 3
+    w = inputs.omega_for_ppw(n, 8.0)
+    m = inputs.bump_medium(n, nbumps=4, seed=7)
+    s = binding.Solver(cuda(m), w, layers=1, ext=E)
+    s.ls_factor()
+    g = cuda(inputs.random_field(n, 5))
+    v = s.ls_sweep(0, g)
+    r = g - s.ls_apply_C(v)
+    assert (torch.linalg.norm(r) / torch.linalg.norm(g)).item() < 1e-11
+    _, it = s.ls_inner_solve(g, 1e-10)
+    assert it == 1
+    s.close()
+
+
+def test_full_size_fp64_apply_sampled():
+    # 1024 x 1024, w = 2 pi 100, 20 bumps: sampled outputs against the direct quadrature sum
+    n = 1024
+    w = 2 * math.pi * 100
+    m = inputs.bump_medium(n, nbumps=20, seed=0)
+    s = binding.Solver(cuda(m), w, layers=16, ext=10)
+    u = inputs.random_field(n, 0)
+    y = s.ls_apply(cuda(u)).cpu().numpy()
+    rng = np.random.default_rng(1)
+    pts = [(0, 0), (n - 1, n - 1), (0, n - 1), (n // 2, n // 3)] + [tuple(rng.integers(0, n, 2)) for _ in range(6)]
+    ref = greens.apply_H_points(u, m, 1.0 / n, w, pts)
+    got = np.array([y[j, i] for j, i in pts])
+    assert np.max(np.abs(got - ref)) < 1e-10 * np.max(np.abs(ref))
+    s.close()
+
+
+def test_full_size_fp32_apply_sampled():
+    n = 2048
+    w = 2 * math.pi * 200
+    m = inputs.bump_medium(n, nbumps=20, seed=0)
+    s = binding.Solver(cuda(m), w, layers=32, ext=10, precision=binding.LS_MIXED)
+    u = inputs.random_field(n, 0)
+    y = s.ls_apply_f32(cuda(u.astype(np.complex64))).cpu().numpy()
+    y64 = s.ls_apply(cuda(u)).cpu().numpy()
+    pts = [(0, 0), (n - 1, n - 1), (n - 1, 0), (1023, 1024), (5, 2000)]
+    ref = greens.apply_H_points(u, m, 1.0 / n, w, pts)
+    scale = np.max(np.abs(ref))
+    assert np.max(np.abs(np.array([y64[j, i] for j, i in pts]) - ref)) < 1e-10 * scale
+    assert np.max(np.abs(np.array([y[j, i] for j, i in pts]) - ref)) < 2e-5 * scale
+    assert rel(y, y64) < 2e-5
+    s.close()

@@ -1,0 +1,144 @@
+"""GPU parity of the two-level solve (Sec. 4) vs the oracle, through the C ABI.
+
+The converged scattered field depends only on H (Sec. 2), so the GPU solve must
+match the oracle's solution to 1e-6 relative L2 (both solved to 1e-10 or
+tighter); iteration counts are reported, not compared.
+"""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+from oracle import greens, solver as osolver  # noqa: E402
+from paper_1602_07652_gb300 import binding, inputs  # noqa: E402
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def cuda(x):
+    return torch.from_numpy(np.ascontiguousarray(x)).cuda()
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    from paper_1602_07652_gb300 import build_lib
+    build_lib.build()
+    binding.load()
+
+
+@pytest.mark.parametrize("prec", [binding.LS_FP64, binding.LS_MIXED])
+def test_c1_configuration_matches_oracle(prec):
+    # 64 x 64, w = 2 pi 8, Gaussian disk medium, theta = 0, 4 layers
+    n, L, E = 64, 4, 10
+    w = 2 * math.pi * 8
+    m = inputs.gaussian_disk_medium(n)
+    s = binding.Solver(cuda(m), w, layers=L, ext=E, precision=prec)
+    s.ls_factor()
+    f = s.ls_incident_rhs(0.0)
+    u, st, rc = s.ls_solve(f, 1e-10)
+    prob = osolver.Problem(m, w, L=L, E=E)
+    u_ref, info = osolver.solve(prob, prob.rhs(0.0), tol=1e-12)
+    err = rel(u.cpu().numpy(), u_ref)
+    print("C1 prec=%d: rel err %.2e outer %d inner %d (oracle outer %d)" %
+          (prec, err, st["outer_iters"], st["inner_iters_total"], info["iters"]))
+    assert err < 1e-6
+    assert st["true_rel_residual"] <= 1e-10
+    s.close()
+
+
+def test_ragged_size_and_seeded_angle():
+    n, L, E = 48, 3, 4
+    w = inputs.omega_for_ppw(n, 8.0)
+    m = inputs.bump_medium(n, nbumps=8, seed=11)
+    th = inputs.seeded_angle(3)
+    s = binding.Solver(cuda(m), w, layers=L, ext=E)
+    s.ls_factor()
+    u, st = s.ls_solve_plane_wave(th, 1e-10)
+    prob = osolver.Problem(m, w, L=L, E=E)
+    u_ref, _ = osolver.solve(prob, prob.rhs(th), tol=1e-12)
+    assert rel(u.cpu().numpy(), u_ref) < 1e-6
+    s.close()
+
+
+def test_zero_medium_gives_zero_field():
+    n = 32
+    s = binding.Solver(cuda(np.zeros((n, n))), 2 * math.pi * 4, layers=2, ext=4)
+    s.ls_factor()
+    u, st = s.ls_solve_plane_wave(0.3, 1e-8)
+    assert not u.abs().max().item()
+    assert st["outer_iters"] == 0
+    s.close()
+
+
+def test_host_buffers_match_device_solve():
+    n, L, E = 64, 4, 6
+    w = 2 * math.pi * 6
+    m = inputs.bump_medium(n, nbumps=6, seed=2)
+    s = binding.Solver(cuda(m), w, layers=L, ext=E)
+    s.ls_factor()
+    f = s.ls_incident_rhs(1.0)
+    u_dev, _, _ = s.ls_solve(f, 1e-9)
+    fh = f.cpu().pin_memory()
+    uh = torch.empty_like(fh).pin_memory()
+    s.ls_solve_host(fh, 1e-9, uh)
+    assert torch.equal(uh, u_dev.cpu())
+    s.close()
+
+
+def test_reciprocity_of_solution_operator():
+    # S = H^{-1} G is complex symmetric: e_b^T H^{-1} G e_a = e_a^T H^{-1} G e_b
+    n = 32
+    w = 2 * math.pi * 3
+    m = inputs.gaussian_disk_medium(n, amp=0.3, sigma=0.15, radius=0.4)
+    s = binding.Solver(cuda(m), w, layers=2, ext=4)
+    s.ls_factor()
+    a, b = (5, 7), (20, 26)
+    W = greens.kernel_weights(n - 1, 1.0 / n, w)
+    jj, ii = np.meshgrid(np.arange(n), np.arange(n), indexing="ij")
+
+    def column(p):  # G e_p
+        return W[jj - p[0] + n - 1, ii - p[1] + n - 1]
+
+    ua, _, _ = s.ls_solve(cuda(column(a)), 1e-12)
+    ub, _, _ = s.ls_solve(cuda(column(b)), 1e-12)
+    x = ua.cpu().numpy()[b]
+    y = ub.cpu().numpy()[a]
+    assert abs(x - y) < 1e-9 * abs(x)
+    s.close()
+
+
+def test_nan_input_is_rejected():
+    n = 16
+    s = binding.Solver(cuda(inputs.bump_medium(n, nbumps=2, seed=1)), 2 * math.pi * 2, layers=2, ext=2)
+    s.ls_factor()
+    f = torch.zeros((n, n), dtype=torch.complex128, device="cuda")
+    f[3, 3] = float("nan")
+    _, _, rc = s.ls_solve(f, 1e-8, check=False)
+    assert rc == -6  # LS_ENAN
+    s.close()
+
+
+def test_mixed_2048_solve_meets_tolerance_fp64_residual():
+    # the mixed-precision configuration at full size: 2048^2, w = 2 pi 200, 20 bumps, 32 layers
+    n = 2048
+    w = 2 * math.pi * 200
+    m = inputs.bump_medium(n, nbumps=20, seed=0)
+    s = binding.Solver(cuda(m), w, layers=32, ext=10, precision=binding.LS_MIXED)
+    s.ls_factor()
+    th = inputs.seeded_angle(0)
+    u, st = s.ls_solve_plane_wave(th, 1e-6)
+    # true residual with the oracle's FP64 H and f (numpy FFT convolution)
+    u_np = u.cpu().numpy()
+    f = greens.rhs(m, 1.0 / n, w, greens.incident_plane_wave(n, w, th))
+    r = np.linalg.norm(f - greens.apply_H(u_np, m, 1.0 / n, w)) / np.linalg.norm(f)
+    print("2048 mixed: outer %d inner %d refine %d res %.2e (oracle %.2e) t %.2fs" %
+          (st["outer_iters"], st["inner_iters_total"], st["refine_steps"], st["true_rel_residual"], r,
+           st["t_solve_s"]))
+    assert r <= 1e-6
+    s.close()
