@@ -63,6 +63,8 @@ typedef struct {
     int refine_maxit;      /* LS_MIXED: refinement steps cap (default 6)                    */
     double refine_inner_tol; /* LS_MIXED: relative tolerance of each FP32 correction solve
                                 (default 1e-4)                                               */
+    int use_graphs;        /* 1 (default): replay Algorithm 2 as a captured CUDA graph;
+                              0: launch its kernels one by one (same arithmetic)            */
 } ls_opts;
 
 typedef struct {
@@ -72,8 +74,11 @@ typedef struct {
     int refine_steps;        /* LS_MIXED refinement steps (1 = no correction needed)         */
     double true_rel_residual;/* ||f - H u|| / ||f|| with an FP64 apply of H                 */
     double t_solve_s;        /* wall time of the call                                        */
-    double t_apply_ms;       /* total device time of LS-apply launches (if timing enabled)  */
-    int n_apply;             /* LS-apply launches counted in t_apply_ms                      */
+    double t_apply_ms;       /* device time of FP32-arithmetic LS-applies (LS_MIXED) or of all
+                                FP64 LS-applies (LS_FP64), if timing is enabled            */
+    int n_apply;             /* LS-applies counted in t_apply_ms                             */
+    double t_apply64_ms;     /* LS_MIXED: device time of the FP64 refinement-residual applies */
+    int n_apply64;           /* LS-applies counted in t_apply64_ms                           */
     double t_sweep_ms;       /* total device time of Algorithm 2 applications (if timing)   */
     int n_sweep;             /* Algorithm 2 applications counted in t_sweep_ms               */
     long long kernel_launches; /* kernels this library launched during the call            */

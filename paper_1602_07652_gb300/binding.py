@@ -36,7 +36,8 @@ class Opts(ctypes.Structure):
     _fields_ = [("inner_tol", ctypes.c_double), ("inner_restart", ctypes.c_int),
                 ("inner_maxit", ctypes.c_int), ("outer_restart", ctypes.c_int),
                 ("outer_maxit", ctypes.c_int), ("shift", ctypes.c_double),
-                ("refine_maxit", ctypes.c_int), ("refine_inner_tol", ctypes.c_double)]
+                ("refine_maxit", ctypes.c_int), ("refine_inner_tol", ctypes.c_double),
+                ("use_graphs", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -44,6 +45,7 @@ class Stats(ctypes.Structure):
                 ("inner_calls", ctypes.c_int), ("refine_steps", ctypes.c_int),
                 ("true_rel_residual", ctypes.c_double), ("t_solve_s", ctypes.c_double),
                 ("t_apply_ms", ctypes.c_double), ("n_apply", ctypes.c_int),
+                ("t_apply64_ms", ctypes.c_double), ("n_apply64", ctypes.c_int),
                 ("t_sweep_ms", ctypes.c_double), ("n_sweep", ctypes.c_int),
                 ("kernel_launches", ctypes.c_longlong)]
 

@@ -50,7 +50,7 @@ void release(ls_handle* h) {
         *b = HostBufs{};
     }
     void* ptrs[] = {h->m64, h->m32, h->mT64, h->ghat64, h->ghat32, h->tw64, h->tw32, h->fftws, h->incx,
-                    h->incz, h->dtabs, h->srhs, h->ssol, h->vtmp, h->vtmp2, h->red};
+                    h->incz, h->dtabs, h->srhs, h->ssol, h->vtmp, h->vtmp2, h->red, h->bd_in, h->bd_out};
     for (void* p : ptrs) cudaFree(p);
     if (h->red_host) cudaFreeHost(h->red_host);
     if (h->ev0) cudaEventDestroy(h->ev0);
@@ -87,6 +87,9 @@ int ls_timing_end(ls_handle* h, int kind) {
     if (kind == 0) {
         h->t_apply_ms += ms;
         h->n_apply++;
+    } else if (kind == 2) {
+        h->t_apply64_ms += ms;
+        h->n_apply64++;
     } else {
         h->t_sweep_ms += ms;
         h->n_sweep++;
@@ -106,6 +109,7 @@ void ls_default_opts(ls_opts* o) {
     o->shift = 10.0;
     o->refine_maxit = 6;
     o->refine_inner_tol = 1e-4;
+    o->use_graphs = 1;
 }
 
 const char* ls_strerror(int code) {
@@ -230,8 +234,8 @@ int ls_solve(ls_handle* h, const ls_c64* f, double tol, ls_c64* u, int use_x0, l
     ls_stats local{};
     ls_stats* s = st ? st : &local;
     std::memset(s, 0, sizeof(*s));
-    h->t_apply_ms = h->t_sweep_ms = 0;
-    h->n_apply = h->n_sweep = 0;
+    h->t_apply_ms = h->t_sweep_ms = h->t_apply64_ms = 0;
+    h->n_apply = h->n_sweep = h->n_apply64 = 0;
     const long long l0 = h->launches;
     const auto t0 = std::chrono::steady_clock::now();
     int rc = ls_outer_solve(h, reinterpret_cast<const double2*>(f), tol, reinterpret_cast<double2*>(u), use_x0, s);
@@ -239,6 +243,8 @@ int ls_solve(ls_handle* h, const ls_c64* f, double tol, ls_c64* u, int use_x0, l
     s->t_solve_s = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     s->t_apply_ms = h->t_apply_ms;
     s->n_apply = h->n_apply;
+    s->t_apply64_ms = h->t_apply64_ms;
+    s->n_apply64 = h->n_apply64;
     s->t_sweep_ms = h->t_sweep_ms;
     s->n_sweep = h->n_sweep;
     s->kernel_launches = h->launches - l0;

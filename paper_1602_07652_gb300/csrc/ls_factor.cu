@@ -489,6 +489,7 @@ int ls_factor_all(ls_handle* h) {
 }
 
 void ls_factor_free(ls_handle* h) {
+    ls_bd_graph_free(h);
     for (int d = 0; d < 2; ++d) {
         cudaFree(h->fac[d].pool64);
         cudaFree(h->fac[d].pool32);

@@ -152,9 +152,16 @@ struct ls_handle {
     double* red_host = nullptr;
     size_t red_cap = 0;
 
+    // Algorithm 2 as a captured CUDA graph (inputs/outputs staged through bd_in / bd_out)
+    cudaGraph_t bd_graph = nullptr;
+    cudaGraphExec_t bd_exec = nullptr;
+    double2* bd_in = nullptr;
+    double2* bd_out = nullptr;
+    long long bd_nodes = 0;
+
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
-    double t_apply_ms = 0, t_sweep_ms = 0;
-    int n_apply = 0, n_sweep = 0;
+    double t_apply_ms = 0, t_sweep_ms = 0, t_apply64_ms = 0;
+    int n_apply = 0, n_sweep = 0, n_apply64 = 0;
 };
 
 // ------------------------------------------------------------------ errors
@@ -213,6 +220,7 @@ void ls_factor_free(ls_handle* h);
 int ls_sweep_alloc(ls_handle* h);
 int ls_sweep_dir(ls_handle* h, int dir, const double2* g, double2* v);   // Algorithm 1
 int ls_bd(ls_handle* h, const double2* g, double2* v);                   // Algorithm 2
+void ls_bd_graph_free(ls_handle* h);
 int ls_strip_solve(ls_handle* h, int dir, int layer, const double2* b, double2* x);
 
 // Krylov (ls_krylov.cu)

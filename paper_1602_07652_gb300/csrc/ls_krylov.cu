@@ -301,7 +301,7 @@ int ls_outer_solve(ls_handle* h, const double2* f, double tol, double2* u, int u
     for (;;) {
         LS_TRY(ls_timing_begin(h));
         LS_TRY(ls_apply64(h, u, d));  // d = H u (FP64)
-        LS_TRY(ls_timing_end(h, 0));
+        LS_TRY(ls_timing_end(h, 2));
         LS_TRY(ls_vec_axpby(h, make_double2(1, 0), f, make_double2(-1, 0), d));  // d = f - H u
         double nr;
         LS_TRY(ls_vec_norm(h, d, &nr));

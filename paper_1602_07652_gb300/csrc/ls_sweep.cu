@@ -124,6 +124,80 @@ __global__ void k_top(int q, Pool<T> pool, size_t off_top, cpx_t<T>* __restrict_
     if (r < q) x[r] = matvec_row<T>(pool.mat(off_top), vb, q, r, czero<C>(), false);
 }
 
+// The last levels of the reduction (at most kTopBlocks blocks) in one block of
+// threads: forward levels k0..K-1, the top block, backward levels K-1..k0, with
+// block barriers between levels instead of separate launches.  Thread group g
+// (of kGroups, 128 threads each) handles blocks g, g + kGroups, ...; global
+// memory written before a __syncthreads is visible to the whole block after it.
+constexpr int kGroups = 4;
+constexpr int kTopBlocks = 2 * kGroups;
+
+struct TopLevels {
+    int k0, K;
+    int nk[16];
+    size_t off_dinv[16], off_p[16], off_q[16], off_f[16], off_g[16];
+    size_t off_top;
+};
+
+template <typename T>
+__global__ void __launch_bounds__(128 * kGroups) k_top_levels(int q, TopLevels tl, Pool<T> pool, cpx_t<T>* __restrict__ x) {
+    using C = cpx_t<T>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int grp = threadIdx.x / 128, r = threadIdx.x % 128;
+    C* v0 = reinterpret_cast<C*>(smem_raw) + (size_t)grp * 3 * q;
+    C* v1 = v0 + q;
+    C* v2 = v1 + q;
+    for (int k = tl.k0; k < tl.K; ++k) {  // forward: even blocks
+        const int nk = tl.nk[k];
+        const size_t s = (size_t)1 << k;
+        const int neven = (nk + 1) / 2;
+        for (int base = 0; base < neven; base += kGroups) {
+            const int e = base + grp;
+            const int j = 2 * e;
+            const bool act = e < neven, hw = act && j >= 1, he = act && j + 1 < nk;
+            if (r < q) {
+                if (hw) v0[r] = x[((size_t)(j - 1) * s) * q + r];
+                if (he) v1[r] = x[((size_t)(j + 1) * s) * q + r];
+            }
+            __syncthreads();
+            if (act && r < q) {
+                C acc = x[((size_t)j * s) * q + r];
+                if (hw) acc = matvec_row<T>(pool.mat(tl.off_f[k] + e), v0, q, r, acc, true);
+                if (he) acc = matvec_row<T>(pool.mat(tl.off_g[k] + e), v1, q, r, acc, true);
+                x[((size_t)j * s) * q + r] = acc;
+            }
+            __syncthreads();
+        }
+    }
+    if (grp == 0 && r < q) v0[r] = x[r];  // top block
+    __syncthreads();
+    if (grp == 0 && r < q) x[r] = matvec_row<T>(pool.mat(tl.off_top), v0, q, r, czero<C>(), false);
+    __syncthreads();
+    for (int k = tl.K - 1; k >= tl.k0; --k) {  // backward: odd blocks
+        const int nk = tl.nk[k];
+        const size_t s = (size_t)1 << k;
+        const int nodd = nk / 2;
+        for (int base = 0; base < nodd; base += kGroups) {
+            const int o = base + grp;
+            const int j = 2 * o + 1;
+            const bool act = o < nodd, he = act && j + 1 < nk;
+            if (act && r < q) {
+                v0[r] = x[((size_t)j * s) * q + r];
+                v1[r] = x[((size_t)(j - 1) * s) * q + r];
+                if (he) v2[r] = x[((size_t)(j + 1) * s) * q + r];
+            }
+            __syncthreads();
+            if (act && r < q) {
+                C acc = matvec_row<T>(pool.mat(tl.off_dinv[k] + o), v0, q, r, czero<C>(), false);
+                acc = matvec_row<T>(pool.mat(tl.off_p[k] + o), v1, q, r, acc, true);
+                if (he) acc = matvec_row<T>(pool.mat(tl.off_q[k] + o), v2, q, r, acc, true);
+                x[((size_t)j * s) * q + r] = acc;
+            }
+            __syncthreads();
+        }
+    }
+}
+
 // level k >= 1 backward, odd blocks: x_j = Dinv_j b_j - P_j x_{j-1} - Q_j x_{j+1}
 template <typename T>
 __global__ void k_bwd(int q, int k, int nk, Pool<T> pool, size_t off_dinv, size_t off_p, size_t off_q,
@@ -286,12 +360,29 @@ int cr_solve(ls_handle* h, int dir, int l, cpx_t<T>* x) {
     const CrLevel& l0 = F.lev[0];
     if (l0.nodd) LS_LAUNCH(h, k_l0_odd<T>, l0.nodd, thr, sizeof(C) * q, q, pool, l0.off_dinv, x);
     LS_LAUNCH(h, k_l0_even<T>, l0.neven, thr, 0, g, F.tab, F.m, l, n, x);
-    for (int k = 1; k < F.K; ++k) {
+    // levels >= 1 with more than kTopBlocks blocks get one launch each; the rest
+    // (and the top block) run in one single-block launch
+    int k0 = 1;
+    while (k0 < F.K && F.lev[k0].nk > kTopBlocks) ++k0;
+    for (int k = 1; k < k0; ++k) {
         const CrLevel& lv = F.lev[k];
         LS_LAUNCH(h, k_fwd<T>, lv.neven, thr, 2 * sizeof(C) * q, q, k, lv.nk, pool, lv.off_f, lv.off_g, x);
     }
-    LS_LAUNCH(h, k_top<T>, 1, thr, sizeof(C) * q, q, pool, F.off_top, x);
-    for (int k = F.K - 1; k >= 1; --k) {
+    if (F.K > 16) return LS_EINVAL;
+    TopLevels tl{};
+    tl.k0 = k0;
+    tl.K = F.K;
+    for (int k = k0; k < F.K; ++k) {
+        tl.nk[k] = F.lev[k].nk;
+        tl.off_dinv[k] = F.lev[k].off_dinv;
+        tl.off_p[k] = F.lev[k].off_p;
+        tl.off_q[k] = F.lev[k].off_q;
+        tl.off_f[k] = F.lev[k].off_f;
+        tl.off_g[k] = F.lev[k].off_g;
+    }
+    tl.off_top = F.off_top;
+    LS_LAUNCH(h, k_top_levels<T>, 1, 128 * kGroups, 3 * kGroups * sizeof(C) * q, q, tl, pool, x);
+    for (int k = k0 - 1; k >= 1; --k) {
         const CrLevel& lv = F.lev[k];
         if (lv.nodd)
             LS_LAUNCH(h, k_bwd<T>, lv.nodd, thr, 3 * sizeof(C) * q, q, k, lv.nk, pool, lv.off_dinv, lv.off_p,
@@ -335,6 +426,8 @@ int ls_sweep_alloc(ls_handle* h) {
     LS_CUDA(cudaMalloc(&h->ssol, es * cnt));
     const size_t N = (size_t)h->n * h->n;
     LS_CUDA(cudaMalloc(&h->vtmp, sizeof(double2) * N * 4));
+    LS_CUDA(cudaMalloc(&h->bd_in, sizeof(double2) * N));
+    LS_CUDA(cudaMalloc(&h->bd_out, sizeof(double2) * N));
     return LS_OK;
 }
 
@@ -354,7 +447,7 @@ int ls_sweep_dir(ls_handle* h, int dir, const double2* g, double2* v) {
 }
 
 // Algorithm 2: v = u1 + u2, u1 = Alg. 1 horizontal (g), u2 = Alg. 1 vertical (g - C u1).
-int ls_bd(ls_handle* h, const double2* g, double2* v) {
+static int bd_direct(ls_handle* h, const double2* g, double2* v) {
     const size_t N = (size_t)h->n * h->n;
     double2* u1 = static_cast<double2*>(h->vtmp) + 2 * N;
     double2* e = u1 + N;
@@ -362,6 +455,61 @@ int ls_bd(ls_handle* h, const double2* g, double2* v) {
     LS_TRY(ls_stencil_apply(h, 0, 2, u1, g, e));   // e = g - C u1
     LS_TRY(ls_sweep_dir(h, 1, e, v));
     LS_LAUNCH(h, k_add, 608, 256, 0, N, u1, v);
+    return LS_OK;
+}
+
+void ls_bd_graph_free(ls_handle* h) {
+    if (h->bd_exec) cudaGraphExecDestroy(h->bd_exec);
+    if (h->bd_graph) cudaGraphDestroy(h->bd_graph);
+    h->bd_exec = nullptr;
+    h->bd_graph = nullptr;
+    h->bd_nodes = 0;
+}
+
+// Capture Algorithm 2 on the staging buffers once (the sequence of launches and all
+// pointers are fixed after ls_factor), then replay it.
+static int bd_capture(ls_handle* h) {
+    cudaStream_t cap = nullptr;
+    LS_CUDA(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+    cudaStream_t saved = h->stream;
+    const long long l0 = h->launches;
+    h->stream = cap;
+    int rc = LS_OK;
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        rc = bd_direct(h, h->bd_in, h->bd_out);
+        e = cudaStreamEndCapture(cap, &graph);
+    }
+    h->stream = saved;
+    const long long nodes = h->launches - l0;
+    h->launches = l0;
+    cudaStreamDestroy(cap);
+    if (rc != LS_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return rc;
+    }
+    if (e != cudaSuccess) return ls_cuda_fail(e);
+    cudaGraphExec_t exec = nullptr;
+    e = cudaGraphInstantiate(&exec, graph, 0);
+    if (e != cudaSuccess) {
+        cudaGraphDestroy(graph);
+        return ls_cuda_fail(e);
+    }
+    h->bd_graph = graph;
+    h->bd_exec = exec;
+    h->bd_nodes = nodes;
+    return LS_OK;
+}
+
+int ls_bd(ls_handle* h, const double2* g, double2* v) {
+    if (!h->opts.use_graphs) return bd_direct(h, g, v);
+    if (!h->bd_exec) LS_TRY(bd_capture(h));
+    const size_t N = (size_t)h->n * h->n;
+    LS_CUDA(cudaMemcpyAsync(h->bd_in, g, sizeof(double2) * N, cudaMemcpyDeviceToDevice, h->stream));
+    LS_CUDA(cudaGraphLaunch(h->bd_exec, h->stream));
+    h->launches += h->bd_nodes;
+    LS_CUDA(cudaMemcpyAsync(v, h->bd_out, sizeof(double2) * N, cudaMemcpyDeviceToDevice, h->stream));
     return LS_OK;
 }
 

@@ -179,3 +179,20 @@ def test_full_size_fp32_apply_sampled():
     assert np.max(np.abs(np.array([y[j, i] for j, i in pts]) - ref)) < 2e-5 * scale
     assert rel(y, y64) < 2e-5
     s.close()
+
+
+def test_bd_graph_replay_equals_direct_launches():
+    n, L, E = 64, 4, 6
+    w = inputs.omega_for_ppw(n, 8.0)
+    m = inputs.bump_medium(n, nbumps=6, seed=9)
+    g = cuda(inputs.random_field(n, 2))
+    outs = []
+    for graphs in (0, 1):
+        o = binding.default_opts()
+        o.use_graphs = graphs
+        s = binding.Solver(cuda(m), w, layers=L, ext=E, opts=o)
+        s.ls_factor()
+        outs.append(s.ls_precond_bd(g).cpu())
+        outs.append(s.ls_precond_bd(g).cpu())   # replay twice
+        s.close()
+    assert torch.equal(outs[0], outs[2]) and torch.equal(outs[2], outs[3]) and torch.equal(outs[0], outs[1])
