@@ -65,6 +65,47 @@ def config_dict(wl, prec="mixed"):
             "parallelism": "replicas"}
 
 
+def cr_factor_flops(n, L, q):
+    """Algorithmic FP64 flops of the block-cyclic-reduction factorisation of 2L strips.
+
+    Level 0: one q x q inversion (q^3 complex multiply-adds) per odd block.
+    Levels >= 1: per odd block an inversion and P = D^-1 W, Q = D^-1 E; per even
+    block F, G and the three reduced blocks (two products for D', one each for
+    W', E'); every product q^3 complex multiply-adds.  8 real flops each.
+    """
+    cm = 0
+    nk, k = n, 0
+    while nk > 1:
+        nodd, neven = nk // 2, (nk + 1) // 2
+        if k == 0:
+            cm += nodd
+        else:
+            cm += 3 * nodd
+            for j in range(0, nk, 2):
+                hw, he = j >= 1, j + 1 < nk
+                cm += hw + he + hw + he + (hw and j >= 2) + (he and j + 2 < nk)
+        nk, k = neven, k + 1
+    cm += 1  # top block
+    return 8.0 * q ** 3 * cm * 2 * L
+
+
+def fp64_peak_tflops():
+    """FP64 GEMM rate of this GPU measured with cuBLAS (torch.matmul, 4096^3, best of 3)."""
+    import torch
+    a = torch.randn(4096, 4096, dtype=torch.float64, device="cuda")
+    b = torch.randn_like(a)
+    torch.matmul(a, b)
+    best = 1e30
+    for _ in range(3):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        torch.matmul(a, b)
+        e1.record()
+        torch.cuda.synchronize()
+        best = min(best, e0.elapsed_time(e1))
+    return 2 * 4096 ** 3 / (best / 1e3) / 1e12
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -265,6 +306,14 @@ def run_ours(args):
         e2e = t.item()
     if rank == 0:
         hbm, src = peaks()
+        try:
+            dpk = fp64_peak_tflops()
+        except Exception:
+            dpk = None
+        fl = cr_factor_flops(n, wl["layers"], n // wl["layers"] + 2 * wl["ext"])
+        factor_roof = {"bound": "alu", "achieved": fl / t_factor / 1e12, "unit": "TFLOP/s",
+                       "peak": dpk, "peak_source": "measured cuBLAS DGEMM 4096^3 (torch.matmul)",
+                       "frac": (fl / t_factor / 1e12 / dpk) if dpk else None, "flops": fl}
         n_app = sum(st["n_apply"] for st in stats)
         t_app = sum(st["t_apply_ms"] for st in stats)
         # mixed LS-apply: FP64 input/output, FP32 arithmetic; algorithmic bytes per apply:
@@ -290,6 +339,7 @@ def run_ours(args):
                        "d2h_bytes_per_step": 16 * n * n},
                "gpu_launches": int(sum(st["kernel_launches"] for st in stats)),
                "offline_s": {"setup": t_setup, "factor": t_factor},
+               "factor_roofline": factor_roof,
                "iterations": {"outer": outer, "inner_total": inner,
                               "refine_steps": statistics.mean(st["refine_steps"] for st in stats),
                               "true_rel_residual_max": max(st["true_rel_residual"] for st in stats)},

@@ -158,3 +158,27 @@ def apply_H_points(u: np.ndarray, m: np.ndarray, h: float, omega: float, points)
         W[~nz] = diagonal_weight(h, omega)
         out.append(u[j, i] + omega * omega * np.sum(W * mu))
     return np.array(out)
+
+
+class Convolution:
+    """apply_G / apply_H / rhs with the FFT of the Toeplitz embedding computed once (Sec. 2).
+
+    Same arithmetic as the functions above (zero-padded P = 2n circulant
+    embedding, numpy FFT), for large grids where re-evaluating the kernel
+    weights on every call would dominate.
+    """
+
+    def __init__(self, n: int, h: float, omega: float):
+        self.n, self.h, self.omega, self.P = n, h, omega, 2 * n
+        self.Gf = np.fft.fft2(toeplitz_embedding(n, h, omega, self.P))
+
+    def G(self, v: np.ndarray) -> np.ndarray:
+        V = np.zeros((self.P, self.P), dtype=np.complex128)
+        V[:self.n, :self.n] = v
+        return np.fft.ifft2(self.Gf * np.fft.fft2(V))[:self.n, :self.n]
+
+    def H(self, u: np.ndarray, m: np.ndarray) -> np.ndarray:
+        return u + self.omega * self.omega * self.G(m * u)
+
+    def rhs(self, m: np.ndarray, u_inc: np.ndarray) -> np.ndarray:
+        return -self.omega * self.omega * self.G(m * u_inc)

@@ -34,8 +34,17 @@ are empty in the available text, and Algorithm 1's layer indices are garbled)
   * Algorithm 1, downward sweep l = L-1..0: layer l receives from layer l+1
     (eq. pde_GRF_down): g^l += -delta_{n} C^l_{n,n+1} w^{l+1}_1
     + delta_{n+1} C^l_{n+1,n} w^{l+1}_0.  Upward sweep l = 0..L-1 keeps that g^l
-    and receives from layer l-1: g^l += -delta_1 C^l_{1,0} v^{l-1}_n
-    + delta_0 C^l_{0,1} v^{l-1}_{n+1}.  Output: interior rows of v^l.
+    and receives from layer l-1 through the same formula at its bottom rows,
+    g^l += -delta_1 C^l_{1,0} p_0 + delta_0 C^l_{0,1} p_1, with the up-going
+    traces p_0 = v^{l-1}_n - w^l_0 and p_1 = v^{l-1}_{n+1}.  The pair injected must
+    be the traces of one wave field: the top injection of layer l-1 reproduces
+    the down-going wave in its row n but cancels it in its extension row n+1, so
+    the literal pair (v^{l-1}_n, v^{l-1}_{n+1}) carries the down-going wave in one
+    row only and acts as a spurious source (a point source in the top layer is
+    then reproduced with O(1) error).  Removing that wave from row n -- it is
+    w^l_0, the continuation of layer l's own down-sweep solution below it --
+    leaves the up-going field, which is what the upward sweep transmits (Sec. 3.4:
+    polarized traces).  Output: interior rows of v^l.
   * "Preconditioner^T" in Algorithm 2 is Algorithm 1 on vertical layers, i.e. on
     the grid with x and z exchanged (the left-right pass of Sec. 3.5).
 """
@@ -130,11 +139,12 @@ class Layering:
         b[rn] -= self.coupling(l, rn, rn + 1, w_up[E])       # w^{l+1}_1
         b[rn + 1] += self.coupling(l, rn + 1, rn, w_up[E - 1])  # w^{l+1}_0
 
-    def inject_from_below(self, l: int, b: np.ndarray, v_dn: np.ndarray) -> None:
-        """b += -delta_1 C^l_{1,0} v^{l-1}_n + delta_0 C^l_{0,1} v^{l-1}_{n+1} (upward sweep)."""
+    def inject_from_below(self, l: int, b: np.ndarray, v_dn: np.ndarray, w_self: np.ndarray) -> None:
+        """b += -delta_1 C^l_{1,0} p_0 + delta_0 C^l_{0,1} p_1 with the up-going traces
+        p_0 = v^{l-1}_n - w^l_0, p_1 = v^{l-1}_{n+1} (upward sweep; reading in the module docstring)."""
         E, t = self.E, self.t
-        b[E] -= self.coupling(l, E, E - 1, v_dn[E + t - 1])      # v^{l-1}_n
-        b[E - 1] += self.coupling(l, E - 1, E, v_dn[E + t])      # v^{l-1}_{n+1}
+        b[E] -= self.coupling(l, E, E - 1, v_dn[E + t - 1] - w_self[E - 1])   # p_0
+        b[E - 1] += self.coupling(l, E - 1, E, v_dn[E + t])                    # p_1 = v^{l-1}_{n+1}
 
 
 def sweep(lay: Layering, g: np.ndarray) -> np.ndarray:
@@ -150,7 +160,7 @@ def sweep(lay: Layering, g: np.ndarray) -> np.ndarray:
     v = [None] * L
     for l in range(L):                      # upwards sweep
         if l != 0:
-            lay.inject_from_below(l, gl[l], v[l - 1])
+            lay.inject_from_below(l, gl[l], v[l - 1], w[l])
         v[l] = lay.solve_local(l, gl[l])
     out = np.empty_like(g, dtype=np.complex128)
     for l in range(L):                      # concatenation

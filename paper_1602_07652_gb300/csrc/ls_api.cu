@@ -50,7 +50,7 @@ void release(ls_handle* h) {
         *b = HostBufs{};
     }
     void* ptrs[] = {h->m64, h->m32, h->mT64, h->ghat64, h->ghat32, h->tw64, h->tw32, h->fftws, h->incx,
-                    h->incz, h->dtabs, h->srhs, h->ssol, h->vtmp, h->vtmp2, h->red, h->bd_in, h->bd_out};
+                    h->incz, h->dtabs, h->srhs, h->ssol, h->strace, h->vtmp, h->vtmp2, h->red, h->bd_in, h->bd_out};
     for (void* p : ptrs) cudaFree(p);
     if (h->red_host) cudaFreeHost(h->red_host);
     if (h->ev0) cudaEventDestroy(h->ev0);

@@ -142,6 +142,7 @@ struct ls_handle {
     // sweep buffers per direction: rhs and solution of every strip (n*q each)
     void* srhs = nullptr;
     void* ssol = nullptr;
+    void* strace = nullptr;    // per layer: row 0 of its down-sweep solution (w^l_0), n each
     void* vtmp = nullptr;      // n*n complex scratch (FP64) for transposes
     void* vtmp2 = nullptr;
 

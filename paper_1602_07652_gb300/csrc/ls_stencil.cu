@@ -229,7 +229,8 @@ int ls_vec_update(ls_handle* h, int nvec, const double2* V, size_t ld, const dou
 int ls_vec_norm(ls_handle* h, const double2* w, double* out_host) {
     double2 d;
     LS_TRY(ls_vec_dots(h, 1, w, 0, w, &d));
-    *out_host = sqrt(d.x > 0 ? d.x : 0.0);
+    // a NaN or Inf anywhere in w must surface as a non-finite norm
+    *out_host = d.x >= 0 ? sqrt(d.x) : (d.x < 0 ? 0.0 : d.x);
     return LS_OK;
 }
 

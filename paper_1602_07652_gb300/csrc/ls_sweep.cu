@@ -12,9 +12,12 @@
 //   downward, l = L-1..0:  g^l = chi g;  if l < L-1:
 //        g^l[n]   -= C^l_{n,n+1} w^{l+1}_1,   g^l[n+1] += C^l_{n+1,n} w^{l+1}_0   (eq. pde_GRF_down)
 //        w^l = (C^l)^{-1} g^l
-//   upward, l = 1..L-1 (keeping g^l):
-//        g^l[1] -= C^l_{1,0} v^{l-1}_n,  g^l[0] += C^l_{0,1} v^{l-1}_{n+1};  v^l = (C^l)^{-1} g^l
-//   (v^0 = w^0: the upward pass leaves layer 0's right-hand side unchanged.)
+//   upward, l = 1..L-1 (keeping g^l), with the up-going traces of the layer below:
+//        g^l[1] -= C^l_{1,0} (v^{l-1}_n - w^l_0),  g^l[0] += C^l_{0,1} v^{l-1}_{n+1};  v^l = (C^l)^{-1} g^l
+//   (the top injection of layer l-1 reproduces the down-going wave in its row n but
+//   cancels it in its extension row n+1; w^l_0, the continuation of layer l's own
+//   down-sweep solution below it, is that wave, so the injected pair is the
+//   up-going field in both rows.  v^0 = w^0: layer 0 receives nothing upward.)
 //   v = rows 1..n of every v^l.
 // Algorithm 2: u1 = Alg. 1 on horizontal layers; e = g - C u1; u2 = Alg. 1 on
 // vertical layers (the transposed grid); v = u1 + u2.
@@ -256,12 +259,13 @@ __global__ void k_l0_back(StripGeom g, const StencilTables* __restrict__ tab, co
 template <typename T>
 __global__ void k_gather(StripGeom g, const StencilTables* __restrict__ tab, const double* __restrict__ m, int l,
                          const double2* __restrict__ gf, cpx_t<T>* __restrict__ rhs, cpx_t<T>* __restrict__ sol,
-                         const cpx_t<T>* __restrict__ above) {
+                         const cpx_t<T>* __restrict__ above, cpx_t<T>* __restrict__ trace_above) {
     using C = cpx_t<T>;
     const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int q = g.q, n = g.n, E = g.E, t = g.t;
     if (e >= (size_t)n * q) return;
     const int i = (int)(e / q), r = (int)(e % q);
+    if (above && r == 0) trace_above[i] = above[(size_t)i * q + E - 1];  // w^{l+1}_0, kept for the upward sweep
     double2 val = make_double2(0, 0);
     if (r >= E && r < E + t) val = gf[(size_t)(l * t - E + r) * n + i];
     if (above) {
@@ -286,7 +290,7 @@ __global__ void k_gather(StripGeom g, const StencilTables* __restrict__ tab, con
 template <typename T>
 __global__ void k_inject_up(StripGeom g, const StencilTables* __restrict__ tab, const double* __restrict__ m, int l,
                             const cpx_t<T>* __restrict__ rhs, cpx_t<T>* __restrict__ sol,
-                            const cpx_t<T>* __restrict__ below) {
+                            const cpx_t<T>* __restrict__ below, const cpx_t<T>* __restrict__ trace_self) {
     using C = cpx_t<T>;
     const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int q = g.q, n = g.n, E = g.E, t = g.t;
@@ -297,10 +301,11 @@ __global__ void k_inject_up(StripGeom g, const StencilTables* __restrict__ tab, 
         return;
     }
     double2 val = ccast<double2>(rhs[e]);
-    if (r == E) {  // -C^l_{1,0} v^{l-1}_n ; v^{l-1}_n = row E+t-1 of layer l-1
+    if (r == E) {  // -C^l_{1,0} (v^{l-1}_n - w^l_0) ; v^{l-1}_n = row E+t-1 of layer l-1
         for (int dx = -1; dx <= 1; ++dx) {
             if (i + dx < 0 || i + dx >= n) continue;
-            val = cfms(strip_coef(g, tab, m, l, r, i, dx, -1), ccast<double2>(below[(size_t)(i + dx) * q + E + t - 1]), val);
+            const double2 p0 = ccast<double2>(below[(size_t)(i + dx) * q + E + t - 1]) - ccast<double2>(trace_self[i + dx]);
+            val = cfms(strip_coef(g, tab, m, l, r, i, dx, -1), p0, val);
         }
     } else {  // +C^l_{0,1} v^{l-1}_{n+1} ; v^{l-1}_{n+1} = row E+t of layer l-1
         for (int dx = -1; dx <= 1; ++dx) {
@@ -399,17 +404,19 @@ int sweep_impl(ls_handle* h, int dir, const double2* g, double2* v) {
     const size_t sstride = (size_t)n * q;
     C* rhs = static_cast<C*>(h->srhs);
     C* sol = static_cast<C*>(h->ssol);
+    C* trc = static_cast<C*>(h->strace);
     const DirFactors& F = h->fac[dir];
     const StripGeom geo = geom_of(h);
     const unsigned nbs = (unsigned)((sstride + 255) / 256);
     for (int l = L - 1; l >= 0; --l) {  // downward sweep
         LS_LAUNCH(h, k_gather<T>, nbs, 256, 0, geo, F.tab, F.m, l, g, rhs + l * sstride, sol + l * sstride,
-                  l < L - 1 ? sol + (l + 1) * sstride : (const C*)nullptr);
+                  l < L - 1 ? sol + (l + 1) * sstride : (const C*)nullptr,
+                  l < L - 1 ? trc + (size_t)(l + 1) * n : (C*)nullptr);
         LS_TRY(cr_solve<T>(h, dir, l, sol + l * sstride));
     }
     for (int l = 1; l < L; ++l) {  // upward sweep
         LS_LAUNCH(h, k_inject_up<T>, nbs, 256, 0, geo, F.tab, F.m, l, rhs + l * sstride, sol + l * sstride,
-                  sol + (l - 1) * sstride);
+                  sol + (l - 1) * sstride, trc + (size_t)l * n);
         LS_TRY(cr_solve<T>(h, dir, l, sol + l * sstride));
     }
     const size_t N = (size_t)n * n;
@@ -424,6 +431,7 @@ int ls_sweep_alloc(ls_handle* h) {
     const size_t es = h->prec == LS_MIXED ? sizeof(float2) : sizeof(double2);
     LS_CUDA(cudaMalloc(&h->srhs, es * cnt));
     LS_CUDA(cudaMalloc(&h->ssol, es * cnt));
+    LS_CUDA(cudaMalloc(&h->strace, es * (size_t)h->L * h->n));
     const size_t N = (size_t)h->n * h->n;
     LS_CUDA(cudaMalloc(&h->vtmp, sizeof(double2) * N * 4));
     LS_CUDA(cudaMalloc(&h->bd_in, sizeof(double2) * N));

@@ -135,8 +135,9 @@ def test_mixed_2048_solve_meets_tolerance_fp64_residual():
     u, st = s.ls_solve_plane_wave(th, 1e-6)
     # true residual with the oracle's FP64 H and f (numpy FFT convolution)
     u_np = u.cpu().numpy()
-    f = greens.rhs(m, 1.0 / n, w, greens.incident_plane_wave(n, w, th))
-    r = np.linalg.norm(f - greens.apply_H(u_np, m, 1.0 / n, w)) / np.linalg.norm(f)
+    op = greens.Convolution(n, 1.0 / n, w)
+    f = op.rhs(m, greens.incident_plane_wave(n, w, th))
+    r = np.linalg.norm(f - op.H(u_np, m)) / np.linalg.norm(f)
     print("2048 mixed: outer %d inner %d refine %d res %.2e (oracle %.2e) t %.2fs" %
           (st["outer_iters"], st["inner_iters_total"], st["refine_steps"], st["true_rel_residual"], r,
            st["t_solve_s"]))

@@ -163,3 +163,14 @@ def test_reciprocity_of_scattering_operator():
     H = np.eye(n * n) + w * w * Gd * m.ravel()[None, :]
     S = np.linalg.solve(H, Gd)
     assert np.max(np.abs(S - S.T)) < 1e-12 * np.max(np.abs(S))
+
+
+def test_cached_convolution_equals_apply_H():
+    n, w = 24, 2 * math.pi * 3
+    h = 1.0 / n
+    u = inputs.random_field(n, 12)
+    m = inputs.bump_medium(n, nbumps=3, seed=4)
+    op = greens.Convolution(n, h, w)
+    assert np.array_equal(op.H(u, m), greens.apply_H(u, m, h, w))
+    ui = greens.incident_plane_wave(n, w, 0.3)
+    assert np.array_equal(op.rhs(m, ui), greens.rhs(m, h, w, ui))

@@ -105,3 +105,41 @@ def test_cutoff_profile():
     xs = [polarized.cutoff(d, E) for d in range(0, E + 1)]
     assert xs[0] == 1.0 and xs[1] == 1.0 and abs(xs[E]) < 1e-15
     assert all(xs[i] >= xs[i + 1] for i in range(E))
+
+
+def test_one_sweep_transmits_a_source_from_any_layer():
+    # Sec. 3.4: the down sweep carries down-going waves through every layer and the up sweep
+    # the up-going ones, so one application of Algorithm 1 reproduces the field of a point
+    # source wherever it sits (up to the local absorbing conditions), not only below it.
+    import scipy.sparse.linalg as spla
+    n, L, E = 128, 4, 10
+    w = inputs.omega_for_ppw(n, 10.24)
+    st = sparsify.Stencils(n, 1.0 / n, w)
+    for m in (np.zeros((n, n)), inputs.bump_medium(n, nbumps=8, seed=2)):
+        C = sparsify.matrix_C(m, st, w).tocsc()
+        lay = polarized.Layering(m, st, w, L, E)
+        t = lay.t
+        for l in range(L):
+            g = np.zeros((n, n), complex)
+            g[l * t + t // 2, n // 3] = 1.0
+            v = spla.spsolve(C, g.ravel()).reshape(n, n)
+            u = polarized.sweep(lay, g)
+            assert np.linalg.norm(u - v) / np.linalg.norm(v) < 6e-2, l   # literal reading: O(1)
+
+
+def test_bidirectional_iterations_do_not_grow_with_layers():
+    # Table 1 trend: Algorithm 2 needs a few GMRES iterations, independent of L
+    from oracle import krylov
+    n, E = 128, 10
+    w = inputs.omega_for_ppw(n, 10.24)
+    m = inputs.bump_medium(n, nbumps=10, seed=3)
+    st = sparsify.Stencils(n, 1.0 / n, w)
+    C = sparsify.matrix_C(m, st, w)
+    g = inputs.random_field(n, 1)
+    its = []
+    for L in (2, 4, 8):
+        bd = polarized.BiDirectional(m, st, w, L, E)
+        _, info = krylov.fgmres(lambda x: (C @ x.ravel()).reshape(n, n), g, bd, tol=1e-6, restart=30, maxit=30)
+        assert info["converged"]
+        its.append(info["iters"])
+    assert max(its) <= 5, its
