@@ -39,7 +39,8 @@ enum {
     LS_ENOCONV = -5,    /* iteration limit reached; output holds the best iterate   */
     LS_ENAN = -6,       /* NaN or Inf in an input or a residual                     */
     LS_ETIMEOUT = -7,   /* a bounded device-side wait ran out                       */
-    LS_ESTATE = -8      /* call out of order (e.g. solve before ls_factor)          */
+    LS_ESTATE = -8,     /* call out of order (e.g. solve before ls_factor)          */
+    LS_ETOOBIG = -9     /* size beyond the fixed scratch of ls_apply_f32_noalloc    */
 };
 
 enum { LS_FP64 = 0, LS_MIXED = 1 };
@@ -159,6 +160,27 @@ int ls_inner_solve(ls_handle* h, const ls_c64* g, double tol, ls_c64* v, int* it
  * local row r <-> global row l*t - ext + r (rows outside Omega are identity
  * rows), x fastest.  Uses the factors of ls_factor in the handle's precision. */
 int ls_local_solve(ls_handle* h, int dir, int layer, const ls_c64* b, ls_c64* x);
+
+/* ls_apply_f32_noalloc -- the FP32 LS-apply y = u + IFFT2(Ghat .* FFT2(pad(m u)))[0:n, 0:n]
+ * of ls_apply_f32, for callers that must not allocate device memory when they call it:
+ * code that runs under a memory manager which owns the whole device budget and forbids
+ * driver allocations after start-up, or a latency-critical loop that cannot afford the
+ * device synchronisation an allocation may cause.  It needs no handle and allocates
+ * nothing: its n x P scratch and its twiddle tables are fixed file-scope device arrays
+ * (16 MiB + 32 KiB, held by every GPU that loads the library until the process exits).
+ * The paper has no counterpart; it is the operator of Sec. 2 in another calling form.
+ *   n: grid points per direction, 8 <= n <= 1024 (n * P <= 2^21, P = smallest power of
+ *      two >= 2n - 1); larger n returns LS_ETOOBIG and does nothing.
+ *   m: DEVICE float[n*n], the contrast (x fastest).
+ *   ghat: DEVICE ls_c32[(P/2+1)^2], the spectral quadrant of ls_get_spectrum rounded to
+ *      FP32 (index kx*(P/2+1) + kz).
+ *   u, y: DEVICE ls_c32[n*n]; may alias.  stream: cudaStream_t (NULL = legacy stream).
+ * The first call on a device (with that device current) sets up the arrays for that
+ * device -- resolves their addresses, fills the twiddle tables, synchronises `stream`
+ * once -- so it should come before any stream capture.  The scratch needs no clearing
+ * (pass 1 writes every element the later passes read), but all calls on a device share
+ * it: calls that overlap on the GPU (other streams, other host threads) race. */
+int ls_apply_f32_noalloc(int n, const float* m, const ls_c32* ghat, const ls_c32* u, ls_c32* y, void* stream);
 
 /* ---- introspection (host copies of small tables) ---- */
 

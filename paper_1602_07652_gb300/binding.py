@@ -79,6 +79,7 @@ _SIGS = {
     "ls_kernel_count": (ctypes.c_longlong, [_P]),
     "ls_destroy": (None, [_P]),
     "ls_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+    "ls_apply_f32_noalloc": (ctypes.c_int, [ctypes.c_int, _P, _P, _P, _P, _P]),
 }
 
 EXPORTED = tuple(_SIGS)
@@ -125,6 +126,29 @@ def default_opts() -> Opts:
     o = Opts()
     load_library().ls_default_opts(ctypes.byref(o))
     return o
+
+
+def ls_apply_f32_noalloc(n: int, m32: torch.Tensor, ghat32: torch.Tensor, u: torch.Tensor,
+                         y: torch.Tensor | None = None, stream: torch.cuda.Stream | None = None,
+                         check: bool = True):
+    """FP32 LS-apply that allocates nothing in the library (fixed device scratch).
+
+    m32: CUDA float32 (n, n); ghat32: CUDA complex64 spectral quadrant; u, y: CUDA
+    complex64 (n, n).  Returns (y, status); raises on a non-zero status if check.
+    """
+    lib = load()
+    y = torch.empty_like(u) if y is None else y
+    for t in (m32, ghat32, u, y):
+        if not t.is_cuda or not t.is_contiguous():
+            raise ValueError("ls_apply_f32_noalloc takes contiguous CUDA tensors")
+    if m32.dtype != torch.float32 or u.dtype != torch.complex64 or y.dtype != torch.complex64 \
+            or ghat32.dtype != torch.complex64:
+        raise ValueError("ls_apply_f32_noalloc: m float32, ghat/u/y complex64")
+    st = stream if stream is not None else torch.cuda.current_stream()
+    rc = lib.ls_apply_f32_noalloc(int(n), _ptr(m32), _ptr(ghat32), _ptr(u), _ptr(y), ctypes.c_void_p(st.cuda_stream))
+    if check:
+        _ck(rc, "ls_apply_f32_noalloc")
+    return y, rc
 
 
 class Solver:

@@ -123,6 +123,7 @@ const char* ls_strerror(int code) {
         case LS_ENAN: return "NaN or Inf in an input or a residual";
         case LS_ETIMEOUT: return "a bounded device wait ran out";
         case LS_ESTATE: return "call out of order (ls_factor required first)";
+        case LS_ETOOBIG: return "size exceeds the fixed scratch of ls_apply_f32_noalloc (n <= 1024)";
         default: return "unknown status";
     }
 }

@@ -20,6 +20,7 @@
 // Ghat is even in both indices (G_w is even), so only its (P/2+1)^2 quadrant is
 // stored and read.
 #include <cmath>
+#include <mutex>
 
 #include "ls_internal.cuh"
 
@@ -486,3 +487,90 @@ int ls_rhs64(ls_handle* h, double theta, double2* f) {
     return LS_OK;
 }
 
+
+// ---------------------------------------------------------------- FP32 LS-apply without allocation
+// ls_apply_f32_noalloc runs the same three passes as ls_apply32, but its n x P
+// scratch and its twiddle tables are file-scope device arrays of fixed size
+// instead of memory owned by a handle, so a call allocates nothing.  Those
+// arrays exist once per GPU that loads the library and stay until exit; every
+// call on a device uses the same scratch.
+namespace {
+
+constexpr size_t kNoAllocMaxElems = (size_t)1 << 21;  // n * P <= 2^21 float2 (16 MiB): n <= 1024
+constexpr int kNoAllocTwElems = 4096;                  // twiddles of every P = 16..2048, P at offset P - 16
+constexpr int kNoAllocMaxDevices = 64;
+
+static __device__ __align__(256) float2 g_noalloc_scratch[kNoAllocMaxElems];
+static __device__ __align__(256) float2 g_noalloc_tw[kNoAllocTwElems];
+
+struct NoAllocDevice {
+    bool ready = false;
+    float2* scratch = nullptr;  // device address of g_noalloc_scratch on this device
+    float2* tw = nullptr;       // device address of g_noalloc_tw on this device
+};
+NoAllocDevice g_noalloc_dev[kNoAllocMaxDevices];
+std::mutex g_noalloc_mu;
+
+// tw[P - 16 + m] = exp(-2 pi i m / P) for every P = 16, 32, ..., 2048 and m < P
+__global__ void k_noalloc_twiddles(float2* tw) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= kNoAllocTwElems - 16) return;
+    int P = 16;
+    while (k >= 2 * P - 16) P *= 2;  // segment [P - 16, 2P - 16) belongs to P
+    const int m = k - (P - 16);
+    double s, c;
+    sincospi(2.0 * (double)m / (double)P, &s, &c);
+    tw[k] = make_float2((float)c, (float)-s);
+}
+
+// First call on a device (that device current): resolve the arrays' device
+// addresses, fill the twiddle tables and raise the shared-memory limit of the
+// column kernel.  Synchronises `stream` once.
+int noalloc_setup(int dev, cudaStream_t stream, NoAllocDevice** out) {
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    NoAllocDevice& d = g_noalloc_dev[dev];
+    if (!d.ready) {
+        void* p = nullptr;
+        LS_CUDA(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+        d.scratch = static_cast<float2*>(p);
+        LS_CUDA(cudaGetSymbolAddress(&p, g_noalloc_tw));
+        d.tw = static_cast<float2*>(p);
+        k_noalloc_twiddles<<<(kNoAllocTwElems + 255) / 256, 256, 0, stream>>>(d.tw);
+        LS_CUDA(cudaPeekAtLastError());
+        LS_TRY(allow_smem(k_cols<float, EC32, CW32, 0>, sizeof(float2) * CW32 * 2048));
+        LS_CUDA(cudaStreamSynchronize(stream));
+        d.ready = true;
+    }
+    *out = &d;
+    return LS_OK;
+}
+
+}  // namespace
+
+extern "C" int ls_apply_f32_noalloc(int n, const float* m, const ls_c32* ghat, const ls_c32* u, ls_c32* y,
+                                    void* stream_) {
+    if (n < 8 || !m || !ghat || !u || !y) return LS_EINVAL;
+    int lp = 0;
+    while ((1 << lp) < 2 * n - 1) ++lp;
+    const int P = 1 << lp;
+    if ((size_t)n * P > kNoAllocMaxElems || P > 2048) return LS_ETOOBIG;
+    int dev = 0;
+    LS_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kNoAllocMaxDevices) return LS_EINVAL;
+    cudaStream_t stream = static_cast<cudaStream_t>(stream_);
+    NoAllocDevice* d = nullptr;
+    LS_TRY(noalloc_setup(dev, stream, &d));
+    const float2* tw = d->tw + (P - 16);
+    const FftPlan pr = make_plan(lp, 4), pc = make_plan(lp, 3);
+    float2* X = d->scratch;
+    SrcMU<float, float2> src{m, reinterpret_cast<const float2*>(u), n};
+    k_rows_fwd<float, E32, SrcMU<float, float2>><<<n, P / E32, sizeof(float2) * P, stream>>>(pr, n, src, X, tw);
+    LS_CUDA(cudaPeekAtLastError());
+    k_cols<float, EC32, CW32, 0><<<P / CW32, CW32 * (P / EC32), sizeof(float2) * CW32 * P, stream>>>(
+        pc, n, n, X, reinterpret_cast<const float2*>(ghat), (float2*)nullptr, 0.0f, tw);
+    LS_CUDA(cudaPeekAtLastError());
+    DstApply<float2> dst{reinterpret_cast<const float2*>(u), reinterpret_cast<float2*>(y), n};
+    k_rows_inv<float, E32, DstApply<float2>><<<n, P / E32, sizeof(float2) * P, stream>>>(pr, n, X, dst, tw);
+    LS_CUDA(cudaPeekAtLastError());
+    return LS_OK;
+}
