@@ -29,8 +29,8 @@
 //   backward level k:  x_j = D_j^{-1} b_j - P_j x_{j-1} - Q_j x_{j+1} (odd j)
 //            level 0:  x_j = y_j - D_j^{-1} (W_j x_{j-1} + E_j x_{j+1}) (odd j)
 // Each kernel is one launch per level over all blocks of that level; a block of
-// threads handles one q x q mat-vec set with one thread per row, reading the
-// column-major matrices coalesced.
+// 256 threads handles one block's mat-vecs, its warps splitting the columns of
+// the column-major matrices (coalesced reads, all loads independent).
 #include "ls_internal.cuh"
 #include "ls_strip.cuh"
 
@@ -43,32 +43,127 @@ struct Pool {
     __device__ __forceinline__ const cpx_t<T>* mat(size_t off) const { return base + off * qq; }
 };
 
-// acc -= M v (or +=), thread `r` = row; M column-major q x q, v in shared memory
-template <typename T>
-__device__ __forceinline__ cpx_t<T> matvec_row(const cpx_t<T>* __restrict__ M, const cpx_t<T>* v, int q, int r,
-                                               cpx_t<T> acc, bool subtract) {
-    if (subtract) {
+// Mat-vecs spread over a whole block of kMvThreads threads: warp w takes columns
+// w, w + kMvWarps, ...; lane l takes rows l, l + 32, ... (RPT rows, q <= 32 RPT).
+// Every thread issues its loads independently of the others (column-major
+// matrices, so a warp reads 32 consecutive entries of a column), and the
+// per-warp partial sums are reduced through shared memory.  A thread-per-row
+// loop instead walks all q columns of a matrix one load at a time.
+constexpr int kMvWarps = 8;
+constexpr int kMvThreads = 32 * kMvWarps;
+
+template <typename T, int RPT>
+__device__ __forceinline__ void mv_accumulate(const cpx_t<T>* __restrict__ M, const cpx_t<T>* vs, int q,
+                                              cpx_t<T> (&part)[RPT]) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll 4
-        for (int c = 0; c < q; ++c) acc = cfms(__ldg(&M[(size_t)c * q + r]), v[c], acc);
-    } else {
-#pragma unroll 4
-        for (int c = 0; c < q; ++c) acc = cfma(__ldg(&M[(size_t)c * q + r]), v[c], acc);
+    for (int c = warp; c < q; c += kMvWarps) {
+        const cpx_t<T> vc = vs[c];
+#pragma unroll
+        for (int k = 0; k < RPT; ++k) {
+            const int r = lane + 32 * k;
+            if (r < q) part[k] = cfma(__ldg(&M[(size_t)c * q + r]), vc, part[k]);
+        }
     }
-    return acc;
 }
 
-// level 0, odd blocks: y_j = Dinv_j b_j
-template <typename T>
-__global__ void k_l0_odd(int q, Pool<T> pool, size_t off_dinv, cpx_t<T>* __restrict__ x) {
+// red: kMvWarps * q entries of shared memory; returns the full sum for row threadIdx.x (< q)
+template <typename T, int RPT>
+__device__ __forceinline__ cpx_t<T> mv_reduce(cpx_t<T> (&part)[RPT], cpx_t<T>* red, int q) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < RPT; ++k) {
+        const int r = lane + 32 * k;
+        if (r < q) red[warp * q + r] = part[k];
+    }
+    __syncthreads();
+    cpx_t<T> s = czero<cpx_t<T>>();
+    if ((int)threadIdx.x < q)
+        for (int w = 0; w < kMvWarps; ++w) s = s + red[w * q + threadIdx.x];
+    return s;
+}
+
+// One step of the reduction for one block: out = base + sum_t M_t v_t, where the
+// vectors are staged in shared memory with their signs applied.  MODE:
+//   0 (level 0 odd):      x_j = D^{-1} x_j
+//   1 (forward, level k): x_j = x_j - F x_{j-1} - G x_{j+1}            (even j)
+//   2 (backward, level k): x_j = D^{-1} x_j - P x_{j-1} - Q x_{j+1}     (odd j)
+//   3 (top block):         x_0 = D^{-1} x_0
+template <typename T, int RPT, int MODE>
+__global__ void __launch_bounds__(kMvThreads) k_cr_step(int q, int k, int nk, Pool<T> pool, size_t off_a,
+                                                       size_t off_b, size_t off_c, cpx_t<T>* __restrict__ x) {
     using C = cpx_t<T>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    C* vb = reinterpret_cast<C*>(smem_raw);
-    const int j = 2 * blockIdx.x + 1;
+    C* v0 = reinterpret_cast<C*>(smem_raw);
+    C* v1 = v0 + q;
+    C* v2 = v1 + q;
+    C* red = v2 + q;
+    const int idx = blockIdx.x;
+    const size_t s = (size_t)1 << k;
+    const int j = MODE == 1 ? 2 * idx : (MODE == 3 ? 0 : 2 * idx + 1);
+    const bool hw = j >= 1, he = j + 1 < nk;
     const int r = threadIdx.x;
-    C* xb = x + (size_t)j * q;
-    if (r < q) vb[r] = xb[r];
+    C* xj = x + ((size_t)j * s) * q;
+    if (r < q) {
+        if (MODE == 0 || MODE == 3) v0[r] = xj[r];
+        if (MODE == 1) {
+            v1[r] = hw ? -x[((size_t)(j - 1) * s) * q + r] : czero<C>();
+            v2[r] = he ? -x[((size_t)(j + 1) * s) * q + r] : czero<C>();
+        }
+        if (MODE == 2) {
+            v0[r] = xj[r];
+            v1[r] = -x[((size_t)(j - 1) * s) * q + r];
+            v2[r] = he ? -x[((size_t)(j + 1) * s) * q + r] : czero<C>();
+        }
+    }
     __syncthreads();
-    if (r < q) xb[r] = matvec_row<T>(pool.mat(off_dinv + blockIdx.x), vb, q, r, czero<C>(), false);
+    C part[RPT];
+#pragma unroll
+    for (int i = 0; i < RPT; ++i) part[i] = czero<C>();
+    if (MODE == 0 || MODE == 3) mv_accumulate<T, RPT>(pool.mat(off_a + idx), v0, q, part);
+    if (MODE == 1) {
+        if (hw) mv_accumulate<T, RPT>(pool.mat(off_b + idx), v1, q, part);
+        if (he) mv_accumulate<T, RPT>(pool.mat(off_c + idx), v2, q, part);
+    }
+    if (MODE == 2) {
+        mv_accumulate<T, RPT>(pool.mat(off_a + idx), v0, q, part);
+        mv_accumulate<T, RPT>(pool.mat(off_b + idx), v1, q, part);
+        if (he) mv_accumulate<T, RPT>(pool.mat(off_c + idx), v2, q, part);
+    }
+    const C sum = mv_reduce<T, RPT>(part, red, q);
+    if (r < q) xj[r] = MODE == 1 ? xj[r] + sum : sum;
+}
+
+// level 0 backward, odd blocks: x_j = y_j - D^{-1} (W_j x_{j-1} + E_j x_{j+1})
+template <typename T, int RPT>
+__global__ void __launch_bounds__(kMvThreads) k_cr_l0_back(StripGeom g, const StencilTables* __restrict__ tab,
+                                                          const double* __restrict__ m, int l, int nb, Pool<T> pool,
+                                                          size_t off_dinv, cpx_t<T>* __restrict__ x) {
+    using C = cpx_t<T>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* vt = reinterpret_cast<C*>(smem_raw);
+    C* red = vt + g.q;
+    const int o = blockIdx.x;
+    const int j = 2 * o + 1;
+    const int r = threadIdx.x, q = g.q;
+    if (r < q) {
+        double2 acc = make_double2(0, 0);
+#pragma unroll
+        for (int dz = -1; dz <= 1; ++dz) {
+            const int rr = r + dz;
+            if (rr < 0 || rr >= q) continue;
+            acc = cfma(strip_coef(g, tab, m, l, r, j, -1, dz), ccast<double2>(x[(size_t)(j - 1) * q + rr]), acc);
+            if (j + 1 < nb) acc = cfma(strip_coef(g, tab, m, l, r, j, 1, dz), ccast<double2>(x[(size_t)(j + 1) * q + rr]), acc);
+        }
+        vt[r] = -ccast<C>(acc);
+    }
+    __syncthreads();
+    C part[RPT];
+#pragma unroll
+    for (int i = 0; i < RPT; ++i) part[i] = czero<C>();
+    mv_accumulate<T, RPT>(pool.mat(off_dinv + o), vt, q, part);
+    const C sum = mv_reduce<T, RPT>(part, red, q);
+    if (r < q) x[(size_t)j * q + r] = x[(size_t)j * q + r] + sum;
 }
 
 // level 0, even blocks: b_j -= W_j y_{j-1} + E_j y_{j+1} (W, E tridiagonal from the stencil)
@@ -88,171 +183,6 @@ __global__ void k_l0_even(StripGeom g, const StencilTables* __restrict__ tab, co
         if (j + 1 < nb) acc = cfms(strip_coef(g, tab, m, l, r, j, 1, dz), ccast<double2>(x[(size_t)(j + 1) * q + rr]), acc);
     }
     x[(size_t)j * q + r] = ccast<C>(acc);
-}
-
-// level k >= 1 forward, even blocks j of level k (global block j << k):
-// b_j -= F_j b_{j-1} + G_j b_{j+1}
-template <typename T>
-__global__ void k_fwd(int q, int k, int nk, Pool<T> pool, size_t off_f, size_t off_g, cpx_t<T>* __restrict__ x) {
-    using C = cpx_t<T>;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    C* vw = reinterpret_cast<C*>(smem_raw);
-    C* ve = vw + q;
-    const int e = blockIdx.x;  // even index / 2
-    const int j = 2 * e;
-    const int r = threadIdx.x;
-    const bool hw = j >= 1, he = j + 1 < nk;
-    const size_t s = (size_t)1 << k;
-    if (r < q) {
-        if (hw) vw[r] = x[((size_t)(j - 1) * s) * q + r];
-        if (he) ve[r] = x[((size_t)(j + 1) * s) * q + r];
-    }
-    __syncthreads();
-    if (r >= q) return;
-    C acc = x[((size_t)j * s) * q + r];
-    if (hw) acc = matvec_row<T>(pool.mat(off_f + e), vw, q, r, acc, true);
-    if (he) acc = matvec_row<T>(pool.mat(off_g + e), ve, q, r, acc, true);
-    x[((size_t)j * s) * q + r] = acc;
-}
-
-// top: x_0 = Dinv b_0
-template <typename T>
-__global__ void k_top(int q, Pool<T> pool, size_t off_top, cpx_t<T>* __restrict__ x) {
-    using C = cpx_t<T>;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    C* vb = reinterpret_cast<C*>(smem_raw);
-    const int r = threadIdx.x;
-    if (r < q) vb[r] = x[r];
-    __syncthreads();
-    if (r < q) x[r] = matvec_row<T>(pool.mat(off_top), vb, q, r, czero<C>(), false);
-}
-
-// The last levels of the reduction (at most kTopBlocks blocks) in one block of
-// threads: forward levels k0..K-1, the top block, backward levels K-1..k0, with
-// block barriers between levels instead of separate launches.  Thread group g
-// (of kGroups, 128 threads each) handles blocks g, g + kGroups, ...; global
-// memory written before a __syncthreads is visible to the whole block after it.
-constexpr int kGroups = 4;
-constexpr int kTopBlocks = 2 * kGroups;
-
-struct TopLevels {
-    int k0, K;
-    int nk[16];
-    size_t off_dinv[16], off_p[16], off_q[16], off_f[16], off_g[16];
-    size_t off_top;
-};
-
-template <typename T>
-__global__ void __launch_bounds__(128 * kGroups) k_top_levels(int q, TopLevels tl, Pool<T> pool, cpx_t<T>* __restrict__ x) {
-    using C = cpx_t<T>;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int grp = threadIdx.x / 128, r = threadIdx.x % 128;
-    C* v0 = reinterpret_cast<C*>(smem_raw) + (size_t)grp * 3 * q;
-    C* v1 = v0 + q;
-    C* v2 = v1 + q;
-    for (int k = tl.k0; k < tl.K; ++k) {  // forward: even blocks
-        const int nk = tl.nk[k];
-        const size_t s = (size_t)1 << k;
-        const int neven = (nk + 1) / 2;
-        for (int base = 0; base < neven; base += kGroups) {
-            const int e = base + grp;
-            const int j = 2 * e;
-            const bool act = e < neven, hw = act && j >= 1, he = act && j + 1 < nk;
-            if (r < q) {
-                if (hw) v0[r] = x[((size_t)(j - 1) * s) * q + r];
-                if (he) v1[r] = x[((size_t)(j + 1) * s) * q + r];
-            }
-            __syncthreads();
-            if (act && r < q) {
-                C acc = x[((size_t)j * s) * q + r];
-                if (hw) acc = matvec_row<T>(pool.mat(tl.off_f[k] + e), v0, q, r, acc, true);
-                if (he) acc = matvec_row<T>(pool.mat(tl.off_g[k] + e), v1, q, r, acc, true);
-                x[((size_t)j * s) * q + r] = acc;
-            }
-            __syncthreads();
-        }
-    }
-    if (grp == 0 && r < q) v0[r] = x[r];  // top block
-    __syncthreads();
-    if (grp == 0 && r < q) x[r] = matvec_row<T>(pool.mat(tl.off_top), v0, q, r, czero<C>(), false);
-    __syncthreads();
-    for (int k = tl.K - 1; k >= tl.k0; --k) {  // backward: odd blocks
-        const int nk = tl.nk[k];
-        const size_t s = (size_t)1 << k;
-        const int nodd = nk / 2;
-        for (int base = 0; base < nodd; base += kGroups) {
-            const int o = base + grp;
-            const int j = 2 * o + 1;
-            const bool act = o < nodd, he = act && j + 1 < nk;
-            if (act && r < q) {
-                v0[r] = x[((size_t)j * s) * q + r];
-                v1[r] = x[((size_t)(j - 1) * s) * q + r];
-                if (he) v2[r] = x[((size_t)(j + 1) * s) * q + r];
-            }
-            __syncthreads();
-            if (act && r < q) {
-                C acc = matvec_row<T>(pool.mat(tl.off_dinv[k] + o), v0, q, r, czero<C>(), false);
-                acc = matvec_row<T>(pool.mat(tl.off_p[k] + o), v1, q, r, acc, true);
-                if (he) acc = matvec_row<T>(pool.mat(tl.off_q[k] + o), v2, q, r, acc, true);
-                x[((size_t)j * s) * q + r] = acc;
-            }
-            __syncthreads();
-        }
-    }
-}
-
-// level k >= 1 backward, odd blocks: x_j = Dinv_j b_j - P_j x_{j-1} - Q_j x_{j+1}
-template <typename T>
-__global__ void k_bwd(int q, int k, int nk, Pool<T> pool, size_t off_dinv, size_t off_p, size_t off_q,
-                      cpx_t<T>* __restrict__ x) {
-    using C = cpx_t<T>;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    C* vb = reinterpret_cast<C*>(smem_raw);
-    C* vw = vb + q;
-    C* ve = vw + q;
-    const int o = blockIdx.x;  // odd index
-    const int j = 2 * o + 1;
-    const int r = threadIdx.x;
-    const bool he = j + 1 < nk;
-    const size_t s = (size_t)1 << k;
-    if (r < q) {
-        vb[r] = x[((size_t)j * s) * q + r];
-        vw[r] = x[((size_t)(j - 1) * s) * q + r];
-        if (he) ve[r] = x[((size_t)(j + 1) * s) * q + r];
-    }
-    __syncthreads();
-    if (r >= q) return;
-    C acc = matvec_row<T>(pool.mat(off_dinv + o), vb, q, r, czero<C>(), false);
-    acc = matvec_row<T>(pool.mat(off_p + o), vw, q, r, acc, true);
-    if (he) acc = matvec_row<T>(pool.mat(off_q + o), ve, q, r, acc, true);
-    x[((size_t)j * s) * q + r] = acc;
-}
-
-// level 0 backward, odd blocks: x_j = y_j - Dinv_j (W_j x_{j-1} + E_j x_{j+1})
-template <typename T>
-__global__ void k_l0_back(StripGeom g, const StencilTables* __restrict__ tab, const double* __restrict__ m, int l,
-                          int nb, Pool<T> pool, size_t off_dinv, cpx_t<T>* __restrict__ x) {
-    using C = cpx_t<T>;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    C* vt = reinterpret_cast<C*>(smem_raw);
-    const int o = blockIdx.x;
-    const int j = 2 * o + 1;
-    const int r = threadIdx.x, q = g.q;
-    if (r < q) {
-        double2 acc = make_double2(0, 0);
-#pragma unroll
-        for (int dz = -1; dz <= 1; ++dz) {
-            const int rr = r + dz;
-            if (rr < 0 || rr >= q) continue;
-            acc = cfma(strip_coef(g, tab, m, l, r, j, -1, dz), ccast<double2>(x[(size_t)(j - 1) * q + rr]), acc);
-            if (j + 1 < nb) acc = cfma(strip_coef(g, tab, m, l, r, j, 1, dz), ccast<double2>(x[(size_t)(j + 1) * q + rr]), acc);
-        }
-        vt[r] = ccast<C>(acc);
-    }
-    __syncthreads();
-    if (r >= q) return;
-    C* xb = x + (size_t)j * q;
-    xb[r] = matvec_row<T>(pool.mat(off_dinv + o), vt, q, r, xb[r], true);
 }
 
 // g^l = chi_{Omega^l} g (+ injection from the layer above), copied to the solution buffer
@@ -350,8 +280,8 @@ __global__ void k_add(size_t N, const double2* __restrict__ a, double2* __restri
 
 StripGeom geom_of(const ls_handle* h) { return StripGeom{h->n, h->t, h->E, h->q, h->opts.shift / h->omega}; }
 
-template <typename T>
-int cr_solve(ls_handle* h, int dir, int l, cpx_t<T>* x) {
+template <typename T, int RPT>
+int cr_solve_rpt(ls_handle* h, int dir, int l, cpx_t<T>* x) {
     using C = cpx_t<T>;
     const DirFactors& F = h->fac[dir];
     const int q = h->q, n = h->n;
@@ -362,39 +292,39 @@ int cr_solve(ls_handle* h, int dir, int l, cpx_t<T>* x) {
     Pool<T> pool{base + (size_t)l * F.mats_per_strip * qq, qq};
     const StripGeom g = geom_of(h);
     const int thr = (q + 31) / 32 * 32;
+    const size_t sm_step = (3 + kMvWarps) * sizeof(C) * q;
+    const size_t sm_back = (1 + kMvWarps) * sizeof(C) * q;
     const CrLevel& l0 = F.lev[0];
-    if (l0.nodd) LS_LAUNCH(h, k_l0_odd<T>, l0.nodd, thr, sizeof(C) * q, q, pool, l0.off_dinv, x);
+    if (l0.nodd)
+        LS_LAUNCH(h, (k_cr_step<T, RPT, 0>), l0.nodd, kMvThreads, sm_step, q, 0, l0.nk, pool, l0.off_dinv,
+                  (size_t)0, (size_t)0, x);
     LS_LAUNCH(h, k_l0_even<T>, l0.neven, thr, 0, g, F.tab, F.m, l, n, x);
-    // levels >= 1 with more than kTopBlocks blocks get one launch each; the rest
-    // (and the top block) run in one single-block launch
-    int k0 = 1;
-    while (k0 < F.K && F.lev[k0].nk > kTopBlocks) ++k0;
-    for (int k = 1; k < k0; ++k) {
+    for (int k = 1; k < F.K; ++k) {
         const CrLevel& lv = F.lev[k];
-        LS_LAUNCH(h, k_fwd<T>, lv.neven, thr, 2 * sizeof(C) * q, q, k, lv.nk, pool, lv.off_f, lv.off_g, x);
+        LS_LAUNCH(h, (k_cr_step<T, RPT, 1>), lv.neven, kMvThreads, sm_step, q, k, lv.nk, pool, (size_t)0, lv.off_f,
+                  lv.off_g, x);
     }
-    if (F.K > 16) return LS_EINVAL;
-    TopLevels tl{};
-    tl.k0 = k0;
-    tl.K = F.K;
-    for (int k = k0; k < F.K; ++k) {
-        tl.nk[k] = F.lev[k].nk;
-        tl.off_dinv[k] = F.lev[k].off_dinv;
-        tl.off_p[k] = F.lev[k].off_p;
-        tl.off_q[k] = F.lev[k].off_q;
-        tl.off_f[k] = F.lev[k].off_f;
-        tl.off_g[k] = F.lev[k].off_g;
-    }
-    tl.off_top = F.off_top;
-    LS_LAUNCH(h, k_top_levels<T>, 1, 128 * kGroups, 3 * kGroups * sizeof(C) * q, q, tl, pool, x);
-    for (int k = k0 - 1; k >= 1; --k) {
+    LS_LAUNCH(h, (k_cr_step<T, RPT, 3>), 1, kMvThreads, sm_step, q, 0, 1, pool, F.off_top, (size_t)0, (size_t)0, x);
+    for (int k = F.K - 1; k >= 1; --k) {
         const CrLevel& lv = F.lev[k];
         if (lv.nodd)
-            LS_LAUNCH(h, k_bwd<T>, lv.nodd, thr, 3 * sizeof(C) * q, q, k, lv.nk, pool, lv.off_dinv, lv.off_p,
-                      lv.off_q, x);
+            LS_LAUNCH(h, (k_cr_step<T, RPT, 2>), lv.nodd, kMvThreads, sm_step, q, k, lv.nk, pool, lv.off_dinv,
+                      lv.off_p, lv.off_q, x);
     }
-    if (l0.nodd) LS_LAUNCH(h, k_l0_back<T>, l0.nodd, thr, sizeof(C) * q, g, F.tab, F.m, l, n, pool, l0.off_dinv, x);
+    if (l0.nodd)
+        LS_LAUNCH(h, (k_cr_l0_back<T, RPT>), l0.nodd, kMvThreads, sm_back, g, F.tab, F.m, l, n, pool, l0.off_dinv, x);
     return LS_OK;
+}
+
+template <typename T>
+int cr_solve(ls_handle* h, int dir, int l, cpx_t<T>* x) {
+    const int rpt = (h->q + 31) / 32;
+    switch (rpt) {
+        case 1: return cr_solve_rpt<T, 1>(h, dir, l, x);
+        case 2: return cr_solve_rpt<T, 2>(h, dir, l, x);
+        case 3: return cr_solve_rpt<T, 3>(h, dir, l, x);
+        default: return cr_solve_rpt<T, 4>(h, dir, l, x);
+    }
 }
 
 template <typename T>
