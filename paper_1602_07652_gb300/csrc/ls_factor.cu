@@ -244,6 +244,29 @@ __global__ void __launch_bounds__(256) k_gemm(const GemmTask* __restrict__ tasks
     }
 }
 
+// Couplings the local solves read (so the solve path never evaluates the FP64
+// stencil coefficients): level-0 west/east blocks and the four injection rows.
+template <typename C>
+__global__ void k_coef_tables(StripGeom g, const StencilTables* tab, const double* m, int L, C* cw, C* ce, C* cinj) {
+    const int n = g.n, q = g.q, E = g.E, t = g.t;
+    const size_t total = (size_t)L * n * 3 * q;
+    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+        const int r = (int)(e % q);
+        const int dzi = (int)((e / q) % 3);
+        const int i = (int)((e / ((size_t)3 * q)) % n);
+        const int l = (int)(e / ((size_t)3 * q * n));
+        cw[e] = ccast<C>(strip_coef(g, tab, m, l, r, i, -1, dzi - 1));
+        ce[e] = ccast<C>(strip_coef(g, tab, m, l, r, i, 1, dzi - 1));
+        if (r == 0) {  // one thread per (l, i, dx) fills the four injection rows
+            const int dx = dzi - 1;
+            const int rows[4] = {E + t - 1, E + t, E, E - 1};
+            const int dzs[4] = {1, -1, -1, 1};
+            for (int sl = 0; sl < 4; ++sl)
+                cinj[(((size_t)l * 4 + sl) * 3 + dzi) * n + i] = ccast<C>(strip_coef(g, tab, m, l, rows[sl], i, dx, dzs[sl]));
+        }
+    }
+}
+
 __global__ void k_to32(size_t cnt, const double2* __restrict__ a, float2* __restrict__ b) {
     for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < cnt; i += (size_t)gridDim.x * blockDim.x)
         b[i] = ccast<float2>(a[i]);
@@ -464,6 +487,22 @@ int factor_direction(ls_handle* h, int dir, Scratch& S) {
         LS_TRY(upload(h, it, &S.inv, &S.inv_cap));
         LS_LAUNCH(h, k_invert, (unsigned)it.size(), 256, inv_smem, (int)it.size(), S.inv, g, tab, m, S.err);
     }
+    {  // coupling tables for the solve
+        const size_t cnt = (size_t)L * n * 3 * q, ci = (size_t)L * 4 * 3 * n;
+        if (h->prec == LS_MIXED) {
+            LS_CUDA(cudaMalloc(&F.cw, sizeof(float2) * cnt));
+            LS_CUDA(cudaMalloc(&F.ce, sizeof(float2) * cnt));
+            LS_CUDA(cudaMalloc(&F.cinj, sizeof(float2) * ci));
+            LS_LAUNCH(h, k_coef_tables<float2>, 1216, 256, 0, g, tab, m, L, static_cast<float2*>(F.cw),
+                      static_cast<float2*>(F.ce), static_cast<float2*>(F.cinj));
+        } else {
+            LS_CUDA(cudaMalloc(&F.cw, sizeof(double2) * cnt));
+            LS_CUDA(cudaMalloc(&F.ce, sizeof(double2) * cnt));
+            LS_CUDA(cudaMalloc(&F.cinj, sizeof(double2) * ci));
+            LS_LAUNCH(h, k_coef_tables<double2>, 1216, 256, 0, g, tab, m, L, static_cast<double2*>(F.cw),
+                      static_cast<double2*>(F.ce), static_cast<double2*>(F.cinj));
+        }
+    }
     int herr = 0;
     LS_CUDA(cudaMemcpyAsync(&herr, S.err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
     LS_CUDA(cudaStreamSynchronize(h->stream));
@@ -491,9 +530,14 @@ int ls_factor_all(ls_handle* h) {
 void ls_factor_free(ls_handle* h) {
     ls_bd_graph_free(h);
     for (int d = 0; d < 2; ++d) {
-        cudaFree(h->fac[d].pool64);
-        cudaFree(h->fac[d].pool32);
-        h->fac[d].pool64 = nullptr;
-        h->fac[d].pool32 = nullptr;
+        DirFactors& F = h->fac[d];
+        cudaFree(F.pool64);
+        cudaFree(F.pool32);
+        cudaFree(F.cw);
+        cudaFree(F.ce);
+        cudaFree(F.cinj);
+        F.pool64 = nullptr;
+        F.pool32 = nullptr;
+        F.cw = F.ce = F.cinj = nullptr;
     }
 }

@@ -107,13 +107,19 @@ __device__ __forceinline__ void stage_compute(C (&v)[E], int j, int TPC, int ls,
     }
 }
 
+// Shared-memory slot of element idx: one padding slot every 2^PS elements, so that
+// the strided stores of the first Stockham stage (stride = radix) and the unit-
+// stride loads of the others both hit distinct banks.
+template <int PS>
+__device__ __forceinline__ int padx(int idx) { return idx + (idx >> PS); }
+
 // A full transform of length P = plan.P.  On entry v holds the first stage's
 // inputs (element j + e*TPC + r*P/R0 in v[e*R0 + r]); on exit v holds the last
-// stage's outputs in the same form for the last radix.  buf: CW interleaved
-// transforms of length P in shared memory (element idx of column c at idx*CW + c).
+// stage's outputs in the same form for the last radix.  buf: the transform in
+// shared memory, element idx at slot padx<PS>(idx) (P + P/2^PS slots).
 // The inverse (DIR = -1) runs the plan's stages in reverse order.
-template <int E, int DIR, int CW, int MAXR = 16, typename C>
-__device__ __forceinline__ void fft_core(C (&v)[E], C* buf, const FftPlan& pl, int j, int TPC, int c,
+template <int E, int DIR, int PS, typename C>
+__device__ __forceinline__ void fft_core(C (&v)[E], C* buf, const FftPlan& pl, int j, int TPC,
                                          const C* __restrict__ tw) {
     int ls = 0;
     for (int s = 0; s < pl.ns; ++s) {
@@ -123,7 +129,7 @@ __device__ __forceinline__ void fft_core(C (&v)[E], C* buf, const FftPlan& pl, i
             for (int qq = 0; qq < E; ++qq) {
                 const int e = qq >> lr, r = qq & ((1 << lr) - 1);
                 const int idx = j + e * TPC + (r << (pl.lp - lr));
-                v[qq] = buf[idx * CW + c];
+                v[qq] = buf[padx<PS>(idx)];
             }
         }
         switch (lr) {
@@ -133,7 +139,7 @@ __device__ __forceinline__ void fft_core(C (&v)[E], C* buf, const FftPlan& pl, i
                 if constexpr (E >= 8) stage_compute<8, DIR>(v, j, TPC, ls, pl.lp, tw);
                 break;
             default:
-                if constexpr (E >= 16 && MAXR >= 16) stage_compute<16, DIR>(v, j, TPC, ls, pl.lp, tw);
+                if constexpr (E >= 16) stage_compute<16, DIR>(v, j, TPC, ls, pl.lp, tw);
                 break;
         }
         if (s < pl.ns - 1) {
@@ -143,7 +149,120 @@ __device__ __forceinline__ void fft_core(C (&v)[E], C* buf, const FftPlan& pl, i
                 const int e = qq >> lr, r = qq & ((1 << lr) - 1);
                 const int b = j + e * TPC;
                 const int dst = ((b >> ls) << (ls + lr)) + (b & ((1 << ls) - 1)) + (r << ls);
-                buf[dst * CW + c] = v[qq];
+                buf[padx<PS>(dst)] = v[qq];
+            }
+            __syncthreads();
+        }
+        ls += lr;
+    }
+}
+
+// ---------------------------------------------------------------- column-vectorised transform
+// The column pass transforms CW adjacent columns together: a thread owns the same
+// butterflies of all CW columns, so the butterfly index arithmetic and the
+// twiddle loads are paid once per CW elements, and every shared-memory and
+// global access moves the CW contiguous values of one row (32 bytes).
+template <typename C, int CW>
+struct RowVec;  // CW contiguous complex values
+template <>
+struct RowVec<float2, 4> {
+    __device__ __forceinline__ static void load(const float2* p, float2 (&o)[4]) {
+        const float4 a = reinterpret_cast<const float4*>(p)[0], b = reinterpret_cast<const float4*>(p)[1];
+        o[0] = make_float2(a.x, a.y); o[1] = make_float2(a.z, a.w); o[2] = make_float2(b.x, b.y); o[3] = make_float2(b.z, b.w);
+    }
+    __device__ __forceinline__ static void store(float2* p, const float2 (&o)[4]) {
+        reinterpret_cast<float4*>(p)[0] = make_float4(o[0].x, o[0].y, o[1].x, o[1].y);
+        reinterpret_cast<float4*>(p)[1] = make_float4(o[2].x, o[2].y, o[3].x, o[3].y);
+    }
+};
+template <>
+struct RowVec<double2, 2> {
+    __device__ __forceinline__ static void load(const double2* p, double2 (&o)[2]) { o[0] = p[0]; o[1] = p[1]; }
+    __device__ __forceinline__ static void store(double2* p, const double2 (&o)[2]) { p[0] = o[0]; p[1] = o[1]; }
+};
+
+template <int R, int DIR, int E, int CW, typename C>
+__device__ __forceinline__ void stage_compute_vec(C (&v)[CW][E], int j, int TPC, int ls, int lp,
+                                                  const C* __restrict__ tw) {
+    constexpr int LR = ilog2c<R>();
+#pragma unroll
+    for (int e = 0; e < E / R; ++e) {
+        if (ls > 0) {
+            const int b = j + e * TPC;
+            const int k = b & ((1 << ls) - 1);
+            const int sh = lp - ls - LR;
+#pragma unroll
+            for (int r = 1; r < R; ++r) {
+                C w = __ldg(&tw[(k * r) << sh]);
+                if (DIR < 0) w.y = -w.y;
+#pragma unroll
+                for (int c = 0; c < CW; ++c) v[c][e * R + r] = v[c][e * R + r] * w;
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < CW; ++c) dft_reg<R, DIR>(&v[c][e * R]);
+    }
+}
+
+// Same contract as fft_core, with v[c][.] holding column c.  Shared memory holds
+// each row's CW values as two 16-byte halves in two separate padded arrays
+// (half h of element idx at bufh[padx<3>(idx)]), so 128-bit accesses of
+// consecutive elements are conflict-free.
+template <typename C, int CW>
+struct Halves;
+template <>
+struct Halves<float2, 4> {  // half = 2 columns = float4
+    using H = float4;
+    __device__ __forceinline__ static void split(const float2 (&r)[4], float4& a, float4& b) {
+        a = make_float4(r[0].x, r[0].y, r[1].x, r[1].y);
+        b = make_float4(r[2].x, r[2].y, r[3].x, r[3].y);
+    }
+    __device__ __forceinline__ static void join(const float4& a, const float4& b, float2 (&r)[4]) {
+        r[0] = make_float2(a.x, a.y); r[1] = make_float2(a.z, a.w); r[2] = make_float2(b.x, b.y); r[3] = make_float2(b.z, b.w);
+    }
+};
+template <>
+struct Halves<double2, 2> {  // half = 1 column = double2
+    using H = double2;
+    __device__ __forceinline__ static void split(const double2 (&r)[2], double2& a, double2& b) { a = r[0]; b = r[1]; }
+    __device__ __forceinline__ static void join(const double2& a, const double2& b, double2 (&r)[2]) { r[0] = a; r[1] = b; }
+};
+
+template <int E, int DIR, int CW, typename C>
+__device__ __forceinline__ void fft_core_vec(C (&v)[CW][E], typename Halves<C, CW>::H* buf0,
+                                             typename Halves<C, CW>::H* buf1, const FftPlan& pl, int j, int TPC,
+                                             const C* __restrict__ tw) {
+    using HV = Halves<C, CW>;
+    int ls = 0;
+    for (int s = 0; s < pl.ns; ++s) {
+        const int lr = pl.lr[DIR > 0 ? s : pl.ns - 1 - s];
+        if (s > 0) {
+#pragma unroll
+            for (int qq = 0; qq < E; ++qq) {
+                const int e = qq >> lr, r = qq & ((1 << lr) - 1);
+                const int idx = padx<3>(j + e * TPC + (r << (pl.lp - lr)));
+                C row[CW];
+                HV::join(buf0[idx], buf1[idx], row);
+#pragma unroll
+                for (int c = 0; c < CW; ++c) v[c][qq] = row[c];
+            }
+        }
+        switch (lr) {
+            case 1: stage_compute_vec<2, DIR>(v, j, TPC, ls, pl.lp, tw); break;
+            case 2: stage_compute_vec<4, DIR>(v, j, TPC, ls, pl.lp, tw); break;
+            default: stage_compute_vec<8, DIR>(v, j, TPC, ls, pl.lp, tw); break;
+        }
+        if (s < pl.ns - 1) {
+            __syncthreads();
+#pragma unroll
+            for (int qq = 0; qq < E; ++qq) {
+                const int e = qq >> lr, r = qq & ((1 << lr) - 1);
+                const int b = j + e * TPC;
+                const int dst = ((b >> ls) << (ls + lr)) + (b & ((1 << ls) - 1)) + (r << ls);
+                C row[CW];
+#pragma unroll
+                for (int c = 0; c < CW; ++c) row[c] = v[c][qq];
+                HV::split(row, buf0[padx<3>(dst)], buf1[padx<3>(dst)]);
             }
             __syncthreads();
         }
@@ -228,7 +347,7 @@ __global__ void k_rows_fwd(FftPlan pl, int nin, Src src, cpx_t<T>* __restrict__ 
         const int x = j + e * TPC + (r << (pl.lp - lr0));
         v[qq] = x < nin ? src.template load<C>(z, x) : czero<C>();
     }
-    fft_core<E, +1, 1>(v, buf, pl, j, TPC, 0, tw);
+    fft_core<E, +1, (E == 16 ? 4 : 3)>(v, buf, pl, j, TPC, tw);
     const int lrl = pl.lr[pl.ns - 1];
     C* o = out + (size_t)z * pl.P;
 #pragma unroll
@@ -238,57 +357,77 @@ __global__ void k_rows_fwd(FftPlan pl, int nin, Src src, cpx_t<T>* __restrict__ 
     }
 }
 
-// MODE 0: forward z-FFT, times Ghat, inverse z-FFT, rows < nout written back in place.
-// MODE 1: forward z-FFT only; the (P/2+1)^2 quadrant of qscale * result is written.
-template <typename T, int E, int CW, int MODE>
-__global__ void __launch_bounds__(512, 1) k_cols(FftPlan pl, int nin, int nout, cpx_t<T>* __restrict__ X,
-                       const cpx_t<T>* __restrict__ ghat, cpx_t<T>* __restrict__ quad, T qscale,
-                       const cpx_t<T>* __restrict__ tw) {
+// Column pass with column-vectorised transforms (radix <= 8, EV elements per
+// column per thread).  MODE 0: forward z-FFT, times Ghat, inverse z-FFT, rows
+// < nout written back in place; MODE 1: forward only, quadrant of qscale * result.
+template <typename T, int EV, int CW, int MODE>
+__global__ void __launch_bounds__(512) k_cols_vec(FftPlan pl, int nin, int nout, cpx_t<T>* __restrict__ X,
+                                                  const cpx_t<T>* __restrict__ ghat, cpx_t<T>* __restrict__ quad,
+                                                  T qscale, const cpx_t<T>* __restrict__ tw) {
     using C = cpx_t<T>;
+    using H = typename Halves<C, CW>::H;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    C* buf = reinterpret_cast<C*>(smem_raw);
     const int P = pl.P, lp = pl.lp;
+    H* buf0 = reinterpret_cast<H*>(smem_raw);
+    H* buf1 = buf0 + (P + (P >> 3));
     const int ntile = P / CW;
     const int b = blockIdx.x;
-    // mirror tiles (kx and P - kx read the same Ghat rows) run back to back
     const int tile = (b & 1) ? (ntile - 1 - (b >> 1)) : (b >> 1);
-    const int c = threadIdx.x % CW, j = threadIdx.x / CW, TPC = blockDim.x / CW;
-    const int kx = tile * CW + c;
-    C v[E];
+    const int kx0 = tile * CW;
+    const int j = threadIdx.x, TPC = blockDim.x;
+    C v[CW][EV];
     const int lr0 = pl.lr[0];
 #pragma unroll
-    for (int qq = 0; qq < E; ++qq) {
+    for (int qq = 0; qq < EV; ++qq) {
         const int e = qq >> lr0, r = qq & ((1 << lr0) - 1);
         const int z = j + e * TPC + (r << (lp - lr0));
-        v[qq] = z < nin ? X[(size_t)z * P + kx] : czero<C>();
+        C row[CW];
+        if (z < nin) RowVec<C, CW>::load(X + (size_t)z * P + kx0, row);
+        else {
+#pragma unroll
+            for (int c = 0; c < CW; ++c) row[c] = czero<C>();
+        }
+#pragma unroll
+        for (int c = 0; c < CW; ++c) v[c][qq] = row[c];
     }
-    fft_core<E, +1, CW, 8>(v, buf, pl, j, TPC, c, tw);
+    fft_core_vec<EV, +1, CW>(v, buf0, buf1, pl, j, TPC, tw);
     const int lrl = pl.lr[pl.ns - 1];
     if constexpr (MODE == 0) {
-        const int kxq = kx <= P / 2 ? kx : P - kx;
-        const C* g = ghat + (size_t)kxq * (P / 2 + 1);
+        const C* g[CW];
 #pragma unroll
-        for (int qq = 0; qq < E; ++qq) {
+        for (int c = 0; c < CW; ++c) {
+            const int kx = kx0 + c;
+            g[c] = ghat + (size_t)(kx <= P / 2 ? kx : P - kx) * (P / 2 + 1);
+        }
+#pragma unroll
+        for (int qq = 0; qq < EV; ++qq) {
             const int e = qq >> lrl, r = qq & ((1 << lrl) - 1);
             const int kz = j + e * TPC + (r << (lp - lrl));
             const int kzq = kz <= P / 2 ? kz : P - kz;
-            v[qq] = v[qq] * __ldg(&g[kzq]);
-        }
-        fft_core<E, -1, CW, 8>(v, buf, pl, j, TPC, c, tw);
 #pragma unroll
-        for (int qq = 0; qq < E; ++qq) {
+            for (int c = 0; c < CW; ++c) v[c][qq] = v[c][qq] * __ldg(&g[c][kzq]);
+        }
+        fft_core_vec<EV, -1, CW>(v, buf0, buf1, pl, j, TPC, tw);
+#pragma unroll
+        for (int qq = 0; qq < EV; ++qq) {
             const int e = qq >> lr0, r = qq & ((1 << lr0) - 1);
             const int z = j + e * TPC + (r << (lp - lr0));
-            if (z < nout) X[(size_t)z * P + kx] = v[qq];
+            if (z < nout) {
+                C row[CW];
+#pragma unroll
+                for (int c = 0; c < CW; ++c) row[c] = v[c][qq];
+                RowVec<C, CW>::store(X + (size_t)z * P + kx0, row);
+            }
         }
     } else {
-        if (kx <= P / 2) {
 #pragma unroll
-            for (int qq = 0; qq < E; ++qq) {
-                const int e = qq >> lrl, r = qq & ((1 << lrl) - 1);
-                const int kz = j + e * TPC + (r << (lp - lrl));
-                if (kz <= P / 2) quad[(size_t)kx * (P / 2 + 1) + kz] = qscale * v[qq];
-            }
+        for (int qq = 0; qq < EV; ++qq) {
+            const int e = qq >> lrl, r = qq & ((1 << lrl) - 1);
+            const int kz = j + e * TPC + (r << (lp - lrl));
+            if (kz > P / 2) continue;
+#pragma unroll
+            for (int c = 0; c < CW; ++c)
+                if (kx0 + c <= P / 2) quad[(size_t)(kx0 + c) * (P / 2 + 1) + kz] = qscale * v[c][qq];
         }
     }
 }
@@ -309,7 +448,7 @@ __global__ void k_rows_inv(FftPlan pl, int n, const cpx_t<T>* __restrict__ X, Ds
         const int e = qq >> lrl, r = qq & ((1 << lrl) - 1);
         v[qq] = xr[j + e * TPC + (r << (pl.lp - lrl))];
     }
-    fft_core<E, -1, 1>(v, buf, pl, j, TPC, 0, tw);
+    fft_core<E, -1, (E == 16 ? 4 : 3)>(v, buf, pl, j, TPC, tw);
     const int lr0 = pl.lr[0];
 #pragma unroll
     for (int qq = 0; qq < E; ++qq) {
@@ -343,12 +482,16 @@ __global__ void k_quad_to32(size_t cnt, const double2* a, float2* b) {
     if (i < cnt) b[i] = ccast<float2>(a[i]);
 }
 
-// Elements per thread: row passes FP64 8 / FP32 16; column pass FP64 16 / FP32 32
-// (a column tile is CW transforms, so fewer threads keep the register file within
-// one 64K-register SM).  Column tiles are 2 (FP64) or 4 (FP32) columns: 32-byte
-// row segments either way.
-constexpr int E64 = 8, EC64 = 16, CW64 = 2;
-constexpr int E32 = 16, EC32 = 32, CW32 = 4;
+// Elements per thread: row passes FP64 8 / FP32 16; column pass 8 per column of
+// its tile.  Column tiles are 2 (FP64) or 4 (FP32) columns: 32-byte row segments.
+constexpr int E64 = 8, CW64 = 2;
+constexpr int E32 = 16, CW32 = 4;
+constexpr int EV = 8;  // column pass: elements per column per thread (radix <= 8)
+
+// shared memory of the padded layouts (one slot every 8 or 16 elements)
+constexpr size_t row_smem64(int P) { return sizeof(double2) * (size_t)(P + (P >> 3)); }
+constexpr size_t row_smem32(int P) { return sizeof(float2) * (size_t)(P + (P >> 4)); }
+constexpr size_t col_smem(int P) { return 2 * 16 * (size_t)(P + (P >> 3)); }
 
 FftPlan make_plan(int lp, int lrmax) {
     FftPlan p{};
@@ -383,18 +526,18 @@ int ls_fft_init(ls_handle* h) {
     LS_CUDA(cudaMalloc(&h->incx, sizeof(double2) * h->n));
     LS_CUDA(cudaMalloc(&h->incz, sizeof(double2) * h->n));
     LS_LAUNCH(h, k_twiddles, (P + 255) / 256, 256, 0, P, h->tw64, h->tw32);
-    LS_TRY(allow_smem(k_cols<double, EC64, CW64, 0>, sizeof(double2) * CW64 * P));
-    LS_TRY(allow_smem(k_cols<double, EC64, CW64, 1>, sizeof(double2) * CW64 * P));
-    LS_TRY(allow_smem(k_cols<float, EC32, CW32, 0>, sizeof(float2) * CW32 * P));
-    LS_TRY(allow_smem(k_rows_fwd<double, E64, SrcMU<double, double2>>, sizeof(double2) * P));
-    LS_TRY(allow_smem(k_rows_fwd<double, E64, SrcInc<double>>, sizeof(double2) * P));
-    LS_TRY(allow_smem(k_rows_fwd<double, E64, SrcGpad>, sizeof(double2) * P));
-    LS_TRY(allow_smem(k_rows_inv<double, E64, DstApply<double2>>, sizeof(double2) * P));
-    LS_TRY(allow_smem(k_rows_inv<double, E64, DstRhs>, sizeof(double2) * P));
-    LS_TRY(allow_smem(k_rows_fwd<float, E32, SrcMU<float, float2>>, sizeof(float2) * P));
-    LS_TRY(allow_smem(k_rows_fwd<float, E32, SrcMU<float, double2>>, sizeof(float2) * P));
-    LS_TRY(allow_smem(k_rows_inv<float, E32, DstApply<float2>>, sizeof(float2) * P));
-    LS_TRY(allow_smem(k_rows_inv<float, E32, DstApply<double2>>, sizeof(float2) * P));
+    LS_TRY(allow_smem(k_cols_vec<double, EV, CW64, 0>, col_smem(P)));
+    LS_TRY(allow_smem(k_cols_vec<double, EV, CW64, 1>, col_smem(P)));
+    LS_TRY(allow_smem(k_cols_vec<float, EV, CW32, 0>, col_smem(P)));
+    LS_TRY(allow_smem(k_rows_fwd<double, E64, SrcMU<double, double2>>, row_smem64(P)));
+    LS_TRY(allow_smem(k_rows_fwd<double, E64, SrcInc<double>>, row_smem64(P)));
+    LS_TRY(allow_smem(k_rows_fwd<double, E64, SrcGpad>, row_smem64(P)));
+    LS_TRY(allow_smem(k_rows_inv<double, E64, DstApply<double2>>, row_smem64(P)));
+    LS_TRY(allow_smem(k_rows_inv<double, E64, DstRhs>, row_smem64(P)));
+    LS_TRY(allow_smem(k_rows_fwd<float, E32, SrcMU<float, float2>>, row_smem32(P)));
+    LS_TRY(allow_smem(k_rows_fwd<float, E32, SrcMU<float, double2>>, row_smem32(P)));
+    LS_TRY(allow_smem(k_rows_inv<float, E32, DstApply<float2>>, row_smem32(P)));
+    LS_TRY(allow_smem(k_rows_inv<float, E32, DstApply<double2>>, row_smem32(P)));
     return LS_OK;
 }
 
@@ -409,10 +552,10 @@ int ls_spectrum_build(ls_handle* h, const double2* gtab) {
     int rc = LS_OK;
     do {
         SrcGpad src{gtab, n, P};
-        k_rows_fwd<double, E64, SrcGpad><<<P, P / E64, sizeof(double2) * P, h->stream>>>(pl, P, src, work, h->tw64);
+        k_rows_fwd<double, E64, SrcGpad><<<P, P / E64, row_smem64(P), h->stream>>>(pl, P, src, work, h->tw64);
         h->launches++;
         const double qscale = h->omega * h->omega / ((double)P * (double)P);
-        k_cols<double, EC64, CW64, 1><<<P / CW64, CW64 * (P / EC64), sizeof(double2) * CW64 * P, h->stream>>>(
+        k_cols_vec<double, EV, CW64, 1><<<P / CW64, (P / EV), col_smem(P), h->stream>>>(
             h->planc64, P, P, work, nullptr, h->ghat64, qscale, h->tw64);
         h->launches++;
         const size_t cnt = q1 * q1;
@@ -431,12 +574,12 @@ int ls_apply64(ls_handle* h, const double2* u, double2* y) {
     const FftPlan& pl = h->plan64;
     double2* X = static_cast<double2*>(h->fftws);
     SrcMU<double, double2> src{h->m64, u, n};
-    LS_LAUNCH(h, (k_rows_fwd<double, E64, SrcMU<double, double2>>), n, P / E64, sizeof(double2) * P,
+    LS_LAUNCH(h, (k_rows_fwd<double, E64, SrcMU<double, double2>>), n, P / E64, row_smem64(P),
               pl, n, src, X, h->tw64);
-    LS_LAUNCH(h, (k_cols<double, EC64, CW64, 0>), P / CW64, CW64 * (P / EC64), sizeof(double2) * CW64 * P,
+    LS_LAUNCH(h, (k_cols_vec<double, EV, CW64, 0>), P / CW64, (P / EV), col_smem(P),
               h->planc64, n, n, X, h->ghat64, (double2*)nullptr, 0.0, h->tw64);
     DstApply<double2> dst{u, y, n};
-    LS_LAUNCH(h, (k_rows_inv<double, E64, DstApply<double2>>), n, P / E64, sizeof(double2) * P,
+    LS_LAUNCH(h, (k_rows_inv<double, E64, DstApply<double2>>), n, P / E64, row_smem64(P),
               pl, n, X, dst, h->tw64);
     return LS_OK;
 }
@@ -446,12 +589,12 @@ int ls_apply32(ls_handle* h, const float2* u, float2* y) {
     const FftPlan& pl = h->plan32;
     float2* X = static_cast<float2*>(h->fftws);
     SrcMU<float, float2> src{h->m32, u, n};
-    LS_LAUNCH(h, (k_rows_fwd<float, E32, SrcMU<float, float2>>), n, P / E32, sizeof(float2) * P,
+    LS_LAUNCH(h, (k_rows_fwd<float, E32, SrcMU<float, float2>>), n, P / E32, row_smem32(P),
               pl, n, src, X, h->tw32);
-    LS_LAUNCH(h, (k_cols<float, EC32, CW32, 0>), P / CW32, CW32 * (P / EC32), sizeof(float2) * CW32 * P,
+    LS_LAUNCH(h, (k_cols_vec<float, EV, CW32, 0>), P / CW32, (P / EV), col_smem(P),
               h->planc32, n, n, X, h->ghat32, (float2*)nullptr, 0.0f, h->tw32);
     DstApply<float2> dst{u, y, n};
-    LS_LAUNCH(h, (k_rows_inv<float, E32, DstApply<float2>>), n, P / E32, sizeof(float2) * P,
+    LS_LAUNCH(h, (k_rows_inv<float, E32, DstApply<float2>>), n, P / E32, row_smem32(P),
               pl, n, X, dst, h->tw32);
     return LS_OK;
 }
@@ -461,12 +604,12 @@ int ls_apply_mixed(ls_handle* h, const double2* u, double2* y) {
     const FftPlan& pl = h->plan32;
     float2* X = static_cast<float2*>(h->fftws);
     SrcMU<float, double2> src{h->m32, u, n};
-    LS_LAUNCH(h, (k_rows_fwd<float, E32, SrcMU<float, double2>>), n, P / E32, sizeof(float2) * P,
+    LS_LAUNCH(h, (k_rows_fwd<float, E32, SrcMU<float, double2>>), n, P / E32, row_smem32(P),
               pl, n, src, X, h->tw32);
-    LS_LAUNCH(h, (k_cols<float, EC32, CW32, 0>), P / CW32, CW32 * (P / EC32), sizeof(float2) * CW32 * P,
+    LS_LAUNCH(h, (k_cols_vec<float, EV, CW32, 0>), P / CW32, (P / EV), col_smem(P),
               h->planc32, n, n, X, h->ghat32, (float2*)nullptr, 0.0f, h->tw32);
     DstApply<double2> dst{u, y, n};
-    LS_LAUNCH(h, (k_rows_inv<float, E32, DstApply<double2>>), n, P / E32, sizeof(float2) * P,
+    LS_LAUNCH(h, (k_rows_inv<float, E32, DstApply<double2>>), n, P / E32, row_smem32(P),
               pl, n, X, dst, h->tw32);
     return LS_OK;
 }
@@ -478,12 +621,12 @@ int ls_rhs64(ls_handle* h, double theta, double2* f) {
     LS_LAUNCH(h, k_incident_factors, (n + 255) / 256, 256, 0, n, h->omega * h->h, std::cos(theta),
               std::sin(theta), h->incx, h->incz);
     SrcInc<double> src{h->m64, h->incx, h->incz, n};
-    LS_LAUNCH(h, (k_rows_fwd<double, E64, SrcInc<double>>), n, P / E64, sizeof(double2) * P,
+    LS_LAUNCH(h, (k_rows_fwd<double, E64, SrcInc<double>>), n, P / E64, row_smem64(P),
               pl, n, src, X, h->tw64);
-    LS_LAUNCH(h, (k_cols<double, EC64, CW64, 0>), P / CW64, CW64 * (P / EC64), sizeof(double2) * CW64 * P,
+    LS_LAUNCH(h, (k_cols_vec<double, EV, CW64, 0>), P / CW64, (P / EV), col_smem(P),
               h->planc64, n, n, X, h->ghat64, (double2*)nullptr, 0.0, h->tw64);
     DstRhs dst{f, n};
-    LS_LAUNCH(h, (k_rows_inv<double, E64, DstRhs>), n, P / E64, sizeof(double2) * P, pl, n, X, dst, h->tw64);
+    LS_LAUNCH(h, (k_rows_inv<double, E64, DstRhs>), n, P / E64, row_smem64(P), pl, n, X, dst, h->tw64);
     return LS_OK;
 }
 
@@ -537,7 +680,7 @@ int noalloc_setup(int dev, cudaStream_t stream, NoAllocDevice** out) {
         d.tw = static_cast<float2*>(p);
         k_noalloc_twiddles<<<(kNoAllocTwElems + 255) / 256, 256, 0, stream>>>(d.tw);
         LS_CUDA(cudaPeekAtLastError());
-        LS_TRY(allow_smem(k_cols<float, EC32, CW32, 0>, sizeof(float2) * CW32 * 2048));
+        LS_TRY(allow_smem(k_cols_vec<float, EV, CW32, 0>, col_smem(2048)));
         LS_CUDA(cudaStreamSynchronize(stream));
         d.ready = true;
     }
@@ -564,13 +707,13 @@ extern "C" int ls_apply_f32_noalloc(int n, const float* m, const ls_c32* ghat, c
     const FftPlan pr = make_plan(lp, 4), pc = make_plan(lp, 3);
     float2* X = d->scratch;
     SrcMU<float, float2> src{m, reinterpret_cast<const float2*>(u), n};
-    k_rows_fwd<float, E32, SrcMU<float, float2>><<<n, P / E32, sizeof(float2) * P, stream>>>(pr, n, src, X, tw);
+    k_rows_fwd<float, E32, SrcMU<float, float2>><<<n, P / E32, row_smem32(P), stream>>>(pr, n, src, X, tw);
     LS_CUDA(cudaPeekAtLastError());
-    k_cols<float, EC32, CW32, 0><<<P / CW32, CW32 * (P / EC32), sizeof(float2) * CW32 * P, stream>>>(
+    k_cols_vec<float, EV, CW32, 0><<<P / CW32, (P / EV), col_smem(P), stream>>>(
         pc, n, n, X, reinterpret_cast<const float2*>(ghat), (float2*)nullptr, 0.0f, tw);
     LS_CUDA(cudaPeekAtLastError());
     DstApply<float2> dst{reinterpret_cast<const float2*>(u), reinterpret_cast<float2*>(y), n};
-    k_rows_inv<float, E32, DstApply<float2>><<<n, P / E32, sizeof(float2) * P, stream>>>(pr, n, X, dst, tw);
+    k_rows_inv<float, E32, DstApply<float2>><<<n, P / E32, row_smem32(P), stream>>>(pr, n, X, dst, tw);
     LS_CUDA(cudaPeekAtLastError());
     return LS_OK;
 }

@@ -107,6 +107,13 @@ struct DirFactors {
     const double* m = nullptr;    // medium of this direction's grid (n x n, long axis fastest)
     StencilTables* tab = nullptr; // device copy of the tables of this direction
     StencilTables host_tab;
+    // couplings the solve needs, tabulated in the solve precision (float2 in LS_MIXED):
+    //   cw, ce: [l][i][dz+1][r]  west / east neighbour blocks of level 0 (tridiagonal)
+    //   cinj:   [l][slot][dx+1][i] trace-injection rows: 0 = row E+t-1 -> E+t, 1 = row E+t -> E+t-1,
+    //                              2 = row E -> E-1, 3 = row E-1 -> E
+    void* cw = nullptr;
+    void* ce = nullptr;
+    void* cinj = nullptr;
 };
 
 // ------------------------------------------------------------------ handle

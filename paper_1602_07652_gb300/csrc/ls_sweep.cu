@@ -67,6 +67,33 @@ __device__ __forceinline__ void mv_accumulate(const cpx_t<T>* __restrict__ M, co
     }
 }
 
+// The same for NM matrices at once: the loads of all of them for a column are
+// issued before any multiply, so one pass over the columns has NM times more
+// loads in flight.  Absent terms pass a valid matrix and a zero vector.
+template <typename T, int RPT, int NM>
+__device__ __forceinline__ void mv_accumulate_n(const cpx_t<T>* const (&M)[NM], const cpx_t<T>* const (&vs)[NM], int q,
+                                                cpx_t<T> (&part)[RPT]) {
+    using C = cpx_t<T>;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll 2
+    for (int c = warp; c < q; c += kMvWarps) {
+        C a[NM][RPT];
+#pragma unroll
+        for (int t = 0; t < NM; ++t)
+#pragma unroll
+            for (int k = 0; k < RPT; ++k) {
+                const int r = lane + 32 * k;
+                a[t][k] = r < q ? __ldg(&M[t][(size_t)c * q + r]) : czero<C>();
+            }
+#pragma unroll
+        for (int t = 0; t < NM; ++t) {
+            const C vc = vs[t][c];
+#pragma unroll
+            for (int k = 0; k < RPT; ++k) part[k] = cfma(a[t][k], vc, part[k]);
+        }
+    }
+}
+
 // red: kMvWarps * q entries of shared memory; returns the full sum for row threadIdx.x (< q)
 template <typename T, int RPT>
 __device__ __forceinline__ cpx_t<T> mv_reduce(cpx_t<T> (&part)[RPT], cpx_t<T>* red, int q) {
@@ -121,14 +148,18 @@ __global__ void __launch_bounds__(kMvThreads) k_cr_step(int q, int k, int nk, Po
 #pragma unroll
     for (int i = 0; i < RPT; ++i) part[i] = czero<C>();
     if (MODE == 0 || MODE == 3) mv_accumulate<T, RPT>(pool.mat(off_a + idx), v0, q, part);
-    if (MODE == 1) {
-        if (hw) mv_accumulate<T, RPT>(pool.mat(off_b + idx), v1, q, part);
-        if (he) mv_accumulate<T, RPT>(pool.mat(off_c + idx), v2, q, part);
+    if (MODE == 1) {  // a missing neighbour has a zero vector; its matrix slot reuses the other one
+        const C* F = pool.mat(off_b + idx);
+        const C* G = pool.mat(off_c + idx);
+        const C* const Ms[2] = {hw ? F : G, he ? G : F};
+        const C* const Vs[2] = {v1, v2};
+        mv_accumulate_n<T, RPT, 2>(Ms, Vs, q, part);
     }
     if (MODE == 2) {
-        mv_accumulate<T, RPT>(pool.mat(off_a + idx), v0, q, part);
-        mv_accumulate<T, RPT>(pool.mat(off_b + idx), v1, q, part);
-        if (he) mv_accumulate<T, RPT>(pool.mat(off_c + idx), v2, q, part);
+        const C* Dm = pool.mat(off_a + idx);
+        const C* const Ms[3] = {Dm, pool.mat(off_b + idx), he ? pool.mat(off_c + idx) : Dm};
+        const C* const Vs[3] = {v0, v1, v2};
+        mv_accumulate_n<T, RPT, 3>(Ms, Vs, q, part);
     }
     const C sum = mv_reduce<T, RPT>(part, red, q);
     if (r < q) xj[r] = MODE == 1 ? xj[r] + sum : sum;
@@ -136,26 +167,28 @@ __global__ void __launch_bounds__(kMvThreads) k_cr_step(int q, int k, int nk, Po
 
 // level 0 backward, odd blocks: x_j = y_j - D^{-1} (W_j x_{j-1} + E_j x_{j+1})
 template <typename T, int RPT>
-__global__ void __launch_bounds__(kMvThreads) k_cr_l0_back(StripGeom g, const StencilTables* __restrict__ tab,
-                                                          const double* __restrict__ m, int l, int nb, Pool<T> pool,
+__global__ void __launch_bounds__(kMvThreads) k_cr_l0_back(int q, int nb, const cpx_t<T>* __restrict__ cw,
+                                                          const cpx_t<T>* __restrict__ ce, Pool<T> pool,
                                                           size_t off_dinv, cpx_t<T>* __restrict__ x) {
     using C = cpx_t<T>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* vt = reinterpret_cast<C*>(smem_raw);
-    C* red = vt + g.q;
+    C* red = vt + q;
     const int o = blockIdx.x;
     const int j = 2 * o + 1;
-    const int r = threadIdx.x, q = g.q;
+    const int r = threadIdx.x;
     if (r < q) {
-        double2 acc = make_double2(0, 0);
+        C acc = czero<C>();
+        const C* wj = cw + (size_t)j * 3 * q;
+        const C* ej = ce + (size_t)j * 3 * q;
 #pragma unroll
         for (int dz = -1; dz <= 1; ++dz) {
             const int rr = r + dz;
             if (rr < 0 || rr >= q) continue;
-            acc = cfma(strip_coef(g, tab, m, l, r, j, -1, dz), ccast<double2>(x[(size_t)(j - 1) * q + rr]), acc);
-            if (j + 1 < nb) acc = cfma(strip_coef(g, tab, m, l, r, j, 1, dz), ccast<double2>(x[(size_t)(j + 1) * q + rr]), acc);
+            acc = cfma(wj[(dz + 1) * q + r], x[(size_t)(j - 1) * q + rr], acc);
+            if (j + 1 < nb) acc = cfma(ej[(dz + 1) * q + r], x[(size_t)(j + 1) * q + rr], acc);
         }
-        vt[r] = -ccast<C>(acc);
+        vt[r] = -acc;
     }
     __syncthreads();
     C part[RPT];
@@ -168,26 +201,28 @@ __global__ void __launch_bounds__(kMvThreads) k_cr_l0_back(StripGeom g, const St
 
 // level 0, even blocks: b_j -= W_j y_{j-1} + E_j y_{j+1} (W, E tridiagonal from the stencil)
 template <typename T>
-__global__ void k_l0_even(StripGeom g, const StencilTables* __restrict__ tab, const double* __restrict__ m, int l,
-                          int nb, cpx_t<T>* __restrict__ x) {
+__global__ void k_l0_even(int q, int nb, const cpx_t<T>* __restrict__ cw, const cpx_t<T>* __restrict__ ce,
+                          cpx_t<T>* __restrict__ x) {
     using C = cpx_t<T>;
     const int j = 2 * blockIdx.x;
-    const int r = threadIdx.x, q = g.q;
+    const int r = threadIdx.x;
     if (r >= q) return;
-    double2 acc = ccast<double2>(x[(size_t)j * q + r]);
+    C acc = x[(size_t)j * q + r];
+    const C* wj = cw + (size_t)j * 3 * q;
+    const C* ej = ce + (size_t)j * 3 * q;
 #pragma unroll
     for (int dz = -1; dz <= 1; ++dz) {
         const int rr = r + dz;
         if (rr < 0 || rr >= q) continue;
-        if (j >= 1) acc = cfms(strip_coef(g, tab, m, l, r, j, -1, dz), ccast<double2>(x[(size_t)(j - 1) * q + rr]), acc);
-        if (j + 1 < nb) acc = cfms(strip_coef(g, tab, m, l, r, j, 1, dz), ccast<double2>(x[(size_t)(j + 1) * q + rr]), acc);
+        if (j >= 1) acc = cfms(wj[(dz + 1) * q + r], x[(size_t)(j - 1) * q + rr], acc);
+        if (j + 1 < nb) acc = cfms(ej[(dz + 1) * q + r], x[(size_t)(j + 1) * q + rr], acc);
     }
-    x[(size_t)j * q + r] = ccast<C>(acc);
+    x[(size_t)j * q + r] = acc;
 }
 
 // g^l = chi_{Omega^l} g (+ injection from the layer above), copied to the solution buffer
 template <typename T>
-__global__ void k_gather(StripGeom g, const StencilTables* __restrict__ tab, const double* __restrict__ m, int l,
+__global__ void k_gather(StripGeom g, const cpx_t<T>* __restrict__ inj, int l,
                          const double2* __restrict__ gf, cpx_t<T>* __restrict__ rhs, cpx_t<T>* __restrict__ sol,
                          const cpx_t<T>* __restrict__ above, cpx_t<T>* __restrict__ trace_above) {
     using C = cpx_t<T>;
@@ -199,15 +234,18 @@ __global__ void k_gather(StripGeom g, const StencilTables* __restrict__ tab, con
     double2 val = make_double2(0, 0);
     if (r >= E && r < E + t) val = gf[(size_t)(l * t - E + r) * n + i];
     if (above) {
+        const cpx_t<T>* c0 = inj + (size_t)l * 12 * n;  // slots 0, 1 of layer l: [slot][dx+1][i]
         if (r == E + t - 1) {  // -C^l_{n,n+1} w^{l+1}_1 ; w^{l+1}_1 = row E of layer l+1
             for (int dx = -1; dx <= 1; ++dx) {
                 if (i + dx < 0 || i + dx >= n) continue;
-                val = cfms(strip_coef(g, tab, m, l, r, i, dx, 1), ccast<double2>(above[(size_t)(i + dx) * q + E]), val);
+                val = cfms(ccast<double2>(c0[(size_t)(0 * 3 + dx + 1) * n + i]),
+                           ccast<double2>(above[(size_t)(i + dx) * q + E]), val);
             }
         } else if (r == E + t) {  // +C^l_{n+1,n} w^{l+1}_0 ; w^{l+1}_0 = row E-1 of layer l+1
             for (int dx = -1; dx <= 1; ++dx) {
                 if (i + dx < 0 || i + dx >= n) continue;
-                val = cfma(strip_coef(g, tab, m, l, r, i, dx, -1), ccast<double2>(above[(size_t)(i + dx) * q + E - 1]), val);
+                val = cfma(ccast<double2>(c0[(size_t)(1 * 3 + dx + 1) * n + i]),
+                           ccast<double2>(above[(size_t)(i + dx) * q + E - 1]), val);
             }
         }
     }
@@ -218,7 +256,7 @@ __global__ void k_gather(StripGeom g, const StencilTables* __restrict__ tab, con
 
 // sol = g^l + injection from the layer below (upward sweep)
 template <typename T>
-__global__ void k_inject_up(StripGeom g, const StencilTables* __restrict__ tab, const double* __restrict__ m, int l,
+__global__ void k_inject_up(StripGeom g, const cpx_t<T>* __restrict__ inj, int l,
                             const cpx_t<T>* __restrict__ rhs, cpx_t<T>* __restrict__ sol,
                             const cpx_t<T>* __restrict__ below, const cpx_t<T>* __restrict__ trace_self) {
     using C = cpx_t<T>;
@@ -231,16 +269,18 @@ __global__ void k_inject_up(StripGeom g, const StencilTables* __restrict__ tab, 
         return;
     }
     double2 val = ccast<double2>(rhs[e]);
+    const cpx_t<T>* c0 = inj + (size_t)l * 12 * n;  // slots 2, 3 of layer l: [slot][dx+1][i]
     if (r == E) {  // -C^l_{1,0} (v^{l-1}_n - w^l_0) ; v^{l-1}_n = row E+t-1 of layer l-1
         for (int dx = -1; dx <= 1; ++dx) {
             if (i + dx < 0 || i + dx >= n) continue;
             const double2 p0 = ccast<double2>(below[(size_t)(i + dx) * q + E + t - 1]) - ccast<double2>(trace_self[i + dx]);
-            val = cfms(strip_coef(g, tab, m, l, r, i, dx, -1), p0, val);
+            val = cfms(ccast<double2>(c0[(size_t)(2 * 3 + dx + 1) * n + i]), p0, val);
         }
     } else {  // +C^l_{0,1} v^{l-1}_{n+1} ; v^{l-1}_{n+1} = row E+t of layer l-1
         for (int dx = -1; dx <= 1; ++dx) {
             if (i + dx < 0 || i + dx >= n) continue;
-            val = cfma(strip_coef(g, tab, m, l, r, i, dx, 1), ccast<double2>(below[(size_t)(i + dx) * q + E + t]), val);
+            val = cfma(ccast<double2>(c0[(size_t)(3 * 3 + dx + 1) * n + i]),
+                       ccast<double2>(below[(size_t)(i + dx) * q + E + t]), val);
         }
     }
     sol[e] = ccast<C>(val);
@@ -290,7 +330,6 @@ int cr_solve_rpt(ls_handle* h, int dir, int l, cpx_t<T>* x) {
     if constexpr (sizeof(T) == 4) base = F.pool32;
     else base = F.pool64;
     Pool<T> pool{base + (size_t)l * F.mats_per_strip * qq, qq};
-    const StripGeom g = geom_of(h);
     const int thr = (q + 31) / 32 * 32;
     const size_t sm_step = (3 + kMvWarps) * sizeof(C) * q;
     const size_t sm_back = (1 + kMvWarps) * sizeof(C) * q;
@@ -298,7 +337,9 @@ int cr_solve_rpt(ls_handle* h, int dir, int l, cpx_t<T>* x) {
     if (l0.nodd)
         LS_LAUNCH(h, (k_cr_step<T, RPT, 0>), l0.nodd, kMvThreads, sm_step, q, 0, l0.nk, pool, l0.off_dinv,
                   (size_t)0, (size_t)0, x);
-    LS_LAUNCH(h, k_l0_even<T>, l0.neven, thr, 0, g, F.tab, F.m, l, n, x);
+    const C* cw = static_cast<const C*>(F.cw) + (size_t)l * n * 3 * q;
+    const C* ce = static_cast<const C*>(F.ce) + (size_t)l * n * 3 * q;
+    LS_LAUNCH(h, k_l0_even<T>, l0.neven, thr, 0, q, n, cw, ce, x);
     for (int k = 1; k < F.K; ++k) {
         const CrLevel& lv = F.lev[k];
         LS_LAUNCH(h, (k_cr_step<T, RPT, 1>), lv.neven, kMvThreads, sm_step, q, k, lv.nk, pool, (size_t)0, lv.off_f,
@@ -312,7 +353,7 @@ int cr_solve_rpt(ls_handle* h, int dir, int l, cpx_t<T>* x) {
                       lv.off_p, lv.off_q, x);
     }
     if (l0.nodd)
-        LS_LAUNCH(h, (k_cr_l0_back<T, RPT>), l0.nodd, kMvThreads, sm_back, g, F.tab, F.m, l, n, pool, l0.off_dinv, x);
+        LS_LAUNCH(h, (k_cr_l0_back<T, RPT>), l0.nodd, kMvThreads, sm_back, q, n, cw, ce, pool, l0.off_dinv, x);
     return LS_OK;
 }
 
@@ -339,13 +380,13 @@ int sweep_impl(ls_handle* h, int dir, const double2* g, double2* v) {
     const StripGeom geo = geom_of(h);
     const unsigned nbs = (unsigned)((sstride + 255) / 256);
     for (int l = L - 1; l >= 0; --l) {  // downward sweep
-        LS_LAUNCH(h, k_gather<T>, nbs, 256, 0, geo, F.tab, F.m, l, g, rhs + l * sstride, sol + l * sstride,
+        LS_LAUNCH(h, k_gather<T>, nbs, 256, 0, geo, static_cast<const C*>(F.cinj), l, g, rhs + l * sstride, sol + l * sstride,
                   l < L - 1 ? sol + (l + 1) * sstride : (const C*)nullptr,
                   l < L - 1 ? trc + (size_t)(l + 1) * n : (C*)nullptr);
         LS_TRY(cr_solve<T>(h, dir, l, sol + l * sstride));
     }
     for (int l = 1; l < L; ++l) {  // upward sweep
-        LS_LAUNCH(h, k_inject_up<T>, nbs, 256, 0, geo, F.tab, F.m, l, rhs + l * sstride, sol + l * sstride,
+        LS_LAUNCH(h, k_inject_up<T>, nbs, 256, 0, geo, static_cast<const C*>(F.cinj), l, rhs + l * sstride, sol + l * sstride,
                   sol + (l - 1) * sstride, trc + (size_t)l * n);
         LS_TRY(cr_solve<T>(h, dir, l, sol + l * sstride));
     }
