@@ -31,6 +31,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "solve s/RHS to 1e-6 rel. residual at 2048^2; LS-apply % of HBM roofline"
 N_DEFAULT, PPW_W, LAYERS, EXT, TOL = 2048, 200, 32, 10, 1e-6
+BATCH_DEFAULT = 1
 
 
 def parse():
@@ -42,11 +43,22 @@ def parse():
     ap.add_argument("--n", type=int, default=N_DEFAULT)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--batch", type=int, default=BATCH_DEFAULT,
+                    help="right-hand sides (incident directions) solved together per step")
     ap.add_argument("--apply-only", action="store_true",
                     help="time only the LS-apply (setup, no factorisation): profiling driver")
     ap.add_argument("--sweep-only", action="store_true",
                     help="time only Algorithm 2 applications (setup + factorisation): profiling driver")
     ap.add_argument("--fp64", action="store_true", help="plain FP64 method instead of mixed precision")
+    ap.add_argument("--mixed", action="store_true", help="--apply-only: FP64 I/O with FP32 arithmetic (the solve's apply)")
+    ap.add_argument("--no-graphs", action="store_true",
+                    help="launch Algorithm 2 kernel by kernel instead of replaying its CUDA graph (same arithmetic; "
+                         "for profilers that cannot follow graph replay)")
+    ap.add_argument("--table1", action="store_true",
+                    help="Table 1 analogue: sparsified system C u = A f solved by GMRES (tol 1e-6) preconditioned "
+                         "by Algorithm 1 (one direction) or Algorithm 2, +/- Gaussian perturbation, 10 ppw, L = n/50")
+    ap.add_argument("--table1-n", default="200,400,800,1600")
+    ap.add_argument("--table1-rhs", type=int, default=8)
     return ap.parse_args()
 
 
@@ -55,11 +67,14 @@ def workload(n):
     return dict(n=n, omega=w, layers=LAYERS * n // 2048 if n >= 2048 else max(1, n // 64), ext=EXT, tol=TOL)
 
 
-def config_dict(wl, prec="mixed"):
+def config_dict(wl, prec="mixed", rhs_per_step=1):
+    per = "one plane wave per step" if rhs_per_step == 1 else \
+        "%d plane waves per step, solved as one lockstep batch" % rhs_per_step
     return {"workload": "%dx%d unit square, w=2pi*%g (10.24 ppw), 20 seeded Gaussian bumps (disk r=0.4), "
-                        "%d layers/direction ext %d, %s precision, tol %g, one plane wave per step"
-                        % (wl["n"], wl["n"], wl["omega"] / (2 * math.pi), wl["layers"], wl["ext"], prec, wl["tol"]),
-            "n": wl["n"], "omega": wl["omega"], "layers": wl["layers"], "ext": wl["ext"], "tol": wl["tol"],
+                        "%d layers/direction ext %d, %s precision, tol %g, %s"
+                        % (wl["n"], wl["n"], wl["omega"] / (2 * math.pi), wl["layers"], wl["ext"], prec, wl["tol"],
+                           per),
+            "rhs_per_step": rhs_per_step, "n": wl["n"], "omega": wl["omega"], "layers": wl["layers"], "ext": wl["ext"], "tol": wl["tol"],
             "l2": "inputs larger than L2: every sweep streams ~%.0f GB of local-solve factors" %
                   (4 * wl["layers"] * wl["n"] * (wl["n"] // wl["layers"] + 2 * wl["ext"]) ** 2 * 8 * 1.75 / 1e9),
             "parallelism": "replicas"}
@@ -252,21 +267,31 @@ def run_ours(args):
     n = wl["n"]
     m = inputs.bump_medium(n, nbumps=20, seed=0)
     t0 = time.perf_counter()
+    o = binding.default_opts()
+    o.use_graphs = 0 if args.no_graphs else 1
     s = binding.Solver(torch.from_numpy(m), wl["omega"], layers=wl["layers"], ext=wl["ext"],
-                       precision=binding.LS_MIXED)
+                       precision=binding.LS_MIXED, opts=o)
     t_setup = time.perf_counter() - t0
     t0 = time.perf_counter()
     s.ls_factor()
     torch.cuda.synchronize()
     t_factor = time.perf_counter() - t0
     base = inputs.seeded_angle(0)
-    u = torch.empty((n, n), dtype=torch.complex128, device="cuda")
+    B = args.batch
+    f = torch.empty((B, n, n), dtype=torch.complex128, device="cuda")
+    u = torch.empty_like(f)
 
     def theta(k):  # 64 directions on the circle, rank-strided
         return base + 2 * math.pi * ((k * world + rank) % 64) / 64
 
+    def step(k):  # B incident plane waves: right-hand sides on the device, one batched solve
+        for b in range(B):
+            s.ls_incident_rhs(theta(k * B + b), f[b])
+        _, st, _ = s.ls_solve_batch(f, wl["tol"], u)
+        return st
+
     for k in range(args.warmup):
-        s.ls_solve_plane_wave(theta(k), wl["tol"], u)
+        step(k)
     s.ls_set_timing(True)
     stream = s.stream
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -278,8 +303,7 @@ def run_ours(args):
     ev0.record(stream)
     stats = []
     for k in range(args.steps):
-        _, st = s.ls_solve_plane_wave(theta(args.warmup + k), wl["tol"], u)
-        stats.append(st)
+        stats.append(step(args.warmup + k))
     ev1.record(stream)
     torch.cuda.synchronize()
     clk = clocks.stop()
@@ -294,18 +318,24 @@ def run_ours(args):
     # end to end through the C ABI with host buffers: the same directions as the timed
     # steps, right-hand sides prepared in pinned host memory beforehand; each step copies
     # f host->device, solves, and copies u device->host inside the timed region
-    f_hosts = [s.ls_incident_rhs(theta(args.warmup + k)).cpu().pin_memory() for k in range(args.e2e_steps)]
-    u_host = torch.empty_like(f_hosts[0]).pin_memory()
-    s.ls_solve_host(f_hosts[0], wl["tol"], u_host)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for k in range(args.e2e_steps):
-        s.ls_solve_host(f_hosts[k], wl["tol"], u_host)
-    e2e = (time.perf_counter() - t0) / args.e2e_steps
-    if world > 1:
-        t = torch.tensor([e2e], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e = t.item()
+    e2e = None
+    if args.e2e_steps > 0:
+        f_hosts = []
+        for k in range(args.e2e_steps):
+            for b in range(B):
+                s.ls_incident_rhs(theta((args.warmup + k) * B + b), f[b])
+            f_hosts.append(f.cpu().pin_memory())
+        u_host = torch.empty_like(f_hosts[0]).pin_memory()
+        s.ls_solve_batch_host(f_hosts[0], wl["tol"], u_host)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for k in range(args.e2e_steps):
+            s.ls_solve_batch_host(f_hosts[k], wl["tol"], u_host)
+        e2e = (time.perf_counter() - t0) / (args.e2e_steps * B)
+        if world > 1:
+            t = torch.tensor([e2e], device="cuda", dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e = t.item()
     if rank == 0:
         hbm, src = peaks()
         try:
@@ -324,21 +354,21 @@ def run_ours(args):
         # u (16 n^2) and writes y (16 n^2): 124 n^2 bytes.
         bytes_apply = 124.0 * n * n
         ach = bytes_apply / (t_app / n_app / 1e3) / 1e9 if n_app else None
-        outer = statistics.mean(st["outer_iters"] for st in stats)
-        inner = statistics.mean(st["inner_iters_total"] for st in stats)
-        value = ms / 1e3 / (args.steps * world)
+        outer = statistics.mean(st["outer_iters"] for st in stats) / B  # per right-hand side
+        inner = statistics.mean(st["inner_iters_total"] for st in stats) / B
+        value = ms / 1e3 / (args.steps * B * world)
         out = {"metric": METRIC, "value": value, "unit": "s/RHS", "n_gpus": world, "steps": args.steps,
                "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": False,
                "scaling": "weak", "vs_baseline": None, "dtype": "mixed c64/c128", "data": "synthetic",
-               "config": config_dict(wl),
+               "config": config_dict(wl, rhs_per_step=B),
                "roofline": {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
                             "frac": (ach / hbm) if ach else None, "traffic": None,
                             "kernel": "LS-apply (3 FFT passes), FP32 arithmetic, FP64 I/O",
                             "algorithmic_bytes": bytes_apply, "peak_source": src,
                             "launches": n_app, "avg_ms": t_app / n_app if n_app else None},
                "clocks": clk,
-               "e2e": {"value": e2e, "unit": "s/RHS", "h2d_bytes_per_step": 16 * n * n,
-                       "d2h_bytes_per_step": 16 * n * n},
+               "e2e": {"value": e2e, "unit": "s/RHS", "h2d_bytes_per_step": 16 * n * n * B,
+                       "d2h_bytes_per_step": 16 * n * n * B},
                "gpu_launches": int(sum(st["kernel_launches"] for st in stats)),
                "offline_s": {"setup": t_setup, "factor": t_factor},
                "factor_roofline": factor_roof,
@@ -367,20 +397,26 @@ def run_component(args):
     n = wl["n"]
     prec = binding.LS_FP64 if args.fp64 else binding.LS_MIXED
     m = inputs.bump_medium(n, nbumps=20, seed=0)
-    s = binding.Solver(torch.from_numpy(m), wl["omega"], layers=wl["layers"], ext=wl["ext"], precision=prec)
+    o = binding.default_opts()
+    o.use_graphs = 0 if args.no_graphs else 1
+    s = binding.Solver(torch.from_numpy(m), wl["omega"], layers=wl["layers"], ext=wl["ext"], precision=prec, opts=o)
     stream = s.stream
     if args.apply_only:
         if args.fp64:
             x = torch.from_numpy(inputs.random_field(n, 0)).cuda()
             fn, nbytes, kind = (lambda: s.ls_apply(x, x)), 200.0 * n * n, "LS-apply FP64"
+        elif args.mixed:
+            x = torch.from_numpy(inputs.random_field(n, 0)).cuda()
+            fn, nbytes, kind = (lambda: s.ls_apply_mixed(x, x)), 124.0 * n * n, "LS-apply mixed (FP64 I/O, FP32 arithmetic)"
         else:
             x = torch.from_numpy(inputs.random_field(n, 0).astype("complex64")).cuda()
             fn, nbytes, kind = (lambda: s.ls_apply_f32(x, x)), 100.0 * n * n, "LS-apply FP32"
     else:
         s.ls_factor()
-        g = torch.from_numpy(inputs.random_field(n, 0)).cuda()
+        B = args.batch
+        g = torch.stack([torch.from_numpy(inputs.random_field(n, b)) for b in range(B)]).cuda()
         v = torch.empty_like(g)
-        fn, nbytes, kind = (lambda: s.ls_precond_bd(g, v)), None, "Algorithm 2"
+        fn, nbytes, kind = (lambda: s.ls_precond_bd_batch(g, v)), None, "Algorithm 2 x %d fields" % B
     for _ in range(args.warmup):
         fn()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -394,6 +430,8 @@ def run_component(args):
     ms = ev0.elapsed_time(ev1) / args.steps
     hbm, src = peaks()
     out = {"component": kind, "n": n, "ms": ms, "launches_per_call": (s.ls_kernel_count() - k0) / args.steps}
+    if args.sweep_only:
+        out["ms_per_field"] = ms / args.batch
     if nbytes:
         out["achieved_gbs"] = nbytes / (ms / 1e3) / 1e9
         out["frac_hbm"] = out["achieved_gbs"] / hbm
@@ -403,8 +441,58 @@ def run_component(args):
     return 0
 
 
+def run_table1(args):
+    """Table 1 analogue (Sec. 5): iterations and time per right-hand side of the
+    sparsified system C u = A f (eq. global_sparse_system) under GMRES with tolerance
+    1e-6, preconditioned by the one-directional Gauss-Seidel sweep (Algorithm 1,
+    horizontal layers: "PT") or by the bi-directional Algorithm 2 ("BD").  Media: a
+    Gaussian perturbation m = +/-0.2 exp(-|x-c|^2 / (2 0.1^2)) on the disk r <= 0.3
+    (the paper's Fig. 1 perturbation is not given in its text).  10 points per
+    wavelength (w = 2 pi n / 10), L = n / 50 layers of 50 rows extended by 10, FP64,
+    right-hand sides f for directions 2 pi j / R.  One JSON line per (sign, n, preconditioner)."""
+    import torch
+    from paper_1602_07652_gb300 import binding, inputs
+    binding.load()
+    for sign in (+1, -1):
+        for n in (int(x) for x in args.table1_n.split(",")):
+            L = n // 50
+            w = 2 * math.pi * n / 10.0
+            m = inputs.gaussian_disk_medium(n, amp=0.2 * sign)
+            for pc, name in ((binding.LS_PC_GS, "PT (Algorithm 1)"), (binding.LS_PC_BD, "BD (Algorithm 2)")):
+                o = binding.default_opts()
+                o.inner_precond = pc
+                o.inner_maxit = 400
+                o.inner_restart = 60 if pc == binding.LS_PC_GS else 30
+                s = binding.Solver(torch.from_numpy(m), w, layers=L, ext=10, precision=binding.LS_FP64, opts=o)
+                t0 = time.perf_counter()
+                s.ls_factor()
+                torch.cuda.synchronize()
+                t_fac = time.perf_counter() - t0
+                its, ts, unconv = [], [], 0
+                for j in range(args.table1_rhs):
+                    f = s.ls_incident_rhs(2 * math.pi * j / args.table1_rhs)
+                    g = s.ls_apply_A(f)
+                    torch.cuda.synchronize()
+                    t0 = time.perf_counter()
+                    _, it, rc = s.ls_inner_solve(g, 1e-6, check=False)
+                    ts.append(time.perf_counter() - t0)
+                    its.append(it)
+                    if rc == -5:
+                        unconv += 1
+                    elif rc != 0:
+                        raise binding.LSError(rc, "ls_inner_solve")
+                print(json.dumps({"table1": name, "perturbation": "+" if sign > 0 else "-", "n": n, "N": n * n,
+                                  "omega_over_2pi": w / (2 * math.pi), "L": L, "rhs": args.table1_rhs,
+                                  "iters_avg": statistics.mean(its), "s_per_rhs": statistics.mean(ts),
+                                  "not_converged": unconv, "factor_s": t_fac}), flush=True)
+                s.close()
+    return 0
+
+
 def main():
     args = parse()
+    if args.table1:
+        return run_table1(args)
     if args.impl == "reference":
         return run_reference(args)
     if args.apply_only or args.sweep_only:

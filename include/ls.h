@@ -45,6 +45,10 @@ enum {
 
 enum { LS_FP64 = 0, LS_MIXED = 1 };
 
+/* Right-hand sides per batched call: ls_solve_batch takes up to LS_MAX_BATCH;
+ * ls_precond_bd_batch takes up to LS_MAX_BD_BATCH (LS_MIXED) or 4 (LS_FP64). */
+enum { LS_MAX_BATCH = 16, LS_MAX_BD_BATCH = 8 };
+
 typedef struct {
     int nx, nz;       /* grid points per direction (this build requires nx == nz >= 8)      */
     int layers;       /* L, number of layers per direction (Sec. 3.1); must divide nz       */
@@ -66,7 +70,13 @@ typedef struct {
                                 (default 1e-4)                                               */
     int use_graphs;        /* 1 (default): replay Algorithm 2 as a captured CUDA graph;
                               0: launch its kernels one by one (same arithmetic)            */
+    int inner_precond;     /* preconditioner of the inner GMRES: LS_PC_BD (default,
+                              Algorithm 2) or LS_PC_GS (Algorithm 1 on horizontal layers
+                              only, the one-directional polarized-traces sweep that
+                              Table 1 compares against)                                      */
 } ls_opts;
+
+enum { LS_PC_BD = 0, LS_PC_GS = 1 };
 
 typedef struct {
     int outer_iters;         /* outer (flexible) GMRES iterations, all refinement steps     */
@@ -115,6 +125,10 @@ int ls_apply(ls_handle* h, const ls_c64* u, ls_c64* y);
 /* ls_apply_f32 -- the same operator with FP32 complex arithmetic and FP32 I/O. */
 int ls_apply_f32(ls_handle* h, const ls_c32* u, ls_c32* y);
 
+/* ls_apply_mixed -- the same operator with FP64 input/output and FP32 complex arithmetic
+ * (the apply LS_MIXED uses inside its refinement loop).  u, y: device, nz*nx; may alias. */
+int ls_apply_mixed(ls_handle* h, const ls_c64* u, ls_c64* y);
+
 /* ls_incident_rhs -- f = -w^2 G (m u_I) with u_I = exp(i w (x cos theta + z sin theta))
  * generated on the device (Sec. 2, f = -w^2 G D u_I).  f: device, nz*nx. */
 int ls_incident_rhs(ls_handle* h, double theta, ls_c64* f);
@@ -135,6 +149,26 @@ int ls_solve_host(ls_handle* h, const ls_c64* f_host, double tol, ls_c64* u_host
 /* ls_solve_plane_wave -- f = ls_incident_rhs(theta) followed by ls_solve. */
 int ls_solve_plane_wave(ls_handle* h, double theta, double tol, ls_c64* u, ls_stats* stats);
 
+/* ls_solve_batch -- nrhs independent solves H u_b = f_b (1 <= nrhs <= LS_MAX_BATCH)
+ * in one call: f and u hold nrhs fields back to back (field b at offset b*nz*nx).
+ * The same H serves every right-hand side (Sec. 6 solves one scatterer for many
+ * incident waves); the members iterate in lockstep, each with its own Krylov
+ * spaces and stopping test, and share every application of Algorithm 2 (its
+ * factor traffic and its chain of launches).  Each u_b is what ls_solve would
+ * return for f_b up to rounding.  stats: iteration counts summed over the
+ * members; refine_steps and true_rel_residual the largest over the members.
+ * Device memory: the Krylov spaces grow to nrhs * (outer_restart +
+ * inner_restart + 4) fields (LS_ENOMEM if they do not fit).  Return codes as
+ * ls_solve; LS_ENOCONV if any member misses the tolerance. */
+int ls_solve_batch(ls_handle* h, int nrhs, const ls_c64* f, double tol, ls_c64* u, int use_x0,
+                   ls_stats* stats);
+
+/* ls_solve_batch_host -- ls_solve_batch with HOST arrays f and u of nrhs fields
+ * (pinned or pageable); the host<->device copies run on the handle's stream
+ * inside the call. */
+int ls_solve_batch_host(ls_handle* h, int nrhs, const ls_c64* f_host, double tol, ls_c64* u_host,
+                        ls_stats* stats);
+
 /* ---- operators of the inner level (Sec. 2-3), exposed for checking and reuse ---- */
 
 /* y = A r: sparsifying stencil (Sec. 2), 9-point with boundary types.  FP64. */
@@ -150,6 +184,11 @@ int ls_sweep(ls_handle* h, int dir, const ls_c64* g, ls_c64* v);
 
 /* v = Algorithm 2 (bi-directional preconditioner, Sec. 3.5) applied to g. */
 int ls_precond_bd(ls_handle* h, const ls_c64* g, ls_c64* v);
+
+/* Algorithm 2 applied to nrhs fields g_b at once (back to back, as in
+ * ls_solve_batch): v_b equals ls_precond_bd(g_b) up to rounding.  1 <= nrhs <=
+ * LS_MAX_BD_BATCH for LS_MIXED, <= 4 for LS_FP64 (else LS_EINVAL). */
+int ls_precond_bd_batch(ls_handle* h, int nrhs, const ls_c64* g, ls_c64* v);
 
 /* Inner level of Algorithm 3: GMRES on C v = g preconditioned by Algorithm 2,
  * from v = 0, to relative tolerance tol.  *iters receives the iteration count. */

@@ -18,6 +18,8 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libls.so")
 
 LS_FP64, LS_MIXED = 0, 1
+LS_MAX_BATCH, LS_MAX_BD_BATCH = 16, 8
+LS_PC_BD, LS_PC_GS = 0, 1
 
 
 class LSError(RuntimeError):
@@ -37,7 +39,7 @@ class Opts(ctypes.Structure):
                 ("inner_maxit", ctypes.c_int), ("outer_restart", ctypes.c_int),
                 ("outer_maxit", ctypes.c_int), ("shift", ctypes.c_double),
                 ("refine_maxit", ctypes.c_int), ("refine_inner_tol", ctypes.c_double),
-                ("use_graphs", ctypes.c_int)]
+                ("use_graphs", ctypes.c_int), ("inner_precond", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -61,14 +63,19 @@ _SIGS = {
     "ls_factor": (ctypes.c_int, [_P]),
     "ls_apply": (ctypes.c_int, [_P, _P, _P]),
     "ls_apply_f32": (ctypes.c_int, [_P, _P, _P]),
+    "ls_apply_mixed": (ctypes.c_int, [_P, _P, _P]),
     "ls_incident_rhs": (ctypes.c_int, [_P, ctypes.c_double, _P]),
     "ls_solve": (ctypes.c_int, [_P, _P, ctypes.c_double, _P, ctypes.c_int, ctypes.POINTER(Stats)]),
+    "ls_solve_batch": (ctypes.c_int, [_P, ctypes.c_int, _P, ctypes.c_double, _P, ctypes.c_int,
+                                      ctypes.POINTER(Stats)]),
+    "ls_solve_batch_host": (ctypes.c_int, [_P, ctypes.c_int, _P, ctypes.c_double, _P, ctypes.POINTER(Stats)]),
     "ls_solve_host": (ctypes.c_int, [_P, _P, ctypes.c_double, _P, ctypes.POINTER(Stats)]),
     "ls_solve_plane_wave": (ctypes.c_int, [_P, ctypes.c_double, ctypes.c_double, _P, ctypes.POINTER(Stats)]),
     "ls_apply_A": (ctypes.c_int, [_P, _P, _P]),
     "ls_apply_C": (ctypes.c_int, [_P, _P, _P]),
     "ls_sweep": (ctypes.c_int, [_P, ctypes.c_int, _P, _P]),
     "ls_precond_bd": (ctypes.c_int, [_P, _P, _P]),
+    "ls_precond_bd_batch": (ctypes.c_int, [_P, ctypes.c_int, _P, _P]),
     "ls_inner_solve": (ctypes.c_int, [_P, _P, ctypes.c_double, _P, ctypes.POINTER(ctypes.c_int)]),
     "ls_local_solve": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, _P, _P]),
     "ls_get_stencils": (ctypes.c_int, [_P, _P, _P]),
@@ -199,6 +206,12 @@ class Solver:
         _ck(self._lib.ls_apply(self._h, _c128(u, self.N, "ls_apply"), _c128(y, self.N, "ls_apply")), "ls_apply")
         return y
 
+    def ls_apply_mixed(self, u, y=None):
+        y = torch.empty_like(u) if y is None else y
+        _ck(self._lib.ls_apply_mixed(self._h, _c128(u, self.N, "ls_apply_mixed"), _c128(y, self.N, "ls_apply_mixed")),
+            "ls_apply_mixed")
+        return y
+
     def ls_apply_f32(self, u, y=None):
         y = torch.empty_like(u) if y is None else y
         if u.dtype != torch.complex64 or y.dtype != torch.complex64:
@@ -220,6 +233,17 @@ class Solver:
             _ck(rc, "ls_solve")
         return u, st.as_dict(), rc
 
+    def ls_solve_batch(self, f, tol, u=None, x0=False, check=True):
+        """f: CUDA complex128 tensor of nrhs fields (nrhs, n, n), back to back."""
+        u = torch.empty_like(f) if u is None else u
+        nrhs = f.numel() // self.N
+        st = Stats()
+        rc = self._lib.ls_solve_batch(self._h, nrhs, _c128(f, nrhs * self.N, "ls_solve_batch"), float(tol),
+                                      _c128(u, nrhs * self.N, "ls_solve_batch"), 1 if x0 else 0, ctypes.byref(st))
+        if check:
+            _ck(rc, "ls_solve_batch")
+        return u, st.as_dict(), rc
+
     def ls_solve_host(self, f_host, tol, u_host):
         """f_host, u_host: CPU complex128 tensors (pinned or pageable)."""
         for t in (f_host, u_host):
@@ -228,6 +252,17 @@ class Solver:
         st = Stats()
         rc = self._lib.ls_solve_host(self._h, _ptr(f_host), float(tol), _ptr(u_host), ctypes.byref(st))
         _ck(rc, "ls_solve_host")
+        return st.as_dict()
+
+    def ls_solve_batch_host(self, f_host, tol, u_host):
+        """f_host, u_host: CPU complex128 tensors of nrhs fields (pinned or pageable)."""
+        nrhs = f_host.numel() // self.N
+        for t in (f_host, u_host):
+            if t.is_cuda or t.dtype != torch.complex128 or not t.is_contiguous() or t.numel() != nrhs * self.N:
+                raise ValueError("ls_solve_batch_host takes contiguous CPU complex128 tensors of whole fields")
+        st = Stats()
+        rc = self._lib.ls_solve_batch_host(self._h, nrhs, _ptr(f_host), float(tol), _ptr(u_host), ctypes.byref(st))
+        _ck(rc, "ls_solve_batch_host")
         return st.as_dict()
 
     def ls_solve_plane_wave(self, theta, tol, u=None):
@@ -259,11 +294,23 @@ class Solver:
             "ls_precond_bd")
         return v
 
-    def ls_inner_solve(self, g, tol, v=None):
+    def ls_precond_bd_batch(self, g, v=None):
+        """g: CUDA complex128 tensor of nrhs fields (nrhs, n, n), back to back."""
+        v = torch.empty_like(g) if v is None else v
+        nrhs = g.numel() // self.N
+        _ck(self._lib.ls_precond_bd_batch(self._h, nrhs, _c128(g, nrhs * self.N, "ls_precond_bd_batch"),
+                                          _c128(v, nrhs * self.N, "ls_precond_bd_batch")), "ls_precond_bd_batch")
+        return v
+
+    def ls_inner_solve(self, g, tol, v=None, check=True):
+        """Returns (v, iterations); with check=False, (v, iterations, status)."""
         v = torch.empty_like(g) if v is None else v
         it = ctypes.c_int()
-        _ck(self._lib.ls_inner_solve(self._h, _c128(g, self.N, "ls_inner_solve"), float(tol),
-                                     _c128(v, self.N, "ls_inner_solve"), ctypes.byref(it)), "ls_inner_solve")
+        rc = self._lib.ls_inner_solve(self._h, _c128(g, self.N, "ls_inner_solve"), float(tol),
+                                      _c128(v, self.N, "ls_inner_solve"), ctypes.byref(it))
+        if not check:
+            return v, it.value, rc
+        _ck(rc, "ls_inner_solve")
         return v, it.value
 
     def ls_local_solve(self, direction, layer, b, x=None):

@@ -22,8 +22,9 @@ __global__ void k_real_to32(size_t n, const double* __restrict__ a, float* __res
 
 struct HostBufs {
     ls_handle* h = nullptr;
-    double2* f = nullptr;
-    double2* u = nullptr;
+    double2* f = nullptr;  // device staging for host right-hand sides / plane-wave sources
+    double2* u = nullptr;  // device staging for host solutions
+    int cap = 0;           // fields each buffer holds
 };
 HostBufs g_hostbufs[64];
 
@@ -37,6 +38,24 @@ HostBufs* host_bufs(ls_handle* h, bool create) {
             return &b;
         }
     return nullptr;
+}
+
+// Staging buffers for nb fields (grown on demand).
+int host_reserve(ls_handle* h, int nb, HostBufs** out) {
+    HostBufs* b = host_bufs(h, true);
+    if (!b) return LS_ENOMEM;
+    if (b->cap < nb) {
+        cudaFree(b->f);
+        cudaFree(b->u);
+        b->f = b->u = nullptr;
+        b->cap = 0;
+        const size_t bytes = sizeof(double2) * (size_t)h->n * h->n * nb;
+        LS_CUDA(cudaMalloc(&b->f, bytes));
+        LS_CUDA(cudaMalloc(&b->u, bytes));
+        b->cap = nb;
+    }
+    *out = b;
+    return LS_OK;
 }
 
 void release(ls_handle* h) {
@@ -55,6 +74,7 @@ void release(ls_handle* h) {
     if (h->red_host) cudaFreeHost(h->red_host);
     if (h->ev0) cudaEventDestroy(h->ev0);
     if (h->ev1) cudaEventDestroy(h->ev1);
+    for (cudaEvent_t e : h->tev) cudaEventDestroy(e);
     delete h;
 }
 
@@ -72,28 +92,48 @@ int ls_cuda_fail(cudaError_t e) {
     return LS_ECUDA;
 }
 
+// Timed intervals are pairs of events recorded on the handle's stream; nothing
+// waits on them until ls_timing_collect, so timing adds no host synchronisation.
 int ls_timing_begin(ls_handle* h) {
     if (!h->timing) return LS_OK;
-    LS_CUDA(cudaEventRecord(h->ev0, h->stream));
+    if (2 * h->tused + 2 > h->tev.size()) {
+        for (int k = 0; k < 64; ++k) {
+            cudaEvent_t e;
+            LS_CUDA(cudaEventCreate(&e));
+            h->tev.push_back(e);
+        }
+        h->tkind.resize(h->tev.size() / 2);
+    }
+    LS_CUDA(cudaEventRecord(h->tev[2 * h->tused], h->stream));
     return LS_OK;
 }
 
 int ls_timing_end(ls_handle* h, int kind) {
     if (!h->timing) return LS_OK;
-    LS_CUDA(cudaEventRecord(h->ev1, h->stream));
-    LS_CUDA(cudaEventSynchronize(h->ev1));
-    float ms = 0;
-    LS_CUDA(cudaEventElapsedTime(&ms, h->ev0, h->ev1));
-    if (kind == 0) {
-        h->t_apply_ms += ms;
-        h->n_apply++;
-    } else if (kind == 2) {
-        h->t_apply64_ms += ms;
-        h->n_apply64++;
-    } else {
-        h->t_sweep_ms += ms;
-        h->n_sweep++;
+    LS_CUDA(cudaEventRecord(h->tev[2 * h->tused + 1], h->stream));
+    h->tkind[h->tused] = kind;
+    h->tused++;
+    return LS_OK;
+}
+
+// Wait for the recorded intervals and add them to the per-kind totals.
+int ls_timing_collect(ls_handle* h) {
+    if (h->tused) LS_CUDA(cudaEventSynchronize(h->tev[2 * h->tused - 1]));
+    for (size_t k = 0; k < h->tused; ++k) {
+        float ms = 0;
+        LS_CUDA(cudaEventElapsedTime(&ms, h->tev[2 * k], h->tev[2 * k + 1]));
+        if (h->tkind[k] == 0) {
+            h->t_apply_ms += ms;
+            h->n_apply++;
+        } else if (h->tkind[k] == 2) {
+            h->t_apply64_ms += ms;
+            h->n_apply64++;
+        } else {
+            h->t_sweep_ms += ms;
+            h->n_sweep++;
+        }
     }
+    h->tused = 0;
     return LS_OK;
 }
 
@@ -110,6 +150,7 @@ void ls_default_opts(ls_opts* o) {
     o->refine_maxit = 6;
     o->refine_inner_tol = 1e-4;
     o->use_graphs = 1;
+    o->inner_precond = LS_PC_BD;
 }
 
 const char* ls_strerror(int code) {
@@ -157,7 +198,7 @@ int ls_setup(const ls_grid* grid, double hstep, double omega, const double* m, c
     ls_default_opts(&h->opts);
     if (opts) h->opts = *opts;
     if (h->opts.outer_restart < 1 || h->opts.outer_restart > 63 || h->opts.inner_restart < 1 ||
-        h->opts.inner_restart > 63) {
+        h->opts.inner_restart > 63 || (h->opts.inner_precond != LS_PC_BD && h->opts.inner_precond != LS_PC_GS)) {
         delete h;
         return LS_EINVAL;
     }
@@ -224,13 +265,18 @@ int ls_apply_f32(ls_handle* h, const ls_c32* u, ls_c32* y) {
     return ls_apply32(h, reinterpret_cast<const float2*>(u), reinterpret_cast<float2*>(y));
 }
 
+int ls_apply_mixed(ls_handle* h, const ls_c64* u, ls_c64* y) {
+    if (!h || !u || !y) return LS_EINVAL;
+    return ls_apply_mx(h, reinterpret_cast<const double2*>(u), reinterpret_cast<double2*>(y));
+}
+
 int ls_incident_rhs(ls_handle* h, double theta, ls_c64* f) {
     if (!h || !f || !std::isfinite(theta)) return LS_EINVAL;
     return ls_rhs64(h, theta, reinterpret_cast<double2*>(f));
 }
 
-int ls_solve(ls_handle* h, const ls_c64* f, double tol, ls_c64* u, int use_x0, ls_stats* st) {
-    if (!h || !f || !u || !(tol > 0)) return LS_EINVAL;
+int ls_solve_batch(ls_handle* h, int nrhs, const ls_c64* f, double tol, ls_c64* u, int use_x0, ls_stats* st) {
+    if (!h || !f || !u || !(tol > 0) || nrhs < 1 || nrhs > LS_MAX_BATCH) return LS_EINVAL;
     if (!h->factored) return LS_ESTATE;
     ls_stats local{};
     ls_stats* s = st ? st : &local;
@@ -239,8 +285,12 @@ int ls_solve(ls_handle* h, const ls_c64* f, double tol, ls_c64* u, int use_x0, l
     h->n_apply = h->n_sweep = h->n_apply64 = 0;
     const long long l0 = h->launches;
     const auto t0 = std::chrono::steady_clock::now();
-    int rc = ls_outer_solve(h, reinterpret_cast<const double2*>(f), tol, reinterpret_cast<double2*>(u), use_x0, s);
+    h->tused = 0;
+    int rc = ls_outer_solve_b(h, nrhs, reinterpret_cast<const double2*>(f), tol, reinterpret_cast<double2*>(u),
+                              use_x0, s);
     if (cudaStreamSynchronize(h->stream) != cudaSuccess && rc == LS_OK) rc = ls_cuda_fail(cudaGetLastError());
+    const int rct = ls_timing_collect(h);
+    if (rc == LS_OK) rc = rct;
     s->t_solve_s = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     s->t_apply_ms = h->t_apply_ms;
     s->n_apply = h->n_apply;
@@ -252,13 +302,15 @@ int ls_solve(ls_handle* h, const ls_c64* f, double tol, ls_c64* u, int use_x0, l
     return rc;
 }
 
+int ls_solve(ls_handle* h, const ls_c64* f, double tol, ls_c64* u, int use_x0, ls_stats* st) {
+    return ls_solve_batch(h, 1, f, tol, u, use_x0, st);
+}
+
 int ls_solve_plane_wave(ls_handle* h, double theta, double tol, ls_c64* u, ls_stats* st) {
     if (!h || !u) return LS_EINVAL;
     if (!h->factored) return LS_ESTATE;
-    HostBufs* b = host_bufs(h, true);
-    if (!b) return LS_ENOMEM;
-    const size_t N = (size_t)h->n * h->n;
-    if (!b->f) LS_CUDA(cudaMalloc(&b->f, sizeof(double2) * N));
+    HostBufs* b = nullptr;
+    LS_TRY(host_reserve(h, 1, &b));
     const long long l0 = h->launches;
     LS_TRY(ls_rhs64(h, theta, b->f));
     const long long extra = h->launches - l0;
@@ -267,20 +319,23 @@ int ls_solve_plane_wave(ls_handle* h, double theta, double tol, ls_c64* u, ls_st
     return rc;
 }
 
-int ls_solve_host(ls_handle* h, const ls_c64* f_host, double tol, ls_c64* u_host, ls_stats* st) {
-    if (!h || !f_host || !u_host) return LS_EINVAL;
+int ls_solve_batch_host(ls_handle* h, int nrhs, const ls_c64* f_host, double tol, ls_c64* u_host, ls_stats* st) {
+    if (!h || !f_host || !u_host || nrhs < 1 || nrhs > LS_MAX_BATCH) return LS_EINVAL;
     if (!h->factored) return LS_ESTATE;
-    HostBufs* b = host_bufs(h, true);
-    if (!b) return LS_ENOMEM;
-    const size_t N = (size_t)h->n * h->n;
-    if (!b->f) LS_CUDA(cudaMalloc(&b->f, sizeof(double2) * N));
-    if (!b->u) LS_CUDA(cudaMalloc(&b->u, sizeof(double2) * N));
-    LS_CUDA(cudaMemcpyAsync(b->f, f_host, sizeof(double2) * N, cudaMemcpyHostToDevice, h->stream));
-    const int rc = ls_solve(h, reinterpret_cast<const ls_c64*>(b->f), tol, reinterpret_cast<ls_c64*>(b->u), 0, st);
+    HostBufs* b = nullptr;
+    LS_TRY(host_reserve(h, nrhs, &b));
+    const size_t bytes = sizeof(double2) * (size_t)h->n * h->n * nrhs;
+    LS_CUDA(cudaMemcpyAsync(b->f, f_host, bytes, cudaMemcpyHostToDevice, h->stream));
+    const int rc = ls_solve_batch(h, nrhs, reinterpret_cast<const ls_c64*>(b->f), tol,
+                                  reinterpret_cast<ls_c64*>(b->u), 0, st);
     if (rc != LS_OK && rc != LS_ENOCONV) return rc;
-    LS_CUDA(cudaMemcpyAsync(u_host, b->u, sizeof(double2) * N, cudaMemcpyDeviceToHost, h->stream));
+    LS_CUDA(cudaMemcpyAsync(u_host, b->u, bytes, cudaMemcpyDeviceToHost, h->stream));
     LS_CUDA(cudaStreamSynchronize(h->stream));
     return rc;
+}
+
+int ls_solve_host(ls_handle* h, const ls_c64* f_host, double tol, ls_c64* u_host, ls_stats* st) {
+    return ls_solve_batch_host(h, 1, f_host, tol, u_host, st);
 }
 
 int ls_apply_A(ls_handle* h, const ls_c64* r, ls_c64* y) {
@@ -303,6 +358,12 @@ int ls_precond_bd(ls_handle* h, const ls_c64* g, ls_c64* v) {
     if (!h || !g || !v) return LS_EINVAL;
     if (!h->factored) return LS_ESTATE;
     return ls_bd(h, reinterpret_cast<const double2*>(g), reinterpret_cast<double2*>(v));
+}
+
+int ls_precond_bd_batch(ls_handle* h, int nrhs, const ls_c64* g, ls_c64* v) {
+    if (!h || !g || !v || nrhs < 1 || nrhs > (h->prec == LS_MIXED ? LS_MAX_BD_BATCH : 4)) return LS_EINVAL;
+    if (!h->factored) return LS_ESTATE;
+    return ls_bd_b(h, reinterpret_cast<const double2*>(g), reinterpret_cast<double2*>(v), nrhs);
 }
 
 int ls_inner_solve(ls_handle* h, const ls_c64* g, double tol, ls_c64* v, int* iters) {

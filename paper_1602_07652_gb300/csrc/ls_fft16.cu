@@ -1,0 +1,323 @@
+// ls_fft16.cu -- the FP32 LS-apply (Sec. 2) with transforms specialised on the
+// padded length P = 2^LP (256 <= P <= 4096).
+//
+// Same three HBM passes as the generic path (rows forward, columns forward x
+// Ghat x inverse, rows inverse), with everything a transform does fixed at
+// compile time:
+//   * radix-16 Stockham stages (the last forward / first inverse stage takes
+//     the remaining radix), so P = 4096 needs two shared-memory exchanges per
+//     transform instead of three;
+//   * a thread owns one radix-16 butterfly per stage (16 elements; in the
+//     column pass, 16 elements of each of its 2 columns), all index arithmetic
+//     is constant-folded and the stage loop is fully unrolled;
+//   * twiddles W^r, r = 1..15, come from 4 table loads (W, W^2, W^4, W^8) and
+//     11 complex products instead of 15 loads;
+//   * the zero padding is pruned: the first forward stage sees only its lower
+//     8 inputs (z, x < n <= P/2), so its first butterfly layer only rotates.
+// Small P groups several transforms per 256-thread CTA.
+#include "ls_fft_common.cuh"
+
+namespace {
+
+template <int LP>
+struct Geo {
+    static constexpr int P = 1 << LP;
+    static constexpr int T = P / 16;                  // threads per transform
+    static constexpr int G = T >= 256 ? 1 : 256 / T;  // transforms per CTA
+    static constexpr int NS = (LP + 3) / 4;           // stages
+    static constexpr int LRL = LP - 4 * (NS - 1);     // log2 radix of the last forward stage
+    static constexpr int SLOTS = P + (P >> 4);        // padded shared-memory slots per transform
+};
+
+__device__ __forceinline__ int pad16(int i) { return i + (i >> 4); }
+
+template <int DIR>
+__device__ __forceinline__ float2 ld_tw(const float2* __restrict__ tw, int m) {
+    float2 w = __ldg(&tw[m]);
+    if (DIR < 0) w.y = -w.y;
+    return w;
+}
+
+// v[c][e R + r] *= W^(k r), W = exp(-DIR 2 pi i / 2^(LS+LR)), r = 1..R-1.
+// tw[m] = exp(-2 pi i m / P), so W^s = tw[s << (LP - LS - LR)].
+template <int LR, int LS, int DIR, int LP, int CW>
+__device__ __forceinline__ void twiddle(float2 (&v)[CW][16], int e, int k, const float2* __restrict__ tw) {
+    constexpr int R = 1 << LR;
+    constexpr int SH = LP - LS - LR;
+    float2 w[16];
+    w[1] = ld_tw<DIR>(tw, k << SH);
+    if (R > 2) w[2] = ld_tw<DIR>(tw, (2 * k) << SH);
+    if (R > 4) w[4] = ld_tw<DIR>(tw, (4 * k) << SH);
+    if (R > 8) w[8] = ld_tw<DIR>(tw, (8 * k) << SH);
+    if (R > 2) w[3] = w[2] * w[1];
+    if (R > 4) {
+        w[5] = w[4] * w[1];
+        w[6] = w[4] * w[2];
+        w[7] = w[4] * w[3];
+    }
+    if (R > 8) {
+#pragma unroll
+        for (int r = 9; r < 16; ++r) w[r] = w[8] * w[r - 8];
+    }
+#pragma unroll
+    for (int c = 0; c < CW; ++c)
+#pragma unroll
+        for (int r = 1; r < R; ++r) v[c][e * R + r] = v[c][e * R + r] * w[r];
+}
+
+// One Stockham stage: radix 2^LR, Ns = 2^LS.  Butterfly b = j + e T (e < 16/R)
+// holds inputs b + r P/R in v[.][e R + r]; twiddle by W^((b mod Ns) r), DFT.
+template <int LR, int LS, int DIR, int LP, bool HZ, int CW>
+__device__ __forceinline__ void stage(float2 (&v)[CW][16], int j, const float2* __restrict__ tw) {
+    constexpr int R = 1 << LR, T = Geo<LP>::T;
+#pragma unroll
+    for (int e = 0; e < 16 / R; ++e) {
+        if constexpr (LS > 0) twiddle<LR, LS, DIR, LP, CW>(v, e, (j + e * T) & ((1 << LS) - 1), tw);
+#pragma unroll
+        for (int c = 0; c < CW; ++c) dft_reg<R, DIR, HZ>(&v[c][e * R]);
+    }
+}
+
+// Shared-memory element: one complex (rows) or the two complex values of a row of
+// a 2-column tile (columns).
+template <int CW>
+struct Elem;
+template <>
+struct Elem<1> {
+    using T = float2;
+    __device__ __forceinline__ static T pack(const float2 (&v)[1][16], int q) { return v[0][q]; }
+    __device__ __forceinline__ static void unpack(T a, float2 (&v)[1][16], int q) { v[0][q] = a; }
+};
+template <>
+struct Elem<2> {
+    using T = float4;
+    __device__ __forceinline__ static T pack(const float2 (&v)[2][16], int q) {
+        return make_float4(v[0][q].x, v[0][q].y, v[1][q].x, v[1][q].y);
+    }
+    __device__ __forceinline__ static void unpack(T a, float2 (&v)[2][16], int q) {
+        v[0][q] = make_float2(a.x, a.y);
+        v[1][q] = make_float2(a.z, a.w);
+    }
+};
+
+// Outputs of a stage (radix 2^LR, Ns = 2^LS: output (b / Ns) Ns R + b mod Ns + r Ns)
+// through shared memory into the inputs of the next stage (radix 2^LRN).
+// FIRST: the buffer has not been read since the CTA started, no barrier before
+// the stores.
+template <int LR, int LS, int LRN, int LP, bool FIRST, int CW>
+__device__ __forceinline__ void exchange(float2 (&v)[CW][16], typename Elem<CW>::T* buf, int j) {
+    constexpr int R = 1 << LR, RN = 1 << LRN, T = Geo<LP>::T, P = Geo<LP>::P;
+    if (!FIRST) __syncthreads();
+#pragma unroll
+    for (int e = 0; e < 16 / R; ++e) {
+        const int b = j + e * T;
+        const int base = ((b >> LS) << (LS + LR)) + (b & ((1 << LS) - 1));
+#pragma unroll
+        for (int r = 0; r < R; ++r) buf[pad16(base + (r << LS))] = Elem<CW>::pack(v, e * R + r);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int e = 0; e < 16 / RN; ++e) {
+        const int b = j + e * T;
+#pragma unroll
+        for (int r = 0; r < RN; ++r) Elem<CW>::unpack(buf[pad16(b + r * (P / RN))], v, e * RN + r);
+    }
+}
+
+// Forward transform.  In: v[.][t] = x[j + t T] with x[j + t T] = 0 for t >= 8.
+// Out: v[.][e R + r] = X[b + r P/R], b = j + e T, R = 2^LRL.
+template <int LP, bool FIRST, int CW>
+__device__ __forceinline__ void fft_fwd(float2 (&v)[CW][16], typename Elem<CW>::T* buf, int j,
+                                        const float2* __restrict__ tw) {
+    constexpr int NS = Geo<LP>::NS, LRL = Geo<LP>::LRL;
+    stage<4, 0, +1, LP, true>(v, j, tw);
+    if constexpr (NS == 2) {
+        exchange<4, 0, 4, LP, FIRST>(v, buf, j);
+        stage<4, 4, +1, LP, false>(v, j, tw);
+    } else {
+        exchange<4, 0, 4, LP, FIRST>(v, buf, j);
+        stage<4, 4, +1, LP, false>(v, j, tw);
+        exchange<4, 4, LRL, LP, false>(v, buf, j);
+        stage<LRL, 8, +1, LP, false>(v, j, tw);
+    }
+}
+
+// Inverse (unnormalised) transform: the forward stages in reverse order.
+// In: v[.][e R + r] = X[b + r P/R] as fft_fwd leaves it.  Out: v[.][t] = x[j + t T].
+template <int LP, bool FIRST, int CW>
+__device__ __forceinline__ void fft_inv(float2 (&v)[CW][16], typename Elem<CW>::T* buf, int j,
+                                        const float2* __restrict__ tw) {
+    constexpr int NS = Geo<LP>::NS, LRL = Geo<LP>::LRL;
+    if constexpr (NS == 2) {
+        stage<4, 0, -1, LP, false>(v, j, tw);
+        exchange<4, 0, 4, LP, FIRST>(v, buf, j);
+        stage<4, 4, -1, LP, false>(v, j, tw);
+    } else {
+        stage<LRL, 0, -1, LP, false>(v, j, tw);
+        exchange<LRL, 0, 4, LP, FIRST>(v, buf, j);
+        stage<4, LRL, -1, LP, false>(v, j, tw);
+        exchange<4, LRL, 4, LP, false>(v, buf, j);
+        stage<4, LRL + 4, -1, LP, false>(v, j, tw);
+    }
+}
+
+// Pass 1: X[z, :] = FFT_x(pad(m u)[z, :]) for rows z < nrows.
+template <int LP, class Src>
+__global__ void __launch_bounds__(256) k_rows16_fwd(int nrows, int nin, Src src, float2* __restrict__ X,
+                                                   const float2* __restrict__ tw) {
+    using Gm = Geo<LP>;
+    constexpr int P = Gm::P, T = Gm::T, R = 1 << Gm::LRL;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int grp = threadIdx.x / T, j = threadIdx.x % T;
+    float2* buf = reinterpret_cast<float2*>(smem_raw) + grp * Gm::SLOTS;
+    const int z = blockIdx.x * Gm::G + grp;
+    const bool live = z < nrows;
+    float2 v[1][16];
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
+        const int x = j + t * T;
+        v[0][t] = (live && x < nin) ? src.template load<float2>(z, x) : make_float2(0.f, 0.f);
+    }
+    fft_fwd<LP, true>(v, buf, j, tw);
+    if (!live) return;
+    float2* o = X + (size_t)z * P;
+#pragma unroll
+    for (int e = 0; e < 16 / R; ++e)
+#pragma unroll
+        for (int r = 0; r < R; ++r) o[j + e * T + r * (P / R)] = v[0][e * R + r];
+}
+
+// Pass 2: for the 2-column tile (kx0, kx0 + 1): forward z-FFT (rows >= nin are
+// zero), times Ghat, inverse z-FFT; rows z < nout written back in place.
+// Consecutive tiles pair kx with P - kx, so the second read of a Ghat quadrant
+// row finds it in L2.
+template <int LP>
+__global__ void __launch_bounds__(256, 2) k_cols16(int nin, int nout, float2* __restrict__ X,
+                                                  const float2* __restrict__ ghat, const float2* __restrict__ tw) {
+    using Gm = Geo<LP>;
+    constexpr int P = Gm::P, T = Gm::T, R = 1 << Gm::LRL;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int grp = threadIdx.x / T, j = threadIdx.x % T;
+    float4* buf = reinterpret_cast<float4*>(smem_raw) + grp * Gm::SLOTS;
+    constexpr int ntile = P / 2;
+    const int lin = blockIdx.x * Gm::G + grp;
+    const int tile = (lin & 1) ? (ntile - 1 - (lin >> 1)) : (lin >> 1);
+    const int kx0 = 2 * tile;
+    float2 v[2][16];
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
+        const int z = j + t * T;
+        float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (z < nin) a = *reinterpret_cast<const float4*>(X + (size_t)z * P + kx0);
+        v[0][t] = make_float2(a.x, a.y);
+        v[1][t] = make_float2(a.z, a.w);
+    }
+    fft_fwd<LP, true>(v, buf, j, tw);
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+        const int kx = kx0 + c;
+        const float2* g = ghat + (size_t)(kx <= P / 2 ? kx : P - kx) * (P / 2 + 1);
+#pragma unroll
+        for (int e = 0; e < 16 / R; ++e)
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                const int kz = j + e * T + r * (P / R);
+                v[c][e * R + r] = v[c][e * R + r] * __ldg(&g[kz <= P / 2 ? kz : P - kz]);
+            }
+    }
+    fft_inv<LP, false>(v, buf, j, tw);
+#pragma unroll
+    for (int t = 0; t < 16; ++t) {
+        const int z = j + t * T;
+        if (z < nout)
+            *reinterpret_cast<float4*>(X + (size_t)z * P + kx0) =
+                make_float4(v[0][t].x, v[0][t].y, v[1][t].x, v[1][t].y);
+    }
+}
+
+// Pass 3: y[z, x] = u[z, x] + IFFT_x(X[z, :])[x] for x < n.
+template <int LP, class Dst>
+__global__ void __launch_bounds__(256) k_rows16_inv(int nrows, int n, const float2* __restrict__ X, Dst dst,
+                                                   const float2* __restrict__ tw) {
+    using Gm = Geo<LP>;
+    constexpr int P = Gm::P, T = Gm::T, R = 1 << Gm::LRL;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int grp = threadIdx.x / T, j = threadIdx.x % T;
+    float2* buf = reinterpret_cast<float2*>(smem_raw) + grp * Gm::SLOTS;
+    const int z = blockIdx.x * Gm::G + grp;
+    const bool live = z < nrows;
+    float2 v[1][16];
+    const float2* xr = X + (size_t)(live ? z : 0) * P;
+#pragma unroll
+    for (int e = 0; e < 16 / R; ++e)
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[0][e * R + r] = xr[j + e * T + r * (P / R)];
+    fft_inv<LP, true>(v, buf, j, tw);
+    if (!live) return;
+#pragma unroll
+    for (int t = 0; t < 16; ++t) {
+        const int x = j + t * T;
+        if (x < n) dst.template store<float2>(z, x, v[0][t]);
+    }
+}
+
+// G transforms of P = 4096 / G elements, padded: 256 * 17 slots for every P
+constexpr size_t row_smem16() { return sizeof(float2) * 256 * 17; }
+constexpr size_t col_smem16() { return sizeof(float4) * 256 * 17; }
+
+template <int LP, class Src, class Dst>
+int apply_lp(ls_handle* h, Src src, Dst dst, float2* X) {
+    using Gm = Geo<LP>;
+    const int n = h->n;
+    const float2* tw = static_cast<const float2*>(h->tw32);
+    const unsigned rows_grid = (unsigned)((n + Gm::G - 1) / Gm::G);
+    LS_LAUNCH(h, (k_rows16_fwd<LP, Src>), rows_grid, 256, row_smem16(), n, n, src, X, tw);
+    LS_LAUNCH(h, k_cols16<LP>, (unsigned)(Gm::P / 2 / Gm::G), 256, col_smem16(), n, n, X,
+              static_cast<const float2*>(h->ghat32), tw);
+    LS_LAUNCH(h, (k_rows16_inv<LP, Dst>), rows_grid, 256, row_smem16(), n, n, X, dst, tw);
+    return LS_OK;
+}
+
+template <class Src, class Dst>
+int apply_any(ls_handle* h, Src src, Dst dst) {
+    float2* X = static_cast<float2*>(h->fftws);
+    switch (h->lp) {
+        case 8: return apply_lp<8>(h, src, dst, X);
+        case 9: return apply_lp<9>(h, src, dst, X);
+        case 10: return apply_lp<10>(h, src, dst, X);
+        case 11: return apply_lp<11>(h, src, dst, X);
+        case 12: return apply_lp<12>(h, src, dst, X);
+        default: return LS_EINVAL;
+    }
+}
+
+template <int LP>
+int optin_lp() {
+    LS_CUDA(cudaFuncSetAttribute(k_cols16<LP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)col_smem16()));
+    return LS_OK;
+}
+
+}  // namespace
+
+bool ls_fft16_supported(const ls_handle* h) { return h->lp >= 8 && h->lp <= 12; }
+
+int ls_fft16_init(ls_handle* h) {
+    if (!ls_fft16_supported(h)) return LS_OK;
+    LS_TRY(optin_lp<8>());
+    LS_TRY(optin_lp<9>());
+    LS_TRY(optin_lp<10>());
+    LS_TRY(optin_lp<11>());
+    return optin_lp<12>();
+}
+
+int ls_apply32_fft16(ls_handle* h, const float2* u, float2* y) {
+    SrcMU<float, float2> src{h->m32, u, h->n};
+    DstApply<float2> dst{u, y, h->n};
+    return apply_any(h, src, dst);
+}
+
+int ls_apply_mx_fft16(ls_handle* h, const double2* u, double2* y) {
+    SrcMU<float, double2> src{h->m32, u, h->n};
+    DstApply<double2> dst{u, y, h->n};
+    return apply_any(h, src, dst);
+}

@@ -117,6 +117,8 @@ struct DirFactors {
 };
 
 // ------------------------------------------------------------------ handle
+constexpr int kMaxBatch = 8;   // right-hand sides per batched Algorithm 2 (FP64: 4)
+
 struct ls_handle {
     int n = 0, L = 0, E = 0, t = 0, q = 0, P = 0, lp = 0, prec = LS_FP64;
     double h = 0, omega = 0;
@@ -160,16 +162,23 @@ struct ls_handle {
     double* red_host = nullptr;
     size_t red_cap = 0;
 
-    // Algorithm 2 as a captured CUDA graph (inputs/outputs staged through bd_in / bd_out)
-    cudaGraph_t bd_graph = nullptr;
-    cudaGraphExec_t bd_exec = nullptr;
+    // Algorithm 2 as captured CUDA graphs, one per batch size (inputs/outputs staged
+    // through bd_in / bd_out, sized for nb_cap right-hand sides)
+    cudaGraph_t bd_graph[9] = {};
+    cudaGraphExec_t bd_exec[9] = {};
+    long long bd_nodes[9] = {};
     double2* bd_in = nullptr;
     double2* bd_out = nullptr;
-    long long bd_nodes = 0;
+    int nb_cap = 0;
 
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     double t_apply_ms = 0, t_sweep_ms = 0, t_apply64_ms = 0;
     int n_apply = 0, n_sweep = 0, n_apply64 = 0;
+    // timing without host synchronisation: event pairs recorded during a solve and
+    // read once at its end (kind 0: FP32/mixed or FP64 apply, 1: Algorithm 2, 2: FP64 refinement apply)
+    std::vector<cudaEvent_t> tev;   // 2 per interval
+    std::vector<int> tkind;
+    size_t tused = 0;
 };
 
 // ------------------------------------------------------------------ errors
@@ -202,7 +211,11 @@ int ls_fft_init(ls_handle* h);                                   // twiddles, pl
 int ls_spectrum_build(ls_handle* h, const double2* gtab);       // Ghat from the G_w table
 int ls_apply64(ls_handle* h, const double2* u, double2* y);     // y = H u (FP64)
 int ls_apply32(ls_handle* h, const float2* u, float2* y);       // y = H u (FP32)
-int ls_apply_mixed(ls_handle* h, const double2* u, double2* y); // FP64 I/O, FP32 arithmetic
+int ls_apply_mx(ls_handle* h, const double2* u, double2* y);    // FP64 I/O, FP32 arithmetic
+bool ls_fft16_supported(const ls_handle* h);                     // radix-16 FP32 path: 256 <= P <= 4096
+int ls_fft16_init(ls_handle* h);
+int ls_apply32_fft16(ls_handle* h, const float2* u, float2* y);
+int ls_apply_mx_fft16(ls_handle* h, const double2* u, double2* y);
 int ls_rhs64(ls_handle* h, double theta, double2* f);           // f = -w^2 G (m u_I)
 
 // setup (ls_setup_kernels.cu)
@@ -212,6 +225,8 @@ int ls_stencils_build(ls_handle* h, const double2* gtab);      // alpha, beta fo
 // stencils + vector kernels (ls_stencil.cu)
 int ls_stencil_apply(ls_handle* h, int dir, int withm, const double2* v, const double2* g, double2* y);
 int ls_transpose64(ls_handle* h, const double2* a, double2* b);
+int ls_transpose64_b(ls_handle* h, const double2* a, double2* b, int nb);
+int ls_stencil_apply_b(ls_handle* h, int dir, int withm, const double2* v, const double2* g, double2* y, int nb);
 int ls_vec_dots(ls_handle* h, int nvec, const double2* V, size_t ld, const double2* w, double2* out_host);
 int ls_vec_update(ls_handle* h, int nvec, const double2* V, size_t ld, const double2* coef_dev, double2* w);
 int ls_vec_norm(ls_handle* h, const double2* w, double* out_host);
@@ -227,6 +242,9 @@ void ls_factor_free(ls_handle* h);
 // sweeps (ls_sweep.cu)
 int ls_sweep_alloc(ls_handle* h);
 int ls_sweep_dir(ls_handle* h, int dir, const double2* g, double2* v);   // Algorithm 1
+int ls_sweep_dir_b(ls_handle* h, int dir, const double2* g, double2* v, int nb);
+int ls_sweep_reserve(ls_handle* h, int nb);
+int ls_bd_b(ls_handle* h, const double2* g, double2* v, int nb);         // Algorithm 2, nb right-hand sides
 int ls_bd(ls_handle* h, const double2* g, double2* v);                   // Algorithm 2
 void ls_bd_graph_free(ls_handle* h);
 int ls_strip_solve(ls_handle* h, int dir, int layer, const double2* b, double2* x);
@@ -234,3 +252,4 @@ int ls_strip_solve(ls_handle* h, int dir, int layer, const double2* b, double2* 
 // Krylov (ls_krylov.cu)
 int ls_inner_gmres(ls_handle* h, const double2* g, double tol, double2* v, int* iters);
 int ls_outer_solve(ls_handle* h, const double2* f, double tol, double2* u, int use_x0, ls_stats* st);
+int ls_outer_solve_b(ls_handle* h, int nb, const double2* f, double tol, double2* u, int use_x0, ls_stats* st);

@@ -13,6 +13,13 @@
 // Arnoldi: classical Gram-Schmidt applied twice (CGS2), dot products and norms
 // accumulated in FP64 on the device; the small Hessenberg least-squares problem
 // (Givens rotations) is solved on the host, with one device->host copy per step.
+//
+// Batches: nb right-hand sides iterate in lockstep, each with its own Krylov
+// space, Hessenberg matrix and stopping test; a step applies the preconditioner
+// to the whole block of current directions at once, so every Algorithm 2
+// application (the dominant cost) serves all members still iterating.  A
+// member that has converged leaves the cycle; its slot in the block is zeroed.
+// With nb = 1 this is exactly the single right-hand-side iteration.
 #include <chrono>
 #include <cmath>
 #include <complex>
@@ -31,32 +38,37 @@ using cd = std::complex<double>;
 enum Op { OP_H64, OP_HMIX, OP_C };
 enum Pc { PC_NONE, PC_BD, PC_LS };
 
+// Vectors of a Krylov space for up to nbcap members: direction j of member b is
+// V + (j * nbcap + b) * N, so the members' j-th directions form one contiguous
+// block (what the batched preconditioner reads and writes).
 struct KrylovSpace {
-    double2* V = nullptr;   // (m+1) vectors
-    double2* Z = nullptr;   // m vectors
-    double2* w = nullptr;   // work vectors
-    double2* r = nullptr;
-    double2* hdev = nullptr;  // 2 * (m+1) + 1 coefficients on the device
+    double2* V = nullptr;     // (m+1) blocks
+    double2* Z = nullptr;     // m blocks (preconditioned directions)
+    double2* w = nullptr;     // one block of work vectors
+    double2* r = nullptr;     // one block of residuals
+    double2* hdev = nullptr;  // per member: 2 (m+1) + 2 coefficients
     int m = 0;
 };
 
 struct Ctx {
     ls_handle* h;
     KrylovSpace outer, inner;
-    double2* tmpA = nullptr;  // A r for Algorithm 3
-    bool ready = false;
+    double2* tmpA = nullptr;  // A r for Algorithm 3, one block
+    int nbcap = 0;
 };
 
 Ctx* ctx_of(ls_handle* h);
 
-int alloc_space(ls_handle* h, KrylovSpace& S, int m) {
+size_t hstride(int m) { return 2 * (size_t)(m + 1) + 2; }
+
+int alloc_space(ls_handle* h, KrylovSpace& S, int m, int nbcap) {
     const size_t N = (size_t)h->n * h->n;
     S.m = m;
-    LS_CUDA(cudaMalloc(&S.V, sizeof(double2) * N * (m + 1)));
-    LS_CUDA(cudaMalloc(&S.Z, sizeof(double2) * N * m));
-    LS_CUDA(cudaMalloc(&S.w, sizeof(double2) * N));
-    LS_CUDA(cudaMalloc(&S.r, sizeof(double2) * N));
-    LS_CUDA(cudaMalloc(&S.hdev, sizeof(double2) * (2 * (m + 1) + 2)));
+    LS_CUDA(cudaMalloc(&S.V, sizeof(double2) * N * (m + 1) * nbcap));
+    LS_CUDA(cudaMalloc(&S.Z, sizeof(double2) * N * m * nbcap));
+    LS_CUDA(cudaMalloc(&S.w, sizeof(double2) * N * nbcap));
+    LS_CUDA(cudaMalloc(&S.r, sizeof(double2) * N * nbcap));
+    LS_CUDA(cudaMalloc(&S.hdev, sizeof(double2) * hstride(m) * nbcap));
     return LS_OK;
 }
 
@@ -69,7 +81,7 @@ int apply_op(ls_handle* h, Op op, const double2* x, double2* y) {
         }
         case OP_HMIX: {
             LS_TRY(ls_timing_begin(h));
-            LS_TRY(ls_apply_mixed(h, x, y));
+            LS_TRY(ls_apply_mx(h, x, y));
             return ls_timing_end(h, 0);
         }
         default: return ls_stencil_apply(h, 0, 1, x, nullptr, y);
@@ -82,126 +94,215 @@ struct Result {
     bool converged = false;
 };
 
-int fgmres(ls_handle* h, KrylovSpace& S, Op op, Pc pc, const double2* b, double2* x, bool x0, double tol,
-           int maxit, Result& res, ls_stats* st);
+int fgmres_b(ls_handle* h, Ctx* c, KrylovSpace& S, Op op, Pc pc, const double2* b, double2* x, bool x0,
+             const double* tol, int maxit, int nb, const unsigned char* live, Result* res, ls_stats* st);
 
-int apply_pc(ls_handle* h, Pc pc, const double2* v, double2* z, ls_stats* st) {
-    if (pc == PC_NONE) return ls_vec_copy(h, v, z);
+// Right-hand sides per batched Algorithm 2 call (the FP64 sweep kernels stop at 4).
+int bd_chunk(const ls_handle* h) { return h->prec == LS_MIXED ? kMaxBatch : 4; }
+
+// z_b = M v_b for the members with on[b]; v and z are blocks of nb vectors.
+// Members that are off have their slot of v zeroed (their z is not used).
+int apply_pc_b(ls_handle* h, Pc pc, double2* v, double2* z, int nb, const unsigned char* on, ls_stats* st) {
+    const size_t N = (size_t)h->n * h->n;
+    int top = 0;
+    for (int b = 0; b < nb; ++b)
+        if (on[b]) top = b + 1;
+    if (pc == PC_NONE) {
+        for (int b = 0; b < top; ++b)
+            if (on[b]) LS_TRY(ls_vec_copy(h, v + b * N, z + b * N));
+        return LS_OK;
+    }
     if (pc == PC_BD) {
-        LS_TRY(ls_timing_begin(h));
-        LS_TRY(ls_bd(h, v, z));
-        return ls_timing_end(h, 1);
+        for (int b = 0; b < top; ++b)
+            if (!on[b]) LS_TRY(ls_vec_zero(h, v + b * N));
+        const int ch = bd_chunk(h);
+        for (int b0 = 0; b0 < top; b0 += ch) {
+            const int cnt = top - b0 < ch ? top - b0 : ch;
+            LS_TRY(ls_timing_begin(h));
+            if (h->opts.inner_precond == LS_PC_GS) LS_TRY(ls_sweep_dir_b(h, 0, v + b0 * N, z + b0 * N, cnt));
+            else LS_TRY(ls_bd_b(h, v + b0 * N, z + b0 * N, cnt));
+            LS_TRY(ls_timing_end(h, 1));
+        }
+        return LS_OK;
     }
-    // Algorithm 3: z = GMRES(C, A v, Algorithm 2, inner_tol)
+    // Algorithm 3: z = GMRES(C, A v, Algorithm 2, inner_tol), all members at once
     Ctx* c = ctx_of(h);
-    LS_TRY(ls_stencil_apply(h, 0, 0, v, nullptr, c->tmpA));
-    Result r;
-    LS_TRY(fgmres(h, c->inner, OP_C, PC_BD, c->tmpA, z, false, h->opts.inner_tol, h->opts.inner_maxit, r, nullptr));
-    if (st) {
-        st->inner_iters_total += r.iters;
-        st->inner_calls += 1;
-    }
+    for (int b = 0; b < top; ++b)
+        if (on[b]) LS_TRY(ls_stencil_apply(h, 0, 0, v + b * N, nullptr, c->tmpA + b * N));
+    std::vector<double> tl(nb, h->opts.inner_tol);
+    std::vector<Result> r(nb);
+    LS_TRY(fgmres_b(h, c, c->inner, OP_C, PC_BD, c->tmpA, z, false, tl.data(), h->opts.inner_maxit, top, on,
+                    r.data(), nullptr));
+    if (st)
+        for (int b = 0; b < top; ++b)
+            if (on[b]) {
+                st->inner_iters_total += r[b].iters;
+                st->inner_calls += 1;
+            }
     return LS_OK;
 }
 
-int fgmres(ls_handle* h, KrylovSpace& S, Op op, Pc pc, const double2* b, double2* x, bool x0, double tol,
-           int maxit, Result& res, ls_stats* st) {
+struct Member {
+    double nb = 0, beta = 0, relres = 0;
+    int total = 0, k = 0;
+    bool active = false;  // still iterating (not converged, under maxit)
+    bool cyc = false;     // taking part in the current Arnoldi cycle
+    std::vector<cd> H, cs, sn, gv, y;
+};
+
+// Flexible GMRES for members b < nb with live[b]: S.V, S.Z hold the members'
+// spaces; b, x are blocks of nb vectors (stride N).
+int fgmres_b(ls_handle* h, Ctx* c, KrylovSpace& S, Op op, Pc pc, const double2* b, double2* x, bool x0,
+             const double* tol, int maxit, int nb, const unsigned char* live, Result* res, ls_stats* st) {
     const size_t N = (size_t)h->n * h->n;
+    const size_t ldv = N * c->nbcap;  // distance between directions j and j+1 of a member
     const int m = S.m;
-    double nb;
-    LS_TRY(ls_vec_norm(h, b, &nb));
-    if (!std::isfinite(nb)) return LS_ENAN;
-    res = Result{};
-    if (nb == 0.0) {
-        LS_TRY(ls_vec_zero(h, x));
-        res.converged = true;
-        return LS_OK;
+    const size_t HS = hstride(m);
+    auto V = [&](int j, int mb) { return S.V + (size_t)j * ldv + mb * N; };
+    auto Zb = [&](int j) { return S.Z + (size_t)j * ldv; };
+    std::vector<Member> M(nb);
+    for (int i = 0; i < nb; ++i) {
+        res[i] = Result{};
+        if (!live[i]) continue;
+        Member& e = M[i];
+        const double2* bi = b + i * N;
+        double2* xi = x + i * N;
+        double2* ri = S.r + i * N;
+        LS_TRY(ls_vec_norm(h, bi, &e.nb));
+        if (!std::isfinite(e.nb)) return LS_ENAN;
+        if (e.nb == 0.0) {
+            LS_TRY(ls_vec_zero(h, xi));
+            res[i].converged = true;
+            continue;
+        }
+        if (x0) {
+            LS_TRY(apply_op(h, op, xi, ri));
+            LS_TRY(ls_vec_axpby(h, make_double2(1, 0), bi, make_double2(-1, 0), ri));  // r = b - A x
+        } else {
+            LS_TRY(ls_vec_zero(h, xi));
+            LS_TRY(ls_vec_copy(h, bi, ri));
+        }
+        LS_TRY(ls_vec_norm(h, ri, &e.beta));
+        e.relres = e.beta / e.nb;
+        if (!std::isfinite(e.relres)) return LS_ENAN;
+        e.active = e.relres > tol[i] && e.total < maxit;
+        e.H.assign((size_t)(m + 1) * m, cd(0));
+        e.cs.assign(m, cd(0));
+        e.sn.assign(m, cd(0));
+        e.gv.assign(m + 1, cd(0));
+        e.y.assign(m, cd(0));
     }
-    if (x0) {
-        LS_TRY(apply_op(h, op, x, S.r));
-        LS_TRY(ls_vec_axpby(h, make_double2(1, 0), b, make_double2(-1, 0), S.r));  // r = b - A x
-    } else {
-        LS_TRY(ls_vec_zero(h, x));
-        LS_TRY(ls_vec_copy(h, b, S.r));
-    }
-    double beta;
-    LS_TRY(ls_vec_norm(h, S.r, &beta));
-    double relres = beta / nb;
-    std::vector<cd> H((size_t)(m + 1) * m), cs(m), sn(m), gv(m + 1), y(m);
-    std::vector<double2> hh(2 * (m + 1) + 2);
-    int total = 0;
-    while (relres > tol && total < maxit) {
-        if (!std::isfinite(relres)) return LS_ENAN;
-        LS_TRY(ls_vec_axpby(h, make_double2(1.0 / beta, 0), S.r, make_double2(0, 0), S.V));  // V0 = r / beta
-        std::fill(gv.begin(), gv.end(), cd(0));
-        std::fill(H.begin(), H.end(), cd(0));
-        gv[0] = beta;
-        int k = 0;
+    std::vector<double2> hh_all(HS * nb);  // host copy of the members' coefficients
+    std::vector<unsigned char> on(nb);
+    for (;;) {
+        bool any = false;
+        for (int i = 0; i < nb; ++i) {
+            Member& e = M[i];
+            e.cyc = e.active;
+            if (!e.active) continue;
+            any = true;
+            LS_TRY(ls_vec_axpby(h, make_double2(1.0 / e.beta, 0), S.r + i * N, make_double2(0, 0), V(0, i)));
+            std::fill(e.gv.begin(), e.gv.end(), cd(0));
+            std::fill(e.H.begin(), e.H.end(), cd(0));
+            e.gv[0] = e.beta;
+            e.k = 0;
+        }
+        if (!any) break;
         for (int j = 0; j < m; ++j) {
-            double2* vj = S.V + (size_t)j * N;
-            double2* zj = S.Z + (size_t)j * N;
-            double2* vn = S.V + (size_t)(j + 1) * N;
-            LS_TRY(apply_pc(h, pc, vj, zj, st));
-            LS_TRY(apply_op(h, op, zj, vn));
-            // CGS2 against V_0..V_j; coefficients stay on the device between the passes
-            LS_TRY(ls_vec_dots_dev(h, j + 1, S.V, N, vn, S.hdev));
-            LS_TRY(ls_vec_update(h, j + 1, S.V, N, S.hdev, vn));
-            LS_TRY(ls_vec_dots_dev(h, j + 1, S.V, N, vn, S.hdev + (m + 1)));
-            LS_TRY(ls_vec_update(h, j + 1, S.V, N, S.hdev + (m + 1), vn));
-            LS_TRY(ls_vec_dots_dev(h, 1, vn, 0, vn, S.hdev + 2 * (m + 1)));
-            LS_CUDA(cudaMemcpyAsync(hh.data(), S.hdev, sizeof(double2) * (2 * (m + 1) + 1), cudaMemcpyDeviceToHost,
+            bool inc = false;
+            for (int i = 0; i < nb; ++i) {
+                on[i] = M[i].cyc;
+                inc = inc || M[i].cyc;
+            }
+            if (!inc) break;
+            LS_TRY(apply_pc_b(h, pc, V(j, 0), Zb(j), nb, on.data(), st));
+            for (int i = 0; i < nb; ++i) {
+                if (!on[i]) continue;
+                double2* vn = V(j + 1, i);
+                double2* hd = S.hdev + i * HS;
+                LS_TRY(apply_op(h, op, Zb(j) + i * N, vn));
+                // CGS2 against V_0..V_j; coefficients stay on the device between the passes
+                LS_TRY(ls_vec_dots_dev(h, j + 1, V(0, i), ldv, vn, hd));
+                LS_TRY(ls_vec_update(h, j + 1, V(0, i), ldv, hd, vn));
+                LS_TRY(ls_vec_dots_dev(h, j + 1, V(0, i), ldv, vn, hd + (m + 1)));
+                LS_TRY(ls_vec_update(h, j + 1, V(0, i), ldv, hd + (m + 1), vn));
+                LS_TRY(ls_vec_dots_dev(h, 1, vn, 0, vn, hd + 2 * (m + 1)));
+            }
+            LS_CUDA(cudaMemcpyAsync(hh_all.data(), S.hdev, sizeof(double2) * HS * nb, cudaMemcpyDeviceToHost,
                                     h->stream));
             LS_CUDA(cudaStreamSynchronize(h->stream));
-            for (int i = 0; i <= j; ++i)
-                H[(size_t)i * m + j] = cd(hh[i].x + hh[m + 1 + i].x, hh[i].y + hh[m + 1 + i].y);
-            const double hn = std::sqrt(std::max(hh[2 * (m + 1)].x, 0.0));
-            if (!std::isfinite(hn)) return LS_ENAN;
-            H[(size_t)(j + 1) * m + j] = hn;
-            for (int i = 0; i < j; ++i) {  // previous rotations
-                const cd t = cs[i] * H[(size_t)i * m + j] + sn[i] * H[(size_t)(i + 1) * m + j];
-                H[(size_t)(i + 1) * m + j] = -std::conj(sn[i]) * H[(size_t)i * m + j] + cs[i] * H[(size_t)(i + 1) * m + j];
-                H[(size_t)i * m + j] = t;
+            for (int i = 0; i < nb; ++i) {
+                if (!on[i]) continue;
+                Member& e = M[i];
+                const double2* hh = hh_all.data() + i * HS;
+                std::vector<cd>& H = e.H;
+                for (int r = 0; r <= j; ++r)
+                    H[(size_t)r * m + j] = cd(hh[r].x + hh[m + 1 + r].x, hh[r].y + hh[m + 1 + r].y);
+                const double hn = std::sqrt(std::max(hh[2 * (m + 1)].x, 0.0));
+                if (!std::isfinite(hn)) return LS_ENAN;
+                H[(size_t)(j + 1) * m + j] = hn;
+                for (int r = 0; r < j; ++r) {  // previous rotations
+                    const cd t = e.cs[r] * H[(size_t)r * m + j] + e.sn[r] * H[(size_t)(r + 1) * m + j];
+                    H[(size_t)(r + 1) * m + j] =
+                        -std::conj(e.sn[r]) * H[(size_t)r * m + j] + e.cs[r] * H[(size_t)(r + 1) * m + j];
+                    H[(size_t)r * m + j] = t;
+                }
+                const cd a = H[(size_t)j * m + j], cc = H[(size_t)(j + 1) * m + j];
+                const double den = std::sqrt(std::norm(a) + std::norm(cc));
+                if (den == 0.0) {
+                    e.cs[j] = 1.0;
+                    e.sn[j] = 0.0;
+                } else if (std::abs(a) == 0.0) {
+                    e.cs[j] = 0.0;
+                    e.sn[j] = 1.0;
+                } else {
+                    e.cs[j] = std::abs(a) / den;
+                    e.sn[j] = (a / std::abs(a)) * std::conj(cc) / den;
+                }
+                H[(size_t)j * m + j] = e.cs[j] * a + e.sn[j] * cc;
+                H[(size_t)(j + 1) * m + j] = 0.0;
+                e.gv[j + 1] = -std::conj(e.sn[j]) * e.gv[j];
+                e.gv[j] = e.cs[j] * e.gv[j];
+                ++e.total;
+                e.k = j + 1;
+                e.relres = std::abs(e.gv[j + 1]) / e.nb;
+                if (e.relres <= tol[i] || e.total >= maxit || hn == 0.0) {
+                    e.cyc = false;
+                    continue;
+                }
+                double2* vn = V(j + 1, i);
+                LS_TRY(ls_vec_axpby(h, make_double2(1.0 / hn, 0), vn, make_double2(0, 0), vn));
             }
-            const cd a = H[(size_t)j * m + j], c = H[(size_t)(j + 1) * m + j];
-            const double den = std::sqrt(std::norm(a) + std::norm(c));
-            if (den == 0.0) {
-                cs[j] = 1.0;
-                sn[j] = 0.0;
-            } else if (std::abs(a) == 0.0) {
-                cs[j] = 0.0;
-                sn[j] = 1.0;
-            } else {
-                cs[j] = std::abs(a) / den;
-                sn[j] = (a / std::abs(a)) * std::conj(c) / den;
+        }
+        // end of the cycle: x += Z y for every member that iterated, then its true residual
+        for (int i = 0; i < nb; ++i) {
+            Member& e = M[i];
+            if (!e.active) continue;
+            const int k = e.k;
+            for (int r = k - 1; r >= 0; --r) {
+                cd s = e.gv[r];
+                for (int l = r + 1; l < k; ++l) s -= e.H[(size_t)r * m + l] * e.y[l];
+                e.y[r] = s / e.H[(size_t)r * m + r];
             }
-            H[(size_t)j * m + j] = cs[j] * a + sn[j] * c;
-            H[(size_t)(j + 1) * m + j] = 0.0;
-            gv[j + 1] = -std::conj(sn[j]) * gv[j];
-            gv[j] = cs[j] * gv[j];
-            ++total;
-            k = j + 1;
-            relres = std::abs(gv[j + 1]) / nb;
-            if (relres <= tol || total >= maxit || hn == 0.0) break;
-            LS_TRY(ls_vec_axpby(h, make_double2(1.0 / hn, 0), vn, make_double2(0, 0), vn));
+            std::vector<double2> yc(k);
+            for (int r = 0; r < k; ++r) yc[r] = make_double2(e.y[r].real(), e.y[r].imag());
+            double2* xi = x + i * N;
+            double2* ri = S.r + i * N;
+            LS_TRY(ls_vec_combine(h, k, Zb(0) + i * N, ldv, yc.data(), xi));
+            LS_TRY(apply_op(h, op, xi, ri));
+            LS_TRY(ls_vec_axpby(h, make_double2(1, 0), b + i * N, make_double2(-1, 0), ri));
+            LS_TRY(ls_vec_norm(h, ri, &e.beta));
+            e.relres = e.beta / e.nb;
+            if (!std::isfinite(e.relres)) return LS_ENAN;
+            e.active = e.relres > tol[i] && e.total < maxit;
         }
-        for (int i = k - 1; i >= 0; --i) {
-            cd s = gv[i];
-            for (int l = i + 1; l < k; ++l) s -= H[(size_t)i * m + l] * y[l];
-            y[i] = s / H[(size_t)i * m + i];
-        }
-        std::vector<double2> yc(k);
-        for (int i = 0; i < k; ++i) yc[i] = make_double2(y[i].real(), y[i].imag());
-        LS_TRY(ls_vec_combine(h, k, S.Z, N, yc.data(), x));
-        // true residual
-        LS_TRY(apply_op(h, op, x, S.r));
-        LS_TRY(ls_vec_axpby(h, make_double2(1, 0), b, make_double2(-1, 0), S.r));
-        LS_TRY(ls_vec_norm(h, S.r, &beta));
-        relres = beta / nb;
-        if (!std::isfinite(relres)) return LS_ENAN;
     }
-    res.iters = total;
-    res.relres = relres;
-    res.converged = relres <= tol;
+    for (int i = 0; i < nb; ++i) {
+        if (!live[i] || M[i].nb == 0.0) continue;
+        res[i].iters = M[i].total;
+        res[i].relres = M[i].relres;
+        res[i].converged = M[i].relres <= tol[i];
+    }
     return LS_OK;
 }
 
@@ -222,21 +323,6 @@ Ctx* ctx_of(ls_handle* h) {
         if (e.h == h) return e.c;
     return nullptr;
 }
-int ctx_ensure(ls_handle* h) {
-    Ctx* c = ctx_of(h);
-    if (c && c->ready) return LS_OK;
-    if (!c) {
-        c = new Ctx();
-        c->h = h;
-        ctx_list().push_back({h, c});
-    }
-    const size_t N = (size_t)h->n * h->n;
-    LS_TRY(alloc_space(h, c->outer, h->opts.outer_restart));
-    LS_TRY(alloc_space(h, c->inner, h->opts.inner_restart));
-    LS_CUDA(cudaMalloc(&c->tmpA, sizeof(double2) * N));
-    c->ready = true;
-    return LS_OK;
-}
 void free_space(KrylovSpace& S) {
     cudaFree(S.V);
     cudaFree(S.Z);
@@ -244,6 +330,27 @@ void free_space(KrylovSpace& S) {
     cudaFree(S.r);
     cudaFree(S.hdev);
     S = KrylovSpace{};
+}
+// Krylov spaces for nb members (grown on demand, never shrunk).
+int ctx_ensure(ls_handle* h, int nb) {
+    Ctx* c = ctx_of(h);
+    if (c && c->nbcap >= nb) return LS_OK;
+    if (!c) {
+        c = new Ctx();
+        c->h = h;
+        ctx_list().push_back({h, c});
+    }
+    free_space(c->outer);
+    free_space(c->inner);
+    cudaFree(c->tmpA);
+    c->tmpA = nullptr;
+    c->nbcap = 0;
+    const size_t N = (size_t)h->n * h->n;
+    LS_TRY(alloc_space(h, c->outer, h->opts.outer_restart, nb));
+    LS_TRY(alloc_space(h, c->inner, h->opts.inner_restart, nb));
+    LS_CUDA(cudaMalloc(&c->tmpA, sizeof(double2) * N * nb));
+    c->nbcap = nb;
+    return LS_OK;
 }
 }  // namespace
 
@@ -261,66 +368,115 @@ void ls_krylov_free(ls_handle* h) {
 }
 
 int ls_inner_gmres(ls_handle* h, const double2* g, double tol, double2* v, int* iters) {
-    LS_TRY(ctx_ensure(h));
+    LS_TRY(ctx_ensure(h, 1));
     Ctx* c = ctx_of(h);
     Result r;
-    LS_TRY(fgmres(h, c->inner, OP_C, PC_BD, g, v, false, tol, h->opts.inner_maxit, r, nullptr));
+    const unsigned char live = 1;
+    LS_TRY(fgmres_b(h, c, c->inner, OP_C, PC_BD, g, v, false, &tol, h->opts.inner_maxit, 1, &live, &r, nullptr));
     if (iters) *iters = r.iters;
     return r.converged ? LS_OK : LS_ENOCONV;
 }
 
-int ls_outer_solve(ls_handle* h, const double2* f, double tol, double2* u, int use_x0, ls_stats* st) {
-    LS_TRY(ctx_ensure(h));
+// Solve H u_b = f_b for nb right-hand sides (blocks of nb vectors) in lockstep.
+// Statistics: iteration counts summed over the members, refinement steps and
+// the true relative residual the largest over the members.
+int ls_outer_solve_b(ls_handle* h, int nb, const double2* f, double tol, double2* u, int use_x0, ls_stats* st) {
+    LS_TRY(ctx_ensure(h, nb));
     Ctx* c = ctx_of(h);
-    double nf;
-    LS_TRY(ls_vec_norm(h, f, &nf));
-    if (!std::isfinite(nf)) return LS_ENAN;
-    if (nf == 0.0) {
-        LS_TRY(ls_vec_zero(h, u));
+    const size_t N = (size_t)h->n * h->n;
+    std::vector<double> nf(nb), relres(nb, 0.0), stol(nb);
+    std::vector<unsigned char> live(nb, 0);
+    std::vector<Result> r(nb);
+    int nlive = 0;
+    for (int i = 0; i < nb; ++i) {
+        LS_TRY(ls_vec_norm(h, f + i * N, &nf[i]));
+        if (!std::isfinite(nf[i])) return LS_ENAN;
+        if (nf[i] == 0.0) LS_TRY(ls_vec_zero(h, u + i * N));
+        else {
+            live[i] = 1;
+            ++nlive;
+        }
+    }
+    double worst = 0.0;
+    bool all_conv = true;
+    if (nlive == 0) {
         if (st) st->true_rel_residual = 0.0;
         return LS_OK;
     }
     if (h->prec == LS_FP64) {
-        Result r;
-        LS_TRY(fgmres(h, c->outer, OP_H64, PC_LS, f, u, use_x0 != 0, tol, h->opts.outer_maxit, r, st));
-        if (st) {
-            st->outer_iters += r.iters;
-            st->refine_steps = 1;
-            st->true_rel_residual = r.relres;
+        std::vector<double> tl(nb, tol);
+        LS_TRY(fgmres_b(h, c, c->outer, OP_H64, PC_LS, f, u, use_x0 != 0, tl.data(), h->opts.outer_maxit, nb,
+                        live.data(), r.data(), st));
+        for (int i = 0; i < nb; ++i) {
+            if (!live[i]) continue;
+            if (st) st->outer_iters += r[i].iters;
+            worst = std::max(worst, r[i].relres);
+            all_conv = all_conv && r[i].converged;
         }
-        return r.converged ? LS_OK : LS_ENOCONV;
+        if (st) {
+            st->refine_steps = 1;
+            st->true_rel_residual = worst;
+        }
+        return all_conv ? LS_OK : LS_ENOCONV;
     }
     // LS_MIXED: FP64 iterative refinement around the FP32-apply outer iteration.
-    // Buffers: outer.w holds the refinement right-hand side and inner.w the
-    // correction; flexible GMRES itself never touches either.
+    // Blocks: outer.w holds the refinement right-hand sides and inner.w the
+    // corrections; flexible GMRES itself never touches either.
     double2* d = c->outer.w;
     double2* corr = c->inner.w;
-    if (!use_x0) LS_TRY(ls_vec_zero(h, u));
-    double relres = 1.0;
-    int steps = 0;
+    if (!use_x0)
+        for (int i = 0; i < nb; ++i)
+            if (live[i]) LS_TRY(ls_vec_zero(h, u + i * N));
+    std::vector<unsigned char> act(live);
+    std::vector<int> steps(nb, 0);
     for (;;) {
-        LS_TRY(ls_timing_begin(h));
-        LS_TRY(ls_apply64(h, u, d));  // d = H u (FP64)
-        LS_TRY(ls_timing_end(h, 2));
-        LS_TRY(ls_vec_axpby(h, make_double2(1, 0), f, make_double2(-1, 0), d));  // d = f - H u
-        double nr;
-        LS_TRY(ls_vec_norm(h, d, &nr));
-        relres = nr / nf;
-        if (!std::isfinite(relres)) return LS_ENAN;
-        if (relres <= tol || steps >= h->opts.refine_maxit) break;
-        // ask the FP32 correction for what is still missing, never below what FP32 can deliver
-        double stol = 0.3 * tol / relres;
-        if (stol < h->opts.refine_inner_tol) stol = h->opts.refine_inner_tol;
-        if (stol > 0.5) stol = 0.5;
-        Result r;
-        LS_TRY(fgmres(h, c->outer, OP_HMIX, PC_LS, d, corr, false, stol, h->opts.outer_maxit, r, st));
-        if (st) st->outer_iters += r.iters;
-        LS_TRY(ls_vec_axpby(h, make_double2(1, 0), corr, make_double2(1, 0), u));  // u += correction
-        ++steps;
+        bool any = false;
+        for (int i = 0; i < nb; ++i) {
+            if (!act[i]) continue;
+            double2* di = d + i * N;
+            LS_TRY(ls_timing_begin(h));
+            LS_TRY(ls_apply64(h, u + i * N, di));  // d = H u (FP64)
+            LS_TRY(ls_timing_end(h, 2));
+            LS_TRY(ls_vec_axpby(h, make_double2(1, 0), f + i * N, make_double2(-1, 0), di));  // d = f - H u
+            double nr;
+            LS_TRY(ls_vec_norm(h, di, &nr));
+            relres[i] = nr / nf[i];
+            if (!std::isfinite(relres[i])) return LS_ENAN;
+            if (relres[i] <= tol || steps[i] >= h->opts.refine_maxit) {
+                act[i] = 0;
+                continue;
+            }
+            any = true;
+            // ask the FP32 correction for what is still missing, never below what FP32 can deliver
+            double s = 0.3 * tol / relres[i];
+            if (s < h->opts.refine_inner_tol) s = h->opts.refine_inner_tol;
+            if (s > 0.5) s = 0.5;
+            stol[i] = s;
+        }
+        if (!any) break;
+        LS_TRY(fgmres_b(h, c, c->outer, OP_HMIX, PC_LS, d, corr, false, stol.data(), h->opts.outer_maxit, nb,
+                        act.data(), r.data(), st));
+        for (int i = 0; i < nb; ++i) {
+            if (!act[i]) continue;
+            if (st) st->outer_iters += r[i].iters;
+            LS_TRY(ls_vec_axpby(h, make_double2(1, 0), corr + i * N, make_double2(1, 0), u + i * N));  // u += corr
+            ++steps[i];
+        }
+    }
+    int smax = 0;
+    for (int i = 0; i < nb; ++i) {
+        if (!live[i]) continue;
+        worst = std::max(worst, relres[i]);
+        all_conv = all_conv && relres[i] <= tol;
+        smax = std::max(smax, steps[i]);
     }
     if (st) {
-        st->refine_steps = steps;
-        st->true_rel_residual = relres;
+        st->refine_steps = smax;
+        st->true_rel_residual = worst;
     }
-    return relres <= tol ? LS_OK : LS_ENOCONV;
+    return all_conv ? LS_OK : LS_ENOCONV;
+}
+
+int ls_outer_solve(ls_handle* h, const double2* f, double tol, double2* u, int use_x0, ls_stats* st) {
+    return ls_outer_solve_b(h, 1, f, tol, u, use_x0, st);
 }

@@ -14,10 +14,17 @@
 
 namespace {
 
+// batch member b = blockIdx.y works on v, g, y at offset b * n * n (m is shared)
 template <int MODE>  // 0: y = A v   1: y = C v   2: y = g - C v
 __global__ void k_stencil(int n, const StencilTables* __restrict__ tab, const double* __restrict__ m,
                           const double2* __restrict__ v, const double2* __restrict__ g, double2* __restrict__ y) {
     __shared__ double2 sa[81], sb[81];
+    {
+        const size_t off = (size_t)blockIdx.y * n * n;
+        v += off;
+        y += off;
+        if (MODE == 2) g += off;
+    }
     for (int i = threadIdx.x; i < 81; i += blockDim.x) {
         sa[i] = tab->alpha[i];
         sb[i] = tab->wbeta[i];
@@ -52,6 +59,8 @@ __global__ void k_stencil(int n, const StencilTables* __restrict__ tab, const do
 
 __global__ void k_transpose(int n, const double2* __restrict__ a, double2* __restrict__ b) {
     __shared__ double2 tile[32][33];
+    a += (size_t)blockIdx.z * n * n;   // batch member blockIdx.z
+    b += (size_t)blockIdx.z * n * n;
     const int x0 = blockIdx.x * 32, z0 = blockIdx.y * 32;
     for (int r = threadIdx.y; r < 32; r += blockDim.y) {
         const int z = z0 + r, x = x0 + threadIdx.x;
@@ -161,24 +170,30 @@ __global__ void k_zero(size_t N, double2* __restrict__ y) {
 
 }  // namespace
 
-int ls_stencil_apply(ls_handle* h, int dir, int mode, const double2* v, const double2* g, double2* y) {
+int ls_stencil_apply_b(ls_handle* h, int dir, int mode, const double2* v, const double2* g, double2* y, int nb) {
     const int n = h->n;
     const size_t N = (size_t)n * n;
-    const unsigned nb = (unsigned)((N + 255) / 256);
+    const dim3 grid((unsigned)((N + 255) / 256), nb);
     const double* m = dir == 0 ? h->m64 : h->mT64;
     const StencilTables* tab = h->dtabs + dir;
-    if (mode == 0) LS_LAUNCH(h, k_stencil<0>, nb, 256, 0, n, tab, m, v, g, y);
-    else if (mode == 1) LS_LAUNCH(h, k_stencil<1>, nb, 256, 0, n, tab, m, v, g, y);
-    else LS_LAUNCH(h, k_stencil<2>, nb, 256, 0, n, tab, m, v, g, y);
+    if (mode == 0) LS_LAUNCH(h, k_stencil<0>, grid, 256, 0, n, tab, m, v, g, y);
+    else if (mode == 1) LS_LAUNCH(h, k_stencil<1>, grid, 256, 0, n, tab, m, v, g, y);
+    else LS_LAUNCH(h, k_stencil<2>, grid, 256, 0, n, tab, m, v, g, y);
     return LS_OK;
 }
 
-int ls_transpose64(ls_handle* h, const double2* a, double2* b) {
+int ls_stencil_apply(ls_handle* h, int dir, int mode, const double2* v, const double2* g, double2* y) {
+    return ls_stencil_apply_b(h, dir, mode, v, g, y, 1);
+}
+
+int ls_transpose64_b(ls_handle* h, const double2* a, double2* b, int nb) {
     const int n = h->n;
-    dim3 grid((n + 31) / 32, (n + 31) / 32), block(32, 8);
+    dim3 grid((n + 31) / 32, (n + 31) / 32, nb), block(32, 8);
     LS_LAUNCH(h, k_transpose, grid, block, 0, n, a, b);
     return LS_OK;
 }
+
+int ls_transpose64(ls_handle* h, const double2* a, double2* b) { return ls_transpose64_b(h, a, b, 1); }
 
 int ls_transpose_real(ls_handle* h, const double* a, double* b) {
     const int n = h->n;

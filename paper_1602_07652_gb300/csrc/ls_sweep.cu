@@ -31,6 +31,11 @@
 // Each kernel is one launch per level over all blocks of that level; a block of
 // 256 threads handles one block's mat-vecs, its warps splitting the columns of
 // the column-major matrices (coalesced reads, all loads independent).
+//
+// Batches: every kernel takes nb right-hand sides at once (batch member b's
+// strips at offset b * SB, its grid vectors at offset b * N).  A reduction step
+// loads each factor matrix once and applies it to all nb vectors, so a batch
+// shares both the factor traffic and the chain of dependent launches.
 #include "ls_internal.cuh"
 #include "ls_strip.cuh"
 
@@ -43,198 +48,221 @@ struct Pool {
     __device__ __forceinline__ const cpx_t<T>* mat(size_t off) const { return base + off * qq; }
 };
 
-// Mat-vecs spread over a whole block of kMvThreads threads: warp w takes columns
-// w, w + kMvWarps, ...; lane l takes rows l, l + 32, ... (RPT rows, q <= 32 RPT).
-// Every thread issues its loads independently of the others (column-major
-// matrices, so a warp reads 32 consecutive entries of a column), and the
-// per-warp partial sums are reduced through shared memory.  A thread-per-row
-// loop instead walks all q columns of a matrix one load at a time.
 constexpr int kMvWarps = 8;
 constexpr int kMvThreads = 32 * kMvWarps;
 
-template <typename T, int RPT>
-__device__ __forceinline__ void mv_accumulate(const cpx_t<T>* __restrict__ M, const cpx_t<T>* vs, int q,
-                                              cpx_t<T> (&part)[RPT]) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll 4
-    for (int c = warp; c < q; c += kMvWarps) {
-        const cpx_t<T> vc = vs[c];
-#pragma unroll
-        for (int k = 0; k < RPT; ++k) {
-            const int r = lane + 32 * k;
-            if (r < q) part[k] = cfma(__ldg(&M[(size_t)c * q + r]), vc, part[k]);
-        }
-    }
-}
-
-// The same for NM matrices at once: the loads of all of them for a column are
-// issued before any multiply, so one pass over the columns has NM times more
-// loads in flight.  Absent terms pass a valid matrix and a zero vector.
-template <typename T, int RPT, int NM>
-__device__ __forceinline__ void mv_accumulate_n(const cpx_t<T>* const (&M)[NM], const cpx_t<T>* const (&vs)[NM], int q,
-                                                cpx_t<T> (&part)[RPT]) {
+// One reduction step for one block j and NB (>= nb) batch members:
+//   out_b = base_b + sum_t M_t v_{t,b}
+// Warp w takes columns w, w + 8, ...; lane l takes rows l, l + 32, ... (RPT rows);
+// each matrix entry is loaded once and used for every batch member; the
+// vectors (signs applied) sit in shared memory, partial sums are reduced there.
+//   MODE 0 (level 0 odd):    x_j = D^{-1} x_j
+//   MODE 1 (forward):        x_j = x_j - F x_{j-1} - G x_{j+1}          (even j)
+//   MODE 2 (backward):       x_j = D^{-1} x_j - P x_{j-1} - Q x_{j+1}   (odd j)
+//   MODE 3 (top block):      x_0 = D^{-1} x_0
+template <typename T, int RPT, int MODE, int NB>
+__global__ void __launch_bounds__(kMvThreads, NB >= 4 ? 2 : 1) k_cr_step(int q, int k, int nk, Pool<T> pool, size_t off_a,
+                                                       size_t off_b, size_t off_c, cpx_t<T>* __restrict__ x,
+                                                       size_t SB, int nb) {
     using C = cpx_t<T>;
+    constexpr int NM = MODE == 1 ? 2 : (MODE == 2 ? 3 : 1);
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* vin = reinterpret_cast<C*>(smem_raw);     // [NM][NB][q]
+    C* red = vin + (size_t)NM * NB * q;          // [kMvWarps][NB][q]
+    const int idx = blockIdx.x;
+    const size_t s = (size_t)1 << k;
+    const int j = MODE == 1 ? 2 * idx : (MODE == 3 ? 0 : 2 * idx + 1);
+    const bool hw = j >= 1, he = j + 1 < nk;
+    for (int o = threadIdx.x; o < NM * NB * q; o += kMvThreads) {
+        const int t = o / (NB * q), b = (o / q) % NB, r = o % q;
+        C val = czero<C>();
+        if (b < nb) {
+            const C* xb = x + (size_t)b * SB;
+            if (MODE == 0 || MODE == 3) val = xb[((size_t)j * s) * q + r];
+            if (MODE == 1) {
+                if (t == 0 && hw) val = -xb[((size_t)(j - 1) * s) * q + r];
+                if (t == 1 && he) val = -xb[((size_t)(j + 1) * s) * q + r];
+            }
+            if (MODE == 2) {
+                if (t == 0) val = xb[((size_t)j * s) * q + r];
+                if (t == 1) val = -xb[((size_t)(j - 1) * s) * q + r];
+                if (t == 2 && he) val = -xb[((size_t)(j + 1) * s) * q + r];
+            }
+        }
+        vin[o] = val;
+    }
+    __syncthreads();
+    const C* Ms[NM];
+    if (MODE == 0 || MODE == 3) Ms[0] = pool.mat(off_a + idx);
+    if (MODE == 1) {  // a missing neighbour has zero vectors; its matrix slot reuses the other one
+        const C* F = pool.mat(off_b + idx);
+        const C* G = pool.mat(off_c + idx);
+        Ms[0] = hw ? F : G;
+        Ms[NM - 1] = he ? G : F;
+    }
+    if (MODE == 2) {
+        const C* Dm = pool.mat(off_a + idx);
+        Ms[0] = Dm;
+        Ms[1] = pool.mat(off_b + idx);
+        Ms[NM - 1] = he ? pool.mat(off_c + idx) : Dm;
+    }
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    C part[RPT][NB];
+#pragma unroll
+    for (int kk = 0; kk < RPT; ++kk)
+#pragma unroll
+        for (int b = 0; b < NB; ++b) part[kk][b] = czero<C>();
 #pragma unroll 2
     for (int c = warp; c < q; c += kMvWarps) {
         C a[NM][RPT];
 #pragma unroll
         for (int t = 0; t < NM; ++t)
 #pragma unroll
-            for (int k = 0; k < RPT; ++k) {
-                const int r = lane + 32 * k;
-                a[t][k] = r < q ? __ldg(&M[t][(size_t)c * q + r]) : czero<C>();
+            for (int kk = 0; kk < RPT; ++kk) {
+                const int r = lane + 32 * kk;
+                a[t][kk] = r < q ? __ldg(&Ms[t][(size_t)c * q + r]) : czero<C>();
             }
 #pragma unroll
-        for (int t = 0; t < NM; ++t) {
-            const C vc = vs[t][c];
+        for (int t = 0; t < NM; ++t)
 #pragma unroll
-            for (int k = 0; k < RPT; ++k) part[k] = cfma(a[t][k], vc, part[k]);
-        }
+            for (int b = 0; b < NB; ++b) {
+                const C vc = vin[((size_t)t * NB + b) * q + c];
+#pragma unroll
+                for (int kk = 0; kk < RPT; ++kk) part[kk][b] = cfma(a[t][kk], vc, part[kk][b]);
+            }
     }
-}
-
-// red: kMvWarps * q entries of shared memory; returns the full sum for row threadIdx.x (< q)
-template <typename T, int RPT>
-__device__ __forceinline__ cpx_t<T> mv_reduce(cpx_t<T> (&part)[RPT], cpx_t<T>* red, int q) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
-    for (int k = 0; k < RPT; ++k) {
-        const int r = lane + 32 * k;
-        if (r < q) red[warp * q + r] = part[k];
+    for (int kk = 0; kk < RPT; ++kk) {
+        const int r = lane + 32 * kk;
+        if (r < q)
+#pragma unroll
+            for (int b = 0; b < NB; ++b) red[((size_t)warp * NB + b) * q + r] = part[kk][b];
     }
     __syncthreads();
-    cpx_t<T> s = czero<cpx_t<T>>();
-    if ((int)threadIdx.x < q)
-        for (int w = 0; w < kMvWarps; ++w) s = s + red[w * q + threadIdx.x];
-    return s;
-}
-
-// One step of the reduction for one block: out = base + sum_t M_t v_t, where the
-// vectors are staged in shared memory with their signs applied.  MODE:
-//   0 (level 0 odd):      x_j = D^{-1} x_j
-//   1 (forward, level k): x_j = x_j - F x_{j-1} - G x_{j+1}            (even j)
-//   2 (backward, level k): x_j = D^{-1} x_j - P x_{j-1} - Q x_{j+1}     (odd j)
-//   3 (top block):         x_0 = D^{-1} x_0
-template <typename T, int RPT, int MODE>
-__global__ void __launch_bounds__(kMvThreads) k_cr_step(int q, int k, int nk, Pool<T> pool, size_t off_a,
-                                                       size_t off_b, size_t off_c, cpx_t<T>* __restrict__ x) {
-    using C = cpx_t<T>;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    C* v0 = reinterpret_cast<C*>(smem_raw);
-    C* v1 = v0 + q;
-    C* v2 = v1 + q;
-    C* red = v2 + q;
-    const int idx = blockIdx.x;
-    const size_t s = (size_t)1 << k;
-    const int j = MODE == 1 ? 2 * idx : (MODE == 3 ? 0 : 2 * idx + 1);
-    const bool hw = j >= 1, he = j + 1 < nk;
-    const int r = threadIdx.x;
-    C* xj = x + ((size_t)j * s) * q;
-    if (r < q) {
-        if (MODE == 0 || MODE == 3) v0[r] = xj[r];
-        if (MODE == 1) {
-            v1[r] = hw ? -x[((size_t)(j - 1) * s) * q + r] : czero<C>();
-            v2[r] = he ? -x[((size_t)(j + 1) * s) * q + r] : czero<C>();
-        }
-        if (MODE == 2) {
-            v0[r] = xj[r];
-            v1[r] = -x[((size_t)(j - 1) * s) * q + r];
-            v2[r] = he ? -x[((size_t)(j + 1) * s) * q + r] : czero<C>();
-        }
+    for (int o = threadIdx.x; o < nb * q; o += kMvThreads) {
+        const int b = o / q, r = o % q;
+        C sum = czero<C>();
+        for (int w = 0; w < kMvWarps; ++w) sum = sum + red[((size_t)w * NB + b) * q + r];
+        C* xj = x + (size_t)b * SB + ((size_t)j * s) * q;
+        xj[r] = MODE == 1 ? xj[r] + sum : sum;
     }
-    __syncthreads();
-    C part[RPT];
-#pragma unroll
-    for (int i = 0; i < RPT; ++i) part[i] = czero<C>();
-    if (MODE == 0 || MODE == 3) mv_accumulate<T, RPT>(pool.mat(off_a + idx), v0, q, part);
-    if (MODE == 1) {  // a missing neighbour has a zero vector; its matrix slot reuses the other one
-        const C* F = pool.mat(off_b + idx);
-        const C* G = pool.mat(off_c + idx);
-        const C* const Ms[2] = {hw ? F : G, he ? G : F};
-        const C* const Vs[2] = {v1, v2};
-        mv_accumulate_n<T, RPT, 2>(Ms, Vs, q, part);
-    }
-    if (MODE == 2) {
-        const C* Dm = pool.mat(off_a + idx);
-        const C* const Ms[3] = {Dm, pool.mat(off_b + idx), he ? pool.mat(off_c + idx) : Dm};
-        const C* const Vs[3] = {v0, v1, v2};
-        mv_accumulate_n<T, RPT, 3>(Ms, Vs, q, part);
-    }
-    const C sum = mv_reduce<T, RPT>(part, red, q);
-    if (r < q) xj[r] = MODE == 1 ? xj[r] + sum : sum;
 }
 
 // level 0 backward, odd blocks: x_j = y_j - D^{-1} (W_j x_{j-1} + E_j x_{j+1})
-template <typename T, int RPT>
-__global__ void __launch_bounds__(kMvThreads) k_cr_l0_back(int q, int nb, const cpx_t<T>* __restrict__ cw,
+template <typename T, int RPT, int NB>
+__global__ void __launch_bounds__(kMvThreads, NB >= 4 ? 2 : 1) k_cr_l0_back(int q, int nblk, const cpx_t<T>* __restrict__ cw,
                                                           const cpx_t<T>* __restrict__ ce, Pool<T> pool,
-                                                          size_t off_dinv, cpx_t<T>* __restrict__ x) {
+                                                          size_t off_dinv, cpx_t<T>* __restrict__ x, size_t SB,
+                                                          int nb) {
     using C = cpx_t<T>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    C* vt = reinterpret_cast<C*>(smem_raw);
-    C* red = vt + q;
+    C* vt = reinterpret_cast<C*>(smem_raw);   // [NB][q]
+    C* red = vt + (size_t)NB * q;             // [kMvWarps][NB][q]
     const int o = blockIdx.x;
     const int j = 2 * o + 1;
-    const int r = threadIdx.x;
-    if (r < q) {
+    const C* wj = cw + (size_t)j * 3 * q;
+    const C* ej = ce + (size_t)j * 3 * q;
+    for (int e = threadIdx.x; e < NB * q; e += kMvThreads) {
+        const int b = e / q, r = e % q;
         C acc = czero<C>();
-        const C* wj = cw + (size_t)j * 3 * q;
-        const C* ej = ce + (size_t)j * 3 * q;
+        if (b < nb) {
+            const C* xb = x + (size_t)b * SB;
 #pragma unroll
-        for (int dz = -1; dz <= 1; ++dz) {
-            const int rr = r + dz;
-            if (rr < 0 || rr >= q) continue;
-            acc = cfma(wj[(dz + 1) * q + r], x[(size_t)(j - 1) * q + rr], acc);
-            if (j + 1 < nb) acc = cfma(ej[(dz + 1) * q + r], x[(size_t)(j + 1) * q + rr], acc);
+            for (int dz = -1; dz <= 1; ++dz) {
+                const int rr = r + dz;
+                if (rr < 0 || rr >= q) continue;
+                acc = cfma(wj[(dz + 1) * q + r], xb[(size_t)(j - 1) * q + rr], acc);
+                if (j + 1 < nblk) acc = cfma(ej[(dz + 1) * q + r], xb[(size_t)(j + 1) * q + rr], acc);
+            }
         }
-        vt[r] = -acc;
+        vt[e] = -acc;
     }
     __syncthreads();
-    C part[RPT];
+    const C* M = pool.mat(off_dinv + o);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    C part[RPT][NB];
 #pragma unroll
-    for (int i = 0; i < RPT; ++i) part[i] = czero<C>();
-    mv_accumulate<T, RPT>(pool.mat(off_dinv + o), vt, q, part);
-    const C sum = mv_reduce<T, RPT>(part, red, q);
-    if (r < q) x[(size_t)j * q + r] = x[(size_t)j * q + r] + sum;
+    for (int kk = 0; kk < RPT; ++kk)
+#pragma unroll
+        for (int b = 0; b < NB; ++b) part[kk][b] = czero<C>();
+#pragma unroll 4
+    for (int c = warp; c < q; c += kMvWarps) {
+        C a[RPT];
+#pragma unroll
+        for (int kk = 0; kk < RPT; ++kk) {
+            const int r = lane + 32 * kk;
+            a[kk] = r < q ? __ldg(&M[(size_t)c * q + r]) : czero<C>();
+        }
+#pragma unroll
+        for (int b = 0; b < NB; ++b) {
+            const C vc = vt[(size_t)b * q + c];
+#pragma unroll
+            for (int kk = 0; kk < RPT; ++kk) part[kk][b] = cfma(a[kk], vc, part[kk][b]);
+        }
+    }
+#pragma unroll
+    for (int kk = 0; kk < RPT; ++kk) {
+        const int r = lane + 32 * kk;
+        if (r < q)
+#pragma unroll
+            for (int b = 0; b < NB; ++b) red[((size_t)warp * NB + b) * q + r] = part[kk][b];
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < nb * q; e += kMvThreads) {
+        const int b = e / q, r = e % q;
+        C sum = czero<C>();
+        for (int w = 0; w < kMvWarps; ++w) sum = sum + red[((size_t)w * NB + b) * q + r];
+        C* xj = x + (size_t)b * SB + (size_t)j * q;
+        xj[r] = xj[r] + sum;
+    }
 }
 
-// level 0, even blocks: b_j -= W_j y_{j-1} + E_j y_{j+1} (W, E tridiagonal from the stencil)
+// level 0, even blocks: b_j -= W_j y_{j-1} + E_j y_{j+1} (tabulated tridiagonal couplings)
 template <typename T>
-__global__ void k_l0_even(int q, int nb, const cpx_t<T>* __restrict__ cw, const cpx_t<T>* __restrict__ ce,
-                          cpx_t<T>* __restrict__ x) {
+__global__ void k_l0_even(int q, int nblk, const cpx_t<T>* __restrict__ cw, const cpx_t<T>* __restrict__ ce,
+                          cpx_t<T>* __restrict__ x, size_t SB) {
     using C = cpx_t<T>;
     const int j = 2 * blockIdx.x;
     const int r = threadIdx.x;
     if (r >= q) return;
-    C acc = x[(size_t)j * q + r];
+    C* xb = x + (size_t)blockIdx.y * SB;
+    C acc = xb[(size_t)j * q + r];
     const C* wj = cw + (size_t)j * 3 * q;
     const C* ej = ce + (size_t)j * 3 * q;
 #pragma unroll
     for (int dz = -1; dz <= 1; ++dz) {
         const int rr = r + dz;
         if (rr < 0 || rr >= q) continue;
-        if (j >= 1) acc = cfms(wj[(dz + 1) * q + r], x[(size_t)(j - 1) * q + rr], acc);
-        if (j + 1 < nb) acc = cfms(ej[(dz + 1) * q + r], x[(size_t)(j + 1) * q + rr], acc);
+        if (j >= 1) acc = cfms(wj[(dz + 1) * q + r], xb[(size_t)(j - 1) * q + rr], acc);
+        if (j + 1 < nblk) acc = cfms(ej[(dz + 1) * q + r], xb[(size_t)(j + 1) * q + rr], acc);
     }
-    x[(size_t)j * q + r] = acc;
+    xb[(size_t)j * q + r] = acc;
 }
 
-// g^l = chi_{Omega^l} g (+ injection from the layer above), copied to the solution buffer
+// g^l = chi_{Omega^l} g (+ injection from the layer above), copied to the solution buffer.
+// Batch member b = blockIdx.y: strips at + b * SB, traces at + b * TB, grid vector at + b * N.
 template <typename T>
-__global__ void k_gather(StripGeom g, const cpx_t<T>* __restrict__ inj, int l,
-                         const double2* __restrict__ gf, cpx_t<T>* __restrict__ rhs, cpx_t<T>* __restrict__ sol,
-                         const cpx_t<T>* __restrict__ above, cpx_t<T>* __restrict__ trace_above) {
+__global__ void k_gather(StripGeom g, const cpx_t<T>* __restrict__ inj, int l, const double2* __restrict__ gf,
+                         cpx_t<T>* __restrict__ rhs, cpx_t<T>* __restrict__ sol, const cpx_t<T>* __restrict__ above,
+                         cpx_t<T>* __restrict__ trace_above, size_t SB, size_t TB) {
     using C = cpx_t<T>;
     const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int q = g.q, n = g.n, E = g.E, t = g.t;
     if (e >= (size_t)n * q) return;
+    const size_t b = blockIdx.y;
+    gf += b * (size_t)n * n;
+    rhs += b * SB;
+    sol += b * SB;
+    if (above) {
+        above += b * SB;
+        trace_above += b * TB;
+    }
     const int i = (int)(e / q), r = (int)(e % q);
     if (above && r == 0) trace_above[i] = above[(size_t)i * q + E - 1];  // w^{l+1}_0, kept for the upward sweep
     double2 val = make_double2(0, 0);
     if (r >= E && r < E + t) val = gf[(size_t)(l * t - E + r) * n + i];
     if (above) {
-        const cpx_t<T>* c0 = inj + (size_t)l * 12 * n;  // slots 0, 1 of layer l: [slot][dx+1][i]
+        const C* c0 = inj + (size_t)l * 12 * n;  // slots 0, 1 of layer l: [slot][dx+1][i]
         if (r == E + t - 1) {  // -C^l_{n,n+1} w^{l+1}_1 ; w^{l+1}_1 = row E of layer l+1
             for (int dx = -1; dx <= 1; ++dx) {
                 if (i + dx < 0 || i + dx >= n) continue;
@@ -254,22 +282,27 @@ __global__ void k_gather(StripGeom g, const cpx_t<T>* __restrict__ inj, int l,
     sol[e] = cv;
 }
 
-// sol = g^l + injection from the layer below (upward sweep)
+// sol = g^l + injection from the layer below (upward sweep); batch member b = blockIdx.y
 template <typename T>
-__global__ void k_inject_up(StripGeom g, const cpx_t<T>* __restrict__ inj, int l,
-                            const cpx_t<T>* __restrict__ rhs, cpx_t<T>* __restrict__ sol,
-                            const cpx_t<T>* __restrict__ below, const cpx_t<T>* __restrict__ trace_self) {
+__global__ void k_inject_up(StripGeom g, const cpx_t<T>* __restrict__ inj, int l, const cpx_t<T>* __restrict__ rhs,
+                            cpx_t<T>* __restrict__ sol, const cpx_t<T>* __restrict__ below,
+                            const cpx_t<T>* __restrict__ trace_self, size_t SB, size_t TB) {
     using C = cpx_t<T>;
     const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int q = g.q, n = g.n, E = g.E, t = g.t;
     if (e >= (size_t)n * q) return;
+    const size_t b = blockIdx.y;
+    rhs += b * SB;
+    sol += b * SB;
+    below += b * SB;
+    trace_self += b * TB;
     const int i = (int)(e / q), r = (int)(e % q);
     if (r != E && r != E - 1) {
         sol[e] = rhs[e];
         return;
     }
     double2 val = ccast<double2>(rhs[e]);
-    const cpx_t<T>* c0 = inj + (size_t)l * 12 * n;  // slots 2, 3 of layer l: [slot][dx+1][i]
+    const C* c0 = inj + (size_t)l * 12 * n;  // slots 2, 3 of layer l: [slot][dx+1][i]
     if (r == E) {  // -C^l_{1,0} (v^{l-1}_n - w^l_0) ; v^{l-1}_n = row E+t-1 of layer l-1
         for (int dx = -1; dx <= 1; ++dx) {
             if (i + dx < 0 || i + dx >= n) continue;
@@ -286,15 +319,17 @@ __global__ void k_inject_up(StripGeom g, const cpx_t<T>* __restrict__ inj, int l
     sol[e] = ccast<C>(val);
 }
 
-// v = rows 1..n of every layer's solution (concatenation)
+// v = rows 1..n of every layer's solution (concatenation); batch member b = blockIdx.y
 template <typename T>
-__global__ void k_scatter(StripGeom g, const cpx_t<T>* __restrict__ sol, size_t strip_stride, double2* __restrict__ v) {
+__global__ void k_scatter(StripGeom g, const cpx_t<T>* __restrict__ sol, size_t strip_stride, size_t SB,
+                          double2* __restrict__ v) {
     const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int n = g.n;
     if (e >= (size_t)n * n) return;
+    const size_t b = blockIdx.y;
     const int z = (int)(e / n), i = (int)(e % n);
     const int l = z / g.t, r = z - l * g.t + g.E;
-    v[e] = ccast<double2>(sol[(size_t)l * strip_stride + (size_t)i * g.q + r]);
+    v[b * (size_t)n * n + e] = ccast<double2>(sol[b * SB + (size_t)l * strip_stride + (size_t)i * g.q + r]);
 }
 
 // natural strip layout (q rows x n, x fastest) <-> block layout (i*q + r)
@@ -320,134 +355,201 @@ __global__ void k_add(size_t N, const double2* __restrict__ a, double2* __restri
 
 StripGeom geom_of(const ls_handle* h) { return StripGeom{h->n, h->t, h->E, h->q, h->opts.shift / h->omega}; }
 
-template <typename T, int RPT>
-int cr_solve_rpt(ls_handle* h, int dir, int l, cpx_t<T>* x) {
+template <typename T, int RPT, int NB>
+int cr_solve_rpt(ls_handle* h, int dir, int l, cpx_t<T>* x, size_t SB, int nb) {
     using C = cpx_t<T>;
     const DirFactors& F = h->fac[dir];
     const int q = h->q, n = h->n;
     const size_t qq = (size_t)q * q;
-    const cpx_t<T>* base;
+    const C* base;
     if constexpr (sizeof(T) == 4) base = F.pool32;
     else base = F.pool64;
     Pool<T> pool{base + (size_t)l * F.mats_per_strip * qq, qq};
     const int thr = (q + 31) / 32 * 32;
-    const size_t sm_step = (3 + kMvWarps) * sizeof(C) * q;
-    const size_t sm_back = (1 + kMvWarps) * sizeof(C) * q;
+    const size_t sm_step = (size_t)(3 + kMvWarps) * NB * sizeof(C) * q;
+    const size_t sm_back = (size_t)(1 + kMvWarps) * NB * sizeof(C) * q;
     const CrLevel& l0 = F.lev[0];
-    if (l0.nodd)
-        LS_LAUNCH(h, (k_cr_step<T, RPT, 0>), l0.nodd, kMvThreads, sm_step, q, 0, l0.nk, pool, l0.off_dinv,
-                  (size_t)0, (size_t)0, x);
     const C* cw = static_cast<const C*>(F.cw) + (size_t)l * n * 3 * q;
     const C* ce = static_cast<const C*>(F.ce) + (size_t)l * n * 3 * q;
-    LS_LAUNCH(h, k_l0_even<T>, l0.neven, thr, 0, q, n, cw, ce, x);
+    if (l0.nodd)
+        LS_LAUNCH(h, (k_cr_step<T, RPT, 0, NB>), l0.nodd, kMvThreads, sm_step, q, 0, l0.nk, pool, l0.off_dinv,
+                  (size_t)0, (size_t)0, x, SB, nb);
+    LS_LAUNCH(h, k_l0_even<T>, dim3(l0.neven, nb), thr, 0, q, n, cw, ce, x, SB);
     for (int k = 1; k < F.K; ++k) {
         const CrLevel& lv = F.lev[k];
-        LS_LAUNCH(h, (k_cr_step<T, RPT, 1>), lv.neven, kMvThreads, sm_step, q, k, lv.nk, pool, (size_t)0, lv.off_f,
-                  lv.off_g, x);
+        LS_LAUNCH(h, (k_cr_step<T, RPT, 1, NB>), lv.neven, kMvThreads, sm_step, q, k, lv.nk, pool, (size_t)0,
+                  lv.off_f, lv.off_g, x, SB, nb);
     }
-    LS_LAUNCH(h, (k_cr_step<T, RPT, 3>), 1, kMvThreads, sm_step, q, 0, 1, pool, F.off_top, (size_t)0, (size_t)0, x);
+    LS_LAUNCH(h, (k_cr_step<T, RPT, 3, NB>), 1, kMvThreads, sm_step, q, 0, 1, pool, F.off_top, (size_t)0, (size_t)0,
+              x, SB, nb);
     for (int k = F.K - 1; k >= 1; --k) {
         const CrLevel& lv = F.lev[k];
         if (lv.nodd)
-            LS_LAUNCH(h, (k_cr_step<T, RPT, 2>), lv.nodd, kMvThreads, sm_step, q, k, lv.nk, pool, lv.off_dinv,
-                      lv.off_p, lv.off_q, x);
+            LS_LAUNCH(h, (k_cr_step<T, RPT, 2, NB>), lv.nodd, kMvThreads, sm_step, q, k, lv.nk, pool, lv.off_dinv,
+                      lv.off_p, lv.off_q, x, SB, nb);
     }
     if (l0.nodd)
-        LS_LAUNCH(h, (k_cr_l0_back<T, RPT>), l0.nodd, kMvThreads, sm_back, q, n, cw, ce, pool, l0.off_dinv, x);
+        LS_LAUNCH(h, (k_cr_l0_back<T, RPT, NB>), l0.nodd, kMvThreads, sm_back, q, n, cw, ce, pool, l0.off_dinv, x,
+                  SB, nb);
     return LS_OK;
 }
 
-template <typename T>
-int cr_solve(ls_handle* h, int dir, int l, cpx_t<T>* x) {
-    const int rpt = (h->q + 31) / 32;
-    switch (rpt) {
-        case 1: return cr_solve_rpt<T, 1>(h, dir, l, x);
-        case 2: return cr_solve_rpt<T, 2>(h, dir, l, x);
-        case 3: return cr_solve_rpt<T, 3>(h, dir, l, x);
-        default: return cr_solve_rpt<T, 4>(h, dir, l, x);
+template <typename T, int NB>
+int cr_solve_nb(ls_handle* h, int dir, int l, cpx_t<T>* x, size_t SB, int nb) {
+    switch ((h->q + 31) / 32) {
+        case 1: return cr_solve_rpt<T, 1, NB>(h, dir, l, x, SB, nb);
+        case 2: return cr_solve_rpt<T, 2, NB>(h, dir, l, x, SB, nb);
+        case 3: return cr_solve_rpt<T, 3, NB>(h, dir, l, x, SB, nb);
+        default: return cr_solve_rpt<T, 4, NB>(h, dir, l, x, SB, nb);
     }
 }
 
+// The batch template is the smallest supported NB >= nb (FP64 keeps NB <= 4 for registers).
 template <typename T>
-int sweep_impl(ls_handle* h, int dir, const double2* g, double2* v) {
+int cr_solve(ls_handle* h, int dir, int l, cpx_t<T>* x, size_t SB, int nb) {
+    if (nb <= 1) return cr_solve_nb<T, 1>(h, dir, l, x, SB, nb);
+    if (nb <= 2) return cr_solve_nb<T, 2>(h, dir, l, x, SB, nb);
+    if (nb <= 4) return cr_solve_nb<T, 4>(h, dir, l, x, SB, nb);
+    if constexpr (sizeof(T) == 4) return cr_solve_nb<T, 8>(h, dir, l, x, SB, nb);
+    return LS_EINVAL;
+}
+
+template <typename T>
+int sweep_impl(ls_handle* h, int dir, const double2* g, double2* v, int nb) {
     using C = cpx_t<T>;
     const int n = h->n, q = h->q, L = h->L;
     const size_t sstride = (size_t)n * q;
+    const size_t SB = (size_t)L * sstride, TB = (size_t)L * n;
     C* rhs = static_cast<C*>(h->srhs);
     C* sol = static_cast<C*>(h->ssol);
     C* trc = static_cast<C*>(h->strace);
     const DirFactors& F = h->fac[dir];
     const StripGeom geo = geom_of(h);
-    const unsigned nbs = (unsigned)((sstride + 255) / 256);
+    const dim3 gs((unsigned)((sstride + 255) / 256), nb);
     for (int l = L - 1; l >= 0; --l) {  // downward sweep
-        LS_LAUNCH(h, k_gather<T>, nbs, 256, 0, geo, static_cast<const C*>(F.cinj), l, g, rhs + l * sstride, sol + l * sstride,
-                  l < L - 1 ? sol + (l + 1) * sstride : (const C*)nullptr,
-                  l < L - 1 ? trc + (size_t)(l + 1) * n : (C*)nullptr);
-        LS_TRY(cr_solve<T>(h, dir, l, sol + l * sstride));
+        LS_LAUNCH(h, k_gather<T>, gs, 256, 0, geo, static_cast<const C*>(F.cinj), l, g, rhs + l * sstride,
+                  sol + l * sstride, l < L - 1 ? sol + (l + 1) * sstride : (const C*)nullptr,
+                  l < L - 1 ? trc + (size_t)(l + 1) * n : (C*)nullptr, SB, TB);
+        LS_TRY(cr_solve<T>(h, dir, l, sol + l * sstride, SB, nb));
     }
     for (int l = 1; l < L; ++l) {  // upward sweep
-        LS_LAUNCH(h, k_inject_up<T>, nbs, 256, 0, geo, static_cast<const C*>(F.cinj), l, rhs + l * sstride, sol + l * sstride,
-                  sol + (l - 1) * sstride, trc + (size_t)l * n);
-        LS_TRY(cr_solve<T>(h, dir, l, sol + l * sstride));
+        LS_LAUNCH(h, k_inject_up<T>, gs, 256, 0, geo, static_cast<const C*>(F.cinj), l, rhs + l * sstride,
+                  sol + l * sstride, sol + (l - 1) * sstride, trc + (size_t)l * n, SB, TB);
+        LS_TRY(cr_solve<T>(h, dir, l, sol + l * sstride, SB, nb));
     }
     const size_t N = (size_t)n * n;
-    LS_LAUNCH(h, k_scatter<T>, (unsigned)((N + 255) / 256), 256, 0, geo, sol, sstride, v);
+    LS_LAUNCH(h, k_scatter<T>, dim3((unsigned)((N + 255) / 256), nb), 256, 0, geo, sol, sstride, SB, v);
+    return LS_OK;
+}
+
+template <typename T>
+int smem_optin(int q) {
+    using C = cpx_t<T>;
+    const int rpt = (q + 31) / 32;
+    const size_t s8 = (size_t)(3 + kMvWarps) * 8 * sizeof(C) * q, s4 = (size_t)(3 + kMvWarps) * 4 * sizeof(C) * q;
+    const size_t big = sizeof(T) == 4 ? s8 : s4;
+    if (big <= 48 * 1024) return LS_OK;
+#define LS_OPTIN(R, NB)                                                                                           \
+    do {                                                                                                          \
+        const size_t sz = (size_t)(3 + kMvWarps) * NB * sizeof(C) * q;                                            \
+        LS_CUDA(cudaFuncSetAttribute(k_cr_step<T, R, 0, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sz)); \
+        LS_CUDA(cudaFuncSetAttribute(k_cr_step<T, R, 1, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sz)); \
+        LS_CUDA(cudaFuncSetAttribute(k_cr_step<T, R, 2, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sz)); \
+        LS_CUDA(cudaFuncSetAttribute(k_cr_step<T, R, 3, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sz)); \
+        LS_CUDA(cudaFuncSetAttribute(k_cr_l0_back<T, R, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sz)); \
+    } while (0)
+#define LS_OPTIN_R(NB)                  \
+    switch (rpt) {                      \
+        case 1: LS_OPTIN(1, NB); break; \
+        case 2: LS_OPTIN(2, NB); break; \
+        case 3: LS_OPTIN(3, NB); break; \
+        default: LS_OPTIN(4, NB); break; \
+    }
+    LS_OPTIN_R(2);
+    LS_OPTIN_R(4);
+    if constexpr (sizeof(T) == 4) LS_OPTIN_R(8);
+#undef LS_OPTIN_R
+#undef LS_OPTIN
     return LS_OK;
 }
 
 }  // namespace
 
-int ls_sweep_alloc(ls_handle* h) {
-    const size_t cnt = (size_t)h->L * h->n * h->q;
+// Sweep buffers for batches of up to nb right-hand sides (grown on demand; a
+// capture made for smaller buffers is dropped).
+int ls_sweep_reserve(ls_handle* h, int nb) {
+    if (nb <= h->nb_cap) return LS_OK;
+    ls_bd_graph_free(h);
+    const size_t cnt = (size_t)h->L * h->n * h->q * nb;
     const size_t es = h->prec == LS_MIXED ? sizeof(float2) : sizeof(double2);
+    const size_t N = (size_t)h->n * h->n;
+    void* ptrs[] = {h->srhs, h->ssol, h->strace, h->vtmp, h->bd_in, h->bd_out};
+    for (void* p : ptrs) cudaFree(p);
+    h->srhs = h->ssol = h->strace = h->vtmp = nullptr;
+    h->bd_in = h->bd_out = nullptr;
+    h->nb_cap = 0;
     LS_CUDA(cudaMalloc(&h->srhs, es * cnt));
     LS_CUDA(cudaMalloc(&h->ssol, es * cnt));
-    LS_CUDA(cudaMalloc(&h->strace, es * (size_t)h->L * h->n));
-    const size_t N = (size_t)h->n * h->n;
-    LS_CUDA(cudaMalloc(&h->vtmp, sizeof(double2) * N * 4));
-    LS_CUDA(cudaMalloc(&h->bd_in, sizeof(double2) * N));
-    LS_CUDA(cudaMalloc(&h->bd_out, sizeof(double2) * N));
+    LS_CUDA(cudaMalloc(&h->strace, es * (size_t)h->L * h->n * nb));
+    LS_CUDA(cudaMalloc(&h->vtmp, sizeof(double2) * N * 4 * nb));
+    LS_CUDA(cudaMalloc(&h->bd_in, sizeof(double2) * N * nb));
+    LS_CUDA(cudaMalloc(&h->bd_out, sizeof(double2) * N * nb));
+    h->nb_cap = nb;
     return LS_OK;
 }
 
-// Algorithm 1 on direction dir (0: horizontal layers; 1: vertical layers).
-int ls_sweep_dir(ls_handle* h, int dir, const double2* g, double2* v) {
-    const size_t N = (size_t)h->n * h->n;
-    double2* t0 = static_cast<double2*>(h->vtmp);
-    double2* t1 = t0 + N;
-    if (dir == 0) {
-        if (h->prec == LS_MIXED) return sweep_impl<float>(h, 0, g, v);
-        return sweep_impl<double>(h, 0, g, v);
-    }
-    LS_TRY(ls_transpose64(h, g, t0));
-    if (h->prec == LS_MIXED) LS_TRY(sweep_impl<float>(h, 1, t0, t1));
-    else LS_TRY(sweep_impl<double>(h, 1, t0, t1));
-    return ls_transpose64(h, t1, v);
+int ls_sweep_alloc(ls_handle* h) {
+    if (h->prec == LS_MIXED) LS_TRY(smem_optin<float>(h->q));
+    else LS_TRY(smem_optin<double>(h->q));
+    return ls_sweep_reserve(h, 1);
 }
 
-// Algorithm 2: v = u1 + u2, u1 = Alg. 1 horizontal (g), u2 = Alg. 1 vertical (g - C u1).
-static int bd_direct(ls_handle* h, const double2* g, double2* v) {
+// Algorithm 1 on direction dir (0: horizontal layers; 1: vertical layers) for nb
+// right-hand sides g (nb x N, contiguous) into v.
+int ls_sweep_dir_b(ls_handle* h, int dir, const double2* g, double2* v, int nb) {
+    if (nb < 1 || nb > kMaxBatch || (h->prec != LS_MIXED && nb > 4)) return LS_EINVAL;
+    LS_TRY(ls_sweep_reserve(h, nb));  // no-op when called inside a capture (reserved beforehand)
     const size_t N = (size_t)h->n * h->n;
-    double2* u1 = static_cast<double2*>(h->vtmp) + 2 * N;
-    double2* e = u1 + N;
-    LS_TRY(ls_sweep_dir(h, 0, g, u1));
-    LS_TRY(ls_stencil_apply(h, 0, 2, u1, g, e));   // e = g - C u1
-    LS_TRY(ls_sweep_dir(h, 1, e, v));
-    LS_LAUNCH(h, k_add, 608, 256, 0, N, u1, v);
+    double2* t0 = static_cast<double2*>(h->vtmp);
+    double2* t1 = t0 + N * nb;
+    if (dir == 0) {
+        if (h->prec == LS_MIXED) return sweep_impl<float>(h, 0, g, v, nb);
+        return sweep_impl<double>(h, 0, g, v, nb);
+    }
+    LS_TRY(ls_transpose64_b(h, g, t0, nb));
+    if (h->prec == LS_MIXED) LS_TRY(sweep_impl<float>(h, 1, t0, t1, nb));
+    else LS_TRY(sweep_impl<double>(h, 1, t0, t1, nb));
+    return ls_transpose64_b(h, t1, v, nb);
+}
+
+int ls_sweep_dir(ls_handle* h, int dir, const double2* g, double2* v) { return ls_sweep_dir_b(h, dir, g, v, 1); }
+
+// Algorithm 2 for nb right-hand sides: v = u1 + u2, u1 = Alg. 1 horizontal (g),
+// u2 = Alg. 1 vertical (g - C u1).
+static int bd_direct(ls_handle* h, const double2* g, double2* v, int nb) {
+    const size_t N = (size_t)h->n * h->n;
+    double2* u1 = static_cast<double2*>(h->vtmp) + 2 * N * nb;
+    double2* e = u1 + N * nb;
+    LS_TRY(ls_sweep_dir_b(h, 0, g, u1, nb));
+    LS_TRY(ls_stencil_apply_b(h, 0, 2, u1, g, e, nb));   // e = g - C u1
+    LS_TRY(ls_sweep_dir_b(h, 1, e, v, nb));
+    LS_LAUNCH(h, k_add, 608, 256, 0, N * nb, u1, v);
     return LS_OK;
 }
 
 void ls_bd_graph_free(ls_handle* h) {
-    if (h->bd_exec) cudaGraphExecDestroy(h->bd_exec);
-    if (h->bd_graph) cudaGraphDestroy(h->bd_graph);
-    h->bd_exec = nullptr;
-    h->bd_graph = nullptr;
-    h->bd_nodes = 0;
+    for (int b = 0; b <= kMaxBatch; ++b) {
+        if (h->bd_exec[b]) cudaGraphExecDestroy(h->bd_exec[b]);
+        if (h->bd_graph[b]) cudaGraphDestroy(h->bd_graph[b]);
+        h->bd_exec[b] = nullptr;
+        h->bd_graph[b] = nullptr;
+        h->bd_nodes[b] = 0;
+    }
 }
 
-// Capture Algorithm 2 on the staging buffers once (the sequence of launches and all
-// pointers are fixed after ls_factor), then replay it.
-static int bd_capture(ls_handle* h) {
+// Capture Algorithm 2 for nb right-hand sides on the staging buffers once (the
+// sequence of launches and all pointers are fixed after ls_factor), then replay it.
+static int bd_capture(ls_handle* h, int nb) {
     cudaStream_t cap = nullptr;
     LS_CUDA(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
     cudaStream_t saved = h->stream;
@@ -457,7 +559,7 @@ static int bd_capture(ls_handle* h) {
     cudaGraph_t graph = nullptr;
     cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
-        rc = bd_direct(h, h->bd_in, h->bd_out);
+        rc = bd_direct(h, h->bd_in, h->bd_out, nb);
         e = cudaStreamEndCapture(cap, &graph);
     }
     h->stream = saved;
@@ -475,37 +577,42 @@ static int bd_capture(ls_handle* h) {
         cudaGraphDestroy(graph);
         return ls_cuda_fail(e);
     }
-    h->bd_graph = graph;
-    h->bd_exec = exec;
-    h->bd_nodes = nodes;
+    h->bd_graph[nb] = graph;
+    h->bd_exec[nb] = exec;
+    h->bd_nodes[nb] = nodes;
     return LS_OK;
 }
 
-int ls_bd(ls_handle* h, const double2* g, double2* v) {
-    if (!h->opts.use_graphs) return bd_direct(h, g, v);
-    if (!h->bd_exec) LS_TRY(bd_capture(h));
+int ls_bd_b(ls_handle* h, const double2* g, double2* v, int nb) {
+    if (nb < 1 || nb > kMaxBatch || (h->prec != LS_MIXED && nb > 4)) return LS_EINVAL;
+    LS_TRY(ls_sweep_reserve(h, nb));
+    if (!h->opts.use_graphs) return bd_direct(h, g, v, nb);
+    if (!h->bd_exec[nb]) LS_TRY(bd_capture(h, nb));
     const size_t N = (size_t)h->n * h->n;
-    LS_CUDA(cudaMemcpyAsync(h->bd_in, g, sizeof(double2) * N, cudaMemcpyDeviceToDevice, h->stream));
-    LS_CUDA(cudaGraphLaunch(h->bd_exec, h->stream));
-    h->launches += h->bd_nodes;
-    LS_CUDA(cudaMemcpyAsync(v, h->bd_out, sizeof(double2) * N, cudaMemcpyDeviceToDevice, h->stream));
+    LS_CUDA(cudaMemcpyAsync(h->bd_in, g, sizeof(double2) * N * nb, cudaMemcpyDeviceToDevice, h->stream));
+    LS_CUDA(cudaGraphLaunch(h->bd_exec[nb], h->stream));
+    h->launches += h->bd_nodes[nb];
+    LS_CUDA(cudaMemcpyAsync(v, h->bd_out, sizeof(double2) * N * nb, cudaMemcpyDeviceToDevice, h->stream));
     return LS_OK;
 }
+
+int ls_bd(ls_handle* h, const double2* g, double2* v) { return ls_bd_b(h, g, v, 1); }
 
 int ls_strip_solve(ls_handle* h, int dir, int layer, const double2* b, double2* x) {
     const int n = h->n, q = h->q;
     const size_t cnt = (size_t)n * q;
-    const unsigned nb = (unsigned)((cnt + 255) / 256);
+    const unsigned nblk = (unsigned)((cnt + 255) / 256);
+    const size_t SB = (size_t)h->L * cnt;
     if (h->prec == LS_MIXED) {
         float2* s = static_cast<float2*>(h->ssol);
-        LS_LAUNCH(h, k_strip_in<float>, nb, 256, 0, n, q, b, s);
-        LS_TRY(cr_solve<float>(h, dir, layer, s));
-        LS_LAUNCH(h, k_strip_out<float>, nb, 256, 0, n, q, s, x);
+        LS_LAUNCH(h, k_strip_in<float>, nblk, 256, 0, n, q, b, s);
+        LS_TRY(cr_solve<float>(h, dir, layer, s, SB, 1));
+        LS_LAUNCH(h, k_strip_out<float>, nblk, 256, 0, n, q, s, x);
     } else {
         double2* s = static_cast<double2*>(h->ssol);
-        LS_LAUNCH(h, k_strip_in<double>, nb, 256, 0, n, q, b, s);
-        LS_TRY(cr_solve<double>(h, dir, layer, s));
-        LS_LAUNCH(h, k_strip_out<double>, nb, 256, 0, n, q, s, x);
+        LS_LAUNCH(h, k_strip_in<double>, nblk, 256, 0, n, q, b, s);
+        LS_TRY(cr_solve<double>(h, dir, layer, s, SB, 1));
+        LS_LAUNCH(h, k_strip_out<double>, nblk, 256, 0, n, q, s, x);
     }
     return LS_OK;
 }

@@ -1,0 +1,153 @@
+"""Batched right-hand sides through the C ABI (GPU).
+
+A batch shares H (one scatterer, many incident directions, Sec. 6) and must
+give, member by member, what the one-at-a-time entry points give:
+  * Algorithm 2 on a block of fields equals Algorithm 2 on each field;
+  * the lockstep batched solve reaches the tolerance on every member and its
+    fields match the single solves (the same iterates up to rounding), and the
+    oracle's solution on the small case;
+  * degenerate members (f_b = 0) and bad input (NaN) behave as in ls_solve.
+"""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+from oracle import solver as osolver  # noqa: E402
+from paper_1602_07652_gb300 import binding, inputs  # noqa: E402
+
+
+def rel(a, b):
+    return float(torch.linalg.norm((a - b).flatten()) / torch.linalg.norm(b.flatten()))
+
+
+def cuda(x):
+    return torch.from_numpy(np.ascontiguousarray(x)).cuda()
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    from paper_1602_07652_gb300 import build_lib
+    build_lib.build()
+    binding.load()
+
+
+def _fields(n, nb, seed):
+    return torch.stack([cuda(inputs.random_field(n, seed + b)) for b in range(nb)]).contiguous()
+
+
+@pytest.mark.parametrize("prec,nb", [(binding.LS_FP64, 1), (binding.LS_FP64, 3), (binding.LS_FP64, 4),
+                                     (binding.LS_MIXED, 2), (binding.LS_MIXED, 5), (binding.LS_MIXED, 8)])
+def test_batched_bd_equals_per_member_bd(prec, nb):
+    # ragged: 96 = 6 layers of 16 rows, q = 24 (one warp of rows); nb not a power of two
+    n, L, E = 96, 6, 4
+    w = inputs.omega_for_ppw(n, 10.0)
+    m = inputs.bump_medium(n, nbumps=6, seed=5)
+    s = binding.Solver(cuda(m), w, layers=L, ext=E, precision=prec)
+    s.ls_factor()
+    g = _fields(n, nb, 100)
+    v = s.ls_precond_bd_batch(g)
+    torch.cuda.synchronize()
+    for b in range(nb):
+        vb = s.ls_precond_bd(g[b].contiguous())
+        err = rel(v[b], vb)
+        assert err < (1e-13 if prec == binding.LS_FP64 else 1e-6), (b, err)
+    s.close()
+
+
+@pytest.mark.parametrize("prec", [binding.LS_FP64, binding.LS_MIXED])
+def test_batched_bd_with_two_warps_of_rows(prec):
+    # q = 2 * 8 + 32 = 48 > 32 rows: two rows per lane in the block mat-vecs
+    n, L, E = 128, 4, 8
+    w = inputs.omega_for_ppw(n, 10.0)
+    m = inputs.gaussian_disk_medium(n)
+    s = binding.Solver(cuda(m), w, layers=L, ext=E, precision=prec)
+    s.ls_factor()
+    nb = 4
+    g = _fields(n, nb, 7)
+    v = s.ls_precond_bd_batch(g)
+    for b in range(nb):
+        assert rel(v[b], s.ls_precond_bd(g[b].contiguous())) < (1e-13 if prec == binding.LS_FP64 else 1e-6)
+    s.close()
+
+
+def test_batched_bd_rejects_oversized_batches():
+    n = 32
+    s64 = binding.Solver(cuda(inputs.gaussian_disk_medium(n)), 2 * math.pi * 4, layers=2, ext=4)
+    s64.ls_factor()
+    with pytest.raises(binding.LSError) as e:
+        s64.ls_precond_bd_batch(_fields(n, 5, 0))  # FP64 takes at most 4
+    assert e.value.code == -1
+    s64.close()
+    smx = binding.Solver(cuda(inputs.gaussian_disk_medium(n)), 2 * math.pi * 4, layers=2, ext=4,
+                         precision=binding.LS_MIXED)
+    smx.ls_factor()
+    with pytest.raises(binding.LSError) as e:
+        smx.ls_precond_bd_batch(_fields(n, 9, 0))
+    assert e.value.code == -1
+    smx.close()
+
+
+@pytest.mark.parametrize("prec", [binding.LS_FP64, binding.LS_MIXED])
+def test_batched_solve_matches_single_solves_and_oracle(prec):
+    n, L, E = 64, 4, 8
+    w = 2 * math.pi * 8
+    m = inputs.bump_medium(n, nbumps=6, seed=21)
+    s = binding.Solver(cuda(m), w, layers=L, ext=E, precision=prec)
+    s.ls_factor()
+    thetas = [0.0, 0.7, 2.1, 4.4, 5.9]
+    f = torch.stack([s.ls_incident_rhs(t) for t in thetas]).contiguous()
+    tol = 1e-10
+    u, st, rc = s.ls_solve_batch(f, tol)
+    assert rc == 0
+    assert st["true_rel_residual"] <= tol
+    outer = 0
+    for b, t in enumerate(thetas):
+        ub, stb, _ = s.ls_solve(f[b].contiguous(), tol)
+        outer += stb["outer_iters"]
+        assert rel(u[b], ub) < 1e-9, (b, rel(u[b], ub))
+    assert st["outer_iters"] == outer  # the same iterates, member by member
+    prob = osolver.Problem(m, w, L=L, E=E)
+    for b in (0, 3):
+        u_ref, _ = osolver.solve(prob, prob.rhs(thetas[b]), tol=1e-12)
+        assert rel(u[b].cpu(), torch.from_numpy(u_ref)) < 1e-6
+    s.close()
+
+
+def test_batched_solve_with_a_zero_member_and_ragged_size():
+    n, L, E = 48, 3, 4
+    w = inputs.omega_for_ppw(n, 8.0)
+    m = inputs.bump_medium(n, nbumps=8, seed=11)
+    s = binding.Solver(cuda(m), w, layers=L, ext=E, precision=binding.LS_MIXED)
+    s.ls_factor()
+    f = torch.stack([s.ls_incident_rhs(0.4), torch.zeros((n, n), dtype=torch.complex128, device="cuda"),
+                     s.ls_incident_rhs(3.0)]).contiguous()
+    u = torch.full_like(f, 5.0)
+    u, st, rc = s.ls_solve_batch(f, 1e-8, u)
+    assert rc == 0
+    assert not u[1].abs().max().item()
+    for b in (0, 2):
+        ub, _, _ = s.ls_solve(f[b].contiguous(), 1e-8)
+        assert rel(u[b], ub) < 1e-7
+    s.close()
+
+
+def test_batched_solve_rejects_nan_and_bad_counts():
+    n = 32
+    s = binding.Solver(cuda(inputs.gaussian_disk_medium(n)), 2 * math.pi * 4, layers=2, ext=4)
+    s.ls_factor()
+    f = torch.stack([s.ls_incident_rhs(0.0), s.ls_incident_rhs(1.0)]).contiguous()
+    f[1, 3, 3] = float("nan")
+    _, _, rc = s.ls_solve_batch(f, 1e-8, check=False)
+    assert rc == -6
+    u = torch.empty_like(f)
+    lib = binding.load()
+    rc = lib.ls_solve_batch(s._h, 0, binding._ptr(f), 1e-8, binding._ptr(u), 0, None)
+    assert rc == -1
+    rc = lib.ls_solve_batch(s._h, binding.LS_MAX_BATCH + 1, binding._ptr(f), 1e-8, binding._ptr(u), 0, None)
+    assert rc == -1
+    s.close()

@@ -66,11 +66,29 @@ def test_ls_apply_fp32_and_incident_rhs(n, L, E, ppw):
     s = binding.Solver(cuda(m), w, layers=L, ext=E)
     u = inputs.random_field(n, 9)
     y32 = s.ls_apply_f32(cuda(u.astype(np.complex64))).cpu().numpy()
-    assert rel(y32, greens.apply_H(u, m, 1.0 / n, w)) < 2e-5
+    y_ref = greens.apply_H(u, m, 1.0 / n, w)
+    assert rel(y32, y_ref) < 2e-5
+    ymx = s.ls_apply_mixed(cuda(u)).cpu().numpy()   # FP64 I/O, FP32 arithmetic
+    assert rel(ymx, y_ref) < 2e-5
     th = 0.37
     f = s.ls_incident_rhs(th).cpu().numpy()
     f_ref = greens.rhs(m, 1.0 / n, w, greens.incident_plane_wave(n, w, th))
     assert rel(f, f_ref) < 1e-11
+    s.close()
+
+
+# every length of the radix-16 FP32 path (P = 256 .. 2048), with ragged n (P > 2n - 1)
+@pytest.mark.parametrize("n,L", [(100, 4), (129, 3), (200, 4), (300, 6), (520, 8), (1000, 10)])
+def test_fp32_apply_every_transform_length(n, L):
+    w = inputs.omega_for_ppw(n, 10.0)
+    m = inputs.bump_medium(n, nbumps=6, seed=n + 1)
+    s = binding.Solver(cuda(m), w, layers=L, ext=3, precision=binding.LS_MIXED)
+    u = inputs.random_field(n, 4)
+    y_ref = greens.apply_H(u, m, 1.0 / n, w)
+    y32 = s.ls_apply_f32(cuda(u.astype(np.complex64))).cpu().numpy()
+    ymx = s.ls_apply_mixed(cuda(u)).cpu().numpy()
+    assert rel(y32, y_ref) < 2e-5
+    assert rel(ymx, y_ref) < 2e-5
     s.close()
 
 
