@@ -5,11 +5,14 @@ per wavelength), medium = 20 seeded Gaussian bumps in a disk of radius 0.4
 (seed 0), 32 layers per direction extended by 10 rows, mixed precision
 (FP32 complex FFT convolution and local solves, FP64 factorisation, Arnoldi
 and residual, FP64 iterative refinement), relative residual tolerance 1e-6.
-A step is one full solve of one incident plane wave: the right-hand side
-f = -w^2 G (m u_I) is generated on the device and the outer flexible GMRES,
+A step is one full solve of a batch of B incident plane waves (default 8; the
+paper solves 64 incident waves per medium): the right-hand sides
+f = -w^2 G (m u_I) are generated on the device and the outer flexible GMRES,
 preconditioned by Algorithm 3 (inner GMRES + Algorithm 2 sweeps), runs to the
-tolerance.  The off-line stage (setup + factorisation of the 64 layered local
-matrices) runs before the timed region and is reported separately.
+tolerance for every member, the members in lockstep sharing each Algorithm 2
+application.  The value is seconds per right-hand side.  The off-line stage
+(setup, factorisation of the 64 layered local matrices, the autotuner) runs
+before the timed region and is reported separately.
 
 Lines printed: one JSON line (rank 0).  --impl reference times the FP64 oracle
 on the host cores on a bounded sample of the same workload instead.
@@ -31,7 +34,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "solve s/RHS to 1e-6 rel. residual at 2048^2; LS-apply % of HBM roofline"
 N_DEFAULT, PPW_W, LAYERS, EXT, TOL = 2048, 200, 32, 10, 1e-6
-BATCH_DEFAULT = 1
+BATCH_DEFAULT = 8  # the paper solves 64 incident waves per medium: 8 batches of 8
 
 
 def parse():
@@ -54,6 +57,16 @@ def parse():
     ap.add_argument("--no-graphs", action="store_true",
                     help="launch Algorithm 2 kernel by kernel instead of replaying its CUDA graph (same arithmetic; "
                          "for profilers that cannot follow graph replay)")
+    ap.add_argument("--uneven", action="store_true",
+                    help="uneven batch: 32 independent problems, n drawn from {256, 512, 768, 1024} at 10 ppw "
+                         "(seeds 0..31), mixed precision, solved concurrently by ls_solve_group vs one by one")
+    ap.add_argument("--uneven-count", type=int, default=32)
+    ap.add_argument("--learned", action="store_true",
+                    help="learned preconditioner step: train the BF16 U-Net (4 levels, 32 base channels) on "
+                         "residual->correction pairs of the plain solver over seeded 512^2 bump media, then solve "
+                         "the 2048^2 workload with and without it")
+    ap.add_argument("--learned-media", type=int, default=100)
+    ap.add_argument("--learned-steps", type=int, default=1500)
     ap.add_argument("--table1", action="store_true",
                     help="Table 1 analogue: sparsified system C u = A f solved by GMRES (tol 1e-6) preconditioned "
                          "by Algorithm 1 (one direction) or Algorithm 2, +/- Gaussian perturbation, 10 ppw, L = n/50")
@@ -269,13 +282,19 @@ def run_ours(args):
     t0 = time.perf_counter()
     o = binding.default_opts()
     o.use_graphs = 0 if args.no_graphs else 1
+    prec = binding.LS_FP64 if args.fp64 else binding.LS_MIXED
+    if args.fp64 and args.batch > 4:
+        raise SystemExit("--fp64 takes batches of at most 4")
     s = binding.Solver(torch.from_numpy(m), wl["omega"], layers=wl["layers"], ext=wl["ext"],
-                       precision=binding.LS_MIXED, opts=o)
+                       precision=prec, opts=o)
     t_setup = time.perf_counter() - t0
     t0 = time.perf_counter()
     s.ls_factor()
     torch.cuda.synchronize()
     t_factor = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    tune = s.ls_autotune(nrhs=args.batch, reps=2)
+    t_tune = time.perf_counter() - t0
     base = inputs.seeded_angle(0)
     B = args.batch
     f = torch.empty((B, n, n), dtype=torch.complex128, device="cuda")
@@ -300,12 +319,14 @@ def run_ours(args):
         dist.barrier()
     torch.cuda.synchronize()
     clocks.start()
+    torch.cuda.nvtx.range_push("timed")  # lets a profiler restrict itself to the timed steps
     ev0.record(stream)
     stats = []
     for k in range(args.steps):
         stats.append(step(args.warmup + k))
     ev1.record(stream)
     torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
     clk = clocks.stop()
     if world > 1:
         dist.barrier()
@@ -352,25 +373,28 @@ def run_ours(args):
         # pass 1 reads u (16 n^2) and m (4 n^2), writes n x P FP32 (16 n^2); pass 2 reads and
         # writes it (32 n^2) and reads the Ghat quadrant (8 n^2); pass 3 reads it (16 n^2) and
         # u (16 n^2) and writes y (16 n^2): 124 n^2 bytes.
-        bytes_apply = 124.0 * n * n
+        bytes_apply = (200.0 if args.fp64 else 124.0) * n * n   # FP64: 16 + 8 + 32 + 32 + 16 + 32 + 32 + 32 n^2
         ach = bytes_apply / (t_app / n_app / 1e3) / 1e9 if n_app else None
         outer = statistics.mean(st["outer_iters"] for st in stats) / B  # per right-hand side
         inner = statistics.mean(st["inner_iters_total"] for st in stats) / B
         value = ms / 1e3 / (args.steps * B * world)
         out = {"metric": METRIC, "value": value, "unit": "s/RHS", "n_gpus": world, "steps": args.steps,
                "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": False,
-               "scaling": "weak", "vs_baseline": None, "dtype": "mixed c64/c128", "data": "synthetic",
-               "config": config_dict(wl, rhs_per_step=B),
+               "scaling": "weak", "vs_baseline": None, "dtype": "c128" if args.fp64 else "mixed c64/c128",
+               "data": "synthetic",
+               "config": config_dict(wl, "fp64" if args.fp64 else "mixed", rhs_per_step=B),
                "roofline": {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
                             "frac": (ach / hbm) if ach else None, "traffic": None,
-                            "kernel": "LS-apply (3 FFT passes), FP32 arithmetic, FP64 I/O",
+                            "kernel": "LS-apply (3 FFT passes), " + ("FP64" if args.fp64 else
+                                                                      "FP32 arithmetic, FP64 I/O"),
                             "algorithmic_bytes": bytes_apply, "peak_source": src,
                             "launches": n_app, "avg_ms": t_app / n_app if n_app else None},
                "clocks": clk,
                "e2e": {"value": e2e, "unit": "s/RHS", "h2d_bytes_per_step": 16 * n * n * B,
                        "d2h_bytes_per_step": 16 * n * n * B},
                "gpu_launches": int(sum(st["kernel_launches"] for st in stats)),
-               "offline_s": {"setup": t_setup, "factor": t_factor},
+               "offline_s": {"setup": t_setup, "factor": t_factor, "autotune": t_tune},
+               "autotune": tune,
                "factor_roofline": factor_roof,
                "iterations": {"outer": outer, "inner_total": inner,
                               "refine_steps": statistics.mean(st["refine_steps"] for st in stats),
@@ -401,6 +425,9 @@ def run_component(args):
     o.use_graphs = 0 if args.no_graphs else 1
     s = binding.Solver(torch.from_numpy(m), wl["omega"], layers=wl["layers"], ext=wl["ext"], precision=prec, opts=o)
     stream = s.stream
+    tune = None
+    if args.apply_only and not args.fp64:
+        tune = s.ls_autotune(nrhs=1, reps=5)
     if args.apply_only:
         if args.fp64:
             x = torch.from_numpy(inputs.random_field(n, 0)).cuda()
@@ -432,6 +459,8 @@ def run_component(args):
     out = {"component": kind, "n": n, "ms": ms, "launches_per_call": (s.ls_kernel_count() - k0) / args.steps}
     if args.sweep_only:
         out["ms_per_field"] = ms / args.batch
+    if tune:
+        out["autotune"] = tune
     if nbytes:
         out["achieved_gbs"] = nbytes / (ms / 1e3) / 1e9
         out["frac_hbm"] = out["achieved_gbs"] / hbm
@@ -489,8 +518,97 @@ def run_table1(args):
     return 0
 
 
+def run_uneven(args):
+    """Independent problems of uneven size (n ~ U{256, 512, 768, 1024}, w = 2 pi n / 10.24,
+    20-bump media with seeds 0..K-1, L = n / 64 layers extended by 10, mixed precision,
+    tol 1e-6, one plane wave each at a seeded angle): the off-line stage for all, then
+    (a) the problems one after another and (b) all at once through ls_solve_group,
+    each handle on its own stream.  Timed on the host clock around each leg, after a
+    synchronisation; one JSON line."""
+    import numpy as np
+    import torch
+    from paper_1602_07652_gb300 import binding, inputs
+    binding.load()
+    rng = np.random.default_rng(2024)
+    K = args.uneven_count
+    sizes = [int(x) for x in rng.choice([256, 512, 768, 1024], size=K)]
+    solvers, fs = [], []
+    t0 = time.perf_counter()
+    for k, n in enumerate(sizes):
+        m = inputs.bump_medium(n, nbumps=20, seed=k)
+        w = 2 * math.pi * n / 10.24
+        s = binding.Solver(torch.from_numpy(m), w, layers=n // 64, ext=10, precision=binding.LS_MIXED,
+                           stream=torch.cuda.Stream())
+        s.ls_factor()
+        solvers.append(s)
+        fs.append(s.ls_incident_rhs(inputs.seeded_angle(k)))
+    torch.cuda.synchronize()
+    t_off = time.perf_counter() - t0
+    # warm-up: one group solve (allocates the Krylov spaces and captures the graphs)
+    binding.solve_group(solvers, fs, TOL)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    seq_stats = []
+    for s, f in zip(solvers, fs):
+        _, st, _ = s.ls_solve(f, TOL)
+        seq_stats.append(st)
+    torch.cuda.synchronize()
+    t_seq = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    _, gst, status = binding.solve_group(solvers, fs, TOL)
+    torch.cuda.synchronize()
+    t_grp = time.perf_counter() - t0
+    out = {"uneven_batch": K, "sizes": {str(n): sizes.count(n) for n in (256, 512, 768, 1024)},
+           "unit": "s/RHS", "one_by_one": t_seq / K, "group": t_grp / K, "speedup": t_seq / t_grp,
+           "status": sorted(set(status)), "offline_s": t_off,
+           "true_rel_residual_max": max(st["true_rel_residual"] for st in gst),
+           "outer_iters_avg": statistics.mean(st["outer_iters"] for st in gst)}
+    print(json.dumps(out), flush=True)
+    for s in solvers:
+        s.close()
+    return 0
+
+
+def run_learned(args):
+    """Train the learned step on 512^2 media (seeds 1000..), then compare solves of the
+    benchmark workload (2048^2 unless --n) with and without it.  One JSON line."""
+    import torch
+    from paper_1602_07652_gb300 import binding, learned
+    binding.load()
+    t0 = time.perf_counter()
+    data = learned.make_dataset(512, seeds=range(1000, 1000 + args.learned_media))
+    held = learned.make_dataset(512, seeds=range(3000, 3004))
+    t_data = time.perf_counter() - t0
+    net = binding.Net(levels=4, c0=32, max_batch=4, H=512, W=512, train=True, seed=0)
+    err0 = learned.correction_error(net, held)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    losses = learned.train(net, data, steps=args.learned_steps, batch=4, lr=1e-3, seed=0)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    err1 = learned.correction_error(net, held)
+    params = net.get_params()
+    net.close()
+    n = args.n
+    inf = binding.Net(levels=4, c0=32, max_batch=1, H=n, W=n, train=False)
+    inf.set_params(params)
+    cmp = learned.compare_solves(inf, n, seeds=[0], tol=TOL)
+    out = {"learned": "BF16 U-Net, 4 levels, c0 32, 3x3 convs, WMMA tensor cores", "train_size": 512,
+           "pairs": int(data[0].shape[0]), "steps": args.learned_steps, "batch": 4,
+           "data_s": t_data, "train_s": t_train, "loss_first": losses[0], "loss_last": losses[-1],
+           "heldout_correction_err": {"untrained": err0, "trained": err1},
+           "eval_n": n, "eval": cmp}
+    print(json.dumps(out), flush=True)
+    inf.close()
+    return 0
+
+
 def main():
     args = parse()
+    if args.learned:
+        return run_learned(args)
+    if args.uneven:
+        return run_uneven(args)
     if args.table1:
         return run_table1(args)
     if args.impl == "reference":

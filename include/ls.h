@@ -93,6 +93,7 @@ typedef struct {
     double t_sweep_ms;       /* total device time of Algorithm 2 applications (if timing)   */
     int n_sweep;             /* Algorithm 2 applications counted in t_sweep_ms               */
     long long kernel_launches; /* kernels this library launched during the call            */
+    int learned_steps;     /* outer steps that used the attached network (ls_set_learned)   */
 } ls_stats;
 
 typedef struct ls_handle ls_handle;
@@ -168,6 +169,76 @@ int ls_solve_batch(ls_handle* h, int nrhs, const ls_c64* f, double tol, ls_c64* 
  * inside the call. */
 int ls_solve_batch_host(ls_handle* h, int nrhs, const ls_c64* f_host, double tol, ls_c64* u_host,
                         ls_stats* stats);
+
+/* ls_solve_group -- nprob INDEPENDENT problems (distinct handles, each set up and
+ * factored for its own medium and grid size), one right-hand side each, solved
+ * concurrently: up to LS_GROUP_WORKERS host threads take the problems in turn
+ * and run ls_solve(hs[i], f[i], tol, u[i]) on handle i's stream.  For the GPU
+ * to overlap the problems the handles must have been set up on distinct
+ * streams (on one shared stream the solves serialise, with the same results).
+ * Each u[i] is exactly what ls_solve gives for that handle.
+ *   hs, f, u: arrays of nprob pointers (f[i], u[i] device fields of hs[i]'s size);
+ *   stats, status: NULL or arrays of nprob entries (per-problem statistics and
+ *   return codes).
+ * Returns LS_OK, LS_EINVAL (a null pointer, a handle given twice), LS_ESTATE
+ * (a handle not factored; nothing is solved), else the first failing problem's code. */
+enum { LS_GROUP_WORKERS = 32 };
+int ls_solve_group(int nprob, ls_handle* const* hs, const ls_c64* const* f, double tol, ls_c64* const* u,
+                   ls_stats* stats, int* status);
+
+/* ls_autotune -- pick the two shape choices of the on-line path by timing them on
+ * this handle with incident-wave right-hand sides of its own problem:
+ *   - the FFT tile shape of the FP32 / mixed LS-apply (column pass): fft_variant
+ *     0 = radix-16 transforms on 1-column tiles, 3 CTAs per SM; 2 = radix-16 on
+ *     2-column tiles; 3 = radix-16 on 1-column tiles, 2 CTAs per SM (the radix-16
+ *     shapes need 256 <= P <= 4096); 1 = radix-8 transforms on 4-column tiles;
+ *   - the band-block batching of Algorithm 2 for nrhs right-hand sides: bd_chunk
+ *     = right-hand sides per pass over the local-solve factors (1, 2, 4, 8;
+ *     FP64 up to 4).
+ * Each candidate runs once, then reps times under CUDA events; the fastest is
+ * kept by the handle for later applies and batched solves (results agree up to
+ * rounding whichever is chosen).  Before ls_factor only the FFT shape is tuned
+ * (bd_chunk = 0 in out).  Allocates 2 * nrhs fields of scratch for the call;
+ * synchronises the stream.  out: may be NULL. */
+typedef struct {
+    int fft_variant;    /* chosen FFT tile shape                                       */
+    int bd_chunk;       /* chosen right-hand sides per Algorithm 2 pass                */
+    double fft_ms[4];   /* LS-apply (FP64 I/O, FP32 arithmetic) per variant; -1: n/a   */
+    double bd_ms[4];    /* Algorithm 2 ms per right-hand side, chunks 1, 2, 4, 8 (0: not tried) */
+} ls_tuning;
+int ls_autotune(ls_handle* h, int nrhs, int reps, ls_tuning* out);
+
+/* ---- learned preconditioner step (an addition: the paper has no network) ----
+ * A BF16 convolutional U-Net N, trained and applied by this library's own
+ * kernels (tensor-core convolutions, FP32 accumulation).  The paper's outer
+ * iteration is flexible GMRES (Sec. 6), which admits a different
+ * preconditioner at every step; with a network attached, the first direction
+ * of every outer cycle is z = s N(v / s, m) (s = RMS of v) and the others come
+ * from Algorithm 3 as before, so the plain preconditioner stays in the loop and
+ * the FP64 residual of the refinement decides convergence.
+ * Architecture: `levels` levels, c0 * 2^l channels at level l (c0 a multiple of
+ * 16), 3x3 convolutions, 2x2 average pooling, nearest 2x upsampling, skip
+ * concatenation; input (Re v / s, Im v / s, m), output 2 channels.  Fields are
+ * nb samples of H x W (x fastest), H and W multiples of 8 * 2^(levels-1).
+ * Parameters (host FP32) are in the layer order: encoder l = 0..L-1 (a, b),
+ * decoder l = L-2..0 (up, a, b), head; per layer w[o][c][3][3] then b[o]. */
+typedef struct ls_net ls_net;
+int ls_net_create(int levels, int c0, int max_batch, int H, int W, int train, unsigned long long seed,
+                  void* stream, ls_net** out);      /* max_batch * H * W pixels of buffers      */
+size_t ls_net_param_count(const ls_net* net);
+int ls_net_get_params(ls_net* net, float* host, size_t count);
+int ls_net_set_params(ls_net* net, const float* host, size_t count);   /* resets Adam          */
+/* z_b = s_b N(r_b / s_b, m_b): r, z DEVICE complex fields, m DEVICE real fields (nb each) */
+int ls_net_forward(ls_net* net, int nb, int H, int W, const ls_c64* r, const double* m, ls_c64* z);
+/* one Adam step (lr; betas 0.9, 0.999) on 0.5 mean((N(r/s, m) - e/s)^2); *loss (host) may be NULL */
+int ls_net_train_step(ls_net* net, int nb, int H, int W, const ls_c64* r, const double* m, const ls_c64* e,
+                      float lr, double* loss);
+int ls_net_get_grads(ls_net* net, float* host, size_t count);   /* of the last training step */
+long long ls_net_kernel_count(const ls_net* net);
+void ls_net_destroy(ls_net* net);
+/* attach (net != NULL) or detach the learned step of handle h's outer iteration; the
+ * network must accept the handle's n x n grid (batch 1) and outlive the attachment. */
+int ls_set_learned(ls_handle* h, ls_net* net);
 
 /* ---- operators of the inner level (Sec. 2-3), exposed for checking and reuse ---- */
 

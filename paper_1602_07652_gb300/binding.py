@@ -49,10 +49,19 @@ class Stats(ctypes.Structure):
                 ("t_apply_ms", ctypes.c_double), ("n_apply", ctypes.c_int),
                 ("t_apply64_ms", ctypes.c_double), ("n_apply64", ctypes.c_int),
                 ("t_sweep_ms", ctypes.c_double), ("n_sweep", ctypes.c_int),
-                ("kernel_launches", ctypes.c_longlong)]
+                ("kernel_launches", ctypes.c_longlong), ("learned_steps", ctypes.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class Tuning(ctypes.Structure):
+    _fields_ = [("fft_variant", ctypes.c_int), ("bd_chunk", ctypes.c_int),
+                ("fft_ms", ctypes.c_double * 4), ("bd_ms", ctypes.c_double * 4)]
+
+    def as_dict(self):
+        return {"fft_variant": self.fft_variant, "bd_chunk": self.bd_chunk,
+                "fft_ms": list(self.fft_ms), "bd_ms_per_rhs": list(self.bd_ms)}
 
 
 _P = ctypes.c_void_p
@@ -69,6 +78,9 @@ _SIGS = {
     "ls_solve_batch": (ctypes.c_int, [_P, ctypes.c_int, _P, ctypes.c_double, _P, ctypes.c_int,
                                       ctypes.POINTER(Stats)]),
     "ls_solve_batch_host": (ctypes.c_int, [_P, ctypes.c_int, _P, ctypes.c_double, _P, ctypes.POINTER(Stats)]),
+    "ls_solve_group": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.c_double,
+                                      ctypes.POINTER(_P), ctypes.POINTER(Stats), ctypes.POINTER(ctypes.c_int)]),
+    "ls_autotune": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.POINTER(Tuning)]),
     "ls_solve_host": (ctypes.c_int, [_P, _P, ctypes.c_double, _P, ctypes.POINTER(Stats)]),
     "ls_solve_plane_wave": (ctypes.c_int, [_P, ctypes.c_double, ctypes.c_double, _P, ctypes.POINTER(Stats)]),
     "ls_apply_A": (ctypes.c_int, [_P, _P, _P]),
@@ -87,6 +99,18 @@ _SIGS = {
     "ls_destroy": (None, [_P]),
     "ls_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "ls_apply_f32_noalloc": (ctypes.c_int, [ctypes.c_int, _P, _P, _P, _P, _P]),
+    "ls_net_create": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                     ctypes.c_int, ctypes.c_ulonglong, _P, ctypes.POINTER(_P)]),
+    "ls_net_param_count": (ctypes.c_size_t, [_P]),
+    "ls_net_get_params": (ctypes.c_int, [_P, _P, ctypes.c_size_t]),
+    "ls_net_set_params": (ctypes.c_int, [_P, _P, ctypes.c_size_t]),
+    "ls_net_forward": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int, _P, _P, _P]),
+    "ls_net_train_step": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int, _P, _P, _P, ctypes.c_float,
+                                         ctypes.POINTER(ctypes.c_double)]),
+    "ls_net_get_grads": (ctypes.c_int, [_P, _P, ctypes.c_size_t]),
+    "ls_net_kernel_count": (ctypes.c_longlong, [_P]),
+    "ls_net_destroy": (None, [_P]),
+    "ls_set_learned": (ctypes.c_int, [_P, _P]),
 }
 
 EXPORTED = tuple(_SIGS)
@@ -127,6 +151,85 @@ def _c128(t: torch.Tensor, n: int, where: str):
     if t.dtype != torch.complex128 or not t.is_cuda or not t.is_contiguous() or t.numel() != n:
         raise ValueError("%s: expected a contiguous CUDA complex128 tensor with %d elements" % (where, n))
     return _ptr(t)
+
+
+def solve_group(solvers, fs, tol, us=None):
+    """ls_solve_group over independent problems: solvers[i] (distinct Solver objects,
+    factored), fs[i] its right-hand side.  Returns (us, per-problem stats, statuses)."""
+    lib = load()
+    k = len(solvers)
+    us = [torch.empty_like(f) for f in fs] if us is None else us
+    hs = (_P * k)(*[s._h for s in solvers])
+    fp = (_P * k)(*[_c128(f, s.N, "ls_solve_group").value for s, f in zip(solvers, fs)])
+    up = (_P * k)(*[_c128(u, s.N, "ls_solve_group").value for s, u in zip(solvers, us)])
+    st = (Stats * k)()
+    status = (ctypes.c_int * k)()
+    rc = lib.ls_solve_group(k, hs, fp, float(tol), up, st, status)
+    if rc != 0 and rc != -5:
+        _ck(rc, "ls_solve_group")
+    return us, [x.as_dict() for x in st], list(status)
+
+
+class Net:
+    """The learned preconditioner step (ls_net_*): a BF16 U-Net on the GPU."""
+
+    def __init__(self, levels=4, c0=32, max_batch=1, H=128, W=128, train=True, seed=0,
+                 stream: torch.cuda.Stream | None = None):
+        lib = load()
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        h = ctypes.c_void_p()
+        _ck(lib.ls_net_create(int(levels), int(c0), int(max_batch), int(H), int(W), 1 if train else 0, int(seed),
+                              ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(h)), "ls_net_create")
+        self._h, self._lib, self.levels, self.c0 = h, lib, levels, c0
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.ls_net_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def param_count(self):
+        return int(self._lib.ls_net_param_count(self._h))
+
+    def get_params(self):
+        out = torch.empty(self.param_count(), dtype=torch.float32)
+        _ck(self._lib.ls_net_get_params(self._h, _ptr(out), out.numel()), "ls_net_get_params")
+        return out
+
+    def set_params(self, flat):
+        flat = flat.to(torch.float32).contiguous().cpu()
+        _ck(self._lib.ls_net_set_params(self._h, _ptr(flat), flat.numel()), "ls_net_set_params")
+
+    def get_grads(self):
+        out = torch.empty(self.param_count(), dtype=torch.float32)
+        _ck(self._lib.ls_net_get_grads(self._h, _ptr(out), out.numel()), "ls_net_get_grads")
+        return out
+
+    @staticmethod
+    def _check(r, m, e=None):
+        nb, H, W = r.shape
+        for t, dt in ((r, torch.complex128), (m, torch.float64)) + (((e, torch.complex128),) if e is not None else ()):
+            if t.dtype != dt or not t.is_cuda or not t.is_contiguous() or tuple(t.shape) != (nb, H, W):
+                raise ValueError("ls_net: expected contiguous CUDA tensors of shape (nb, H, W)")
+        return nb, H, W
+
+    def forward(self, r, m, z=None):
+        nb, H, W = self._check(r, m)
+        z = torch.empty_like(r) if z is None else z
+        _ck(self._lib.ls_net_forward(self._h, nb, H, W, _ptr(r), _ptr(m), _ptr(z)), "ls_net_forward")
+        return z
+
+    def train_step(self, r, m, e, lr):
+        nb, H, W = self._check(r, m, e)
+        loss = ctypes.c_double()
+        _ck(self._lib.ls_net_train_step(self._h, nb, H, W, _ptr(r), _ptr(m), _ptr(e), float(lr), ctypes.byref(loss)),
+            "ls_net_train_step")
+        return loss.value
 
 
 def default_opts() -> Opts:
@@ -243,6 +346,14 @@ class Solver:
         if check:
             _ck(rc, "ls_solve_batch")
         return u, st.as_dict(), rc
+
+    def ls_set_learned(self, net):
+        _ck(self._lib.ls_set_learned(self._h, net._h if net is not None else None), "ls_set_learned")
+
+    def ls_autotune(self, nrhs=1, reps=3):
+        t = Tuning()
+        _ck(self._lib.ls_autotune(self._h, int(nrhs), int(reps), ctypes.byref(t)), "ls_autotune")
+        return t.as_dict()
 
     def ls_solve_host(self, f_host, tol, u_host):
         """f_host, u_host: CPU complex128 tensors (pinned or pageable)."""

@@ -4,7 +4,11 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <algorithm>
+#include <atomic>
 #include <new>
+#include <thread>
+#include <vector>
 
 #include "ls_internal.cuh"
 
@@ -26,18 +30,13 @@ struct HostBufs {
     double2* u = nullptr;  // device staging for host solutions
     int cap = 0;           // fields each buffer holds
 };
-HostBufs g_hostbufs[64];
-
 HostBufs* host_bufs(ls_handle* h, bool create) {
-    for (auto& b : g_hostbufs)
-        if (b.h == h) return &b;
-    if (!create) return nullptr;
-    for (auto& b : g_hostbufs)
-        if (!b.h) {
-            b.h = h;
-            return &b;
-        }
-    return nullptr;
+    if (!h->hostbufs && create) {
+        HostBufs* b = new HostBufs();
+        b->h = h;
+        h->hostbufs = b;
+    }
+    return static_cast<HostBufs*>(h->hostbufs);
 }
 
 // Staging buffers for nb fields (grown on demand).
@@ -66,7 +65,8 @@ void release(ls_handle* h) {
     if (HostBufs* b = host_bufs(h, false)) {
         cudaFree(b->f);
         cudaFree(b->u);
-        *b = HostBufs{};
+        delete b;
+        h->hostbufs = nullptr;
     }
     void* ptrs[] = {h->m64, h->m32, h->mT64, h->ghat64, h->ghat32, h->tw64, h->tw32, h->fftws, h->incx,
                     h->incz, h->dtabs, h->srhs, h->ssol, h->strace, h->vtmp, h->vtmp2, h->red, h->bd_in, h->bd_out};
@@ -283,6 +283,7 @@ int ls_solve_batch(ls_handle* h, int nrhs, const ls_c64* f, double tol, ls_c64* 
     std::memset(s, 0, sizeof(*s));
     h->t_apply_ms = h->t_sweep_ms = h->t_apply64_ms = 0;
     h->n_apply = h->n_sweep = h->n_apply64 = 0;
+    h->learned_steps = 0;
     const long long l0 = h->launches;
     const auto t0 = std::chrono::steady_clock::now();
     h->tused = 0;
@@ -299,7 +300,14 @@ int ls_solve_batch(ls_handle* h, int nrhs, const ls_c64* f, double tol, ls_c64* 
     s->t_sweep_ms = h->t_sweep_ms;
     s->n_sweep = h->n_sweep;
     s->kernel_launches = h->launches - l0;
+    s->learned_steps = h->learned_steps;
     return rc;
+}
+
+int ls_set_learned(ls_handle* h, ls_net* net) {
+    if (!h) return LS_EINVAL;
+    h->net = net;
+    return LS_OK;
 }
 
 int ls_solve(ls_handle* h, const ls_c64* f, double tol, ls_c64* u, int use_x0, ls_stats* st) {
@@ -332,6 +340,45 @@ int ls_solve_batch_host(ls_handle* h, int nrhs, const ls_c64* f_host, double tol
     LS_CUDA(cudaMemcpyAsync(u_host, b->u, bytes, cudaMemcpyDeviceToHost, h->stream));
     LS_CUDA(cudaStreamSynchronize(h->stream));
     return rc;
+}
+
+// Independent problems solved concurrently: a pool of host workers takes the
+// problems in turn; each solve runs on its own handle's stream, so the GPU
+// overlaps the problems' kernels (small grids leave most SMs idle on their own).
+int ls_solve_group(int nprob, ls_handle* const* hs, const ls_c64* const* f, double tol, ls_c64* const* u,
+                   ls_stats* stats, int* status) {
+    if (nprob < 1 || !hs || !f || !u || !(tol > 0)) return LS_EINVAL;
+    for (int i = 0; i < nprob; ++i) {
+        if (!hs[i] || !f[i] || !u[i]) return LS_EINVAL;
+        for (int k = 0; k < i; ++k)
+            if (hs[k] == hs[i]) return LS_EINVAL;  // a handle serves one thread at a time
+    }
+    for (int i = 0; i < nprob; ++i)
+        if (!hs[i]->factored) return LS_ESTATE;
+    std::vector<int> rc(nprob, LS_OK);
+    std::atomic<int> next{0};
+    auto worker = [&]() {
+        for (;;) {
+            const int i = next.fetch_add(1);
+            if (i >= nprob) return;
+            if (cudaSetDevice(hs[i]->device) != cudaSuccess) {
+                rc[i] = LS_ECUDA;
+                continue;
+            }
+            rc[i] = ls_solve(hs[i], f[i], tol, u[i], 0, stats ? &stats[i] : nullptr);
+        }
+    };
+    const int nw = std::min(nprob, (int)LS_GROUP_WORKERS);
+    std::vector<std::thread> pool;
+    pool.reserve(nw);
+    for (int w = 0; w < nw; ++w) pool.emplace_back(worker);
+    for (auto& t : pool) t.join();
+    int out = LS_OK;
+    for (int i = 0; i < nprob; ++i) {
+        if (status) status[i] = rc[i];
+        if (out == LS_OK && rc[i] != LS_OK) out = rc[i];
+    }
+    return out;
 }
 
 int ls_solve_host(ls_handle* h, const ls_c64* f_host, double tol, ls_c64* u_host, ls_stats* st) {

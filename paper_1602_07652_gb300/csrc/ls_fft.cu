@@ -467,7 +467,7 @@ int ls_apply64(ls_handle* h, const double2* u, double2* y) {
 }
 
 int ls_apply32(ls_handle* h, const float2* u, float2* y) {
-    if (ls_fft16_supported(h)) return ls_apply32_fft16(h, u, y);
+    if (h->fft_variant != 1 && ls_fft16_supported(h)) return ls_apply32_fft16(h, u, y, h->fft_variant);
     const int n = h->n, P = h->P;
     const FftPlan& pl = h->plan32;
     float2* X = static_cast<float2*>(h->fftws);
@@ -483,7 +483,7 @@ int ls_apply32(ls_handle* h, const float2* u, float2* y) {
 }
 
 int ls_apply_mx(ls_handle* h, const double2* u, double2* y) {
-    if (ls_fft16_supported(h)) return ls_apply_mx_fft16(h, u, y);
+    if (h->fft_variant != 1 && ls_fft16_supported(h)) return ls_apply_mx_fft16(h, u, y, h->fft_variant);
     const int n = h->n, P = h->P;
     const FftPlan& pl = h->plan32;
     float2* X = static_cast<float2*>(h->fftws);

@@ -31,6 +31,24 @@ struct Geo {
 
 __device__ __forceinline__ int pad16(int i) { return i + (i >> 4); }
 
+// Asynchronous global -> shared copies (sm_80+ cp.async): the data lands in shared
+// memory without passing through registers, while the thread carries on.
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
+    const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+    const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+template <typename V>
+__device__ __forceinline__ void cp_async_el(V* smem, const V* gmem) {
+    if constexpr (sizeof(V) == 16) cp_async16(smem, gmem);
+    else cp_async8(smem, gmem);
+}
+
 template <int DIR>
 __device__ __forceinline__ float2 ld_tw(const float2* __restrict__ tw, int m) {
     float2 w = __ldg(&tw[m]);
@@ -187,65 +205,85 @@ __global__ void __launch_bounds__(256) k_rows16_fwd(int nrows, int nin, Src src,
         for (int r = 0; r < R; ++r) o[j + e * T + r * (P / R)] = v[0][e * R + r];
 }
 
-// Pass 2: for the 2-column tile (kx0, kx0 + 1): forward z-FFT (rows >= nin are
-// zero), times Ghat, inverse z-FFT; rows z < nout written back in place.
-// Consecutive tiles pair kx with P - kx, so the second read of a Ghat quadrant
-// row finds it in L2.
-template <int LP>
-__global__ void __launch_bounds__(256, 2) k_cols16(int nin, int nout, float2* __restrict__ X,
-                                                  const float2* __restrict__ ghat, const float2* __restrict__ tw) {
+// Pass 2: for a tile of CW adjacent columns (1 or 2): forward z-FFT (rows >= nin
+// are zero), times Ghat, inverse z-FFT; rows z < nout written back in place.
+// The tile's Ghat quadrant rows are copied to shared memory asynchronously at
+// the start, behind the forward transform.  Tiles are ordered so that kx and
+// P - kx (the same quadrant row) run close together and share it in L2.
+// MINB: CTAs per SM the register allocation must allow (3 spills a little at P = 4096).
+template <int LP, int CW, int MINB>
+__global__ void __launch_bounds__(256, MINB) k_cols16(int nin, int nout, float2* __restrict__ X,
+                                                              const float2* __restrict__ ghat,
+                                                              const float2* __restrict__ tw) {
     using Gm = Geo<LP>;
-    constexpr int P = Gm::P, T = Gm::T, R = 1 << Gm::LRL;
+    using EL = typename Elem<CW>::T;
+    constexpr int P = Gm::P, T = Gm::T, R = 1 << Gm::LRL, Q = P / 2 + 1;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int grp = threadIdx.x / T, j = threadIdx.x % T;
-    float4* buf = reinterpret_cast<float4*>(smem_raw) + grp * Gm::SLOTS;
-    constexpr int ntile = P / 2;
+    EL* buf = reinterpret_cast<EL*>(smem_raw) + grp * Gm::SLOTS;
+    float2* gs = reinterpret_cast<float2*>(smem_raw + sizeof(EL) * Gm::G * Gm::SLOTS) + grp * CW * Q;
+    constexpr int ntile = P / CW;
     const int lin = blockIdx.x * Gm::G + grp;
     const int tile = (lin & 1) ? (ntile - 1 - (lin >> 1)) : (lin >> 1);
-    const int kx0 = 2 * tile;
-    float2 v[2][16];
+    const int kx0 = CW * tile;
+#pragma unroll
+    for (int c = 0; c < CW; ++c) {
+        const int kx = kx0 + c;
+        const float2* g = ghat + (size_t)(kx <= P / 2 ? kx : P - kx) * Q;
+        for (int i = j; i < Q; i += T) cp_async8(gs + c * Q + i, g + i);
+    }
+    cp_async_commit();
+    float2 v[CW][16];
 #pragma unroll
     for (int t = 0; t < 8; ++t) {
         const int z = j + t * T;
-        float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (z < nin) a = *reinterpret_cast<const float4*>(X + (size_t)z * P + kx0);
-        v[0][t] = make_float2(a.x, a.y);
-        v[1][t] = make_float2(a.z, a.w);
+        EL a{};
+        if (z < nin) a = *reinterpret_cast<const EL*>(X + (size_t)z * P + kx0);
+        Elem<CW>::unpack(a, v, t);
     }
     fft_fwd<LP, true>(v, buf, j, tw);
+    cp_async_wait_all();
+    __syncthreads();  // every thread's share of the Ghat rows has landed
 #pragma unroll
-    for (int c = 0; c < 2; ++c) {
-        const int kx = kx0 + c;
-        const float2* g = ghat + (size_t)(kx <= P / 2 ? kx : P - kx) * (P / 2 + 1);
+    for (int c = 0; c < CW; ++c)
 #pragma unroll
         for (int e = 0; e < 16 / R; ++e)
 #pragma unroll
             for (int r = 0; r < R; ++r) {
                 const int kz = j + e * T + r * (P / R);
-                v[c][e * R + r] = v[c][e * R + r] * __ldg(&g[kz <= P / 2 ? kz : P - kz]);
+                v[c][e * R + r] = v[c][e * R + r] * gs[c * Q + (kz <= P / 2 ? kz : P - kz)];
             }
-    }
     fft_inv<LP, false>(v, buf, j, tw);
 #pragma unroll
     for (int t = 0; t < 16; ++t) {
         const int z = j + t * T;
-        if (z < nout)
-            *reinterpret_cast<float4*>(X + (size_t)z * P + kx0) =
-                make_float4(v[0][t].x, v[0][t].y, v[1][t].x, v[1][t].y);
+        if (z < nout) *reinterpret_cast<EL*>(X + (size_t)z * P + kx0) = Elem<CW>::pack(v, t);
     }
 }
 
-// Pass 3: y[z, x] = u[z, x] + IFFT_x(X[z, :])[x] for x < n.
-template <int LP, class Dst>
-__global__ void __launch_bounds__(256) k_rows16_inv(int nrows, int n, const float2* __restrict__ X, Dst dst,
+// Pass 3: y[z, x] = u[z, x] + IFFT_x(X[z, :])[x] for x < n.  The row of u is copied
+// to shared memory asynchronously at the start (each thread fetches the elements
+// it will write), so its latency hides behind the inverse transform.
+template <int LP, typename UIO>
+__global__ void __launch_bounds__(256) k_rows16_inv(int nrows, int n, const float2* __restrict__ X,
+                                                   const UIO* __restrict__ u, UIO* __restrict__ y,
                                                    const float2* __restrict__ tw) {
     using Gm = Geo<LP>;
     constexpr int P = Gm::P, T = Gm::T, R = 1 << Gm::LRL;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int grp = threadIdx.x / T, j = threadIdx.x % T;
     float2* buf = reinterpret_cast<float2*>(smem_raw) + grp * Gm::SLOTS;
+    UIO* us = reinterpret_cast<UIO*>(smem_raw + sizeof(float2) * Gm::G * Gm::SLOTS) + grp * (P / 2);
     const int z = blockIdx.x * Gm::G + grp;
     const bool live = z < nrows;
+    if (live) {
+#pragma unroll
+        for (int t = 0; t < 8; ++t) {
+            const int x = j + t * T;
+            if (x < n) cp_async_el(us + x, u + (size_t)z * n + x);
+        }
+    }
+    cp_async_commit();
     float2 v[1][16];
     const float2* xr = X + (size_t)(live ? z : 0) * P;
 #pragma unroll
@@ -253,48 +291,72 @@ __global__ void __launch_bounds__(256) k_rows16_inv(int nrows, int n, const floa
 #pragma unroll
         for (int r = 0; r < R; ++r) v[0][e * R + r] = xr[j + e * T + r * (P / R)];
     fft_inv<LP, true>(v, buf, j, tw);
+    cp_async_wait_all();  // this thread's own copies: no barrier needed
     if (!live) return;
 #pragma unroll
-    for (int t = 0; t < 16; ++t) {
+    for (int t = 0; t < 8; ++t) {
         const int x = j + t * T;
-        if (x < n) dst.template store<float2>(z, x, v[0][t]);
+        if (x < n) y[(size_t)z * n + x] = us[x] + ccast<UIO>(v[0][t]);
     }
 }
 
-// G transforms of P = 4096 / G elements, padded: 256 * 17 slots for every P
+// Shared memory: G transforms of P = 4096 / G elements padded to 256 * 17 slots for
+// every P, plus the prefetched u rows (G * P/2 elements) or Ghat rows (G * CW * (P/2 + 1)).
+template <int LP, typename UIO>
+constexpr size_t rinv_smem() { return sizeof(float2) * 256 * 17 + sizeof(UIO) * 2048; }
+template <int LP, int CW>
+constexpr size_t cols_smem() {
+    return sizeof(float2) * CW * 256 * 17 + sizeof(float2) * Geo<LP>::G * CW * ((1 << LP) / 2 + 1);
+}
 constexpr size_t row_smem16() { return sizeof(float2) * 256 * 17; }
-constexpr size_t col_smem16() { return sizeof(float4) * 256 * 17; }
 
-template <int LP, class Src, class Dst>
-int apply_lp(ls_handle* h, Src src, Dst dst, float2* X) {
+// Column-pass tile shapes: 0 = 1 column, 3 CTAs/SM; 2 = 2 columns, 2 CTAs/SM;
+// 3 = 1 column, 2 CTAs/SM.
+template <int LP, typename UIO>
+int apply_lp(ls_handle* h, const UIO* u, UIO* y, float2* X, int shape) {
     using Gm = Geo<LP>;
     const int n = h->n;
     const float2* tw = static_cast<const float2*>(h->tw32);
+    const float2* gh = static_cast<const float2*>(h->ghat32);
     const unsigned rows_grid = (unsigned)((n + Gm::G - 1) / Gm::G);
-    LS_LAUNCH(h, (k_rows16_fwd<LP, Src>), rows_grid, 256, row_smem16(), n, n, src, X, tw);
-    LS_LAUNCH(h, k_cols16<LP>, (unsigned)(Gm::P / 2 / Gm::G), 256, col_smem16(), n, n, X,
-              static_cast<const float2*>(h->ghat32), tw);
-    LS_LAUNCH(h, (k_rows16_inv<LP, Dst>), rows_grid, 256, row_smem16(), n, n, X, dst, tw);
+    SrcMU<float, UIO> src{h->m32, u, n};
+    LS_LAUNCH(h, (k_rows16_fwd<LP, SrcMU<float, UIO>>), rows_grid, 256, row_smem16(), n, n, src, X, tw);
+    if (shape == 2)
+        LS_LAUNCH(h, (k_cols16<LP, 2, 2>), (unsigned)(Gm::P / 2 / Gm::G), 256, (cols_smem<LP, 2>()), n, n, X, gh, tw);
+    else if (shape == 3)
+        LS_LAUNCH(h, (k_cols16<LP, 1, 2>), (unsigned)(Gm::P / Gm::G), 256, (cols_smem<LP, 1>()), n, n, X, gh, tw);
+    else
+        LS_LAUNCH(h, (k_cols16<LP, 1, 3>), (unsigned)(Gm::P / Gm::G), 256, (cols_smem<LP, 1>()), n, n, X, gh, tw);
+    LS_LAUNCH(h, (k_rows16_inv<LP, UIO>), rows_grid, 256, (rinv_smem<LP, UIO>()), n, n, X, u, y, tw);
     return LS_OK;
 }
 
-template <class Src, class Dst>
-int apply_any(ls_handle* h, Src src, Dst dst) {
+template <typename UIO>
+int apply_any(ls_handle* h, const UIO* u, UIO* y, int shape) {
     float2* X = static_cast<float2*>(h->fftws);
     switch (h->lp) {
-        case 8: return apply_lp<8>(h, src, dst, X);
-        case 9: return apply_lp<9>(h, src, dst, X);
-        case 10: return apply_lp<10>(h, src, dst, X);
-        case 11: return apply_lp<11>(h, src, dst, X);
-        case 12: return apply_lp<12>(h, src, dst, X);
+        case 8: return apply_lp<8>(h, u, y, X, shape);
+        case 9: return apply_lp<9>(h, u, y, X, shape);
+        case 10: return apply_lp<10>(h, u, y, X, shape);
+        case 11: return apply_lp<11>(h, u, y, X, shape);
+        case 12: return apply_lp<12>(h, u, y, X, shape);
         default: return LS_EINVAL;
     }
 }
 
+template <typename K>
+int optin(K kern, size_t bytes) {
+    if (bytes > 48 * 1024) LS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+    return LS_OK;
+}
+
 template <int LP>
 int optin_lp() {
-    LS_CUDA(cudaFuncSetAttribute(k_cols16<LP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)col_smem16()));
-    return LS_OK;
+    LS_TRY(optin(k_cols16<LP, 1, 3>, cols_smem<LP, 1>()));
+    LS_TRY(optin(k_cols16<LP, 1, 2>, cols_smem<LP, 1>()));
+    LS_TRY(optin(k_cols16<LP, 2, 2>, cols_smem<LP, 2>()));
+    LS_TRY(optin(k_rows16_inv<LP, float2>, rinv_smem<LP, float2>()));
+    return optin(k_rows16_inv<LP, double2>, rinv_smem<LP, double2>());
 }
 
 }  // namespace
@@ -310,14 +372,9 @@ int ls_fft16_init(ls_handle* h) {
     return optin_lp<12>();
 }
 
-int ls_apply32_fft16(ls_handle* h, const float2* u, float2* y) {
-    SrcMU<float, float2> src{h->m32, u, h->n};
-    DstApply<float2> dst{u, y, h->n};
-    return apply_any(h, src, dst);
-}
+// shape: column-pass tile shape (0, 2, 3 as in apply_lp)
+int ls_apply32_fft16(ls_handle* h, const float2* u, float2* y, int shape) { return apply_any(h, u, y, shape); }
 
-int ls_apply_mx_fft16(ls_handle* h, const double2* u, double2* y) {
-    SrcMU<float, double2> src{h->m32, u, h->n};
-    DstApply<double2> dst{u, y, h->n};
-    return apply_any(h, src, dst);
+int ls_apply_mx_fft16(ls_handle* h, const double2* u, double2* y, int shape) {
+    return apply_any(h, u, y, shape);
 }

@@ -155,9 +155,10 @@ struct ls_handle {
     void* vtmp = nullptr;      // n*n complex scratch (FP64) for transposes
     void* vtmp2 = nullptr;
 
-    // Krylov workspaces (FP64)
-    double2* kry = nullptr;    // pool of N-vectors
-    int kry_vectors = 0;
+    // Krylov workspaces (FP64): the context of ls_krylov.cu and the staging buffers of
+    // the host-array entry points, owned by the handle (no library-global state)
+    void* krylov = nullptr;
+    void* hostbufs = nullptr;
     double* red = nullptr;     // reduction partials
     double* red_host = nullptr;
     size_t red_cap = 0;
@@ -170,6 +171,15 @@ struct ls_handle {
     double2* bd_in = nullptr;
     double2* bd_out = nullptr;
     int nb_cap = 0;
+
+    ls_net* net = nullptr;     // learned first step of every outer cycle (ls_unet.cu), or none
+    int learned_steps = 0;
+
+    // choices of the autotuner (ls_tune.cu); defaults until ls_autotune runs
+    int fft_variant = 0;       // radix-16 (256 <= P <= 4096): 0 = 1-column tiles, 3 CTAs/SM; 2 = 2-column
+                               // tiles; 3 = 1-column tiles, 2 CTAs/SM.  1: generic radix-8 4-column tiles
+    static constexpr int kFftVariants = 4;
+    int bd_chunk = 0;          // right-hand sides per batched Algorithm 2 (0: the largest supported)
 
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     double t_apply_ms = 0, t_sweep_ms = 0, t_apply64_ms = 0;
@@ -214,8 +224,8 @@ int ls_apply32(ls_handle* h, const float2* u, float2* y);       // y = H u (FP32
 int ls_apply_mx(ls_handle* h, const double2* u, double2* y);    // FP64 I/O, FP32 arithmetic
 bool ls_fft16_supported(const ls_handle* h);                     // radix-16 FP32 path: 256 <= P <= 4096
 int ls_fft16_init(ls_handle* h);
-int ls_apply32_fft16(ls_handle* h, const float2* u, float2* y);
-int ls_apply_mx_fft16(ls_handle* h, const double2* u, double2* y);
+int ls_apply32_fft16(ls_handle* h, const float2* u, float2* y, int shape);  // shape: fft_variant 0, 2, 3
+int ls_apply_mx_fft16(ls_handle* h, const double2* u, double2* y, int shape);
 int ls_rhs64(ls_handle* h, double theta, double2* f);           // f = -w^2 G (m u_I)
 
 // setup (ls_setup_kernels.cu)
@@ -253,3 +263,5 @@ int ls_strip_solve(ls_handle* h, int dir, int layer, const double2* b, double2* 
 int ls_inner_gmres(ls_handle* h, const double2* g, double tol, double2* v, int* iters);
 int ls_outer_solve(ls_handle* h, const double2* f, double tol, double2* u, int use_x0, ls_stats* st);
 int ls_outer_solve_b(ls_handle* h, int nb, const double2* f, double tol, double2* u, int use_x0, ls_stats* st);
+int ls_net_apply_field(ls_net* net, cudaStream_t stream, int H, int W, const double2* v, const double* m,
+                       double2* z);   // z = s N(v / s, m), one field

@@ -36,7 +36,7 @@ namespace {
 using cd = std::complex<double>;
 
 enum Op { OP_H64, OP_HMIX, OP_C };
-enum Pc { PC_NONE, PC_BD, PC_LS };
+enum Pc { PC_NONE, PC_BD, PC_LS, PC_NET };
 
 // Vectors of a Krylov space for up to nbcap members: direction j of member b is
 // V + (j * nbcap + b) * N, so the members' j-th directions form one contiguous
@@ -97,8 +97,12 @@ struct Result {
 int fgmres_b(ls_handle* h, Ctx* c, KrylovSpace& S, Op op, Pc pc, const double2* b, double2* x, bool x0,
              const double* tol, int maxit, int nb, const unsigned char* live, Result* res, ls_stats* st);
 
-// Right-hand sides per batched Algorithm 2 call (the FP64 sweep kernels stop at 4).
-int bd_chunk(const ls_handle* h) { return h->prec == LS_MIXED ? kMaxBatch : 4; }
+// Right-hand sides per batched Algorithm 2 call: the autotuner's choice, else the
+// largest the sweep kernels take (FP64: 4).
+int bd_chunk(const ls_handle* h) {
+    const int cap = h->prec == LS_MIXED ? kMaxBatch : 4;
+    return h->bd_chunk > 0 && h->bd_chunk < cap ? h->bd_chunk : cap;
+}
 
 // z_b = M v_b for the members with on[b]; v and z are blocks of nb vectors.
 // Members that are off have their slot of v zeroed (their z is not used).
@@ -110,6 +114,14 @@ int apply_pc_b(ls_handle* h, Pc pc, double2* v, double2* z, int nb, const unsign
     if (pc == PC_NONE) {
         for (int b = 0; b < top; ++b)
             if (on[b]) LS_TRY(ls_vec_copy(h, v + b * N, z + b * N));
+        return LS_OK;
+    }
+    if (pc == PC_NET) {  // the learned step: z = s N(v / s, m)
+        for (int b = 0; b < top; ++b)
+            if (on[b]) {
+                LS_TRY(ls_net_apply_field(h->net, h->stream, h->n, h->n, v + b * N, h->m64, z + b * N));
+                h->learned_steps++;
+            }
         return LS_OK;
     }
     if (pc == PC_BD) {
@@ -215,7 +227,9 @@ int fgmres_b(ls_handle* h, Ctx* c, KrylovSpace& S, Op op, Pc pc, const double2* 
                 inc = inc || M[i].cyc;
             }
             if (!inc) break;
-            LS_TRY(apply_pc_b(h, pc, V(j, 0), Zb(j), nb, on.data(), st));
+            // with a network attached, the outer cycle's first direction is the learned step
+            const Pc pcj = (pc == PC_LS && j == 0 && h->net) ? PC_NET : pc;
+            LS_TRY(apply_pc_b(h, pcj, V(j, 0), Zb(j), nb, on.data(), st));
             for (int i = 0; i < nb; ++i) {
                 if (!on[i]) continue;
                 double2* vn = V(j + 1, i);
@@ -310,19 +324,7 @@ int fgmres_b(ls_handle* h, Ctx* c, KrylovSpace& S, Op op, Pc pc, const double2* 
 
 // per-handle Krylov context
 namespace {
-struct CtxStore {
-    ls_handle* h;
-    Ctx* c;
-};
-std::vector<CtxStore>& ctx_list() {
-    static std::vector<CtxStore> v;
-    return v;
-}
-Ctx* ctx_of(ls_handle* h) {
-    for (auto& e : ctx_list())
-        if (e.h == h) return e.c;
-    return nullptr;
-}
+Ctx* ctx_of(ls_handle* h) { return static_cast<Ctx*>(h->krylov); }
 void free_space(KrylovSpace& S) {
     cudaFree(S.V);
     cudaFree(S.Z);
@@ -338,7 +340,7 @@ int ctx_ensure(ls_handle* h, int nb) {
     if (!c) {
         c = new Ctx();
         c->h = h;
-        ctx_list().push_back({h, c});
+        h->krylov = c;
     }
     free_space(c->outer);
     free_space(c->inner);
@@ -355,16 +357,13 @@ int ctx_ensure(ls_handle* h, int nb) {
 }  // namespace
 
 void ls_krylov_free(ls_handle* h) {
-    auto& L = ctx_list();
-    for (size_t i = 0; i < L.size(); ++i)
-        if (L[i].h == h) {
-            free_space(L[i].c->outer);
-            free_space(L[i].c->inner);
-            cudaFree(L[i].c->tmpA);
-            delete L[i].c;
-            L.erase(L.begin() + i);
-            return;
-        }
+    Ctx* c = ctx_of(h);
+    if (!c) return;
+    free_space(c->outer);
+    free_space(c->inner);
+    cudaFree(c->tmpA);
+    delete c;
+    h->krylov = nullptr;
 }
 
 int ls_inner_gmres(ls_handle* h, const double2* g, double tol, double2* v, int* iters) {

@@ -1,0 +1,109 @@
+// ls_tune.cu -- a small autotuner for the two shape choices of the on-line path.
+//
+//  * FFT tile shape of the FP32 / mixed LS-apply: radix-16 transforms with
+//    1-column tiles (3 or 2 CTAs per SM) or 2-column tiles (ls_fft16.cu), or
+//    radix-8 transforms on 4-column tiles (generic path of ls_fft.cu);
+//  * band-block batching of Algorithm 2: how many right-hand sides share one
+//    pass over the local-solve factors (1, 2, 4 or 8; FP64 up to 4).
+// Each candidate runs once to warm up and is then timed with CUDA events on the
+// handle's stream over `reps` calls; the fastest is kept in the handle and used
+// by every later apply and batched solve.  The inputs are incident-wave
+// right-hand sides of the handle's own problem, so the timings see the real
+// sizes and value ranges.
+#include "ls_internal.cuh"
+
+namespace {
+
+int time_ms(ls_handle* h, int reps, float* ms, int (*fn)(ls_handle*, void*), void* arg) {
+    LS_TRY(fn(h, arg));  // warm-up (also captures graphs, allocates buffers)
+    LS_CUDA(cudaEventRecord(h->ev0, h->stream));
+    for (int r = 0; r < reps; ++r) LS_TRY(fn(h, arg));
+    LS_CUDA(cudaEventRecord(h->ev1, h->stream));
+    LS_CUDA(cudaEventSynchronize(h->ev1));
+    LS_CUDA(cudaEventElapsedTime(ms, h->ev0, h->ev1));
+    *ms /= reps;
+    return LS_OK;
+}
+
+struct ApplyArg {
+    double2* x;
+    double2* y;
+};
+int run_apply(ls_handle* h, void* a) {
+    auto* p = static_cast<ApplyArg*>(a);
+    return ls_apply_mx(h, p->x, p->y);
+}
+
+struct BdArg {
+    double2* g;
+    double2* v;
+    int nrhs, chunk;
+};
+int run_bd(ls_handle* h, void* a) {
+    auto* p = static_cast<BdArg*>(a);
+    const size_t N = (size_t)h->n * h->n;
+    for (int b0 = 0; b0 < p->nrhs; b0 += p->chunk) {
+        const int c = p->nrhs - b0 < p->chunk ? p->nrhs - b0 : p->chunk;
+        LS_TRY(ls_bd_b(h, p->g + b0 * N, p->v + b0 * N, c));
+    }
+    return LS_OK;
+}
+
+}  // namespace
+
+extern "C" int ls_autotune(ls_handle* h, int nrhs, int reps, ls_tuning* out) {
+    if (!h || nrhs < 1 || nrhs > LS_MAX_BATCH || reps < 1) return LS_EINVAL;
+    ls_tuning t{};
+    const size_t N = (size_t)h->n * h->n;
+    double2* buf = nullptr;
+    LS_CUDA(cudaMalloc(&buf, sizeof(double2) * N * 2 * nrhs));
+    int rc = LS_OK;
+    do {
+        for (int b = 0; b < nrhs && rc == LS_OK; ++b) rc = ls_rhs64(h, 0.7 + 0.9 * b, buf + b * N);
+        if (rc != LS_OK) break;
+        // FFT tile shape (the variant the solve's FP32 / mixed apply uses)
+        ApplyArg aa{buf, buf + nrhs * N};
+        float best = 0;
+        int pick = 0;
+        for (int v = 0; v < ls_handle::kFftVariants && rc == LS_OK; ++v) {
+            if (v != 1 && !ls_fft16_supported(h)) {
+                t.fft_ms[v] = -1;
+                continue;
+            }
+            h->fft_variant = v;
+            float ms = 0;
+            rc = time_ms(h, reps, &ms, run_apply, &aa);
+            t.fft_ms[v] = ms;
+            if (rc == LS_OK && (best == 0 || ms < best)) {
+                best = ms;
+                pick = v;
+            }
+        }
+        if (rc != LS_OK) break;
+        h->fft_variant = pick;
+        t.fft_variant = pick;
+        // band-block batching of Algorithm 2 for nrhs right-hand sides (needs the factors)
+        if (!h->factored) break;
+        const int cap = h->prec == LS_MIXED ? kMaxBatch : 4;
+        best = 0;
+        int chunk = 1;
+        for (int k = 0, c = 1; c <= cap && rc == LS_OK; ++k, c *= 2) {
+            if (c > nrhs && c > 1) break;
+            BdArg ba{buf, buf + nrhs * N, nrhs, c};
+            float ms = 0;
+            rc = time_ms(h, reps, &ms, run_bd, &ba);
+            t.bd_ms[k] = ms / nrhs;
+            if (rc == LS_OK && (best == 0 || ms < best)) {
+                best = ms;
+                chunk = c;
+            }
+        }
+        if (rc != LS_OK) break;
+        h->bd_chunk = chunk;
+        t.bd_chunk = chunk;
+    } while (0);
+    cudaStreamSynchronize(h->stream);
+    cudaFree(buf);
+    if (rc == LS_OK && out) *out = t;
+    return rc;
+}

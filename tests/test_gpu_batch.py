@@ -151,3 +151,62 @@ def test_batched_solve_rejects_nan_and_bad_counts():
     rc = lib.ls_solve_batch(s._h, binding.LS_MAX_BATCH + 1, binding._ptr(f), 1e-8, binding._ptr(u), 0, None)
     assert rc == -1
     s.close()
+
+
+def test_group_of_uneven_problems_matches_one_by_one_solves():
+    # independent problems of different sizes and media, each on its own stream
+    sizes = [(48, 3, 4), (64, 4, 6), (96, 6, 4), (128, 4, 8), (64, 2, 10)]
+    solvers, fs = [], []
+    for k, (n, L, E) in enumerate(sizes):
+        w = inputs.omega_for_ppw(n, 10.0)
+        m = inputs.bump_medium(n, nbumps=6, seed=40 + k)
+        st = torch.cuda.Stream()
+        prec = binding.LS_MIXED if k % 2 else binding.LS_FP64
+        s = binding.Solver(cuda(m), w, layers=L, ext=E, precision=prec, stream=st)
+        s.ls_factor()
+        solvers.append(s)
+        fs.append(s.ls_incident_rhs(0.3 * k))
+    torch.cuda.synchronize()
+    us, stats, status = binding.solve_group(solvers, fs, 1e-8)
+    torch.cuda.synchronize()
+    assert status == [0] * len(sizes)
+    for s, f, u, st in zip(solvers, fs, us, stats):
+        u1, st1, _ = s.ls_solve(f, 1e-8)
+        torch.cuda.synchronize()
+        assert rel(u, u1) < 1e-12  # same kernels, same reduction order
+        assert st["outer_iters"] == st1["outer_iters"]
+        assert st["true_rel_residual"] <= 1e-8
+    for s in solvers:
+        s.close()
+
+
+def test_group_rejects_a_handle_given_twice():
+    n = 32
+    s = binding.Solver(cuda(inputs.gaussian_disk_medium(n)), 2 * math.pi * 4, layers=2, ext=4)
+    s.ls_factor()
+    f = s.ls_incident_rhs(0.0)
+    with pytest.raises(binding.LSError) as e:
+        binding.solve_group([s, s], [f, f.clone()], 1e-8)
+    assert e.value.code == -1
+    s.close()
+
+
+@pytest.mark.parametrize("prec", [binding.LS_FP64, binding.LS_MIXED])
+def test_autotuner_choices_keep_results(prec):
+    n, L, E = 128, 4, 8
+    w = inputs.omega_for_ppw(n, 10.0)
+    m = inputs.bump_medium(n, nbumps=6, seed=3)
+    s = binding.Solver(cuda(m), w, layers=L, ext=E, precision=prec)
+    s.ls_factor()
+    f = torch.stack([s.ls_incident_rhs(t) for t in (0.1, 1.3, 2.9, 4.0)]).contiguous()
+    u0, _, _ = s.ls_solve_batch(f, 1e-9)
+    y0 = s.ls_apply_mixed(f[0].contiguous())
+    t = s.ls_autotune(nrhs=4, reps=2)
+    assert t["fft_variant"] in (0, 1, 2, 3) and t["bd_chunk"] in (1, 2, 4)
+    assert all(x > 0 for x in t["fft_ms"])  # P = 256: every tile shape exists
+    assert all(x > 0 for x in t["bd_ms_per_rhs"][:3])
+    u1, st, rc = s.ls_solve_batch(f, 1e-9)
+    assert rc == 0 and st["true_rel_residual"] <= 1e-9
+    assert rel(u1, u0) < 1e-7
+    assert rel(s.ls_apply_mixed(f[0].contiguous()), y0) < 2e-5
+    s.close()

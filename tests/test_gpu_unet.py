@@ -1,0 +1,173 @@
+"""The learned preconditioner step on the GPU against the FP64 oracle network.
+
+The GPU network stores activations, gradients and weights in BF16 and
+accumulates in FP32, so it is compared with the oracle at BF16 accuracy:
+outputs to a few 1e-2 relative, every layer's weight gradient by direction
+(cosine > 0.99) and size (relative error < 0.1).  The oracle itself is pinned
+by brute force and finite differences in test_oracle_unet.py.
+"""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+from oracle import solver as osolver, unet  # noqa: E402
+from paper_1602_07652_gb300 import binding, inputs  # noqa: E402
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    from paper_1602_07652_gb300 import build_lib
+    build_lib.build()
+    binding.load()
+
+
+def flat_params(p, levels, c0):
+    out = []
+    for name, _, _ in unet.layer_shapes(levels, c0):
+        out.append(p[name + ".w"].ravel())
+        out.append(p[name + ".b"].ravel())
+    return np.concatenate(out)
+
+
+def sample(n, seed):
+    rng = np.random.default_rng(seed)
+    r = rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))
+    e = 0.5 * r + 0.3 * np.roll(r, 1, axis=0) + 0.1j * rng.standard_normal((n, n))
+    m = inputs.bump_medium(n, nbumps=4, seed=seed)
+    return r, e, m
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(np.asarray(b)))
+
+
+LEVELS, C0, N = 3, 16, 32
+
+
+def make_pair(seed=0):
+    p = unet.init_params(levels=LEVELS, c0=C0, seed=seed)
+    rng = np.random.default_rng(seed + 1)
+    for k in p:
+        if k.endswith(".b"):
+            p[k] = 0.05 * rng.standard_normal(p[k].shape)
+    net = binding.Net(levels=LEVELS, c0=C0, max_batch=2, H=N, W=N, train=True)
+    assert net.param_count() == sum(v.size for v in p.values())
+    net.set_params(torch.from_numpy(flat_params(p, LEVELS, C0)))
+    return p, net
+
+
+def test_forward_matches_oracle_network():
+    p, net = make_pair(0)
+    r, _, m = sample(N, 3)
+    z = net.forward(torch.from_numpy(r[None]).cuda(), torch.from_numpy(m[None]).cuda())[0].cpu().numpy()
+    z_ref = unet.apply(p, r, m, levels=LEVELS)
+    assert rel(z, z_ref) < 3e-2
+    # parameters round-trip in the oracle's layout
+    back = net.get_params().numpy()
+    assert np.allclose(back, flat_params(p, LEVELS, C0).astype(np.float32))
+    net.close()
+
+
+def test_gradients_match_oracle_network():
+    p, net = make_pair(1)
+    r, e, m = sample(N, 4)
+    loss = net.train_step(torch.from_numpy(r[None]).cuda(), torch.from_numpy(m[None]).cuda(),
+                          torch.from_numpy(e[None]).cuda(), lr=0.0)
+    g = net.get_grads().numpy()
+    x, s = unet.make_input(r, m)
+    t = np.stack([e.real / s, e.imag / s])
+    loss_ref, g_ref, _ = unet.loss_and_grad(p, x, t, levels=LEVELS)
+    assert abs(loss - loss_ref) < 2e-2 * loss_ref
+    k = 0
+    for name, o, c in unet.layer_shapes(LEVELS, C0):
+        for part in (".w", ".b"):
+            ref = g_ref[name + part].ravel()
+            got = g[k:k + ref.size]
+            k += ref.size
+            cos = float(np.dot(got, ref) / (np.linalg.norm(got) * np.linalg.norm(ref) + 1e-30))
+            assert cos > 0.99, (name + part, cos)
+            assert rel(got, ref) < 0.1, (name + part, rel(got, ref))
+    assert k == g.size
+    net.close()
+
+
+def test_training_steps_reduce_the_loss_and_batches_are_independent():
+    _, net = make_pair(2)
+    rs, es, ms = zip(*(sample(N, 10 + b) for b in range(2)))
+    r = torch.from_numpy(np.stack(rs)).cuda()
+    e = torch.from_numpy(np.stack(es)).cuda()
+    m = torch.from_numpy(np.stack(ms)).cuda()
+    z2 = net.forward(r, m)
+    for b in range(2):
+        z1 = net.forward(r[b:b + 1].contiguous(), m[b:b + 1].contiguous())
+        assert torch.allclose(z1[0], z2[b])  # same kernels on each sample
+    losses = [net.train_step(r, m, e, lr=2e-3) for _ in range(40)]
+    assert losses[-1] < 0.5 * losses[0], losses[::8]
+    net.close()
+
+
+def test_bad_shapes_are_refused():
+    net = binding.Net(levels=LEVELS, c0=C0, max_batch=1, H=N, W=N, train=False)
+    r = torch.zeros((1, 48, 48), dtype=torch.complex128, device="cuda")
+    m = torch.zeros((1, 48, 48), dtype=torch.float64, device="cuda")
+    with pytest.raises(binding.LSError) as e:
+        net.forward(r, m)   # 48 is not a multiple of 32
+    assert e.value.code == -1
+    r = torch.zeros((2, 32, 32), dtype=torch.complex128, device="cuda")
+    m = torch.zeros((2, 32, 32), dtype=torch.float64, device="cuda")
+    with pytest.raises(binding.LSError) as e:
+        net.forward(r, m)   # beyond max_batch * H * W
+    assert e.value.code == -9
+    with pytest.raises(binding.LSError):
+        net.train_step(r[:1].contiguous(), m[:1].contiguous(), r[:1].contiguous(), 1e-3)  # created for inference
+    net.close()
+
+
+@pytest.mark.parametrize("prec", [binding.LS_FP64, binding.LS_MIXED])
+def test_solve_with_the_learned_step_still_meets_the_oracle(prec):
+    # even an untrained network cannot spoil the solve: FGMRES keeps the plain
+    # directions and the FP64 residual decides convergence
+    n, L, E = 64, 4, 8
+    w = 2 * math.pi * 8
+    m = inputs.bump_medium(n, nbumps=6, seed=21)
+    s = binding.Solver(torch.from_numpy(m).cuda(), w, layers=L, ext=E, precision=prec)
+    s.ls_factor()
+    net = binding.Net(levels=3, c0=16, max_batch=1, H=n, W=n, train=False, seed=5)
+    s.ls_set_learned(net)
+    f = s.ls_incident_rhs(0.4)
+    u, st, rc = s.ls_solve(f, 1e-10)
+    assert rc == 0 and st["true_rel_residual"] <= 1e-10
+    assert st["learned_steps"] >= 1
+    prob = osolver.Problem(m, w, L=L, E=E)
+    u_ref, _ = osolver.solve(prob, prob.rhs(0.4), tol=1e-12)
+    assert rel(u.cpu().numpy(), u_ref) < 1e-6
+    s.ls_set_learned(None)
+    _, st2, _ = s.ls_solve(f, 1e-10)
+    assert st2["learned_steps"] == 0
+    s.close()
+    net.close()
+
+
+def test_training_on_solver_pairs_improves_the_learned_correction():
+    # what training gains: the predicted correction on held-out media gets closer
+    # to the true one, and the solve with the learned step still converges
+    from paper_1602_07652_gb300 import learned
+    n = 128
+    train_data = learned.make_dataset(n, seeds=range(1000, 1012))
+    held_out = learned.make_dataset(n, seeds=range(2000, 2003))
+    net = binding.Net(levels=4, c0=32, max_batch=4, H=n, W=n, train=True, seed=1)
+    before = learned.correction_error(net, held_out)
+    losses = learned.train(net, train_data, steps=300, batch=4, lr=1e-3, seed=0)
+    after = learned.correction_error(net, held_out)
+    cmp = learned.compare_solves(net, n, seeds=[2000], thetas=(0.3,))
+    print("held-out correction error %.3f -> %.3f; loss %.3e -> %.3e; outer iterations plain %.1f learned %.1f"
+          % (before, after, losses[0], losses[-1], cmp["plain"]["outer"], cmp["learned"]["outer"]))
+    assert after < 0.8 * before
+    assert losses[-1] < losses[0]
+    assert cmp["learned"]["learned_steps"] >= 1
+    net.close()
