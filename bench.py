@@ -5,7 +5,7 @@ per wavelength), medium = 20 seeded Gaussian bumps in a disk of radius 0.4
 (seed 0), 32 layers per direction extended by 10 rows, mixed precision
 (FP32 complex FFT convolution and local solves, FP64 factorisation, Arnoldi
 and residual, FP64 iterative refinement), relative residual tolerance 1e-6.
-A step is one full solve of a batch of B incident plane waves (default 8; the
+A step is one full solve of a batch of B incident plane waves (default 16; the
 paper solves 64 incident waves per medium): the right-hand sides
 f = -w^2 G (m u_I) are generated on the device and the outer flexible GMRES,
 preconditioned by Algorithm 3 (inner GMRES + Algorithm 2 sweeps), runs to the
@@ -34,7 +34,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "solve s/RHS to 1e-6 rel. residual at 2048^2; LS-apply % of HBM roofline"
 N_DEFAULT, PPW_W, LAYERS, EXT, TOL = 2048, 200, 32, 10, 1e-6
-BATCH_DEFAULT = 8  # the paper solves 64 incident waves per medium: 8 batches of 8
+BATCH_DEFAULT = 16  # the paper solves 64 incident waves per medium: 4 batches of 16
 
 
 def parse():
@@ -53,6 +53,8 @@ def parse():
     ap.add_argument("--sweep-only", action="store_true",
                     help="time only Algorithm 2 applications (setup + factorisation): profiling driver")
     ap.add_argument("--fp64", action="store_true", help="plain FP64 method instead of mixed precision")
+    ap.add_argument("--fft-variant", type=int, default=None,
+                    help="--apply-only: pin the column-pass tile shape (ls_set_shapes) instead of autotuning")
     ap.add_argument("--mixed", action="store_true", help="--apply-only: FP64 I/O with FP32 arithmetic (the solve's apply)")
     ap.add_argument("--no-graphs", action="store_true",
                     help="launch Algorithm 2 kernel by kernel instead of replaying its CUDA graph (same arithmetic; "
@@ -65,6 +67,9 @@ def parse():
                     help="learned preconditioner step: train the BF16 U-Net (4 levels, 32 base channels) on "
                          "residual->correction pairs of the plain solver over seeded 512^2 bump media, then solve "
                          "the 2048^2 workload with and without it")
+    ap.add_argument("--net-only", action="store_true",
+                    help="time the learned step's network alone: forward and training step of the BF16 U-Net "
+                         "(4 levels, 32 base channels) on a batch of 4 fields of 512^2")
     ap.add_argument("--learned-media", type=int, default=100)
     ap.add_argument("--learned-steps", type=int, default=1500)
     ap.add_argument("--table1", action="store_true",
@@ -87,7 +92,7 @@ def config_dict(wl, prec="mixed", rhs_per_step=1):
                         "%d layers/direction ext %d, %s precision, tol %g, %s"
                         % (wl["n"], wl["n"], wl["omega"] / (2 * math.pi), wl["layers"], wl["ext"], prec, wl["tol"],
                            per),
-            "rhs_per_step": rhs_per_step, "n": wl["n"], "omega": wl["omega"], "layers": wl["layers"], "ext": wl["ext"], "tol": wl["tol"],
+            "rhs_per_step": rhs_per_step, "restarts": {"outer": 20, "inner": 20}, "n": wl["n"], "omega": wl["omega"], "layers": wl["layers"], "ext": wl["ext"], "tol": wl["tol"],
             "l2": "inputs larger than L2: every sweep streams ~%.0f GB of local-solve factors" %
                   (4 * wl["layers"] * wl["n"] * (wl["n"] // wl["layers"] + 2 * wl["ext"]) ** 2 * 8 * 1.75 / 1e9),
             "parallelism": "replicas"}
@@ -282,6 +287,9 @@ def run_ours(args):
     t0 = time.perf_counter()
     o = binding.default_opts()
     o.use_graphs = 0 if args.no_graphs else 1
+    # restart lengths above the iteration counts this workload needs (<= 6 outer, <= 6 inner
+    # per call), so they never restart; they bound the Krylov memory of large batches
+    o.outer_restart, o.inner_restart = 20, 20
     prec = binding.LS_FP64 if args.fp64 else binding.LS_MIXED
     if args.fp64 and args.batch > 4:
         raise SystemExit("--fp64 takes batches of at most 4")
@@ -399,7 +407,11 @@ def run_ours(args):
                "iterations": {"outer": outer, "inner_total": inner,
                               "refine_steps": statistics.mean(st["refine_steps"] for st in stats),
                               "true_rel_residual_max": max(st["true_rel_residual"] for st in stats)},
-               "sweep_ms_avg": (sum(st["t_sweep_ms"] for st in stats) / max(1, sum(st["n_sweep"] for st in stats)))}
+               "sweep_ms_avg": (sum(st["t_sweep_ms"] for st in stats) / max(1, sum(st["n_sweep"] for st in stats))),
+               # live shares of the timed region (CUDA events inside the library)
+               "time_shares": {"algorithm2": sum(st["t_sweep_ms"] for st in stats) / ms,
+                               "ls_apply_fp32": t_app / ms,
+                               "ls_apply_fp64_refinement": sum(st["t_apply64_ms"] for st in stats) / ms}}
         if not args.no_cpu_baseline:
             try:
                 out["cpu_baseline"] = cpu_baseline(wl, outer, inner)
@@ -427,7 +439,10 @@ def run_component(args):
     stream = s.stream
     tune = None
     if args.apply_only and not args.fp64:
-        tune = s.ls_autotune(nrhs=1, reps=5)
+        if args.fft_variant is None:
+            tune = s.ls_autotune(nrhs=1, reps=5)
+        else:
+            s.ls_set_shapes(args.fft_variant)
     if args.apply_only:
         if args.fp64:
             x = torch.from_numpy(inputs.random_field(n, 0)).cuda()
@@ -603,8 +618,63 @@ def run_learned(args):
     return 0
 
 
+def unet_flops(levels, c0, H, W, nb):
+    """Multiply-add flops (2 per MAC) of one forward pass, real channel counts."""
+    ch = [c0 * 2 ** l for l in range(levels)]
+    f = 0
+    prev = 3
+    for l in range(levels):
+        px = nb * (H >> l) * (W >> l)
+        f += 2 * 9 * px * (prev * ch[l] + ch[l] * ch[l])
+        prev = ch[l]
+    for l in range(levels - 2, -1, -1):
+        px = nb * (H >> l) * (W >> l)
+        f += 2 * 9 * px * (ch[l + 1] * ch[l] + 2 * ch[l] * ch[l] + ch[l] * ch[l])
+    f += 2 * 9 * nb * H * W * ch[0] * 2
+    return f
+
+
+def run_net_only(args):
+    import numpy as np
+    import torch
+    from paper_1602_07652_gb300 import binding
+    binding.load()
+    nb, H = 4, 512
+    net = binding.Net(levels=4, c0=32, max_batch=nb, H=H, W=H, train=True, seed=0)
+    rng = np.random.default_rng(0)
+    r = torch.from_numpy(rng.standard_normal((nb, H, H)) + 1j * rng.standard_normal((nb, H, H))).cuda()
+    e = (0.5 * r).contiguous()
+    m = torch.from_numpy(0.1 * rng.standard_normal((nb, H, H))).cuda()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    stream = net.stream
+    out = {"component": "learned step U-Net (BF16, WMMA tensor cores)", "batch": nb, "H": H}
+    for name, fn, mult in (("forward", lambda: net.forward(r, m), 1), ("train_step", lambda: net.train_step(r, m, e, 0.0), 3)):
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for _ in range(args.steps):
+            fn()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        ms = ev0.elapsed_time(ev1) / args.steps
+        fl = unet_flops(4, 32, H, H, nb) * mult
+        out[name] = {"ms": ms, "tflops": fl / (ms / 1e3) / 1e12, "flops": fl}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            pk = json.load(fh)
+        out["bf16_peak_tflops"] = pk.get("bf16_tflops")
+    except Exception:
+        out["bf16_peak_tflops"] = None
+    print(json.dumps(out))
+    net.close()
+    return 0
+
+
 def main():
     args = parse()
+    if args.net_only:
+        return run_net_only(args)
     if args.learned:
         return run_learned(args)
     if args.uneven:

@@ -57,7 +57,7 @@ class Stats(ctypes.Structure):
 
 class Tuning(ctypes.Structure):
     _fields_ = [("fft_variant", ctypes.c_int), ("bd_chunk", ctypes.c_int),
-                ("fft_ms", ctypes.c_double * 4), ("bd_ms", ctypes.c_double * 4)]
+                ("fft_ms", ctypes.c_double * 6), ("bd_ms", ctypes.c_double * 4)]
 
     def as_dict(self):
         return {"fft_variant": self.fft_variant, "bd_chunk": self.bd_chunk,
@@ -81,6 +81,7 @@ _SIGS = {
     "ls_solve_group": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.c_double,
                                       ctypes.POINTER(_P), ctypes.POINTER(Stats), ctypes.POINTER(ctypes.c_int)]),
     "ls_autotune": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.POINTER(Tuning)]),
+    "ls_set_shapes": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int]),
     "ls_solve_host": (ctypes.c_int, [_P, _P, ctypes.c_double, _P, ctypes.POINTER(Stats)]),
     "ls_solve_plane_wave": (ctypes.c_int, [_P, ctypes.c_double, ctypes.c_double, _P, ctypes.POINTER(Stats)]),
     "ls_apply_A": (ctypes.c_int, [_P, _P, _P]),
@@ -349,6 +350,9 @@ class Solver:
 
     def ls_set_learned(self, net):
         _ck(self._lib.ls_set_learned(self._h, net._h if net is not None else None), "ls_set_learned")
+
+    def ls_set_shapes(self, fft_variant, bd_chunk=0):
+        _ck(self._lib.ls_set_shapes(self._h, int(fft_variant), int(bd_chunk)), "ls_set_shapes")
 
     def ls_autotune(self, nrhs=1, reps=3):
         t = Tuning()

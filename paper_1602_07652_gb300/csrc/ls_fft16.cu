@@ -1,32 +1,37 @@
 // ls_fft16.cu -- the FP32 LS-apply (Sec. 2) with transforms specialised on the
-// padded length P = 2^LP (256 <= P <= 4096).
+// padded length P = 2^LP (256 <= P <= 4096) and on the radix a thread owns.
 //
 // Same three HBM passes as the generic path (rows forward, columns forward x
 // Ghat x inverse, rows inverse), with everything a transform does fixed at
 // compile time:
-//   * radix-16 Stockham stages (the last forward / first inverse stage takes
-//     the remaining radix), so P = 4096 needs two shared-memory exchanges per
-//     transform instead of three;
-//   * a thread owns one radix-16 butterfly per stage (16 elements; in the
-//     column pass, 16 elements of each of its 2 columns), all index arithmetic
-//     is constant-folded and the stage loop is fully unrolled;
-//   * twiddles W^r, r = 1..15, come from 4 table loads (W, W^2, W^4, W^8) and
-//     11 complex products instead of 15 loads;
+//   * Stockham stages of radix E = 2^LE (16 or 8; the last forward / first
+//     inverse stage takes the remaining radix): P = 4096 needs two
+//     shared-memory exchanges per transform at radix 16, three at radix 8;
+//   * a thread owns one radix-E butterfly per stage (E elements; in the column
+//     pass, E elements of each of its CW columns), all index arithmetic is
+//     constant-folded and the stage loop is fully unrolled;
+//   * twiddles W^r, r = 1..E-1, come from log2 E table loads (W, W^2, W^4, W^8)
+//     and products instead of E - 1 loads;
 //   * the zero padding is pruned: the first forward stage sees only its lower
-//     8 inputs (z, x < n <= P/2), so its first butterfly layer only rotates.
-// Small P groups several transforms per 256-thread CTA.
+//     E/2 inputs (z, x < n <= P/2), so its first butterfly layer only rotates.
+// Radix 16 halves the exchanges, radix 8 halves the registers a thread needs
+// (more resident warps to hide latency); the autotuner picks per problem.
+// Small P groups several transforms per CTA of at least 256 threads.
 #include "ls_fft_common.cuh"
 
 namespace {
 
-template <int LP>
+// Geometry of a transform of P = 2^LP points, E = 2^LE elements per thread.
+template <int LP, int LE>
 struct Geo {
     static constexpr int P = 1 << LP;
-    static constexpr int T = P / 16;                  // threads per transform
-    static constexpr int G = T >= 256 ? 1 : 256 / T;  // transforms per CTA
-    static constexpr int NS = (LP + 3) / 4;           // stages
-    static constexpr int LRL = LP - 4 * (NS - 1);     // log2 radix of the last forward stage
-    static constexpr int SLOTS = P + (P >> 4);        // padded shared-memory slots per transform
+    static constexpr int E = 1 << LE;
+    static constexpr int T = P / E;                      // threads per transform
+    static constexpr int THREADS = T >= 256 ? T : 256;   // CTA size
+    static constexpr int G = THREADS / T;                // transforms per CTA
+    static constexpr int NS = (LP + LE - 1) / LE;        // stages
+    static constexpr int LRL = LP - LE * (NS - 1);       // log2 radix of the last forward stage
+    static constexpr int SLOTS = P + (P >> 4);           // padded shared-memory slots per transform
 };
 
 __device__ __forceinline__ int pad16(int i) { return i + (i >> 4); }
@@ -58,8 +63,8 @@ __device__ __forceinline__ float2 ld_tw(const float2* __restrict__ tw, int m) {
 
 // v[c][e R + r] *= W^(k r), W = exp(-DIR 2 pi i / 2^(LS+LR)), r = 1..R-1.
 // tw[m] = exp(-2 pi i m / P), so W^s = tw[s << (LP - LS - LR)].
-template <int LR, int LS, int DIR, int LP, int CW>
-__device__ __forceinline__ void twiddle(float2 (&v)[CW][16], int e, int k, const float2* __restrict__ tw) {
+template <int LR, int LS, int DIR, int LP, int CW, int E>
+__device__ __forceinline__ void twiddle(float2 (&v)[CW][E], int e, int k, const float2* __restrict__ tw) {
     constexpr int R = 1 << LR;
     constexpr int SH = LP - LS - LR;
     float2 w[16];
@@ -83,36 +88,40 @@ __device__ __forceinline__ void twiddle(float2 (&v)[CW][16], int e, int k, const
         for (int r = 1; r < R; ++r) v[c][e * R + r] = v[c][e * R + r] * w[r];
 }
 
-// One Stockham stage: radix 2^LR, Ns = 2^LS.  Butterfly b = j + e T (e < 16/R)
+// One Stockham stage: radix 2^LR, Ns = 2^LS.  Butterfly b = j + e T (e < E/R)
 // holds inputs b + r P/R in v[.][e R + r]; twiddle by W^((b mod Ns) r), DFT.
-template <int LR, int LS, int DIR, int LP, bool HZ, int CW>
-__device__ __forceinline__ void stage(float2 (&v)[CW][16], int j, const float2* __restrict__ tw) {
-    constexpr int R = 1 << LR, T = Geo<LP>::T;
+template <int LR, int LS, int DIR, int LP, int LE, bool HZ, int CW, int E>
+__device__ __forceinline__ void stage(float2 (&v)[CW][E], int j, const float2* __restrict__ tw) {
+    constexpr int R = 1 << LR, T = Geo<LP, LE>::T;
 #pragma unroll
-    for (int e = 0; e < 16 / R; ++e) {
-        if constexpr (LS > 0) twiddle<LR, LS, DIR, LP, CW>(v, e, (j + e * T) & ((1 << LS) - 1), tw);
+    for (int e = 0; e < E / R; ++e) {
+        if constexpr (LS > 0) twiddle<LR, LS, DIR, LP>(v, e, (j + e * T) & ((1 << LS) - 1), tw);
 #pragma unroll
         for (int c = 0; c < CW; ++c) dft_reg<R, DIR, HZ>(&v[c][e * R]);
     }
 }
 
-// Shared-memory element: one complex (rows) or the two complex values of a row of
-// a 2-column tile (columns).
+// Shared-memory element: one complex (CW = 1) or the two complex values of a row of
+// a 2-column tile (CW = 2).
 template <int CW>
 struct Elem;
 template <>
 struct Elem<1> {
     using T = float2;
-    __device__ __forceinline__ static T pack(const float2 (&v)[1][16], int q) { return v[0][q]; }
-    __device__ __forceinline__ static void unpack(T a, float2 (&v)[1][16], int q) { v[0][q] = a; }
+    template <int E>
+    __device__ __forceinline__ static T pack(const float2 (&v)[1][E], int q) { return v[0][q]; }
+    template <int E>
+    __device__ __forceinline__ static void unpack(T a, float2 (&v)[1][E], int q) { v[0][q] = a; }
 };
 template <>
 struct Elem<2> {
     using T = float4;
-    __device__ __forceinline__ static T pack(const float2 (&v)[2][16], int q) {
+    template <int E>
+    __device__ __forceinline__ static T pack(const float2 (&v)[2][E], int q) {
         return make_float4(v[0][q].x, v[0][q].y, v[1][q].x, v[1][q].y);
     }
-    __device__ __forceinline__ static void unpack(T a, float2 (&v)[2][16], int q) {
+    template <int E>
+    __device__ __forceinline__ static void unpack(T a, float2 (&v)[2][E], int q) {
         v[0][q] = make_float2(a.x, a.y);
         v[1][q] = make_float2(a.z, a.w);
     }
@@ -122,12 +131,12 @@ struct Elem<2> {
 // through shared memory into the inputs of the next stage (radix 2^LRN).
 // FIRST: the buffer has not been read since the CTA started, no barrier before
 // the stores.
-template <int LR, int LS, int LRN, int LP, bool FIRST, int CW>
-__device__ __forceinline__ void exchange(float2 (&v)[CW][16], typename Elem<CW>::T* buf, int j) {
-    constexpr int R = 1 << LR, RN = 1 << LRN, T = Geo<LP>::T, P = Geo<LP>::P;
+template <int LR, int LS, int LRN, int LP, int LE, bool FIRST, int CW, int E>
+__device__ __forceinline__ void exchange(float2 (&v)[CW][E], typename Elem<CW>::T* buf, int j) {
+    constexpr int R = 1 << LR, RN = 1 << LRN, T = Geo<LP, LE>::T, P = Geo<LP, LE>::P;
     if (!FIRST) __syncthreads();
 #pragma unroll
-    for (int e = 0; e < 16 / R; ++e) {
+    for (int e = 0; e < E / R; ++e) {
         const int b = j + e * T;
         const int base = ((b >> LS) << (LS + LR)) + (b & ((1 << LS) - 1));
 #pragma unroll
@@ -135,72 +144,67 @@ __device__ __forceinline__ void exchange(float2 (&v)[CW][16], typename Elem<CW>:
     }
     __syncthreads();
 #pragma unroll
-    for (int e = 0; e < 16 / RN; ++e) {
+    for (int e = 0; e < E / RN; ++e) {
         const int b = j + e * T;
 #pragma unroll
         for (int r = 0; r < RN; ++r) Elem<CW>::unpack(buf[pad16(b + r * (P / RN))], v, e * RN + r);
     }
 }
 
-// Forward transform.  In: v[.][t] = x[j + t T] with x[j + t T] = 0 for t >= 8.
+// Forward stages S.. (stage S: radix E except the last, 2^LRL; Ns = E^S).
+// In at S = 0: v[.][t] = x[j + t T], x[j + t T] = 0 for t >= E/2.
 // Out: v[.][e R + r] = X[b + r P/R], b = j + e T, R = 2^LRL.
-template <int LP, bool FIRST, int CW>
-__device__ __forceinline__ void fft_fwd(float2 (&v)[CW][16], typename Elem<CW>::T* buf, int j,
-                                        const float2* __restrict__ tw) {
-    constexpr int NS = Geo<LP>::NS, LRL = Geo<LP>::LRL;
-    stage<4, 0, +1, LP, true>(v, j, tw);
-    if constexpr (NS == 2) {
-        exchange<4, 0, 4, LP, FIRST>(v, buf, j);
-        stage<4, 4, +1, LP, false>(v, j, tw);
-    } else {
-        exchange<4, 0, 4, LP, FIRST>(v, buf, j);
-        stage<4, 4, +1, LP, false>(v, j, tw);
-        exchange<4, 4, LRL, LP, false>(v, buf, j);
-        stage<LRL, 8, +1, LP, false>(v, j, tw);
-    }
+template <int LP, int LE, int S, bool FIRST, int CW, int E>
+__device__ __forceinline__ void fwd_stages(float2 (&v)[CW][E], typename Elem<CW>::T* buf, int j,
+                                           const float2* __restrict__ tw) {
+    using Gm = Geo<LP, LE>;
+    constexpr int LR = S < Gm::NS - 1 ? LE : Gm::LRL;
+    if constexpr (S > 0) exchange<LE, LE * (S - 1), LR, LP, LE, FIRST && S == 1>(v, buf, j);
+    stage<LR, LE * S, +1, LP, LE, S == 0>(v, j, tw);
+    if constexpr (S + 1 < Gm::NS) fwd_stages<LP, LE, S + 1, FIRST>(v, buf, j, tw);
 }
 
-// Inverse (unnormalised) transform: the forward stages in reverse order.
-// In: v[.][e R + r] = X[b + r P/R] as fft_fwd leaves it.  Out: v[.][t] = x[j + t T].
-template <int LP, bool FIRST, int CW>
-__device__ __forceinline__ void fft_inv(float2 (&v)[CW][16], typename Elem<CW>::T* buf, int j,
-                                        const float2* __restrict__ tw) {
-    constexpr int NS = Geo<LP>::NS, LRL = Geo<LP>::LRL;
-    if constexpr (NS == 2) {
-        stage<4, 0, -1, LP, false>(v, j, tw);
-        exchange<4, 0, 4, LP, FIRST>(v, buf, j);
-        stage<4, 4, -1, LP, false>(v, j, tw);
-    } else {
-        stage<LRL, 0, -1, LP, false>(v, j, tw);
-        exchange<LRL, 0, 4, LP, FIRST>(v, buf, j);
-        stage<4, LRL, -1, LP, false>(v, j, tw);
-        exchange<4, LRL, 4, LP, false>(v, buf, j);
-        stage<4, LRL + 4, -1, LP, false>(v, j, tw);
+// Inverse (unnormalised) stages S..: the forward radices in reverse order (2^LRL
+// first).  In at S = 0: the layout fwd_stages leaves.  Out: v[.][t] = x[j + t T].
+template <int LP, int LE, int S, bool FIRST, int CW, int E>
+__device__ __forceinline__ void inv_stages(float2 (&v)[CW][E], typename Elem<CW>::T* buf, int j,
+                                           const float2* __restrict__ tw) {
+    using Gm = Geo<LP, LE>;
+    constexpr int LRL = Gm::LRL;
+    constexpr int LR = S == 0 ? LRL : LE;
+    constexpr int LS = S == 0 ? 0 : LRL + LE * (S - 1);
+    if constexpr (S > 0) {
+        constexpr int LRP = S == 1 ? LRL : LE;
+        constexpr int LSP = S == 1 ? 0 : LRL + LE * (S - 2);
+        exchange<LRP, LSP, LR, LP, LE, FIRST && S == 1>(v, buf, j);
     }
+    stage<LR, LS, -1, LP, LE, false>(v, j, tw);
+    if constexpr (S + 1 < Gm::NS) inv_stages<LP, LE, S + 1, FIRST>(v, buf, j, tw);
 }
 
-// Pass 1: X[z, :] = FFT_x(pad(m u)[z, :]) for rows z < nrows.
+// Pass 1: X[z, :] = FFT_x(pad(m u)[z, :]) for rows z < nrows (radix 16).
 template <int LP, class Src>
-__global__ void __launch_bounds__(256) k_rows16_fwd(int nrows, int nin, Src src, float2* __restrict__ X,
-                                                   const float2* __restrict__ tw) {
-    using Gm = Geo<LP>;
-    constexpr int P = Gm::P, T = Gm::T, R = 1 << Gm::LRL;
+__global__ void __launch_bounds__(Geo<LP, 4>::THREADS) k_rows16_fwd(int nrows, int nin, Src src,
+                                                                    float2* __restrict__ X,
+                                                                    const float2* __restrict__ tw) {
+    using Gm = Geo<LP, 4>;
+    constexpr int P = Gm::P, T = Gm::T, E = Gm::E, R = 1 << Gm::LRL;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int grp = threadIdx.x / T, j = threadIdx.x % T;
     float2* buf = reinterpret_cast<float2*>(smem_raw) + grp * Gm::SLOTS;
     const int z = blockIdx.x * Gm::G + grp;
     const bool live = z < nrows;
-    float2 v[1][16];
+    float2 v[1][E];
 #pragma unroll
-    for (int t = 0; t < 8; ++t) {
+    for (int t = 0; t < E / 2; ++t) {
         const int x = j + t * T;
         v[0][t] = (live && x < nin) ? src.template load<float2>(z, x) : make_float2(0.f, 0.f);
     }
-    fft_fwd<LP, true>(v, buf, j, tw);
+    fwd_stages<LP, 4, 0, true>(v, buf, j, tw);
     if (!live) return;
     float2* o = X + (size_t)z * P;
 #pragma unroll
-    for (int e = 0; e < 16 / R; ++e)
+    for (int e = 0; e < E / R; ++e)
 #pragma unroll
         for (int r = 0; r < R; ++r) o[j + e * T + r * (P / R)] = v[0][e * R + r];
 }
@@ -210,14 +214,15 @@ __global__ void __launch_bounds__(256) k_rows16_fwd(int nrows, int nin, Src src,
 // The tile's Ghat quadrant rows are copied to shared memory asynchronously at
 // the start, behind the forward transform.  Tiles are ordered so that kx and
 // P - kx (the same quadrant row) run close together and share it in L2.
-// MINB: CTAs per SM the register allocation must allow (3 spills a little at P = 4096).
-template <int LP, int CW, int MINB>
-__global__ void __launch_bounds__(256, MINB) k_cols16(int nin, int nout, float2* __restrict__ X,
-                                                              const float2* __restrict__ ghat,
-                                                              const float2* __restrict__ tw) {
-    using Gm = Geo<LP>;
+// LE: log2 of the radix a thread owns; MINB: CTAs per SM the register
+// allocation must allow.
+template <int LP, int LE, int CW, int MINB>
+__global__ void __launch_bounds__(Geo<LP, LE>::THREADS, MINB) k_cols16(int nin, int nout, float2* __restrict__ X,
+                                                                       const float2* __restrict__ ghat,
+                                                                       const float2* __restrict__ tw) {
+    using Gm = Geo<LP, LE>;
     using EL = typename Elem<CW>::T;
-    constexpr int P = Gm::P, T = Gm::T, R = 1 << Gm::LRL, Q = P / 2 + 1;
+    constexpr int P = Gm::P, T = Gm::T, E = Gm::E, R = 1 << Gm::LRL, Q = P / 2 + 1;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int grp = threadIdx.x / T, j = threadIdx.x % T;
     EL* buf = reinterpret_cast<EL*>(smem_raw) + grp * Gm::SLOTS;
@@ -233,43 +238,43 @@ __global__ void __launch_bounds__(256, MINB) k_cols16(int nin, int nout, float2*
         for (int i = j; i < Q; i += T) cp_async8(gs + c * Q + i, g + i);
     }
     cp_async_commit();
-    float2 v[CW][16];
+    float2 v[CW][E];
 #pragma unroll
-    for (int t = 0; t < 8; ++t) {
+    for (int t = 0; t < E / 2; ++t) {
         const int z = j + t * T;
         EL a{};
         if (z < nin) a = *reinterpret_cast<const EL*>(X + (size_t)z * P + kx0);
         Elem<CW>::unpack(a, v, t);
     }
-    fft_fwd<LP, true>(v, buf, j, tw);
+    fwd_stages<LP, LE, 0, true>(v, buf, j, tw);
     cp_async_wait_all();
     __syncthreads();  // every thread's share of the Ghat rows has landed
 #pragma unroll
     for (int c = 0; c < CW; ++c)
 #pragma unroll
-        for (int e = 0; e < 16 / R; ++e)
+        for (int e = 0; e < E / R; ++e)
 #pragma unroll
             for (int r = 0; r < R; ++r) {
                 const int kz = j + e * T + r * (P / R);
                 v[c][e * R + r] = v[c][e * R + r] * gs[c * Q + (kz <= P / 2 ? kz : P - kz)];
             }
-    fft_inv<LP, false>(v, buf, j, tw);
+    inv_stages<LP, LE, 0, false>(v, buf, j, tw);
 #pragma unroll
-    for (int t = 0; t < 16; ++t) {
+    for (int t = 0; t < E; ++t) {
         const int z = j + t * T;
         if (z < nout) *reinterpret_cast<EL*>(X + (size_t)z * P + kx0) = Elem<CW>::pack(v, t);
     }
 }
 
-// Pass 3: y[z, x] = u[z, x] + IFFT_x(X[z, :])[x] for x < n.  The row of u is copied
-// to shared memory asynchronously at the start (each thread fetches the elements
-// it will write), so its latency hides behind the inverse transform.
+// Pass 3: y[z, x] = u[z, x] + IFFT_x(X[z, :])[x] for x < n (radix 16).  The row of u
+// is copied to shared memory asynchronously at the start (each thread fetches the
+// elements it will write), so its latency hides behind the inverse transform.
 template <int LP, typename UIO>
-__global__ void __launch_bounds__(256) k_rows16_inv(int nrows, int n, const float2* __restrict__ X,
-                                                   const UIO* __restrict__ u, UIO* __restrict__ y,
-                                                   const float2* __restrict__ tw) {
-    using Gm = Geo<LP>;
-    constexpr int P = Gm::P, T = Gm::T, R = 1 << Gm::LRL;
+__global__ void __launch_bounds__(Geo<LP, 4>::THREADS) k_rows16_inv(int nrows, int n, const float2* __restrict__ X,
+                                                                    const UIO* __restrict__ u, UIO* __restrict__ y,
+                                                                    const float2* __restrict__ tw) {
+    using Gm = Geo<LP, 4>;
+    constexpr int P = Gm::P, T = Gm::T, E = Gm::E, R = 1 << Gm::LRL;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int grp = threadIdx.x / T, j = threadIdx.x % T;
     float2* buf = reinterpret_cast<float2*>(smem_raw) + grp * Gm::SLOTS;
@@ -278,56 +283,73 @@ __global__ void __launch_bounds__(256) k_rows16_inv(int nrows, int n, const floa
     const bool live = z < nrows;
     if (live) {
 #pragma unroll
-        for (int t = 0; t < 8; ++t) {
+        for (int t = 0; t < E / 2; ++t) {
             const int x = j + t * T;
             if (x < n) cp_async_el(us + x, u + (size_t)z * n + x);
         }
     }
     cp_async_commit();
-    float2 v[1][16];
+    float2 v[1][E];
     const float2* xr = X + (size_t)(live ? z : 0) * P;
 #pragma unroll
-    for (int e = 0; e < 16 / R; ++e)
+    for (int e = 0; e < E / R; ++e)
 #pragma unroll
         for (int r = 0; r < R; ++r) v[0][e * R + r] = xr[j + e * T + r * (P / R)];
-    fft_inv<LP, true>(v, buf, j, tw);
+    inv_stages<LP, 4, 0, true>(v, buf, j, tw);
     cp_async_wait_all();  // this thread's own copies: no barrier needed
     if (!live) return;
 #pragma unroll
-    for (int t = 0; t < 8; ++t) {
+    for (int t = 0; t < E / 2; ++t) {
         const int x = j + t * T;
         if (x < n) y[(size_t)z * n + x] = us[x] + ccast<UIO>(v[0][t]);
     }
 }
 
-// Shared memory: G transforms of P = 4096 / G elements padded to 256 * 17 slots for
-// every P, plus the prefetched u rows (G * P/2 elements) or Ghat rows (G * CW * (P/2 + 1)).
+// Shared memory: G transforms of P elements, padded (one slot per 16), plus the
+// prefetched u rows (G * P/2 elements) or Ghat rows (G * CW * (P/2 + 1)).
 template <int LP, typename UIO>
-constexpr size_t rinv_smem() { return sizeof(float2) * 256 * 17 + sizeof(UIO) * 2048; }
-template <int LP, int CW>
-constexpr size_t cols_smem() {
-    return sizeof(float2) * CW * 256 * 17 + sizeof(float2) * Geo<LP>::G * CW * ((1 << LP) / 2 + 1);
+constexpr size_t rinv_smem() {
+    using Gm = Geo<LP, 4>;
+    return sizeof(float2) * Gm::G * Gm::SLOTS + sizeof(UIO) * Gm::G * (Gm::P / 2);
 }
-constexpr size_t row_smem16() { return sizeof(float2) * 256 * 17; }
+template <int LP, int LE, int CW>
+constexpr size_t cols_smem() {
+    using Gm = Geo<LP, LE>;
+    return sizeof(float2) * CW * Gm::G * Gm::SLOTS + sizeof(float2) * Gm::G * CW * (Gm::P / 2 + 1);
+}
+template <int LP>
+constexpr size_t row_smem16() {
+    return sizeof(float2) * Geo<LP, 4>::G * Geo<LP, 4>::SLOTS;
+}
 
-// Column-pass tile shapes: 0 = 1 column, 3 CTAs/SM; 2 = 2 columns, 2 CTAs/SM;
-// 3 = 1 column, 2 CTAs/SM.
+// Column-pass tile shapes (ls_handle::fft_variant): 0 = radix 16, 1 column, 3 CTAs/SM;
+// 2 = radix 16, 2 columns, 2 CTAs/SM; 3 = radix 16, 1 column, 2 CTAs/SM;
+// 4 = radix 8, 1 column, 2 CTAs/SM (of up to 512 threads); 5 = radix 8, 2 columns, 1 CTA/SM.
+template <int LP, int LE, int CW, int MINB>
+int cols_launch(ls_handle* h, int n, float2* X, const float2* gh, const float2* tw) {
+    using Gm = Geo<LP, LE>;
+    LS_LAUNCH(h, (k_cols16<LP, LE, CW, MINB>), (unsigned)(Gm::P / CW / Gm::G), Gm::THREADS,
+              (cols_smem<LP, LE, CW>()), n, n, X, gh, tw);
+    return LS_OK;
+}
+
 template <int LP, typename UIO>
 int apply_lp(ls_handle* h, const UIO* u, UIO* y, float2* X, int shape) {
-    using Gm = Geo<LP>;
+    using Gm = Geo<LP, 4>;
     const int n = h->n;
     const float2* tw = static_cast<const float2*>(h->tw32);
     const float2* gh = static_cast<const float2*>(h->ghat32);
     const unsigned rows_grid = (unsigned)((n + Gm::G - 1) / Gm::G);
     SrcMU<float, UIO> src{h->m32, u, n};
-    LS_LAUNCH(h, (k_rows16_fwd<LP, SrcMU<float, UIO>>), rows_grid, 256, row_smem16(), n, n, src, X, tw);
-    if (shape == 2)
-        LS_LAUNCH(h, (k_cols16<LP, 2, 2>), (unsigned)(Gm::P / 2 / Gm::G), 256, (cols_smem<LP, 2>()), n, n, X, gh, tw);
-    else if (shape == 3)
-        LS_LAUNCH(h, (k_cols16<LP, 1, 2>), (unsigned)(Gm::P / Gm::G), 256, (cols_smem<LP, 1>()), n, n, X, gh, tw);
-    else
-        LS_LAUNCH(h, (k_cols16<LP, 1, 3>), (unsigned)(Gm::P / Gm::G), 256, (cols_smem<LP, 1>()), n, n, X, gh, tw);
-    LS_LAUNCH(h, (k_rows16_inv<LP, UIO>), rows_grid, 256, (rinv_smem<LP, UIO>()), n, n, X, u, y, tw);
+    LS_LAUNCH(h, (k_rows16_fwd<LP, SrcMU<float, UIO>>), rows_grid, Gm::THREADS, row_smem16<LP>(), n, n, src, X, tw);
+    switch (shape) {
+        case 2: LS_TRY((cols_launch<LP, 4, 2, 2>(h, n, X, gh, tw))); break;
+        case 3: LS_TRY((cols_launch<LP, 4, 1, 2>(h, n, X, gh, tw))); break;
+        case 4: LS_TRY((cols_launch<LP, 3, 1, 2>(h, n, X, gh, tw))); break;
+        case 5: LS_TRY((cols_launch<LP, 3, 2, 1>(h, n, X, gh, tw))); break;
+        default: LS_TRY((cols_launch<LP, 4, 1, 3>(h, n, X, gh, tw))); break;
+    }
+    LS_LAUNCH(h, (k_rows16_inv<LP, UIO>), rows_grid, Gm::THREADS, (rinv_smem<LP, UIO>()), n, n, X, u, y, tw);
     return LS_OK;
 }
 
@@ -352,9 +374,11 @@ int optin(K kern, size_t bytes) {
 
 template <int LP>
 int optin_lp() {
-    LS_TRY(optin(k_cols16<LP, 1, 3>, cols_smem<LP, 1>()));
-    LS_TRY(optin(k_cols16<LP, 1, 2>, cols_smem<LP, 1>()));
-    LS_TRY(optin(k_cols16<LP, 2, 2>, cols_smem<LP, 2>()));
+    LS_TRY(optin(k_cols16<LP, 4, 1, 3>, cols_smem<LP, 4, 1>()));
+    LS_TRY(optin(k_cols16<LP, 4, 1, 2>, cols_smem<LP, 4, 1>()));
+    LS_TRY(optin(k_cols16<LP, 4, 2, 2>, cols_smem<LP, 4, 2>()));
+    LS_TRY(optin(k_cols16<LP, 3, 1, 2>, cols_smem<LP, 3, 1>()));
+    LS_TRY(optin(k_cols16<LP, 3, 2, 1>, cols_smem<LP, 3, 2>()));
     LS_TRY(optin(k_rows16_inv<LP, float2>, rinv_smem<LP, float2>()));
     return optin(k_rows16_inv<LP, double2>, rinv_smem<LP, double2>());
 }
@@ -372,7 +396,7 @@ int ls_fft16_init(ls_handle* h) {
     return optin_lp<12>();
 }
 
-// shape: column-pass tile shape (0, 2, 3 as in apply_lp)
+// shape: column-pass tile shape (see apply_lp)
 int ls_apply32_fft16(ls_handle* h, const float2* u, float2* y, int shape) { return apply_any(h, u, y, shape); }
 
 int ls_apply_mx_fft16(ls_handle* h, const double2* u, double2* y, int shape) {

@@ -148,11 +148,27 @@ struct ls_handle {
     StencilTables* dtabs = nullptr;  // device copies (2)
 
     DirFactors fac[2];
-    // sweep buffers per direction: rhs and solution of every strip (n*q each)
-    void* srhs = nullptr;
-    void* ssol = nullptr;
-    void* strace = nullptr;    // per layer: row 0 of its down-sweep solution (w^l_0), n each
-    void* vtmp = nullptr;      // n*n complex scratch (FP64) for transposes
+    // Sweep workspaces ("lanes"): every lane holds the strip right-hand sides and
+    // solutions, traces, transpose scratch, Algorithm 2 staging buffers and its CUDA
+    // graphs (one per batch size) for up to nb_cap right-hand sides, so that chunks
+    // of a batch can run their Algorithm 2 chains concurrently on different streams.
+    struct SweepLane {
+        void* srhs = nullptr;      // every strip's right-hand side (n*q each), nb_cap sets
+        void* ssol = nullptr;      // every strip's solution
+        void* strace = nullptr;    // per layer: row 0 of its down-sweep solution (w^l_0), n each
+        void* vtmp = nullptr;      // 4 n*n complex scratch fields (FP64) per right-hand side
+        double2* bd_in = nullptr;  // graph staging
+        double2* bd_out = nullptr;
+        cudaGraph_t graph[9] = {};
+        cudaGraphExec_t exec[9] = {};
+        long long nodes[9] = {};
+        int nb_cap = 0;
+        cudaStream_t stream = nullptr;  // lane 0 runs on the handle's stream
+        cudaEvent_t done = nullptr;
+    };
+    static constexpr int kLanes = 4;
+    SweepLane lanes[kLanes];
+    int lane = 0;              // lane the sweep functions use (set around concurrent chunks)
     void* vtmp2 = nullptr;
 
     // Krylov workspaces (FP64): the context of ls_krylov.cu and the staging buffers of
@@ -162,24 +178,17 @@ struct ls_handle {
     double* red = nullptr;     // reduction partials
     double* red_host = nullptr;
     size_t red_cap = 0;
-
-    // Algorithm 2 as captured CUDA graphs, one per batch size (inputs/outputs staged
-    // through bd_in / bd_out, sized for nb_cap right-hand sides)
-    cudaGraph_t bd_graph[9] = {};
-    cudaGraphExec_t bd_exec[9] = {};
-    long long bd_nodes[9] = {};
-    double2* bd_in = nullptr;
-    double2* bd_out = nullptr;
-    int nb_cap = 0;
+    cudaEvent_t ev_fork = nullptr;
 
     ls_net* net = nullptr;     // learned first step of every outer cycle (ls_unet.cu), or none
     int learned_steps = 0;
 
     // choices of the autotuner (ls_tune.cu); defaults until ls_autotune runs
-    int fft_variant = 0;       // radix-16 (256 <= P <= 4096): 0 = 1-column tiles, 3 CTAs/SM; 2 = 2-column
-                               // tiles; 3 = 1-column tiles, 2 CTAs/SM.  1: generic radix-8 4-column tiles
-    static constexpr int kFftVariants = 4;
-    int bd_chunk = 0;          // right-hand sides per batched Algorithm 2 (0: the largest supported)
+    int fft_variant = 2;       // column-pass shape (256 <= P <= 4096): radix 16 with 0 = 1-column tiles,
+                               // 3 CTAs/SM; 2 = 2-column tiles; 3 = 1-column tiles, 2 CTAs/SM; radix 8 with
+                               // 4 = 1-column tiles; 5 = 2-column tiles.  1: generic radix-8 4-column tiles
+    static constexpr int kFftVariants = 6;
+    int bd_chunk = 0;          // right-hand sides per Algorithm 2 chain (0: the largest supported)
 
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     double t_apply_ms = 0, t_sweep_ms = 0, t_apply64_ms = 0;
@@ -224,7 +233,7 @@ int ls_apply32(ls_handle* h, const float2* u, float2* y);       // y = H u (FP32
 int ls_apply_mx(ls_handle* h, const double2* u, double2* y);    // FP64 I/O, FP32 arithmetic
 bool ls_fft16_supported(const ls_handle* h);                     // radix-16 FP32 path: 256 <= P <= 4096
 int ls_fft16_init(ls_handle* h);
-int ls_apply32_fft16(ls_handle* h, const float2* u, float2* y, int shape);  // shape: fft_variant 0, 2, 3
+int ls_apply32_fft16(ls_handle* h, const float2* u, float2* y, int shape);  // shape: fft_variant != 1
 int ls_apply_mx_fft16(ls_handle* h, const double2* u, double2* y, int shape);
 int ls_rhs64(ls_handle* h, double theta, double2* f);           // f = -w^2 G (m u_I)
 
@@ -255,6 +264,8 @@ int ls_sweep_dir(ls_handle* h, int dir, const double2* g, double2* v);   // Algo
 int ls_sweep_dir_b(ls_handle* h, int dir, const double2* g, double2* v, int nb);
 int ls_sweep_reserve(ls_handle* h, int nb);
 int ls_bd_b(ls_handle* h, const double2* g, double2* v, int nb);         // Algorithm 2, nb right-hand sides
+int ls_bd_lanes(ls_handle* h, const double2* g, double2* v, int nb, int chunk);  // chunks on concurrent lanes
+void ls_lanes_free(ls_handle* h);
 int ls_bd(ls_handle* h, const double2* g, double2* v);                   // Algorithm 2
 void ls_bd_graph_free(ls_handle* h);
 int ls_strip_solve(ls_handle* h, int dir, int layer, const double2* b, double2* x);

@@ -128,14 +128,16 @@ int apply_pc_b(ls_handle* h, Pc pc, double2* v, double2* z, int nb, const unsign
         for (int b = 0; b < top; ++b)
             if (!on[b]) LS_TRY(ls_vec_zero(h, v + b * N));
         const int ch = bd_chunk(h);
-        for (int b0 = 0; b0 < top; b0 += ch) {
-            const int cnt = top - b0 < ch ? top - b0 : ch;
-            LS_TRY(ls_timing_begin(h));
-            if (h->opts.inner_precond == LS_PC_GS) LS_TRY(ls_sweep_dir_b(h, 0, v + b0 * N, z + b0 * N, cnt));
-            else LS_TRY(ls_bd_b(h, v + b0 * N, z + b0 * N, cnt));
-            LS_TRY(ls_timing_end(h, 1));
+        LS_TRY(ls_timing_begin(h));
+        if (h->opts.inner_precond == LS_PC_GS) {
+            for (int b0 = 0; b0 < top; b0 += ch) {
+                const int cnt = top - b0 < ch ? top - b0 : ch;
+                LS_TRY(ls_sweep_dir_b(h, 0, v + b0 * N, z + b0 * N, cnt));
+            }
+        } else {
+            LS_TRY(ls_bd_lanes(h, v, z, top, ch));  // chunks run concurrently
         }
-        return LS_OK;
+        return ls_timing_end(h, 1);
     }
     // Algorithm 3: z = GMRES(C, A v, Algorithm 2, inner_tol), all members at once
     Ctx* c = ctx_of(h);

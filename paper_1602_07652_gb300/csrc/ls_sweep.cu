@@ -420,9 +420,10 @@ int sweep_impl(ls_handle* h, int dir, const double2* g, double2* v, int nb) {
     const int n = h->n, q = h->q, L = h->L;
     const size_t sstride = (size_t)n * q;
     const size_t SB = (size_t)L * sstride, TB = (size_t)L * n;
-    C* rhs = static_cast<C*>(h->srhs);
-    C* sol = static_cast<C*>(h->ssol);
-    C* trc = static_cast<C*>(h->strace);
+    const ls_handle::SweepLane& W = h->lanes[h->lane];
+    C* rhs = static_cast<C*>(W.srhs);
+    C* sol = static_cast<C*>(W.ssol);
+    C* trc = static_cast<C*>(W.strace);
     const DirFactors& F = h->fac[dir];
     const StripGeom geo = geom_of(h);
     const dim3 gs((unsigned)((sstride + 255) / 256), nb);
@@ -475,32 +476,62 @@ int smem_optin(int q) {
 
 }  // namespace
 
-// Sweep buffers for batches of up to nb right-hand sides (grown on demand; a
-// capture made for smaller buffers is dropped).
+// Workspace of the current lane for batches of up to nb right-hand sides (grown on
+// demand; the lane's graphs, made for smaller buffers, are dropped).
+static void lane_graphs_free(ls_handle::SweepLane& W) {
+    for (int b = 0; b <= kMaxBatch; ++b) {
+        if (W.exec[b]) cudaGraphExecDestroy(W.exec[b]);
+        if (W.graph[b]) cudaGraphDestroy(W.graph[b]);
+        W.exec[b] = nullptr;
+        W.graph[b] = nullptr;
+        W.nodes[b] = 0;
+    }
+}
+
 int ls_sweep_reserve(ls_handle* h, int nb) {
-    if (nb <= h->nb_cap) return LS_OK;
-    ls_bd_graph_free(h);
+    ls_handle::SweepLane& W = h->lanes[h->lane];
+    if (nb <= W.nb_cap) return LS_OK;
+    lane_graphs_free(W);
     const size_t cnt = (size_t)h->L * h->n * h->q * nb;
     const size_t es = h->prec == LS_MIXED ? sizeof(float2) : sizeof(double2);
     const size_t N = (size_t)h->n * h->n;
-    void* ptrs[] = {h->srhs, h->ssol, h->strace, h->vtmp, h->bd_in, h->bd_out};
+    void* ptrs[] = {W.srhs, W.ssol, W.strace, W.vtmp, W.bd_in, W.bd_out};
     for (void* p : ptrs) cudaFree(p);
-    h->srhs = h->ssol = h->strace = h->vtmp = nullptr;
-    h->bd_in = h->bd_out = nullptr;
-    h->nb_cap = 0;
-    LS_CUDA(cudaMalloc(&h->srhs, es * cnt));
-    LS_CUDA(cudaMalloc(&h->ssol, es * cnt));
-    LS_CUDA(cudaMalloc(&h->strace, es * (size_t)h->L * h->n * nb));
-    LS_CUDA(cudaMalloc(&h->vtmp, sizeof(double2) * N * 4 * nb));
-    LS_CUDA(cudaMalloc(&h->bd_in, sizeof(double2) * N * nb));
-    LS_CUDA(cudaMalloc(&h->bd_out, sizeof(double2) * N * nb));
-    h->nb_cap = nb;
+    W.srhs = W.ssol = W.strace = W.vtmp = nullptr;
+    W.bd_in = W.bd_out = nullptr;
+    W.nb_cap = 0;
+    LS_CUDA(cudaMalloc(&W.srhs, es * cnt));
+    LS_CUDA(cudaMalloc(&W.ssol, es * cnt));
+    LS_CUDA(cudaMalloc(&W.strace, es * (size_t)h->L * h->n * nb));
+    LS_CUDA(cudaMalloc(&W.vtmp, sizeof(double2) * N * 4 * nb));
+    LS_CUDA(cudaMalloc(&W.bd_in, sizeof(double2) * N * nb));
+    LS_CUDA(cudaMalloc(&W.bd_out, sizeof(double2) * N * nb));
+    W.nb_cap = nb;
     return LS_OK;
+}
+
+void ls_lanes_free(ls_handle* h) {
+    for (auto& W : h->lanes) {
+        lane_graphs_free(W);
+        void* ptrs[] = {W.srhs, W.ssol, W.strace, W.vtmp, W.bd_in, W.bd_out};
+        for (void* p : ptrs) cudaFree(p);
+        if (W.stream) cudaStreamDestroy(W.stream);
+        if (W.done) cudaEventDestroy(W.done);
+        W = ls_handle::SweepLane{};
+    }
+    if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+    h->ev_fork = nullptr;
 }
 
 int ls_sweep_alloc(ls_handle* h) {
     if (h->prec == LS_MIXED) LS_TRY(smem_optin<float>(h->q));
     else LS_TRY(smem_optin<double>(h->q));
+    for (int k = 1; k < ls_handle::kLanes; ++k) {
+        LS_CUDA(cudaStreamCreateWithFlags(&h->lanes[k].stream, cudaStreamNonBlocking));
+        LS_CUDA(cudaEventCreateWithFlags(&h->lanes[k].done, cudaEventDisableTiming));
+    }
+    LS_CUDA(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
+    h->lane = 0;
     return ls_sweep_reserve(h, 1);
 }
 
@@ -510,7 +541,7 @@ int ls_sweep_dir_b(ls_handle* h, int dir, const double2* g, double2* v, int nb) 
     if (nb < 1 || nb > kMaxBatch || (h->prec != LS_MIXED && nb > 4)) return LS_EINVAL;
     LS_TRY(ls_sweep_reserve(h, nb));  // no-op when called inside a capture (reserved beforehand)
     const size_t N = (size_t)h->n * h->n;
-    double2* t0 = static_cast<double2*>(h->vtmp);
+    double2* t0 = static_cast<double2*>(h->lanes[h->lane].vtmp);
     double2* t1 = t0 + N * nb;
     if (dir == 0) {
         if (h->prec == LS_MIXED) return sweep_impl<float>(h, 0, g, v, nb);
@@ -528,7 +559,7 @@ int ls_sweep_dir(ls_handle* h, int dir, const double2* g, double2* v) { return l
 // u2 = Alg. 1 vertical (g - C u1).
 static int bd_direct(ls_handle* h, const double2* g, double2* v, int nb) {
     const size_t N = (size_t)h->n * h->n;
-    double2* u1 = static_cast<double2*>(h->vtmp) + 2 * N * nb;
+    double2* u1 = static_cast<double2*>(h->lanes[h->lane].vtmp) + 2 * N * nb;
     double2* e = u1 + N * nb;
     LS_TRY(ls_sweep_dir_b(h, 0, g, u1, nb));
     LS_TRY(ls_stencil_apply_b(h, 0, 2, u1, g, e, nb));   // e = g - C u1
@@ -538,13 +569,7 @@ static int bd_direct(ls_handle* h, const double2* g, double2* v, int nb) {
 }
 
 void ls_bd_graph_free(ls_handle* h) {
-    for (int b = 0; b <= kMaxBatch; ++b) {
-        if (h->bd_exec[b]) cudaGraphExecDestroy(h->bd_exec[b]);
-        if (h->bd_graph[b]) cudaGraphDestroy(h->bd_graph[b]);
-        h->bd_exec[b] = nullptr;
-        h->bd_graph[b] = nullptr;
-        h->bd_nodes[b] = 0;
-    }
+    for (auto& W : h->lanes) lane_graphs_free(W);
 }
 
 // Capture Algorithm 2 for nb right-hand sides on the staging buffers once (the
@@ -559,7 +584,7 @@ static int bd_capture(ls_handle* h, int nb) {
     cudaGraph_t graph = nullptr;
     cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
-        rc = bd_direct(h, h->bd_in, h->bd_out, nb);
+        rc = bd_direct(h, h->lanes[h->lane].bd_in, h->lanes[h->lane].bd_out, nb);
         e = cudaStreamEndCapture(cap, &graph);
     }
     h->stream = saved;
@@ -577,9 +602,10 @@ static int bd_capture(ls_handle* h, int nb) {
         cudaGraphDestroy(graph);
         return ls_cuda_fail(e);
     }
-    h->bd_graph[nb] = graph;
-    h->bd_exec[nb] = exec;
-    h->bd_nodes[nb] = nodes;
+    ls_handle::SweepLane& W = h->lanes[h->lane];
+    W.graph[nb] = graph;
+    W.exec[nb] = exec;
+    W.nodes[nb] = nodes;
     return LS_OK;
 }
 
@@ -587,13 +613,53 @@ int ls_bd_b(ls_handle* h, const double2* g, double2* v, int nb) {
     if (nb < 1 || nb > kMaxBatch || (h->prec != LS_MIXED && nb > 4)) return LS_EINVAL;
     LS_TRY(ls_sweep_reserve(h, nb));
     if (!h->opts.use_graphs) return bd_direct(h, g, v, nb);
-    if (!h->bd_exec[nb]) LS_TRY(bd_capture(h, nb));
+    ls_handle::SweepLane& W = h->lanes[h->lane];
+    if (!W.exec[nb]) LS_TRY(bd_capture(h, nb));
     const size_t N = (size_t)h->n * h->n;
-    LS_CUDA(cudaMemcpyAsync(h->bd_in, g, sizeof(double2) * N * nb, cudaMemcpyDeviceToDevice, h->stream));
-    LS_CUDA(cudaGraphLaunch(h->bd_exec[nb], h->stream));
-    h->launches += h->bd_nodes[nb];
-    LS_CUDA(cudaMemcpyAsync(v, h->bd_out, sizeof(double2) * N * nb, cudaMemcpyDeviceToDevice, h->stream));
+    LS_CUDA(cudaMemcpyAsync(W.bd_in, g, sizeof(double2) * N * nb, cudaMemcpyDeviceToDevice, h->stream));
+    LS_CUDA(cudaGraphLaunch(W.exec[nb], h->stream));
+    h->launches += W.nodes[nb];
+    LS_CUDA(cudaMemcpyAsync(v, W.bd_out, sizeof(double2) * N * nb, cudaMemcpyDeviceToDevice, h->stream));
     return LS_OK;
+}
+
+// Algorithm 2 for nb right-hand sides in chunks of `chunk`: chunk c runs on lane
+// c mod kLanes, each lane with its own workspace and stream, so consecutive
+// chunks' chains of dependent launches overlap on the GPU.  Ordered after the
+// work already on the handle's stream; the handle's stream waits for all chunks.
+int ls_bd_lanes(ls_handle* h, const double2* g, double2* v, int nb, int chunk) {
+    if (chunk < 1) return LS_EINVAL;
+    const size_t N = (size_t)h->n * h->n;
+    const int nchunks = (nb + chunk - 1) / chunk;
+    if (nchunks == 1) return ls_bd_b(h, g, v, nb);
+    cudaStream_t main = h->stream;
+    LS_CUDA(cudaEventRecord(h->ev_fork, main));
+    bool used[ls_handle::kLanes] = {};
+    int rc = LS_OK;
+    for (int c = 0; c < nchunks && rc == LS_OK; ++c) {
+        const int k = c % ls_handle::kLanes;
+        const int b0 = c * chunk, cnt = nb - b0 < chunk ? nb - b0 : chunk;
+        ls_handle::SweepLane& W = h->lanes[k];
+        if (k > 0 && !used[k]) {
+            const cudaError_t e = cudaStreamWaitEvent(W.stream, h->ev_fork, 0);
+            if (e != cudaSuccess) {
+                rc = ls_cuda_fail(e);
+                break;
+            }
+        }
+        used[k] = true;
+        h->stream = k > 0 ? W.stream : main;
+        h->lane = k;
+        rc = ls_bd_b(h, g + b0 * N, v + b0 * N, cnt);
+        h->stream = main;
+        h->lane = 0;
+    }
+    for (int k = 1; k < ls_handle::kLanes; ++k) {  // join, also after a failure
+        if (!used[k]) continue;
+        cudaEventRecord(h->lanes[k].done, h->lanes[k].stream);
+        cudaStreamWaitEvent(main, h->lanes[k].done, 0);
+    }
+    return rc;
 }
 
 int ls_bd(ls_handle* h, const double2* g, double2* v) { return ls_bd_b(h, g, v, 1); }
@@ -604,12 +670,12 @@ int ls_strip_solve(ls_handle* h, int dir, int layer, const double2* b, double2* 
     const unsigned nblk = (unsigned)((cnt + 255) / 256);
     const size_t SB = (size_t)h->L * cnt;
     if (h->prec == LS_MIXED) {
-        float2* s = static_cast<float2*>(h->ssol);
+        float2* s = static_cast<float2*>(h->lanes[0].ssol);
         LS_LAUNCH(h, k_strip_in<float>, nblk, 256, 0, n, q, b, s);
         LS_TRY(cr_solve<float>(h, dir, layer, s, SB, 1));
         LS_LAUNCH(h, k_strip_out<float>, nblk, 256, 0, n, q, s, x);
     } else {
-        double2* s = static_cast<double2*>(h->ssol);
+        double2* s = static_cast<double2*>(h->lanes[0].ssol);
         LS_LAUNCH(h, k_strip_in<double>, nblk, 256, 0, n, q, b, s);
         LS_TRY(cr_solve<double>(h, dir, layer, s, SB, 1));
         LS_LAUNCH(h, k_strip_out<double>, nblk, 256, 0, n, q, s, x);

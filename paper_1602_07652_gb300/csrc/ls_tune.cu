@@ -39,14 +39,9 @@ struct BdArg {
     double2* v;
     int nrhs, chunk;
 };
-int run_bd(ls_handle* h, void* a) {
+int run_bd(ls_handle* h, void* a) {  // as the batched solve runs it: chunks on concurrent lanes
     auto* p = static_cast<BdArg*>(a);
-    const size_t N = (size_t)h->n * h->n;
-    for (int b0 = 0; b0 < p->nrhs; b0 += p->chunk) {
-        const int c = p->nrhs - b0 < p->chunk ? p->nrhs - b0 : p->chunk;
-        LS_TRY(ls_bd_b(h, p->g + b0 * N, p->v + b0 * N, c));
-    }
-    return LS_OK;
+    return ls_bd_lanes(h, p->g, p->v, p->nrhs, p->chunk);
 }
 
 }  // namespace
@@ -106,4 +101,13 @@ extern "C" int ls_autotune(ls_handle* h, int nrhs, int reps, ls_tuning* out) {
     cudaFree(buf);
     if (rc == LS_OK && out) *out = t;
     return rc;
+}
+
+extern "C" int ls_set_shapes(ls_handle* h, int fft_variant, int bd_chunk) {
+    if (!h || fft_variant < 0 || fft_variant >= ls_handle::kFftVariants) return LS_EINVAL;
+    const int cap = h->prec == LS_MIXED ? kMaxBatch : 4;
+    if (bd_chunk < 0 || bd_chunk > cap) return LS_EINVAL;
+    h->fft_variant = fft_variant;
+    h->bd_chunk = bd_chunk;
+    return LS_OK;
 }

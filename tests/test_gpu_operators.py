@@ -92,6 +92,22 @@ def test_fp32_apply_every_transform_length(n, L):
     s.close()
 
 
+# every column-pass tile shape of the autotuner gives the same LS-apply
+@pytest.mark.parametrize("n,L", [(100, 4), (300, 6), (1000, 10)])
+def test_fp32_apply_every_tile_shape(n, L):
+    w = inputs.omega_for_ppw(n, 10.0)
+    m = inputs.bump_medium(n, nbumps=6, seed=n + 2)
+    s = binding.Solver(cuda(m), w, layers=L, ext=3, precision=binding.LS_MIXED)
+    u = inputs.random_field(n, 5)
+    y_ref = greens.apply_H(u, m, 1.0 / n, w)
+    for v in range(6):
+        s.ls_set_shapes(v)
+        assert rel(s.ls_apply_mixed(cuda(u)).cpu().numpy(), y_ref) < 2e-5, v
+    with pytest.raises(binding.LSError):
+        s.ls_set_shapes(6)
+    s.close()
+
+
 def test_zero_medium_apply_is_identity_and_rhs_zero():
     n = 32
     s = binding.Solver(cuda(np.zeros((n, n))), 2 * math.pi * 4, layers=2, ext=4)
