@@ -266,8 +266,9 @@ def run_reference(args):
     return 0
 
 
-# outer / inner iteration counts of the benchmark workload on the GPU (used by the reference arm)
-REF_COUNTS = {2048: (6, 30)}
+# outer / inner iteration counts per right-hand side of the benchmark workload, measured by the
+# GPU solver (used by the reference arm to project the oracle's per-iteration cost)
+REF_COUNTS = {2048: (3.86, 11.9)}
 
 
 def run_ours(args):
@@ -383,6 +384,9 @@ def run_ours(args):
         # u (16 n^2) and writes y (16 n^2): 124 n^2 bytes.
         bytes_apply = (200.0 if args.fp64 else 124.0) * n * n   # FP64: 16 + 8 + 32 + 32 + 16 + 32 + 32 + 32 n^2
         ach = bytes_apply / (t_app / n_app / 1e3) / 1e9 if n_app else None
+        # DRAM read + write bytes of one apply (three passes) from the ncu capture summarised in
+        # profiles/ls_apply_mixed_2048_fft16.md: column-pass shape 2 at 2048^2 only
+        traffic = 380.1e6 if (not args.fp64 and n == 2048 and tune.get("fft_variant") == 2) else None
         outer = statistics.mean(st["outer_iters"] for st in stats) / B  # per right-hand side
         inner = statistics.mean(st["inner_iters_total"] for st in stats) / B
         value = ms / 1e3 / (args.steps * B * world)
@@ -392,7 +396,7 @@ def run_ours(args):
                "data": "synthetic",
                "config": config_dict(wl, "fp64" if args.fp64 else "mixed", rhs_per_step=B),
                "roofline": {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
-                            "frac": (ach / hbm) if ach else None, "traffic": None,
+                            "frac": (ach / hbm) if ach else None, "traffic": traffic,
                             "kernel": "LS-apply (3 FFT passes), " + ("FP64" if args.fp64 else
                                                                       "FP32 arithmetic, FP64 I/O"),
                             "algorithmic_bytes": bytes_apply, "peak_source": src,
