@@ -152,10 +152,13 @@ int ls_solve_plane_wave(ls_handle* h, double theta, double tol, ls_c64* u, ls_st
 
 /* ls_solve_batch -- nrhs independent solves H u_b = f_b (1 <= nrhs <= LS_MAX_BATCH)
  * in one call: f and u hold nrhs fields back to back (field b at offset b*nz*nx).
- * The same H serves every right-hand side (Sec. 6 solves one scatterer for many
+ * The same H serves every right-hand side (Sec. 5 solves one scatterer for 64
  * incident waves); the members iterate in lockstep, each with its own Krylov
  * spaces and stopping test, and share every application of Algorithm 2 (its
- * factor traffic and its chain of launches).  Each u_b is what ls_solve would
+ * factor traffic and its chain of launches): the batch is cut into chunks of
+ * up to 8 (ls_autotune / ls_set_shapes pick the size) whose Algorithm 2 chains
+ * run concurrently on up to 8 streams of the handle; chunks whose members have
+ * all converged are skipped.  Each u_b is what ls_solve would
  * return for f_b up to rounding.  stats: iteration counts summed over the
  * members; refine_steps and true_rel_residual the largest over the members.
  * Device memory: the Krylov spaces grow to nrhs * (outer_restart +

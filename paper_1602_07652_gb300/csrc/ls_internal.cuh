@@ -166,7 +166,7 @@ struct ls_handle {
         cudaStream_t stream = nullptr;  // lane 0 runs on the handle's stream
         cudaEvent_t done = nullptr;
     };
-    static constexpr int kLanes = 4;
+    static constexpr int kLanes = 8;
     SweepLane lanes[kLanes];
     int lane = 0;              // lane the sweep functions use (set around concurrent chunks)
     void* vtmp2 = nullptr;
@@ -264,7 +264,8 @@ int ls_sweep_dir(ls_handle* h, int dir, const double2* g, double2* v);   // Algo
 int ls_sweep_dir_b(ls_handle* h, int dir, const double2* g, double2* v, int nb);
 int ls_sweep_reserve(ls_handle* h, int nb);
 int ls_bd_b(ls_handle* h, const double2* g, double2* v, int nb);         // Algorithm 2, nb right-hand sides
-int ls_bd_lanes(ls_handle* h, const double2* g, double2* v, int nb, int chunk);  // chunks on concurrent lanes
+int ls_bd_lanes(ls_handle* h, const double2* g, double2* v, int nb, int chunk,
+                const unsigned char* on = nullptr);  // chunks on concurrent lanes, idle chunks skipped
 void ls_lanes_free(ls_handle* h);
 int ls_bd(ls_handle* h, const double2* g, double2* v);                   // Algorithm 2
 void ls_bd_graph_free(ls_handle* h);

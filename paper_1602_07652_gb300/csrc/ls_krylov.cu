@@ -135,7 +135,7 @@ int apply_pc_b(ls_handle* h, Pc pc, double2* v, double2* z, int nb, const unsign
                 LS_TRY(ls_sweep_dir_b(h, 0, v + b0 * N, z + b0 * N, cnt));
             }
         } else {
-            LS_TRY(ls_bd_lanes(h, v, z, top, ch));  // chunks run concurrently
+            LS_TRY(ls_bd_lanes(h, v, z, top, ch, on));  // chunks run concurrently; idle ones are skipped
         }
         return ls_timing_end(h, 1);
     }
@@ -435,10 +435,14 @@ int ls_outer_solve_b(ls_handle* h, int nb, const double2* f, double tol, double2
         for (int i = 0; i < nb; ++i) {
             if (!act[i]) continue;
             double2* di = d + i * N;
-            LS_TRY(ls_timing_begin(h));
-            LS_TRY(ls_apply64(h, u + i * N, di));  // d = H u (FP64)
-            LS_TRY(ls_timing_end(h, 2));
-            LS_TRY(ls_vec_axpby(h, make_double2(1, 0), f + i * N, make_double2(-1, 0), di));  // d = f - H u
+            if (steps[i] == 0 && !use_x0) {  // u = 0: the residual is f itself
+                LS_TRY(ls_vec_copy(h, f + i * N, di));
+            } else {
+                LS_TRY(ls_timing_begin(h));
+                LS_TRY(ls_apply64(h, u + i * N, di));  // d = H u (FP64)
+                LS_TRY(ls_timing_end(h, 2));
+                LS_TRY(ls_vec_axpby(h, make_double2(1, 0), f + i * N, make_double2(-1, 0), di));  // d = f - H u
+            }
             double nr;
             LS_TRY(ls_vec_norm(h, di, &nr));
             relres[i] = nr / nf[i];

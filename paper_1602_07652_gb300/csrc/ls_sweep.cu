@@ -36,6 +36,8 @@
 // strips at offset b * SB, its grid vectors at offset b * N).  A reduction step
 // loads each factor matrix once and applies it to all nb vectors, so a batch
 // shares both the factor traffic and the chain of dependent launches.
+#include <vector>
+
 #include "ls_internal.cuh"
 #include "ls_strip.cuh"
 
@@ -623,21 +625,34 @@ int ls_bd_b(ls_handle* h, const double2* g, double2* v, int nb) {
     return LS_OK;
 }
 
-// Algorithm 2 for nb right-hand sides in chunks of `chunk`: chunk c runs on lane
-// c mod kLanes, each lane with its own workspace and stream, so consecutive
-// chunks' chains of dependent launches overlap on the GPU.  Ordered after the
-// work already on the handle's stream; the handle's stream waits for all chunks.
-int ls_bd_lanes(ls_handle* h, const double2* g, double2* v, int nb, int chunk) {
+// Algorithm 2 for nb right-hand sides in chunks of `chunk`: the k-th chunk that
+// holds a member with on[b] (all, if on is null) runs on lane k mod kLanes, each
+// lane with its own workspace and stream, so the chunks' chains of dependent
+// launches overlap on the GPU; chunks without such a member are skipped (their
+// outputs are left as they were).  Ordered after the work already on the
+// handle's stream; the handle's stream waits for all chunks.
+int ls_bd_lanes(ls_handle* h, const double2* g, double2* v, int nb, int chunk, const unsigned char* on) {
     if (chunk < 1) return LS_EINVAL;
     const size_t N = (size_t)h->n * h->n;
     const int nchunks = (nb + chunk - 1) / chunk;
-    if (nchunks == 1) return ls_bd_b(h, g, v, nb);
+    std::vector<int> run;
+    for (int c = 0; c < nchunks; ++c) {
+        bool any = !on;
+        for (int b = c * chunk; b < nb && b < (c + 1) * chunk && !any; ++b) any = on[b] != 0;
+        if (any) run.push_back(c);
+    }
+    if (run.empty()) return LS_OK;
+    if (run.size() == 1) {
+        const int b0 = run[0] * chunk, cnt = nb - b0 < chunk ? nb - b0 : chunk;
+        return ls_bd_b(h, g + b0 * N, v + b0 * N, cnt);
+    }
     cudaStream_t main = h->stream;
     LS_CUDA(cudaEventRecord(h->ev_fork, main));
     bool used[ls_handle::kLanes] = {};
     int rc = LS_OK;
-    for (int c = 0; c < nchunks && rc == LS_OK; ++c) {
-        const int k = c % ls_handle::kLanes;
+    for (size_t ci = 0; ci < run.size() && rc == LS_OK; ++ci) {
+        const int c = run[ci];
+        const int k = (int)(ci % ls_handle::kLanes);
         const int b0 = c * chunk, cnt = nb - b0 < chunk ? nb - b0 : chunk;
         ls_handle::SweepLane& W = h->lanes[k];
         if (k > 0 && !used[k]) {

@@ -1,6 +1,6 @@
 """Batched right-hand sides through the C ABI (GPU).
 
-A batch shares H (one scatterer, many incident directions, Sec. 6) and must
+A batch shares H (one scatterer, many incident directions, Sec. 5) and must
 give, member by member, what the one-at-a-time entry points give:
   * Algorithm 2 on a block of fields equals Algorithm 2 on each field;
   * the lockstep batched solve reaches the tolerance on every member and its
