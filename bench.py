@@ -271,6 +271,32 @@ def run_reference(args):
 REF_COUNTS = {2048: (3.86, 11.9)}
 
 
+N_DIRECTIONS = 64
+
+
+def direction(base, k, rank, world):
+    """Incident angle of a rank's k-th right-hand side: the 64 directions on the circle,
+    dealt round-robin over the ranks, so no two ranks solve the same direction while
+    k * world < 64 (independent right-hand sides: the units the ranks share out)."""
+    return base + 2 * math.pi * ((k * world + rank) % N_DIRECTIONS) / N_DIRECTIONS
+
+
+def max_over_ranks(x, world, device):
+    """The largest of every rank's x (the job's time is its slowest rank's)."""
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return t.item()
+
+
+def job_seconds_per_rhs(ms_max, steps, batch, world):
+    """Whole-job throughput metric: the slowest rank's time over every rank's right-hand sides."""
+    return ms_max / 1e3 / (steps * batch * world)
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -309,8 +335,8 @@ def run_ours(args):
     f = torch.empty((B, n, n), dtype=torch.complex128, device="cuda")
     u = torch.empty_like(f)
 
-    def theta(k):  # 64 directions on the circle, rank-strided
-        return base + 2 * math.pi * ((k * world + rank) % 64) / 64
+    def theta(k):
+        return direction(base, k, rank, world)
 
     def step(k):  # B incident plane waves: right-hand sides on the device, one batched solve
         for b in range(B):
@@ -339,11 +365,7 @@ def run_ours(args):
     clk = clocks.stop()
     if world > 1:
         dist.barrier()
-    ms = ev0.elapsed_time(ev1)
-    if world > 1:
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = t.item()
+    ms = max_over_ranks(ev0.elapsed_time(ev1), world, "cuda")
     s.ls_set_timing(False)
     # end to end through the C ABI with host buffers: the same directions as the timed
     # steps, right-hand sides prepared in pinned host memory beforehand; each step copies
@@ -361,11 +383,7 @@ def run_ours(args):
         t0 = time.perf_counter()
         for k in range(args.e2e_steps):
             s.ls_solve_batch_host(f_hosts[k], wl["tol"], u_host)
-        e2e = (time.perf_counter() - t0) / (args.e2e_steps * B)
-        if world > 1:
-            t = torch.tensor([e2e], device="cuda", dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e = t.item()
+        e2e = max_over_ranks(time.perf_counter() - t0, world, "cuda") / (args.e2e_steps * B)
     if rank == 0:
         hbm, src = peaks()
         try:
@@ -389,7 +407,7 @@ def run_ours(args):
         traffic = 380.1e6 if (not args.fp64 and n == 2048 and tune.get("fft_variant") == 2) else None
         outer = statistics.mean(st["outer_iters"] for st in stats) / B  # per right-hand side
         inner = statistics.mean(st["inner_iters_total"] for st in stats) / B
-        value = ms / 1e3 / (args.steps * B * world)
+        value = job_seconds_per_rhs(ms, args.steps, B, world)
         out = {"metric": METRIC, "value": value, "unit": "s/RHS", "n_gpus": world, "steps": args.steps,
                "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": False,
                "scaling": "weak", "vs_baseline": None, "dtype": "c128" if args.fp64 else "mixed c64/c128",

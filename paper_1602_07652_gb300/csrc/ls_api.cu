@@ -70,7 +70,7 @@ void release(ls_handle* h) {
         h->hostbufs = nullptr;
     }
     void* ptrs[] = {h->m64, h->m32, h->mT64, h->ghat64, h->ghat32, h->tw64, h->tw32, h->fftws, h->incx,
-                    h->incz, h->dtabs, h->vtmp2, h->red};
+                    h->incz, h->dtabs, h->red};
     for (void* p : ptrs) cudaFree(p);
     if (h->red_host) cudaFreeHost(h->red_host);
     if (h->ev0) cudaEventDestroy(h->ev0);

@@ -169,7 +169,6 @@ struct ls_handle {
     static constexpr int kLanes = 8;
     SweepLane lanes[kLanes];
     int lane = 0;              // lane the sweep functions use (set around concurrent chunks)
-    void* vtmp2 = nullptr;
 
     // Krylov workspaces (FP64): the context of ls_krylov.cu and the staging buffers of
     // the host-array entry points, owned by the handle (no library-global state)
