@@ -199,7 +199,10 @@ int ls_solve_group(int nprob, ls_handle* const* hs, const ls_c64* const* f, doub
  *     transforms on 4-column tiles;
  *   - the band-block batching of Algorithm 2 for nrhs right-hand sides: bd_chunk
  *     = right-hand sides per pass over the local-solve factors (1, 2, 4, 8;
- *     FP64 up to 4).
+ *     FP64 up to 4), chunks running concurrently on separate streams, and
+ *     cr_split = whether the block-cyclic-reduction steps of levels with few
+ *     blocks split each block over several CTAs (partial sums combined in a
+ *     fixed order, so results are reproducible for a given choice).
  * Each candidate runs once, then reps times under CUDA events; the fastest is
  * kept by the handle for later applies and batched solves (results agree up to
  * rounding whichever is chosen).  Before ls_factor only the FFT shape is tuned
@@ -210,6 +213,9 @@ typedef struct {
     int bd_chunk;       /* chosen right-hand sides per Algorithm 2 pass                */
     double fft_ms[6];   /* LS-apply (FP64 I/O, FP32 arithmetic) per variant; -1: n/a   */
     double bd_ms[4];    /* Algorithm 2 ms per right-hand side, chunks 1, 2, 4, 8 (0: not tried) */
+    double bd_ms_nosplit[4]; /* the same without splitting the blocks of small levels        */
+    int cr_split;       /* 1: the reduction steps of levels with fewer blocks than SMs split
+                           each block's columns over several CTAs; 0: one CTA per block     */
 } ls_tuning;
 int ls_autotune(ls_handle* h, int nrhs, int reps, ls_tuning* out);
 

@@ -57,11 +57,13 @@ class Stats(ctypes.Structure):
 
 class Tuning(ctypes.Structure):
     _fields_ = [("fft_variant", ctypes.c_int), ("bd_chunk", ctypes.c_int),
-                ("fft_ms", ctypes.c_double * 6), ("bd_ms", ctypes.c_double * 4)]
+                ("fft_ms", ctypes.c_double * 6), ("bd_ms", ctypes.c_double * 4),
+                ("bd_ms_nosplit", ctypes.c_double * 4), ("cr_split", ctypes.c_int)]
 
     def as_dict(self):
         return {"fft_variant": self.fft_variant, "bd_chunk": self.bd_chunk,
-                "fft_ms": list(self.fft_ms), "bd_ms_per_rhs": list(self.bd_ms)}
+                "fft_ms": list(self.fft_ms), "bd_ms_per_rhs": list(self.bd_ms),
+                "bd_ms_per_rhs_nosplit": list(self.bd_ms_nosplit), "cr_split": self.cr_split}
 
 
 _P = ctypes.c_void_p

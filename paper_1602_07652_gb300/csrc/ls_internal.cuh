@@ -163,6 +163,8 @@ struct ls_handle {
         cudaGraphExec_t exec[9] = {};
         long long nodes[9] = {};
         int nb_cap = 0;
+        void* cr_part = nullptr;        // partial sums of split reduction steps
+        unsigned* cr_cnt = nullptr;     // arrival counters of split reduction steps (kept at 0)
         cudaStream_t stream = nullptr;  // lane 0 runs on the handle's stream
         cudaEvent_t done = nullptr;
     };
@@ -188,6 +190,7 @@ struct ls_handle {
                                // 4 = 1-column tiles; 5 = 2-column tiles.  1: generic radix-8 4-column tiles
     static constexpr int kFftVariants = 6;
     int bd_chunk = 0;          // right-hand sides per Algorithm 2 chain (0: the largest supported)
+    int cr_split = 1;          // 1: reduction steps of small levels split blocks over several CTAs
 
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     double t_apply_ms = 0, t_sweep_ms = 0, t_apply64_ms = 0;

@@ -62,16 +62,27 @@ constexpr int kMvThreads = 32 * kMvWarps;
 //   MODE 1 (forward):        x_j = x_j - F x_{j-1} - G x_{j+1}          (even j)
 //   MODE 2 (backward):       x_j = D^{-1} x_j - P x_{j-1} - Q x_{j+1}   (odd j)
 //   MODE 3 (top block):      x_0 = D^{-1} x_0
+//
+// Split levels (S > 1, for levels with fewer blocks than the GPU has SMs): S CTAs
+// share a block, CTA p taking the columns [p q / S, (p+1) q / S) of its matrices.
+// Each writes its partial sums to `partial`, and the CTA that arrives last at the
+// block's counter (an atomic increment; nobody waits) adds the S partials in the
+// fixed order p = 0..S-1, writes the block's result and resets the counter.  The
+// result does not depend on which CTA arrives last, and x_j is overwritten only
+// after every CTA of the block has read it.
 template <typename T, int RPT, int MODE, int NB>
 __global__ void __launch_bounds__(kMvThreads, NB >= 4 ? 2 : 1) k_cr_step(int q, int k, int nk, Pool<T> pool, size_t off_a,
                                                        size_t off_b, size_t off_c, cpx_t<T>* __restrict__ x,
-                                                       size_t SB, int nb) {
+                                                       size_t SB, int nb, int S, cpx_t<T>* __restrict__ partial,
+                                                       unsigned* __restrict__ counter) {
     using C = cpx_t<T>;
     constexpr int NM = MODE == 1 ? 2 : (MODE == 2 ? 3 : 1);
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ int last;
     C* vin = reinterpret_cast<C*>(smem_raw);     // [NM][NB][q]
     C* red = vin + (size_t)NM * NB * q;          // [kMvWarps][NB][q]
-    const int idx = blockIdx.x;
+    const int idx = blockIdx.x / S, sp = blockIdx.x - idx * S;
+    const int cbeg = q * sp / S, cend = q * (sp + 1) / S;
     const size_t s = (size_t)1 << k;
     const int j = MODE == 1 ? 2 * idx : (MODE == 3 ? 0 : 2 * idx + 1);
     const bool hw = j >= 1, he = j + 1 < nk;
@@ -115,7 +126,7 @@ __global__ void __launch_bounds__(kMvThreads, NB >= 4 ? 2 : 1) k_cr_step(int q, 
 #pragma unroll
         for (int b = 0; b < NB; ++b) part[kk][b] = czero<C>();
 #pragma unroll 2
-    for (int c = warp; c < q; c += kMvWarps) {
+    for (int c = cbeg + warp; c < cend; c += kMvWarps) {
         C a[NM][RPT];
 #pragma unroll
         for (int t = 0; t < NM; ++t)
@@ -141,13 +152,37 @@ __global__ void __launch_bounds__(kMvThreads, NB >= 4 ? 2 : 1) k_cr_step(int q, 
             for (int b = 0; b < NB; ++b) red[((size_t)warp * NB + b) * q + r] = part[kk][b];
     }
     __syncthreads();
+    if (S == 1) {
+        for (int o = threadIdx.x; o < nb * q; o += kMvThreads) {
+            const int b = o / q, r = o % q;
+            C sum = czero<C>();
+            for (int w = 0; w < kMvWarps; ++w) sum = sum + red[((size_t)w * NB + b) * q + r];
+            C* xj = x + (size_t)b * SB + ((size_t)j * s) * q;
+            xj[r] = MODE == 1 ? xj[r] + sum : sum;
+        }
+        return;
+    }
+    C* mine = partial + ((size_t)idx * S + sp) * NB * q;
     for (int o = threadIdx.x; o < nb * q; o += kMvThreads) {
         const int b = o / q, r = o % q;
         C sum = czero<C>();
         for (int w = 0; w < kMvWarps; ++w) sum = sum + red[((size_t)w * NB + b) * q + r];
-        C* xj = x + (size_t)b * SB + ((size_t)j * s) * q;
-        xj[r] = MODE == 1 ? xj[r] + sum : sum;
+        mine[(size_t)b * q + r] = sum;
     }
+    __threadfence();   // the partial is visible before the counter says so
+    __syncthreads();
+    if (threadIdx.x == 0) last = atomicAdd(&counter[idx], 1u) == (unsigned)(S - 1);
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    for (int o = threadIdx.x; o < nb * q; o += kMvThreads) {
+        const int b = o / q, r = o % q;
+        C tot = czero<C>();
+        for (int p = 0; p < S; ++p) tot = tot + __ldcg(&partial[(((size_t)idx * S + p) * NB + b) * q + r]);
+        C* xj = x + (size_t)b * SB + ((size_t)j * s) * q;
+        xj[r] = MODE == 1 ? xj[r] + tot : tot;
+    }
+    if (threadIdx.x == 0) counter[idx] = 0u;
 }
 
 // level 0 backward, odd blocks: x_j = y_j - D^{-1} (W_j x_{j-1} + E_j x_{j+1})
@@ -357,6 +392,16 @@ __global__ void k_add(size_t N, const double2* __restrict__ a, double2* __restri
 
 StripGeom geom_of(const ls_handle* h) { return StripGeom{h->n, h->t, h->E, h->q, h->opts.shift / h->omega}; }
 
+// CTAs per block of a reduction step: levels with fewer blocks than about two per SM
+// split each block's columns over up to kCrSplitMax CTAs (at most kCrSplitCtas CTAs in all).
+// The handle's cr_split switches it off (1 CTA per block everywhere).
+constexpr int kCrSplitCtas = 304, kCrSplitMax = 8;
+int cr_split_of(const ls_handle* h, int nblk) {
+    if (!h->cr_split) return 1;
+    int S = kCrSplitCtas / (nblk > 0 ? nblk : 1);
+    return S < 1 ? 1 : (S > kCrSplitMax ? kCrSplitMax : S);
+}
+
 template <typename T, int RPT, int NB>
 int cr_solve_rpt(ls_handle* h, int dir, int l, cpx_t<T>* x, size_t SB, int nb) {
     using C = cpx_t<T>;
@@ -373,22 +418,32 @@ int cr_solve_rpt(ls_handle* h, int dir, int l, cpx_t<T>* x, size_t SB, int nb) {
     const CrLevel& l0 = F.lev[0];
     const C* cw = static_cast<const C*>(F.cw) + (size_t)l * n * 3 * q;
     const C* ce = static_cast<const C*>(F.ce) + (size_t)l * n * 3 * q;
-    if (l0.nodd)
-        LS_LAUNCH(h, (k_cr_step<T, RPT, 0, NB>), l0.nodd, kMvThreads, sm_step, q, 0, l0.nk, pool, l0.off_dinv,
-                  (size_t)0, (size_t)0, x, SB, nb);
+    const ls_handle::SweepLane& W = h->lanes[h->lane];
+    C* part = static_cast<C*>(W.cr_part);
+    unsigned* cnt = W.cr_cnt;
+    if (l0.nodd) {
+        const int S = cr_split_of(h, l0.nodd);
+        LS_LAUNCH(h, (k_cr_step<T, RPT, 0, NB>), l0.nodd * S, kMvThreads, sm_step, q, 0, l0.nk, pool, l0.off_dinv,
+                  (size_t)0, (size_t)0, x, SB, nb, S, part, cnt);
+    }
     LS_LAUNCH(h, k_l0_even<T>, dim3(l0.neven, nb), thr, 0, q, n, cw, ce, x, SB);
     for (int k = 1; k < F.K; ++k) {
         const CrLevel& lv = F.lev[k];
-        LS_LAUNCH(h, (k_cr_step<T, RPT, 1, NB>), lv.neven, kMvThreads, sm_step, q, k, lv.nk, pool, (size_t)0,
-                  lv.off_f, lv.off_g, x, SB, nb);
+        const int S = cr_split_of(h, lv.neven);
+        LS_LAUNCH(h, (k_cr_step<T, RPT, 1, NB>), lv.neven * S, kMvThreads, sm_step, q, k, lv.nk, pool, (size_t)0,
+                  lv.off_f, lv.off_g, x, SB, nb, S, part, cnt);
     }
-    LS_LAUNCH(h, (k_cr_step<T, RPT, 3, NB>), 1, kMvThreads, sm_step, q, 0, 1, pool, F.off_top, (size_t)0, (size_t)0,
-              x, SB, nb);
+    {
+        const int S = cr_split_of(h, 1);
+        LS_LAUNCH(h, (k_cr_step<T, RPT, 3, NB>), S, kMvThreads, sm_step, q, 0, 1, pool, F.off_top, (size_t)0,
+                  (size_t)0, x, SB, nb, S, part, cnt);
+    }
     for (int k = F.K - 1; k >= 1; --k) {
         const CrLevel& lv = F.lev[k];
-        if (lv.nodd)
-            LS_LAUNCH(h, (k_cr_step<T, RPT, 2, NB>), lv.nodd, kMvThreads, sm_step, q, k, lv.nk, pool, lv.off_dinv,
-                      lv.off_p, lv.off_q, x, SB, nb);
+        if (!lv.nodd) continue;
+        const int S = cr_split_of(h, lv.nodd);
+        LS_LAUNCH(h, (k_cr_step<T, RPT, 2, NB>), lv.nodd * S, kMvThreads, sm_step, q, k, lv.nk, pool, lv.off_dinv,
+                  lv.off_p, lv.off_q, x, SB, nb, S, part, cnt);
     }
     if (l0.nodd)
         LS_LAUNCH(h, (k_cr_l0_back<T, RPT, NB>), l0.nodd, kMvThreads, sm_back, q, n, cw, ce, pool, l0.off_dinv, x,
@@ -508,6 +563,11 @@ int ls_sweep_reserve(ls_handle* h, int nb) {
     LS_CUDA(cudaMalloc(&W.vtmp, sizeof(double2) * N * 4 * nb));
     LS_CUDA(cudaMalloc(&W.bd_in, sizeof(double2) * N * nb));
     LS_CUDA(cudaMalloc(&W.bd_out, sizeof(double2) * N * nb));
+    if (!W.cr_part) {  // split-level partial sums (kCrSplitCtas CTAs x 8 vectors x q) and counters
+        LS_CUDA(cudaMalloc(&W.cr_part, sizeof(double2) * kCrSplitCtas * 8 * h->q));
+        LS_CUDA(cudaMalloc(&W.cr_cnt, sizeof(unsigned) * kCrSplitCtas));
+        LS_CUDA(cudaMemset(W.cr_cnt, 0, sizeof(unsigned) * kCrSplitCtas));
+    }
     W.nb_cap = nb;
     return LS_OK;
 }
@@ -515,7 +575,7 @@ int ls_sweep_reserve(ls_handle* h, int nb) {
 void ls_lanes_free(ls_handle* h) {
     for (auto& W : h->lanes) {
         lane_graphs_free(W);
-        void* ptrs[] = {W.srhs, W.ssol, W.strace, W.vtmp, W.bd_in, W.bd_out};
+        void* ptrs[] = {W.srhs, W.ssol, W.strace, W.vtmp, W.bd_in, W.bd_out, W.cr_part, W.cr_cnt};
         for (void* p : ptrs) cudaFree(p);
         if (W.stream) cudaStreamDestroy(W.stream);
         if (W.done) cudaEventDestroy(W.done);

@@ -81,21 +81,33 @@ extern "C" int ls_autotune(ls_handle* h, int nrhs, int reps, ls_tuning* out) {
         if (!h->factored) break;
         const int cap = h->prec == LS_MIXED ? kMaxBatch : 4;
         best = 0;
-        int chunk = 1;
-        for (int k = 0, c = 1; c <= cap && rc == LS_OK; ++k, c *= 2) {
-            if (c > nrhs && c > 1) break;
-            BdArg ba{buf, buf + nrhs * N, nrhs, c};
-            float ms = 0;
-            rc = time_ms(h, reps, &ms, run_bd, &ba);
-            t.bd_ms[k] = ms / nrhs;
-            if (rc == LS_OK && (best == 0 || ms < best)) {
-                best = ms;
-                chunk = c;
+        int chunk = 1, split = 1;
+        for (int sp = 1; sp >= 0 && rc == LS_OK; --sp) {  // split reduction steps on, then off
+            if (h->cr_split != sp) {
+                h->cr_split = sp;
+                ls_bd_graph_free(h);  // the captured launches bake the grid shapes in
+            }
+            for (int k = 0, c = 1; c <= cap && rc == LS_OK; ++k, c *= 2) {
+                if (c > nrhs && c > 1) break;
+                BdArg ba{buf, buf + nrhs * N, nrhs, c};
+                float ms = 0;
+                rc = time_ms(h, reps, &ms, run_bd, &ba);
+                (sp ? t.bd_ms : t.bd_ms_nosplit)[k] = ms / nrhs;
+                if (rc == LS_OK && (best == 0 || ms < best)) {
+                    best = ms;
+                    chunk = c;
+                    split = sp;
+                }
             }
         }
         if (rc != LS_OK) break;
+        if (h->cr_split != split) {
+            h->cr_split = split;
+            ls_bd_graph_free(h);
+        }
         h->bd_chunk = chunk;
         t.bd_chunk = chunk;
+        t.cr_split = split;
     } while (0);
     cudaStreamSynchronize(h->stream);
     cudaFree(buf);
