@@ -5,7 +5,7 @@ per wavelength), medium = 20 seeded Gaussian bumps in a disk of radius 0.4
 (seed 0), 32 layers per direction extended by 10 rows, mixed precision
 (FP32 complex FFT convolution and local solves, FP64 factorisation, Arnoldi
 and residual, FP64 iterative refinement), relative residual tolerance 1e-6.
-A step is one full solve of a batch of B incident plane waves (default 16; the
+A step is one full solve of a batch of B incident plane waves (default 32; the
 paper solves 64 incident waves per medium): the right-hand sides
 f = -w^2 G (m u_I) are generated on the device and the outer flexible GMRES,
 preconditioned by Algorithm 3 (inner GMRES + Algorithm 2 sweeps), runs to the
@@ -34,7 +34,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "solve s/RHS to 1e-6 rel. residual at 2048^2; LS-apply % of HBM roofline"
 N_DEFAULT, PPW_W, LAYERS, EXT, TOL = 2048, 200, 32, 10, 1e-6
-BATCH_DEFAULT = 16  # the paper solves 64 incident waves per medium: 4 batches of 16
+BATCH_DEFAULT = 32  # the paper solves 64 incident waves per medium: 2 batches of 32
 
 
 def parse():
@@ -92,7 +92,7 @@ def config_dict(wl, prec="mixed", rhs_per_step=1):
                         "%d layers/direction ext %d, %s precision, tol %g, %s"
                         % (wl["n"], wl["n"], wl["omega"] / (2 * math.pi), wl["layers"], wl["ext"], prec, wl["tol"],
                            per),
-            "rhs_per_step": rhs_per_step, "restarts": {"outer": 20, "inner": 20}, "n": wl["n"], "omega": wl["omega"], "layers": wl["layers"], "ext": wl["ext"], "tol": wl["tol"],
+            "rhs_per_step": rhs_per_step, "restarts": {"outer": 10, "inner": 10}, "n": wl["n"], "omega": wl["omega"], "layers": wl["layers"], "ext": wl["ext"], "tol": wl["tol"],
             "l2": "inputs larger than L2: every sweep streams ~%.0f GB of local-solve factors" %
                   (4 * wl["layers"] * wl["n"] * (wl["n"] // wl["layers"] + 2 * wl["ext"]) ** 2 * 8 * 1.75 / 1e9),
             "parallelism": "replicas"}
@@ -316,7 +316,7 @@ def run_ours(args):
     o.use_graphs = 0 if args.no_graphs else 1
     # restart lengths above the iteration counts this workload needs (<= 6 outer, <= 6 inner
     # per call), so they never restart; they bound the Krylov memory of large batches
-    o.outer_restart, o.inner_restart = 20, 20
+    o.outer_restart, o.inner_restart = 10, 10
     prec = binding.LS_FP64 if args.fp64 else binding.LS_MIXED
     if args.fp64 and args.batch > 4:
         raise SystemExit("--fp64 takes batches of at most 4")

@@ -47,7 +47,7 @@ enum { LS_FP64 = 0, LS_MIXED = 1 };
 
 /* Right-hand sides per batched call: ls_solve_batch takes up to LS_MAX_BATCH;
  * ls_precond_bd_batch takes up to LS_MAX_BD_BATCH (LS_MIXED) or 4 (LS_FP64). */
-enum { LS_MAX_BATCH = 16, LS_MAX_BD_BATCH = 8 };
+enum { LS_MAX_BATCH = 32, LS_MAX_BD_BATCH = 8 };
 
 typedef struct {
     int nx, nz;       /* grid points per direction (this build requires nx == nz >= 8)      */
@@ -161,8 +161,9 @@ int ls_solve_plane_wave(ls_handle* h, double theta, double tol, ls_c64* u, ls_st
  * all converged are skipped.  Each u_b is what ls_solve would
  * return for f_b up to rounding.  stats: iteration counts summed over the
  * members; refine_steps and true_rel_residual the largest over the members.
- * Device memory: the Krylov spaces grow to nrhs * (outer_restart +
- * inner_restart + 4) fields (LS_ENOMEM if they do not fit).  Return codes as
+ * Device memory: the Krylov spaces grow to nrhs * (2 (outer_restart +
+ * inner_restart) + 7) fields (LS_ENOMEM if they do not fit): at 2048^2 and the
+ * default restarts 40 / 30, 9.9 GB per right-hand side.  Return codes as
  * ls_solve; LS_ENOCONV if any member misses the tolerance. */
 int ls_solve_batch(ls_handle* h, int nrhs, const ls_c64* f, double tol, ls_c64* u, int use_x0,
                    ls_stats* stats);

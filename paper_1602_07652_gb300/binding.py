@@ -18,7 +18,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libls.so")
 
 LS_FP64, LS_MIXED = 0, 1
-LS_MAX_BATCH, LS_MAX_BD_BATCH = 16, 8
+LS_MAX_BATCH, LS_MAX_BD_BATCH = 32, 8
 LS_PC_BD, LS_PC_GS = 0, 1
 
 
