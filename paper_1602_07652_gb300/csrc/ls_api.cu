@@ -388,12 +388,12 @@ int ls_solve_host(ls_handle* h, const ls_c64* f_host, double tol, ls_c64* u_host
 
 int ls_apply_A(ls_handle* h, const ls_c64* r, ls_c64* y) {
     if (!h || !r || !y) return LS_EINVAL;
-    return ls_stencil_apply(h, 0, 0, reinterpret_cast<const double2*>(r), nullptr, reinterpret_cast<double2*>(y));
+    return ls_stencil_apply64(h, 0, 0, reinterpret_cast<const double2*>(r), nullptr, reinterpret_cast<double2*>(y));
 }
 
 int ls_apply_C(ls_handle* h, const ls_c64* v, ls_c64* y) {
     if (!h || !v || !y) return LS_EINVAL;
-    return ls_stencil_apply(h, 0, 1, reinterpret_cast<const double2*>(v), nullptr, reinterpret_cast<double2*>(y));
+    return ls_stencil_apply64(h, 0, 1, reinterpret_cast<const double2*>(v), nullptr, reinterpret_cast<double2*>(y));
 }
 
 int ls_sweep(ls_handle* h, int dir, const ls_c64* g, ls_c64* v) {

@@ -14,11 +14,15 @@
 
 namespace {
 
-// batch member b = blockIdx.y works on v, g, y at offset b * n * n (m is shared)
-template <int MODE>  // 0: y = A v   1: y = C v   2: y = g - C v
+// batch member b = blockIdx.y works on v, g, y at offset b * n * n (m is shared).
+// R: arithmetic type of the coefficients and the sum (FP64 I/O either way); FP32 is
+// used where the stencil only feeds the preconditioner in mixed precision (on
+// GB300 the FP64 form is bound by the FP64 units, the FP32 form by memory).
+template <int MODE, typename R>  // 0: y = A v   1: y = C v   2: y = g - C v
 __global__ void k_stencil(int n, const StencilTables* __restrict__ tab, const double* __restrict__ m,
                           const double2* __restrict__ v, const double2* __restrict__ g, double2* __restrict__ y) {
-    __shared__ double2 sa[81], sb[81];
+    using CR = cpx_t<R>;
+    __shared__ CR sa[81], sb[81];
     {
         const size_t off = (size_t)blockIdx.y * n * n;
         v += off;
@@ -26,8 +30,8 @@ __global__ void k_stencil(int n, const StencilTables* __restrict__ tab, const do
         if (MODE == 2) g += off;
     }
     for (int i = threadIdx.x; i < 81; i += blockDim.x) {
-        sa[i] = tab->alpha[i];
-        sb[i] = tab->wbeta[i];
+        sa[i] = ccast<CR>(tab->alpha[i]);
+        sb[i] = ccast<CR>(tab->wbeta[i]);
     }
     __syncthreads();
     const size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -36,7 +40,7 @@ __global__ void k_stencil(int n, const StencilTables* __restrict__ tab, const do
     const int bx = i == 0 ? -1 : (i == n - 1 ? 1 : 0);
     const int bz = j == 0 ? -1 : (j == n - 1 ? 1 : 0);
     const int t = (bz + 1) * 3 + (bx + 1);
-    double2 acc = make_double2(0, 0);
+    CR acc = czero<CR>();
 #pragma unroll
     for (int dz = -1; dz <= 1; ++dz) {
         if ((bz == -1 && dz == -1) || (bz == 1 && dz == 1)) continue;
@@ -45,16 +49,17 @@ __global__ void k_stencil(int n, const StencilTables* __restrict__ tab, const do
             if ((bx == -1 && dx == -1) || (bx == 1 && dx == 1)) continue;
             const int s = (dz + 1) * 3 + (dx + 1);
             const size_t p = k + (long long)dz * n + dx;
-            double2 c = sa[t * 9 + s];
+            CR c = sa[t * 9 + s];
             if (MODE >= 1) {
-                const double mm = __ldg(&m[p]);
+                const R mm = (R)__ldg(&m[p]);
                 c = mkc(fma(mm, sb[t * 9 + s].x, c.x), fma(mm, sb[t * 9 + s].y, c.y));
             }
-            acc = cfma(c, __ldg(&v[p]), acc);
+            acc = cfma(c, ccast<CR>(__ldg(&v[p])), acc);
         }
     }
-    if (MODE == 2) acc = __ldg(&g[k]) - acc;
-    y[k] = acc;
+    double2 out = ccast<double2>(acc);
+    if (MODE == 2) out = __ldg(&g[k]) - out;
+    y[k] = out;
 }
 
 __global__ void k_transpose(int n, const double2* __restrict__ a, double2* __restrict__ b) {
@@ -170,16 +175,29 @@ __global__ void k_zero(size_t N, double2* __restrict__ y) {
 
 }  // namespace
 
-int ls_stencil_apply_b(ls_handle* h, int dir, int mode, const double2* v, const double2* g, double2* y, int nb) {
+template <typename R>
+int stencil_launch(ls_handle* h, int dir, int mode, const double2* v, const double2* g, double2* y, int nb) {
     const int n = h->n;
     const size_t N = (size_t)n * n;
     const dim3 grid((unsigned)((N + 255) / 256), nb);
     const double* m = dir == 0 ? h->m64 : h->mT64;
     const StencilTables* tab = h->dtabs + dir;
-    if (mode == 0) LS_LAUNCH(h, k_stencil<0>, grid, 256, 0, n, tab, m, v, g, y);
-    else if (mode == 1) LS_LAUNCH(h, k_stencil<1>, grid, 256, 0, n, tab, m, v, g, y);
-    else LS_LAUNCH(h, k_stencil<2>, grid, 256, 0, n, tab, m, v, g, y);
+    if (mode == 0) LS_LAUNCH(h, (k_stencil<0, R>), grid, 256, 0, n, tab, m, v, g, y);
+    else if (mode == 1) LS_LAUNCH(h, (k_stencil<1, R>), grid, 256, 0, n, tab, m, v, g, y);
+    else LS_LAUNCH(h, (k_stencil<2, R>), grid, 256, 0, n, tab, m, v, g, y);
     return LS_OK;
+}
+
+// FP64 arithmetic (the operator entry points A and C of the ABI)
+int ls_stencil_apply64(ls_handle* h, int dir, int mode, const double2* v, const double2* g, double2* y) {
+    return stencil_launch<double>(h, dir, mode, v, g, y, 1);
+}
+
+// Inside the solve: FP32 arithmetic in mixed precision (the stencils feed only the
+// preconditioner, Algorithm 3 and Algorithm 2), FP64 otherwise.
+int ls_stencil_apply_b(ls_handle* h, int dir, int mode, const double2* v, const double2* g, double2* y, int nb) {
+    if (h->prec == LS_MIXED) return stencil_launch<float>(h, dir, mode, v, g, y, nb);
+    return stencil_launch<double>(h, dir, mode, v, g, y, nb);
 }
 
 int ls_stencil_apply(ls_handle* h, int dir, int mode, const double2* v, const double2* g, double2* y) {
