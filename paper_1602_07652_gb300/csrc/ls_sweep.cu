@@ -278,15 +278,22 @@ __global__ void k_l0_even(int q, int nblk, const cpx_t<T>* __restrict__ cw, cons
 
 // g^l = chi_{Omega^l} g (+ injection from the layer above), copied to the solution buffer.
 // Batch member b = blockIdx.y: strips at + b * SB, traces at + b * TB, grid vector at + b * N.
+// A CTA moves a tile of kGatherTile columns i: the t rows of g it needs are read along
+// x (coalesced) into shared memory, then written in the strip's block layout
+// (column i = q contiguous values, also coalesced).
+constexpr int kGatherTile = 16;
 template <typename T>
-__global__ void k_gather(StripGeom g, const cpx_t<T>* __restrict__ inj, int l, const double2* __restrict__ gf,
-                         cpx_t<T>* __restrict__ rhs, cpx_t<T>* __restrict__ sol, const cpx_t<T>* __restrict__ above,
-                         cpx_t<T>* __restrict__ trace_above, size_t SB, size_t TB) {
+__global__ void __launch_bounds__(256) k_gather(StripGeom g, const cpx_t<T>* __restrict__ inj, int l,
+                                                const double2* __restrict__ gf, cpx_t<T>* __restrict__ rhs,
+                                                cpx_t<T>* __restrict__ sol, const cpx_t<T>* __restrict__ above,
+                                                cpx_t<T>* __restrict__ trace_above, size_t SB, size_t TB) {
     using C = cpx_t<T>;
-    const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* tile = reinterpret_cast<C*>(smem_raw);  // [t][kGatherTile + 1]
+    constexpr int TI = kGatherTile;
     const int q = g.q, n = g.n, E = g.E, t = g.t;
-    if (e >= (size_t)n * q) return;
     const size_t b = blockIdx.y;
+    const int i0 = blockIdx.x * TI;
     gf += b * (size_t)n * n;
     rhs += b * SB;
     sol += b * SB;
@@ -294,50 +301,59 @@ __global__ void k_gather(StripGeom g, const cpx_t<T>* __restrict__ inj, int l, c
         above += b * SB;
         trace_above += b * TB;
     }
-    const int i = (int)(e / q), r = (int)(e % q);
-    if (above && r == 0) trace_above[i] = above[(size_t)i * q + E - 1];  // w^{l+1}_0, kept for the upward sweep
-    double2 val = make_double2(0, 0);
-    if (r >= E && r < E + t) val = gf[(size_t)(l * t - E + r) * n + i];
-    if (above) {
-        const C* c0 = inj + (size_t)l * 12 * n;  // slots 0, 1 of layer l: [slot][dx+1][i]
-        if (r == E + t - 1) {  // -C^l_{n,n+1} w^{l+1}_1 ; w^{l+1}_1 = row E of layer l+1
-            for (int dx = -1; dx <= 1; ++dx) {
-                if (i + dx < 0 || i + dx >= n) continue;
-                val = cfms(ccast<double2>(c0[(size_t)(0 * 3 + dx + 1) * n + i]),
-                           ccast<double2>(above[(size_t)(i + dx) * q + E]), val);
-            }
-        } else if (r == E + t) {  // +C^l_{n+1,n} w^{l+1}_0 ; w^{l+1}_0 = row E-1 of layer l+1
-            for (int dx = -1; dx <= 1; ++dx) {
-                if (i + dx < 0 || i + dx >= n) continue;
-                val = cfma(ccast<double2>(c0[(size_t)(1 * 3 + dx + 1) * n + i]),
-                           ccast<double2>(above[(size_t)(i + dx) * q + E - 1]), val);
-            }
-        }
+    // rows l t .. l t + t - 1 of g, columns i0 .. i0 + TI - 1 (half a warp per row)
+    for (int o = threadIdx.x; o < t * TI; o += blockDim.x) {
+        const int rr = o / TI, il = o % TI, i = i0 + il;
+        tile[rr * (TI + 1) + il] = i < n ? ccast<C>(gf[(size_t)(l * t + rr) * n + i]) : czero<C>();
     }
-    const C cv = ccast<C>(val);
-    rhs[e] = cv;
-    sol[e] = cv;
+    __syncthreads();
+    const int ncol = n - i0 < TI ? n - i0 : TI;
+    for (int o = threadIdx.x; o < ncol * q; o += blockDim.x) {
+        const int il = o / q, r = o % q, i = i0 + il;
+        const size_t e = (size_t)i * q + r;
+        if (above && r == 0) trace_above[i] = above[(size_t)i * q + E - 1];  // w^{l+1}_0, kept for the upward sweep
+        C cv = (r >= E && r < E + t) ? tile[(r - E) * (TI + 1) + il] : czero<C>();
+        if (above && (r == E + t - 1 || r == E + t)) {
+            double2 val = r == E + t - 1 ? gf[(size_t)(l * t - E + r) * n + i] : make_double2(0, 0);
+            const C* c0 = inj + (size_t)l * 12 * n;  // slots 0, 1 of layer l: [slot][dx+1][i]
+            if (r == E + t - 1) {  // -C^l_{n,n+1} w^{l+1}_1 ; w^{l+1}_1 = row E of layer l+1
+                for (int dx = -1; dx <= 1; ++dx) {
+                    if (i + dx < 0 || i + dx >= n) continue;
+                    val = cfms(ccast<double2>(c0[(size_t)(0 * 3 + dx + 1) * n + i]),
+                               ccast<double2>(above[(size_t)(i + dx) * q + E]), val);
+                }
+            } else {  // +C^l_{n+1,n} w^{l+1}_0 ; w^{l+1}_0 = row E-1 of layer l+1
+                for (int dx = -1; dx <= 1; ++dx) {
+                    if (i + dx < 0 || i + dx >= n) continue;
+                    val = cfma(ccast<double2>(c0[(size_t)(1 * 3 + dx + 1) * n + i]),
+                               ccast<double2>(above[(size_t)(i + dx) * q + E - 1]), val);
+                }
+            }
+            cv = ccast<C>(val);
+        }
+        rhs[e] = cv;
+        sol[e] = cv;
+    }
 }
 
-// sol = g^l + injection from the layer below (upward sweep); batch member b = blockIdx.y
+// Upward sweep: sol = g^l (a device copy of rhs made just before) plus the injection
+// from the layer below, which touches only the two rows E - 1 and E; one thread per
+// (column i, row) of those, batch member b = blockIdx.y.
 template <typename T>
 __global__ void k_inject_up(StripGeom g, const cpx_t<T>* __restrict__ inj, int l, const cpx_t<T>* __restrict__ rhs,
                             cpx_t<T>* __restrict__ sol, const cpx_t<T>* __restrict__ below,
                             const cpx_t<T>* __restrict__ trace_self, size_t SB, size_t TB) {
     using C = cpx_t<T>;
-    const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int o = blockIdx.x * blockDim.x + threadIdx.x;
     const int q = g.q, n = g.n, E = g.E, t = g.t;
-    if (e >= (size_t)n * q) return;
+    if (o >= 2 * n) return;
     const size_t b = blockIdx.y;
     rhs += b * SB;
     sol += b * SB;
     below += b * SB;
     trace_self += b * TB;
-    const int i = (int)(e / q), r = (int)(e % q);
-    if (r != E && r != E - 1) {
-        sol[e] = rhs[e];
-        return;
-    }
+    const int i = o >> 1, r = (o & 1) ? E : E - 1;
+    const size_t e = (size_t)i * q + r;
     double2 val = ccast<double2>(rhs[e]);
     const C* c0 = inj + (size_t)l * 12 * n;  // slots 2, 3 of layer l: [slot][dx+1][i]
     if (r == E) {  // -C^l_{1,0} (v^{l-1}_n - w^l_0) ; v^{l-1}_n = row E+t-1 of layer l-1
@@ -483,15 +499,19 @@ int sweep_impl(ls_handle* h, int dir, const double2* g, double2* v, int nb) {
     C* trc = static_cast<C*>(W.strace);
     const DirFactors& F = h->fac[dir];
     const StripGeom geo = geom_of(h);
-    const dim3 gs((unsigned)((sstride + 255) / 256), nb);
+    const dim3 gg((unsigned)((n + kGatherTile - 1) / kGatherTile), nb);
+    const size_t gsm = sizeof(C) * (size_t)h->t * (kGatherTile + 1);
     for (int l = L - 1; l >= 0; --l) {  // downward sweep
-        LS_LAUNCH(h, k_gather<T>, gs, 256, 0, geo, static_cast<const C*>(F.cinj), l, g, rhs + l * sstride,
+        LS_LAUNCH(h, k_gather<T>, gg, 256, gsm, geo, static_cast<const C*>(F.cinj), l, g, rhs + l * sstride,
                   sol + l * sstride, l < L - 1 ? sol + (l + 1) * sstride : (const C*)nullptr,
                   l < L - 1 ? trc + (size_t)(l + 1) * n : (C*)nullptr, SB, TB);
         LS_TRY(cr_solve<T>(h, dir, l, sol + l * sstride, SB, nb));
     }
-    for (int l = 1; l < L; ++l) {  // upward sweep
-        LS_LAUNCH(h, k_inject_up<T>, gs, 256, 0, geo, static_cast<const C*>(F.cinj), l, rhs + l * sstride,
+    const dim3 gi((unsigned)((2 * n + 255) / 256), nb);
+    for (int l = 1; l < L; ++l) {  // upward sweep: sol = rhs, then the two injected rows
+        LS_CUDA(cudaMemcpy2DAsync(sol + l * sstride, sizeof(C) * SB, rhs + l * sstride, sizeof(C) * SB,
+                                  sizeof(C) * sstride, nb, cudaMemcpyDeviceToDevice, h->stream));
+        LS_LAUNCH(h, k_inject_up<T>, gi, 256, 0, geo, static_cast<const C*>(F.cinj), l, rhs + l * sstride,
                   sol + l * sstride, sol + (l - 1) * sstride, trc + (size_t)l * n, SB, TB);
         LS_TRY(cr_solve<T>(h, dir, l, sol + l * sstride, SB, nb));
     }
