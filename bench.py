@@ -249,7 +249,7 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
-    # iteration counts of this workload measured by the GPU solver (documented in the design doc)
+    # outer / inner iteration counts per right-hand side that the GPU solver needs on this workload
     outer, inner = REF_COUNTS.get(args.n, (6, 30))
     vals = []
     for _ in range(args.warmup + args.steps):
