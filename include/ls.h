@@ -226,6 +226,14 @@ int ls_autotune(ls_handle* h, int nrhs, int reps, ls_tuning* out);
  * otherwise.  Results agree up to rounding whichever shapes are set. */
 int ls_set_shapes(ls_handle* h, int fft_variant, int bd_chunk);
 
+/* ls_set_reduction -- pin the form of the block-cyclic-reduction local solves of
+ * Algorithm 1 (Sec. 3.4): cr_split 1 lets the steps of levels with fewer blocks
+ * than SMs split each block's columns over several CTAs, 0 keeps one CTA per block
+ * (as in ls_tuning).  Synchronises the handle's stream and drops the captured sweep
+ * graphs when the form changes.  LS_EINVAL for other values.  Results agree up to
+ * rounding in either form. */
+int ls_set_reduction(ls_handle* h, int cr_split);
+
 /* ---- learned preconditioner step (an addition: the paper has no network) ----
  * A BF16 convolutional U-Net N, trained and applied by this library's own
  * kernels (tensor-core convolutions, FP32 accumulation).  The paper's outer

@@ -84,6 +84,7 @@ _SIGS = {
                                       ctypes.POINTER(_P), ctypes.POINTER(Stats), ctypes.POINTER(ctypes.c_int)]),
     "ls_autotune": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.POINTER(Tuning)]),
     "ls_set_shapes": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int]),
+    "ls_set_reduction": (ctypes.c_int, [_P, ctypes.c_int]),
     "ls_solve_host": (ctypes.c_int, [_P, _P, ctypes.c_double, _P, ctypes.POINTER(Stats)]),
     "ls_solve_plane_wave": (ctypes.c_int, [_P, ctypes.c_double, ctypes.c_double, _P, ctypes.POINTER(Stats)]),
     "ls_apply_A": (ctypes.c_int, [_P, _P, _P]),
@@ -355,6 +356,9 @@ class Solver:
 
     def ls_set_shapes(self, fft_variant, bd_chunk=0):
         _ck(self._lib.ls_set_shapes(self._h, int(fft_variant), int(bd_chunk)), "ls_set_shapes")
+
+    def ls_set_reduction(self, cr_split):
+        _ck(self._lib.ls_set_reduction(self._h, int(cr_split)), "ls_set_reduction")
 
     def ls_autotune(self, nrhs=1, reps=3):
         t = Tuning()

@@ -123,3 +123,13 @@ extern "C" int ls_set_shapes(ls_handle* h, int fft_variant, int bd_chunk) {
     h->bd_chunk = bd_chunk;
     return LS_OK;
 }
+
+extern "C" int ls_set_reduction(ls_handle* h, int cr_split) {
+    if (!h || (cr_split != 0 && cr_split != 1)) return LS_EINVAL;
+    if (h->cr_split != cr_split) {
+        LS_CUDA(cudaStreamSynchronize(h->stream));
+        h->cr_split = cr_split;
+        ls_bd_graph_free(h);
+    }
+    return LS_OK;
+}

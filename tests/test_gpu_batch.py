@@ -232,3 +232,44 @@ def test_batch_larger_than_a_chunk_runs_two_concurrent_lanes():
     for b in (0, 5):
         assert rel(v8[b], s.ls_precond_bd(g[b].contiguous())) < 1e-6
     s.close()
+
+
+
+@pytest.mark.parametrize("n,L,E,nb", [(96, 6, 4, 3), (128, 4, 8, 8), (256, 4, 10, 5), (64, 2, 10, 1)])
+def test_split_and_unsplit_reduction_steps_agree(n, L, E, nb):
+    # q = 24, 48, 84 (the 2048^2 workload's blocks: 64 rows + 2 x 10), 52; both
+    # forms of the reduction give Algorithm 2's result to FP32 rounding on every
+    # member of a ragged batch, and the split form is reproducible run to run
+    w = inputs.omega_for_ppw(n, 10.0)
+    m = inputs.bump_medium(n, nbumps=6, seed=8)
+    s = binding.Solver(cuda(m), w, layers=L, ext=E, precision=binding.LS_MIXED)
+    s.ls_factor()
+    g = _fields(n, nb, 300)
+    s.ls_set_reduction(0)
+    v0 = s.ls_precond_bd_batch(g).clone()
+    s.ls_set_reduction(1)
+    v1 = s.ls_precond_bd_batch(g).clone()
+    assert torch.equal(s.ls_precond_bd_batch(g), v1)
+    for b in range(nb):
+        assert rel(v1[b], v0[b]) < 1e-6, (b, rel(v1[b], v0[b]))
+    assert rel(v1[nb - 1], s.ls_precond_bd(g[nb - 1].contiguous())) < 1e-6
+    with pytest.raises(binding.LSError):
+        s.ls_set_reduction(2)
+    s.close()
+
+
+def test_unsplit_reduction_inside_a_batched_solve_meets_the_oracle():
+    n, L, E = 256, 4, 10
+    w = inputs.omega_for_ppw(n, 10.0)
+    m = inputs.bump_medium(n, nbumps=6, seed=9)
+    s = binding.Solver(cuda(m), w, layers=L, ext=E, precision=binding.LS_MIXED)
+    s.ls_factor()
+    s.ls_set_reduction(0)
+    thetas = [0.2, 2.5, 4.0]
+    f = torch.stack([s.ls_incident_rhs(t) for t in thetas]).contiguous()
+    u, st, rc = s.ls_solve_batch(f, 1e-9)
+    assert rc == 0 and st["true_rel_residual"] <= 1e-9
+    prob = osolver.Problem(m, w, L=L, E=E)
+    u_ref, _ = osolver.solve(prob, prob.rhs(thetas[1]), tol=1e-12)
+    assert rel(u[1].cpu(), torch.from_numpy(u_ref)) < 1e-7
+    s.close()
