@@ -57,7 +57,7 @@ class Stats(ctypes.Structure):
 
 class Tuning(ctypes.Structure):
     _fields_ = [("fft_variant", ctypes.c_int), ("bd_chunk", ctypes.c_int),
-                ("fft_ms", ctypes.c_double * 6), ("bd_ms", ctypes.c_double * 4),
+                ("fft_ms", ctypes.c_double * 8), ("bd_ms", ctypes.c_double * 4),
                 ("bd_ms_nosplit", ctypes.c_double * 4), ("cr_split", ctypes.c_int)]
 
     def as_dict(self):
@@ -85,6 +85,7 @@ _SIGS = {
     "ls_autotune": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.POINTER(Tuning)]),
     "ls_set_shapes": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int]),
     "ls_set_reduction": (ctypes.c_int, [_P, ctypes.c_int]),
+    "ls_device_timeouts": (ctypes.c_int, [ctypes.POINTER(ctypes.c_uint)]),
     "ls_solve_host": (ctypes.c_int, [_P, _P, ctypes.c_double, _P, ctypes.POINTER(Stats)]),
     "ls_solve_plane_wave": (ctypes.c_int, [_P, ctypes.c_double, ctypes.c_double, _P, ctypes.POINTER(Stats)]),
     "ls_apply_A": (ctypes.c_int, [_P, _P, _P]),
@@ -234,6 +235,13 @@ class Net:
         _ck(self._lib.ls_net_train_step(self._h, nb, H, W, _ptr(r), _ptr(m), _ptr(e), float(lr), ctypes.byref(loss)),
             "ls_net_train_step")
         return loss.value
+
+
+def device_timeouts() -> int:
+    """Column tiles whose TMA data did not arrive in time (0 in a healthy run)."""
+    c = ctypes.c_uint(0)
+    _ck(load().ls_device_timeouts(ctypes.byref(c)), "ls_device_timeouts")
+    return int(c.value)
 
 
 def default_opts() -> Opts:

@@ -17,6 +17,19 @@
 // Radix 16 halves the exchanges, radix 8 halves the registers a thread needs
 // (more resident warps to hide latency); the autotuner picks per problem.
 // Small P groups several transforms per CTA of at least 256 threads.
+//
+// The column pass reads and writes 16-byte row segments (2 columns) of the
+// row-major n x P slab, one per row at a stride of 8P bytes.  Through the LSU each
+// such warp access touches 32 separate lines; the TMA shapes (6, 7) move the
+// tile instead with cp.async.bulk.tensor in boxes of up to 256 rows into shared
+// memory and back, completion tracked by an mbarrier (a wait bounded in time:
+// on expiry the tile is written as NaN and a device counter is raised, so the
+// solver's residual checks see it).
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <mutex>
+
 #include "ls_fft_common.cuh"
 
 namespace {
@@ -266,6 +279,149 @@ __global__ void __launch_bounds__(Geo<LP, LE>::THREADS, MINB) k_cols16(int nin, 
     }
 }
 
+// ------------------------------------------------------------- TMA column tiles
+__device__ unsigned int g_tma_timeouts;  // column tiles whose TMA load did not arrive in time
+
+constexpr unsigned long long kTmaWaitNs = 1000000000ull;  // 1 s
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) {
+    return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+// Box (4 floats = one row of a 2-column tile) x BR rows at (x, y) -> shared memory.
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y, unsigned long long* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], "
+        "[%4];\n" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<unsigned long long>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+        : "memory");
+}
+__device__ __forceinline__ void tma_store_2d(const CUtensorMap* map, int x, int y, const void* src) {
+    asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.tile.bulk_group [%0, {%1, %2}], [%3];\n" ::"l"(
+                     reinterpret_cast<unsigned long long>(map)),
+                 "r"(x), "r"(y), "r"(smem_u32(src))
+                 : "memory");
+}
+// true once the barrier's phase `parity` has completed; false after kTmaWaitNs
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity) {
+    const unsigned long long t0 = global_ns();
+    for (;;) {
+        unsigned done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(smem_u32(bar)), "r"(parity)
+            : "memory");
+        if (done) return true;
+        if (global_ns() - t0 > kTmaWaitNs) return false;
+        __nanosleep(64);
+    }
+}
+
+// Pass 2 on 2-column tiles moved by TMA.  Same transforms, Ghat product and
+// arithmetic as k_cols16<LP, LE, 2, MINB>; the tile's rows land densely (16 B per
+// row) in the front of the exchange buffer, which the first exchange then
+// overwrites (after a barrier), and leave the same way.  BR rows per box.
+template <int LP, int LE, int MINB>
+__global__ void __launch_bounds__(Geo<LP, LE>::THREADS, MINB) k_cols16_tma(const __grid_constant__ CUtensorMap map,
+                                                                           int n, float2* __restrict__ X,
+                                                                           const float2* __restrict__ ghat,
+                                                                           const float2* __restrict__ tw) {
+    using Gm = Geo<LP, LE>;
+    constexpr int CW = 2;
+    using EL = float4;
+    constexpr int P = Gm::P, T = Gm::T, E = Gm::E, R = 1 << Gm::LRL, Q = P / 2 + 1, G = Gm::G;
+    constexpr int BR = P / 2 < 256 ? P / 2 : 256;
+    constexpr int ntile = P / CW;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    const int grp = threadIdx.x / T, j = threadIdx.x % T;
+    EL* buf = reinterpret_cast<EL*>(smem_raw) + grp * Gm::SLOTS;
+    float2* gs = reinterpret_cast<float2*>(smem_raw + sizeof(EL) * G * Gm::SLOTS) + grp * CW * Q;
+    auto* bar = reinterpret_cast<unsigned long long*>(smem_raw + sizeof(EL) * G * Gm::SLOTS +
+                                                      sizeof(float2) * G * CW * Q);
+    int& failed = *reinterpret_cast<int*>(bar + 1);
+    auto tile_of = [&](int g) {
+        const int lin = blockIdx.x * G + g;
+        return (lin & 1) ? (ntile - 1 - (lin >> 1)) : (lin >> 1);
+    };
+    const int kx0 = CW * tile_of(grp);
+    const int nbox = (n + BR - 1) / BR;
+    if (threadIdx.x == 0) {
+        failed = 0;
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(bar)) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const unsigned bytes = (unsigned)(G * nbox * BR * sizeof(EL));
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(bytes)
+                     : "memory");
+        for (int g = 0; g < G; ++g) {
+            EL* stg = reinterpret_cast<EL*>(smem_raw) + g * Gm::SLOTS;
+            const int x = 2 * CW * tile_of(g);   // in floats: 16-byte aligned
+            for (int k = 0; k < nbox; ++k) tma_load_2d(stg + k * BR, &map, x, k * BR, bar);
+        }
+    }
+#pragma unroll
+    for (int c = 0; c < CW; ++c) {
+        const int kx = kx0 + c;
+        const float2* g = ghat + (size_t)(kx <= P / 2 ? kx : P - kx) * Q;
+        for (int i = j; i < Q; i += T) cp_async8(gs + c * Q + i, g + i);
+    }
+    cp_async_commit();
+    if (!mbar_wait(bar, 0)) atomicOr(&failed, 1);
+    __syncthreads();
+    if (failed) {  // rows of this CTA's tiles become NaN: visible to every residual check
+        if (threadIdx.x == 0) atomicAdd(&g_tma_timeouts, 1u);
+        const float nan = __int_as_float(0x7fc00000);
+        for (int z = j; z < n; z += T)
+            *reinterpret_cast<EL*>(X + (size_t)z * P + kx0) = make_float4(nan, nan, nan, nan);
+        cp_async_wait_all();
+        return;
+    }
+    float2 v[CW][E];
+#pragma unroll
+    for (int t = 0; t < E / 2; ++t) {
+        const int z = j + t * T;
+        Elem<CW>::unpack(z < n ? buf[z] : EL{}, v, t);
+    }
+    fwd_stages<LP, LE, 0, false>(v, buf, j, tw);  // its first exchange waits for every staging read
+    cp_async_wait_all();
+    __syncthreads();
+#pragma unroll
+    for (int c = 0; c < CW; ++c)
+#pragma unroll
+        for (int e = 0; e < E / R; ++e)
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                const int kz = j + e * T + r * (P / R);
+                v[c][e * R + r] = v[c][e * R + r] * gs[c * Q + (kz <= P / 2 ? kz : P - kz)];
+            }
+    inv_stages<LP, LE, 0, false>(v, buf, j, tw);
+    __syncthreads();  // every thread is done with the exchange buffer
+#pragma unroll
+    for (int t = 0; t < E; ++t) {
+        const int z = j + t * T;
+        if (z < nbox * BR) buf[z] = Elem<CW>::pack(v, t);
+    }
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int g = 0; g < G; ++g) {
+            const EL* stg = reinterpret_cast<const EL*>(smem_raw) + g * Gm::SLOTS;
+            const int x = 2 * CW * tile_of(g);
+            for (int k = 0; k < nbox; ++k) tma_store_2d(&map, x, k * BR, stg + k * BR);  // rows >= n are clipped
+        }
+        asm volatile("cp.async.bulk.commit_group;\n" ::: "memory");
+        asm volatile("cp.async.bulk.wait_group.read 0;\n" ::: "memory");  // shared memory stays until read
+    }
+}
+
 // Pass 3: y[z, x] = u[z, x] + IFFT_x(X[z, :])[x] for x < n (radix 16).  The row of u
 // is copied to shared memory asynchronously at the start (each thread fetches the
 // elements it will write), so its latency hides behind the inverse transform.
@@ -317,6 +473,10 @@ constexpr size_t cols_smem() {
     using Gm = Geo<LP, LE>;
     return sizeof(float2) * CW * Gm::G * Gm::SLOTS + sizeof(float2) * Gm::G * CW * (Gm::P / 2 + 1);
 }
+template <int LP, int LE>
+constexpr size_t cols_tma_smem() {
+    return cols_smem<LP, LE, 2>() + 16;  // + the mbarrier and the CTA's failure flag
+}
 template <int LP>
 constexpr size_t row_smem16() {
     return sizeof(float2) * Geo<LP, 4>::G * Geo<LP, 4>::SLOTS;
@@ -324,12 +484,49 @@ constexpr size_t row_smem16() {
 
 // Column-pass tile shapes (ls_handle::fft_variant): 0 = radix 16, 1 column, 3 CTAs/SM;
 // 2 = radix 16, 2 columns, 2 CTAs/SM; 3 = radix 16, 1 column, 2 CTAs/SM;
-// 4 = radix 8, 1 column, 2 CTAs/SM (of up to 512 threads); 5 = radix 8, 2 columns, 1 CTA/SM.
+// 4 = radix 8, 1 column, 2 CTAs/SM (of up to 512 threads); 5 = radix 8, 2 columns, 1 CTA/SM;
+// 6, 7 = shapes 2, 5 with the tiles moved by TMA.
 template <int LP, int LE, int CW, int MINB>
 int cols_launch(ls_handle* h, int n, float2* X, const float2* gh, const float2* tw) {
     using Gm = Geo<LP, LE>;
     LS_LAUNCH(h, (k_cols16<LP, LE, CW, MINB>), (unsigned)(Gm::P / CW / Gm::G), Gm::THREADS,
               (cols_smem<LP, LE, CW>()), n, n, X, gh, tw);
+    return LS_OK;
+}
+
+// Tensor map of the n x P slab for the TMA shapes: FP32 elements, rows of 2P, boxes
+// of 4 (one row of a 2-column tile, 16 bytes) x BR rows; rows beyond n read as 0.
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q{};
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    });
+    return fn;
+}
+
+template <int LP, int LE, int MINB>
+int cols_launch_tma(ls_handle* h, int n, float2* X, const float2* gh, const float2* tw) {
+    using Gm = Geo<LP, LE>;
+    constexpr int P = Gm::P, BR = P / 2 < 256 ? P / 2 : 256;
+    auto enc = tensor_map_encoder();
+    if (!enc) return LS_ECUDA;
+    CUtensorMap map;
+    const cuuint64_t dims[2] = {(cuuint64_t)2 * P, (cuuint64_t)n};
+    const cuuint64_t strides[1] = {(cuuint64_t)P * sizeof(float2)};
+    const cuuint32_t box[2] = {4, (cuuint32_t)BR};
+    const cuuint32_t estr[2] = {1, 1};
+    if (enc(&map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, X, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return LS_ECUDA;
+    LS_LAUNCH(h, (k_cols16_tma<LP, LE, MINB>), (unsigned)(P / 2 / Gm::G), Gm::THREADS, (cols_tma_smem<LP, LE>()), map,
+              n, X, gh, tw);
     return LS_OK;
 }
 
@@ -347,6 +544,8 @@ int apply_lp(ls_handle* h, const UIO* u, UIO* y, float2* X, int shape) {
         case 3: LS_TRY((cols_launch<LP, 4, 1, 2>(h, n, X, gh, tw))); break;
         case 4: LS_TRY((cols_launch<LP, 3, 1, 2>(h, n, X, gh, tw))); break;
         case 5: LS_TRY((cols_launch<LP, 3, 2, 1>(h, n, X, gh, tw))); break;
+        case 6: LS_TRY((cols_launch_tma<LP, 4, 2>(h, n, X, gh, tw))); break;
+        case 7: LS_TRY((cols_launch_tma<LP, 3, 1>(h, n, X, gh, tw))); break;
         default: LS_TRY((cols_launch<LP, 4, 1, 3>(h, n, X, gh, tw))); break;
     }
     LS_LAUNCH(h, (k_rows16_inv<LP, UIO>), rows_grid, Gm::THREADS, (rinv_smem<LP, UIO>()), n, n, X, u, y, tw);
@@ -379,6 +578,8 @@ int optin_lp() {
     LS_TRY(optin(k_cols16<LP, 4, 2, 2>, cols_smem<LP, 4, 2>()));
     LS_TRY(optin(k_cols16<LP, 3, 1, 2>, cols_smem<LP, 3, 1>()));
     LS_TRY(optin(k_cols16<LP, 3, 2, 1>, cols_smem<LP, 3, 2>()));
+    LS_TRY(optin(k_cols16_tma<LP, 4, 2>, cols_tma_smem<LP, 4>()));
+    LS_TRY(optin(k_cols16_tma<LP, 3, 1>, cols_tma_smem<LP, 3>()));
     LS_TRY(optin(k_rows16_inv<LP, float2>, rinv_smem<LP, float2>()));
     return optin(k_rows16_inv<LP, double2>, rinv_smem<LP, double2>());
 }
@@ -401,4 +602,10 @@ int ls_apply32_fft16(ls_handle* h, const float2* u, float2* y, int shape) { retu
 
 int ls_apply_mx_fft16(ls_handle* h, const double2* u, double2* y, int shape) {
     return apply_any(h, u, y, shape);
+}
+
+extern "C" int ls_device_timeouts(unsigned* count) {
+    if (!count) return LS_EINVAL;
+    LS_CUDA(cudaMemcpyFromSymbol(count, g_tma_timeouts, sizeof(unsigned)));
+    return LS_OK;
 }

@@ -92,19 +92,25 @@ def test_fp32_apply_every_transform_length(n, L):
     s.close()
 
 
-# every column-pass tile shape of the autotuner gives the same LS-apply
-@pytest.mark.parametrize("n,L", [(100, 4), (300, 6), (1000, 10)])
+# every column-pass tile shape of the autotuner gives the same LS-apply; n = 1100
+# (P = 4096) has a ragged last TMA box of 76 rows, n = 100 (P = 256) 8 tiles per CTA
+@pytest.mark.parametrize("n,L", [(100, 4), (300, 6), (1000, 10), (1100, 11)])
 def test_fp32_apply_every_tile_shape(n, L):
     w = inputs.omega_for_ppw(n, 10.0)
     m = inputs.bump_medium(n, nbumps=6, seed=n + 2)
     s = binding.Solver(cuda(m), w, layers=L, ext=3, precision=binding.LS_MIXED)
     u = inputs.random_field(n, 5)
     y_ref = greens.apply_H(u, m, 1.0 / n, w)
-    for v in range(6):
+    ys = {}
+    for v in range(8):
         s.ls_set_shapes(v)
-        assert rel(s.ls_apply_mixed(cuda(u)).cpu().numpy(), y_ref) < 2e-5, v
+        ys[v] = s.ls_apply_mixed(cuda(u)).cpu().numpy()
+        assert rel(ys[v], y_ref) < 2e-5, v
+    # the TMA shapes move the same tiles: the same arithmetic, bit for bit
+    assert np.array_equal(ys[6], ys[2]) and np.array_equal(ys[7], ys[5])
+    assert binding.device_timeouts() == 0
     with pytest.raises(binding.LSError):
-        s.ls_set_shapes(6)
+        s.ls_set_shapes(8)
     s.close()
 
 
