@@ -86,6 +86,7 @@ _SIGS = {
     "ls_set_shapes": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int]),
     "ls_set_reduction": (ctypes.c_int, [_P, ctypes.c_int]),
     "ls_device_timeouts": (ctypes.c_int, [ctypes.POINTER(ctypes.c_uint)]),
+    "ls_test_tma_shortfall": (ctypes.c_int, [ctypes.c_uint]),
     "ls_solve_host": (ctypes.c_int, [_P, _P, ctypes.c_double, _P, ctypes.POINTER(Stats)]),
     "ls_solve_plane_wave": (ctypes.c_int, [_P, ctypes.c_double, ctypes.c_double, _P, ctypes.POINTER(Stats)]),
     "ls_apply_A": (ctypes.c_int, [_P, _P, _P]),
@@ -242,6 +243,11 @@ def device_timeouts() -> int:
     c = ctypes.c_uint(0)
     _ck(load().ls_device_timeouts(ctypes.byref(c)), "ls_device_timeouts")
     return int(c.value)
+
+
+def test_tma_shortfall(nbytes: int) -> None:
+    """Test hook: make the TMA column pass's waits run out (0 restores)."""
+    _ck(load().ls_test_tma_shortfall(int(nbytes)), "ls_test_tma_shortfall")
 
 
 def default_opts() -> Opts:

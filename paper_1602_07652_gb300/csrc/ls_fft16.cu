@@ -280,7 +280,8 @@ __global__ void __launch_bounds__(Geo<LP, LE>::THREADS, MINB) k_cols16(int nin, 
 }
 
 // ------------------------------------------------------------- TMA column tiles
-__device__ unsigned int g_tma_timeouts;  // column tiles whose TMA load did not arrive in time
+__device__ unsigned int g_tma_timeouts;  // CTAs whose TMA loads did not arrive in time
+unsigned g_tma_shortfall = 0;            // host side: see ls_test_tma_shortfall
 
 constexpr unsigned long long kTmaWaitNs = 1000000000ull;  // 1 s
 
@@ -326,11 +327,14 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned pari
 // arithmetic as k_cols16<LP, LE, 2, MINB>; the tile's rows land densely (16 B per
 // row) in the front of the exchange buffer, which the first exchange then
 // overwrites (after a barrier), and leave the same way.  BR rows per box.
+// shortfall: bytes the barrier expects beyond what the boxes deliver (0; a test sets
+// it to make the wait run out with no copy left in flight).
 template <int LP, int LE, int MINB>
 __global__ void __launch_bounds__(Geo<LP, LE>::THREADS, MINB) k_cols16_tma(const __grid_constant__ CUtensorMap map,
                                                                            int n, float2* __restrict__ X,
                                                                            const float2* __restrict__ ghat,
-                                                                           const float2* __restrict__ tw) {
+                                                                           const float2* __restrict__ tw,
+                                                                           unsigned shortfall) {
     using Gm = Geo<LP, LE>;
     constexpr int CW = 2;
     using EL = float4;
@@ -358,7 +362,7 @@ __global__ void __launch_bounds__(Geo<LP, LE>::THREADS, MINB) k_cols16_tma(const
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        const unsigned bytes = (unsigned)(G * nbox * BR * sizeof(EL));
+        const unsigned bytes = (unsigned)(G * nbox * BR * sizeof(EL)) + shortfall;
         asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(bytes)
                      : "memory");
         for (int g = 0; g < G; ++g) {
@@ -526,7 +530,7 @@ int cols_launch_tma(ls_handle* h, int n, float2* X, const float2* gh, const floa
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
         return LS_ECUDA;
     LS_LAUNCH(h, (k_cols16_tma<LP, LE, MINB>), (unsigned)(P / 2 / Gm::G), Gm::THREADS, (cols_tma_smem<LP, LE>()), map,
-              n, X, gh, tw);
+              n, X, gh, tw, g_tma_shortfall);
     return LS_OK;
 }
 
@@ -602,6 +606,12 @@ int ls_apply32_fft16(ls_handle* h, const float2* u, float2* y, int shape) { retu
 
 int ls_apply_mx_fft16(ls_handle* h, const double2* u, double2* y, int shape) {
     return apply_any(h, u, y, shape);
+}
+
+extern "C" int ls_test_tma_shortfall(unsigned bytes) {
+    if (bytes % 16 || bytes > 4096) return LS_EINVAL;
+    g_tma_shortfall = bytes;
+    return LS_OK;
 }
 
 extern "C" int ls_device_timeouts(unsigned* count) {

@@ -236,3 +236,31 @@ def test_bd_graph_replay_equals_direct_launches():
         outs.append(s.ls_precond_bd(g).cpu())   # replay twice
         s.close()
     assert torch.equal(outs[0], outs[2]) and torch.equal(outs[2], outs[3]) and torch.equal(outs[0], outs[1])
+
+
+def test_tma_wait_that_runs_out_marks_the_tiles_and_is_counted():
+    # the barrier expects 16 bytes more than the boxes bring: every CTA's wait runs
+    # out after one second with no copy in flight, writes its tiles as NaN, counts
+    # itself and returns; the context stays usable and the next apply is exact again
+    n, L = 100, 4   # P = 256: 8 CTAs of 16 tiles
+    w = inputs.omega_for_ppw(n, 10.0)
+    m = inputs.bump_medium(n, nbumps=6, seed=7)
+    s = binding.Solver(cuda(m), w, layers=L, ext=3, precision=binding.LS_MIXED)
+    u = cuda(inputs.random_field(n, 5))
+    s.ls_set_shapes(2)
+    y_ref = s.ls_apply_mixed(u).cpu()
+    s.ls_set_shapes(6)
+    before = binding.device_timeouts()
+    with pytest.raises(binding.LSError):
+        binding.test_tma_shortfall(8)
+    binding.test_tma_shortfall(16)
+    try:
+        y_bad = s.ls_apply_mixed(u).cpu()
+    finally:
+        binding.test_tma_shortfall(0)
+    assert binding.device_timeouts() - before == 8
+    assert torch.isnan(y_bad.real).any()
+    y = s.ls_apply_mixed(u).cpu()
+    assert torch.equal(y, y_ref)
+    assert binding.device_timeouts() - before == 8
+    s.close()
