@@ -197,7 +197,8 @@ int ls_solve_group(int nprob, ls_handle* const* hs, const ls_c64* const* f, doub
  *     2-column tiles (the default); 3 = radix-16 on 1-column tiles, 2 CTAs per SM;
  *     4 = radix-8 per thread on 1-column tiles; 5 = radix-8 per thread on
  *     2-column tiles; 6, 7 = shapes 2 and 5 with the column tiles moved between
- *     HBM and shared memory by TMA (0 and 2..7 need 256 <= P <= 4096); 1 = the
+ *     HBM and shared memory by TMA; 8 = shape 6 with the two columns of a tile in
+ *     packed FP32x2 instructions (0 and 2..8 need 256 <= P <= 4096); 1 = the
  *     generic radix-8 transforms on 4-column tiles;
  *   - the band-block batching of Algorithm 2 for nrhs right-hand sides: bd_chunk
  *     = right-hand sides per pass over the local-solve factors (1, 2, 4, 8;
@@ -213,7 +214,7 @@ int ls_solve_group(int nprob, ls_handle* const* hs, const ls_c64* const* f, doub
 typedef struct {
     int fft_variant;    /* chosen FFT tile shape                                       */
     int bd_chunk;       /* chosen right-hand sides per Algorithm 2 pass                */
-    double fft_ms[8];   /* LS-apply (FP64 I/O, FP32 arithmetic) per variant; -1: n/a   */
+    double fft_ms[9];   /* LS-apply (FP64 I/O, FP32 arithmetic) per variant; -1: n/a   */
     double bd_ms[4];    /* Algorithm 2 ms per right-hand side, chunks 1, 2, 4, 8 (0: not tried) */
     double bd_ms_nosplit[4]; /* the same without splitting the blocks of small levels        */
     int cr_split;       /* 1: the reduction steps of levels with fewer blocks than SMs split
@@ -222,7 +223,7 @@ typedef struct {
 int ls_autotune(ls_handle* h, int nrhs, int reps, ls_tuning* out);
 
 /* ls_set_shapes -- pin the two shape choices (e.g. from an earlier ls_autotune):
- * fft_variant 0..7 as above (a radix-16/8 shape on a P outside 256..4096 falls back
+ * fft_variant 0..8 as above (a radix-16/8 shape on a P outside 256..4096 falls back
  * to the generic one), bd_chunk 1..8 (FP64: 1..4) or 0 for the largest.  LS_EINVAL
  * otherwise.  Results agree up to rounding whichever shapes are set. */
 int ls_set_shapes(ls_handle* h, int fft_variant, int bd_chunk);
@@ -235,7 +236,7 @@ int ls_set_shapes(ls_handle* h, int fft_variant, int bd_chunk);
  * rounding in either form. */
 int ls_set_reduction(ls_handle* h, int cr_split);
 
-/* ls_device_timeouts -- *count = how many CTAs of the TMA tile shapes (6, 7) found
+/* ls_device_timeouts -- *count = how many CTAs of the TMA tile shapes (6, 7, 8) found
  * their column tiles not arrived within one second since the library was loaded; 0
  * in a healthy run.  Such a CTA writes its tiles as NaN (so the solver's residual
  * checks reject the result) and returns instead of waiting on.  Synchronous read of

@@ -57,7 +57,7 @@ class Stats(ctypes.Structure):
 
 class Tuning(ctypes.Structure):
     _fields_ = [("fft_variant", ctypes.c_int), ("bd_chunk", ctypes.c_int),
-                ("fft_ms", ctypes.c_double * 8), ("bd_ms", ctypes.c_double * 4),
+                ("fft_ms", ctypes.c_double * 9), ("bd_ms", ctypes.c_double * 4),
                 ("bd_ms_nosplit", ctypes.c_double * 4), ("cr_split", ctypes.c_int)]
 
     def as_dict(self):

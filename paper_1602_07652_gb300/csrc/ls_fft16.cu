@@ -76,8 +76,8 @@ __device__ __forceinline__ float2 ld_tw(const float2* __restrict__ tw, int m) {
 
 // v[c][e R + r] *= W^(k r), W = exp(-DIR 2 pi i / 2^(LS+LR)), r = 1..R-1.
 // tw[m] = exp(-2 pi i m / P), so W^s = tw[s << (LP - LS - LR)].
-template <int LR, int LS, int DIR, int LP, int CW, int E>
-__device__ __forceinline__ void twiddle(float2 (&v)[CW][E], int e, int k, const float2* __restrict__ tw) {
+template <int LR, int LS, int DIR, int LP, int CW, int E, typename V>
+__device__ __forceinline__ void twiddle(V (&v)[CW][E], int e, int k, const float2* __restrict__ tw) {
     constexpr int R = 1 << LR;
     constexpr int SH = LP - LS - LR;
     float2 w[16];
@@ -103,8 +103,8 @@ __device__ __forceinline__ void twiddle(float2 (&v)[CW][E], int e, int k, const 
 
 // One Stockham stage: radix 2^LR, Ns = 2^LS.  Butterfly b = j + e T (e < E/R)
 // holds inputs b + r P/R in v[.][e R + r]; twiddle by W^((b mod Ns) r), DFT.
-template <int LR, int LS, int DIR, int LP, int LE, bool HZ, int CW, int E>
-__device__ __forceinline__ void stage(float2 (&v)[CW][E], int j, const float2* __restrict__ tw) {
+template <int LR, int LS, int DIR, int LP, int LE, bool HZ, int CW, int E, typename V>
+__device__ __forceinline__ void stage(V (&v)[CW][E], int j, const float2* __restrict__ tw) {
     constexpr int R = 1 << LR, T = Geo<LP, LE>::T;
 #pragma unroll
     for (int e = 0; e < E / R; ++e) {
@@ -114,9 +114,88 @@ __device__ __forceinline__ void stage(float2 (&v)[CW][E], int j, const float2* _
     }
 }
 
+// ------------------------------------------------- two columns per FP32x2 instruction
+// The column pass applies identical operations to the two columns of a tile, so a
+// pair of values (column 0, column 1) can travel in one 64-bit register and be
+// added, multiplied and fused-multiply-added by the packed FP32 instructions of
+// sm_100+ (add/sub/mul/fma .rn.f32x2: two IEEE single-precision operations, each
+// rounded to nearest, in one instruction).  CP holds a complex value of both
+// columns: x = (re0, re1), y = (im0, im1).
+struct F2 {
+    unsigned long long r;
+};
+__device__ __forceinline__ F2 f2(float lo, float hi) {
+    F2 o;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(o.r) : "f"(lo), "f"(hi));
+    return o;
+}
+__device__ __forceinline__ F2 f2s(float a) { return f2(a, a); }
+__device__ __forceinline__ void f2split(F2 a, float& lo, float& hi) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(a.r));
+}
+__device__ __forceinline__ F2 add2(F2 a, F2 b) {
+    F2 o;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(o.r) : "l"(a.r), "l"(b.r));
+    return o;
+}
+__device__ __forceinline__ F2 sub2(F2 a, F2 b) {
+    F2 o;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(o.r) : "l"(a.r), "l"(b.r));
+    return o;
+}
+__device__ __forceinline__ F2 mul2(F2 a, F2 b) {
+    F2 o;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(o.r) : "l"(a.r), "l"(b.r));
+    return o;
+}
+__device__ __forceinline__ F2 fma2(F2 a, F2 b, F2 c) {  // a b + c
+    F2 o;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(o.r) : "l"(a.r), "l"(b.r), "l"(c.r));
+    return o;
+}
+__device__ __forceinline__ F2 neg2(F2 a) {  // flips both sign bits
+    F2 o;
+    asm("xor.b64 %0, %1, 0x8000000080000000;" : "=l"(o.r) : "l"(a.r));
+    return o;
+}
+
+struct CP {
+    F2 x, y;
+};
+__device__ __forceinline__ CP operator+(CP a, CP b) { return CP{add2(a.x, b.x), add2(a.y, b.y)}; }
+__device__ __forceinline__ CP operator-(CP a, CP b) { return CP{sub2(a.x, b.x), sub2(a.y, b.y)}; }
+// the same twiddle w for both columns
+__device__ __forceinline__ CP operator*(CP a, float2 w) {
+    const F2 wx = f2s(w.x), wy = f2s(w.y), nwy = f2s(-w.y);
+    return CP{fma2(a.y, nwy, mul2(a.x, wx)), fma2(a.y, wx, mul2(a.x, wy))};
+}
+// a different factor per column: g = (g0, g1)
+__device__ __forceinline__ CP cmul2(CP a, float2 g0, float2 g1) {
+    const F2 gx = f2(g0.x, g1.x), gy = f2(g0.y, g1.y), ngy = f2(-g0.y, -g1.y);
+    return CP{fma2(a.y, ngy, mul2(a.x, gx)), fma2(a.y, gx, mul2(a.x, gy))};
+}
+// the constant rotations of the in-register DFT (found by argument-dependent lookup)
+template <int DIR>
+__device__ __forceinline__ CP rot16(CP d, int idx) {
+    if (idx == 0) return d;
+    if (idx == 4) return DIR > 0 ? CP{d.y, neg2(d.x)} : CP{neg2(d.y), d.x};
+    const float c = cos16<float>(idx);
+    const float s = cos16<float>(idx <= 4 ? 4 - idx : idx - 4);
+    if (DIR > 0) return CP{fma2(d.y, f2s(s), mul2(d.x, f2s(c))), fma2(d.x, f2s(-s), mul2(d.y, f2s(c)))};
+    return CP{fma2(d.y, f2s(-s), mul2(d.x, f2s(c))), fma2(d.x, f2s(s), mul2(d.y, f2s(c)))};
+}
+// a row of a 2-column tile as stored in the slab: (re0, im0, re1, im1)
+__device__ __forceinline__ CP cp_of(float4 a) { return CP{f2(a.x, a.z), f2(a.y, a.w)}; }
+__device__ __forceinline__ float4 f4_of(CP a) {
+    float4 o;
+    f2split(a.x, o.x, o.z);
+    f2split(a.y, o.y, o.w);
+    return o;
+}
+
 // Shared-memory element: one complex (CW = 1) or the two complex values of a row of
 // a 2-column tile (CW = 2).
-template <int CW>
+template <int CW, typename V = float2>
 struct Elem;
 template <>
 struct Elem<1> {
@@ -140,12 +219,21 @@ struct Elem<2> {
     }
 };
 
+template <>
+struct Elem<1, CP> {  // in shared memory as (re0, re1, im0, im1)
+    using T = ulonglong2;
+    template <int E>
+    __device__ __forceinline__ static T pack(const CP (&v)[1][E], int q) { return make_ulonglong2(v[0][q].x.r, v[0][q].y.r); }
+    template <int E>
+    __device__ __forceinline__ static void unpack(T a, CP (&v)[1][E], int q) { v[0][q] = CP{F2{a.x}, F2{a.y}}; }
+};
+
 // Outputs of a stage (radix 2^LR, Ns = 2^LS: output (b / Ns) Ns R + b mod Ns + r Ns)
 // through shared memory into the inputs of the next stage (radix 2^LRN).
 // FIRST: the buffer has not been read since the CTA started, no barrier before
 // the stores.
-template <int LR, int LS, int LRN, int LP, int LE, bool FIRST, int CW, int E>
-__device__ __forceinline__ void exchange(float2 (&v)[CW][E], typename Elem<CW>::T* buf, int j) {
+template <int LR, int LS, int LRN, int LP, int LE, bool FIRST, int CW, int E, typename V>
+__device__ __forceinline__ void exchange(V (&v)[CW][E], typename Elem<CW, V>::T* buf, int j) {
     constexpr int R = 1 << LR, RN = 1 << LRN, T = Geo<LP, LE>::T, P = Geo<LP, LE>::P;
     if (!FIRST) __syncthreads();
 #pragma unroll
@@ -153,22 +241,22 @@ __device__ __forceinline__ void exchange(float2 (&v)[CW][E], typename Elem<CW>::
         const int b = j + e * T;
         const int base = ((b >> LS) << (LS + LR)) + (b & ((1 << LS) - 1));
 #pragma unroll
-        for (int r = 0; r < R; ++r) buf[pad16(base + (r << LS))] = Elem<CW>::pack(v, e * R + r);
+        for (int r = 0; r < R; ++r) buf[pad16(base + (r << LS))] = Elem<CW, V>::pack(v, e * R + r);
     }
     __syncthreads();
 #pragma unroll
     for (int e = 0; e < E / RN; ++e) {
         const int b = j + e * T;
 #pragma unroll
-        for (int r = 0; r < RN; ++r) Elem<CW>::unpack(buf[pad16(b + r * (P / RN))], v, e * RN + r);
+        for (int r = 0; r < RN; ++r) Elem<CW, V>::unpack(buf[pad16(b + r * (P / RN))], v, e * RN + r);
     }
 }
 
 // Forward stages S.. (stage S: radix E except the last, 2^LRL; Ns = E^S).
 // In at S = 0: v[.][t] = x[j + t T], x[j + t T] = 0 for t >= E/2.
 // Out: v[.][e R + r] = X[b + r P/R], b = j + e T, R = 2^LRL.
-template <int LP, int LE, int S, bool FIRST, int CW, int E>
-__device__ __forceinline__ void fwd_stages(float2 (&v)[CW][E], typename Elem<CW>::T* buf, int j,
+template <int LP, int LE, int S, bool FIRST, int CW, int E, typename V>
+__device__ __forceinline__ void fwd_stages(V (&v)[CW][E], typename Elem<CW, V>::T* buf, int j,
                                            const float2* __restrict__ tw) {
     using Gm = Geo<LP, LE>;
     constexpr int LR = S < Gm::NS - 1 ? LE : Gm::LRL;
@@ -179,8 +267,8 @@ __device__ __forceinline__ void fwd_stages(float2 (&v)[CW][E], typename Elem<CW>
 
 // Inverse (unnormalised) stages S..: the forward radices in reverse order (2^LRL
 // first).  In at S = 0: the layout fwd_stages leaves.  Out: v[.][t] = x[j + t T].
-template <int LP, int LE, int S, bool FIRST, int CW, int E>
-__device__ __forceinline__ void inv_stages(float2 (&v)[CW][E], typename Elem<CW>::T* buf, int j,
+template <int LP, int LE, int S, bool FIRST, int CW, int E, typename V>
+__device__ __forceinline__ void inv_stages(V (&v)[CW][E], typename Elem<CW, V>::T* buf, int j,
                                            const float2* __restrict__ tw) {
     using Gm = Geo<LP, LE>;
     constexpr int LRL = Gm::LRL;
@@ -426,6 +514,108 @@ __global__ void __launch_bounds__(Geo<LP, LE>::THREADS, MINB) k_cols16_tma(const
     }
 }
 
+// k_cols16_tma with the two columns of a tile in packed FP32x2 registers (CP): every
+// butterfly, rotation, twiddle and Ghat product acts on both columns at once.  Same
+// transforms and summation order as the scalar form; the products are contracted
+// to fused multiply-adds in a fixed pattern (results agree to FP32 rounding).
+template <int LP, int LE, int MINB>
+__global__ void __launch_bounds__(Geo<LP, LE>::THREADS, MINB) k_cols16_tma2(const __grid_constant__ CUtensorMap map,
+                                                                            int n, float2* __restrict__ X,
+                                                                            const float2* __restrict__ ghat,
+                                                                            const float2* __restrict__ tw,
+                                                                            unsigned shortfall) {
+    using Gm = Geo<LP, LE>;
+    constexpr int CW = 2;
+    using EL = typename Elem<1, CP>::T;
+    constexpr int P = Gm::P, T = Gm::T, E = Gm::E, R = 1 << Gm::LRL, Q = P / 2 + 1, G = Gm::G;
+    constexpr int BR = P / 2 < 256 ? P / 2 : 256;
+    constexpr int ntile = P / CW;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    const int grp = threadIdx.x / T, j = threadIdx.x % T;
+    EL* buf = reinterpret_cast<EL*>(smem_raw) + grp * Gm::SLOTS;
+    float4* stg = reinterpret_cast<float4*>(buf);  // the tile's rows as the slab stores them
+    float2* gs = reinterpret_cast<float2*>(smem_raw + sizeof(EL) * G * Gm::SLOTS) + grp * CW * Q;
+    auto* bar = reinterpret_cast<unsigned long long*>(smem_raw + sizeof(EL) * G * Gm::SLOTS +
+                                                      sizeof(float2) * G * CW * Q);
+    int& failed = *reinterpret_cast<int*>(bar + 1);
+    auto tile_of = [&](int g) {
+        const int lin = blockIdx.x * G + g;
+        return (lin & 1) ? (ntile - 1 - (lin >> 1)) : (lin >> 1);
+    };
+    const int kx0 = CW * tile_of(grp);
+    const int nbox = (n + BR - 1) / BR;
+    if (threadIdx.x == 0) {
+        failed = 0;
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(bar)) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const unsigned bytes = (unsigned)(G * nbox * BR * sizeof(EL)) + shortfall;
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(bytes)
+                     : "memory");
+        for (int g = 0; g < G; ++g) {
+            EL* dst = reinterpret_cast<EL*>(smem_raw) + g * Gm::SLOTS;
+            const int x = 2 * CW * tile_of(g);
+            for (int k = 0; k < nbox; ++k) tma_load_2d(dst + k * BR, &map, x, k * BR, bar);
+        }
+    }
+#pragma unroll
+    for (int c = 0; c < CW; ++c) {
+        const int kx = kx0 + c;
+        const float2* g = ghat + (size_t)(kx <= P / 2 ? kx : P - kx) * Q;
+        for (int i = j; i < Q; i += T) cp_async8(gs + c * Q + i, g + i);
+    }
+    cp_async_commit();
+    if (!mbar_wait(bar, 0)) atomicOr(&failed, 1);
+    __syncthreads();
+    if (failed) {
+        if (threadIdx.x == 0) atomicAdd(&g_tma_timeouts, 1u);
+        const float nan = __int_as_float(0x7fc00000);
+        for (int z = j; z < n; z += T)
+            *reinterpret_cast<float4*>(X + (size_t)z * P + kx0) = make_float4(nan, nan, nan, nan);
+        cp_async_wait_all();
+        return;
+    }
+    CP v[1][E];
+    const CP zero{F2{0ull}, F2{0ull}};
+#pragma unroll
+    for (int t = 0; t < E / 2; ++t) {
+        const int z = j + t * T;
+        v[0][t] = z < n ? cp_of(stg[z]) : zero;
+    }
+    fwd_stages<LP, LE, 0, false>(v, buf, j, tw);
+    cp_async_wait_all();
+    __syncthreads();
+#pragma unroll
+    for (int e = 0; e < E / R; ++e)
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int kz = j + e * T + r * (P / R);
+            const int kq = kz <= P / 2 ? kz : P - kz;
+            v[0][e * R + r] = cmul2(v[0][e * R + r], gs[kq], gs[Q + kq]);
+        }
+    inv_stages<LP, LE, 0, false>(v, buf, j, tw);
+    __syncthreads();
+#pragma unroll
+    for (int t = 0; t < E; ++t) {
+        const int z = j + t * T;
+        if (z < nbox * BR) stg[z] = f4_of(v[0][t]);
+    }
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int g = 0; g < G; ++g) {
+            const EL* src = reinterpret_cast<const EL*>(smem_raw) + g * Gm::SLOTS;
+            const int x = 2 * CW * tile_of(g);
+            for (int k = 0; k < nbox; ++k) tma_store_2d(&map, x, k * BR, src + k * BR);
+        }
+        asm volatile("cp.async.bulk.commit_group;\n" ::: "memory");
+        asm volatile("cp.async.bulk.wait_group.read 0;\n" ::: "memory");
+    }
+}
+
 // Pass 3: y[z, x] = u[z, x] + IFFT_x(X[z, :])[x] for x < n (radix 16).  The row of u
 // is copied to shared memory asynchronously at the start (each thread fetches the
 // elements it will write), so its latency hides behind the inverse transform.
@@ -489,7 +679,7 @@ constexpr size_t row_smem16() {
 // Column-pass tile shapes (ls_handle::fft_variant): 0 = radix 16, 1 column, 3 CTAs/SM;
 // 2 = radix 16, 2 columns, 2 CTAs/SM; 3 = radix 16, 1 column, 2 CTAs/SM;
 // 4 = radix 8, 1 column, 2 CTAs/SM (of up to 512 threads); 5 = radix 8, 2 columns, 1 CTA/SM;
-// 6, 7 = shapes 2, 5 with the tiles moved by TMA.
+// 6, 7 = shapes 2, 5 with the tiles moved by TMA; 8 = shape 6 in packed FP32x2 arithmetic.
 template <int LP, int LE, int CW, int MINB>
 int cols_launch(ls_handle* h, int n, float2* X, const float2* gh, const float2* tw) {
     using Gm = Geo<LP, LE>;
@@ -514,7 +704,7 @@ PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
     return fn;
 }
 
-template <int LP, int LE, int MINB>
+template <int LP, int LE, int MINB, bool PACKED = false>
 int cols_launch_tma(ls_handle* h, int n, float2* X, const float2* gh, const float2* tw) {
     using Gm = Geo<LP, LE>;
     constexpr int P = Gm::P, BR = P / 2 < 256 ? P / 2 : 256;
@@ -529,8 +719,12 @@ int cols_launch_tma(ls_handle* h, int n, float2* X, const float2* gh, const floa
             CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
         return LS_ECUDA;
-    LS_LAUNCH(h, (k_cols16_tma<LP, LE, MINB>), (unsigned)(P / 2 / Gm::G), Gm::THREADS, (cols_tma_smem<LP, LE>()), map,
-              n, X, gh, tw, g_tma_shortfall);
+    if constexpr (PACKED)
+        LS_LAUNCH(h, (k_cols16_tma2<LP, LE, MINB>), (unsigned)(P / 2 / Gm::G), Gm::THREADS, (cols_tma_smem<LP, LE>()),
+                  map, n, X, gh, tw, g_tma_shortfall);
+    else
+        LS_LAUNCH(h, (k_cols16_tma<LP, LE, MINB>), (unsigned)(P / 2 / Gm::G), Gm::THREADS, (cols_tma_smem<LP, LE>()),
+                  map, n, X, gh, tw, g_tma_shortfall);
     return LS_OK;
 }
 
@@ -550,6 +744,7 @@ int apply_lp(ls_handle* h, const UIO* u, UIO* y, float2* X, int shape) {
         case 5: LS_TRY((cols_launch<LP, 3, 2, 1>(h, n, X, gh, tw))); break;
         case 6: LS_TRY((cols_launch_tma<LP, 4, 2>(h, n, X, gh, tw))); break;
         case 7: LS_TRY((cols_launch_tma<LP, 3, 1>(h, n, X, gh, tw))); break;
+        case 8: LS_TRY((cols_launch_tma<LP, 4, 2, true>(h, n, X, gh, tw))); break;
         default: LS_TRY((cols_launch<LP, 4, 1, 3>(h, n, X, gh, tw))); break;
     }
     LS_LAUNCH(h, (k_rows16_inv<LP, UIO>), rows_grid, Gm::THREADS, (rinv_smem<LP, UIO>()), n, n, X, u, y, tw);
@@ -584,6 +779,7 @@ int optin_lp() {
     LS_TRY(optin(k_cols16<LP, 3, 2, 1>, cols_smem<LP, 3, 2>()));
     LS_TRY(optin(k_cols16_tma<LP, 4, 2>, cols_tma_smem<LP, 4>()));
     LS_TRY(optin(k_cols16_tma<LP, 3, 1>, cols_tma_smem<LP, 3>()));
+    LS_TRY(optin(k_cols16_tma2<LP, 4, 2>, cols_tma_smem<LP, 4>()));
     LS_TRY(optin(k_rows16_inv<LP, float2>, rinv_smem<LP, float2>()));
     return optin(k_rows16_inv<LP, double2>, rinv_smem<LP, double2>());
 }

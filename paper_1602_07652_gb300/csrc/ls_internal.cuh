@@ -188,7 +188,7 @@ struct ls_handle {
     int fft_variant = 2;       // column-pass shape (256 <= P <= 4096): radix 16 with 0 = 1-column tiles,
                                // 3 CTAs/SM; 2 = 2-column tiles; 3 = 1-column tiles, 2 CTAs/SM; radix 8 with
                                // 4 = 1-column tiles; 5 = 2-column tiles.  1: generic radix-8 4-column tiles
-    static constexpr int kFftVariants = 8;
+    static constexpr int kFftVariants = 9;
     int bd_chunk = 0;          // right-hand sides per Algorithm 2 chain (0: the largest supported)
     int cr_split = 1;          // 1: reduction steps of small levels split blocks over several CTAs
 

@@ -202,7 +202,7 @@ def test_autotuner_choices_keep_results(prec):
     u0, _, _ = s.ls_solve_batch(f, 1e-9)
     y0 = s.ls_apply_mixed(f[0].contiguous())
     t = s.ls_autotune(nrhs=4, reps=2)
-    assert t["fft_variant"] in range(8) and t["bd_chunk"] in (1, 2, 4)
+    assert t["fft_variant"] in range(9) and t["bd_chunk"] in (1, 2, 4)
     assert all(x > 0 for x in t["fft_ms"])  # P = 256: every tile shape exists
     assert all(x > 0 for x in t["bd_ms_per_rhs"][:3])
     u1, st, rc = s.ls_solve_batch(f, 1e-9)

@@ -102,15 +102,17 @@ def test_fp32_apply_every_tile_shape(n, L):
     u = inputs.random_field(n, 5)
     y_ref = greens.apply_H(u, m, 1.0 / n, w)
     ys = {}
-    for v in range(8):
+    for v in range(9):
         s.ls_set_shapes(v)
         ys[v] = s.ls_apply_mixed(cuda(u)).cpu().numpy()
         assert rel(ys[v], y_ref) < 2e-5, v
     # the TMA shapes move the same tiles: the same arithmetic, bit for bit
     assert np.array_equal(ys[6], ys[2]) and np.array_equal(ys[7], ys[5])
+    # shape 8 pairs the two columns in FP32x2 instructions: other FMA contractions
+    assert rel(ys[8], ys[6]) < 1e-6
     assert binding.device_timeouts() == 0
     with pytest.raises(binding.LSError):
-        s.ls_set_shapes(8)
+        s.ls_set_shapes(9)
     s.close()
 
 
@@ -238,7 +240,8 @@ def test_bd_graph_replay_equals_direct_launches():
     assert torch.equal(outs[0], outs[2]) and torch.equal(outs[2], outs[3]) and torch.equal(outs[0], outs[1])
 
 
-def test_tma_wait_that_runs_out_marks_the_tiles_and_is_counted():
+@pytest.mark.parametrize("shape", [6, 8])
+def test_tma_wait_that_runs_out_marks_the_tiles_and_is_counted(shape):
     # the barrier expects 16 bytes more than the boxes bring: every CTA's wait runs
     # out after one second with no copy in flight, writes its tiles as NaN, counts
     # itself and returns; the context stays usable and the next apply is exact again
@@ -247,9 +250,8 @@ def test_tma_wait_that_runs_out_marks_the_tiles_and_is_counted():
     m = inputs.bump_medium(n, nbumps=6, seed=7)
     s = binding.Solver(cuda(m), w, layers=L, ext=3, precision=binding.LS_MIXED)
     u = cuda(inputs.random_field(n, 5))
-    s.ls_set_shapes(2)
+    s.ls_set_shapes(shape)
     y_ref = s.ls_apply_mixed(u).cpu()
-    s.ls_set_shapes(6)
     before = binding.device_timeouts()
     with pytest.raises(binding.LSError):
         binding.test_tma_shortfall(8)
