@@ -404,8 +404,9 @@ def run_ours(args):
         ach = bytes_apply / (t_app / n_app / 1e3) / 1e9 if n_app else None
         # DRAM read + write bytes of one apply (three passes) from the ncu capture summarised in
         # profiles/ls_apply_mixed_2048_fft16.md: column-pass shape 2 at 2048^2 only
-        # DRAM read + write of the three passes from one ncu capture per tile shape (2048^2)
-        traffic = {2: 380.1e6, 6: 376.6e6, 8: 377.8e6}.get(tune.get("fft_variant")) if (not args.fp64 and n == 2048) else None
+        # DRAM read + write of the three passes per tile shape (2048^2), each kernel's from an
+        # ncu capture of its current code
+        traffic = {2: 378.2e6, 6: 374.1e6, 8: 375.3e6}.get(tune.get("fft_variant")) if (not args.fp64 and n == 2048) else None
         outer = statistics.mean(st["outer_iters"] for st in stats) / B  # per right-hand side
         inner = statistics.mean(st["inner_iters_total"] for st in stats) / B
         value = job_seconds_per_rhs(ms, args.steps, B, world)

@@ -265,11 +265,17 @@ __device__ __forceinline__ void fwd_stages(V (&v)[CW][E], typename Elem<CW, V>::
     if constexpr (S + 1 < Gm::NS) fwd_stages<LP, LE, S + 1, FIRST>(v, buf, j, tw);
 }
 
+struct NoHook {
+    __device__ __forceinline__ void operator()() const {}
+};
+
 // Inverse (unnormalised) stages S..: the forward radices in reverse order (2^LRL
 // first).  In at S = 0: the layout fwd_stages leaves.  Out: v[.][t] = x[j + t T].
-template <int LP, int LE, int S, bool FIRST, int CW, int E, typename V>
+// before_last runs after the last exchange, before the last stage (the exchange
+// buffer is then free once every thread has passed a barrier).
+template <int LP, int LE, int S, bool FIRST, int CW, int E, typename V, typename Hook = NoHook>
 __device__ __forceinline__ void inv_stages(V (&v)[CW][E], typename Elem<CW, V>::T* buf, int j,
-                                           const float2* __restrict__ tw) {
+                                           const float2* __restrict__ tw, const Hook& before_last = Hook{}) {
     using Gm = Geo<LP, LE>;
     constexpr int LRL = Gm::LRL;
     constexpr int LR = S == 0 ? LRL : LE;
@@ -279,8 +285,9 @@ __device__ __forceinline__ void inv_stages(V (&v)[CW][E], typename Elem<CW, V>::
         constexpr int LSP = S == 1 ? 0 : LRL + LE * (S - 2);
         exchange<LRP, LSP, LR, LP, LE, FIRST && S == 1>(v, buf, j);
     }
+    if constexpr (S + 1 == Gm::NS) before_last();
     stage<LR, LS, -1, LP, LE, false>(v, j, tw);
-    if constexpr (S + 1 < Gm::NS) inv_stages<LP, LE, S + 1, FIRST>(v, buf, j, tw);
+    if constexpr (S + 1 < Gm::NS) inv_stages<LP, LE, S + 1, FIRST>(v, buf, j, tw, before_last);
 }
 
 // Pass 1: X[z, :] = FFT_x(pad(m u)[z, :]) for rows z < nrows (radix 16).
@@ -617,10 +624,11 @@ __global__ void __launch_bounds__(Geo<LP, LE>::THREADS, MINB) k_cols16_tma2(cons
 }
 
 // Pass 3: y[z, x] = u[z, x] + IFFT_x(X[z, :])[x] for x < n (radix 16).  The row of u
-// is copied to shared memory asynchronously at the start (each thread fetches the
-// elements it will write), so its latency hides behind the inverse transform.
+// is copied asynchronously into the exchange buffer once the last exchange is done
+// (each thread fetches the elements it will write), so its latency hides behind the
+// last stage, and the CTA needs no shared memory beyond the exchange buffer.
 template <int LP, typename UIO>
-__global__ void __launch_bounds__(Geo<LP, 4>::THREADS) k_rows16_inv(int nrows, int n, const float2* __restrict__ X,
+__global__ void __launch_bounds__(Geo<LP, 4>::THREADS, 4) k_rows16_inv(int nrows, int n, const float2* __restrict__ X,
                                                                     const UIO* __restrict__ u, UIO* __restrict__ y,
                                                                     const float2* __restrict__ tw) {
     using Gm = Geo<LP, 4>;
@@ -628,24 +636,27 @@ __global__ void __launch_bounds__(Geo<LP, 4>::THREADS) k_rows16_inv(int nrows, i
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int grp = threadIdx.x / T, j = threadIdx.x % T;
     float2* buf = reinterpret_cast<float2*>(smem_raw) + grp * Gm::SLOTS;
-    UIO* us = reinterpret_cast<UIO*>(smem_raw + sizeof(float2) * Gm::G * Gm::SLOTS) + grp * (P / 2);
+    UIO* us = reinterpret_cast<UIO*>(buf);  // the row of u, once the exchanges are done
     const int z = blockIdx.x * Gm::G + grp;
     const bool live = z < nrows;
-    if (live) {
-#pragma unroll
-        for (int t = 0; t < E / 2; ++t) {
-            const int x = j + t * T;
-            if (x < n) cp_async_el(us + x, u + (size_t)z * n + x);
-        }
-    }
-    cp_async_commit();
     float2 v[1][E];
     const float2* xr = X + (size_t)(live ? z : 0) * P;
 #pragma unroll
     for (int e = 0; e < E / R; ++e)
 #pragma unroll
         for (int r = 0; r < R; ++r) v[0][e * R + r] = xr[j + e * T + r * (P / R)];
-    inv_stages<LP, 4, 0, true>(v, buf, j, tw);
+    auto prefetch_u = [&]() {
+        __syncthreads();  // every thread has read its last exchange
+        if (live) {
+#pragma unroll
+            for (int t = 0; t < E / 2; ++t) {
+                const int x = j + t * T;
+                if (x < n) cp_async_el(us + x, u + (size_t)z * n + x);
+            }
+        }
+        cp_async_commit();
+    };
+    inv_stages<LP, 4, 0, true>(v, buf, j, tw, prefetch_u);
     cp_async_wait_all();  // this thread's own copies: no barrier needed
     if (!live) return;
 #pragma unroll
@@ -655,12 +666,13 @@ __global__ void __launch_bounds__(Geo<LP, 4>::THREADS) k_rows16_inv(int nrows, i
     }
 }
 
-// Shared memory: G transforms of P elements, padded (one slot per 16), plus the
-// prefetched u rows (G * P/2 elements) or Ghat rows (G * CW * (P/2 + 1)).
+// Shared memory: G transforms of P elements, padded (one slot per 16), plus, in the
+// column pass, the prefetched Ghat rows (G * CW * (P/2 + 1)).
 template <int LP, typename UIO>
-constexpr size_t rinv_smem() {
+constexpr size_t rinv_smem() {  // the row of u (P/2 elements) reuses the exchange buffer
     using Gm = Geo<LP, 4>;
-    return sizeof(float2) * Gm::G * Gm::SLOTS + sizeof(UIO) * Gm::G * (Gm::P / 2);
+    static_assert(sizeof(UIO) * (Gm::P / 2) <= sizeof(float2) * Gm::SLOTS, "u row must fit");
+    return sizeof(float2) * Gm::G * Gm::SLOTS;
 }
 template <int LP, int LE, int CW>
 constexpr size_t cols_smem() {
