@@ -6,6 +6,7 @@ adaptive quadrature of the exact integral (Sec. 2, order h^4 log h), brute-force
 O(N^2) sums (Sec. 2, Toeplitz/FFT apply), and exact identities of H.
 """
 import math
+import os
 
 import numpy as np
 import pytest
@@ -174,3 +175,32 @@ def test_cached_convolution_equals_apply_H():
     assert np.array_equal(op.H(u, m), greens.apply_H(u, m, h, w))
     ui = greens.incident_plane_wave(n, w, 0.3)
     assert np.array_equal(op.rhs(m, ui), greens.rhs(m, h, w, ui))
+
+
+def _table(name):
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", name)
+    return np.loadtxt(path, comments="#")
+
+
+def test_kernel_weights_match_tabulated_hankel_values():
+    # G_w(d) = h^2 (-i/4) (J_0 + i Y_0)(w h |d|) off the diagonal: real part h^2 Y_0 / 4,
+    # imaginary part -h^2 J_0 / 4.  Offsets along an axis and along the 3-4-5 and 6-8-10
+    # diagonals reach the tabulated arguments, so the |d| norm is pinned as well.
+    tab = {float(x): (j0, y0) for x, j0, y0 in _table("bessel_j0_y0.txt")}
+    h, w = 0.01, 50.0            # w h = 0.5
+    K = 20
+    W = greens.kernel_weights(K, h, w)
+    offsets = [(1, 0), (0, 2), (-3, 0), (0, -4), (5, 0), (6, 0), (0, 10), (20, 0),
+               (3, 4), (-4, 3), (6, -8), (-12, -16)]
+    for dx, dz in offsets:
+        if max(abs(dx), abs(dz)) > K:
+            continue
+        x = round(w * h * math.hypot(dx, dz), 12)
+        j0, y0 = tab[x]
+        g = W[dz + K, dx + K]
+        assert abs(g.real - h * h * y0 / 4) < 1e-10 * h * h, (dx, dz)
+        assert abs(g.imag + h * h * j0 / 4) < 1e-10 * h * h, (dx, dz)
+    # and G itself at the tabulated arguments (r = x / w)
+    for x, (j0, y0) in tab.items():
+        g = complex(greens.green(x / w, w))
+        assert abs(g - (-0.25j) * complex(j0, y0)) < 1e-10, x
