@@ -20,11 +20,12 @@
 //
 // The column pass reads and writes 16-byte row segments (2 columns) of the
 // row-major n x P slab, one per row at a stride of 8P bytes.  Through the LSU each
-// such warp access touches 32 separate lines; the TMA shapes (6, 7) move the
+// such warp access touches 32 separate lines; the TMA shapes (6, 7, 8) move the
 // tile instead with cp.async.bulk.tensor in boxes of up to 256 rows into shared
 // memory and back, completion tracked by an mbarrier (a wait bounded in time:
 // on expiry the tile is written as NaN and a device counter is raised, so the
-// solver's residual checks see it).
+// solver's residual checks see it).  Shape 8 also keeps the two columns of a
+// tile in packed FP32x2 registers, one instruction per operation on both.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
