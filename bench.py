@@ -45,7 +45,9 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=N_DEFAULT)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--e2e-steps", type=int, default=None,
+                    help="steps of the end-to-end (host buffers) leg; default: --steps, the same "
+                         "directions as the device-timed steps")
     ap.add_argument("--batch", type=int, default=BATCH_DEFAULT,
                     help="right-hand sides (incident directions) solved together per step")
     ap.add_argument("--apply-only", action="store_true",
@@ -371,6 +373,8 @@ def run_ours(args):
     # steps, right-hand sides prepared in pinned host memory beforehand; each step copies
     # f host->device, solves, and copies u device->host inside the timed region
     e2e = None
+    if args.e2e_steps is None:
+        args.e2e_steps = args.steps
     if args.e2e_steps > 0:
         f_hosts = []
         for k in range(args.e2e_steps):
