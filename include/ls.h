@@ -236,18 +236,20 @@ int ls_set_shapes(ls_handle* h, int fft_variant, int bd_chunk);
  * rounding in either form. */
 int ls_set_reduction(ls_handle* h, int cr_split);
 
-/* ls_device_timeouts -- *count = how many CTAs of the TMA tile shapes (6, 7, 8) found
- * their column tiles not arrived within one second since the library was loaded; 0
- * in a healthy run.  Such a CTA writes its tiles as NaN (so the solver's residual
- * checks reject the result) and returns instead of waiting on.  Synchronous read of
- * a device counter.  LS_EINVAL if count is NULL. */
+/* ls_device_timeouts -- health counter of the LS-apply's TMA column pass (Sec. 2 defines
+ * the apply; the paper has no counterpart of this counter): *count = how many CTAs of
+ * the TMA tile shapes (6, 7, 8) found their column tiles not arrived within one second
+ * since the library was loaded; 0 in a healthy run.  Such a CTA writes its tiles as NaN
+ * (so the solver's residual checks reject the result) and returns instead of waiting
+ * on.  Synchronous read of a device counter.  LS_EINVAL if count is NULL. */
 int ls_device_timeouts(unsigned* count);
 
-/* ls_test_tma_shortfall -- test hook for the timeout path above: every later launch of
- * the TMA column pass (any handle) makes its barrier expect `bytes` more than its
- * boxes deliver, so each of its waits runs out after one second with every copy
- * already landed.  0 (the default) restores normal operation.  bytes: a multiple of
- * 16, at most 4096, else LS_EINVAL.  Not thread-safe against concurrent applies. */
+/* ls_test_tma_shortfall -- test hook for the timeout path above (no counterpart in the
+ * paper): every later launch of the TMA column pass (any handle) makes its barrier
+ * expect `bytes` more than its boxes deliver, so each of its waits runs out after one
+ * second with every copy already landed.  0 (the default) restores normal operation.
+ * bytes: a multiple of 16, at most 4096, else LS_EINVAL.  Not thread-safe against
+ * concurrent applies. */
 int ls_test_tma_shortfall(unsigned bytes);
 
 /* ---- learned preconditioner step (an addition: the paper has no network) ----
