@@ -44,7 +44,10 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=N_DEFAULT)
-    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true",
+                    help="skip the timed oracle sample (the CPU baseline)")
+    ap.add_argument("--no-fp64-leg", action="store_true", help="skip the plain FP64 GPU leg")
+    ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--e2e-steps", type=int, default=None,
                     help="steps of the end-to-end (host buffers) leg; default: --steps, the same "
                          "directions as the device-timed steps")
@@ -202,75 +205,148 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def cpu_baseline(wl, outer_iters, inner_iters, max_seconds=30.0):
-    """Time the FP64 oracle on a bounded sample of the same workload and project s/RHS.
+def host_info():
+    """Host CPU as the oracle legs see it: logical CPUs, the ones this process may use, model."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.startswith("Model name:"):
+                model = ln.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    if model is None:
+        try:
+            with open("/proc/cpuinfo") as f:
+                for ln in f:
+                    if ln.lower().startswith("model name"):
+                        model = ln.split(":", 1)[1].strip()
+                        break
+        except Exception:
+            pass
+    try:
+        usable = len(os.sched_getaffinity(0))
+    except Exception:
+        usable = os.cpu_count()
+    return {"nproc": os.cpu_count(), "usable": usable, "model": model, "machine": os.uname().machine}
 
-    Sample: (1) one oracle LS-apply of H at the full size (including the
-    oracle's own evaluation of the quadrature weights, as it stands); (2) local
-    solves of one layered strip of the same height q = t + 2E and the same
-    w h, but 256 columns long, scaled by n / 256 (a local solve costs O(n q^2),
-    linear in the strip length).  The projection multiplies them by the solve's
-    operation counts: one H apply per outer iteration and 2(2L - 1) local
-    solves (Algorithm 2: two directions, L down + L-1 up) per inner iteration.
-    """
+
+THREAD_VARS = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")
+
+
+C1_SCRIPT = r"""
+import json, math, sys, time
+sys.path.insert(0, %r)
+from oracle import solver
+from paper_1602_07652_gb300 import inputs
+n, L = 64, 4
+w = 2 * math.pi * 8
+m = inputs.gaussian_disk_medium(n)
+out = []
+for _ in range(3):
+    t0 = time.perf_counter()
+    prob = solver.Problem(m, w, L=L, E=10)
+    t1 = time.perf_counter()
+    u, info = solver.solve(prob, prob.rhs(0.0), tol=1e-8)
+    t2 = time.perf_counter()
+    out.append([t1 - t0, t2 - t1, info["iters"], info["relres"]])
+print(json.dumps(out))
+"""
+
+
+def c1_oracle_times():
+    """The oracle's full solve of the 64^2 configuration (w = 2 pi 8, Gaussian disk medium,
+    theta = 0, 4 layers, tol 1e-8), single-core and all-core: median of 3 runs each, in
+    fresh processes with the BLAS thread count fixed."""
+    res = {}
+    for label, threads in (("single_core", 1), ("all_cores", os.cpu_count() or 1)):
+        env = dict(os.environ)
+        for v in THREAD_VARS:
+            env[v] = str(threads)
+        try:
+            out = subprocess.run([sys.executable, "-c", C1_SCRIPT % ROOT], capture_output=True, text=True,
+                                 env=env, timeout=600)
+            runs = json.loads(out.stdout.strip().splitlines()[-1])
+            res[label] = {"threads": threads, "setup_s": statistics.median(r[0] for r in runs),
+                          "solve_s": statistics.median(r[1] for r in runs), "outer": runs[0][2],
+                          "relres": runs[0][3], "runs": 3}
+        except Exception as e:
+            res[label] = {"threads": threads, "failed": str(e)[:200]}
+    return res
+
+
+def oracle_digest(n):
+    """The stored digest of the FP64 oracle's solution of the benchmark problem at size n
+    (tests/golden/make_oracle_digests.py runs only the oracle): the field's sketch and
+    sampled values, and the oracle's own iteration counts at the benchmark tolerance."""
+    try:
+        with open(os.path.join(ROOT, "tests", "golden", "oracle_digest_%d.json" % n)) as f:
+            return json.load(f)
+    except Exception:
+        return None
+
+
+def oracle_sample(wl, counts, steps, warmup=0):
+    """The FP64 oracle timed on a bounded sample of the benchmark workload: one oracle
+    LS-apply at full size and one oracle local solve of a full-size layered strip (its
+    banded LU factored once, before the timed samples), projected to seconds per
+    right-hand side with the oracle's own iteration counts on this problem: one H apply
+    per outer iteration, 2 (2L - 1) local solves per inner iteration (Algorithm 2 over
+    two directions).  Returns (median s/RHS, per-sample wall ms, description)."""
     from oracle import greens, polarized, sparsify
     from paper_1602_07652_gb300 import inputs
     n, w, L, E = wl["n"], wl["omega"], wl["layers"], wl["ext"]
-    h = 1.0 / n
+    outer, inner = counts["outer"], counts["inner_total"]
     m = inputs.bump_medium(n, nbumps=20, seed=0)
+    t0 = time.perf_counter()
+    conv = greens.Convolution(n, 1.0 / n, w)
+    st = sparsify.Stencils(n, 1.0 / n, w)
+    lay = polarized.Layering(m, st, w, L, E)
+    t_prep = time.perf_counter() - t0
     u = inputs.random_field(n, 0)
-    t0 = time.perf_counter()
-    greens.apply_H(u, m, h, w)
-    t_apply = time.perf_counter() - t0
-    t = n // L
-    ns = 256
-    Ls = ns // t
-    ws = w * ns / n
-    ms_ = inputs.bump_medium(ns, nbumps=20, seed=0)
-    st = sparsify.Stencils(ns, 1.0 / ns, ws)
-    lay = polarized.Layering(ms_, st, ws, Ls, E)
-    b = inputs.random_field(ns, 1, nz=lay.q)
-    reps = 0
-    t0 = time.perf_counter()
-    while True:
-        lay.solve_local(Ls // 2, b)
-        reps += 1
-        if reps >= 20 or time.perf_counter() - t0 > max_seconds / 3:
-            break
-    t_local = (time.perf_counter() - t0) / reps * (n / ns)
-    per_rhs = outer_iters * t_apply + inner_iters * 2 * (2 * L - 1) * t_local
-    return {"value": per_rhs, "unit": "s/RHS", "cores": 1, "kind": "oracle",
-            "sample": "oracle: 1 FFT LS-apply at %d^2 (%.2f s) + %d sparse-LU local solves of a %dx%d strip "
-                      "scaled x%d to %dx%d (%.3f s each); projected with %g outer and %g inner iterations "
-                      "(%d local solves each)" % (n, t_apply, reps, lay.q, ns, n // ns, lay.q, n, t_local,
-                                                  outer_iters, inner_iters, 2 * (2 * L - 1))}
+    b = inputs.random_field(n, 1, nz=lay.q)
+    step_ms, vals = [], []
+    for k in range(warmup + steps):
+        t0 = time.perf_counter()
+        conv.H(u, m)
+        t1 = time.perf_counter()
+        lay.solve_local(L // 2, b)
+        t2 = time.perf_counter()
+        if k >= warmup:
+            step_ms.append((t2 - t0) * 1e3)
+            vals.append(outer * (t1 - t0) + inner * 2 * (2 * L - 1) * (t2 - t1))
+    desc = ("per sample: one oracle LS-apply at %d^2 and one banded-LU local solve of a full %dx%d strip "
+            "(one core: numpy FFT, sparse LU); projected with the oracle's own %d outer / %d inner iterations "
+            "per right-hand side at tol %g (2(2L-1) = %d local solves per inner iteration); set-up of one "
+            "direction's strips %.1f s not included" % (n, lay.q, n, outer, inner, wl["tol"], 2 * (2 * L - 1), t_prep))
+    return statistics.median(vals), step_ms, desc
 
 
 def run_reference(args):
+    """The FP64 oracle timed on the host cores (rank 0 only), on a bounded sample of the
+    benchmark workload per step (oracle_sample); ms_per_step is what a step took."""
     wl = workload(args.n)
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
-    # outer / inner iteration counts per right-hand side that the GPU solver needs on this workload
-    outer, inner = REF_COUNTS.get(args.n, (6, 30))
-    vals = []
-    for _ in range(args.warmup + args.steps):
-        vals.append(cpu_baseline(wl, outer, inner, max_seconds=10.0))
-    timed = vals[args.warmup:]
-    v = statistics.median(x["value"] for x in timed)
+    dg = oracle_digest(wl["n"])
+    if dg is None:
+        print(json.dumps({"impl": "reference", "unavailable": "no stored oracle digest for n=%d" % wl["n"]}))
+        return 0
+    counts = dg["at_tol_1e-6"]
+    v, step_ms, desc = oracle_sample(wl, counts, args.steps, args.warmup)
     out = {"impl": "reference", "metric": METRIC, "value": v, "unit": "s/RHS", "n_gpus": args.gpus,
-           "steps": args.steps, "warmup": args.warmup, "ms_per_step": v * 1000.0, "higher_is_better": False,
-           "scaling": "weak", "vs_baseline": None, "dtype": "c128", "data": "synthetic",
-           "config": config_dict(wl, "fp64 oracle"),
-           "cpu_baseline": {"kind": "oracle", "cores": 1, "sample": timed[-1]["sample"], "value": v, "unit": "s/RHS"},
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": statistics.mean(step_ms),
+           "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "c128",
+           "data": "synthetic", "config": config_dict(wl, "fp64 oracle"),
+           "cpu_baseline": {"kind": "oracle", "cores": 1, "sample": desc, "value": v, "unit": "s/RHS",
+                            "host": host_info(), "oracle_counts": counts},
            "e2e": {"value": v, "unit": "s/RHS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    if not args.no_cpu_baseline:
+        out["c1_full_solve"] = c1_oracle_times()
     print(json.dumps(out))
     return 0
-
-
-# outer / inner iteration counts per right-hand side of the benchmark workload, measured by the
-# GPU solver (used by the reference arm to project the oracle's per-iteration cost)
-REF_COUNTS = {2048: (3.86, 11.9)}
 
 
 N_DIRECTIONS = 64
@@ -300,17 +376,17 @@ def job_seconds_per_rhs(ms_max, steps, batch, world):
 
 
 def run_ours(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    wl = workload(args.n)
     import torch
     import torch.distributed as dist
     from paper_1602_07652_gb300 import binding, inputs
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
     if world > 1:
         dist.init_process_group("nccl")
-    wl = workload(args.n)
     n = wl["n"]
     m = inputs.bump_medium(n, nbumps=20, seed=0)
     t0 = time.perf_counter()
@@ -346,8 +422,11 @@ def run_ours(args):
         _, st, _ = s.ls_solve_batch(f, wl["tol"], u)
         return st
 
+    u_first = None
     for k in range(args.warmup):
         step(k)
+        if k == 0:
+            u_first = u[0].cpu().numpy()   # direction theta(0): the field the oracle also solves
     s.ls_set_timing(True)
     stream = s.stream
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -400,17 +479,14 @@ def run_ours(args):
                        "frac": (fl / t_factor / 1e12 / dpk) if dpk else None, "flops": fl}
         n_app = sum(st["n_apply"] for st in stats)
         t_app = sum(st["t_apply_ms"] for st in stats)
-        # mixed LS-apply: FP64 input/output, FP32 arithmetic; algorithmic bytes per apply:
-        # pass 1 reads u (16 n^2) and m (4 n^2), writes n x P FP32 (16 n^2); pass 2 reads and
-        # writes it (32 n^2) and reads the Ghat quadrant (8 n^2); pass 3 reads it (16 n^2) and
-        # u (16 n^2) and writes y (16 n^2): 124 n^2 bytes.
-        bytes_apply = (200.0 if args.fp64 else 124.0) * n * n   # FP64: 16 + 8 + 32 + 32 + 16 + 32 + 32 + 32 n^2
+        # algorithmic bytes of one LS-apply (three HBM passes over the n x P slab, P = 2n):
+        # FP32: pass 1 reads u (8 n^2) and m (4 n^2) and writes the slab (16 n^2); pass 2
+        # reads and writes it (32 n^2) and reads the Ghat quadrant (8 n^2); pass 3 reads it
+        # (16 n^2) and u (8 n^2) and writes y (8 n^2): 100 n^2.  FP64: 200 n^2.  The solve's
+        # mixed apply takes and returns FP64 fields (24 n^2 more moved); the method's bytes
+        # are the FP32 ones, so those are what the fraction is taken on.
+        bytes_apply = (200.0 if args.fp64 else 100.0) * n * n
         ach = bytes_apply / (t_app / n_app / 1e3) / 1e9 if n_app else None
-        # DRAM read + write bytes of one apply (three passes) from the ncu capture summarised in
-        # profiles/ls_apply_mixed_2048_fft16.md: column-pass shape 2 at 2048^2 only
-        # DRAM read + write of the three passes per tile shape (2048^2), each kernel's from an
-        # ncu capture of its current code
-        traffic = {2: 378.2e6, 6: 374.1e6, 8: 375.3e6}.get(tune.get("fft_variant")) if (not args.fp64 and n == 2048) else None
         outer = statistics.mean(st["outer_iters"] for st in stats) / B  # per right-hand side
         inner = statistics.mean(st["inner_iters_total"] for st in stats) / B
         value = job_seconds_per_rhs(ms, args.steps, B, world)
@@ -419,8 +495,10 @@ def run_ours(args):
                "scaling": "weak", "vs_baseline": None, "dtype": "c128" if args.fp64 else "mixed c64/c128",
                "data": "synthetic",
                "config": config_dict(wl, "fp64" if args.fp64 else "mixed", rhs_per_step=B),
+               # traffic: DRAM bytes per launch need an ncu capture of the current kernels;
+               # this run takes none, so it is null here (the committed summaries give it)
                "roofline": {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
-                            "frac": (ach / hbm) if ach else None, "traffic": traffic,
+                            "frac": (ach / hbm) if ach else None, "traffic": None,
                             "kernel": "LS-apply (3 FFT passes), " + ("FP64" if args.fp64 else
                                                                       "FP32 arithmetic, FP64 I/O"),
                             "algorithmic_bytes": bytes_apply, "peak_source": src,
@@ -440,17 +518,69 @@ def run_ours(args):
                "time_shares": {"algorithm2": sum(st["t_sweep_ms"] for st in stats) / ms,
                                "ls_apply_fp32": t_app / ms,
                                "ls_apply_fp64_refinement": sum(st["t_apply64_ms"] for st in stats) / ms}}
-        if not args.no_cpu_baseline:
+    s.close()
+    if rank == 0 and world == 1 and not args.fp64 and not args.no_fp64_leg:
+        # the plain FP64 GPU method on the same problem and tolerance, one right-hand side at
+        # a time (directions of the first timed step), outside the timed region
+        try:
+            out["fp64_reference"] = fp64_leg(wl, theta, args.warmup * B, steps=args.fp64_steps)
+            out["fp64_reference"]["mixed_batched_speedup"] = out["fp64_reference"]["value"] / out["value"]
+        except Exception as e:
+            out["fp64_reference"] = {"value": None, "failed": str(e)[:300]}
+    if rank == 0 and world == 1:
+        dg = oracle_digest(n)
+        if dg is not None and u_first is not None:
+            # the GPU field of the first incident wave against the oracle's (solved to 1e-10)
+            from tests.golden import digest as _dig
+            c = _dig.compare(u_first, dg)
+            out["error_vs_oracle"] = {"rel_l2": c["rel_l2_est"], "max_rel_points": c["max_rel_points"],
+                                      "how": "sketch of the field (about 2 % accurate) and its values at %d "
+                                             "seeded points vs the stored digest of the FP64 oracle's field "
+                                             "solved to %g" % (len(dg["points"]), dg["tol"]),
+                                      "gpu": "mixed precision, batched, tol %g, first incident wave" % wl["tol"]}
+        if not args.no_cpu_baseline and dg is not None:
             try:
-                out["cpu_baseline"] = cpu_baseline(wl, outer, inner)
+                v, step_ms, desc = oracle_sample(wl, dg["at_tol_1e-6"], steps=3)
+                out["cpu_baseline"] = {"value": v, "unit": "s/RHS", "cores": 1, "kind": "oracle", "sample": desc,
+                                       "sample_ms": step_ms, "host": host_info(),
+                                       "c1_full_solve": c1_oracle_times()}
             except Exception as e:  # the baseline is reported, never required
                 out["cpu_baseline"] = {"value": None, "unit": "s/RHS", "cores": 1, "kind": "oracle",
-                                       "sample": "failed: %s" % e}
+                                       "sample": "failed: %s" % str(e)[:200]}
+    if rank == 0:
         print(json.dumps(out))
-    s.close()
     if world > 1:
         dist.destroy_process_group()
     return 0
+
+
+def fp64_leg(wl, theta, k0, steps=2, warmup=1):
+    """Seconds per right-hand side of the plain FP64 GPU method: FP64 convolution, local
+    solves, Krylov levels; one plane wave per solve; CUDA events around `steps` solves."""
+    import torch
+    from paper_1602_07652_gb300 import binding, inputs
+    n = wl["n"]
+    m = inputs.bump_medium(n, nbumps=20, seed=0)
+    s = binding.Solver(torch.from_numpy(m), wl["omega"], layers=wl["layers"], ext=wl["ext"],
+                       precision=binding.LS_FP64)
+    s.ls_factor()
+    u = torch.empty((n, n), dtype=torch.complex128, device="cuda")
+    for k in range(warmup):
+        s.ls_solve_plane_wave(theta(k0 + k), wl["tol"], u)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record(s.stream)
+    sts = []
+    for k in range(steps):
+        _, st = s.ls_solve_plane_wave(theta(k0 + k), wl["tol"], u)
+        sts.append(st)
+    ev1.record(s.stream)
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    s.close()
+    return {"value": ms / 1e3 / steps, "unit": "s/RHS", "rhs": steps, "warmup": warmup, "dtype": "c128",
+            "tol": wl["tol"], "outer": statistics.mean(st["outer_iters"] for st in sts),
+            "true_rel_residual_max": max(st["true_rel_residual"] for st in sts)}
 
 
 def run_component(args):

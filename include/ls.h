@@ -130,6 +130,12 @@ int ls_apply_f32(ls_handle* h, const ls_c32* u, ls_c32* y);
  * (the apply LS_MIXED uses inside its refinement loop).  u, y: device, nz*nx; may alias. */
 int ls_apply_mixed(ls_handle* h, const ls_c64* u, ls_c64* y);
 
+/* ls_axpby -- y = a x + b y over the nz*nx grid (a = a_re + i a_im, b likewise), on
+ * the handle's stream: the residual r = f - H u (ls_apply, then a = 1, b = -1 with
+ * y = H u) and corrections e = u* - u of the outer iteration (Sec. 4) without
+ * leaving the device.  x, y: device, nz*nx; may alias. */
+int ls_axpby(ls_handle* h, double a_re, double a_im, const ls_c64* x, double b_re, double b_im, ls_c64* y);
+
 /* ls_incident_rhs -- f = -w^2 G (m u_I) with u_I = exp(i w (x cos theta + z sin theta))
  * generated on the device (Sec. 2, f = -w^2 G D u_I).  f: device, nz*nx. */
 int ls_incident_rhs(ls_handle* h, double theta, ls_c64* f);
@@ -322,13 +328,15 @@ int ls_local_solve(ls_handle* h, int dir, int layer, const ls_c64* b, ls_c64* x)
  * device synchronisation an allocation may cause.  It needs no handle and allocates
  * nothing: its n x P scratch and its twiddle tables are fixed file-scope device arrays
  * (16 MiB + 32 KiB, held by every GPU that loads the library until the process exits).
- * The paper has no counterpart; it is the operator of Sec. 2 in another calling form.
+ * The paper has no counterpart.
  *   n: grid points per direction, 8 <= n <= 1024 (n * P <= 2^21, P = smallest power of
  *      two >= 2n - 1); larger n returns LS_ETOOBIG and does nothing.
  *   m: DEVICE float[n*n], the contrast (x fastest).
  *   ghat: DEVICE ls_c32[(P/2+1)^2], the spectral quadrant of ls_get_spectrum rounded to
  *      FP32 (index kx*(P/2+1) + kz).
  *   u, y: DEVICE ls_c32[n*n]; may alias.  stream: cudaStream_t (NULL = legacy stream).
+ *   m, ghat, u and y must be memory of the CURRENT device (device or managed
+ *   allocations); a buffer on another device, or host memory, returns LS_EINVAL.
  * The first call on a device (with that device current) sets up the arrays for that
  * device -- resolves their addresses, fills the twiddle tables, synchronises `stream`
  * once -- so it should come before any stream capture.  The scratch needs no clearing

@@ -14,6 +14,9 @@ Paper passages followed
     rows of Omega^l_ext, and an O(w) complex shift in the cut-off region.
   * Sec. 3.4, eq. pde_GRF_down and Algorithm 1 (Gauss-Seidel preconditioner).
   * Sec. 3.5, Algorithm 2 (bi-directional preconditioner).
+  * Sec. 4.1, local factorisations: the paper calls them "circulant"; read as
+    banded (C^l is block tridiagonal in x-slow order), factored by a partial-
+    pivoted sparse LU in that order (no fill-reducing column permutation).
 
 Readings (the paper's displays for xi^l, delta_k and eq. local_discrete_sparse_pde
 are empty in the available text, and Algorithm 1's layer indices are garbled)
@@ -112,7 +115,12 @@ class Layering:
         if r_hi < q - 1:
             blocks.append(sps.identity((q - 1 - r_hi) * nx, dtype=np.complex128))
         Cl = sps.block_diag(blocks, format="csc")
-        return dict(C=Cl, lu=spla.splu(Cl), mcoef=mcoef, types_z=types_z, real=real)
+        # Banded LU (Sec. 4.1 "local factorisation"): unknowns reordered x-slow, so C^l is
+        # block tridiagonal with q x q blocks (band q + 1 each side); partial-pivoted LU in
+        # that natural order keeps the fill inside the band.
+        perm = np.arange(q * nx).reshape(q, nx).T.ravel()   # x-slow index (i, r) -> r nx + i
+        lu = spla.splu(Cl[perm][:, perm].tocsc(), permc_spec="NATURAL")
+        return dict(C=Cl, lu=lu, perm=perm, mcoef=mcoef, types_z=types_z, real=real)
 
     # -- blocks of C^l between two local rows, applied to a trace (Sec. 3.2) --
     def coupling(self, l: int, r_from: int, r_to: int, p: np.ndarray) -> np.ndarray:
@@ -129,8 +137,12 @@ class Layering:
         return b
 
     def solve_local(self, l: int, b: np.ndarray) -> np.ndarray:
-        """w^l = (C^l)^{-1} b (local solve)."""
-        return self.layers[l]["lu"].solve(b.ravel()).reshape(self.q, self.nx)
+        """w^l = (C^l)^{-1} b (local solve, by the banded LU of the x-slow reordering)."""
+        lay = self.layers[l]
+        perm = lay["perm"]
+        x = np.empty(self.q * self.nx, dtype=np.complex128)
+        x[perm] = lay["lu"].solve(np.ascontiguousarray(b).ravel()[perm])
+        return x.reshape(self.q, self.nx)
 
     def inject_from_above(self, l: int, b: np.ndarray, w_up: np.ndarray) -> None:
         """b += -delta_n C^l_{n,n+1} w^{l+1}_1 + delta_{n+1} C^l_{n+1,n} w^{l+1}_0 (eq. pde_GRF_down)."""

@@ -35,9 +35,11 @@ class Problem:
         self.A = sparsify.matrix_A(self.n, self.st)
         self.bd = polarized.BiDirectional(self.m, self.st, self.omega, self.L, self.E, self.shift)
         self.C = self.bd.C
+        # FFT of the circulant embedding of G, computed once (greens.apply_H's arithmetic)
+        self.conv = greens.Convolution(self.n, self.h, self.omega)
 
     def apply_H(self, u):
-        return greens.apply_H(u, self.m, self.h, self.omega)
+        return self.conv.H(u, self.m)
 
     def apply_A(self, r):
         return (self.A @ r.ravel()).reshape(r.shape)
@@ -46,8 +48,7 @@ class Problem:
         return (self.C @ v.ravel()).reshape(v.shape)
 
     def rhs(self, theta: float):
-        return greens.rhs(self.m, self.h, self.omega,
-                          greens.incident_plane_wave(self.n, self.omega, theta))
+        return self.conv.rhs(self.m, greens.incident_plane_wave(self.n, self.omega, theta))
 
 
 def inner_solve(prob: Problem, g, tol=1e-3, restart=30, maxit=300):
@@ -63,10 +64,14 @@ def ls_preconditioner(prob: Problem, f, inner_tol=1e-3, stats=None):
     return u
 
 
-def solve(prob: Problem, f, tol=1e-8, inner_tol=1e-3, restart=50, maxit=500):
-    """Outer level: flexible GMRES on H u = f preconditioned by Algorithm 3."""
+def solve(prob: Problem, f, tol=1e-8, inner_tol=1e-3, restart=50, maxit=500, x0=None):
+    """Outer level: flexible GMRES on H u = f preconditioned by Algorithm 3.
+
+    x0: optional starting iterate (e.g. a looser solve continued to a tighter
+    tolerance); the tolerance stays relative to ||f||.
+    """
     inner = []
     u, info = krylov.fgmres(prob.apply_H, f, lambda v: ls_preconditioner(prob, v, inner_tol, inner),
-                            tol=tol, restart=restart, maxit=maxit)
+                            tol=tol, restart=restart, maxit=maxit, x0=x0)
     info["inner_iters"] = inner
     return u, info

@@ -59,11 +59,16 @@ def point_type(i: int, n: int) -> int:
     return -1 if i == 0 else (1 if i == n - 1 else 0)
 
 
-def sparsifying_stencil(n: int, h: float, omega: float, bx: int = 0, bz: int = 0) -> np.ndarray:
-    """alpha for stencil type (bx, bz): a length-9 vector (zeros off mu) (Sec. 2, SVD problem)."""
+def sparsifying_stencil(n: int, h: float, omega: float, bx: int = 0, bz: int = 0,
+                        W: np.ndarray | None = None) -> np.ndarray:
+    """alpha for stencil type (bx, bz): a length-9 vector (zeros off mu) (Sec. 2, SVD problem).
+
+    W, if given, is greens.kernel_weights(n, h, omega) (the same table for every type).
+    """
     slots = stencil_slots(bx, bz)
     K = n  # offsets d - p reach |.| <= n
-    W = greens.kernel_weights(K, h, omega)
+    if W is None:
+        W = greens.kernel_weights(K, h, omega)
     rng = np.arange(-(n - 1), n)
     px = rng if bx == 0 else (rng[rng >= 0] if bx == -1 else rng[rng <= 0])
     pz = rng if bz == 0 else (rng[rng >= 0] if bz == -1 else rng[rng <= 0])
@@ -113,9 +118,10 @@ class Stencils:
         self.n, self.h, self.omega = n, h, omega
         self.alpha = np.zeros((3, 3, 9), dtype=np.complex128)
         self.beta = np.zeros((3, 3, 9), dtype=np.complex128)
+        W = greens.kernel_weights(n, h, omega)  # one table of G_w serves the 9 SVD problems
         for bz in (-1, 0, 1):
             for bx in (-1, 0, 1):
-                a = sparsifying_stencil(n, h, omega, bx, bz)
+                a = sparsifying_stencil(n, h, omega, bx, bz, W)
                 self.alpha[bz + 1, bx + 1] = a
                 self.beta[bz + 1, bx + 1] = beta_table(a, bx, bz, h, omega)
 

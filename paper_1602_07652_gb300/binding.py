@@ -73,6 +73,7 @@ _SIGS = {
                                 ctypes.POINTER(Opts), _P, ctypes.POINTER(_P)]),
     "ls_factor": (ctypes.c_int, [_P]),
     "ls_apply": (ctypes.c_int, [_P, _P, _P]),
+    "ls_axpby": (ctypes.c_int, [_P, ctypes.c_double, ctypes.c_double, _P, ctypes.c_double, ctypes.c_double, _P]),
     "ls_apply_f32": (ctypes.c_int, [_P, _P, _P]),
     "ls_apply_mixed": (ctypes.c_int, [_P, _P, _P]),
     "ls_incident_rhs": (ctypes.c_int, [_P, ctypes.c_double, _P]),
@@ -266,12 +267,26 @@ def ls_apply_f32_noalloc(n: int, m32: torch.Tensor, ghat32: torch.Tensor, u: tor
     """
     lib = load()
     y = torch.empty_like(u) if y is None else y
+    dev = torch.cuda.current_device()
     for t in (m32, ghat32, u, y):
         if not t.is_cuda or not t.is_contiguous():
             raise ValueError("ls_apply_f32_noalloc takes contiguous CUDA tensors")
+        if t.device.index != dev:
+            raise ValueError("ls_apply_f32_noalloc: every tensor must be on the current device (cuda:%d)" % dev)
     if m32.dtype != torch.float32 or u.dtype != torch.complex64 or y.dtype != torch.complex64 \
             or ghat32.dtype != torch.complex64:
         raise ValueError("ls_apply_f32_noalloc: m float32, ghat/u/y complex64")
+    # the library takes n from the caller and trusts the buffers to hold n*n and
+    # (P/2+1)^2 elements: check that here, P as the library computes it
+    n = int(n)
+    if n >= 8:
+        P = 1
+        while P < 2 * n - 1:
+            P *= 2
+        if not (m32.numel() == u.numel() == y.numel() == n * n):
+            raise ValueError("ls_apply_f32_noalloc: m, u and y must hold n*n = %d elements" % (n * n))
+        if ghat32.numel() < (P // 2 + 1) ** 2:
+            raise ValueError("ls_apply_f32_noalloc: ghat must hold (P/2+1)^2 = %d elements" % ((P // 2 + 1) ** 2))
     st = stream if stream is not None else torch.cuda.current_stream()
     rc = lib.ls_apply_f32_noalloc(int(n), _ptr(m32), _ptr(ghat32), _ptr(u), _ptr(y), ctypes.c_void_p(st.cuda_stream))
     if check:
@@ -325,6 +340,13 @@ class Solver:
     def ls_apply(self, u, y=None):
         y = torch.empty_like(u) if y is None else y
         _ck(self._lib.ls_apply(self._h, _c128(u, self.N, "ls_apply"), _c128(y, self.N, "ls_apply")), "ls_apply")
+        return y
+
+    def ls_axpby(self, a, x, b, y):
+        """y = a x + b y in the library (a, b complex scalars); returns y."""
+        a, b = complex(a), complex(b)
+        _ck(self._lib.ls_axpby(self._h, a.real, a.imag, _c128(x, self.N, "ls_axpby"), b.real, b.imag,
+                               _c128(y, self.N, "ls_axpby")), "ls_axpby")
         return y
 
     def ls_apply_mixed(self, u, y=None):

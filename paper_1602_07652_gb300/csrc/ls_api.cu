@@ -261,6 +261,12 @@ int ls_apply(ls_handle* h, const ls_c64* u, ls_c64* y) {
     return ls_apply64(h, reinterpret_cast<const double2*>(u), reinterpret_cast<double2*>(y));
 }
 
+int ls_axpby(ls_handle* h, double a_re, double a_im, const ls_c64* x, double b_re, double b_im, ls_c64* y) {
+    if (!h || !x || !y) return LS_EINVAL;
+    return ls_vec_axpby(h, make_double2(a_re, a_im), reinterpret_cast<const double2*>(x), make_double2(b_re, b_im),
+                        reinterpret_cast<double2*>(y));
+}
+
 int ls_apply_f32(ls_handle* h, const ls_c32* u, ls_c32* y) {
     if (!h || !u || !y) return LS_EINVAL;
     return ls_apply32(h, reinterpret_cast<const float2*>(u), reinterpret_cast<float2*>(y));

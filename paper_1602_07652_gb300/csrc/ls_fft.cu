@@ -584,6 +584,18 @@ extern "C" int ls_apply_f32_noalloc(int n, const float* m, const ls_c32* ghat, c
     int dev = 0;
     LS_CUDA(cudaGetDevice(&dev));
     if (dev < 0 || dev >= kNoAllocMaxDevices) return LS_EINVAL;
+    // every buffer must be device (or managed) memory of the current device: the
+    // scratch used below is this device's, and a launch here cannot read another's
+    const void* bufs[4] = {m, ghat, u, y};
+    for (const void* b : bufs) {
+        cudaPointerAttributes a{};
+        if (cudaPointerGetAttributes(&a, b) != cudaSuccess) {
+            (void)cudaGetLastError();
+            return LS_EINVAL;
+        }
+        if ((a.type != cudaMemoryTypeDevice && a.type != cudaMemoryTypeManaged) || a.device != dev)
+            return LS_EINVAL;
+    }
     cudaStream_t stream = static_cast<cudaStream_t>(stream_);
     NoAllocDevice* d = nullptr;
     LS_TRY(noalloc_setup(dev, stream, &d));

@@ -31,8 +31,12 @@ def pairs_for_medium(n, seed, tols=(3e-1, 1e-1, 3e-2), ppw=10.24, precision=bind
     rs, es = [], []
     for tol in tols:
         uk, _, _ = s.ls_solve(f, tol, check=False)
-        rs.append(f - s.ls_apply(uk))
-        es.append(u_star - uk)
+        r = s.ls_apply(uk)                       # H u_k
+        s.ls_axpby(1.0, f, -1.0, r)              # r_k = f - H u_k
+        e = u_star.clone()
+        s.ls_axpby(-1.0, uk, 1.0, e)             # e_k = u* - u_k
+        rs.append(r)
+        es.append(e)
     s.close()
     md = torch.from_numpy(m).cuda()
     return torch.stack(rs), torch.stack(es), md.expand(len(tols), n, n).contiguous()
