@@ -47,6 +47,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true",
                     help="skip the timed oracle sample (the CPU baseline)")
     ap.add_argument("--no-fp64-leg", action="store_true", help="skip the plain FP64 GPU leg")
+    ap.add_argument("--no-tensor-steps", action="store_true",
+                    help="mixed precision: local-solve reduction steps on the CUDA cores (FP32) instead of the "
+                         "tensor cores (TF32)")
     ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--e2e-steps", type=int, default=None,
                     help="steps of the end-to-end (host buffers) leg; default: --steps, the same "
@@ -405,6 +408,8 @@ def run_ours(args):
     s.ls_factor()
     torch.cuda.synchronize()
     t_factor = time.perf_counter() - t0
+    if args.no_tensor_steps and not args.fp64:
+        s.ls_set_tensor_steps(0)
     t0 = time.perf_counter()
     tune = s.ls_autotune(nrhs=args.batch, reps=2)
     t_tune = time.perf_counter() - t0
@@ -613,6 +618,8 @@ def run_component(args):
             fn, nbytes, kind = (lambda: s.ls_apply_f32(x, x)), 100.0 * n * n, "LS-apply FP32"
     else:
         s.ls_factor()
+        if args.no_tensor_steps and not args.fp64:
+            s.ls_set_tensor_steps(0)
         B = args.batch
         g = torch.stack([torch.from_numpy(inputs.random_field(n, b)) for b in range(B)]).cuda()
         v = torch.empty_like(g)

@@ -46,8 +46,9 @@ enum {
 enum { LS_FP64 = 0, LS_MIXED = 1 };
 
 /* Right-hand sides per batched call: ls_solve_batch takes up to LS_MAX_BATCH;
- * ls_precond_bd_batch takes up to LS_MAX_BD_BATCH (LS_MIXED) or 4 (LS_FP64). */
-enum { LS_MAX_BATCH = 32, LS_MAX_BD_BATCH = 8 };
+ * ls_precond_bd_batch takes up to LS_MAX_BD_BATCH (LS_MIXED with the reduction steps
+ * on the tensor cores), 8 (LS_MIXED on the CUDA cores) or 4 (LS_FP64). */
+enum { LS_MAX_BATCH = 64, LS_MAX_BD_BATCH = 32 };
 
 typedef struct {
     int nx, nz;       /* grid points per direction (this build requires nx == nz >= 8)      */
@@ -225,14 +226,30 @@ typedef struct {
     double bd_ms_nosplit[4]; /* the same without splitting the blocks of small levels        */
     int cr_split;       /* 1: the reduction steps of levels with fewer blocks than SMs split
                            each block's columns over several CTAs; 0: one CTA per block     */
+    double bd_ms_tc[4]; /* LS_MIXED: the same with the reduction steps on the tensor cores,
+                           chunks 1, 8, 16, 32 (0: not tried; tried only while that form
+                           is switched on, see ls_set_tensor_steps)                        */
+    int tensor_steps;   /* 1: the tensor-core steps were chosen                            */
 } ls_tuning;
 int ls_autotune(ls_handle* h, int nrhs, int reps, ls_tuning* out);
 
 /* ls_set_shapes -- pin the two shape choices (e.g. from an earlier ls_autotune):
  * fft_variant 0..8 as above (a radix-16/8 shape on a P outside 256..4096 falls back
- * to the generic one), bd_chunk 1..8 (FP64: 1..4) or 0 for the largest.  LS_EINVAL
- * otherwise.  Results agree up to rounding whichever shapes are set. */
+ * to the generic one), bd_chunk 1..32 with the tensor-core steps, 1..8 on the CUDA
+ * cores (FP64: 1..4), or 0 for the largest.  LS_EINVAL otherwise.  Results agree up to
+ * rounding whichever shapes are set. */
 int ls_set_shapes(ls_handle* h, int fft_variant, int bd_chunk);
+
+/* ls_set_tensor_steps -- LS_MIXED: run the block-cyclic-reduction steps of the local
+ * solves (Algorithm 1's (C^l)^{-1}, Sec. 3.4; factors of Sec. 4.1) on the tensor cores
+ * (on = 1, the default after ls_factor: each step one TF32 matrix product over the
+ * whole batch, factor tiles streamed by TMA, accumulators in tensor memory) or on the
+ * CUDA cores in FP32 (on = 0).  The tensor-core form rounds the factors and vectors to
+ * TF32 (about 3 decimal digits): it changes the preconditioner by that much, never the
+ * converged solution, which the FP64 residual judges.  Synchronises the stream and
+ * drops the captured sweep graphs on a change.  LS_ESTATE when on = 1 and the form is
+ * not built (LS_FP64, before ls_factor, or q > 112); LS_EINVAL for other values. */
+int ls_set_tensor_steps(ls_handle* h, int on);
 
 /* ls_set_reduction -- pin the form of the block-cyclic-reduction local solves of
  * Algorithm 1 (Sec. 3.4): cr_split 1 lets the steps of levels with fewer blocks
@@ -242,12 +259,14 @@ int ls_set_shapes(ls_handle* h, int fft_variant, int bd_chunk);
  * rounding in either form. */
 int ls_set_reduction(ls_handle* h, int cr_split);
 
-/* ls_device_timeouts -- health counter of the LS-apply's TMA column pass (Sec. 2 defines
- * the apply; the paper has no counterpart of this counter): *count = how many CTAs of
- * the TMA tile shapes (6, 7, 8) found their column tiles not arrived within one second
- * since the library was loaded; 0 in a healthy run.  Such a CTA writes its tiles as NaN
- * (so the solver's residual checks reject the result) and returns instead of waiting
- * on.  Synchronous read of a device counter.  LS_EINVAL if count is NULL. */
+/* ls_device_timeouts -- health counter of the kernels fed by TMA (the paper has no
+ * counterpart of this counter): *count = how many CTAs found their copies or their
+ * tensor-core products not complete within one second since the library was loaded --
+ * CTAs of the LS-apply's TMA column tile shapes (6, 7, 8; Sec. 2) and of the
+ * tensor-core reduction steps of the local solves (Sec. 3.4-3.5); 0 in a healthy run.
+ * Such a CTA writes its outputs as NaN (so the solver's residual checks reject the
+ * result) and returns instead of waiting on.  Synchronous read of device counters.
+ * LS_EINVAL if count is NULL. */
 int ls_device_timeouts(unsigned* count);
 
 /* ls_test_tma_shortfall -- test hook for the timeout path above (no counterpart in the

@@ -18,7 +18,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libls.so")
 
 LS_FP64, LS_MIXED = 0, 1
-LS_MAX_BATCH, LS_MAX_BD_BATCH = 32, 8
+LS_MAX_BATCH, LS_MAX_BD_BATCH = 64, 32
 LS_PC_BD, LS_PC_GS = 0, 1
 
 
@@ -58,12 +58,14 @@ class Stats(ctypes.Structure):
 class Tuning(ctypes.Structure):
     _fields_ = [("fft_variant", ctypes.c_int), ("bd_chunk", ctypes.c_int),
                 ("fft_ms", ctypes.c_double * 9), ("bd_ms", ctypes.c_double * 4),
-                ("bd_ms_nosplit", ctypes.c_double * 4), ("cr_split", ctypes.c_int)]
+                ("bd_ms_nosplit", ctypes.c_double * 4), ("cr_split", ctypes.c_int),
+                ("bd_ms_tc", ctypes.c_double * 4), ("tensor_steps", ctypes.c_int)]
 
     def as_dict(self):
         return {"fft_variant": self.fft_variant, "bd_chunk": self.bd_chunk,
                 "fft_ms": list(self.fft_ms), "bd_ms_per_rhs": list(self.bd_ms),
-                "bd_ms_per_rhs_nosplit": list(self.bd_ms_nosplit), "cr_split": self.cr_split}
+                "bd_ms_per_rhs_nosplit": list(self.bd_ms_nosplit), "cr_split": self.cr_split,
+                "bd_ms_per_rhs_tc": list(self.bd_ms_tc), "tensor_steps": self.tensor_steps}
 
 
 _P = ctypes.c_void_p
@@ -86,6 +88,7 @@ _SIGS = {
     "ls_autotune": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.POINTER(Tuning)]),
     "ls_set_shapes": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int]),
     "ls_set_reduction": (ctypes.c_int, [_P, ctypes.c_int]),
+    "ls_set_tensor_steps": (ctypes.c_int, [_P, ctypes.c_int]),
     "ls_device_timeouts": (ctypes.c_int, [ctypes.POINTER(ctypes.c_uint)]),
     "ls_test_tma_shortfall": (ctypes.c_int, [ctypes.c_uint]),
     "ls_solve_host": (ctypes.c_int, [_P, _P, ctypes.c_double, _P, ctypes.POINTER(Stats)]),
@@ -395,6 +398,9 @@ class Solver:
 
     def ls_set_reduction(self, cr_split):
         _ck(self._lib.ls_set_reduction(self._h, int(cr_split)), "ls_set_reduction")
+
+    def ls_set_tensor_steps(self, on):
+        _ck(self._lib.ls_set_tensor_steps(self._h, int(on)), "ls_set_tensor_steps")
 
     def ls_autotune(self, nrhs=1, reps=3):
         t = Tuning()

@@ -247,7 +247,8 @@ int ls_factor(ls_handle* h) {
     if (!h) return LS_EINVAL;
     ls_factor_free(h);
     h->factored = false;
-    const int rc = ls_factor_all(h);
+    int rc = ls_factor_all(h);
+    if (rc == LS_OK) rc = ls_cr_tc_prepare(h);   // LS_MIXED: TF32 planes for the tensor-core steps
     if (rc != LS_OK) {
         ls_factor_free(h);
         return rc;
@@ -415,8 +416,9 @@ int ls_precond_bd(ls_handle* h, const ls_c64* g, ls_c64* v) {
 }
 
 int ls_precond_bd_batch(ls_handle* h, int nrhs, const ls_c64* g, ls_c64* v) {
-    if (!h || !g || !v || nrhs < 1 || nrhs > (h->prec == LS_MIXED ? LS_MAX_BD_BATCH : 4)) return LS_EINVAL;
+    if (!h || !g || !v || nrhs < 1) return LS_EINVAL;
     if (!h->factored) return LS_ESTATE;
+    if (nrhs > ls_bd_cap(h)) return LS_EINVAL;
     return ls_bd_b(h, reinterpret_cast<const double2*>(g), reinterpret_cast<double2*>(v), nrhs);
 }
 

@@ -1,0 +1,529 @@
+// ls_cr_mma.cu -- the block cyclic reduction steps of the local solves (Sec. 3.4-3.5,
+// Algorithm 1's (C^l)^{-1} g^l) on the fifth-generation tensor cores, for batches of
+// up to 32 right-hand sides in FP32 (mixed precision).
+//
+// One reduction step for block j of a level applies up to three q x q complex
+// factor matrices to the batch's vectors at the neighbouring blocks:
+//   MODE 0 (level 0, odd j)       x_j = D^{-1} x_j
+//   MODE 1 (level k >= 1, even j) x_j = x_j + F (-x_{j-1}) + G (-x_{j+1})
+//   MODE 2 (level k >= 1, odd j)  x_j = D^{-1} x_j + P (-x_{j-1}) + Q (-x_{j+1})
+//   MODE 3 (top block)            x_0 = D^{-1} x_0
+//   MODE 4 (level 0 back, odd j)  x_j = x_j + D^{-1} t,  t = -(W x_{j-1} + E x_{j+1})
+//                                 (W, E: the tridiagonal couplings of level 0)
+// With NB right-hand sides this is a complex (q x q) . (q x NB) product per matrix:
+// a dense contraction, done as a real GEMM with M = 128 rows (q <= 112 real ones),
+// N = 2 NB, K = 2 q per matrix:
+//   [D_re | D_im] += M_re [X_re | X_im] + M_im [-X_im | X_re].
+// Operand A is a factor matrix: each plane (re, im) stored row-major in TF32
+// (rounded to nearest once, when factored), streamed from HBM by TMA
+// (cp.async.bulk.tensor, 128-byte swizzle, rows beyond q zero-filled) through a
+// ring of shared-memory stages; each matrix byte is read once per step for the
+// whole batch.  Operand B is built by the CTA's threads from the vectors (the
+// sign of the step folded in, rounded to TF32): per vector three planes of NB
+// rows [-X_im; X_re; X_im], so that rows [NB, 3NB) are [X_re; X_im] and rows
+// [0, 2NB) are [-X_im; X_re].  One thread issues tcgen05.mma (kind::tf32, K = 8
+// per instruction) into a TMEM accumulator of 128 lanes x 2NB FP32 columns; the
+// epilogue reads it back with tcgen05.ld and writes (or adds to) x_j.
+// Roles in a CTA of 256 threads: thread 0 loads A stages (TMA), thread 32 issues
+// the MMAs, everyone builds B and runs the epilogue.  Every wait is bounded (1 s
+// on %globaltimer); on expiry the step's outputs become NaN and a device counter
+// (ls_device_timeouts) is raised, so every residual check rejects the result.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <mutex>
+
+#include "ls_internal.cuh"
+
+namespace {
+
+__device__ unsigned g_cr_timeouts;   // steps whose TMA loads or MMAs did not complete in time
+
+constexpr int kThreads = 256;
+constexpr int kStages = 4;                  // A ring
+constexpr int kStageBytes = 128 * 128;      // 128 rows x 128 bytes (32 TF32 of K)
+constexpr unsigned long long kWaitNs = 1000000000ull;
+
+__device__ __forceinline__ unsigned su32(const void* p) { return static_cast<unsigned>(__cvta_generic_to_shared(p)); }
+__device__ __forceinline__ unsigned long long gtime() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+__device__ __forceinline__ bool bar_wait(unsigned long long* bar, unsigned parity) {
+    const unsigned long long t0 = gtime();
+    for (;;) {
+        unsigned done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(su32(bar)), "r"(parity)
+            : "memory");
+        if (done) return true;
+        if (gtime() - t0 > kWaitNs) return false;
+    }
+}
+__device__ __forceinline__ void bar_init(unsigned long long* bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(su32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ float tf32_rna(float x) {
+    unsigned r;
+    asm("cvt.rna.tf32.f32 %0, %1;\n" : "=r"(r) : "f"(x));
+    return __uint_as_float(r);
+}
+
+// Shared-memory matrix descriptor of a K-major operand tile in the 128-byte swizzle
+// layout: rows of 128 bytes, 8-row groups 1024 bytes apart (stride byte offset),
+// descriptor version 1, swizzle mode 2 (128 bytes).
+__device__ __forceinline__ unsigned long long sdesc(unsigned addr) {
+    unsigned long long d = 0;
+    d |= (unsigned long long)((addr >> 4) & 0x3FFF);
+    d |= (unsigned long long)(16 >> 4) << 16;      // leading byte offset (unused when swizzled)
+    d |= (unsigned long long)(1024 >> 4) << 32;    // stride byte offset
+    d |= 1ull << 46;                                // version
+    d |= 2ull << 61;                                // 128-byte swizzle
+    return d;
+}
+// Instruction descriptor, kind::tf32: D FP32, A and B TF32, both K-major, M x N.
+__host__ __device__ constexpr unsigned idesc_tf32(int M, int N) {
+    return (1u << 4) | (2u << 7) | (2u << 10) | ((unsigned)(N >> 3) << 17) | ((unsigned)(M >> 4) << 24);
+}
+__device__ __forceinline__ void mma_tf32(unsigned dtmem, unsigned long long a, unsigned long long b, unsigned id,
+                                         unsigned acc) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(dtmem),
+        "l"(a), "l"(b), "r"(id), "r"(acc)
+        : "memory");
+}
+__device__ __forceinline__ void mma_commit(unsigned long long* bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(su32(bar))
+                 : "memory");
+}
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int x, int y, int z,
+                                            unsigned long long* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+        "[%5];\n" ::"r"(su32(dst)),
+        "l"(reinterpret_cast<unsigned long long>(map)), "r"(x), "r"(y), "r"(z), "r"(su32(bar))
+        : "memory");
+}
+// 8 consecutive FP32 columns of this warp's 32 TMEM lanes
+__device__ __forceinline__ void tmem_ld8(unsigned taddr, float* v) {
+    unsigned r[8];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];\n"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                 : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+template <int MODE> struct ModeOf {
+    static constexpr int NV = MODE == 1 ? 2 : (MODE == 2 ? 3 : 1);   // vectors (= matrices) per step
+    static constexpr bool ADD = MODE == 1 || MODE == 4;              // x_j += D instead of x_j = D
+};
+
+// Shared memory of one CTA: A ring | B (NV vectors x KA atoms x 3NB rows x 128 B) |
+// barriers (full[kStages], empty[kStages], done) | TMEM address | failure flag.
+template <int MODE, int NB, int KA>
+constexpr size_t tc_smem() {
+    return 1024 /* alignment slack */ + (size_t)kStages * kStageBytes +
+           (size_t)ModeOf<MODE>::NV * KA * 3 * NB * 128 + 8 * (2 * kStages + 1) + 16;
+}
+
+struct StepArgs {
+    int q, k, nk;             // strip height, level, blocks at this level
+    size_t mat0;              // first matrix of this strip in the direction's pool (matrix index)
+    size_t off_a, off_b, off_c;  // level offsets (matrices) of the step's 1st, 2nd, 3rd matrix
+    float2* x;                // strip vectors of batch member 0 (block layout); member b at + b * SB
+    size_t SB;
+    int nb;                   // members present (<= NB)
+    const float2* cw;         // MODE 4: level-0 couplings of this strip [i][dz+1][r]
+    const float2* ce;
+};
+
+template <int MODE, int NB, int KA>
+__global__ void __launch_bounds__(kThreads, 1) k_cr_mma(const __grid_constant__ CUtensorMap amap, StepArgs a) {
+    using MO = ModeOf<MODE>;
+    constexpr int NV = MO::NV;
+    constexpr int KP = 32 * KA;                   // padded K of one plane
+    constexpr int BROWS = 3 * NB;                 // rows of one vector's B atom
+    constexpr unsigned BATOM = BROWS * 128;       // bytes of one vector's B atom
+    constexpr int NCOL = 2 * NB;                  // accumulator columns
+    constexpr int TCOLS = NCOL <= 32 ? 32 : (NCOL <= 64 ? 64 : 128);
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    unsigned char* As = base;
+    unsigned char* Bs = As + kStages * kStageBytes;
+    auto* full = reinterpret_cast<unsigned long long*>(Bs + (size_t)NV * KA * BATOM);
+    auto* empty = full + kStages;
+    auto* done = empty + kStages;
+    unsigned* tslot = reinterpret_cast<unsigned*>(done + 1);
+    int* failed = reinterpret_cast<int*>(tslot + 1);
+
+    const int q = a.q, tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int idx = blockIdx.x;
+    const size_t s = (size_t)1 << a.k;
+    const int j = (MODE == 1) ? 2 * idx : (MODE == 3 ? 0 : 2 * idx + 1);
+    const bool hw = j >= 1, he = j + 1 < a.nk;
+    // vector slot t: present?, its block, its sign, its matrix (index in the pool)
+    bool pres[3];
+    long long blk[3];
+    float sgn[3];
+    size_t mat[3];
+    if (MODE == 0 || MODE == 3 || MODE == 4) {
+        pres[0] = true; blk[0] = (long long)j * s; sgn[0] = 1.f; mat[0] = a.mat0 + a.off_a + idx;
+    }
+    if (MODE == 1) {
+        pres[0] = hw; blk[0] = (long long)(j - 1) * s; sgn[0] = -1.f; mat[0] = a.mat0 + a.off_b + idx;
+        pres[1] = he; blk[1] = (long long)(j + 1) * s; sgn[1] = -1.f; mat[1] = a.mat0 + a.off_c + idx;
+    }
+    if (MODE == 2) {
+        pres[0] = true; blk[0] = (long long)j * s; sgn[0] = 1.f; mat[0] = a.mat0 + a.off_a + idx;
+        pres[1] = true; blk[1] = (long long)(j - 1) * s; sgn[1] = -1.f; mat[1] = a.mat0 + a.off_b + idx;
+        pres[2] = he; blk[2] = (long long)(j + 1) * s; sgn[2] = -1.f; mat[2] = a.mat0 + a.off_c + idx;
+    }
+    int nat = 0;   // A atoms to stream: present vectors x 2 planes x KA
+#pragma unroll
+    for (int t = 0; t < NV; ++t) nat += pres[t] ? 2 * KA : 0;
+
+    if (tid == 0) {
+        *failed = 0;
+        for (int i = 0; i < kStages; ++i) {
+            bar_init(&full[i], 1);
+            bar_init(&empty[i], 1);
+        }
+        bar_init(done, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+    }
+    if (warp == 0) {   // TMEM accumulator: 128 lanes x TCOLS columns
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(su32(tslot)),
+                     "r"(TCOLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    const unsigned tmem = *tslot;
+
+    // producer: the first min(nat, kStages) A stages start streaming before B is built
+    auto atom_coords = [&](int i, int& x, int& z) {
+        int t = 0, r = i;
+        while (!pres[t] || r >= 2 * KA) {
+            if (pres[t]) r -= 2 * KA;
+            ++t;
+        }
+        const int p = r / KA, at = r % KA;
+        x = 32 * at;
+        z = (int)(2 * mat[t] + p);
+    };
+    const unsigned abytes = 128u * (unsigned)((q + 7) / 8 * 8 < 128 ? (q + 7) / 8 * 8 : 128);
+    if (tid == 0) {
+        for (int i = 0; i < nat && i < kStages; ++i) {
+            int x, z;
+            atom_coords(i, x, z);
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(su32(&full[i])), "r"(abytes)
+                         : "memory");
+            tma_load_3d(As + i * kStageBytes, &amap, x, 0, z, &full[i]);
+        }
+    }
+
+    // B: per vector t, atom at, rows [0,NB) = -X_im, [NB,2NB) = X_re, [2NB,3NB) = X_im (TF32).
+    // Every load of the thread is issued before the first store, so their latencies overlap.
+    constexpr int PER = NB * KP / kThreads;   // elements of one vector per thread
+    float2 val[NV][PER];
+#pragma unroll
+    for (int t = 0; t < NV; ++t)
+#pragma unroll
+        for (int u = 0; u < PER; ++u) {
+            const int o = tid + u * kThreads, b = o / KP, kk = o % KP;
+            float2 v = make_float2(0.f, 0.f);
+            if (pres[t] && b < a.nb && kk < q) {
+                const float2* xb = a.x + (size_t)b * a.SB;
+                if (MODE == 4) {   // t = -(W x_{j-1} + E x_{j+1}), tridiagonal couplings
+                    const float2* wj = a.cw + (size_t)j * 3 * q;
+                    const float2* ej = a.ce + (size_t)j * 3 * q;
+                    float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+                    for (int dz = -1; dz <= 1; ++dz) {
+                        const int rr = kk + dz;
+                        if (rr < 0 || rr >= q) continue;
+                        acc = cfma(__ldg(&wj[(dz + 1) * q + kk]), xb[(size_t)(j - 1) * q + rr], acc);
+                        if (he) acc = cfma(__ldg(&ej[(dz + 1) * q + kk]), xb[(size_t)(j + 1) * q + rr], acc);
+                    }
+                    v = make_float2(-acc.x, -acc.y);
+                } else {
+                    v = xb[(size_t)blk[t] * q + kk];
+                    v = make_float2(sgn[t] * v.x, sgn[t] * v.y);
+                }
+            }
+            val[t][u] = v;
+        }
+#pragma unroll
+    for (int t = 0; t < NV; ++t) {
+        unsigned char* Bt = Bs + (size_t)t * KA * BATOM;
+#pragma unroll
+        for (int u = 0; u < PER; ++u) {
+            const int o = tid + u * kThreads, b = o / KP, kk = o % KP;
+            const float re = tf32_rna(val[t][u].x), im = tf32_rna(val[t][u].y);
+            const int at = kk >> 5, kc = kk & 31;
+            unsigned char* atom = Bt + (size_t)at * BATOM;
+            const int rows[3] = {b, NB + b, 2 * NB + b};
+            const float vals[3] = {-im, re, im};
+#pragma unroll
+            for (int w3 = 0; w3 < 3; ++w3) {
+                const int nrow = rows[w3];
+                const unsigned off = (unsigned)(nrow >> 3) * 1024u + (unsigned)(nrow & 7) * 128u +
+                                     (unsigned)(((kc >> 2) ^ (nrow & 7)) << 4) + (unsigned)(kc & 3) * 4u;
+                *reinterpret_cast<float*>(atom + off) = vals[w3];
+            }
+        }
+    }
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");   // B visible to the tensor cores
+    __syncthreads();
+
+    if (tid == 32) {   // MMA issuer
+        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+        constexpr unsigned ID = idesc_tf32(128, NCOL);
+        int i = 0;
+        bool ok = true;
+        for (int t = 0; t < NV && ok; ++t) {
+            if (!pres[t]) continue;
+            const unsigned bt = su32(Bs + (size_t)t * KA * BATOM);
+            for (int p = 0; p < 2 && ok; ++p)
+                for (int at = 0; at < KA; ++at, ++i) {
+                    const int st = i % kStages;
+                    if (!bar_wait(&full[st], (unsigned)(i / kStages) & 1u)) {
+                        ok = false;
+                        break;
+                    }
+                    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+                    const unsigned aaddr = su32(As + st * kStageBytes);
+                    // plane re: B rows [NB, 3NB) = [X_re; X_im]; plane im: rows [0, 2NB) = [-X_im; X_re]
+                    const unsigned baddr = bt + (unsigned)at * BATOM + (p == 0 ? (unsigned)NB * 128u : 0u);
+#pragma unroll
+                    for (int k8 = 0; k8 < 4; ++k8)
+                        mma_tf32(tmem, sdesc(aaddr + 32u * k8), sdesc(baddr + 32u * k8), ID, (i | k8) ? 1u : 0u);
+                    mma_commit(&empty[st]);   // the stage is free once these MMAs have read it
+                }
+        }
+        if (!ok) atomicOr(failed, 1);
+        mma_commit(done);   // every MMA issued above has completed
+    }
+    if (tid == 0) {   // producer: refill each stage once the MMAs of its previous use are done
+        for (int i = kStages; i < nat; ++i) {
+            const int st = i % kStages;
+            if (!bar_wait(&empty[st], (unsigned)(i / kStages - 1) & 1u)) {
+                atomicOr(failed, 2);
+                break;
+            }
+            int x, z;
+            atom_coords(i, x, z);
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(su32(&full[st])),
+                         "r"(abytes)
+                         : "memory");
+            tma_load_3d(As + st * kStageBytes, &amap, x, 0, z, &full[st]);
+        }
+    }
+    // epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31 (rows r), columns split between w and w + 4
+    const int r = 32 * (warp & 3) + lane;
+    const int half = warp >> 2;   // 0: members [0, NB/2), 1: [NB/2, NB)
+    constexpr int HB = NB / 2;
+    float2 old[HB];   // x_j before the step (the steps that add), read while the products run
+#pragma unroll
+    for (int c = 0; c < HB; ++c) {
+        const int b = half * HB + c;
+        old[c] = (MO::ADD && r < q && b < a.nb) ? a.x[(size_t)b * a.SB + (size_t)j * s * q + r] : make_float2(0.f, 0.f);
+    }
+    const bool fin = bar_wait(done, 0);
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    const bool bad = !fin || *failed;
+    float dre[HB], dim[HB];
+#pragma unroll
+    for (int c = 0; c < HB; c += 8) {   // NB >= 16 here; NB = 8 handled by the HB % 8 guard
+        if (c + 8 <= HB) {
+            tmem_ld8(tmem + ((unsigned)(32 * (warp & 3)) << 16) + (unsigned)(half * HB + c), dre + c);
+            tmem_ld8(tmem + ((unsigned)(32 * (warp & 3)) << 16) + (unsigned)(NB + half * HB + c), dim + c);
+        }
+    }
+    if constexpr (HB % 8 != 0) {   // NB = 8: each half takes 4 members; read 8 and keep its 4
+        float tr[8], ti[8];
+        tmem_ld8(tmem + ((unsigned)(32 * (warp & 3)) << 16), tr);
+        tmem_ld8(tmem + ((unsigned)(32 * (warp & 3)) << 16) + (unsigned)NB, ti);
+#pragma unroll
+        for (int c = 0; c < HB; ++c) {
+            dre[c] = tr[half * HB + c];
+            dim[c] = ti[half * HB + c];
+        }
+    }
+    if (r < q) {
+#pragma unroll
+        for (int c = 0; c < HB; ++c) {
+            const int b = half * HB + c;
+            if (b >= a.nb) continue;
+            float2* xj = a.x + (size_t)b * a.SB + (size_t)j * s * q + r;
+            float2 v = bad ? make_float2(__int_as_float(0x7fc00000), __int_as_float(0x7fc00000))
+                           : make_float2(dre[c], dim[c]);
+            if (MO::ADD && !bad) v = make_float2(old[c].x + v.x, old[c].y + v.y);
+            *xj = v;
+        }
+    }
+    if (bad && tid == 0) atomicAdd(&g_cr_timeouts, 1u);
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(TCOLS) : "memory");
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encoder() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult qr{};
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &qr) ==
+                cudaSuccess &&
+            qr == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    });
+    return fn;
+}
+
+// column-major complex q x q (FP64) -> two row-major TF32 planes of q rows x ld
+__global__ void k_pack_tc(size_t nmat, int q, int ld, const float2* __restrict__ src, float* __restrict__ dst) {
+    const size_t per = (size_t)q * q;
+    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < nmat * per; e += (size_t)gridDim.x * blockDim.x) {
+        const size_t mi = e / per;
+        const int rc = (int)(e % per), c = rc / q, r = rc % q;   // source element (r, c) at c q + r
+        const float2 v = src[e];
+        float* d = dst + mi * 2 * (size_t)q * ld;
+        d[(size_t)r * ld + c] = tf32_rna(v.x);
+        d[(size_t)q * ld + (size_t)r * ld + c] = tf32_rna(v.y);
+    }
+}
+
+template <int MODE, int NB, int KA>
+int set_smem() {
+    const size_t sz = tc_smem<MODE, NB, KA>();
+    LS_CUDA(cudaFuncSetAttribute(k_cr_mma<MODE, NB, KA>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sz));
+    return LS_OK;
+}
+
+template <int NB, int KA>
+int set_smem_all() {
+    LS_TRY((set_smem<0, NB, KA>()));
+    LS_TRY((set_smem<1, NB, KA>()));
+    LS_TRY((set_smem<2, NB, KA>()));
+    LS_TRY((set_smem<3, NB, KA>()));
+    LS_TRY((set_smem<4, NB, KA>()));
+    return LS_OK;
+}
+
+template <int MODE, int NB, int KA>
+int launch(ls_handle* h, const CUtensorMap* map, unsigned grid, const StepArgs& a) {
+    LS_LAUNCH(h, (k_cr_mma<MODE, NB, KA>), grid, kThreads, (tc_smem<MODE, NB, KA>()), *map, a);
+    return LS_OK;
+}
+
+template <int NB, int KA>
+int launch_mode(ls_handle* h, int mode, const CUtensorMap* map, unsigned grid, const StepArgs& a) {
+    switch (mode) {
+        case 0: return launch<0, NB, KA>(h, map, grid, a);
+        case 1: return launch<1, NB, KA>(h, map, grid, a);
+        case 2: return launch<2, NB, KA>(h, map, grid, a);
+        case 3: return launch<3, NB, KA>(h, map, grid, a);
+        default: return launch<4, NB, KA>(h, map, grid, a);
+    }
+}
+
+template <int NB>
+int launch_ka(ls_handle* h, int mode, const CUtensorMap* map, unsigned grid, const StepArgs& a) {
+    switch ((a.q + 31) / 32) {
+        case 1: return launch_mode<NB, 1>(h, mode, map, grid, a);
+        case 2: return launch_mode<NB, 2>(h, mode, map, grid, a);
+        case 3: return launch_mode<NB, 3>(h, mode, map, grid, a);
+        default: return launch_mode<NB, 4>(h, mode, map, grid, a);
+    }
+}
+
+}  // namespace
+
+// The TF32 planes of both directions' factors and their tensor maps (after ls_factor,
+// LS_MIXED).  One map per direction covers all its matrices: dims (K = q, rows = q,
+// plane = 2 x matrices), boxes of 32 x round8(q) x 1 with the 128-byte swizzle.
+int ls_cr_tc_prepare(ls_handle* h) {
+    if (h->prec != LS_MIXED || h->q > 112) return LS_OK;
+    auto enc = encoder();
+    if (!enc) return LS_OK;   // no TMA encoder: the CUDA-core steps stay in use
+    const int q = h->q, ld = (q + 3) / 4 * 4;
+    for (int d = 0; d < 2; ++d) {
+        DirFactors& F = h->fac[d];
+        if (!F.pool32) return LS_ESTATE;
+        const size_t nmat = F.mats_per_strip * (size_t)h->L;
+        cudaFree(F.pool_tc);
+        F.pool_tc = nullptr;
+        LS_CUDA(cudaMalloc(&F.pool_tc, sizeof(float) * 2 * (size_t)q * ld * nmat));
+        LS_LAUNCH(h, k_pack_tc, 1216, 256, 0, nmat, q, ld, F.pool32, F.pool_tc);
+        const cuuint64_t dims[3] = {(cuuint64_t)q, (cuuint64_t)q, (cuuint64_t)(2 * nmat)};
+        const cuuint64_t strides[2] = {(cuuint64_t)ld * sizeof(float), (cuuint64_t)q * ld * sizeof(float)};
+        const int boxr = (q + 7) / 8 * 8;
+        const cuuint32_t box[3] = {32, (cuuint32_t)boxr, 1};
+        const cuuint32_t estr[3] = {1, 1, 1};
+        CUtensorMap* map = reinterpret_cast<CUtensorMap*>(F.tc_map);
+        if (enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, F.pool_tc, dims, strides, box, estr,
+                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return LS_ECUDA;
+    }
+    static std::once_flag once;
+    static int rc = LS_OK;
+    std::call_once(once, [] {
+        int r = LS_OK;
+        auto all = [&](auto f) { if (r == LS_OK) r = f(); };
+        all([] { return set_smem_all<8, 1>(); });  all([] { return set_smem_all<8, 2>(); });
+        all([] { return set_smem_all<8, 3>(); });  all([] { return set_smem_all<8, 4>(); });
+        all([] { return set_smem_all<16, 1>(); }); all([] { return set_smem_all<16, 2>(); });
+        all([] { return set_smem_all<16, 3>(); }); all([] { return set_smem_all<16, 4>(); });
+        all([] { return set_smem_all<32, 1>(); }); all([] { return set_smem_all<32, 2>(); });
+        all([] { return set_smem_all<32, 3>(); }); all([] { return set_smem_all<32, 4>(); });
+        rc = r;
+    });
+    LS_CUDA(cudaStreamSynchronize(h->stream));
+    if (rc != LS_OK) return rc;
+    h->tc_ready = true;
+    return LS_OK;
+}
+
+void ls_cr_tc_free(ls_handle* h) {
+    for (int d = 0; d < 2; ++d) {
+        cudaFree(h->fac[d].pool_tc);
+        h->fac[d].pool_tc = nullptr;
+    }
+    h->tc_ready = false;
+}
+
+// Largest batch one tensor-core step takes (the B operand of 32 right-hand sides and
+// three vectors fills most of the shared memory).
+int ls_cr_tc_max_nb(const ls_handle*) { return 32; }
+
+int ls_cr_tc_timeouts(unsigned* count) {
+    LS_CUDA(cudaMemcpyFromSymbol(count, g_cr_timeouts, sizeof(unsigned)));
+    return LS_OK;
+}
+
+// One reduction step on the tensor cores: `mode` as in k_cr_mma, `grid` blocks of the
+// level (one CTA each), strip l of direction dir, nb <= ls_cr_tc_max_nb members.
+int ls_cr_tc_step(ls_handle* h, int dir, int l, int mode, int k, int nk, unsigned grid, size_t off_a, size_t off_b,
+                  size_t off_c, float2* x, size_t SB, int nb, const float2* cw, const float2* ce) {
+    const DirFactors& F = h->fac[dir];
+    StepArgs a{h->q, k, nk, (size_t)l * F.mats_per_strip, off_a, off_b, off_c, x, SB, nb, cw, ce};
+    const CUtensorMap* map = reinterpret_cast<const CUtensorMap*>(F.tc_map);
+    if (nb <= 8) return launch_ka<8>(h, mode, map, grid, a);
+    if (nb <= 16) return launch_ka<16>(h, mode, map, grid, a);
+    if (nb <= 32) return launch_ka<32>(h, mode, map, grid, a);
+    return LS_EINVAL;
+}

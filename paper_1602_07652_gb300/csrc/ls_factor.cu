@@ -529,6 +529,7 @@ int ls_factor_all(ls_handle* h) {
 
 void ls_factor_free(ls_handle* h) {
     ls_bd_graph_free(h);
+    ls_cr_tc_free(h);
     for (int d = 0; d < 2; ++d) {
         DirFactors& F = h->fac[d];
         cudaFree(F.pool64);

@@ -825,6 +825,9 @@ extern "C" int ls_test_tma_shortfall(unsigned bytes) {
 
 extern "C" int ls_device_timeouts(unsigned* count) {
     if (!count) return LS_EINVAL;
-    LS_CUDA(cudaMemcpyFromSymbol(count, g_tma_timeouts, sizeof(unsigned)));
+    unsigned cols = 0, steps = 0;
+    LS_CUDA(cudaMemcpyFromSymbol(&cols, g_tma_timeouts, sizeof(unsigned)));
+    LS_TRY(ls_cr_tc_timeouts(&steps));
+    *count = cols + steps;
     return LS_OK;
 }

@@ -103,6 +103,10 @@ struct DirFactors {
     size_t mats_per_strip = 0;    // matrices per strip in the pool
     double2* pool64 = nullptr;    // L * mats_per_strip * q*q (FP64; freed in LS_MIXED)
     float2* pool32 = nullptr;     // same layout in FP32 (LS_MIXED)
+    // LS_MIXED, tensor-core steps (ls_cr_mma.cu): every matrix as two row-major TF32
+    // planes (re, im) of q rows x ld (ld = q rounded up to 4), and the TMA map over them
+    float* pool_tc = nullptr;
+    alignas(64) unsigned char tc_map[128] = {};
     // problem of this direction (the vertical direction is the transposed grid)
     const double* m = nullptr;    // medium of this direction's grid (n x n, long axis fastest)
     StencilTables* tab = nullptr; // device copy of the tables of this direction
@@ -117,7 +121,7 @@ struct DirFactors {
 };
 
 // ------------------------------------------------------------------ handle
-constexpr int kMaxBatch = 8;   // right-hand sides per batched Algorithm 2 (FP64: 4)
+constexpr int kMaxBatch = 32;  // right-hand sides per batched Algorithm 2 (ls_bd_cap: the form's own limit)
 
 struct ls_handle {
     int n = 0, L = 0, E = 0, t = 0, q = 0, P = 0, lp = 0, prec = LS_FP64;
@@ -159,9 +163,9 @@ struct ls_handle {
         void* vtmp = nullptr;      // 4 n*n complex scratch fields (FP64) per right-hand side
         double2* bd_in = nullptr;  // graph staging
         double2* bd_out = nullptr;
-        cudaGraph_t graph[9] = {};
-        cudaGraphExec_t exec[9] = {};
-        long long nodes[9] = {};
+        cudaGraph_t graph[kMaxBatch + 1] = {};
+        cudaGraphExec_t exec[kMaxBatch + 1] = {};
+        long long nodes[kMaxBatch + 1] = {};
         int nb_cap = 0;
         void* cr_part = nullptr;        // partial sums of split reduction steps
         unsigned* cr_cnt = nullptr;     // arrival counters of split reduction steps (kept at 0)
@@ -191,6 +195,8 @@ struct ls_handle {
     static constexpr int kFftVariants = 9;
     int bd_chunk = 0;          // right-hand sides per Algorithm 2 chain (0: the largest supported)
     int cr_split = 1;          // 1: reduction steps of small levels split blocks over several CTAs
+    bool tc_ready = false;     // LS_MIXED: TF32 factor planes and tensor maps built (ls_cr_tc_prepare)
+    int cr_tc = 1;             // 1: FP32 reduction steps on the tensor cores when tc_ready
 
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     double t_apply_ms = 0, t_sweep_ms = 0, t_apply64_ms = 0;
@@ -271,8 +277,17 @@ int ls_bd_lanes(ls_handle* h, const double2* g, double2* v, int nb, int chunk,
                 const unsigned char* on = nullptr);  // chunks on concurrent lanes, idle chunks skipped
 void ls_lanes_free(ls_handle* h);
 int ls_bd(ls_handle* h, const double2* g, double2* v);                   // Algorithm 2
+int ls_bd_cap(const ls_handle* h);   // right-hand sides one Algorithm 2 pass takes: FP64 4, mixed 8 (32 on tensor cores)
 void ls_bd_graph_free(ls_handle* h);
 int ls_strip_solve(ls_handle* h, int dir, int layer, const double2* b, double2* x);
+
+// tensor-core reduction steps (ls_cr_mma.cu)
+int ls_cr_tc_prepare(ls_handle* h);
+void ls_cr_tc_free(ls_handle* h);
+int ls_cr_tc_max_nb(const ls_handle* h);
+int ls_cr_tc_timeouts(unsigned* count);
+int ls_cr_tc_step(ls_handle* h, int dir, int l, int mode, int k, int nk, unsigned grid, size_t off_a, size_t off_b,
+                  size_t off_c, float2* x, size_t SB, int nb, const float2* cw, const float2* ce);
 
 // Krylov (ls_krylov.cu)
 int ls_inner_gmres(ls_handle* h, const double2* g, double tol, double2* v, int* iters);

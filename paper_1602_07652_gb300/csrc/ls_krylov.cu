@@ -100,7 +100,7 @@ int fgmres_b(ls_handle* h, Ctx* c, KrylovSpace& S, Op op, Pc pc, const double2* 
 // Right-hand sides per batched Algorithm 2 call: the autotuner's choice, else the
 // largest the sweep kernels take (FP64: 4).
 int bd_chunk(const ls_handle* h) {
-    const int cap = h->prec == LS_MIXED ? kMaxBatch : 4;
+    const int cap = ls_bd_cap(h);
     return h->bd_chunk > 0 && h->bd_chunk < cap ? h->bd_chunk : cap;
 }
 

@@ -477,9 +477,39 @@ int cr_solve_nb(ls_handle* h, int dir, int l, cpx_t<T>* x, size_t SB, int nb) {
     }
 }
 
+// The same local solve with the reduction steps on the tensor cores (ls_cr_mma.cu):
+// every step a TF32 GEMM over the whole batch (up to 32 right-hand sides), the
+// level-0 even update on the CUDA cores as above.
+int cr_solve_tc(ls_handle* h, int dir, int l, float2* x, size_t SB, int nb) {
+    const DirFactors& F = h->fac[dir];
+    const int q = h->q, n = h->n;
+    const CrLevel& l0 = F.lev[0];
+    const float2* cw = static_cast<const float2*>(F.cw) + (size_t)l * n * 3 * q;
+    const float2* ce = static_cast<const float2*>(F.ce) + (size_t)l * n * 3 * q;
+    const int thr = (q + 31) / 32 * 32;
+    if (l0.nodd) LS_TRY(ls_cr_tc_step(h, dir, l, 0, 0, l0.nk, (unsigned)l0.nodd, l0.off_dinv, 0, 0, x, SB, nb, cw, ce));
+    LS_LAUNCH(h, k_l0_even<float>, dim3(l0.neven, nb), thr, 0, q, n, cw, ce, x, SB);
+    for (int k = 1; k < F.K; ++k) {
+        const CrLevel& lv = F.lev[k];
+        LS_TRY(ls_cr_tc_step(h, dir, l, 1, k, lv.nk, (unsigned)lv.neven, 0, lv.off_f, lv.off_g, x, SB, nb, cw, ce));
+    }
+    LS_TRY(ls_cr_tc_step(h, dir, l, 3, 0, 1, 1u, F.off_top, 0, 0, x, SB, nb, cw, ce));
+    for (int k = F.K - 1; k >= 1; --k) {
+        const CrLevel& lv = F.lev[k];
+        if (!lv.nodd) continue;
+        LS_TRY(ls_cr_tc_step(h, dir, l, 2, k, lv.nk, (unsigned)lv.nodd, lv.off_dinv, lv.off_p, lv.off_q, x, SB, nb, cw,
+                             ce));
+    }
+    if (l0.nodd) LS_TRY(ls_cr_tc_step(h, dir, l, 4, 0, l0.nk, (unsigned)l0.nodd, l0.off_dinv, 0, 0, x, SB, nb, cw, ce));
+    return LS_OK;
+}
+
 // The batch template is the smallest supported NB >= nb (FP64 keeps NB <= 4 for registers).
 template <typename T>
 int cr_solve(ls_handle* h, int dir, int l, cpx_t<T>* x, size_t SB, int nb) {
+    if constexpr (sizeof(T) == 4) {
+        if (h->tc_ready && h->cr_tc) return cr_solve_tc(h, dir, l, x, SB, nb);
+    }
     if (nb <= 1) return cr_solve_nb<T, 1>(h, dir, l, x, SB, nb);
     if (nb <= 2) return cr_solve_nb<T, 2>(h, dir, l, x, SB, nb);
     if (nb <= 4) return cr_solve_nb<T, 4>(h, dir, l, x, SB, nb);
@@ -620,7 +650,7 @@ int ls_sweep_alloc(ls_handle* h) {
 // Algorithm 1 on direction dir (0: horizontal layers; 1: vertical layers) for nb
 // right-hand sides g (nb x N, contiguous) into v.
 int ls_sweep_dir_b(ls_handle* h, int dir, const double2* g, double2* v, int nb) {
-    if (nb < 1 || nb > kMaxBatch || (h->prec != LS_MIXED && nb > 4)) return LS_EINVAL;
+    if (nb < 1 || nb > ls_bd_cap(h)) return LS_EINVAL;
     LS_TRY(ls_sweep_reserve(h, nb));  // no-op when called inside a capture (reserved beforehand)
     const size_t N = (size_t)h->n * h->n;
     double2* t0 = static_cast<double2*>(h->lanes[h->lane].vtmp);
@@ -692,7 +722,7 @@ static int bd_capture(ls_handle* h, int nb) {
 }
 
 int ls_bd_b(ls_handle* h, const double2* g, double2* v, int nb) {
-    if (nb < 1 || nb > kMaxBatch || (h->prec != LS_MIXED && nb > 4)) return LS_EINVAL;
+    if (nb < 1 || nb > ls_bd_cap(h)) return LS_EINVAL;
     LS_TRY(ls_sweep_reserve(h, nb));
     if (!h->opts.use_graphs) return bd_direct(h, g, v, nb);
     ls_handle::SweepLane& W = h->lanes[h->lane];
@@ -758,6 +788,11 @@ int ls_bd_lanes(ls_handle* h, const double2* g, double2* v, int nb, int chunk, c
 }
 
 int ls_bd(ls_handle* h, const double2* g, double2* v) { return ls_bd_b(h, g, v, 1); }
+
+int ls_bd_cap(const ls_handle* h) {
+    if (h->prec != LS_MIXED) return 4;
+    return h->tc_ready && h->cr_tc ? ls_cr_tc_max_nb(h) : 8;
+}
 
 int ls_strip_solve(ls_handle* h, int dir, int layer, const double2* b, double2* x) {
     const int n = h->n, q = h->q;

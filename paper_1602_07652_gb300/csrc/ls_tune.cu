@@ -77,37 +77,47 @@ extern "C" int ls_autotune(ls_handle* h, int nrhs, int reps, ls_tuning* out) {
         if (rc != LS_OK) break;
         h->fft_variant = pick;
         t.fft_variant = pick;
-        // band-block batching of Algorithm 2 for nrhs right-hand sides (needs the factors)
+        // band-block batching of Algorithm 2 for nrhs right-hand sides (needs the factors):
+        // reduction steps on the CUDA cores (chunks 1, 2, 4, 8, blocks of small levels split
+        // over several CTAs or not) and, when built, on the tensor cores (chunks 1, 8, 16, 32)
         if (!h->factored) break;
-        const int cap = h->prec == LS_MIXED ? kMaxBatch : 4;
         best = 0;
-        int chunk = 1, split = 1;
-        for (int sp = 1; sp >= 0 && rc == LS_OK; --sp) {  // split reduction steps on, then off
-            if (h->cr_split != sp) {
+        int chunk = 1, split = 1, tc = 0;
+        const int tc_avail = h->tc_ready && h->cr_tc ? 1 : 0;   // switched off by ls_set_tensor_steps: not tried
+        for (int form = tc_avail ? 2 : 1; form >= 0 && rc == LS_OK; --form) {  // 2: tensor cores, 1: split, 0: unsplit
+            const int want_tc = form == 2, sp = form == 2 ? h->cr_split : form;
+            if (h->cr_split != sp || h->cr_tc != want_tc) {
                 h->cr_split = sp;
+                h->cr_tc = want_tc;
                 ls_bd_graph_free(h);  // the captured launches bake the grid shapes in
             }
-            for (int k = 0, c = 1; c <= cap && rc == LS_OK; ++k, c *= 2) {
-                if (c > nrhs && c > 1) break;
+            const int cap = ls_bd_cap(h);
+            const int tc_chunks[4] = {1, 8, 16, 32};
+            for (int k = 0; k < 4 && rc == LS_OK; ++k) {
+                const int c = want_tc ? tc_chunks[k] : (1 << k);
+                if (c > cap || (c > nrhs && c > 1)) break;
                 BdArg ba{buf, buf + nrhs * N, nrhs, c};
                 float ms = 0;
                 rc = time_ms(h, reps, &ms, run_bd, &ba);
-                (sp ? t.bd_ms : t.bd_ms_nosplit)[k] = ms / nrhs;
+                (want_tc ? t.bd_ms_tc : (sp ? t.bd_ms : t.bd_ms_nosplit))[k] = ms / nrhs;
                 if (rc == LS_OK && (best == 0 || ms < best)) {
                     best = ms;
                     chunk = c;
                     split = sp;
+                    tc = want_tc;
                 }
             }
         }
         if (rc != LS_OK) break;
-        if (h->cr_split != split) {
+        if (h->cr_split != split || h->cr_tc != tc) {
             h->cr_split = split;
+            h->cr_tc = tc;
             ls_bd_graph_free(h);
         }
         h->bd_chunk = chunk;
         t.bd_chunk = chunk;
         t.cr_split = split;
+        t.tensor_steps = tc;
     } while (0);
     cudaStreamSynchronize(h->stream);
     cudaFree(buf);
@@ -117,7 +127,7 @@ extern "C" int ls_autotune(ls_handle* h, int nrhs, int reps, ls_tuning* out) {
 
 extern "C" int ls_set_shapes(ls_handle* h, int fft_variant, int bd_chunk) {
     if (!h || fft_variant < 0 || fft_variant >= ls_handle::kFftVariants) return LS_EINVAL;
-    const int cap = h->prec == LS_MIXED ? kMaxBatch : 4;
+    const int cap = ls_bd_cap(h);
     if (bd_chunk < 0 || bd_chunk > cap) return LS_EINVAL;
     h->fft_variant = fft_variant;
     h->bd_chunk = bd_chunk;
@@ -129,6 +139,18 @@ extern "C" int ls_set_reduction(ls_handle* h, int cr_split) {
     if (h->cr_split != cr_split) {
         LS_CUDA(cudaStreamSynchronize(h->stream));
         h->cr_split = cr_split;
+        ls_bd_graph_free(h);
+    }
+    return LS_OK;
+}
+
+extern "C" int ls_set_tensor_steps(ls_handle* h, int on) {
+    if (!h || (on != 0 && on != 1)) return LS_EINVAL;
+    if (on && !h->tc_ready) return LS_ESTATE;
+    if (h->cr_tc != on) {
+        LS_CUDA(cudaStreamSynchronize(h->stream));
+        h->cr_tc = on;
+        if (h->bd_chunk > ls_bd_cap(h)) h->bd_chunk = 0;
         ls_bd_graph_free(h);
     }
     return LS_OK;

@@ -87,6 +87,10 @@ def test_batched_bd_rejects_oversized_batches():
                          precision=binding.LS_MIXED)
     smx.ls_factor()
     with pytest.raises(binding.LSError) as e:
+        smx.ls_precond_bd_batch(_fields(n, binding.LS_MAX_BD_BATCH + 1, 0))
+    assert e.value.code == -1
+    smx.ls_set_tensor_steps(0)   # the CUDA-core steps take at most 8
+    with pytest.raises(binding.LSError) as e:
         smx.ls_precond_bd_batch(_fields(n, 9, 0))
     assert e.value.code == -1
     smx.close()

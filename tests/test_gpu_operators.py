@@ -176,6 +176,8 @@ def test_local_solves_match_oracle(n, L, E, ppw, prec, tol):
     m = inputs.bump_medium(n, nbumps=6, seed=3 * n)
     s = binding.Solver(cuda(m), w, layers=L, ext=E, precision=prec)
     s.ls_factor()
+    if prec == binding.LS_MIXED:
+        s.ls_set_tensor_steps(0)   # the FP32 CUDA-core steps (tensor-core TF32 steps: test_gpu_tensor_steps)
     st = sparsify.Stencils(n, 1.0 / n, w)
     lay = polarized.Layering(m, st, w, L, E)
     lay_t = polarized.Layering(m.T.copy(), st.transposed(), w, L, E)
@@ -194,6 +196,8 @@ def test_sweeps_match_oracle(n, L, E, ppw, prec, tol):
     m = inputs.bump_medium(n, nbumps=6, seed=4 * n)
     s = binding.Solver(cuda(m), w, layers=L, ext=E, precision=prec)
     s.ls_factor()
+    if prec == binding.LS_MIXED:
+        s.ls_set_tensor_steps(0)
     st = sparsify.Stencils(n, 1.0 / n, w)
     bd = polarized.BiDirectional(m, st, w, L, E)
     g = inputs.random_field(n, 21)
