@@ -363,6 +363,17 @@ int ls_local_solve(ls_handle* h, int dir, int layer, const ls_c64* b, ls_c64* x)
  * it: calls that overlap on the GPU (other streams, other host threads) race. */
 int ls_apply_f32_noalloc(int n, const float* m, const ls_c32* ghat, const ls_c32* u, ls_c32* y, void* stream);
 
+/* ls_check_conversions -- self-check of the FP64 <-> FP32 conversions the mixed-
+ * precision kernels use (integer-pipe routines: GB300's FP64 units, which the
+ * hardware conversions occupy, are few; the paper has no counterpart): for
+ * i < n compares the library's double -> float (round to nearest even) of d[i] and
+ * float -> double of f[i] with the hardware's, bit for bit (NaN inputs: NaN-ness
+ * only).  d, f: DEVICE arrays of n elements; *mismatches (host) = the number of
+ * differing results, 0 when the routines are exact.  Runs on the legacy stream and
+ * synchronises; allocates 8 bytes of device memory for the call.  LS_EINVAL on NULL
+ * pointers or n < 0. */
+int ls_check_conversions(const double* d, const float* f, long long n, unsigned long long* mismatches);
+
 /* ---- introspection (host copies of small tables) ---- */
 
 /* alpha, beta: host arrays of 81 ls_c64 each, index [type*9 + slot] with

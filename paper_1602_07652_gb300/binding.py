@@ -89,6 +89,7 @@ _SIGS = {
     "ls_set_shapes": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int]),
     "ls_set_reduction": (ctypes.c_int, [_P, ctypes.c_int]),
     "ls_set_tensor_steps": (ctypes.c_int, [_P, ctypes.c_int]),
+    "ls_check_conversions": (ctypes.c_int, [_P, _P, ctypes.c_longlong, ctypes.POINTER(ctypes.c_ulonglong)]),
     "ls_device_timeouts": (ctypes.c_int, [ctypes.POINTER(ctypes.c_uint)]),
     "ls_test_tma_shortfall": (ctypes.c_int, [ctypes.c_uint]),
     "ls_solve_host": (ctypes.c_int, [_P, _P, ctypes.c_double, _P, ctypes.POINTER(Stats)]),
@@ -258,6 +259,18 @@ def default_opts() -> Opts:
     o = Opts()
     load_library().ls_default_opts(ctypes.byref(o))
     return o
+
+
+def check_conversions(d: torch.Tensor, f: torch.Tensor) -> int:
+    """Mismatches of the library's FP64 <-> FP32 conversions against the hardware's
+    (d: CUDA float64, f: CUDA float32, same number of elements)."""
+    lib = load()
+    if d.dtype != torch.float64 or f.dtype != torch.float32 or not d.is_cuda or not f.is_cuda \
+            or not d.is_contiguous() or not f.is_contiguous() or d.numel() != f.numel():
+        raise ValueError("check_conversions: contiguous CUDA float64 and float32 tensors of one size")
+    out = ctypes.c_ulonglong(0)
+    _ck(lib.ls_check_conversions(_ptr(d), _ptr(f), d.numel(), ctypes.byref(out)), "ls_check_conversions")
+    return int(out.value)
 
 
 def ls_apply_f32_noalloc(n: int, m32: torch.Tensor, ghat32: torch.Tensor, u: torch.Tensor,

@@ -40,8 +40,6 @@ namespace {
 __device__ unsigned g_cr_timeouts;   // steps whose TMA loads or MMAs did not complete in time
 
 constexpr int kThreads = 256;
-constexpr int kStages = 4;                  // A ring
-constexpr int kStageBytes = 128 * 128;      // 128 rows x 128 bytes (32 TF32 of K)
 constexpr unsigned long long kWaitNs = 1000000000ull;
 
 __device__ __forceinline__ unsigned su32(const void* p) { return static_cast<unsigned>(__cvta_generic_to_shared(p)); }
@@ -124,12 +122,29 @@ template <int MODE> struct ModeOf {
     static constexpr bool ADD = MODE == 1 || MODE == 4;              // x_j += D instead of x_j = D
 };
 
-// Shared memory of one CTA: A ring | B (NV vectors x KA atoms x 3NB rows x 128 B) |
-// barriers (full[kStages], empty[kStages], done) | TMEM address | failure flag.
+// Shared memory of one CTA: A ring (S stages of ROWS x 128 B; the MMA reads 128 rows
+// from a stage's start, so the ring is followed by 128 - ROWS rows of slack, and rows
+// past the box land on the next stage: garbage rows of D that are never read) |
+// B (NV vectors x KA atoms x 3NB rows x 128 B) | barriers (full[S], empty[S], done) |
+// TMEM address | failure flag.  S: as many stages as the atoms of a step need, within
+// 110 KB for one-matrix steps (two CTAs per SM) and 225 KB otherwise.
+template <int MODE, int NB, int KA>
+struct Cfg {
+    static constexpr int NV = ModeOf<MODE>::NV;
+    static constexpr int ROWS = 32 * KA < 128 ? 32 * KA : 128;
+    static constexpr int STAGE = ROWS * 128;
+    static constexpr int SLACK = 128 * 128 - STAGE;
+    static constexpr int BBYTES = NV * KA * 3 * NB * 128;
+    static constexpr int NAT = NV * 2 * KA;
+    static constexpr int BUDGET = (NV == 1 ? 110 : 225) * 1024 - BBYTES - SLACK - 1024 - 256;
+    static constexpr int FIT = BUDGET / STAGE;
+    static constexpr int S = NAT < FIT ? (NAT < 12 ? NAT : 12) : (FIT < 12 ? FIT : 12);
+    static_assert(S >= 2, "shared memory too small for two A stages");
+    static constexpr size_t SMEM = 1024 + (size_t)S * STAGE + SLACK + BBYTES + 8 * (2 * S + 1) + 16;
+};
 template <int MODE, int NB, int KA>
 constexpr size_t tc_smem() {
-    return 1024 /* alignment slack */ + (size_t)kStages * kStageBytes +
-           (size_t)ModeOf<MODE>::NV * KA * 3 * NB * 128 + 8 * (2 * kStages + 1) + 16;
+    return Cfg<MODE, NB, KA>::SMEM;
 }
 
 struct StepArgs {
@@ -152,10 +167,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_cr_mma(const __grid_constant__ 
     constexpr unsigned BATOM = BROWS * 128;       // bytes of one vector's B atom
     constexpr int NCOL = 2 * NB;                  // accumulator columns
     constexpr int TCOLS = NCOL <= 32 ? 32 : (NCOL <= 64 ? 64 : 128);
+    using CF = Cfg<MODE, NB, KA>;
+    constexpr int kStages = CF::S, kStageBytes = CF::STAGE;
     extern __shared__ unsigned char smem_raw[];
     unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     unsigned char* As = base;
-    unsigned char* Bs = As + kStages * kStageBytes;
+    unsigned char* Bs = As + kStages * kStageBytes + CF::SLACK;
     auto* full = reinterpret_cast<unsigned long long*>(Bs + (size_t)NV * KA * BATOM);
     auto* empty = full + kStages;
     auto* done = empty + kStages;

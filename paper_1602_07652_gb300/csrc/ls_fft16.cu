@@ -663,7 +663,7 @@ __global__ void __launch_bounds__(Geo<LP, 4>::THREADS, 4) k_rows16_inv(int nrows
 #pragma unroll
     for (int t = 0; t < E / 2; ++t) {
         const int x = j + t * T;
-        if (x < n) y[(size_t)z * n + x] = us[x] + ccast<UIO>(v[0][t]);
+        if (x < n) y[(size_t)z * n + x] = us[x] + hw_cast<UIO>(v[0][t]);
     }
 }
 

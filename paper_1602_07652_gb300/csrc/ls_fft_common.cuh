@@ -80,7 +80,7 @@ struct SrcMU {  // m u  (Sec. 2: D u)
     template <typename C>
     __device__ __forceinline__ C load(int z, int x) const {
         const size_t i = (size_t)z * n + x;
-        return m[i] * ccast<C>(__ldg(&u[i]));
+        return m[i] * hw_cast<C>(__ldg(&u[i]));
     }
 };
 
@@ -118,7 +118,7 @@ struct DstApply {  // y = u + (G-term)
     template <typename C>
     __device__ __forceinline__ void store(int z, int x, C v) const {
         const size_t i = (size_t)z * n + x;
-        y[i] = u[i] + ccast<UIO>(v);
+        y[i] = u[i] + hw_cast<UIO>(v);
     }
 };
 

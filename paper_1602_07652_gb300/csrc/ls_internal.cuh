@@ -53,13 +53,76 @@ LS_CPX_OPS(float2, float)
 LS_CPX_OPS(double2, double)
 #undef LS_CPX_OPS
 
+// FP64 <-> FP32 conversions on the integer pipes.  GB300's FP64 units are few (about
+// 1/64 of the FP32 rate) and the hardware conversions run on them, so kernels that move
+// FP64 fields into FP32 arithmetic and back (the mixed-precision path) were bound by
+// conversions.  These give the same results as the hardware's round-to-nearest-even
+// conversion (double -> float) and the exact widening (float -> double), subnormals,
+// infinities and NaNs (quieted) included; ls_check_conversions tests them against it.
+__host__ __device__ __forceinline__ float d2f_rn(double d) {
+#ifdef __CUDA_ARCH__
+    const unsigned long long b = (unsigned long long)__double_as_longlong(d);
+    const unsigned sgn = (unsigned)(b >> 32) & 0x80000000u;
+    const int e = (int)((b >> 52) & 0x7FF);
+    const unsigned long long m = b & 0xFFFFFFFFFFFFFull;
+    if (e == 0x7FF) return __uint_as_float(sgn | 0x7F800000u | (m ? (0x400000u | (unsigned)(m >> 29)) : 0u));
+    int ef = e - 1023 + 127;                       // biased float exponent of a normal result
+    if (ef >= 255) return __uint_as_float(sgn | 0x7F800000u);
+    const unsigned long long mm = m | (e ? (1ull << 52) : 0ull);   // 53-bit significand
+    int sh = 29;                                   // bits dropped for a normal result
+    if (ef <= 0) {                                 // subnormal (or zero) float
+        sh += 1 - ef;
+        ef = 0;
+        if (sh > 62) return __uint_as_float(sgn);  // below half the smallest subnormal
+    }
+    const unsigned long long qv = mm >> sh, rem = mm & ((1ull << sh) - 1), half = 1ull << (sh - 1);
+    const unsigned long long r = qv + ((rem > half || (rem == half && (qv & 1ull))) ? 1ull : 0ull);
+    // normal: exponent field (ef - 1) plus the significand with its leading 1 (a carry
+    // out of the significand bumps the exponent); subnormal: the significand alone
+    const unsigned bits = ef > 0 ? ((unsigned)(ef - 1) << 23) + (unsigned)r : (unsigned)r;
+    return __uint_as_float(sgn | bits);
+#else
+    return (float)d;
+#endif
+}
+__host__ __device__ __forceinline__ double f2d(float f) {
+#ifdef __CUDA_ARCH__
+    const unsigned b = __float_as_uint(f);
+    const unsigned long long sgn = (unsigned long long)(b & 0x80000000u) << 32;
+    const int e = (int)((b >> 23) & 0xFF);
+    const unsigned m = b & 0x7FFFFFu;
+    if (e == 0xFF)
+        return __longlong_as_double((long long)(sgn | 0x7FF0000000000000ull | ((unsigned long long)m << 29) |
+                                                (m ? 0x8000000000000ull : 0ull)));
+    if (e == 0) {
+        if (!m) return __longlong_as_double((long long)sgn);
+        const int top = 31 - __clz(m);             // m = 2^top (1.f), value = m 2^-149
+        const unsigned long long frac = ((unsigned long long)m << (52 - top)) & 0xFFFFFFFFFFFFFull;
+        return __longlong_as_double((long long)(sgn | ((unsigned long long)(top - 149 + 1023) << 52) | frac));
+    }
+    return __longlong_as_double(
+        (long long)(sgn | ((unsigned long long)(e - 127 + 1023) << 52) | ((unsigned long long)m << 29)));
+#else
+    return (double)f;
+#endif
+}
+
 template <typename D, typename S> __host__ __device__ __forceinline__ D ccast(S a);
 template <> __host__ __device__ __forceinline__ float2 ccast<float2, float2>(float2 a) { return a; }
 template <> __host__ __device__ __forceinline__ double2 ccast<double2, double2>(double2 a) { return a; }
 template <> __host__ __device__ __forceinline__ float2 ccast<float2, double2>(double2 a) {
-    return make_float2((float)a.x, (float)a.y);
+    return make_float2(d2f_rn(a.x), d2f_rn(a.y));
 }
 template <> __host__ __device__ __forceinline__ double2 ccast<double2, float2>(float2 a) {
+    return make_double2(f2d(a.x), f2d(a.y));
+}
+// The same casts by the hardware conversions (FP64 pipe), for kernels whose integer and
+// FP32 pipes are the busy ones (the FFT passes of the mixed LS-apply).
+template <typename D, typename S> __host__ __device__ __forceinline__ D hw_cast(S a) { return ccast<D>(a); }
+template <> __host__ __device__ __forceinline__ float2 hw_cast<float2, double2>(double2 a) {
+    return make_float2((float)a.x, (float)a.y);
+}
+template <> __host__ __device__ __forceinline__ double2 hw_cast<double2, float2>(float2 a) {
     return make_double2((double)a.x, (double)a.y);
 }
 

@@ -14,52 +14,89 @@
 
 namespace {
 
-// batch member b = blockIdx.y works on v, g, y at offset b * n * n (m is shared).
+// batch member b = blockIdx.z works on v, g, y at offset b * n * n (m is shared).
 // R: arithmetic type of the coefficients and the sum (FP64 I/O either way); FP32 is
 // used where the stencil only feeds the preconditioner in mixed precision (on
 // GB300 the FP64 form is bound by the FP64 units, the FP32 form by memory).
+// A CTA of 32 x 8 threads computes a tile of 32 x 32 points (4 rows per thread): the
+// tile's v and m with a one-point halo are staged in shared memory (in the
+// arithmetic type) by loads that are all issued before the first store, so every
+// value of v and m is read from HBM about once.
+constexpr int kStX = 32, kStZ = 32, kStRows = 4;   // tile, rows per thread (threads 32 x 8)
 template <int MODE, typename R>  // 0: y = A v   1: y = C v   2: y = g - C v
-__global__ void k_stencil(int n, const StencilTables* __restrict__ tab, const double* __restrict__ m,
-                          const double2* __restrict__ v, const double2* __restrict__ g, double2* __restrict__ y) {
+__global__ void __launch_bounds__(256) k_stencil(int n, const StencilTables* __restrict__ tab,
+                                                 const double* __restrict__ m, const double2* __restrict__ v,
+                                                 const double2* __restrict__ g, double2* __restrict__ y) {
     using CR = cpx_t<R>;
+    constexpr int HX = kStX + 2, HZ = kStZ + 2, HN = HX * HZ;
     __shared__ CR sa[81], sb[81];
+    __shared__ CR sv[HZ][HX];
+    __shared__ R sm[MODE >= 1 ? HZ : 1][MODE >= 1 ? HX : 1];
     {
-        const size_t off = (size_t)blockIdx.y * n * n;
+        const size_t off = (size_t)blockIdx.z * n * n;
         v += off;
         y += off;
         if (MODE == 2) g += off;
     }
-    for (int i = threadIdx.x; i < 81; i += blockDim.x) {
+    const int tid = threadIdx.y * kStX + threadIdx.x;
+    for (int i = tid; i < 81; i += 256) {
         sa[i] = ccast<CR>(tab->alpha[i]);
         sb[i] = ccast<CR>(tab->wbeta[i]);
     }
-    __syncthreads();
-    const size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= (size_t)n * n) return;
-    const int i = (int)(k % n), j = (int)(k / n);
-    const int bx = i == 0 ? -1 : (i == n - 1 ? 1 : 0);
-    const int bz = j == 0 ? -1 : (j == n - 1 ? 1 : 0);
-    const int t = (bz + 1) * 3 + (bx + 1);
-    CR acc = czero<CR>();
+    const int x0 = blockIdx.x * kStX - 1, z0 = blockIdx.y * kStZ - 1;
+    constexpr int PER = (HN + 255) / 256;   // halo tile elements per thread
+    double2 vv[PER];
+    double mv[PER];
 #pragma unroll
-    for (int dz = -1; dz <= 1; ++dz) {
-        if ((bz == -1 && dz == -1) || (bz == 1 && dz == 1)) continue;
+    for (int u = 0; u < PER; ++u) {
+        const int e = tid + u * 256, hz = e / HX, hx = e % HX, x = x0 + hx, z = z0 + hz;
+        const bool in = e < HN && x >= 0 && x < n && z >= 0 && z < n;
+        vv[u] = in ? __ldg(&v[(size_t)z * n + x]) : make_double2(0.0, 0.0);
+        if (MODE >= 1) mv[u] = in ? __ldg(&m[(size_t)z * n + x]) : 0.0;
+    }
 #pragma unroll
-        for (int dx = -1; dx <= 1; ++dx) {
-            if ((bx == -1 && dx == -1) || (bx == 1 && dx == 1)) continue;
-            const int s = (dz + 1) * 3 + (dx + 1);
-            const size_t p = k + (long long)dz * n + dx;
-            CR c = sa[t * 9 + s];
-            if (MODE >= 1) {
-                const R mm = (R)__ldg(&m[p]);
-                c = mkc(fma(mm, sb[t * 9 + s].x, c.x), fma(mm, sb[t * 9 + s].y, c.y));
+    for (int u = 0; u < PER; ++u) {
+        const int e = tid + u * 256;
+        if (e < HN) {
+            sv[e / HX][e % HX] = ccast<CR>(vv[u]);
+            if constexpr (MODE >= 1) {
+                if constexpr (sizeof(R) == 4) sm[e / HX][e % HX] = d2f_rn(mv[u]);
+                else sm[e / HX][e % HX] = mv[u];
             }
-            acc = cfma(c, ccast<CR>(__ldg(&v[p])), acc);
         }
     }
-    double2 out = ccast<double2>(acc);
-    if (MODE == 2) out = __ldg(&g[k]) - out;
-    y[k] = out;
+    __syncthreads();
+    const int i = blockIdx.x * kStX + threadIdx.x;
+    if (i >= n) return;
+    const int bx = i == 0 ? -1 : (i == n - 1 ? 1 : 0);
+#pragma unroll
+    for (int rr = 0; rr < kStRows; ++rr) {
+        const int lz = threadIdx.y + 8 * rr, j = blockIdx.y * kStZ + lz;
+        if (j >= n) break;
+        const int bz = j == 0 ? -1 : (j == n - 1 ? 1 : 0);
+        const int t = (bz + 1) * 3 + (bx + 1);
+        CR acc = czero<CR>();
+#pragma unroll
+        for (int dz = -1; dz <= 1; ++dz) {
+            if ((bz == -1 && dz == -1) || (bz == 1 && dz == 1)) continue;
+#pragma unroll
+            for (int dx = -1; dx <= 1; ++dx) {
+                if ((bx == -1 && dx == -1) || (bx == 1 && dx == 1)) continue;
+                const int sl = (dz + 1) * 3 + (dx + 1);
+                CR c = sa[t * 9 + sl];
+                const int hz = lz + 1 + dz, hx = threadIdx.x + 1 + dx;
+                if (MODE >= 1) {
+                    const R mm = sm[hz][hx];
+                    c = mkc(fma(mm, sb[t * 9 + sl].x, c.x), fma(mm, sb[t * 9 + sl].y, c.y));
+                }
+                acc = cfma(c, sv[hz][hx], acc);
+            }
+        }
+        const size_t k = (size_t)j * n + i;
+        double2 out = ccast<double2>(acc);
+        if (MODE == 2) out = __ldg(&g[k]) - out;
+        y[k] = out;
+    }
 }
 
 __global__ void k_transpose(int n, const double2* __restrict__ a, double2* __restrict__ b) {
@@ -173,18 +210,49 @@ __global__ void k_zero(size_t N, double2* __restrict__ y) {
         y[k] = make_double2(0, 0);
 }
 
+// mismatches of the integer-pipe conversions against the hardware ones (NaN: NaN-ness only)
+__global__ void k_check_conv(long long n, const double* __restrict__ d, const float* __restrict__ f,
+                             unsigned long long* __restrict__ bad) {
+    unsigned long long cnt = 0;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const float a = d2f_rn(d[i]), h = __double2float_rn(d[i]);
+        if (isnan(h) ? !isnan(a) : __float_as_uint(a) != __float_as_uint(h)) ++cnt;
+        const double a2 = f2d(f[i]), h2 = (double)f[i];
+        if (isnan(h2) ? !isnan(a2) : __double_as_longlong(a2) != __double_as_longlong(h2)) ++cnt;
+    }
+    if (cnt) atomicAdd(bad, cnt);
+}
+
 }  // namespace
+
+extern "C" int ls_check_conversions(const double* d, const float* f, long long n, unsigned long long* mismatches) {
+    if (!d || !f || !mismatches || n < 0) return LS_EINVAL;
+    unsigned long long* dev = nullptr;
+    LS_CUDA(cudaMalloc(&dev, sizeof(unsigned long long)));
+    int rc = LS_OK;
+    if (cudaMemset(dev, 0, sizeof(unsigned long long)) != cudaSuccess) rc = LS_ECUDA;
+    if (rc == LS_OK && n > 0) {
+        k_check_conv<<<608, 256>>>(n, d, f, dev);
+        if (cudaPeekAtLastError() != cudaSuccess) rc = LS_ECUDA;
+    }
+    if (rc == LS_OK && cudaMemcpy(mismatches, dev, sizeof(unsigned long long), cudaMemcpyDeviceToHost) != cudaSuccess)
+        rc = LS_ECUDA;
+    cudaFree(dev);
+    return rc;
+}
 
 template <typename R>
 int stencil_launch(ls_handle* h, int dir, int mode, const double2* v, const double2* g, double2* y, int nb) {
     const int n = h->n;
     const size_t N = (size_t)n * n;
-    const dim3 grid((unsigned)((N + 255) / 256), nb);
+    (void)N;
+    const dim3 grid((unsigned)((n + kStX - 1) / kStX), (unsigned)((n + kStZ - 1) / kStZ), nb);
+    const dim3 block(kStX, 256 / kStX);
     const double* m = dir == 0 ? h->m64 : h->mT64;
     const StencilTables* tab = h->dtabs + dir;
-    if (mode == 0) LS_LAUNCH(h, (k_stencil<0, R>), grid, 256, 0, n, tab, m, v, g, y);
-    else if (mode == 1) LS_LAUNCH(h, (k_stencil<1, R>), grid, 256, 0, n, tab, m, v, g, y);
-    else LS_LAUNCH(h, (k_stencil<2, R>), grid, 256, 0, n, tab, m, v, g, y);
+    if (mode == 0) LS_LAUNCH(h, (k_stencil<0, R>), grid, block, 0, n, tab, m, v, g, y);
+    else if (mode == 1) LS_LAUNCH(h, (k_stencil<1, R>), grid, block, 0, n, tab, m, v, g, y);
+    else LS_LAUNCH(h, (k_stencil<2, R>), grid, block, 0, n, tab, m, v, g, y);
     return LS_OK;
 }
 

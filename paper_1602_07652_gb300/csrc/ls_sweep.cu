@@ -277,23 +277,22 @@ __global__ void k_l0_even(int q, int nblk, const cpx_t<T>* __restrict__ cw, cons
 }
 
 // g^l = chi_{Omega^l} g (+ injection from the layer above), copied to the solution buffer.
-// Batch member b = blockIdx.y: strips at + b * SB, traces at + b * TB, grid vector at + b * N.
-// A CTA moves a tile of kGatherTile columns i: the t rows of g it needs are read along
-// x (coalesced) into shared memory, then written in the strip's block layout
-// (column i = q contiguous values, also coalesced).
-constexpr int kGatherTile = 16;
+// Batch member b = blockIdx.z: strips at + b * SB, traces at + b * TB, grid vector at + b * N.
+// A tiled transpose: a CTA of 32 x 8 threads takes 32 strip rows r x 32 columns i; it
+// reads the rows of g that fall in Omega^l along x (coalesced) into shared memory and
+// writes the strip's block layout (column i = q contiguous values) along r (coalesced).
+// The injected rows (eq. pde_GRF_down) are computed in the strip's precision.
+constexpr int kGatherTile = 32;
 template <typename T>
 __global__ void __launch_bounds__(256) k_gather(StripGeom g, const cpx_t<T>* __restrict__ inj, int l,
                                                 const double2* __restrict__ gf, cpx_t<T>* __restrict__ rhs,
                                                 cpx_t<T>* __restrict__ sol, const cpx_t<T>* __restrict__ above,
                                                 cpx_t<T>* __restrict__ trace_above, size_t SB, size_t TB) {
     using C = cpx_t<T>;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    C* tile = reinterpret_cast<C*>(smem_raw);  // [t][kGatherTile + 1]
-    constexpr int TI = kGatherTile;
+    __shared__ C tile[kGatherTile][kGatherTile + 1];   // [r - r0][i - i0]
     const int q = g.q, n = g.n, E = g.E, t = g.t;
-    const size_t b = blockIdx.y;
-    const int i0 = blockIdx.x * TI;
+    const size_t b = blockIdx.z;
+    const int i0 = blockIdx.x * kGatherTile, r0 = blockIdx.y * kGatherTile;
     gf += b * (size_t)n * n;
     rhs += b * SB;
     sol += b * SB;
@@ -301,35 +300,34 @@ __global__ void __launch_bounds__(256) k_gather(StripGeom g, const cpx_t<T>* __r
         above += b * SB;
         trace_above += b * TB;
     }
-    // rows l t .. l t + t - 1 of g, columns i0 .. i0 + TI - 1 (half a warp per row)
-    for (int o = threadIdx.x; o < t * TI; o += blockDim.x) {
-        const int rr = o / TI, il = o % TI, i = i0 + il;
-        tile[rr * (TI + 1) + il] = i < n ? ccast<C>(gf[(size_t)(l * t + rr) * n + i]) : czero<C>();
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    double2 v[kGatherTile / 8];
+#pragma unroll
+    for (int u = 0; u < kGatherTile / 8; ++u) {   // rows of Omega^l (E <= r < E + t), along x
+        const int r = r0 + ty + 8 * u, i = i0 + tx;
+        v[u] = (r >= E && r < E + t && i < n) ? __ldg(&gf[(size_t)(l * t - E + r) * n + i]) : make_double2(0.0, 0.0);
     }
+#pragma unroll
+    for (int u = 0; u < kGatherTile / 8; ++u) tile[ty + 8 * u][tx] = ccast<C>(v[u]);
     __syncthreads();
-    const int ncol = n - i0 < TI ? n - i0 : TI;
-    for (int o = threadIdx.x; o < ncol * q; o += blockDim.x) {
-        const int il = o / q, r = o % q, i = i0 + il;
+#pragma unroll
+    for (int u = 0; u < kGatherTile / 8; ++u) {   // strip columns, along r
+        const int i = i0 + ty + 8 * u, r = r0 + tx;
+        if (i >= n || r >= q) continue;
         const size_t e = (size_t)i * q + r;
-        if (above && r == 0) trace_above[i] = above[(size_t)i * q + E - 1];  // w^{l+1}_0, kept for the upward sweep
-        C cv = (r >= E && r < E + t) ? tile[(r - E) * (TI + 1) + il] : czero<C>();
-        if (above && (r == E + t - 1 || r == E + t)) {
-            double2 val = r == E + t - 1 ? gf[(size_t)(l * t - E + r) * n + i] : make_double2(0, 0);
+        C cv = tile[tx][ty + 8 * u];
+        if (above) {
+            if (r == 0) trace_above[i] = above[(size_t)i * q + E - 1];  // w^{l+1}_0, kept for the upward sweep
             const C* c0 = inj + (size_t)l * 12 * n;  // slots 0, 1 of layer l: [slot][dx+1][i]
             if (r == E + t - 1) {  // -C^l_{n,n+1} w^{l+1}_1 ; w^{l+1}_1 = row E of layer l+1
-                for (int dx = -1; dx <= 1; ++dx) {
-                    if (i + dx < 0 || i + dx >= n) continue;
-                    val = cfms(ccast<double2>(c0[(size_t)(0 * 3 + dx + 1) * n + i]),
-                               ccast<double2>(above[(size_t)(i + dx) * q + E]), val);
-                }
-            } else {  // +C^l_{n+1,n} w^{l+1}_0 ; w^{l+1}_0 = row E-1 of layer l+1
-                for (int dx = -1; dx <= 1; ++dx) {
-                    if (i + dx < 0 || i + dx >= n) continue;
-                    val = cfma(ccast<double2>(c0[(size_t)(1 * 3 + dx + 1) * n + i]),
-                               ccast<double2>(above[(size_t)(i + dx) * q + E - 1]), val);
-                }
+                for (int dx = -1; dx <= 1; ++dx)
+                    if (i + dx >= 0 && i + dx < n)
+                        cv = cfms(c0[(size_t)(0 * 3 + dx + 1) * n + i], above[(size_t)(i + dx) * q + E], cv);
+            } else if (r == E + t) {  // +C^l_{n+1,n} w^{l+1}_0 ; w^{l+1}_0 = row E-1 of layer l+1
+                for (int dx = -1; dx <= 1; ++dx)
+                    if (i + dx >= 0 && i + dx < n)
+                        cv = cfma(c0[(size_t)(1 * 3 + dx + 1) * n + i], above[(size_t)(i + dx) * q + E - 1], cv);
             }
-            cv = ccast<C>(val);
         }
         rhs[e] = cv;
         sol[e] = cv;
@@ -354,22 +352,21 @@ __global__ void k_inject_up(StripGeom g, const cpx_t<T>* __restrict__ inj, int l
     trace_self += b * TB;
     const int i = o >> 1, r = (o & 1) ? E : E - 1;
     const size_t e = (size_t)i * q + r;
-    double2 val = ccast<double2>(rhs[e]);
+    C val = rhs[e];   // the injection in the strip's precision
     const C* c0 = inj + (size_t)l * 12 * n;  // slots 2, 3 of layer l: [slot][dx+1][i]
     if (r == E) {  // -C^l_{1,0} (v^{l-1}_n - w^l_0) ; v^{l-1}_n = row E+t-1 of layer l-1
         for (int dx = -1; dx <= 1; ++dx) {
             if (i + dx < 0 || i + dx >= n) continue;
-            const double2 p0 = ccast<double2>(below[(size_t)(i + dx) * q + E + t - 1]) - ccast<double2>(trace_self[i + dx]);
-            val = cfms(ccast<double2>(c0[(size_t)(2 * 3 + dx + 1) * n + i]), p0, val);
+            const C p0 = below[(size_t)(i + dx) * q + E + t - 1] - trace_self[i + dx];
+            val = cfms(c0[(size_t)(2 * 3 + dx + 1) * n + i], p0, val);
         }
     } else {  // +C^l_{0,1} v^{l-1}_{n+1} ; v^{l-1}_{n+1} = row E+t of layer l-1
         for (int dx = -1; dx <= 1; ++dx) {
             if (i + dx < 0 || i + dx >= n) continue;
-            val = cfma(ccast<double2>(c0[(size_t)(3 * 3 + dx + 1) * n + i]),
-                       ccast<double2>(below[(size_t)(i + dx) * q + E + t]), val);
+            val = cfma(c0[(size_t)(3 * 3 + dx + 1) * n + i], below[(size_t)(i + dx) * q + E + t], val);
         }
     }
-    sol[e] = ccast<C>(val);
+    sol[e] = val;
 }
 
 // v = rows 1..n of every layer's solution (concatenation); batch member b = blockIdx.y
@@ -529,10 +526,10 @@ int sweep_impl(ls_handle* h, int dir, const double2* g, double2* v, int nb) {
     C* trc = static_cast<C*>(W.strace);
     const DirFactors& F = h->fac[dir];
     const StripGeom geo = geom_of(h);
-    const dim3 gg((unsigned)((n + kGatherTile - 1) / kGatherTile), nb);
-    const size_t gsm = sizeof(C) * (size_t)h->t * (kGatherTile + 1);
+    const dim3 gg((unsigned)((n + kGatherTile - 1) / kGatherTile), (unsigned)((q + kGatherTile - 1) / kGatherTile), nb);
+    const dim3 gb(kGatherTile, 8);
     for (int l = L - 1; l >= 0; --l) {  // downward sweep
-        LS_LAUNCH(h, k_gather<T>, gg, 256, gsm, geo, static_cast<const C*>(F.cinj), l, g, rhs + l * sstride,
+        LS_LAUNCH(h, k_gather<T>, gg, gb, 0, geo, static_cast<const C*>(F.cinj), l, g, rhs + l * sstride,
                   sol + l * sstride, l < L - 1 ? sol + (l + 1) * sstride : (const C*)nullptr,
                   l < L - 1 ? trc + (size_t)(l + 1) * n : (C*)nullptr, SB, TB);
         LS_TRY(cr_solve<T>(h, dir, l, sol + l * sstride, SB, nb));

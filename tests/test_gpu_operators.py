@@ -128,6 +128,25 @@ def test_fp32_apply_every_tile_shape(n, L):
     s.close()
 
 
+def test_integer_pipe_conversions_match_the_hardware():
+    # doubles spread over and beyond the float range (subnormal results, overflow), exact
+    # halfway cases of the rounding, signed zeros, infinities, NaN; floats of every class
+    rng = np.random.default_rng(7)
+    cnt = 1 << 21
+    e = rng.integers(1023 - 160, 1023 + 140, cnt).astype(np.uint64)
+    mant = rng.integers(0, 1 << 52, cnt, dtype=np.uint64)
+    mant[: cnt // 4] = (mant[: cnt // 4] & ~np.uint64((1 << 29) - 1)) | np.uint64(1 << 28)   # halfway
+    sign = rng.integers(0, 2, cnt).astype(np.uint64) << np.uint64(63)
+    dbits = sign | (e << np.uint64(52)) | mant
+    dbits[:8] = np.array([0, 1 << 63, 0x7FF0000000000000, 0xFFF0000000000000, 0x7FF8000000000001, 1,
+                          0x47EFFFFFE0000000, 0x47EFFFFFF0000000], dtype=np.uint64)
+    fbits = rng.integers(0, 1 << 32, cnt, dtype=np.uint64).astype(np.uint32)
+    fbits[:6] = np.array([0, 0x80000000, 1, 0x7FFFFF, 0x7F800000, 0x7FC00001], dtype=np.uint32)
+    d = torch.from_numpy(dbits.view(np.float64)).cuda()
+    f = torch.from_numpy(fbits.view(np.float32)).cuda()
+    assert binding.check_conversions(d, f) == 0
+
+
 def test_axpby_forms_the_residual_on_the_device():
     n = 48
     w = inputs.omega_for_ppw(n, 8.0)
