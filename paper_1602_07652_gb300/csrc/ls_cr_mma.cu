@@ -14,30 +14,29 @@
 // a dense contraction, done as a real GEMM with M = 128 rows (q <= 112 real ones),
 // N = 2 NB, K = 2 q per matrix:
 //   [D_re | D_im] += M_re [X_re | X_im] + M_im [-X_im | X_re].
-// Operand A is a factor matrix: each plane (re, im) stored row-major in TF32
-// (rounded to nearest once, when factored), streamed from HBM by TMA
-// (cp.async.bulk.tensor, 128-byte swizzle, rows beyond q zero-filled) through a
-// ring of shared-memory stages; each matrix byte is read once per step for the
+// Operand A is a factor matrix: each plane (re, im) stored in TF32 (rounded to
+// nearest once, when factored) already in the tensor cores' 128-byte-swizzled
+// K-major layout -- ceil(q/32) atoms of 32 K-columns x (q rounded up to 8) rows --
+// so a plane is one contiguous bulk copy (cp.async.bulk) from HBM into a ring of
+// plane-sized shared-memory stages; each matrix byte is read once per step for the
 // whole batch.  Operand B is built by the CTA's threads from the vectors (the
 // sign of the step folded in, rounded to TF32): per vector three planes of NB
 // rows [-X_im; X_re; X_im], so that rows [NB, 3NB) are [X_re; X_im] and rows
 // [0, 2NB) are [-X_im; X_re].  One thread issues tcgen05.mma (kind::tf32, K = 8
-// per instruction) into a TMEM accumulator of 128 lanes x 2NB FP32 columns; the
-// epilogue reads it back with tcgen05.ld and writes (or adds to) x_j.
-// Roles in a CTA of 256 threads: thread 0 loads A stages (TMA), thread 32 issues
+// per instruction; K slices past q, all zero, skipped) into a TMEM accumulator of
+// 128 lanes x 2NB FP32 columns; the epilogue reads it back with tcgen05.ld and
+// writes (or adds to) x_j.
+// Roles in a CTA of 256 threads: thread 0 loads A planes (bulk copies), thread 32 issues
 // the MMAs, everyone builds B and runs the epilogue.  Every wait is bounded (1 s
 // on %globaltimer); on expiry the step's outputs become NaN and a device counter
 // (ls_device_timeouts) is raised, so every residual check rejects the result.
-#include <cuda.h>
-#include <cudaTypedefs.h>
-
 #include <mutex>
 
 #include "ls_internal.cuh"
 
 namespace {
 
-__device__ unsigned g_cr_timeouts;   // steps whose TMA loads or MMAs did not complete in time
+__device__ unsigned g_cr_timeouts;   // steps whose copies or MMAs did not complete in time
 
 constexpr int kThreads = 256;
 constexpr unsigned long long kWaitNs = 1000000000ull;
@@ -98,13 +97,14 @@ __device__ __forceinline__ void mma_commit(unsigned long long* bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(su32(bar))
                  : "memory");
 }
-__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int x, int y, int z,
-                                            unsigned long long* bar) {
-    asm volatile(
-        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
-        "[%5];\n" ::"r"(su32(dst)),
-        "l"(reinterpret_cast<unsigned long long>(map)), "r"(x), "r"(y), "r"(z), "r"(su32(bar))
-        : "memory");
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, unsigned bytes, unsigned long long* bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+                     su32(dst)),
+                 "l"(src), "r"(bytes), "r"(su32(bar))
+                 : "memory");
+}
+__host__ __device__ __forceinline__ unsigned swz(int row, int kc) {   // byte offset in a 128-byte-swizzled atom
+    return (unsigned)row * 128u + (unsigned)(((kc >> 2) ^ (row & 7)) << 4) + (unsigned)(kc & 3) * 4u;
 }
 // 8 consecutive FP32 columns of this warp's 32 TMEM lanes
 __device__ __forceinline__ void tmem_ld8(unsigned taddr, float* v) {
@@ -122,35 +122,39 @@ template <int MODE> struct ModeOf {
     static constexpr bool ADD = MODE == 1 || MODE == 4;              // x_j += D instead of x_j = D
 };
 
-// Shared memory of one CTA: A ring (S stages of ROWS x 128 B; the MMA reads 128 rows
-// from a stage's start, so the ring is followed by 128 - ROWS rows of slack, and rows
-// past the box land on the next stage: garbage rows of D that are never read) |
-// B (NV vectors x KA atoms x 3NB rows x 128 B) | barriers (full[S], empty[S], done) |
-// TMEM address | failure flag.  S: as many stages as the atoms of a step need, within
-// 110 KB for one-matrix steps (two CTAs per SM) and 225 KB otherwise.
+// Shared memory of one CTA: A ring (S stages of one factor plane each: KA atoms of
+// BR x 128 bytes; the MMA reads 128 rows from an atom's start, so the ring is followed
+// by (128 - BR) rows of slack, and rows past an atom land on the next one: garbage rows
+// of D that are never read) | B (NV vectors x KA atoms x 3NB rows x 128 B) | barriers
+// (full[S], empty[S], done) | TMEM address | failure flag.  S: as many stages as the
+// step's planes, within 110 KB for one-matrix steps (two CTAs per SM) and 225 KB
+// otherwise.
+constexpr int kMaxStages = 6;
 template <int MODE, int NB, int KA>
 struct Cfg {
     static constexpr int NV = ModeOf<MODE>::NV;
-    static constexpr int ROWS = 32 * KA < 128 ? 32 * KA : 128;
-    static constexpr int STAGE = ROWS * 128;
-    static constexpr int SLACK = 128 * 128 - STAGE;
     static constexpr int BBYTES = NV * KA * 3 * NB * 128;
-    static constexpr int NAT = NV * 2 * KA;
-    static constexpr int BUDGET = (NV == 1 ? 110 : 225) * 1024 - BBYTES - SLACK - 1024 - 256;
-    static constexpr int FIT = BUDGET / STAGE;
-    static constexpr int S = NAT < FIT ? (NAT < 12 ? NAT : 12) : (FIT < 12 ? FIT : 12);
-    static_assert(S >= 2, "shared memory too small for two A stages");
-    static constexpr size_t SMEM = 1024 + (size_t)S * STAGE + SLACK + BBYTES + 8 * (2 * S + 1) + 16;
+    static constexpr int NP = 2 * NV;   // planes per step
+    static constexpr int BUDGET = (NV == 1 ? 110 : 225) * 1024 - BBYTES - 1024 - 8 * (2 * kMaxStages + 1) - 16;
+    static int plane_bytes(int q) { return KA * ((q + 7) / 8 * 8) * 128; }
+    static int slack(int q) { return (128 - (q + 7) / 8 * 8) * 128; }
+    static int stages(int q) {
+        const int fit = (BUDGET - slack(q)) / plane_bytes(q);
+        return fit < NP ? (fit < kMaxStages ? fit : kMaxStages) : (NP < kMaxStages ? NP : kMaxStages);
+    }
+    static size_t smem(int q) {
+        return 1024 + (size_t)stages(q) * plane_bytes(q) + slack(q) + BBYTES + 8 * (2 * kMaxStages + 1) + 16;
+    }
+    // bound of smem(q) over every q (stages x plane + slack never exceeds BUDGET)
+    static constexpr size_t kMaxSmem = 1024 + (size_t)BUDGET + BBYTES + 8 * (2 * kMaxStages + 1) + 16;
 };
-template <int MODE, int NB, int KA>
-constexpr size_t tc_smem() {
-    return Cfg<MODE, NB, KA>::SMEM;
-}
 
 struct StepArgs {
     int q, k, nk;             // strip height, level, blocks at this level
     size_t mat0;              // first matrix of this strip in the direction's pool (matrix index)
     size_t off_a, off_b, off_c;  // level offsets (matrices) of the step's 1st, 2nd, 3rd matrix
+    const float* pool;        // TF32 planes, pre-swizzled: [matrix][plane][KA atoms][BR rows][32]
+    int stages;               // A ring stages (Cfg::stages(q))
     float2* x;                // strip vectors of batch member 0 (block layout); member b at + b * SB
     size_t SB;
     int nb;                   // members present (<= NB)
@@ -159,7 +163,7 @@ struct StepArgs {
 };
 
 template <int MODE, int NB, int KA>
-__global__ void __launch_bounds__(kThreads, 1) k_cr_mma(const __grid_constant__ CUtensorMap amap, StepArgs a) {
+__global__ void __launch_bounds__(kThreads, 1) k_cr_mma(StepArgs a) {
     using MO = ModeOf<MODE>;
     constexpr int NV = MO::NV;
     constexpr int KP = 32 * KA;                   // padded K of one plane
@@ -167,19 +171,21 @@ __global__ void __launch_bounds__(kThreads, 1) k_cr_mma(const __grid_constant__ 
     constexpr unsigned BATOM = BROWS * 128;       // bytes of one vector's B atom
     constexpr int NCOL = 2 * NB;                  // accumulator columns
     constexpr int TCOLS = NCOL <= 32 ? 32 : (NCOL <= 64 ? 64 : 128);
-    using CF = Cfg<MODE, NB, KA>;
-    constexpr int kStages = CF::S, kStageBytes = CF::STAGE;
+    const int q = a.q;
+    const int BR = (q + 7) / 8 * 8;
+    const int kStages = a.stages;
+    const unsigned kPlane = (unsigned)KA * (unsigned)BR * 128u;
     extern __shared__ unsigned char smem_raw[];
     unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     unsigned char* As = base;
-    unsigned char* Bs = As + kStages * kStageBytes + CF::SLACK;
+    unsigned char* Bs = As + (size_t)kStages * kPlane + (size_t)(128 - BR) * 128;
     auto* full = reinterpret_cast<unsigned long long*>(Bs + (size_t)NV * KA * BATOM);
-    auto* empty = full + kStages;
-    auto* done = empty + kStages;
+    auto* empty = full + kMaxStages;
+    auto* done = empty + kMaxStages;
     unsigned* tslot = reinterpret_cast<unsigned*>(done + 1);
     int* failed = reinterpret_cast<int*>(tslot + 1);
 
-    const int q = a.q, tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int idx = blockIdx.x;
     const size_t s = (size_t)1 << a.k;
     const int j = (MODE == 1) ? 2 * idx : (MODE == 3 ? 0 : 2 * idx + 1);
@@ -193,17 +199,17 @@ __global__ void __launch_bounds__(kThreads, 1) k_cr_mma(const __grid_constant__ 
         pres[0] = true; blk[0] = (long long)j * s; sgn[0] = 1.f; mat[0] = a.mat0 + a.off_a + idx;
     }
     if (MODE == 1) {
-        pres[0] = hw; blk[0] = (long long)(j - 1) * s; sgn[0] = -1.f; mat[0] = a.mat0 + a.off_b + idx;
+        pres[0] = hw; blk[0] = (long long)(j - 1) * (long long)s; sgn[0] = -1.f; mat[0] = a.mat0 + a.off_b + idx;
         pres[1] = he; blk[1] = (long long)(j + 1) * s; sgn[1] = -1.f; mat[1] = a.mat0 + a.off_c + idx;
     }
     if (MODE == 2) {
         pres[0] = true; blk[0] = (long long)j * s; sgn[0] = 1.f; mat[0] = a.mat0 + a.off_a + idx;
-        pres[1] = true; blk[1] = (long long)(j - 1) * s; sgn[1] = -1.f; mat[1] = a.mat0 + a.off_b + idx;
+        pres[1] = true; blk[1] = (long long)(j - 1) * (long long)s; sgn[1] = -1.f; mat[1] = a.mat0 + a.off_b + idx;
         pres[2] = he; blk[2] = (long long)(j + 1) * s; sgn[2] = -1.f; mat[2] = a.mat0 + a.off_c + idx;
     }
-    int nat = 0;   // A atoms to stream: present vectors x 2 planes x KA
+    int npl = 0;   // A planes to stream: present vectors x 2
 #pragma unroll
-    for (int t = 0; t < NV; ++t) nat += pres[t] ? 2 * KA : 0;
+    for (int t = 0; t < NV; ++t) npl += pres[t] ? 2 : 0;
 
     if (tid == 0) {
         *failed = 0;
@@ -226,25 +232,20 @@ __global__ void __launch_bounds__(kThreads, 1) k_cr_mma(const __grid_constant__ 
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
     const unsigned tmem = *tslot;
 
-    // producer: the first min(nat, kStages) A stages start streaming before B is built
-    auto atom_coords = [&](int i, int& x, int& z) {
+    // producer: the first min(npl, kStages) planes start streaming before B is built
+    auto plane_src = [&](int i) {   // i-th present plane: (vector slot, re/im)
         int t = 0, r = i;
-        while (!pres[t] || r >= 2 * KA) {
-            if (pres[t]) r -= 2 * KA;
+        while (!pres[t] || r >= 2) {
+            if (pres[t]) r -= 2;
             ++t;
         }
-        const int p = r / KA, at = r % KA;
-        x = 32 * at;
-        z = (int)(2 * mat[t] + p);
+        return a.pool + (2 * mat[t] + r) * (size_t)KA * BR * 32;
     };
-    const unsigned abytes = 128u * (unsigned)((q + 7) / 8 * 8 < 128 ? (q + 7) / 8 * 8 : 128);
     if (tid == 0) {
-        for (int i = 0; i < nat && i < kStages; ++i) {
-            int x, z;
-            atom_coords(i, x, z);
-            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(su32(&full[i])), "r"(abytes)
+        for (int i = 0; i < npl && i < kStages; ++i) {
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(su32(&full[i])), "r"(kPlane)
                          : "memory");
-            tma_load_3d(As + i * kStageBytes, &amap, x, 0, z, &full[i]);
+            bulk_load(As + (size_t)i * kPlane, plane_src(i), kPlane, &full[i]);
         }
     }
 
@@ -257,25 +258,47 @@ __global__ void __launch_bounds__(kThreads, 1) k_cr_mma(const __grid_constant__ 
 #pragma unroll
         for (int u = 0; u < PER; ++u) {
             const int o = tid + u * kThreads, b = o / KP, kk = o % KP;
+            const bool live = pres[t] && b < a.nb && kk < q;
             float2 v = make_float2(0.f, 0.f);
-            if (pres[t] && b < a.nb && kk < q) {
-                const float2* xb = a.x + (size_t)b * a.SB;
-                if (MODE == 4) {   // t = -(W x_{j-1} + E x_{j+1}), tridiagonal couplings
+            if constexpr (MODE == 4) {
+                // t = -(W x_{j-1} + E x_{j+1}) with the tridiagonal couplings; a warp holds 32
+                // consecutive rows kk of one member (KP is a multiple of 32), so the rows
+                // kk -+ 1 come from the neighbour lanes (shuffles), loads only at the warp's ends
+                const float2* xb = a.x + (size_t)(b < a.nb ? b : 0) * a.SB;
+                const float2 z2 = make_float2(0.f, 0.f);
+                const float2 xm = live ? xb[(size_t)(j - 1) * q + kk] : z2;
+                const float2 xp = (live && he) ? xb[(size_t)(j + 1) * q + kk] : z2;
+                float2 xml, xmr, xpl, xpr;
+                xml.x = __shfl_up_sync(0xffffffffu, xm.x, 1); xml.y = __shfl_up_sync(0xffffffffu, xm.y, 1);
+                xpl.x = __shfl_up_sync(0xffffffffu, xp.x, 1); xpl.y = __shfl_up_sync(0xffffffffu, xp.y, 1);
+                xmr.x = __shfl_down_sync(0xffffffffu, xm.x, 1); xmr.y = __shfl_down_sync(0xffffffffu, xm.y, 1);
+                xpr.x = __shfl_down_sync(0xffffffffu, xp.x, 1); xpr.y = __shfl_down_sync(0xffffffffu, xp.y, 1);
+                if (lane == 0) {
+                    xml = (live && kk >= 1) ? xb[(size_t)(j - 1) * q + kk - 1] : z2;
+                    xpl = (live && he && kk >= 1) ? xb[(size_t)(j + 1) * q + kk - 1] : z2;
+                }
+                if (lane == 31) {
+                    xmr = (live && kk + 1 < q) ? xb[(size_t)(j - 1) * q + kk + 1] : z2;
+                    xpr = (live && he && kk + 1 < q) ? xb[(size_t)(j + 1) * q + kk + 1] : z2;
+                }
+                if (live) {
                     const float2* wj = a.cw + (size_t)j * 3 * q;
                     const float2* ej = a.ce + (size_t)j * 3 * q;
-                    float2 acc = make_float2(0.f, 0.f);
-#pragma unroll
-                    for (int dz = -1; dz <= 1; ++dz) {
-                        const int rr = kk + dz;
-                        if (rr < 0 || rr >= q) continue;
-                        acc = cfma(__ldg(&wj[(dz + 1) * q + kk]), xb[(size_t)(j - 1) * q + rr], acc);
-                        if (he) acc = cfma(__ldg(&ej[(dz + 1) * q + kk]), xb[(size_t)(j + 1) * q + rr], acc);
+                    // row kk - 1 / kk + 1 outside the strip: its value is zero (loads above)
+                    float2 acc = cfma(__ldg(&wj[kk]), kk >= 1 ? xml : z2, z2);
+                    acc = cfma(__ldg(&wj[q + kk]), xm, acc);
+                    acc = cfma(__ldg(&wj[2 * q + kk]), kk + 1 < q ? xmr : z2, acc);
+                    if (he) {
+                        acc = cfma(__ldg(&ej[kk]), kk >= 1 ? xpl : z2, acc);
+                        acc = cfma(__ldg(&ej[q + kk]), xp, acc);
+                        acc = cfma(__ldg(&ej[2 * q + kk]), kk + 1 < q ? xpr : z2, acc);
                     }
                     v = make_float2(-acc.x, -acc.y);
-                } else {
-                    v = xb[(size_t)blk[t] * q + kk];
-                    v = make_float2(sgn[t] * v.x, sgn[t] * v.y);
                 }
+            } else if (live) {
+                const float2* xb = a.x + (size_t)b * a.SB;
+                v = xb[(size_t)blk[t] * q + kk];
+                v = make_float2(sgn[t] * v.x, sgn[t] * v.y);
             }
             val[t][u] = v;
         }
@@ -305,44 +328,45 @@ __global__ void __launch_bounds__(kThreads, 1) k_cr_mma(const __grid_constant__ 
     if (tid == 32) {   // MMA issuer
         asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
         constexpr unsigned ID = idesc_tf32(128, NCOL);
-        int i = 0;
+        int i = 0, issued = 0;
         bool ok = true;
         for (int t = 0; t < NV && ok; ++t) {
             if (!pres[t]) continue;
             const unsigned bt = su32(Bs + (size_t)t * KA * BATOM);
-            for (int p = 0; p < 2 && ok; ++p)
-                for (int at = 0; at < KA; ++at, ++i) {
-                    const int st = i % kStages;
-                    if (!bar_wait(&full[st], (unsigned)(i / kStages) & 1u)) {
-                        ok = false;
-                        break;
-                    }
-                    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-                    const unsigned aaddr = su32(As + st * kStageBytes);
+            for (int p = 0; p < 2; ++p, ++i) {
+                const int st = i % kStages;
+                if (!bar_wait(&full[st], (unsigned)(i / kStages) & 1u)) {
+                    ok = false;
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+                const unsigned pa = su32(As + (size_t)st * kPlane);
+                for (int at = 0; at < KA; ++at) {
+                    const unsigned aaddr = pa + (unsigned)at * (unsigned)BR * 128u;
                     // plane re: B rows [NB, 3NB) = [X_re; X_im]; plane im: rows [0, 2NB) = [-X_im; X_re]
                     const unsigned baddr = bt + (unsigned)at * BATOM + (p == 0 ? (unsigned)NB * 128u : 0u);
-#pragma unroll
-                    for (int k8 = 0; k8 < 4; ++k8)
-                        mma_tf32(tmem, sdesc(aaddr + 32u * k8), sdesc(baddr + 32u * k8), ID, (i | k8) ? 1u : 0u);
-                    mma_commit(&empty[st]);   // the stage is free once these MMAs have read it
+                    const int kleft = q - 32 * at;   // K slices of 8 beyond q are zero: skipped
+                    const int nk8 = kleft >= 32 ? 4 : (kleft + 7) / 8;
+                    for (int k8 = 0; k8 < nk8; ++k8, ++issued)
+                        mma_tf32(tmem, sdesc(aaddr + 32u * k8), sdesc(baddr + 32u * k8), ID, issued ? 1u : 0u);
                 }
+                mma_commit(&empty[st]);   // the stage is free once these MMAs have read it
+            }
         }
         if (!ok) atomicOr(failed, 1);
         mma_commit(done);   // every MMA issued above has completed
     }
     if (tid == 0) {   // producer: refill each stage once the MMAs of its previous use are done
-        for (int i = kStages; i < nat; ++i) {
+        for (int i = kStages; i < npl; ++i) {
             const int st = i % kStages;
             if (!bar_wait(&empty[st], (unsigned)(i / kStages - 1) & 1u)) {
                 atomicOr(failed, 2);
                 break;
             }
-            int x, z;
-            atom_coords(i, x, z);
             asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(su32(&full[st])),
-                         "r"(abytes)
+                         "r"(kPlane)
                          : "memory");
-            tma_load_3d(As + st * kStageBytes, &amap, x, 0, z, &full[st]);
+            bulk_load(As + (size_t)st * kPlane, plane_src(i), kPlane, &full[st]);
         }
     }
     // epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31 (rows r), columns split between w and w + 4
@@ -396,36 +420,33 @@ __global__ void __launch_bounds__(kThreads, 1) k_cr_mma(const __grid_constant__ 
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(TCOLS) : "memory");
 }
 
-PFN_cuTensorMapEncodeTiled_v12000 encoder() {
-    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-    static std::once_flag once;
-    std::call_once(once, [] {
-        void* p = nullptr;
-        cudaDriverEntryPointQueryResult qr{};
-        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &qr) ==
-                cudaSuccess &&
-            qr == cudaDriverEntryPointSuccess)
-            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
-    });
-    return fn;
-}
-
-// column-major complex q x q (FP64) -> two row-major TF32 planes of q rows x ld
-__global__ void k_pack_tc(size_t nmat, int q, int ld, const float2* __restrict__ src, float* __restrict__ dst) {
-    const size_t per = (size_t)q * q;
+// column-major complex q x q (FP32) -> two TF32 planes per matrix in the 128-byte-swizzled
+// K-major layout of the tensor cores: [plane][KA atoms][BR rows][32 K-columns], zeros
+// beyond q (rows and K)
+__global__ void k_pack_tc(size_t nmat, int q, int KA, int BR, const float2* __restrict__ src, float* __restrict__ dst) {
+    const size_t per = (size_t)2 * KA * BR * 32;   // floats per matrix
     for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < nmat * per; e += (size_t)gridDim.x * blockDim.x) {
         const size_t mi = e / per;
-        const int rc = (int)(e % per), c = rc / q, r = rc % q;   // source element (r, c) at c q + r
-        const float2 v = src[e];
-        float* d = dst + mi * 2 * (size_t)q * ld;
-        d[(size_t)r * ld + c] = tf32_rna(v.x);
-        d[(size_t)q * ld + (size_t)r * ld + c] = tf32_rna(v.y);
+        size_t rem = e % per;
+        const int pl = (int)(rem / ((size_t)KA * BR * 32));
+        rem %= (size_t)KA * BR * 32;
+        const int at = (int)(rem / ((size_t)BR * 32));
+        rem %= (size_t)BR * 32;
+        const int row = (int)(rem / 32), kc = (int)(rem % 32);
+        const int c = 32 * at + kc;   // K index = column of M
+        float v = 0.f;
+        if (row < q && c < q) {
+            const float2 m = src[mi * (size_t)q * q + (size_t)c * q + row];
+            v = tf32_rna(pl == 0 ? m.x : m.y);
+        }
+        float* atom = dst + mi * per + ((size_t)pl * KA + at) * BR * 32;   // (row, kc) at its swizzled offset
+        atom[swz(row, kc) / 4] = v;
     }
 }
 
 template <int MODE, int NB, int KA>
 int set_smem() {
-    const size_t sz = tc_smem<MODE, NB, KA>();
+    const size_t sz = Cfg<MODE, NB, KA>::kMaxSmem;
     LS_CUDA(cudaFuncSetAttribute(k_cr_mma<MODE, NB, KA>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sz));
     return LS_OK;
 }
@@ -441,60 +462,51 @@ int set_smem_all() {
 }
 
 template <int MODE, int NB, int KA>
-int launch(ls_handle* h, const CUtensorMap* map, unsigned grid, const StepArgs& a) {
-    LS_LAUNCH(h, (k_cr_mma<MODE, NB, KA>), grid, kThreads, (tc_smem<MODE, NB, KA>()), *map, a);
+int launch(ls_handle* h, unsigned grid, StepArgs a) {
+    using CF = Cfg<MODE, NB, KA>;
+    a.stages = CF::stages(a.q);
+    if (a.stages < 1) return LS_EINVAL;
+    LS_LAUNCH(h, (k_cr_mma<MODE, NB, KA>), grid, kThreads, CF::smem(a.q), a);
     return LS_OK;
 }
 
 template <int NB, int KA>
-int launch_mode(ls_handle* h, int mode, const CUtensorMap* map, unsigned grid, const StepArgs& a) {
+int launch_mode(ls_handle* h, int mode, unsigned grid, const StepArgs& a) {
     switch (mode) {
-        case 0: return launch<0, NB, KA>(h, map, grid, a);
-        case 1: return launch<1, NB, KA>(h, map, grid, a);
-        case 2: return launch<2, NB, KA>(h, map, grid, a);
-        case 3: return launch<3, NB, KA>(h, map, grid, a);
-        default: return launch<4, NB, KA>(h, map, grid, a);
+        case 0: return launch<0, NB, KA>(h, grid, a);
+        case 1: return launch<1, NB, KA>(h, grid, a);
+        case 2: return launch<2, NB, KA>(h, grid, a);
+        case 3: return launch<3, NB, KA>(h, grid, a);
+        default: return launch<4, NB, KA>(h, grid, a);
     }
 }
 
 template <int NB>
-int launch_ka(ls_handle* h, int mode, const CUtensorMap* map, unsigned grid, const StepArgs& a) {
+int launch_ka(ls_handle* h, int mode, unsigned grid, const StepArgs& a) {
     switch ((a.q + 31) / 32) {
-        case 1: return launch_mode<NB, 1>(h, mode, map, grid, a);
-        case 2: return launch_mode<NB, 2>(h, mode, map, grid, a);
-        case 3: return launch_mode<NB, 3>(h, mode, map, grid, a);
-        default: return launch_mode<NB, 4>(h, mode, map, grid, a);
+        case 1: return launch_mode<NB, 1>(h, mode, grid, a);
+        case 2: return launch_mode<NB, 2>(h, mode, grid, a);
+        case 3: return launch_mode<NB, 3>(h, mode, grid, a);
+        default: return launch_mode<NB, 4>(h, mode, grid, a);
     }
 }
 
 }  // namespace
 
-// The TF32 planes of both directions' factors and their tensor maps (after ls_factor,
-// LS_MIXED).  One map per direction covers all its matrices: dims (K = q, rows = q,
-// plane = 2 x matrices), boxes of 32 x round8(q) x 1 with the 128-byte swizzle.
+// The TF32 planes of both directions' factors (after ls_factor, LS_MIXED): per matrix
+// two planes of KA = ceil(q/32) atoms of BR = q rounded up to 8 rows x 32 K-columns,
+// already in the tensor cores' swizzled layout.
 int ls_cr_tc_prepare(ls_handle* h) {
     if (h->prec != LS_MIXED || h->q > 112) return LS_OK;
-    auto enc = encoder();
-    if (!enc) return LS_OK;   // no TMA encoder: the CUDA-core steps stay in use
-    const int q = h->q, ld = (q + 3) / 4 * 4;
+    const int q = h->q, KA = (q + 31) / 32, BR = (q + 7) / 8 * 8;
     for (int d = 0; d < 2; ++d) {
         DirFactors& F = h->fac[d];
         if (!F.pool32) return LS_ESTATE;
         const size_t nmat = F.mats_per_strip * (size_t)h->L;
         cudaFree(F.pool_tc);
         F.pool_tc = nullptr;
-        LS_CUDA(cudaMalloc(&F.pool_tc, sizeof(float) * 2 * (size_t)q * ld * nmat));
-        LS_LAUNCH(h, k_pack_tc, 1216, 256, 0, nmat, q, ld, F.pool32, F.pool_tc);
-        const cuuint64_t dims[3] = {(cuuint64_t)q, (cuuint64_t)q, (cuuint64_t)(2 * nmat)};
-        const cuuint64_t strides[2] = {(cuuint64_t)ld * sizeof(float), (cuuint64_t)q * ld * sizeof(float)};
-        const int boxr = (q + 7) / 8 * 8;
-        const cuuint32_t box[3] = {32, (cuuint32_t)boxr, 1};
-        const cuuint32_t estr[3] = {1, 1, 1};
-        CUtensorMap* map = reinterpret_cast<CUtensorMap*>(F.tc_map);
-        if (enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, F.pool_tc, dims, strides, box, estr,
-                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
-            return LS_ECUDA;
+        LS_CUDA(cudaMalloc(&F.pool_tc, sizeof(float) * 2 * (size_t)KA * BR * 32 * nmat));
+        LS_LAUNCH(h, k_pack_tc, 1216, 256, 0, nmat, q, KA, BR, F.pool32, F.pool_tc);
     }
     static std::once_flag once;
     static int rc = LS_OK;
@@ -537,10 +549,9 @@ int ls_cr_tc_timeouts(unsigned* count) {
 int ls_cr_tc_step(ls_handle* h, int dir, int l, int mode, int k, int nk, unsigned grid, size_t off_a, size_t off_b,
                   size_t off_c, float2* x, size_t SB, int nb, const float2* cw, const float2* ce) {
     const DirFactors& F = h->fac[dir];
-    StepArgs a{h->q, k, nk, (size_t)l * F.mats_per_strip, off_a, off_b, off_c, x, SB, nb, cw, ce};
-    const CUtensorMap* map = reinterpret_cast<const CUtensorMap*>(F.tc_map);
-    if (nb <= 8) return launch_ka<8>(h, mode, map, grid, a);
-    if (nb <= 16) return launch_ka<16>(h, mode, map, grid, a);
-    if (nb <= 32) return launch_ka<32>(h, mode, map, grid, a);
+    StepArgs a{h->q, k, nk, (size_t)l * F.mats_per_strip, off_a, off_b, off_c, F.pool_tc, 0, x, SB, nb, cw, ce};
+    if (nb <= 8) return launch_ka<8>(h, mode, grid, a);
+    if (nb <= 16) return launch_ka<16>(h, mode, grid, a);
+    if (nb <= 32) return launch_ka<32>(h, mode, grid, a);
     return LS_EINVAL;
 }

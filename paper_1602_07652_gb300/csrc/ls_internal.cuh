@@ -166,10 +166,10 @@ struct DirFactors {
     size_t mats_per_strip = 0;    // matrices per strip in the pool
     double2* pool64 = nullptr;    // L * mats_per_strip * q*q (FP64; freed in LS_MIXED)
     float2* pool32 = nullptr;     // same layout in FP32 (LS_MIXED)
-    // LS_MIXED, tensor-core steps (ls_cr_mma.cu): every matrix as two row-major TF32
-    // planes (re, im) of q rows x ld (ld = q rounded up to 4), and the TMA map over them
+    // LS_MIXED, tensor-core steps (ls_cr_mma.cu): every matrix as two TF32 planes (re, im)
+    // in the tensor cores' 128-byte-swizzled K-major layout (ceil(q/32) atoms of 32
+    // K-columns x q rounded up to 8 rows each), so a plane is one contiguous copy
     float* pool_tc = nullptr;
-    alignas(64) unsigned char tc_map[128] = {};
     // problem of this direction (the vertical direction is the transposed grid)
     const double* m = nullptr;    // medium of this direction's grid (n x n, long axis fastest)
     StencilTables* tab = nullptr; // device copy of the tables of this direction
