@@ -71,6 +71,10 @@ def parse():
                     help="uneven batch: 32 independent problems, n drawn from {256, 512, 768, 1024} at 10 ppw "
                          "(seeds 0..31), mixed precision, solved concurrently by ls_solve_group vs one by one")
     ap.add_argument("--uneven-count", type=int, default=32)
+    ap.add_argument("--c4", action="store_true",
+                    help="batched configuration: 64 plane-wave directions 2 pi j / 64 at 1024^2 (w = 2 pi 100, "
+                         "20 seeded bumps, 16 layers) solved in one ls_solve_batch call, mixed precision, tol 1e-6, "
+                         "then the uneven batch of --uneven; one JSON line")
     ap.add_argument("--learned", action="store_true",
                     help="learned preconditioner step: train the BF16 U-Net (4 levels, 32 base channels) on "
                          "residual->correction pairs of the plain solver over seeded 512^2 bump media, then solve "
@@ -757,6 +761,56 @@ def run_uneven(args):
     return 0
 
 
+def run_c4(args):
+    """The batched configuration: 64 incident directions on the circle at 1024^2 in ONE
+    ls_solve_batch call (lockstep Krylov levels, Algorithm 2 in chunks of up to 32 right-hand
+    sides on concurrent lanes, captured graphs, autotuned shapes), timed with CUDA events
+    after warm-up calls; then the uneven batch (independent problems of four sizes through
+    ls_solve_group).  One JSON line."""
+    import torch
+    from paper_1602_07652_gb300 import binding, inputs
+    binding.load()
+    n, L, B = 1024, 16, 64
+    w = 2 * math.pi * 100
+    m = inputs.bump_medium(n, nbumps=20, seed=0)
+    o = binding.default_opts()
+    o.outer_restart, o.inner_restart = 10, 10
+    t0 = time.perf_counter()
+    s = binding.Solver(torch.from_numpy(m), w, layers=L, ext=10, precision=binding.LS_MIXED, opts=o)
+    s.ls_factor()
+    torch.cuda.synchronize()
+    t_off = time.perf_counter() - t0
+    tune = s.ls_autotune(nrhs=32, reps=2)
+    f = torch.empty((B, n, n), dtype=torch.complex128, device="cuda")
+    base = inputs.seeded_angle(0)
+    for j in range(B):
+        s.ls_incident_rhs(base + 2 * math.pi * j / B, f[j])
+    u = torch.empty_like(f)
+    for _ in range(max(1, args.warmup)):
+        s.ls_solve_batch(f, TOL, u)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record(s.stream)
+    sts = []
+    for _ in range(args.steps):
+        _, st, _ = s.ls_solve_batch(f, TOL, u)
+        sts.append(st)
+    ev1.record(s.stream)
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    out = {"c4_directions": {"n": n, "omega": w, "layers": L, "rhs_per_call": B, "calls": args.steps,
+                             "ms_per_call": ms, "value": ms / 1e3 / B, "unit": "s/RHS", "tol": TOL,
+                             "outer_per_rhs": statistics.mean(st["outer_iters"] for st in sts) / B,
+                             "true_rel_residual_max": max(st["true_rel_residual"] for st in sts),
+                             "gpu_launches_per_call": statistics.mean(st["kernel_launches"] for st in sts),
+                             "offline_s": t_off, "autotune": {"fft_variant": tune["fft_variant"],
+                                                             "bd_chunk": tune["bd_chunk"],
+                                                             "tensor_steps": tune["tensor_steps"]}}}
+    s.close()
+    print(json.dumps(out), flush=True)
+    return run_uneven(args)
+
+
 def run_learned(args):
     """Train the learned step on 512^2 media (seeds 1000..), then compare solves of the
     benchmark workload (2048^2 unless --n) with and without it.  One JSON line."""
@@ -781,7 +835,7 @@ def run_learned(args):
     inf = binding.Net(levels=4, c0=32, max_batch=1, H=n, W=n, train=False)
     inf.set_params(params)
     cmp = learned.compare_solves(inf, n, seeds=[0], tol=TOL)
-    out = {"learned": "BF16 U-Net, 4 levels, c0 32, 3x3 convs, WMMA tensor cores", "train_size": 512,
+    out = {"learned": "BF16 U-Net, 4 levels, c0 32, 3x3 convs, tcgen05 tensor cores", "train_size": 512,
            "pairs": int(data[0].shape[0]), "steps": args.learned_steps, "batch": 4,
            "data_s": t_data, "train_s": t_train, "loss_first": losses[0], "loss_last": losses[-1],
            "heldout_correction_err": {"untrained": err0, "trained": err1},
@@ -820,7 +874,8 @@ def run_net_only(args):
     m = torch.from_numpy(0.1 * rng.standard_normal((nb, H, H))).cuda()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     stream = net.stream
-    out = {"component": "learned step U-Net (BF16, WMMA tensor cores)", "batch": nb, "H": H}
+    out = {"component": "learned step U-Net (BF16; forward and backward-data convolutions on tcgen05, weight "
+                        "gradients on WMMA)", "batch": nb, "H": H}
     for name, fn, mult in (("forward", lambda: net.forward(r, m), 1), ("train_step", lambda: net.train_step(r, m, e, 0.0), 3)):
         for _ in range(args.warmup):
             fn()
@@ -850,6 +905,8 @@ def main():
         return run_net_only(args)
     if args.learned:
         return run_learned(args)
+    if args.c4:
+        return run_c4(args)
     if args.uneven:
         return run_uneven(args)
     if args.table1:

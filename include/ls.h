@@ -229,7 +229,7 @@ typedef struct {
     double bd_ms_tc[4]; /* LS_MIXED: the same with the reduction steps on the tensor cores,
                            chunks 1, 8, 16, 32 (0: not tried; tried only while that form
                            is switched on, see ls_set_tensor_steps)                        */
-    int tensor_steps;   /* 1: the tensor-core steps were chosen                            */
+    int tensor_steps;   /* 1: the tensor-core steps were chosen (the handle keeps on = 2)   */
 } ls_tuning;
 int ls_autotune(ls_handle* h, int nrhs, int reps, ls_tuning* out);
 
@@ -240,14 +240,16 @@ int ls_autotune(ls_handle* h, int nrhs, int reps, ls_tuning* out);
  * rounding whichever shapes are set. */
 int ls_set_shapes(ls_handle* h, int fft_variant, int bd_chunk);
 
-/* ls_set_tensor_steps -- LS_MIXED: run the block-cyclic-reduction steps of the local
- * solves (Algorithm 1's (C^l)^{-1}, Sec. 3.4; factors of Sec. 4.1) on the tensor cores
- * (on = 1, the default after ls_factor: each step one TF32 matrix product over the
- * whole batch, factor tiles streamed by TMA, accumulators in tensor memory) or on the
- * CUDA cores in FP32 (on = 0).  The tensor-core form rounds the factors and vectors to
+/* ls_set_tensor_steps -- LS_MIXED: where the block-cyclic-reduction steps of the local
+ * solves (Algorithm 1's (C^l)^{-1}, Sec. 3.4; factors of Sec. 4.1) run: on the tensor
+ * cores (each step one TF32 matrix product over the whole batch, factor planes copied
+ * in bulk, accumulators in tensor memory) or on the CUDA cores in FP32.  on = 0: CUDA
+ * cores; 1 (the default after ls_factor): tensor cores for passes of 5 or more
+ * right-hand sides, CUDA cores below; 2: tensor cores always.  ls_autotune leaves the
+ * measured choice (0 or 2).  The tensor-core form rounds the factors and vectors to
  * TF32 (about 3 decimal digits): it changes the preconditioner by that much, never the
  * converged solution, which the FP64 residual judges.  Synchronises the stream and
- * drops the captured sweep graphs on a change.  LS_ESTATE when on = 1 and the form is
+ * drops the captured sweep graphs on a change.  LS_ESTATE when on > 0 and the form is
  * not built (LS_FP64, before ls_factor, or q > 112); LS_EINVAL for other values. */
 int ls_set_tensor_steps(ls_handle* h, int on);
 
@@ -262,8 +264,9 @@ int ls_set_reduction(ls_handle* h, int cr_split);
 /* ls_device_timeouts -- health counter of the kernels fed by TMA (the paper has no
  * counterpart of this counter): *count = how many CTAs found their copies or their
  * tensor-core products not complete within one second since the library was loaded --
- * CTAs of the LS-apply's TMA column tile shapes (6, 7, 8; Sec. 2) and of the
- * tensor-core reduction steps of the local solves (Sec. 3.4-3.5); 0 in a healthy run.
+ * CTAs of the LS-apply's TMA column tile shapes (6, 7, 8; Sec. 2), of the tensor-core
+ * reduction steps of the local solves (Sec. 3.4-3.5) and of the learned step's
+ * tensor-core convolutions; 0 in a healthy run.
  * Such a CTA writes its outputs as NaN (so the solver's residual checks reject the
  * result) and returns instead of waiting on.  Synchronous read of device counters.
  * LS_EINVAL if count is NULL. */
@@ -305,6 +308,14 @@ int ls_net_train_step(ls_net* net, int nb, int H, int W, const ls_c64* r, const 
 int ls_net_get_grads(ls_net* net, float* host, size_t count);   /* of the last training step */
 long long ls_net_kernel_count(const ls_net* net);
 void ls_net_destroy(ls_net* net);
+/* ls_net_set_tensor_cores -- where the network's forward and backward-data convolutions
+ * run (no counterpart in the paper; the network is the learned step of Sec. 6's
+ * flexible outer iteration): on = 1 (the default) on the fifth-generation tensor cores
+ * (tcgen05.mma kind::f16 on BF16 operands, FP32 accumulation in tensor memory), 0 on the
+ * WMMA path; both accumulate in FP32, so results agree to BF16 rounding of the outputs.
+ * The weight gradients use WMMA either way.  LS_EINVAL for a NULL net or other values. */
+int ls_net_set_tensor_cores(ls_net* net, int on);
+
 /* attach (net != NULL) or detach the learned step of handle h's outer iteration; the
  * network must accept the handle's n x n grid (batch 1) and outlive the attachment. */
 int ls_set_learned(ls_handle* h, ls_net* net);

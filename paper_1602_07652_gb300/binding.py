@@ -122,6 +122,7 @@ _SIGS = {
     "ls_net_kernel_count": (ctypes.c_longlong, [_P]),
     "ls_net_destroy": (None, [_P]),
     "ls_set_learned": (ctypes.c_int, [_P, _P]),
+    "ls_net_set_tensor_cores": (ctypes.c_int, [_P, ctypes.c_int]),
 }
 
 EXPORTED = tuple(_SIGS)
@@ -203,6 +204,10 @@ class Net:
             self.close()
         except Exception:
             pass
+
+    def set_tensor_cores(self, on):
+        """Forward / backward-data convolutions on tcgen05 (1, default) or WMMA (0)."""
+        _ck(self._lib.ls_net_set_tensor_cores(self._h, int(on)), "ls_net_set_tensor_cores")
 
     def param_count(self):
         return int(self._lib.ls_net_param_count(self._h))

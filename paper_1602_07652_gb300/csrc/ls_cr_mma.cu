@@ -33,89 +33,25 @@
 #include <mutex>
 
 #include "ls_internal.cuh"
+#include "ls_umma.cuh"
 
 namespace {
 
 __device__ unsigned g_cr_timeouts;   // steps whose copies or MMAs did not complete in time
 
 constexpr int kThreads = 256;
-constexpr unsigned long long kWaitNs = 1000000000ull;
 
-__device__ __forceinline__ unsigned su32(const void* p) { return static_cast<unsigned>(__cvta_generic_to_shared(p)); }
-__device__ __forceinline__ unsigned long long gtime() {
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-__device__ __forceinline__ bool bar_wait(unsigned long long* bar, unsigned parity) {
-    const unsigned long long t0 = gtime();
-    for (;;) {
-        unsigned done;
-        asm volatile(
-            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-            : "=r"(done)
-            : "r"(su32(bar)), "r"(parity)
-            : "memory");
-        if (done) return true;
-        if (gtime() - t0 > kWaitNs) return false;
-    }
-}
-__device__ __forceinline__ void bar_init(unsigned long long* bar, unsigned count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(su32(bar)), "r"(count) : "memory");
-}
+using namespace umma;
+
 __device__ __forceinline__ float tf32_rna(float x) {
     unsigned r;
     asm("cvt.rna.tf32.f32 %0, %1;\n" : "=r"(r) : "f"(x));
     return __uint_as_float(r);
 }
-
-// Shared-memory matrix descriptor of a K-major operand tile in the 128-byte swizzle
-// layout: rows of 128 bytes, 8-row groups 1024 bytes apart (stride byte offset),
-// descriptor version 1, swizzle mode 2 (128 bytes).
-__device__ __forceinline__ unsigned long long sdesc(unsigned addr) {
-    unsigned long long d = 0;
-    d |= (unsigned long long)((addr >> 4) & 0x3FFF);
-    d |= (unsigned long long)(16 >> 4) << 16;      // leading byte offset (unused when swizzled)
-    d |= (unsigned long long)(1024 >> 4) << 32;    // stride byte offset
-    d |= 1ull << 46;                                // version
-    d |= 2ull << 61;                                // 128-byte swizzle
-    return d;
+__host__ __device__ __forceinline__ unsigned swz(int row, int kc) {   // byte offset of TF32 kc in a swizzled atom
+    return swz16(row, kc >> 2) + (unsigned)(kc & 3) * 4u;
 }
-// Instruction descriptor, kind::tf32: D FP32, A and B TF32, both K-major, M x N.
-__host__ __device__ constexpr unsigned idesc_tf32(int M, int N) {
-    return (1u << 4) | (2u << 7) | (2u << 10) | ((unsigned)(N >> 3) << 17) | ((unsigned)(M >> 4) << 24);
-}
-__device__ __forceinline__ void mma_tf32(unsigned dtmem, unsigned long long a, unsigned long long b, unsigned id,
-                                         unsigned acc) {
-    asm volatile(
-        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-        " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(dtmem),
-        "l"(a), "l"(b), "r"(id), "r"(acc)
-        : "memory");
-}
-__device__ __forceinline__ void mma_commit(unsigned long long* bar) {
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(su32(bar))
-                 : "memory");
-}
-__device__ __forceinline__ void bulk_load(void* dst, const void* src, unsigned bytes, unsigned long long* bar) {
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
-                     su32(dst)),
-                 "l"(src), "r"(bytes), "r"(su32(bar))
-                 : "memory");
-}
-__host__ __device__ __forceinline__ unsigned swz(int row, int kc) {   // byte offset in a 128-byte-swizzled atom
-    return (unsigned)row * 128u + (unsigned)(((kc >> 2) ^ (row & 7)) << 4) + (unsigned)(kc & 3) * 4u;
-}
-// 8 consecutive FP32 columns of this warp's 32 TMEM lanes
-__device__ __forceinline__ void tmem_ld8(unsigned taddr, float* v) {
-    unsigned r[8];
-    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];\n"
-                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
-                 : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
-#pragma unroll
-    for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
-}
+__host__ __device__ constexpr unsigned idesc_tf32(int M, int N) { return idesc(2u, M, N); }
 
 template <int MODE> struct ModeOf {
     static constexpr int NV = MODE == 1 ? 2 : (MODE == 2 ? 3 : 1);   // vectors (= matrices) per step

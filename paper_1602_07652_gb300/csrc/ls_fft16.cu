@@ -825,9 +825,10 @@ extern "C" int ls_test_tma_shortfall(unsigned bytes) {
 
 extern "C" int ls_device_timeouts(unsigned* count) {
     if (!count) return LS_EINVAL;
-    unsigned cols = 0, steps = 0;
+    unsigned cols = 0, steps = 0, convs = 0;
     LS_CUDA(cudaMemcpyFromSymbol(&cols, g_tma_timeouts, sizeof(unsigned)));
     LS_TRY(ls_cr_tc_timeouts(&steps));
-    *count = cols + steps;
+    LS_TRY(ls_conv_timeouts(&convs));
+    *count = cols + steps + convs;
     return LS_OK;
 }

@@ -259,7 +259,8 @@ struct ls_handle {
     int bd_chunk = 0;          // right-hand sides per Algorithm 2 chain (0: the largest supported)
     int cr_split = 1;          // 1: reduction steps of small levels split blocks over several CTAs
     bool tc_ready = false;     // LS_MIXED: TF32 factor planes and tensor maps built (ls_cr_tc_prepare)
-    int cr_tc = 1;             // 1: FP32 reduction steps on the tensor cores when tc_ready
+    int cr_tc = 1;             // FP32 reduction steps on the tensor cores when tc_ready: 0 never,
+                               // 1 for batches of 5 or more right-hand sides, 2 always
 
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     double t_apply_ms = 0, t_sweep_ms = 0, t_apply64_ms = 0;
@@ -349,6 +350,7 @@ int ls_cr_tc_prepare(ls_handle* h);
 void ls_cr_tc_free(ls_handle* h);
 int ls_cr_tc_max_nb(const ls_handle* h);
 int ls_cr_tc_timeouts(unsigned* count);
+int ls_conv_timeouts(unsigned* count);   // tensor-core convolutions of the learned step (ls_unet.cu)
 int ls_cr_tc_step(ls_handle* h, int dir, int l, int mode, int k, int nk, unsigned grid, size_t off_a, size_t off_b,
                   size_t off_c, float2* x, size_t SB, int nb, const float2* cw, const float2* ce);
 

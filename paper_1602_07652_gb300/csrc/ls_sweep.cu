@@ -505,7 +505,9 @@ int cr_solve_tc(ls_handle* h, int dir, int l, float2* x, size_t SB, int nb) {
 template <typename T>
 int cr_solve(ls_handle* h, int dir, int l, cpx_t<T>* x, size_t SB, int nb) {
     if constexpr (sizeof(T) == 4) {
-        if (h->tc_ready && h->cr_tc) return cr_solve_tc(h, dir, l, x, SB, nb);
+        // tensor cores: always (cr_tc 2), or for batches past the CUDA-core steps' sweet spot
+        // (cr_tc 1: at least 5 right-hand sides; a one-matrix product per step does not fill them)
+        if (h->tc_ready && (h->cr_tc == 2 || (h->cr_tc == 1 && nb >= 5))) return cr_solve_tc(h, dir, l, x, SB, nb);
     }
     if (nb <= 1) return cr_solve_nb<T, 1>(h, dir, l, x, SB, nb);
     if (nb <= 2) return cr_solve_nb<T, 2>(h, dir, l, x, SB, nb);

@@ -84,11 +84,12 @@ extern "C" int ls_autotune(ls_handle* h, int nrhs, int reps, ls_tuning* out) {
         best = 0;
         int chunk = 1, split = 1, tc = 0;
         const int tc_avail = h->tc_ready && h->cr_tc ? 1 : 0;   // switched off by ls_set_tensor_steps: not tried
+        const int tc_user = h->cr_tc;
         for (int form = tc_avail ? 2 : 1; form >= 0 && rc == LS_OK; --form) {  // 2: tensor cores, 1: split, 0: unsplit
             const int want_tc = form == 2, sp = form == 2 ? h->cr_split : form;
-            if (h->cr_split != sp || h->cr_tc != want_tc) {
+            if (h->cr_split != sp || h->cr_tc != 2 * want_tc) {
                 h->cr_split = sp;
-                h->cr_tc = want_tc;
+                h->cr_tc = 2 * want_tc;   // measured in the pure forms
                 ls_bd_graph_free(h);  // the captured launches bake the grid shapes in
             }
             const int cap = ls_bd_cap(h);
@@ -108,10 +109,13 @@ extern "C" int ls_autotune(ls_handle* h, int nrhs, int reps, ls_tuning* out) {
                 }
             }
         }
-        if (rc != LS_OK) break;
-        if (h->cr_split != split || h->cr_tc != tc) {
+        if (rc != LS_OK) {
+            h->cr_tc = tc_user;
+            break;
+        }
+        if (h->cr_split != split || h->cr_tc != 2 * tc) {
             h->cr_split = split;
-            h->cr_tc = tc;
+            h->cr_tc = 2 * tc;
             ls_bd_graph_free(h);
         }
         h->bd_chunk = chunk;
@@ -145,7 +149,7 @@ extern "C" int ls_set_reduction(ls_handle* h, int cr_split) {
 }
 
 extern "C" int ls_set_tensor_steps(ls_handle* h, int on) {
-    if (!h || (on != 0 && on != 1)) return LS_EINVAL;
+    if (!h || on < 0 || on > 2) return LS_EINVAL;
     if (on && !h->tc_ready) return LS_ESTATE;
     if (h->cr_tc != on) {
         LS_CUDA(cudaStreamSynchronize(h->stream));

@@ -16,11 +16,14 @@
 // FP32 master copy + Adam moments; BF16 copies [cout][tap][cin] for the forward
 // convolution and [cin][8 - tap][cout] for the backward-data convolution.
 //
-// Convolutions are implicit GEMMs on the tensor cores (WMMA bf16 16x16x16,
-// FP32 accumulation): forward and backward-data with M = pixels, N = output
-// channels, K = 9 x input channels, gathering the 3x3 neighbourhood while
-// staging the A tile; backward-weights with M = output channels, N = 9 x input
-// channels, K = pixels, split over pixel chunks and reduced with FP32 atomics.
+// Convolutions are implicit GEMMs on the tensor cores with FP32 accumulation.
+// Forward and backward-data (M = pixels, N = output channels, K = 9 x input
+// channels) run on the fifth-generation tensor cores (k_conv_umma): tiles of 128
+// pixels, the 3x3 neighbourhood gathered into 128-byte-swizzled shared memory while
+// the previous K-slice's tcgen05.mma (kind::f16, BF16 operands) run, the
+// accumulator in tensor memory, bias and ReLU applied on its way out.
+// Backward-weights (M = output channels, N = 9 x input channels, K = pixels, split
+// over pixel chunks and reduced with FP32 atomics) uses WMMA bf16 16x16x16.
 #include <mma.h>
 
 #include <cmath>
@@ -30,6 +33,7 @@
 #include <vector>
 
 #include "ls_internal.cuh"
+#include "ls_umma.cuh"
 
 using bf16 = __nv_bfloat16;
 
@@ -114,6 +118,150 @@ __global__ void __launch_bounds__(kConvThreads) k_conv_fwd(ConvArgs a) {
         if (a.relu) v = fmaxf(v, 0.0f);
         a.y[(size_t)(m0 + mm) * a.ys + a.yo + n0 + nn] = __float2bfloat16(v);
     }
+}
+
+// The same convolution on the fifth-generation tensor cores: a CTA of 128 threads
+// computes 128 pixels x BN output channels (BN = cout <= 256).  K = 9 cin runs in
+// atoms of 64 (one 128-byte swizzled row per pixel or channel).  Each atom's A (the
+// gathered 3x3 neighbourhoods, 16-byte chunks of 8 channels) and B (weights
+// [cout][tap][cin], K-major) go straight from global to one of kCvStages shared-memory
+// stages by asynchronous 16-byte copies (cp.async, zero-filled outside the image),
+// kCvStages - 1 atoms ahead of the tensor cores; once an atom has landed, thread 0
+// issues its four K = 16 MMAs (kind::f16, BF16 operands) and commits them to the
+// stage's barrier, which the copies into that stage wait on.  A thread always moves
+// chunk (tid mod 8) of its 8 pixels, so their coordinates are computed once.  Waits
+// are bounded (1 s); on expiry the tile is written as NaN and the device counter
+// ls_device_timeouts counts it.
+__device__ unsigned g_conv_timeouts;
+constexpr int kCvThreads = 128, kCvStages = 4;
+template <int BN>
+constexpr size_t conv_umma_smem() {
+    return 1024 + (size_t)kCvStages * (128 * 128 + BN * 128) + 8 * (kCvStages + 1) + 16;
+}
+__device__ __forceinline__ void cp_async16_zfill(void* smem, const void* gmem, bool valid) {
+    const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(s), "l"(gmem), "r"(valid ? 16 : 0)
+                 : "memory");
+}
+template <int BN>
+__global__ void __launch_bounds__(kCvThreads) k_conv_umma(ConvArgs a) {
+    using namespace umma;
+    constexpr unsigned ABYTES = 128 * 128, BBYTES = BN * 128, STAGE = ABYTES + BBYTES;
+    constexpr int TCOLS = BN < 32 ? 32 : BN;
+    constexpr int S = kCvStages;
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    auto* sbar = reinterpret_cast<unsigned long long*>(base + S * STAGE);
+    auto* done = sbar + S;
+    unsigned* tslot = reinterpret_cast<unsigned*>(done + 1);
+    int* failed = reinterpret_cast<int*>(tslot + 1);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int m0 = blockIdx.x * 128, n0 = blockIdx.y * BN;
+    const int K = 9 * a.cin, HW = a.H * a.W, NK = (K + 63) / 64;
+    // this thread's 8 pixels (rows tid/8 + 16u, u < 8: the 128 rows of the tile, each once
+    // per chunk) and chunk c = tid % 8 of every atom
+    constexpr int RPT = 128 * 8 / kCvThreads;   // chunks (= rows) per thread: 8
+    static_assert(RPT * 16 == 128, "rows tid / 8 + 16 u cover the tile once per chunk");
+    const int c = tid & 7;
+    int pb[RPT], py[RPT], px[RPT];
+#pragma unroll
+    for (int u = 0; u < RPT; ++u) {
+        const int p = m0 + (tid >> 3) + 16 * u;
+        const int bb = p / HW, rem = p - bb * HW;
+        pb[u] = p < a.M ? bb : -1;
+        py[u] = rem / a.W;
+        px[u] = rem - py[u] * a.W;
+    }
+    if (tid == 0) {
+        *failed = 0;
+        for (int i = 0; i < S; ++i) bar_init(&sbar[i], 1);
+        bar_init(done, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    if (warp == 0) tmem_alloc(tslot, TCOLS);
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const unsigned tmem = *tslot;
+    constexpr unsigned ID = idesc(1u, 128, BN);
+    auto issue = [&](int ka) {   // asynchronous copies of atom ka into stage ka % S
+        unsigned char* As = base + (size_t)(ka % S) * STAGE;
+        unsigned char* Bs = As + ABYTES;
+        const int k = ka * 64 + c * 8;
+        const bool kin = k < K;
+        const int tap = kin ? k / a.cin : 0, ci = kin ? k - tap * a.cin : 0;
+        const int dy = tap / 3 - 1, dx = tap % 3 - 1;
+#pragma unroll
+        for (int u = 0; u < RPT; ++u) {
+            const int row = (tid >> 3) + 16 * u;
+            const int sy = py[u] + dy, sx = px[u] + dx;
+            const bool ok = kin && pb[u] >= 0 && sy >= 0 && sy < a.H && sx >= 0 && sx < a.W;
+            const bf16* src = ok ? a.x + (size_t)(pb[u] * HW + sy * a.W + sx) * a.xs + a.xo + ci : a.x;
+            cp_async16_zfill(As + swz16(row, c), src, ok);
+        }
+        for (int v = tid; v < BN * 8; v += kCvThreads) {
+            const int row = v >> 3, cc = v & 7, kk = ka * 64 + cc * 8;
+            const bool ok = kk < K;
+            cp_async16_zfill(Bs + swz16(row, cc), ok ? a.w + (size_t)(n0 + row) * K + kk : a.w, ok);
+        }
+    };
+#pragma unroll 1
+    for (int ka = 0; ka < S - 1 && ka < NK; ++ka) {
+        issue(ka);
+        asm volatile("cp.async.commit_group;\n" ::: "memory");
+    }
+#pragma unroll 1
+    for (int ka = 0; ka < NK; ++ka) {
+        // atom ka has landed once at most S - 2 newer groups are still pending
+        asm volatile("cp.async.wait_group %0;\n" ::"n"(S - 2) : "memory");
+        fence_async_smem();
+        __syncthreads();
+        if (*failed) break;
+        if (tid == 0) {
+            fence_after();
+            const unsigned aa = su32(base + (size_t)(ka % S) * STAGE), bb = aa + ABYTES;
+#pragma unroll
+            for (int k16 = 0; k16 < 4; ++k16)
+                if (ka * 64 + k16 * 16 < K)
+                    mma_bf16(tmem, sdesc(aa + 32u * k16), sdesc(bb + 32u * k16), ID, (ka | k16) ? 1u : 0u);
+            mma_commit(&sbar[ka % S]);
+        }
+        // refill the stage that atom ka - 1 used, once its MMAs are done
+        const int kn = ka + S - 1;
+        if (kn < NK) {
+            if (ka >= 1 && !bar_wait(&sbar[(ka - 1) % S], (unsigned)((ka - 1) / S) & 1u)) atomicOr(failed, 1);
+            issue(kn);
+        }
+        asm volatile("cp.async.commit_group;\n" ::: "memory");   // (possibly empty) group per step
+    }
+    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+    if (tid == 0) mma_commit(done);
+    if (!bar_wait(done, 0)) atomicOr(failed, 2);
+    fence_after();
+    __syncthreads();
+    const bool bad = *failed != 0;
+    if (bad && tid == 0) atomicAdd(&g_conv_timeouts, 1u);
+    // epilogue: warp w holds pixels m0 + 32 w + lane (TMEM lanes 32 w ..)
+    const int r = 32 * warp + lane, p = m0 + r;
+    const unsigned lrow = tmem + ((unsigned)(32 * warp) << 16);
+#pragma unroll 1
+    for (int cc = 0; cc < BN; cc += 8) {
+        float v[8];
+        tmem_ld8(lrow + (unsigned)cc, v);
+        if (p < a.M) {
+            __align__(16) bf16 o[8];
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+                float t = bad ? __int_as_float(0x7fc00000) : v[e] + (a.bias ? a.bias[n0 + cc + e] : 0.0f);
+                if (a.relu) t = fmaxf(t, 0.0f);
+                o[e] = __float2bfloat16(t);
+            }
+            *reinterpret_cast<uint4*>(a.y + (size_t)p * a.ys + a.yo + n0 + cc) = *reinterpret_cast<const uint4*>(o);
+        }
+    }
+    fence_before();
+    __syncthreads();
+    if (warp == 0) tmem_dealloc(tmem, TCOLS);
 }
 
 struct WgradArgs {
@@ -401,6 +549,7 @@ struct ls_net {
     float *w = nullptr, *m1 = nullptr, *m2 = nullptr, *g = nullptr;
     bf16 *wf = nullptr, *wt = nullptr;
     int step = 0;
+    int umma = 1;            // 1: forward / backward-data convolutions on tcgen05; 0: WMMA
     // activations (level l has pix >> 2l pixels)
     bf16* in0 = nullptr;
     std::vector<bf16*> pool, ea, cat, up, da, dbo;
@@ -454,6 +603,17 @@ int conv(ls_net* n, int li, View x, View y, int H, int W, int M, bool relu, bool
         a.w = n->wt + Ly.woff;
         a.bias = nullptr;
         a.relu = 0;
+    }
+    if (n->umma) {   // tensor cores, fifth generation: one CTA per 128 pixels x all output channels
+        const dim3 grid((unsigned)((M + 127) / 128), 1);
+        switch (a.cout) {
+            case 16: NET_LAUNCH(n, k_conv_umma<16>, grid, kCvThreads, conv_umma_smem<16>(), a); return LS_OK;
+            case 32: NET_LAUNCH(n, k_conv_umma<32>, grid, kCvThreads, conv_umma_smem<32>(), a); return LS_OK;
+            case 64: NET_LAUNCH(n, k_conv_umma<64>, grid, kCvThreads, conv_umma_smem<64>(), a); return LS_OK;
+            case 128: NET_LAUNCH(n, k_conv_umma<128>, grid, kCvThreads, conv_umma_smem<128>(), a); return LS_OK;
+            case 256: NET_LAUNCH(n, k_conv_umma<256>, grid, kCvThreads, conv_umma_smem<256>(), a); return LS_OK;
+            default: break;   // other widths: the WMMA form below
+        }
     }
     const int BN = a.cout >= 64 ? 64 : a.cout;
     const dim3 grid((unsigned)(M / 64), (unsigned)(a.cout / BN));
@@ -586,14 +746,41 @@ int backward(ls_net* n, int nb, int H, int W) {
 
 }  // namespace
 
+int ls_conv_timeouts(unsigned* count) {
+    LS_CUDA(cudaMemcpyFromSymbol(count, g_conv_timeouts, sizeof(unsigned)));
+    return LS_OK;
+}
+
 // ------------------------------------------------------------------ C ABI
 extern "C" {
+
+int ls_net_set_tensor_cores(ls_net* n, int on) {
+    if (!n || (on != 0 && on != 1)) return LS_EINVAL;
+    n->umma = on;
+    return LS_OK;
+}
 
 int ls_net_create(int levels, int c0, int max_batch, int H, int W, int train, unsigned long long seed, void* stream,
                   ls_net** out) {
     if (!out || levels < 2 || levels > 6 || c0 < 16 || c0 % 16 || max_batch < 1) return LS_EINVAL;
     const int q = 8 << (levels - 1);
     if (H < q || W < q || H % q || W % q) return LS_EINVAL;
+    {   // the tensor-core convolutions take more than the default 48 KB of shared memory
+        const cudaError_t e = [] {
+            cudaError_t r = cudaFuncSetAttribute(k_conv_umma<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 (int)conv_umma_smem<16>());
+            if (r == cudaSuccess) r = cudaFuncSetAttribute(k_conv_umma<32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                           (int)conv_umma_smem<32>());
+            if (r == cudaSuccess) r = cudaFuncSetAttribute(k_conv_umma<64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                           (int)conv_umma_smem<64>());
+            if (r == cudaSuccess) r = cudaFuncSetAttribute(k_conv_umma<128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                           (int)conv_umma_smem<128>());
+            if (r == cudaSuccess) r = cudaFuncSetAttribute(k_conv_umma<256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                           (int)conv_umma_smem<256>());
+            return r;
+        }();
+        if (e != cudaSuccess) return ls_cuda_fail(e);
+    }
     ls_net* n = new (std::nothrow) ls_net();
     if (!n) return LS_ENOMEM;
     n->L = levels;

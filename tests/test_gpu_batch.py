@@ -49,6 +49,8 @@ def test_batched_bd_equals_per_member_bd(prec, nb):
     m = inputs.bump_medium(n, nbumps=6, seed=5)
     s = binding.Solver(cuda(m), w, layers=L, ext=E, precision=prec)
     s.ls_factor()
+    if prec == binding.LS_MIXED:
+        s.ls_set_tensor_steps(0)   # the CUDA-core steps (the tensor-core form: test_gpu_tensor_steps)
     g = _fields(n, nb, 100)
     v = s.ls_precond_bd_batch(g)
     torch.cuda.synchronize()
@@ -103,6 +105,8 @@ def test_batched_solve_matches_single_solves_and_oracle(prec):
     m = inputs.bump_medium(n, nbumps=6, seed=21)
     s = binding.Solver(cuda(m), w, layers=L, ext=E, precision=prec)
     s.ls_factor()
+    if prec == binding.LS_MIXED:
+        s.ls_set_tensor_steps(2)   # one form for the batch and the single solves
     thetas = [0.0, 0.7, 2.1, 4.4, 5.9]
     f = torch.stack([s.ls_incident_rhs(t) for t in thetas]).contiguous()
     tol = 1e-10
@@ -223,6 +227,7 @@ def test_batch_larger_than_a_chunk_runs_two_concurrent_lanes():
     m = inputs.bump_medium(n, nbumps=6, seed=31)
     s = binding.Solver(cuda(m), w, layers=L, ext=E, precision=binding.LS_MIXED)
     s.ls_factor()
+    s.ls_set_tensor_steps(0)   # the CUDA-core steps: chunks of at most 8
     thetas = [0.5 * k for k in range(12)]
     f = torch.stack([s.ls_incident_rhs(t) for t in thetas]).contiguous()
     u, st, rc = s.ls_solve_batch(f, 1e-9)
@@ -248,6 +253,7 @@ def test_split_and_unsplit_reduction_steps_agree(n, L, E, nb):
     m = inputs.bump_medium(n, nbumps=6, seed=8)
     s = binding.Solver(cuda(m), w, layers=L, ext=E, precision=binding.LS_MIXED)
     s.ls_factor()
+    s.ls_set_tensor_steps(0)   # the split / unsplit forms are those of the CUDA-core steps
     g = _fields(n, nb, 300)
     s.ls_set_reduction(0)
     v0 = s.ls_precond_bd_batch(g).clone()
@@ -276,4 +282,24 @@ def test_unsplit_reduction_inside_a_batched_solve_meets_the_oracle():
     prob = osolver.Problem(m, w, L=L, E=E)
     u_ref, _ = osolver.solve(prob, prob.rhs(thetas[1]), tol=1e-12)
     assert rel(u[1].cpu(), torch.from_numpy(u_ref)) < 1e-7
+    s.close()
+
+
+def test_sixty_four_directions_in_one_call_match_single_solves():
+    # the paper's 64 incident waves per medium (Sec. 5) in one ls_solve_batch call:
+    # Algorithm 2 runs in chunks of up to 32 on concurrent lanes
+    n, L, E = 96, 2, 6
+    w = inputs.omega_for_ppw(n, 10.0)
+    m = inputs.bump_medium(n, nbumps=6, seed=64)
+    s = binding.Solver(cuda(m), w, layers=L, ext=E, precision=binding.LS_MIXED)
+    s.ls_factor()
+    s.ls_set_tensor_steps(2)   # one form for the batch and the single solves
+    B = binding.LS_MAX_BATCH
+    assert B == 64
+    f = torch.stack([s.ls_incident_rhs(2 * math.pi * j / B) for j in range(B)]).contiguous()
+    u, st, rc = s.ls_solve_batch(f, 1e-9)
+    assert rc == 0 and st["true_rel_residual"] <= 1e-9
+    for b in (0, 31, 32, 63):
+        ub, _, _ = s.ls_solve(f[b].contiguous(), 1e-9)
+        assert rel(u[b], ub) < 1e-7, b
     s.close()

@@ -59,7 +59,7 @@ def test_tensor_core_local_solves_match_oracle(n, L, E):
         for l in sorted({0, L // 2, L - 1}):
             b = inputs.random_field(n, 300 + 7 * l + d, nz=lays[d].q)
             ref = lays[d].solve_local(l, b)
-            s.ls_set_tensor_steps(1)
+            s.ls_set_tensor_steps(2)   # always (one right-hand side)
             x_tc = s.ls_local_solve(d, l, cuda(b)).cpu().numpy()
             s.ls_set_tensor_steps(0)
             x_cc = s.ls_local_solve(d, l, cuda(b)).cpu().numpy()
@@ -82,7 +82,7 @@ def test_tensor_core_batch_members_are_independent(nb):
     before = binding.device_timeouts()
     s = binding.Solver(cuda(m), w, layers=L, ext=E, precision=binding.LS_MIXED)
     s.ls_factor()
-    s.ls_set_tensor_steps(1)
+    s.ls_set_tensor_steps(2)
     g = torch.stack([cuda(inputs.random_field(n, 500 + b)) for b in range(nb)]).contiguous()
     v = s.ls_precond_bd_batch(g)
     for b in sorted({0, nb // 2, nb - 1}):
@@ -100,18 +100,18 @@ def test_tensor_core_preconditioner_solve_matches_oracle():
     s = binding.Solver(cuda(m), w, layers=L, ext=E, precision=binding.LS_MIXED)
     s.ls_factor()
     out = {}
-    for tc in (1, 0):
+    for tc in (2, 0):
         s.ls_set_tensor_steps(tc)
         u, st = s.ls_solve_plane_wave(th, 1e-10)
         out[tc] = (u.cpu().numpy(), st)
     prob = osolver.Problem(m, w, L=L, E=E)
     u_ref, _ = osolver.solve(prob, prob.rhs(th), tol=1e-12)
-    e1, e0 = rel(out[1][0], u_ref), rel(out[0][0], u_ref)
+    e1, e0 = rel(out[2][0], u_ref), rel(out[0][0], u_ref)
     print("solve: tensor cores rel err %.2e (outer %d, inner %d); CUDA cores %.2e (outer %d, inner %d)"
-          % (e1, out[1][1]["outer_iters"], out[1][1]["inner_iters_total"], e0, out[0][1]["outer_iters"],
+          % (e1, out[2][1]["outer_iters"], out[2][1]["inner_iters_total"], e0, out[0][1]["outer_iters"],
              out[0][1]["inner_iters_total"]))
     assert e1 < 1e-6 and e0 < 1e-6
-    assert out[1][1]["true_rel_residual"] <= 1e-10
+    assert out[2][1]["true_rel_residual"] <= 1e-10
     s.close()
 
 
@@ -119,8 +119,12 @@ def test_tensor_steps_switch_needs_the_mixed_factors():
     n = 32
     s = binding.Solver(cuda(inputs.gaussian_disk_medium(n)), 2 * math.pi * 4, layers=2, ext=4)
     s.ls_factor()   # FP64: no tensor-core form
-    with pytest.raises(binding.LSError) as e:
-        s.ls_set_tensor_steps(1)
-    assert e.value.code == -8   # LS_ESTATE
+    for on in (1, 2):
+        with pytest.raises(binding.LSError) as e:
+            s.ls_set_tensor_steps(on)
+        assert e.value.code == -8   # LS_ESTATE
     s.ls_set_tensor_steps(0)
+    with pytest.raises(binding.LSError) as e:
+        s.ls_set_tensor_steps(3)
+    assert e.value.code == -1
     s.close()

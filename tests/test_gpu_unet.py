@@ -102,6 +102,126 @@ def test_gradients_match_oracle_network():
     net.close()
 
 
+def bf16(a):
+    """Round to the nearest BF16 (ties to even), returned in FP64."""
+    a32 = np.ascontiguousarray(np.asarray(a, dtype=np.float32))
+    b = a32.view(np.uint32).astype(np.uint64)
+    r = ((b + np.uint64(0x7FFF) + ((b >> np.uint64(16)) & np.uint64(1))) >> np.uint64(16)) << np.uint64(16)
+    return r.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def bf16_storage_model(p, r, m, e, levels):
+    """The network as the GPU stores it: the oracle's FP64 layers (unet.conv3x3 and its
+    backward, pooling, upsampling) with every stored activation, gradient and weight copy
+    rounded to BF16 where the GPU rounds it; sums are exact (FP64), so what is left between
+    the two is the GPU's FP32 accumulation order and the BF16 roundings it flips."""
+    x, sc = unet.make_input(r, m)
+    x = bf16(x)
+    W = {k: (bf16(v) if k.endswith(".w") else v) for k, v in p.items()}
+    conv = lambda h, name, act: bf16(np.maximum(unet.conv3x3(h, W[name + ".w"], W[name + ".b"]), 0.0)
+                                     if act else unet.conv3x3(h, W[name + ".w"], W[name + ".b"]))
+    cache, skips, h = {}, [], x
+    for l in range(levels):
+        if l > 0:
+            h = bf16(unet.avgpool2(h))
+        for sfx in ("a", "b"):
+            name = "enc%d_%s" % (l, sfx)
+            cache[name + ".in"] = h
+            h = conv(h, name, True)
+            cache[name + ".out"] = h
+        skips.append(h)
+    for l in range(levels - 2, -1, -1):
+        up = unet.upsample2(h)
+        name = "dec%d_up" % l
+        cache[name + ".in"] = up
+        h = conv(up, name, True)
+        cache[name + ".out"] = h
+        h = np.concatenate([h, skips[l]], axis=0)
+        for sfx in ("a", "b"):
+            name = "dec%d_%s" % (l, sfx)
+            cache[name + ".in"] = h
+            h = conv(h, name, True)
+            cache[name + ".out"] = h
+    cache["head.in"] = h
+    y = conv(h, "head", False)
+    t = np.stack([e.real / sc, e.imag / sc])
+    d = y - t
+    loss = 0.5 * float(np.mean(d * d))
+    g = {}
+
+    def back(name, dy, store=True):   # weight grads from BF16 dy and inputs; dx rounded like the GPU's
+        dx, g[name + ".w"], g[name + ".b"] = unet.conv3x3_backward(cache[name + ".in"], W[name + ".w"], dy)
+        return bf16(dx) if store else dx
+
+    dh = back("head", bf16(d / d.size))
+    dskip = [None] * levels
+    for l in range(0, levels - 1):
+        for sfx in ("b", "a"):
+            name = "dec%d_%s" % (l, sfx)
+            dh = back(name, dh * (cache[name + ".out"] > 0))
+        c = p["dec%d_up.w" % l].shape[0]
+        dskip[l] = dh[c:]
+        dh = dh[:c]
+        name = "dec%d_up" % l
+        dh = bf16(unet.upsample2_backward(back(name, dh * (cache[name + ".out"] > 0))))
+    for l in range(levels - 1, -1, -1):
+        if dskip[l] is not None:
+            dh = bf16(dh + dskip[l])
+        for sfx in ("b", "a"):
+            name = "enc%d_%s" % (l, sfx)
+            dh = back(name, dh * (cache[name + ".out"] > 0), store=(l > 0 or sfx == "b"))
+        if l > 0:
+            dh = unet.avgpool2_backward(dh)
+    return loss, g, sc * (y[0] + 1j * y[1])
+
+
+@pytest.mark.parametrize("tensor_cores", [1, 0])
+def test_forward_and_gradients_match_the_bf16_storage_model(tensor_cores):
+    # the GPU network against the same network with BF16 storage at the GPU's rounding points
+    # (all sums exact): outputs within a few BF16 ulps (2^-8 relative each), every layer's
+    # gradient to cos > 0.999 and 2 % relative L2 (FP32 accumulation over K <= 9 x 2c0 x 4
+    # terms and the BF16 roundings it flips)
+    p, net = make_pair(5)
+    net.set_tensor_cores(tensor_cores)
+    r, e, m = sample(N, 6)
+    z = net.forward(torch.from_numpy(r[None]).cuda(), torch.from_numpy(m[None]).cuda())[0].cpu().numpy()
+    loss = net.train_step(torch.from_numpy(r[None]).cuda(), torch.from_numpy(m[None]).cuda(),
+                          torch.from_numpy(e[None]).cuda(), lr=0.0)
+    gv = net.get_grads().numpy()
+    loss_m, g_m, z_m = bf16_storage_model(p, r, m, e, LEVELS)
+    print("BF16 model (tensor cores %d): output rel %.2e, loss rel %.2e" % (tensor_cores, rel(z, z_m),
+                                                                             abs(loss - loss_m) / loss_m))
+    assert rel(z, z_m) < 4e-3
+    assert abs(loss - loss_m) < 4e-3 * loss_m
+    k, worst = 0, (1.0, 0.0)
+    for name, o, c in unet.layer_shapes(LEVELS, C0):
+        for part in (".w", ".b"):
+            ref = g_m[name + part].ravel()
+            got = gv[k:k + ref.size]
+            k += ref.size
+            cos = float(np.dot(got, ref) / (np.linalg.norm(got) * np.linalg.norm(ref) + 1e-30))
+            worst = (min(worst[0], cos), max(worst[1], rel(got, ref)))
+            assert cos > 0.999, (name + part, cos)
+            assert rel(got, ref) < 2e-2, (name + part, rel(got, ref))
+    print("BF16 model gradients: worst cos %.6f, worst rel %.2e" % worst)
+    net.close()
+
+
+def test_tensor_core_and_wmma_convolutions_agree():
+    # both accumulate BF16 products in FP32 and round the output to BF16: they may differ
+    # by the ulps their summation orders flip
+    _, net = make_pair(7)
+    r, _, m = sample(N, 8)
+    rt, mt = torch.from_numpy(r[None]).cuda(), torch.from_numpy(m[None]).cuda()
+    net.set_tensor_cores(1)
+    z1 = net.forward(rt, mt)[0].cpu().numpy()
+    net.set_tensor_cores(0)
+    z0 = net.forward(rt, mt)[0].cpu().numpy()
+    assert rel(z1, z0) < 4e-3
+    assert np.abs(z1 - z0).max() < 3e-2 * np.abs(z0).max()
+    net.close()
+
+
 def test_training_steps_reduce_the_loss_and_batches_are_independent():
     _, net = make_pair(2)
     rs, es, ms = zip(*(sample(N, 10 + b) for b in range(2)))
