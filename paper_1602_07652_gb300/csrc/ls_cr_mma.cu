@@ -123,6 +123,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_cr_mma(StepArgs a) {
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int idx = blockIdx.x;
+    // The next step may be scheduled now (programmatic dependent launch): its CTAs set up
+    // and start streaming their factor planes, which no step writes, while this one runs.
+    asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
     const size_t s = (size_t)1 << a.k;
     const int j = (MODE == 1) ? 2 * idx : (MODE == 3 ? 0 : 2 * idx + 1);
     const bool hw = j >= 1, he = j + 1 < a.nk;
@@ -185,59 +188,98 @@ __global__ void __launch_bounds__(kThreads, 1) k_cr_mma(StepArgs a) {
         }
     }
 
+    // Vectors are read and written only after the previous kernel of the stream has
+    // completed and its writes are visible.
+    asm volatile("griddepcontrol.wait;\n" ::: "memory");
+
     // B: per vector t, atom at, rows [0,NB) = -X_im, [NB,2NB) = X_re, [2NB,3NB) = X_im (TF32).
-    // Every load of the thread is issued before the first store, so their latencies overlap.
+    // Element u of the thread is (member b, row kk) with b * KP + kk = tid + 256 u.  Every
+    // load is issued (at a clamped, valid address) before any value is used, so their
+    // latencies overlap; absent vectors, members and padding rows are zeroed afterwards.
     constexpr int PER = NB * KP / kThreads;   // elements of one vector per thread
+    const int nbc = a.nb < 1 ? 0 : a.nb - 1;
     float2 val[NV][PER];
+    if constexpr (MODE == 4) {
+        // t = -(W x_{j-1} + E x_{j+1}) with the tridiagonal couplings of level 0.  A warp
+        // holds 32 consecutive rows kk of one member (KP is a multiple of 32): rows kk -+ 1
+        // come from the neighbour lanes, and from loads at the warp's two ends.  The rows of
+        // a thread repeat with period KP / gcd(256, KP) <= 3, so it loads the couplings of
+        // at most 3 rows.
+        constexpr int G = (kThreads % KP == 0) ? KP : (KP % 64 == 0 ? 64 : 32);   // gcd(256, KP)
+        constexpr int PERIOD = KP / G;
+        const float2* wj = a.cw + (size_t)j * 3 * q;
+        const float2* ej = a.ce + (size_t)j * 3 * q;
+        const float2 z2 = make_float2(0.f, 0.f);
+        float2 cwr[PERIOD][3], cer[PERIOD][3];
 #pragma unroll
-    for (int t = 0; t < NV; ++t)
+        for (int u = 0; u < PERIOD; ++u) {
+            const int kk = (tid + u * kThreads) % KP, kc = kk < q ? kk : q - 1;
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                cwr[u][d] = __ldg(&wj[(size_t)d * q + kc]);
+                cer[u][d] = __ldg(&ej[(size_t)d * q + kc]);
+            }
+        }
+        const size_t om = (size_t)(j - 1) * q, op = (size_t)(he ? j + 1 : j - 1) * q;
+        float2 xm[PER], xp[PER], el[PER][2], er[PER][2];
 #pragma unroll
         for (int u = 0; u < PER; ++u) {
             const int o = tid + u * kThreads, b = o / KP, kk = o % KP;
-            const bool live = pres[t] && b < a.nb && kk < q;
-            float2 v = make_float2(0.f, 0.f);
-            if constexpr (MODE == 4) {
-                // t = -(W x_{j-1} + E x_{j+1}) with the tridiagonal couplings; a warp holds 32
-                // consecutive rows kk of one member (KP is a multiple of 32), so the rows
-                // kk -+ 1 come from the neighbour lanes (shuffles), loads only at the warp's ends
-                const float2* xb = a.x + (size_t)(b < a.nb ? b : 0) * a.SB;
-                const float2 z2 = make_float2(0.f, 0.f);
-                const float2 xm = live ? xb[(size_t)(j - 1) * q + kk] : z2;
-                const float2 xp = (live && he) ? xb[(size_t)(j + 1) * q + kk] : z2;
-                float2 xml, xmr, xpl, xpr;
-                xml.x = __shfl_up_sync(0xffffffffu, xm.x, 1); xml.y = __shfl_up_sync(0xffffffffu, xm.y, 1);
-                xpl.x = __shfl_up_sync(0xffffffffu, xp.x, 1); xpl.y = __shfl_up_sync(0xffffffffu, xp.y, 1);
-                xmr.x = __shfl_down_sync(0xffffffffu, xm.x, 1); xmr.y = __shfl_down_sync(0xffffffffu, xm.y, 1);
-                xpr.x = __shfl_down_sync(0xffffffffu, xp.x, 1); xpr.y = __shfl_down_sync(0xffffffffu, xp.y, 1);
-                if (lane == 0) {
-                    xml = (live && kk >= 1) ? xb[(size_t)(j - 1) * q + kk - 1] : z2;
-                    xpl = (live && he && kk >= 1) ? xb[(size_t)(j + 1) * q + kk - 1] : z2;
-                }
-                if (lane == 31) {
-                    xmr = (live && kk + 1 < q) ? xb[(size_t)(j - 1) * q + kk + 1] : z2;
-                    xpr = (live && he && kk + 1 < q) ? xb[(size_t)(j + 1) * q + kk + 1] : z2;
-                }
-                if (live) {
-                    const float2* wj = a.cw + (size_t)j * 3 * q;
-                    const float2* ej = a.ce + (size_t)j * 3 * q;
-                    // row kk - 1 / kk + 1 outside the strip: its value is zero (loads above)
-                    float2 acc = cfma(__ldg(&wj[kk]), kk >= 1 ? xml : z2, z2);
-                    acc = cfma(__ldg(&wj[q + kk]), xm, acc);
-                    acc = cfma(__ldg(&wj[2 * q + kk]), kk + 1 < q ? xmr : z2, acc);
-                    if (he) {
-                        acc = cfma(__ldg(&ej[kk]), kk >= 1 ? xpl : z2, acc);
-                        acc = cfma(__ldg(&ej[q + kk]), xp, acc);
-                        acc = cfma(__ldg(&ej[2 * q + kk]), kk + 1 < q ? xpr : z2, acc);
-                    }
-                    v = make_float2(-acc.x, -acc.y);
-                }
-            } else if (live) {
-                const float2* xb = a.x + (size_t)b * a.SB;
-                v = xb[(size_t)blk[t] * q + kk];
-                v = make_float2(sgn[t] * v.x, sgn[t] * v.y);
-            }
-            val[t][u] = v;
+            const int kc = kk < q ? kk : q - 1, kl = kc >= 1 ? kc - 1 : 0, kr = kc + 1 < q ? kc + 1 : q - 1;
+            const float2* xb = a.x + (size_t)(b < a.nb ? b : nbc) * a.SB;
+            xm[u] = xb[om + kc];
+            xp[u] = xb[op + kc];
+            el[u][0] = lane == 0 ? xb[om + kl] : z2;
+            el[u][1] = lane == 0 ? xb[op + kl] : z2;
+            er[u][0] = lane == 31 ? xb[om + kr] : z2;
+            er[u][1] = lane == 31 ? xb[op + kr] : z2;
         }
+#pragma unroll
+        for (int u = 0; u < PER; ++u) {
+            const int o = tid + u * kThreads, b = o / KP, kk = o % KP;
+            const bool live = b < a.nb && kk < q;
+            float2 xml, xmr, xpl, xpr;
+            xml.x = __shfl_up_sync(0xffffffffu, xm[u].x, 1); xml.y = __shfl_up_sync(0xffffffffu, xm[u].y, 1);
+            xpl.x = __shfl_up_sync(0xffffffffu, xp[u].x, 1); xpl.y = __shfl_up_sync(0xffffffffu, xp[u].y, 1);
+            xmr.x = __shfl_down_sync(0xffffffffu, xm[u].x, 1); xmr.y = __shfl_down_sync(0xffffffffu, xm[u].y, 1);
+            xpr.x = __shfl_down_sync(0xffffffffu, xp[u].x, 1); xpr.y = __shfl_down_sync(0xffffffffu, xp[u].y, 1);
+            if (lane == 0) { xml = el[u][0]; xpl = el[u][1]; }
+            if (lane == 31) { xmr = er[u][0]; xpr = er[u][1]; }
+            // rows kk - 1 / kk + 1 outside the strip hold zero
+            if (kk < 1) { xml = z2; xpl = z2; }
+            if (kk + 1 >= q) { xmr = z2; xpr = z2; }
+            const int c = u % PERIOD;
+            float2 acc = cfma(cwr[c][0], xml, z2);
+            acc = cfma(cwr[c][1], xm[u], acc);
+            acc = cfma(cwr[c][2], xmr, acc);
+            if (he) {
+                acc = cfma(cer[c][0], xpl, acc);
+                acc = cfma(cer[c][1], xp[u], acc);
+                acc = cfma(cer[c][2], xpr, acc);
+            }
+            val[0][u] = live ? make_float2(-acc.x, -acc.y) : z2;
+        }
+    } else {
+        size_t ob[NV];   // absent vectors read the step's own block (a valid address), then zeroed
+#pragma unroll
+        for (int t = 0; t < NV; ++t) ob[t] = (size_t)(pres[t] ? blk[t] : (long long)j * (long long)s) * q;
+#pragma unroll
+        for (int t = 0; t < NV; ++t)
+#pragma unroll
+            for (int u = 0; u < PER; ++u) {
+                const int o = tid + u * kThreads, b = o / KP, kk = o % KP;
+                const int kc = kk < q ? kk : q - 1;
+                val[t][u] = a.x[(size_t)(b < a.nb ? b : nbc) * a.SB + ob[t] + kc];
+            }
+#pragma unroll
+        for (int t = 0; t < NV; ++t)
+#pragma unroll
+            for (int u = 0; u < PER; ++u) {
+                const int o = tid + u * kThreads, b = o / KP, kk = o % KP;
+                const bool live = pres[t] && b < a.nb && kk < q;
+                val[t][u] = live ? make_float2(sgn[t] * val[t][u].x, sgn[t] * val[t][u].y) : make_float2(0.f, 0.f);
+            }
+    }
 #pragma unroll
     for (int t = 0; t < NV; ++t) {
         unsigned char* Bt = Bs + (size_t)t * KA * BATOM;
@@ -402,7 +444,21 @@ int launch(ls_handle* h, unsigned grid, StepArgs a) {
     using CF = Cfg<MODE, NB, KA>;
     a.stages = CF::stages(a.q);
     if (a.stages < 1) return LS_EINVAL;
-    LS_LAUNCH(h, (k_cr_mma<MODE, NB, KA>), grid, kThreads, CF::smem(a.q), a);
+    // programmatic stream serialization: the kernel waits (griddepcontrol.wait) for its
+    // predecessor before it touches the vectors
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(kThreads);
+    cfg.dynamicSmemBytes = CF::smem(a.q);
+    cfg.stream = h->stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    const cudaError_t e = cudaLaunchKernelEx(&cfg, k_cr_mma<MODE, NB, KA>, a);
+    h->launches++;
+    if (e != cudaSuccess) return ls_cuda_fail(e);
     return LS_OK;
 }
 

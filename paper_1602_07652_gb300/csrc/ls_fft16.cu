@@ -403,19 +403,27 @@ __device__ __forceinline__ void tma_store_2d(const CUtensorMap* map, int x, int 
                  "r"(x), "r"(y), "r"(smem_u32(src))
                  : "memory");
 }
-// true once the barrier's phase `parity` has completed; false after kTmaWaitNs
+__device__ __forceinline__ bool mbar_test(unsigned long long* bar, unsigned parity) {
+    unsigned done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return done != 0;
+}
+// true once the barrier's phase `parity` has completed; false after kTmaWaitNs.  The
+// global timer (slow to read) is read only after a first failed test, then every 32 tests.
 __device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity) {
+    if (mbar_test(bar, parity)) return true;
     const unsigned long long t0 = global_ns();
     for (;;) {
-        unsigned done;
-        asm volatile(
-            "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-            : "=r"(done)
-            : "r"(smem_u32(bar)), "r"(parity)
-            : "memory");
-        if (done) return true;
+#pragma unroll 1
+        for (int i = 0; i < 32; ++i) {
+            if (mbar_test(bar, parity)) return true;
+            __nanosleep(64);
+        }
         if (global_ns() - t0 > kTmaWaitNs) return false;
-        __nanosleep(64);
     }
 }
 

@@ -15,17 +15,25 @@ __device__ __forceinline__ unsigned long long gtime() {
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
     return t;
 }
-// true once phase `parity` of the barrier has completed; false after kWaitNs
+__device__ __forceinline__ bool bar_try(unsigned long long* bar, unsigned parity) {
+    unsigned done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(su32(bar)), "r"(parity)
+        : "memory");
+    return done != 0;
+}
+// true once phase `parity` of the barrier has completed; false after kWaitNs.  The
+// global timer is slow to read (hundreds of ns), so it is read only once the phase was
+// found incomplete, and then once every 32 polls.
 __device__ __forceinline__ bool bar_wait(unsigned long long* bar, unsigned parity) {
+    if (bar_try(bar, parity)) return true;
     const unsigned long long t0 = gtime();
     for (;;) {
-        unsigned done;
-        asm volatile(
-            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-            : "=r"(done)
-            : "r"(su32(bar)), "r"(parity)
-            : "memory");
-        if (done) return true;
+#pragma unroll 1
+        for (int i = 0; i < 32; ++i)
+            if (bar_try(bar, parity)) return true;
         if (gtime() - t0 > kWaitNs) return false;
     }
 }
