@@ -193,13 +193,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_cr_mma(StepArgs a) {
     asm volatile("griddepcontrol.wait;\n" ::: "memory");
 
     // B: per vector t, atom at, rows [0,NB) = -X_im, [NB,2NB) = X_re, [2NB,3NB) = X_im (TF32).
-    // Element u of the thread is (member b, row kk) with b * KP + kk = tid + 256 u.  Every
-    // load is issued (at a clamped, valid address) before any value is used, so their
+    // Every load is issued (at a clamped, valid address) before any value is used, so their
     // latencies overlap; absent vectors, members and padding rows are zeroed afterwards.
+    // Tridiagonal step: element u of the thread is (member b, row kk), b * KP + kk = tid + 256 u.
     constexpr int PER = NB * KP / kThreads;   // elements of one vector per thread
     const int nbc = a.nb < 1 ? 0 : a.nb - 1;
-    float2 val[NV][PER];
     if constexpr (MODE == 4) {
+        float2 val[1][PER];
         // t = -(W x_{j-1} + E x_{j+1}) with the tridiagonal couplings of level 0.  A warp
         // holds 32 consecutive rows kk of one member (KP is a multiple of 32): rows kk -+ 1
         // come from the neighbour lanes, and from loads at the warp's two ends.  The rows of
@@ -259,44 +259,58 @@ __global__ void __launch_bounds__(kThreads, 1) k_cr_mma(StepArgs a) {
             }
             val[0][u] = live ? make_float2(-acc.x, -acc.y) : z2;
         }
-    } else {
-        size_t ob[NV];   // absent vectors read the step's own block (a valid address), then zeroed
-#pragma unroll
-        for (int t = 0; t < NV; ++t) ob[t] = (size_t)(pres[t] ? blk[t] : (long long)j * (long long)s) * q;
-#pragma unroll
-        for (int t = 0; t < NV; ++t)
-#pragma unroll
-            for (int u = 0; u < PER; ++u) {
-                const int o = tid + u * kThreads, b = o / KP, kk = o % KP;
-                const int kc = kk < q ? kk : q - 1;
-                val[t][u] = a.x[(size_t)(b < a.nb ? b : nbc) * a.SB + ob[t] + kc];
-            }
-#pragma unroll
-        for (int t = 0; t < NV; ++t)
-#pragma unroll
-            for (int u = 0; u < PER; ++u) {
-                const int o = tid + u * kThreads, b = o / KP, kk = o % KP;
-                const bool live = pres[t] && b < a.nb && kk < q;
-                val[t][u] = live ? make_float2(sgn[t] * val[t][u].x, sgn[t] * val[t][u].y) : make_float2(0.f, 0.f);
-            }
-    }
-#pragma unroll
-    for (int t = 0; t < NV; ++t) {
-        unsigned char* Bt = Bs + (size_t)t * KA * BATOM;
+        // the tridiagonal step's single vector, one TF32 element per store
+        unsigned char* Bt = Bs;
 #pragma unroll
         for (int u = 0; u < PER; ++u) {
             const int o = tid + u * kThreads, b = o / KP, kk = o % KP;
-            const float re = tf32_rna(val[t][u].x), im = tf32_rna(val[t][u].y);
-            const int at = kk >> 5, kc = kk & 31;
-            unsigned char* atom = Bt + (size_t)at * BATOM;
-            const int rows[3] = {b, NB + b, 2 * NB + b};
-            const float vals[3] = {-im, re, im};
+            const float re = tf32_rna(val[0][u].x), im = tf32_rna(val[0][u].y);
+            unsigned char* atom = Bt + (size_t)(kk >> 5) * BATOM;
+            // rows b, NB + b, 2NB + b share (row & 7) (NB is a multiple of 8): NB * 128 bytes apart
+            const int kc = kk & 31;
+            const unsigned off = (unsigned)(b >> 3) * 1024u + (unsigned)(b & 7) * 128u +
+                                 (unsigned)(((kc >> 2) ^ (b & 7)) << 4) + (unsigned)(kc & 3) * 4u;
+            *reinterpret_cast<float*>(atom + off) = -im;
+            *reinterpret_cast<float*>(atom + off + NB * 128u) = re;
+            *reinterpret_cast<float*>(atom + off + 2u * NB * 128u) = im;
+        }
+    } else {
+        // Groups of 4 consecutive rows of one member: one 16-byte chunk of a swizzled atom
+        // row, so each of the three B rows takes one 16-byte store.
+        constexpr int KG = KP / 4, NG = NB * KG, PERG = (NG + kThreads - 1) / kThreads;
+        size_t ob[NV];   // absent vectors read the step's own block (a valid address), then zeroed
 #pragma unroll
-            for (int w3 = 0; w3 < 3; ++w3) {
-                const int nrow = rows[w3];
-                const unsigned off = (unsigned)(nrow >> 3) * 1024u + (unsigned)(nrow & 7) * 128u +
-                                     (unsigned)(((kc >> 2) ^ (nrow & 7)) << 4) + (unsigned)(kc & 3) * 4u;
-                *reinterpret_cast<float*>(atom + off) = vals[w3];
+        for (int t = 0; t < NV; ++t) ob[t] = (size_t)(pres[t] ? blk[t] : (long long)j * (long long)s) * q;
+        float2 xv[NV][PERG][4];
+#pragma unroll
+        for (int t = 0; t < NV; ++t)
+#pragma unroll
+            for (int g = 0; g < PERG; ++g) {
+                const int o4 = tid + g * kThreads, b = o4 / KG, k0 = 4 * (o4 % KG);
+                const float2* xb = a.x + (size_t)(o4 < NG && b < a.nb ? b : nbc) * a.SB + ob[t];
+#pragma unroll
+                for (int e = 0; e < 4; ++e) xv[t][g][e] = xb[k0 + e < q ? k0 + e : q - 1];
+            }
+#pragma unroll
+        for (int t = 0; t < NV; ++t) {
+            unsigned char* Bt = Bs + (size_t)t * KA * BATOM;
+#pragma unroll
+            for (int g = 0; g < PERG; ++g) {
+                const int o4 = tid + g * kThreads, b = o4 / KG, c4 = o4 % KG, k0 = 4 * c4;
+                if (o4 >= NG) continue;
+                float re[4], im[4];
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const bool live = pres[t] && b < a.nb && k0 + e < q;
+                    re[e] = live ? tf32_rna(sgn[t] * xv[t][g][e].x) : 0.f;
+                    im[e] = live ? tf32_rna(sgn[t] * xv[t][g][e].y) : 0.f;
+                }
+                const int ch = c4 & 7;   // 16-byte chunk of the 128-byte row in atom c4 / 8
+                unsigned char* row = Bt + (size_t)(c4 >> 3) * BATOM + (size_t)(b >> 3) * 1024u + (size_t)(b & 7) * 128u +
+                                     (size_t)((ch ^ (b & 7)) << 4);
+                *reinterpret_cast<float4*>(row) = make_float4(-im[0], -im[1], -im[2], -im[3]);
+                *reinterpret_cast<float4*>(row + NB * 128u) = make_float4(re[0], re[1], re[2], re[3]);
+                *reinterpret_cast<float4*>(row + 2u * NB * 128u) = make_float4(im[0], im[1], im[2], im[3]);
             }
         }
     }
@@ -318,15 +332,25 @@ __global__ void __launch_bounds__(kThreads, 1) k_cr_mma(StepArgs a) {
                     break;
                 }
                 asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-                const unsigned pa = su32(As + (size_t)st * kPlane);
+                // descriptors built once per plane; a K slice of 8 TF32 (32 bytes) advances the
+                // start-address field (address / 16) by 2, an atom by its size / 16
+                const unsigned long long ad0 = sdesc(su32(As + (size_t)st * kPlane));
+                // plane re: B rows [NB, 3NB) = [X_re; X_im]; plane im: rows [0, 2NB) = [-X_im; X_re]
+                const unsigned long long bd0 = sdesc(bt + (p == 0 ? (unsigned)NB * 128u : 0u));
+#pragma unroll
                 for (int at = 0; at < KA; ++at) {
-                    const unsigned aaddr = pa + (unsigned)at * (unsigned)BR * 128u;
-                    // plane re: B rows [NB, 3NB) = [X_re; X_im]; plane im: rows [0, 2NB) = [-X_im; X_re]
-                    const unsigned baddr = bt + (unsigned)at * BATOM + (p == 0 ? (unsigned)NB * 128u : 0u);
+                    const unsigned long long ad = ad0 + (unsigned long long)((unsigned)at * (unsigned)BR * 8u);
+                    const unsigned long long bd = bd0 + (unsigned long long)((unsigned)at * (BATOM >> 4));
                     const int kleft = q - 32 * at;   // K slices of 8 beyond q are zero: skipped
-                    const int nk8 = kleft >= 32 ? 4 : (kleft + 7) / 8;
-                    for (int k8 = 0; k8 < nk8; ++k8, ++issued)
-                        mma_tf32(tmem, sdesc(aaddr + 32u * k8), sdesc(baddr + 32u * k8), ID, issued ? 1u : 0u);
+                    if (kleft >= 32) {
+#pragma unroll
+                        for (int k8 = 0; k8 < 4; ++k8, ++issued)
+                            mma_tf32(tmem, ad + 2ull * k8, bd + 2ull * k8, ID, issued ? 1u : 0u);
+                    } else {
+                        const int nk8 = (kleft + 7) / 8;
+                        for (int k8 = 0; k8 < nk8; ++k8, ++issued)
+                            mma_tf32(tmem, ad + 2ull * k8, bd + 2ull * k8, ID, issued ? 1u : 0u);
+                    }
                 }
                 mma_commit(&empty[st]);   // the stage is free once these MMAs have read it
             }
