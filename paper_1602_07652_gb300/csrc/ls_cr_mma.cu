@@ -99,7 +99,7 @@ struct StepArgs {
 };
 
 template <int MODE, int NB, int KA>
-__global__ void __launch_bounds__(kThreads, 1) k_cr_mma(StepArgs a) {
+__global__ void __launch_bounds__(kThreads, (ModeOf<MODE>::NV == 1 ? 2 : 1)) k_cr_mma(StepArgs a) {
     using MO = ModeOf<MODE>;
     constexpr int NV = MO::NV;
     constexpr int KP = 32 * KA;                   // padded K of one plane
@@ -195,84 +195,84 @@ __global__ void __launch_bounds__(kThreads, 1) k_cr_mma(StepArgs a) {
     // B: per vector t, atom at, rows [0,NB) = -X_im, [NB,2NB) = X_re, [2NB,3NB) = X_im (TF32).
     // Every load is issued (at a clamped, valid address) before any value is used, so their
     // latencies overlap; absent vectors, members and padding rows are zeroed afterwards.
-    // Tridiagonal step: element u of the thread is (member b, row kk), b * KP + kk = tid + 256 u.
-    constexpr int PER = NB * KP / kThreads;   // elements of one vector per thread
     const int nbc = a.nb < 1 ? 0 : a.nb - 1;
     if constexpr (MODE == 4) {
-        float2 val[1][PER];
-        // t = -(W x_{j-1} + E x_{j+1}) with the tridiagonal couplings of level 0.  A warp
-        // holds 32 consecutive rows kk of one member (KP is a multiple of 32): rows kk -+ 1
-        // come from the neighbour lanes, and from loads at the warp's two ends.  The rows of
-        // a thread repeat with period KP / gcd(256, KP) <= 3, so it loads the couplings of
-        // at most 3 rows.
-        constexpr int G = (kThreads % KP == 0) ? KP : (KP % 64 == 0 ? 64 : 32);   // gcd(256, KP)
-        constexpr int PERIOD = KP / G;
+        // t = -(W x_{j-1} + E x_{j+1}) with the tridiagonal couplings of level 0.  Warp w
+        // takes members b = w + 8 m (m < NB / 8) and rows kk = 32 c + lane (c < KA): the
+        // rows kk -+ 1 of a member are in the same warp (the neighbour lane, or lane 31 / 0
+        // of the neighbouring chunk), and the couplings of row kk serve all its members.
+        constexpr int MW = NB / 8;
+        const float2 z2 = make_float2(0.f, 0.f);
         const float2* wj = a.cw + (size_t)j * 3 * q;
         const float2* ej = a.ce + (size_t)j * 3 * q;
-        const float2 z2 = make_float2(0.f, 0.f);
-        float2 cwr[PERIOD][3], cer[PERIOD][3];
+        float2 cwr[KA][3], cer[KA][3];
 #pragma unroll
-        for (int u = 0; u < PERIOD; ++u) {
-            const int kk = (tid + u * kThreads) % KP, kc = kk < q ? kk : q - 1;
+        for (int c = 0; c < KA; ++c) {
+            const int kk = 32 * c + lane, kc = kk < q ? kk : q - 1;
 #pragma unroll
             for (int d = 0; d < 3; ++d) {
-                cwr[u][d] = __ldg(&wj[(size_t)d * q + kc]);
-                cer[u][d] = __ldg(&ej[(size_t)d * q + kc]);
+                cwr[c][d] = __ldg(&wj[(size_t)d * q + kc]);
+                cer[c][d] = __ldg(&ej[(size_t)d * q + kc]);
             }
         }
         const size_t om = (size_t)(j - 1) * q, op = (size_t)(he ? j + 1 : j - 1) * q;
-        float2 xm[PER], xp[PER], el[PER][2], er[PER][2];
+        float2 xm[MW][KA], xp[MW][KA];
 #pragma unroll
-        for (int u = 0; u < PER; ++u) {
-            const int o = tid + u * kThreads, b = o / KP, kk = o % KP;
-            const int kc = kk < q ? kk : q - 1, kl = kc >= 1 ? kc - 1 : 0, kr = kc + 1 < q ? kc + 1 : q - 1;
-            const float2* xb = a.x + (size_t)(b < a.nb ? b : nbc) * a.SB;
-            xm[u] = xb[om + kc];
-            xp[u] = xb[op + kc];
-            el[u][0] = lane == 0 ? xb[om + kl] : z2;
-            el[u][1] = lane == 0 ? xb[op + kl] : z2;
-            er[u][0] = lane == 31 ? xb[om + kr] : z2;
-            er[u][1] = lane == 31 ? xb[op + kr] : z2;
-        }
+        for (int m = 0; m < MW; ++m)
 #pragma unroll
-        for (int u = 0; u < PER; ++u) {
-            const int o = tid + u * kThreads, b = o / KP, kk = o % KP;
-            const bool live = b < a.nb && kk < q;
-            float2 xml, xmr, xpl, xpr;
-            xml.x = __shfl_up_sync(0xffffffffu, xm[u].x, 1); xml.y = __shfl_up_sync(0xffffffffu, xm[u].y, 1);
-            xpl.x = __shfl_up_sync(0xffffffffu, xp[u].x, 1); xpl.y = __shfl_up_sync(0xffffffffu, xp[u].y, 1);
-            xmr.x = __shfl_down_sync(0xffffffffu, xm[u].x, 1); xmr.y = __shfl_down_sync(0xffffffffu, xm[u].y, 1);
-            xpr.x = __shfl_down_sync(0xffffffffu, xp[u].x, 1); xpr.y = __shfl_down_sync(0xffffffffu, xp[u].y, 1);
-            if (lane == 0) { xml = el[u][0]; xpl = el[u][1]; }
-            if (lane == 31) { xmr = er[u][0]; xpr = er[u][1]; }
-            // rows kk - 1 / kk + 1 outside the strip hold zero
-            if (kk < 1) { xml = z2; xpl = z2; }
-            if (kk + 1 >= q) { xmr = z2; xpr = z2; }
-            const int c = u % PERIOD;
-            float2 acc = cfma(cwr[c][0], xml, z2);
-            acc = cfma(cwr[c][1], xm[u], acc);
-            acc = cfma(cwr[c][2], xmr, acc);
-            if (he) {
-                acc = cfma(cer[c][0], xpl, acc);
-                acc = cfma(cer[c][1], xp[u], acc);
-                acc = cfma(cer[c][2], xpr, acc);
+            for (int c = 0; c < KA; ++c) {
+                const int b = warp + 8 * m, kk = 32 * c + lane, kc = kk < q ? kk : q - 1;
+                const float2* xb = a.x + (size_t)(b < a.nb ? b : nbc) * a.SB;
+                xm[m][c] = xb[om + kc];
+                xp[m][c] = xb[op + kc];
             }
-            val[0][u] = live ? make_float2(-acc.x, -acc.y) : z2;
-        }
-        // the tridiagonal step's single vector, one TF32 element per store
-        unsigned char* Bt = Bs;
 #pragma unroll
-        for (int u = 0; u < PER; ++u) {
-            const int o = tid + u * kThreads, b = o / KP, kk = o % KP;
-            const float re = tf32_rna(val[0][u].x), im = tf32_rna(val[0][u].y);
-            unsigned char* atom = Bt + (size_t)(kk >> 5) * BATOM;
-            // rows b, NB + b, 2NB + b share (row & 7) (NB is a multiple of 8): NB * 128 bytes apart
-            const int kc = kk & 31;
-            const unsigned off = (unsigned)(b >> 3) * 1024u + (unsigned)(b & 7) * 128u +
-                                 (unsigned)(((kc >> 2) ^ (b & 7)) << 4) + (unsigned)(kc & 3) * 4u;
-            *reinterpret_cast<float*>(atom + off) = -im;
-            *reinterpret_cast<float*>(atom + off + NB * 128u) = re;
-            *reinterpret_cast<float*>(atom + off + 2u * NB * 128u) = im;
+        for (int m = 0; m < MW; ++m)
+#pragma unroll
+            for (int c = 0; c < KA; ++c)
+                if (32 * c + lane >= q) {   // rows outside the strip hold zero
+                    xm[m][c] = z2;
+                    xp[m][c] = z2;
+                }
+        auto shf = [](float2 v, int src) {
+            return make_float2(__shfl_sync(0xffffffffu, v.x, src), __shfl_sync(0xffffffffu, v.y, src));
+        };
+        auto up1 = [](float2 v) {
+            return make_float2(__shfl_up_sync(0xffffffffu, v.x, 1), __shfl_up_sync(0xffffffffu, v.y, 1));
+        };
+        auto dn1 = [](float2 v) {
+            return make_float2(__shfl_down_sync(0xffffffffu, v.x, 1), __shfl_down_sync(0xffffffffu, v.y, 1));
+        };
+#pragma unroll
+        for (int m = 0; m < MW; ++m) {
+            const int b = warp + 8 * m;
+#pragma unroll
+            for (int c = 0; c < KA; ++c) {
+                float2 ml = up1(xm[m][c]), pl = up1(xp[m][c]), mr = dn1(xm[m][c]), pr = dn1(xp[m][c]);
+                const float2 mlc = c > 0 ? shf(xm[m][c > 0 ? c - 1 : 0], 31) : z2;
+                const float2 plc = c > 0 ? shf(xp[m][c > 0 ? c - 1 : 0], 31) : z2;
+                const float2 mrc = c + 1 < KA ? shf(xm[m][c + 1 < KA ? c + 1 : c], 0) : z2;
+                const float2 prc = c + 1 < KA ? shf(xp[m][c + 1 < KA ? c + 1 : c], 0) : z2;
+                if (lane == 0) { ml = mlc; pl = plc; }
+                if (lane == 31) { mr = mrc; pr = prc; }
+                float2 acc = cfma(cwr[c][0], ml, z2);
+                acc = cfma(cwr[c][1], xm[m][c], acc);
+                acc = cfma(cwr[c][2], mr, acc);
+                if (he) {
+                    acc = cfma(cer[c][0], pl, acc);
+                    acc = cfma(cer[c][1], xp[m][c], acc);
+                    acc = cfma(cer[c][2], pr, acc);
+                }
+                const bool live = b < a.nb && 32 * c + lane < q;
+                const float re = live ? tf32_rna(-acc.x) : 0.f, im = live ? tf32_rna(-acc.y) : 0.f;
+                // rows b, NB + b, 2NB + b share (row & 7) (NB is a multiple of 8): NB * 128 bytes apart
+                unsigned char* atom = Bs + (size_t)c * BATOM;
+                const unsigned off = (unsigned)(b >> 3) * 1024u + (unsigned)(b & 7) * 128u +
+                                     (unsigned)(((lane >> 2) ^ (b & 7)) << 4) + (unsigned)(lane & 3) * 4u;
+                *reinterpret_cast<float*>(atom + off) = -im;
+                *reinterpret_cast<float*>(atom + off + NB * 128u) = re;
+                *reinterpret_cast<float*>(atom + off + 2u * NB * 128u) = im;
+            }
         }
     } else {
         // Groups of 4 consecutive rows of one member: one 16-byte chunk of a swizzled atom
