@@ -11,21 +11,20 @@
 //   MODE 4 (level 0 back, odd j)  x_j = x_j + D^{-1} t,  t = -(W x_{j-1} + E x_{j+1})
 //                                 (W, E: the tridiagonal couplings of level 0)
 // With NB right-hand sides this is a complex (q x q) . (q x NB) product per matrix:
-// a dense contraction, done as a real GEMM with M = 128 rows (q <= 112 real ones),
-// N = 2 NB, K = 2 q per matrix:
-//   [D_re | D_im] += M_re [X_re | X_im] + M_im [-X_im | X_re].
+// a dense contraction, done as two real GEMMs with M = 128 rows (q <= 112 real ones),
+// N = 2 NB, K = q per matrix, into two accumulators:
+//   acc0 += M_re [X_re | X_im],  acc1 += M_im [X_re | X_im],
+//   D_re = acc0[:, :NB] - acc1[:, NB:],  D_im = acc0[:, NB:] + acc1[:, :NB].
 // Operand A is a factor matrix: each plane (re, im) stored in TF32 (rounded to
 // nearest once, when factored) already in the tensor cores' 128-byte-swizzled
 // K-major layout -- ceil(q/32) atoms of 32 K-columns x (q rounded up to 8) rows --
 // so a plane is one contiguous bulk copy (cp.async.bulk) from HBM into a ring of
 // plane-sized shared-memory stages; each matrix byte is read once per step for the
 // whole batch.  Operand B is built by the CTA's threads from the vectors (the
-// sign of the step folded in, rounded to TF32): per vector three planes of NB
-// rows [-X_im; X_re; X_im], so that rows [NB, 3NB) are [X_re; X_im] and rows
-// [0, 2NB) are [-X_im; X_re].  One thread issues tcgen05.mma (kind::tf32, K = 8
-// per instruction; K slices past q, all zero, skipped) into a TMEM accumulator of
-// 128 lanes x 2NB FP32 columns; the epilogue reads it back with tcgen05.ld and
-// writes (or adds to) x_j.
+// sign of the step folded in, rounded to TF32): per vector 2NB rows [X_re; X_im].
+// One thread issues tcgen05.mma (kind::tf32, K = 8 per instruction; K slices past q,
+// all zero, skipped) into the TMEM accumulators (128 lanes x 2 x 2NB FP32 columns); the
+// epilogue reads them back with tcgen05.ld and writes (or adds to) x_j.
 // Roles in a CTA of 256 threads: thread 0 loads A planes (bulk copies), thread 32 issues
 // the MMAs, everyone builds B and runs the epilogue.  Every wait is bounded (1 s
 // on %globaltimer); on expiry the step's outputs become NaN and a device counter
@@ -59,30 +58,33 @@ template <int MODE> struct ModeOf {
 };
 
 // Shared memory of one CTA: A ring (S stages of one factor plane each: KA atoms of
-// BR x 128 bytes; the MMA reads 128 rows from an atom's start, so the ring is followed
-// by (128 - BR) rows of slack, and rows past an atom land on the next one: garbage rows
-// of D that are never read) | B (NV vectors x KA atoms x 3NB rows x 128 B) | barriers
-// (full[S], empty[S], done) | TMEM address | failure flag.  S: as many stages as the
-// step's planes, within 110 KB for one-matrix steps (two CTAs per SM) and 225 KB
-// otherwise.
+// BR x 128 bytes) | B (NV vectors x KA atoms x 2NB rows x 128 B) | barriers (full[S],
+// empty[S], done) | TMEM address | failure flag | slack.  The MMA reads 128 rows from
+// an atom's start: rows past an atom land on the next atom, on B or on the slack
+// (garbage rows of D that are never read); the slack makes the ring's last atom plus
+// 128 rows end inside the allocation.  S: as many stages as the step's planes (at most
+// kMaxStages) within the budget: 113 KB when two CTAs share an SM (every one-matrix
+// step, and the steps of levels with more blocks than SMs), 227 KB otherwise.
 constexpr int kMaxStages = 6;
+constexpr int kSmemTwo = 113 * 1024, kSmemOne = 227 * 1024;
 template <int MODE, int NB, int KA>
 struct Cfg {
     static constexpr int NV = ModeOf<MODE>::NV;
-    static constexpr int BBYTES = NV * KA * 3 * NB * 128;
+    static constexpr int BBYTES = NV * KA * 2 * NB * 128;
     static constexpr int NP = 2 * NV;   // planes per step
-    static constexpr int BUDGET = (NV == 1 ? 110 : 225) * 1024 - BBYTES - 1024 - 8 * (2 * kMaxStages + 1) - 16;
+    static constexpr int FIXED = 1024 + 8 * (2 * kMaxStages + 1) + 16;   // alignment, barriers, slot, flags
     static int plane_bytes(int q) { return KA * ((q + 7) / 8 * 8) * 128; }
-    static int slack(int q) { return (128 - (q + 7) / 8 * 8) * 128; }
-    static int stages(int q) {
-        const int fit = (BUDGET - slack(q)) / plane_bytes(q);
-        return fit < NP ? (fit < kMaxStages ? fit : kMaxStages) : (NP < kMaxStages ? NP : kMaxStages);
+    static int slack(int q) {
+        const int over = (128 - (q + 7) / 8 * 8) * 128 - BBYTES - (FIXED - 1024);
+        return over > 0 ? over : 0;
     }
-    static size_t smem(int q) {
-        return 1024 + (size_t)stages(q) * plane_bytes(q) + slack(q) + BBYTES + 8 * (2 * kMaxStages + 1) + 16;
+    static int stages(int q, bool two) {
+        const int fit = ((two ? kSmemTwo : kSmemOne) - FIXED - BBYTES - slack(q)) / plane_bytes(q);
+        const int cap = NP < kMaxStages ? NP : kMaxStages;
+        return fit < cap ? fit : cap;
     }
-    // bound of smem(q) over every q (stages x plane + slack never exceeds BUDGET)
-    static constexpr size_t kMaxSmem = 1024 + (size_t)BUDGET + BBYTES + 8 * (2 * kMaxStages + 1) + 16;
+    static size_t smem(int q, int stages) { return (size_t)FIXED + (size_t)stages * plane_bytes(q) + BBYTES + slack(q); }
+    static constexpr size_t kMaxSmem = kSmemOne;   // bound of smem() for every q and budget
 };
 
 struct StepArgs {
@@ -99,14 +101,14 @@ struct StepArgs {
 };
 
 template <int MODE, int NB, int KA>
-__global__ void __launch_bounds__(kThreads, (ModeOf<MODE>::NV == 1 ? 2 : 1)) k_cr_mma(StepArgs a) {
+__global__ void __launch_bounds__(kThreads, 2) k_cr_mma(StepArgs a) {
     using MO = ModeOf<MODE>;
     constexpr int NV = MO::NV;
     constexpr int KP = 32 * KA;                   // padded K of one plane
-    constexpr int BROWS = 3 * NB;                 // rows of one vector's B atom
+    constexpr int BROWS = 2 * NB;                 // rows of one vector's B atom: [X_re; X_im]
     constexpr unsigned BATOM = BROWS * 128;       // bytes of one vector's B atom
-    constexpr int NCOL = 2 * NB;                  // accumulator columns
-    constexpr int TCOLS = NCOL <= 32 ? 32 : (NCOL <= 64 ? 64 : 128);
+    constexpr int NCOL = 2 * NB;                  // columns of one accumulator
+    constexpr int TCOLS = 2 * NCOL;               // two accumulators: M_re B, M_im B (32, 64 or 128)
     const int q = a.q;
     const int BR = (q + 7) / 8 * 8;
     const int kStages = a.stages;
@@ -114,7 +116,7 @@ __global__ void __launch_bounds__(kThreads, (ModeOf<MODE>::NV == 1 ? 2 : 1)) k_c
     extern __shared__ unsigned char smem_raw[];
     unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     unsigned char* As = base;
-    unsigned char* Bs = As + (size_t)kStages * kPlane + (size_t)(128 - BR) * 128;
+    unsigned char* Bs = As + (size_t)kStages * kPlane;
     auto* full = reinterpret_cast<unsigned long long*>(Bs + (size_t)NV * KA * BATOM);
     auto* empty = full + kMaxStages;
     auto* done = empty + kMaxStages;
@@ -192,7 +194,7 @@ __global__ void __launch_bounds__(kThreads, (ModeOf<MODE>::NV == 1 ? 2 : 1)) k_c
     // completed and its writes are visible.
     asm volatile("griddepcontrol.wait;\n" ::: "memory");
 
-    // B: per vector t, atom at, rows [0,NB) = -X_im, [NB,2NB) = X_re, [2NB,3NB) = X_im (TF32).
+    // B: per vector t, atom at, rows [0,NB) = X_re, [NB,2NB) = X_im (TF32, the step's sign folded in).
     // Every load is issued (at a clamped, valid address) before any value is used, so their
     // latencies overlap; absent vectors, members and padding rows are zeroed afterwards.
     const int nbc = a.nb < 1 ? 0 : a.nb - 1;
@@ -265,18 +267,17 @@ __global__ void __launch_bounds__(kThreads, (ModeOf<MODE>::NV == 1 ? 2 : 1)) k_c
                 }
                 const bool live = b < a.nb && 32 * c + lane < q;
                 const float re = live ? tf32_rna(-acc.x) : 0.f, im = live ? tf32_rna(-acc.y) : 0.f;
-                // rows b, NB + b, 2NB + b share (row & 7) (NB is a multiple of 8): NB * 128 bytes apart
+                // rows b and NB + b share (row & 7) (NB is a multiple of 8): NB * 128 bytes apart
                 unsigned char* atom = Bs + (size_t)c * BATOM;
                 const unsigned off = (unsigned)(b >> 3) * 1024u + (unsigned)(b & 7) * 128u +
                                      (unsigned)(((lane >> 2) ^ (b & 7)) << 4) + (unsigned)(lane & 3) * 4u;
-                *reinterpret_cast<float*>(atom + off) = -im;
-                *reinterpret_cast<float*>(atom + off + NB * 128u) = re;
-                *reinterpret_cast<float*>(atom + off + 2u * NB * 128u) = im;
+                *reinterpret_cast<float*>(atom + off) = re;
+                *reinterpret_cast<float*>(atom + off + NB * 128u) = im;
             }
         }
     } else {
         // Groups of 4 consecutive rows of one member: one 16-byte chunk of a swizzled atom
-        // row, so each of the three B rows takes one 16-byte store.
+        // row, so each of the two B rows takes one 16-byte store.
         constexpr int KG = KP / 4, NG = NB * KG, PERG = (NG + kThreads - 1) / kThreads;
         size_t ob[NV];   // absent vectors read the step's own block (a valid address), then zeroed
 #pragma unroll
@@ -308,9 +309,8 @@ __global__ void __launch_bounds__(kThreads, (ModeOf<MODE>::NV == 1 ? 2 : 1)) k_c
                 const int ch = c4 & 7;   // 16-byte chunk of the 128-byte row in atom c4 / 8
                 unsigned char* row = Bt + (size_t)(c4 >> 3) * BATOM + (size_t)(b >> 3) * 1024u + (size_t)(b & 7) * 128u +
                                      (size_t)((ch ^ (b & 7)) << 4);
-                *reinterpret_cast<float4*>(row) = make_float4(-im[0], -im[1], -im[2], -im[3]);
-                *reinterpret_cast<float4*>(row + NB * 128u) = make_float4(re[0], re[1], re[2], re[3]);
-                *reinterpret_cast<float4*>(row + 2u * NB * 128u) = make_float4(im[0], im[1], im[2], im[3]);
+                *reinterpret_cast<float4*>(row) = make_float4(re[0], re[1], re[2], re[3]);
+                *reinterpret_cast<float4*>(row + NB * 128u) = make_float4(im[0], im[1], im[2], im[3]);
             }
         }
     }
@@ -320,7 +320,7 @@ __global__ void __launch_bounds__(kThreads, (ModeOf<MODE>::NV == 1 ? 2 : 1)) k_c
     if (tid == 32) {   // MMA issuer
         asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
         constexpr unsigned ID = idesc_tf32(128, NCOL);
-        int i = 0, issued = 0;
+        int i = 0, issued[2] = {0, 0};   // MMAs into each accumulator so far
         bool ok = true;
         for (int t = 0; t < NV && ok; ++t) {
             if (!pres[t]) continue;
@@ -335,8 +335,10 @@ __global__ void __launch_bounds__(kThreads, (ModeOf<MODE>::NV == 1 ? 2 : 1)) k_c
                 // descriptors built once per plane; a K slice of 8 TF32 (32 bytes) advances the
                 // start-address field (address / 16) by 2, an atom by its size / 16
                 const unsigned long long ad0 = sdesc(su32(As + (size_t)st * kPlane));
-                // plane re: B rows [NB, 3NB) = [X_re; X_im]; plane im: rows [0, 2NB) = [-X_im; X_re]
-                const unsigned long long bd0 = sdesc(bt + (p == 0 ? (unsigned)NB * 128u : 0u));
+                // plane re into accumulator 0 (M_re [X_re | X_im]), plane im into accumulator 1
+                const unsigned long long bd0 = sdesc(bt);
+                const unsigned dacc = tmem + (unsigned)(p * NCOL);
+                int& iss = issued[p];
 #pragma unroll
                 for (int at = 0; at < KA; ++at) {
                     const unsigned long long ad = ad0 + (unsigned long long)((unsigned)at * (unsigned)BR * 8u);
@@ -344,12 +346,12 @@ __global__ void __launch_bounds__(kThreads, (ModeOf<MODE>::NV == 1 ? 2 : 1)) k_c
                     const int kleft = q - 32 * at;   // K slices of 8 beyond q are zero: skipped
                     if (kleft >= 32) {
 #pragma unroll
-                        for (int k8 = 0; k8 < 4; ++k8, ++issued)
-                            mma_tf32(tmem, ad + 2ull * k8, bd + 2ull * k8, ID, issued ? 1u : 0u);
+                        for (int k8 = 0; k8 < 4; ++k8, ++iss)
+                            mma_tf32(dacc, ad + 2ull * k8, bd + 2ull * k8, ID, iss ? 1u : 0u);
                     } else {
                         const int nk8 = (kleft + 7) / 8;
-                        for (int k8 = 0; k8 < nk8; ++k8, ++issued)
-                            mma_tf32(tmem, ad + 2ull * k8, bd + 2ull * k8, ID, issued ? 1u : 0u);
+                        for (int k8 = 0; k8 < nk8; ++k8, ++iss)
+                            mma_tf32(dacc, ad + 2ull * k8, bd + 2ull * k8, ID, iss ? 1u : 0u);
                     }
                 }
                 mma_commit(&empty[st]);   // the stage is free once these MMAs have read it
@@ -385,22 +387,35 @@ __global__ void __launch_bounds__(kThreads, (ModeOf<MODE>::NV == 1 ? 2 : 1)) k_c
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
     __syncthreads();
     const bool bad = !fin || *failed;
+    // D_re = M_re X_re - M_im X_im = acc0[:, b] - acc1[:, NB + b],
+    // D_im = M_re X_im + M_im X_re = acc0[:, NB + b] + acc1[:, b]
     float dre[HB], dim[HB];
+    const unsigned tl = tmem + ((unsigned)(32 * (warp & 3)) << 16);
+    if constexpr (HB % 8 == 0) {
 #pragma unroll
-    for (int c = 0; c < HB; c += 8) {   // NB >= 16 here; NB = 8 handled by the HB % 8 guard
-        if (c + 8 <= HB) {
-            tmem_ld8(tmem + ((unsigned)(32 * (warp & 3)) << 16) + (unsigned)(half * HB + c), dre + c);
-            tmem_ld8(tmem + ((unsigned)(32 * (warp & 3)) << 16) + (unsigned)(NB + half * HB + c), dim + c);
+        for (int c = 0; c < HB; c += 8) {
+            float rr[8], ri[8], ir[8], ii[8];
+            const unsigned col = (unsigned)(half * HB + c);
+            tmem_ld8(tl + col, rr);
+            tmem_ld8(tl + (unsigned)NB + col, ri);
+            tmem_ld8(tl + (unsigned)NCOL + col, ir);
+            tmem_ld8(tl + (unsigned)(NCOL + NB) + col, ii);
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+                dre[c + e] = rr[e] - ii[e];
+                dim[c + e] = ri[e] + ir[e];
+            }
         }
-    }
-    if constexpr (HB % 8 != 0) {   // NB = 8: each half takes 4 members; read 8 and keep its 4
-        float tr[8], ti[8];
-        tmem_ld8(tmem + ((unsigned)(32 * (warp & 3)) << 16), tr);
-        tmem_ld8(tmem + ((unsigned)(32 * (warp & 3)) << 16) + (unsigned)NB, ti);
+    } else {   // NB = 8: each half takes 4 members; read 8 and keep its 4
+        float rr[8], ri[8], ir[8], ii[8];
+        tmem_ld8(tl, rr);
+        tmem_ld8(tl + (unsigned)NB, ri);
+        tmem_ld8(tl + (unsigned)NCOL, ir);
+        tmem_ld8(tl + (unsigned)(NCOL + NB), ii);
 #pragma unroll
         for (int c = 0; c < HB; ++c) {
-            dre[c] = tr[half * HB + c];
-            dim[c] = ti[half * HB + c];
+            dre[c] = rr[half * HB + c] - ii[half * HB + c];
+            dim[c] = ri[half * HB + c] + ir[half * HB + c];
         }
     }
     if (r < q) {
@@ -466,14 +481,19 @@ int set_smem_all() {
 template <int MODE, int NB, int KA>
 int launch(ls_handle* h, unsigned grid, StepArgs a) {
     using CF = Cfg<MODE, NB, KA>;
-    a.stages = CF::stages(a.q);
+    // two CTAs per SM for one-matrix steps and for levels with more blocks than SMs (one
+    // CTA's operand build and epilogue overlap the other's copies and products); one CTA
+    // with every plane in flight for the small levels
+    const bool two = CF::NV == 1 || (int)grid > h->tc_sms;
+    a.stages = CF::stages(a.q, two);
+    if (a.stages < 1) a.stages = CF::stages(a.q, false);
     if (a.stages < 1) return LS_EINVAL;
     // programmatic stream serialization: the kernel waits (griddepcontrol.wait) for its
     // predecessor before it touches the vectors
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);
     cfg.blockDim = dim3(kThreads);
-    cfg.dynamicSmemBytes = CF::smem(a.q);
+    cfg.dynamicSmemBytes = CF::smem(a.q, a.stages);
     cfg.stream = h->stream;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
@@ -539,6 +559,9 @@ int ls_cr_tc_prepare(ls_handle* h) {
     });
     LS_CUDA(cudaStreamSynchronize(h->stream));
     if (rc != LS_OK) return rc;
+    int dev = 0;
+    LS_CUDA(cudaGetDevice(&dev));
+    LS_CUDA(cudaDeviceGetAttribute(&h->tc_sms, cudaDevAttrMultiProcessorCount, dev));
     h->tc_ready = true;
     return LS_OK;
 }
@@ -552,7 +575,7 @@ void ls_cr_tc_free(ls_handle* h) {
 }
 
 // Largest batch one tensor-core step takes (the B operand of 32 right-hand sides and
-// three vectors fills most of the shared memory).
+// three vectors takes a third of the shared memory).
 int ls_cr_tc_max_nb(const ls_handle*) { return 32; }
 
 int ls_cr_tc_timeouts(unsigned* count) {

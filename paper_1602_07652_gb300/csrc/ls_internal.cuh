@@ -259,6 +259,7 @@ struct ls_handle {
     int bd_chunk = 0;          // right-hand sides per Algorithm 2 chain (0: the largest supported)
     int cr_split = 1;          // 1: reduction steps of small levels split blocks over several CTAs
     bool tc_ready = false;     // LS_MIXED: TF32 factor planes and tensor maps built (ls_cr_tc_prepare)
+    int tc_sms = 0;            // SMs of the device (tensor-core steps: CTAs per SM by level size)
     int cr_tc = 1;             // FP32 reduction steps on the tensor cores when tc_ready: 0 never,
                                // 1 for batches of 5 or more right-hand sides, 2 always
 
