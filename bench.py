@@ -105,8 +105,8 @@ def config_dict(wl, prec="mixed", rhs_per_step=1):
                         % (wl["n"], wl["n"], wl["omega"] / (2 * math.pi), wl["layers"], wl["ext"], prec, wl["tol"],
                            per),
             "rhs_per_step": rhs_per_step, "restarts": {"outer": 10, "inner": 10}, "n": wl["n"], "omega": wl["omega"], "layers": wl["layers"], "ext": wl["ext"], "tol": wl["tol"],
-            "l2": "inputs larger than L2: every sweep streams ~%.0f GB of local-solve factors" %
-                  (4 * wl["layers"] * wl["n"] * (wl["n"] // wl["layers"] + 2 * wl["ext"]) ** 2 * 8 * 1.75 / 1e9),
+            "l2": "inputs larger than L2: every Algorithm 2 streams ~%.0f GB of local-solve factors" %
+                  (4 * wl["layers"] * wl["n"] * (wl["n"] // wl["layers"] + 2 * wl["ext"]) ** 2 * 8 * 3.5 / 1e9),
             "parallelism": "replicas"}
 
 
