@@ -253,6 +253,18 @@ int ls_set_shapes(ls_handle* h, int fft_variant, int bd_chunk);
  * not built (LS_FP64, before ls_factor, or q > 112); LS_EINVAL for other values. */
 int ls_set_tensor_steps(ls_handle* h, int on);
 
+/* ls_set_reduced_inverse -- LS_MIXED, tensor-core local solves (Sec. 3.4; factors of
+ * Sec. 4.1): the block-cyclic-reduction steps of the levels at and above the first level
+ * with at most 32 blocks (its even-block reductions, the top block and the back
+ * substitution down to it) form one linear map, the inverse of that level's reduced
+ * system.  ls_factor precomputes it per strip (those steps applied to the identity's
+ * columns, stored as TF32 planes: (32 q)^2 complex values per strip) and on = 1 (the
+ * default) applies it as one tensor-core product instead of those steps; on = 0 runs the
+ * steps.  Both round to TF32; they differ by that rounding (the inverse is rounded once
+ * more).  Synchronises the stream and drops the captured sweep graphs on a change.
+ * LS_EINVAL for other values of on. */
+int ls_set_reduced_inverse(ls_handle* h, int on);
+
 /* ls_set_reduction -- pin the form of the block-cyclic-reduction local solves of
  * Algorithm 1 (Sec. 3.4): cr_split 1 lets the steps of levels with fewer blocks
  * than SMs split each block's columns over several CTAs, 0 keeps one CTA per block

@@ -89,6 +89,7 @@ _SIGS = {
     "ls_set_shapes": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int]),
     "ls_set_reduction": (ctypes.c_int, [_P, ctypes.c_int]),
     "ls_set_tensor_steps": (ctypes.c_int, [_P, ctypes.c_int]),
+    "ls_set_reduced_inverse": (ctypes.c_int, [_P, ctypes.c_int]),
     "ls_check_conversions": (ctypes.c_int, [_P, _P, ctypes.c_longlong, ctypes.POINTER(ctypes.c_ulonglong)]),
     "ls_device_timeouts": (ctypes.c_int, [ctypes.POINTER(ctypes.c_uint)]),
     "ls_test_tma_shortfall": (ctypes.c_int, [ctypes.c_uint]),
@@ -419,6 +420,9 @@ class Solver:
 
     def ls_set_tensor_steps(self, on):
         _ck(self._lib.ls_set_tensor_steps(self._h, int(on)), "ls_set_tensor_steps")
+
+    def ls_set_reduced_inverse(self, on):
+        _ck(self._lib.ls_set_reduced_inverse(self._h, int(on)), "ls_set_reduced_inverse")
 
     def ls_autotune(self, nrhs=1, reps=3):
         t = Tuning()

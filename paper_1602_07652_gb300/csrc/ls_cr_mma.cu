@@ -461,10 +461,228 @@ __global__ void k_pack_tc(size_t nmat, int q, int KA, int BR, const float2* __re
     }
 }
 
+// ------------------------------------------------------------------ reduced-system inverse
+// The steps of levels k >= c of a local solve -- the even-block reductions of levels c..K-1,
+// the top block and the back substitution down to level c (Sec. 3.4 local solves, factors
+// of Sec. 4.1) -- touch only the level-c blocks (strip blocks j 2^c) and map the values
+// there linearly to the solution there: x_c = S_c^{-1} b_c, S_c the reduced block-
+// tridiagonal system of level c, nc = blocks x q unknowns.  For the first level with at
+// most kDenseBlocks blocks that inverse is precomputed (the same steps run on the columns of
+// the identity) and stored as TF32 planes in blocks of 128 rows x 128 columns,
+// [strip][row tile mt][column chunk kc][plane re, im][4 atoms][128 rows][32], each block
+// already in the swizzled K-major layout of the MMA operand A.  A local solve then applies
+// it as one product: one CTA per (column chunk, row tile) multiplies its block by the
+// batch's values at its 128 columns and writes a partial product; a second kernel adds the
+// chunks' partials in the fixed order kc = 0, 1, ... and writes the level-c blocks.
+constexpr int kDenseBlocks = 32, kDenseKC = 128, kDenseAtoms = kDenseKC / 32;
+constexpr unsigned kDensePlane = kDenseAtoms * 128u * 128u;   // bytes of one plane of a block
+
+struct DenseArgs {
+    const float* A;      // this strip's blocks
+    int nc, ks, q, c;    // unknowns, column chunks, block height, level
+    const float2* x;     // strip vectors, member b at + b * SB (level-c block j at (j << c) * q)
+    size_t SB;
+    int nb;              // members present
+    float2* part;        // [kc][NB][rows] partial products
+    int rows;            // row tiles x 128
+};
+
+template <int NB>
+constexpr size_t dense_smem() {
+    return 1024 + 2 * (size_t)kDensePlane + (size_t)kDenseAtoms * 2 * NB * 128 + 8 * 3 + 16;
+}
+
+template <int NB>
+__global__ void __launch_bounds__(kThreads, 1) k_dense_mma(DenseArgs a) {
+    constexpr int NCOL = 2 * NB, TCOLS = 2 * NCOL;
+    constexpr unsigned BATOM = 2 * NB * 128;
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    unsigned char* As = base;                       // planes re, im of block (mt, kc)
+    unsigned char* Bs = As + 2 * kDensePlane;       // 4 atoms x 2NB rows [X_re; X_im]
+    auto* full = reinterpret_cast<unsigned long long*>(Bs + kDenseAtoms * BATOM);
+    auto* done = full + 2;
+    unsigned* tslot = reinterpret_cast<unsigned*>(done + 1);
+    int* failed = reinterpret_cast<int*>(tslot + 1);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int kc = blockIdx.x, mt = blockIdx.y;
+    asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
+    if (tid == 0) {
+        *failed = 0;
+        bar_init(&full[0], 1);
+        bar_init(&full[1], 1);
+        bar_init(done, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+    }
+    if (warp == 0) tmem_alloc(tslot, TCOLS);
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const unsigned tmem = *tslot;
+    if (tid == 0) {   // the block's two planes (constant data: before the predecessor completes)
+        const float* src = a.A + ((size_t)mt * a.ks + kc) * 2 * (kDensePlane / 4);
+        for (int p = 0; p < 2; ++p) {
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(su32(&full[p])),
+                         "r"(kDensePlane)
+                         : "memory");
+            bulk_load(As + (size_t)p * kDensePlane, src + (size_t)p * (kDensePlane / 4), kDensePlane, &full[p]);
+        }
+    }
+    asm volatile("griddepcontrol.wait;\n" ::: "memory");
+
+    // B: column col = 128 kc + kk is unknown (block col / q, row col % q) of level c
+    constexpr int PER = NB * kDenseKC / kThreads;
+    const int nbc = a.nb < 1 ? 0 : a.nb - 1;
+    float2 v[PER];
+#pragma unroll
+    for (int u = 0; u < PER; ++u) {
+        const int o = tid + u * kThreads, b = o / kDenseKC, kk = o % kDenseKC;
+        int col = kc * kDenseKC + kk;
+        col = col < a.nc ? col : a.nc - 1;
+        const int jb = col / a.q, r = col - jb * a.q;
+        v[u] = a.x[(size_t)(b < a.nb ? b : nbc) * a.SB + ((size_t)jb << a.c) * a.q + r];
+    }
+#pragma unroll
+    for (int u = 0; u < PER; ++u) {
+        const int o = tid + u * kThreads, b = o / kDenseKC, kk = o % kDenseKC;
+        const bool live = b < a.nb && kc * kDenseKC + kk < a.nc;
+        const float re = live ? tf32_rna(v[u].x) : 0.f, im = live ? tf32_rna(v[u].y) : 0.f;
+        const int k32 = kk & 31;
+        unsigned char* atom = Bs + (size_t)(kk >> 5) * BATOM;
+        const unsigned off = (unsigned)(b >> 3) * 1024u + (unsigned)(b & 7) * 128u +
+                             (unsigned)(((k32 >> 2) ^ (b & 7)) << 4) + (unsigned)(k32 & 3) * 4u;
+        *reinterpret_cast<float*>(atom + off) = re;
+        *reinterpret_cast<float*>(atom + off + NB * 128u) = im;
+    }
+    fence_async_smem();
+    __syncthreads();
+
+    if (tid == 32) {   // MMA issuer: plane re into accumulator 0, plane im into accumulator 1
+        fence_after();
+        constexpr unsigned ID = idesc_tf32(128, NCOL);
+        bool ok = true;
+        const unsigned long long bd0 = sdesc(su32(Bs));
+        for (int p = 0; p < 2 && ok; ++p) {
+            if (!bar_wait(&full[p], 0u)) {
+                ok = false;
+                break;
+            }
+            fence_after();
+            const unsigned long long ad0 = sdesc(su32(As + (size_t)p * kDensePlane));
+            const unsigned dacc = tmem + (unsigned)(p * NCOL);
+#pragma unroll
+            for (int at = 0; at < kDenseAtoms; ++at)
+#pragma unroll
+                for (int k8 = 0; k8 < 4; ++k8)
+                    mma_tf32(dacc, ad0 + (unsigned long long)(at * 1024 + 2 * k8),
+                             bd0 + (unsigned long long)(at * (BATOM >> 4) + 2 * k8), ID, (at | k8) ? 1u : 0u);
+        }
+        if (!ok) atomicOr(failed, 1);
+        mma_commit(done);
+    }
+    const int r = 32 * (warp & 3) + lane;
+    const int half = warp >> 2;
+    constexpr int HB = NB / 2;
+    const bool fin = bar_wait(done, 0);
+    fence_after();
+    __syncthreads();
+    const bool bad = !fin || *failed;
+    float dre[HB], dim[HB];
+    const unsigned tl = tmem + ((unsigned)(32 * (warp & 3)) << 16);
+    if constexpr (HB % 8 == 0) {
+#pragma unroll
+        for (int c = 0; c < HB; c += 8) {
+            float rr[8], ri[8], ir[8], ii[8];
+            const unsigned col = (unsigned)(half * HB + c);
+            tmem_ld8(tl + col, rr);
+            tmem_ld8(tl + (unsigned)NB + col, ri);
+            tmem_ld8(tl + (unsigned)NCOL + col, ir);
+            tmem_ld8(tl + (unsigned)(NCOL + NB) + col, ii);
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+                dre[c + e] = rr[e] - ii[e];
+                dim[c + e] = ri[e] + ir[e];
+            }
+        }
+    } else {
+        float rr[8], ri[8], ir[8], ii[8];
+        tmem_ld8(tl, rr);
+        tmem_ld8(tl + (unsigned)NB, ri);
+        tmem_ld8(tl + (unsigned)NCOL, ir);
+        tmem_ld8(tl + (unsigned)(NCOL + NB), ii);
+#pragma unroll
+        for (int c = 0; c < HB; ++c) {
+            dre[c] = rr[half * HB + c] - ii[half * HB + c];
+            dim[c] = ri[half * HB + c] + ir[half * HB + c];
+        }
+    }
+    const int row = mt * 128 + r;
+    if (row < a.nc) {
+        float2* pp = a.part + (size_t)kc * NB * a.rows + row;
+        const float2 nan2 = make_float2(__int_as_float(0x7fc00000), __int_as_float(0x7fc00000));
+#pragma unroll
+        for (int c = 0; c < HB; ++c) {
+            const int b = half * HB + c;
+            if (b < a.nb) pp[(size_t)b * a.rows] = bad ? nan2 : make_float2(dre[c], dim[c]);
+        }
+    }
+    if (bad && tid == 0) atomicAdd(&g_cr_timeouts, 1u);
+    fence_before();
+    __syncthreads();
+    if (warp == 0) tmem_dealloc(tmem, TCOLS);
+}
+
+// x at the level-c blocks = the sum of the column chunks' partial products (fixed order)
+__global__ void k_dense_sum(const float2* __restrict__ part, int ks, int nbt, int rows, int nc, int q, int c,
+                            float2* __restrict__ x, size_t SB) {
+    const int row = blockIdx.x * blockDim.x + threadIdx.x, b = blockIdx.y;
+    if (row >= nc) return;
+    float2 sum = make_float2(0.f, 0.f);
+    for (int k = 0; k < ks; ++k) {
+        const float2 v = part[((size_t)k * nbt + b) * rows + row];
+        sum = make_float2(sum.x + v.x, sum.y + v.y);
+    }
+    const int jb = row / q, r = row - jb * q;
+    x[(size_t)b * SB + ((size_t)jb << c) * q + r] = sum;
+}
+
+// set-up: member b of the batch = column col0 + b of the identity (level-c unknowns)
+__global__ void k_dense_identity(float2* x, size_t SB, int q, int c, int nc, int col0, int nbm) {
+    const int b = threadIdx.x, col = col0 + b;
+    if (b >= nbm || col >= nc) return;
+    const int jb = col / q, r = col - jb * q;
+    x[(size_t)b * SB + ((size_t)jb << c) * q + r] = make_float2(1.f, 0.f);
+}
+
+// set-up: the solutions of the identity columns -> columns col0.. of the inverse, as TF32
+// planes in the block layout (rows and columns past nc stay zero)
+__global__ void k_dense_pack(const float2* __restrict__ x, size_t SB, int q, int c, int nc, int col0, int nbm, int ks,
+                             float* __restrict__ A) {
+    const size_t total = (size_t)nbm * nc;
+    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+        const int b = (int)(e / nc), row = (int)(e % nc), col = col0 + b;
+        if (col >= nc) continue;
+        const int jb = row / q, r = row - jb * q;
+        const float2 v = x[(size_t)b * SB + ((size_t)jb << c) * q + r];
+        const int mt = row >> 7, rr = row & 127, kc = col >> 7, kk = col & 127;
+        float* blk = A + ((size_t)mt * ks + kc) * 2 * (kDensePlane / 4);
+        const size_t off = (size_t)(kk >> 5) * (128 * 32) + swz(rr, kk & 31) / 4;
+        blk[off] = tf32_rna(v.x);
+        blk[kDensePlane / 4 + off] = tf32_rna(v.y);
+    }
+}
+
 template <int MODE, int NB, int KA>
 int set_smem() {
     const size_t sz = Cfg<MODE, NB, KA>::kMaxSmem;
     LS_CUDA(cudaFuncSetAttribute(k_cr_mma<MODE, NB, KA>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sz));
+    return LS_OK;
+}
+
+template <int NB>
+int set_smem_dense() {
+    LS_CUDA(cudaFuncSetAttribute(k_dense_mma<NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dense_smem<NB>()));
     return LS_OK;
 }
 
@@ -529,6 +747,70 @@ int launch_ka(ls_handle* h, int mode, unsigned grid, const StepArgs& a) {
 
 }  // namespace
 
+// The inverse of each strip's reduced system at the first level with at most
+// kDenseBlocks blocks, from the tensor-core steps of the levels above it applied to the
+// identity's columns, 32 at a time (called once the TF32 planes exist).
+static int dense_prepare(ls_handle* h) {
+    const int q = h->q, n = h->n;
+    const size_t SB = (size_t)n * q;
+    float2* xt = nullptr;
+    for (int d = 0; d < 2; ++d) {
+        DirFactors& F = h->fac[d];
+        cudaFree(F.dense_tc);
+        F.dense_tc = nullptr;
+        F.dense_nc = 0;
+        int c = 0;
+        for (int k = 1; k < F.K; ++k)
+            if (F.lev[k].nk <= kDenseBlocks) {
+                c = k;
+                break;
+            }
+        if (!c) continue;   // no level small enough (or a single level): the steps stay
+        const int nc = F.lev[c].nk * q, mt = (nc + 127) / 128, ks = (nc + kDenseKC - 1) / kDenseKC;
+        const size_t per_strip = (size_t)mt * ks * 2 * (kDensePlane / 4);   // floats
+        LS_CUDA(cudaMalloc(&F.dense_tc, sizeof(float) * per_strip * h->L));
+        LS_CUDA(cudaMemsetAsync(F.dense_tc, 0, sizeof(float) * per_strip * h->L, h->stream));
+        if (!xt) LS_CUDA(cudaMalloc(&xt, sizeof(float2) * SB * 32));
+        for (int l = 0; l < h->L; ++l) {
+            const float2* cw = static_cast<const float2*>(F.cw) + (size_t)l * n * 3 * q;
+            const float2* ce = static_cast<const float2*>(F.ce) + (size_t)l * n * 3 * q;
+            for (int col0 = 0; col0 < nc; col0 += 32) {
+                const int nbm = nc - col0 < 32 ? nc - col0 : 32;
+                LS_CUDA(cudaMemsetAsync(xt, 0, sizeof(float2) * SB * nbm, h->stream));
+                LS_LAUNCH(h, k_dense_identity, 1, 32, 0, xt, SB, q, c, nc, col0, nbm);
+                for (int k = c; k < F.K; ++k) {
+                    const CrLevel& lv = F.lev[k];
+                    LS_TRY(ls_cr_tc_step(h, d, l, 1, k, lv.nk, (unsigned)lv.neven, 0, lv.off_f, lv.off_g, xt, SB, nbm,
+                                         cw, ce));
+                }
+                LS_TRY(ls_cr_tc_step(h, d, l, 3, 0, 1, 1u, F.off_top, 0, 0, xt, SB, nbm, cw, ce));
+                for (int k = F.K - 1; k >= c; --k) {
+                    const CrLevel& lv = F.lev[k];
+                    if (!lv.nodd) continue;
+                    LS_TRY(ls_cr_tc_step(h, d, l, 2, k, lv.nk, (unsigned)lv.nodd, lv.off_dinv, lv.off_p, lv.off_q, xt,
+                                         SB, nbm, cw, ce));
+                }
+                LS_LAUNCH(h, k_dense_pack, 304, 256, 0, xt, SB, q, c, nc, col0, nbm, ks,
+                          F.dense_tc + per_strip * l);
+            }
+        }
+        F.dense_c = c;
+        F.dense_nc = nc;
+        F.dense_mt = mt;
+        F.dense_ks = ks;
+    }
+    LS_CUDA(cudaStreamSynchronize(h->stream));
+    cudaFree(xt);
+    // every lane's buffer of partial products (the lanes run Algorithm 2 chunks concurrently)
+    const size_t e = ls_cr_dense_part_elems(h);
+    for (auto& W : h->lanes) {
+        cudaFree(W.dense_part);
+        W.dense_part = nullptr;
+        if (e) LS_CUDA(cudaMalloc(&W.dense_part, sizeof(float2) * e));
+    }
+    return LS_OK;
+}
+
 // The TF32 planes of both directions' factors (after ls_factor, LS_MIXED): per matrix
 // two planes of KA = ceil(q/32) atoms of BR = q rounded up to 8 rows x 32 K-columns,
 // already in the tensor cores' swizzled layout.
@@ -555,6 +837,8 @@ int ls_cr_tc_prepare(ls_handle* h) {
         all([] { return set_smem_all<16, 3>(); }); all([] { return set_smem_all<16, 4>(); });
         all([] { return set_smem_all<32, 1>(); }); all([] { return set_smem_all<32, 2>(); });
         all([] { return set_smem_all<32, 3>(); }); all([] { return set_smem_all<32, 4>(); });
+        all([] { return set_smem_dense<8>(); });   all([] { return set_smem_dense<16>(); });
+        all([] { return set_smem_dense<32>(); });
         rc = r;
     });
     LS_CUDA(cudaStreamSynchronize(h->stream));
@@ -563,13 +847,16 @@ int ls_cr_tc_prepare(ls_handle* h) {
     LS_CUDA(cudaGetDevice(&dev));
     LS_CUDA(cudaDeviceGetAttribute(&h->tc_sms, cudaDevAttrMultiProcessorCount, dev));
     h->tc_ready = true;
-    return LS_OK;
+    return dense_prepare(h);
 }
 
 void ls_cr_tc_free(ls_handle* h) {
     for (int d = 0; d < 2; ++d) {
         cudaFree(h->fac[d].pool_tc);
         h->fac[d].pool_tc = nullptr;
+        cudaFree(h->fac[d].dense_tc);
+        h->fac[d].dense_tc = nullptr;
+        h->fac[d].dense_nc = 0;
     }
     h->tc_ready = false;
 }
@@ -593,4 +880,56 @@ int ls_cr_tc_step(ls_handle* h, int dir, int l, int mode, int k, int nk, unsigne
     if (nb <= 16) return launch_ka<16>(h, mode, grid, a);
     if (nb <= 32) return launch_ka<32>(h, mode, grid, a);
     return LS_EINVAL;
+}
+
+// float2 entries of a lane's partial-product buffer for the reduced inverse (0: not built)
+size_t ls_cr_dense_part_elems(const ls_handle* h) {
+    size_t e = 0;
+    for (int d = 0; d < 2; ++d) {
+        const DirFactors& F = h->fac[d];
+        if (!F.dense_nc) continue;
+        const size_t need = (size_t)F.dense_ks * 32 * F.dense_mt * 128;
+        e = need > e ? need : e;
+    }
+    return e;
+}
+
+// Levels >= c of the local solve of strip l as one product with the reduced inverse: the
+// values at the level-c blocks of x (nb <= 32 members) are replaced by the solution there.
+int ls_cr_dense_apply(ls_handle* h, int dir, int l, float2* x, size_t SB, int nb) {
+    const DirFactors& F = h->fac[dir];
+    const ls_handle::SweepLane& W = h->lanes[h->lane];
+    if (!F.dense_nc || !W.dense_part || nb < 1 || nb > 32) return LS_ESTATE;
+    const size_t per_strip = (size_t)F.dense_mt * F.dense_ks * 2 * (kDensePlane / 4);
+    DenseArgs a{F.dense_tc + per_strip * l, F.dense_nc, F.dense_ks, h->q, F.dense_c, x, SB, nb, W.dense_part,
+                F.dense_mt * 128};
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)F.dense_ks, (unsigned)F.dense_mt);
+    cfg.blockDim = dim3(kThreads);
+    cfg.stream = h->stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaError_t e;
+    int nbt;
+    if (nb <= 8) {
+        cfg.dynamicSmemBytes = dense_smem<8>();
+        e = cudaLaunchKernelEx(&cfg, k_dense_mma<8>, a);
+        nbt = 8;
+    } else if (nb <= 16) {
+        cfg.dynamicSmemBytes = dense_smem<16>();
+        e = cudaLaunchKernelEx(&cfg, k_dense_mma<16>, a);
+        nbt = 16;
+    } else {
+        cfg.dynamicSmemBytes = dense_smem<32>();
+        e = cudaLaunchKernelEx(&cfg, k_dense_mma<32>, a);
+        nbt = 32;
+    }
+    h->launches++;
+    if (e != cudaSuccess) return ls_cuda_fail(e);
+    LS_LAUNCH(h, k_dense_sum, dim3((unsigned)((F.dense_nc + 255) / 256), (unsigned)nb), 256, 0, W.dense_part,
+              F.dense_ks, nbt, F.dense_mt * 128, F.dense_nc, h->q, F.dense_c, x, SB);
+    return LS_OK;
 }

@@ -170,6 +170,12 @@ struct DirFactors {
     // in the tensor cores' 128-byte-swizzled K-major layout (ceil(q/32) atoms of 32
     // K-columns x q rounded up to 8 rows each), so a plane is one contiguous copy
     float* pool_tc = nullptr;
+    // LS_MIXED, tensor-core steps: the inverse of the reduced system of level dense_c (the
+    // first level with at most 32 blocks), nc = blocks x q unknowns, per strip as TF32
+    // planes in blocks of 128 rows x 128 columns (mt row tiles x ks column chunks), so the
+    // levels >= dense_c of a local solve are one dense product (ls_cr_dense_apply)
+    float* dense_tc = nullptr;
+    int dense_c = 0, dense_nc = 0, dense_mt = 0, dense_ks = 0;
     // problem of this direction (the vertical direction is the transposed grid)
     const double* m = nullptr;    // medium of this direction's grid (n x n, long axis fastest)
     StencilTables* tab = nullptr; // device copy of the tables of this direction
@@ -232,6 +238,7 @@ struct ls_handle {
         int nb_cap = 0;
         void* cr_part = nullptr;        // partial sums of split reduction steps
         unsigned* cr_cnt = nullptr;     // arrival counters of split reduction steps (kept at 0)
+        float2* dense_part = nullptr;   // column-chunk partial products of the reduced inverse
         cudaStream_t stream = nullptr;  // lane 0 runs on the handle's stream
         cudaEvent_t done = nullptr;
     };
@@ -260,6 +267,7 @@ struct ls_handle {
     int cr_split = 1;          // 1: reduction steps of small levels split blocks over several CTAs
     bool tc_ready = false;     // LS_MIXED: TF32 factor planes and tensor maps built (ls_cr_tc_prepare)
     int tc_sms = 0;            // SMs of the device (tensor-core steps: CTAs per SM by level size)
+    int tc_dense = 1;          // tensor-core local solves: levels with <= 32 blocks as one dense product
     int cr_tc = 1;             // FP32 reduction steps on the tensor cores when tc_ready: 0 never,
                                // 1 for batches of 5 or more right-hand sides, 2 always
 
@@ -354,6 +362,8 @@ int ls_cr_tc_timeouts(unsigned* count);
 int ls_conv_timeouts(unsigned* count);   // tensor-core convolutions of the learned step (ls_unet.cu)
 int ls_cr_tc_step(ls_handle* h, int dir, int l, int mode, int k, int nk, unsigned grid, size_t off_a, size_t off_b,
                   size_t off_c, float2* x, size_t SB, int nb, const float2* cw, const float2* ce);
+size_t ls_cr_dense_part_elems(const ls_handle* h);   // float2 entries of a lane's dense_part (0: no dense form)
+int ls_cr_dense_apply(ls_handle* h, int dir, int l, float2* x, size_t SB, int nb);
 
 // Krylov (ls_krylov.cu)
 int ls_inner_gmres(ls_handle* h, const double2* g, double tol, double2* v, int* iters);

@@ -484,14 +484,18 @@ int cr_solve_tc(ls_handle* h, int dir, int l, float2* x, size_t SB, int nb) {
     const float2* cw = static_cast<const float2*>(F.cw) + (size_t)l * n * 3 * q;
     const float2* ce = static_cast<const float2*>(F.ce) + (size_t)l * n * 3 * q;
     const int thr = (q + 31) / 32 * 32;
+    // levels >= dense_c as one product with the reduced system's inverse, where it is built
+    const bool dense = h->tc_dense && F.dense_nc && h->lanes[h->lane].dense_part;
+    const int ktop = dense ? F.dense_c : F.K;
     if (l0.nodd) LS_TRY(ls_cr_tc_step(h, dir, l, 0, 0, l0.nk, (unsigned)l0.nodd, l0.off_dinv, 0, 0, x, SB, nb, cw, ce));
     LS_LAUNCH(h, k_l0_even<float>, dim3(l0.neven, nb), thr, 0, q, n, cw, ce, x, SB);
-    for (int k = 1; k < F.K; ++k) {
+    for (int k = 1; k < ktop; ++k) {
         const CrLevel& lv = F.lev[k];
         LS_TRY(ls_cr_tc_step(h, dir, l, 1, k, lv.nk, (unsigned)lv.neven, 0, lv.off_f, lv.off_g, x, SB, nb, cw, ce));
     }
-    LS_TRY(ls_cr_tc_step(h, dir, l, 3, 0, 1, 1u, F.off_top, 0, 0, x, SB, nb, cw, ce));
-    for (int k = F.K - 1; k >= 1; --k) {
+    if (dense) LS_TRY(ls_cr_dense_apply(h, dir, l, x, SB, nb));
+    else LS_TRY(ls_cr_tc_step(h, dir, l, 3, 0, 1, 1u, F.off_top, 0, 0, x, SB, nb, cw, ce));
+    for (int k = ktop - 1; k >= 1; --k) {
         const CrLevel& lv = F.lev[k];
         if (!lv.nodd) continue;
         LS_TRY(ls_cr_tc_step(h, dir, l, 2, k, lv.nk, (unsigned)lv.nodd, lv.off_dinv, lv.off_p, lv.off_q, x, SB, nb, cw,
@@ -624,7 +628,7 @@ int ls_sweep_reserve(ls_handle* h, int nb) {
 void ls_lanes_free(ls_handle* h) {
     for (auto& W : h->lanes) {
         lane_graphs_free(W);
-        void* ptrs[] = {W.srhs, W.ssol, W.strace, W.vtmp, W.bd_in, W.bd_out, W.cr_part, W.cr_cnt};
+        void* ptrs[] = {W.srhs, W.ssol, W.strace, W.vtmp, W.bd_in, W.bd_out, W.cr_part, W.cr_cnt, W.dense_part};
         for (void* p : ptrs) cudaFree(p);
         if (W.stream) cudaStreamDestroy(W.stream);
         if (W.done) cudaEventDestroy(W.done);

@@ -159,3 +159,13 @@ extern "C" int ls_set_tensor_steps(ls_handle* h, int on) {
     }
     return LS_OK;
 }
+
+extern "C" int ls_set_reduced_inverse(ls_handle* h, int on) {
+    if (!h || on < 0 || on > 1) return LS_EINVAL;
+    if (h->tc_dense != on) {
+        LS_CUDA(cudaStreamSynchronize(h->stream));
+        h->tc_dense = on;
+        ls_bd_graph_free(h);
+    }
+    return LS_OK;
+}
