@@ -638,10 +638,16 @@ __global__ void k_dense_sum(const float2* __restrict__ part, int ks, int nbt, in
                             float2* __restrict__ x, size_t SB) {
     const int row = blockIdx.x * blockDim.x + threadIdx.x, b = blockIdx.y;
     if (row >= nc) return;
+    // the chunks in groups of 8: the group's loads are issued together, then added in order
     float2 sum = make_float2(0.f, 0.f);
-    for (int k = 0; k < ks; ++k) {
-        const float2 v = part[((size_t)k * nbt + b) * rows + row];
-        sum = make_float2(sum.x + v.x, sum.y + v.y);
+    for (int k0 = 0; k0 < ks; k0 += 8) {
+        float2 v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+            v[u] = k0 + u < ks ? part[((size_t)(k0 + u) * nbt + b) * rows + row] : make_float2(0.f, 0.f);
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+            if (k0 + u < ks) sum = make_float2(sum.x + v[u].x, sum.y + v[u].y);
     }
     const int jb = row / q, r = row - jb * q;
     x[(size_t)b * SB + ((size_t)jb << c) * q + r] = sum;

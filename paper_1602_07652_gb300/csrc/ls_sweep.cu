@@ -282,8 +282,11 @@ __global__ void k_l0_even(int q, int nblk, const cpx_t<T>* __restrict__ cw, cons
 // reads the rows of g that fall in Omega^l along x (coalesced) into shared memory and
 // writes the strip's block layout (column i = q contiguous values) along r (coalesced).
 // The injected rows (eq. pde_GRF_down) are computed in the strip's precision.
+// TR: g is the field of the other direction (the vertical layers' grid is the transpose
+// of the field's): strip row r, column i is g[i][l t - E + r], contiguous along r, so the
+// reads go straight to the strip layout without the shared-memory tile.
 constexpr int kGatherTile = 32;
-template <typename T>
+template <typename T, bool TR>
 __global__ void __launch_bounds__(256) k_gather(StripGeom g, const cpx_t<T>* __restrict__ inj, int l,
                                                 const double2* __restrict__ gf, cpx_t<T>* __restrict__ rhs,
                                                 cpx_t<T>* __restrict__ sol, const cpx_t<T>* __restrict__ above,
@@ -302,20 +305,28 @@ __global__ void __launch_bounds__(256) k_gather(StripGeom g, const cpx_t<T>* __r
     }
     const int tx = threadIdx.x, ty = threadIdx.y;
     double2 v[kGatherTile / 8];
+    if constexpr (TR) {
 #pragma unroll
-    for (int u = 0; u < kGatherTile / 8; ++u) {   // rows of Omega^l (E <= r < E + t), along x
-        const int r = r0 + ty + 8 * u, i = i0 + tx;
-        v[u] = (r >= E && r < E + t && i < n) ? __ldg(&gf[(size_t)(l * t - E + r) * n + i]) : make_double2(0.0, 0.0);
+        for (int u = 0; u < kGatherTile / 8; ++u) {   // rows of Omega^l (E <= r < E + t), along r
+            const int i = i0 + ty + 8 * u, r = r0 + tx;
+            v[u] = (r >= E && r < E + t && i < n) ? __ldg(&gf[(size_t)i * n + (l * t - E + r)]) : make_double2(0.0, 0.0);
+        }
+    } else {
+#pragma unroll
+        for (int u = 0; u < kGatherTile / 8; ++u) {   // rows of Omega^l (E <= r < E + t), along x
+            const int r = r0 + ty + 8 * u, i = i0 + tx;
+            v[u] = (r >= E && r < E + t && i < n) ? __ldg(&gf[(size_t)(l * t - E + r) * n + i]) : make_double2(0.0, 0.0);
+        }
+#pragma unroll
+        for (int u = 0; u < kGatherTile / 8; ++u) tile[ty + 8 * u][tx] = ccast<C>(v[u]);
+        __syncthreads();
     }
-#pragma unroll
-    for (int u = 0; u < kGatherTile / 8; ++u) tile[ty + 8 * u][tx] = ccast<C>(v[u]);
-    __syncthreads();
 #pragma unroll
     for (int u = 0; u < kGatherTile / 8; ++u) {   // strip columns, along r
         const int i = i0 + ty + 8 * u, r = r0 + tx;
         if (i >= n || r >= q) continue;
         const size_t e = (size_t)i * q + r;
-        C cv = tile[tx][ty + 8 * u];
+        C cv = TR ? ccast<C>(v[u]) : tile[tx][ty + 8 * u];
         if (above) {
             if (r == 0) trace_above[i] = above[(size_t)i * q + E - 1];  // w^{l+1}_0, kept for the upward sweep
             const C* c0 = inj + (size_t)l * 12 * n;  // slots 0, 1 of layer l: [slot][dx+1][i]
@@ -382,6 +393,22 @@ __global__ void k_scatter(StripGeom g, const cpx_t<T>* __restrict__ sol, size_t 
     v[b * (size_t)n * n + e] = ccast<double2>(sol[b * SB + (size_t)l * strip_stride + (size_t)i * g.q + r]);
 }
 
+// The same for the other direction's field, added to a field of this one:
+// v[i][z] = u[i][z] + (row z of the layers' solutions)[i]  (the vertical sweep's result
+// transposed back and added to the horizontal one, Algorithm 2); along z, coalesced.
+template <typename T>
+__global__ void k_scatter_tadd(StripGeom g, const cpx_t<T>* __restrict__ sol, size_t strip_stride, size_t SB,
+                               const double2* __restrict__ u, double2* __restrict__ v) {
+    const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int n = g.n;
+    if (e >= (size_t)n * n) return;
+    const size_t b = blockIdx.y;
+    const int i = (int)(e / n), z = (int)(e % n);
+    const int l = z / g.t, r = z - l * g.t + g.E;
+    const size_t o = b * (size_t)n * n + e;
+    v[o] = u[o] + ccast<double2>(sol[b * SB + (size_t)l * strip_stride + (size_t)i * g.q + r]);
+}
+
 // natural strip layout (q rows x n, x fastest) <-> block layout (i*q + r)
 template <typename T>
 __global__ void k_strip_in(int n, int q, const double2* __restrict__ b, cpx_t<T>* __restrict__ x) {
@@ -398,10 +425,6 @@ __global__ void k_strip_out(int n, int q, const cpx_t<T>* __restrict__ x, double
     b[e] = ccast<double2>(x[(size_t)i * q + r]);
 }
 
-__global__ void k_add(size_t N, const double2* __restrict__ a, double2* __restrict__ b) {
-    for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < N; k += (size_t)gridDim.x * blockDim.x)
-        b[k] = b[k] + a[k];
-}
 
 StripGeom geom_of(const ls_handle* h) { return StripGeom{h->n, h->t, h->E, h->q, h->opts.shift / h->omega}; }
 
@@ -521,7 +544,10 @@ int cr_solve(ls_handle* h, int dir, int l, cpx_t<T>* x, size_t SB, int nb) {
 }
 
 template <typename T>
-int sweep_impl(ls_handle* h, int dir, const double2* g, double2* v, int nb) {
+// tr: g and v are fields of the other direction's grid (read and written transposed);
+// add: v = add + the result (tr only).
+int sweep_impl(ls_handle* h, int dir, const double2* g, double2* v, int nb, bool tr = false,
+               const double2* add = nullptr) {
     using C = cpx_t<T>;
     const int n = h->n, q = h->q, L = h->L;
     const size_t sstride = (size_t)n * q;
@@ -535,9 +561,14 @@ int sweep_impl(ls_handle* h, int dir, const double2* g, double2* v, int nb) {
     const dim3 gg((unsigned)((n + kGatherTile - 1) / kGatherTile), (unsigned)((q + kGatherTile - 1) / kGatherTile), nb);
     const dim3 gb(kGatherTile, 8);
     for (int l = L - 1; l >= 0; --l) {  // downward sweep
-        LS_LAUNCH(h, k_gather<T>, gg, gb, 0, geo, static_cast<const C*>(F.cinj), l, g, rhs + l * sstride,
-                  sol + l * sstride, l < L - 1 ? sol + (l + 1) * sstride : (const C*)nullptr,
-                  l < L - 1 ? trc + (size_t)(l + 1) * n : (C*)nullptr, SB, TB);
+        if (tr)
+            LS_LAUNCH(h, (k_gather<T, true>), gg, gb, 0, geo, static_cast<const C*>(F.cinj), l, g, rhs + l * sstride,
+                      sol + l * sstride, l < L - 1 ? sol + (l + 1) * sstride : (const C*)nullptr,
+                      l < L - 1 ? trc + (size_t)(l + 1) * n : (C*)nullptr, SB, TB);
+        else
+            LS_LAUNCH(h, (k_gather<T, false>), gg, gb, 0, geo, static_cast<const C*>(F.cinj), l, g, rhs + l * sstride,
+                      sol + l * sstride, l < L - 1 ? sol + (l + 1) * sstride : (const C*)nullptr,
+                      l < L - 1 ? trc + (size_t)(l + 1) * n : (C*)nullptr, SB, TB);
         LS_TRY(cr_solve<T>(h, dir, l, sol + l * sstride, SB, nb));
     }
     const dim3 gi((unsigned)((2 * n + 255) / 256), nb);
@@ -549,7 +580,10 @@ int sweep_impl(ls_handle* h, int dir, const double2* g, double2* v, int nb) {
         LS_TRY(cr_solve<T>(h, dir, l, sol + l * sstride, SB, nb));
     }
     const size_t N = (size_t)n * n;
-    LS_LAUNCH(h, k_scatter<T>, dim3((unsigned)((N + 255) / 256), nb), 256, 0, geo, sol, sstride, SB, v);
+    if (tr && add)
+        LS_LAUNCH(h, k_scatter_tadd<T>, dim3((unsigned)((N + 255) / 256), nb), 256, 0, geo, sol, sstride, SB, add, v);
+    else
+        LS_LAUNCH(h, k_scatter<T>, dim3((unsigned)((N + 255) / 256), nb), 256, 0, geo, sol, sstride, SB, v);
     return LS_OK;
 }
 
@@ -678,9 +712,10 @@ static int bd_direct(ls_handle* h, const double2* g, double2* v, int nb) {
     double2* e = u1 + N * nb;
     LS_TRY(ls_sweep_dir_b(h, 0, g, u1, nb));
     LS_TRY(ls_stencil_apply_b(h, 0, 2, u1, g, e, nb));   // e = g - C u1
-    LS_TRY(ls_sweep_dir_b(h, 1, e, v, nb));
-    LS_LAUNCH(h, k_add, 608, 256, 0, N * nb, u1, v);
-    return LS_OK;
+    // vertical layers on e as it is stored (their grid is its transpose): the gather reads
+    // it transposed, and the scatter writes v = u1 + the result, transposed back
+    if (h->prec == LS_MIXED) return sweep_impl<float>(h, 1, e, v, nb, true, u1);
+    return sweep_impl<double>(h, 1, e, v, nb, true, u1);
 }
 
 void ls_bd_graph_free(ls_handle* h) {
