@@ -488,20 +488,24 @@ struct DenseArgs {
 };
 
 template <int NB>
-constexpr size_t dense_smem() {
-    return 1024 + 2 * (size_t)kDensePlane + (size_t)kDenseAtoms * 2 * NB * 128 + 8 * 3 + 16;
+constexpr size_t dense_smem() {   // ring of 2 atom stages (re and im: 2 x 16 KB) | B | barriers
+    return 1024 + 2 * 2 * 16384 + (size_t)kDenseAtoms * 2 * NB * 128 + 8 * 5 + 16;
 }
 
 template <int NB>
-__global__ void __launch_bounds__(kThreads, 1) k_dense_mma(DenseArgs a) {
+__global__ void __launch_bounds__(kThreads, 2) k_dense_mma(DenseArgs a) {
     constexpr int NCOL = 2 * NB, TCOLS = 2 * NCOL;
     constexpr unsigned BATOM = 2 * NB * 128;
     extern __shared__ unsigned char smem_raw[];
     unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    unsigned char* As = base;                       // planes re, im of block (mt, kc)
-    unsigned char* Bs = As + 2 * kDensePlane;       // 4 atoms x 2NB rows [X_re; X_im]
+    // A: a ring of two stages, each one K atom of the block (its re and im parts, 16 KB each),
+    // so that two CTAs fit on an SM; B: 4 atoms x 2NB rows [X_re; X_im]
+    constexpr unsigned kAtom = 128u * 128u, kStage = 2 * kAtom;
+    unsigned char* As = base;
+    unsigned char* Bs = As + 2 * kStage;
     auto* full = reinterpret_cast<unsigned long long*>(Bs + kDenseAtoms * BATOM);
-    auto* done = full + 2;
+    auto* empty = full + 2;
+    auto* done = empty + 2;
     unsigned* tslot = reinterpret_cast<unsigned*>(done + 1);
     int* failed = reinterpret_cast<int*>(tslot + 1);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -509,8 +513,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_dense_mma(DenseArgs a) {
     asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
     if (tid == 0) {
         *failed = 0;
-        bar_init(&full[0], 1);
-        bar_init(&full[1], 1);
+        for (int i = 0; i < 2; ++i) {
+            bar_init(&full[i], 1);
+            bar_init(&empty[i], 1);
+        }
         bar_init(done, 1);
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
@@ -520,14 +526,18 @@ __global__ void __launch_bounds__(kThreads, 1) k_dense_mma(DenseArgs a) {
     __syncthreads();
     fence_after();
     const unsigned tmem = *tslot;
-    if (tid == 0) {   // the block's two planes (constant data: before the predecessor completes)
-        const float* src = a.A + ((size_t)mt * a.ks + kc) * 2 * (kDensePlane / 4);
-        for (int p = 0; p < 2; ++p) {
-            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(su32(&full[p])),
-                         "r"(kDensePlane)
-                         : "memory");
-            bulk_load(As + (size_t)p * kDensePlane, src + (size_t)p * (kDensePlane / 4), kDensePlane, &full[p]);
-        }
+    // atom at of the block: re part at src + at * 16 KB, im part one plane further
+    const float* src = a.A + ((size_t)mt * a.ks + kc) * 2 * (kDensePlane / 4);
+    auto load_atom = [&](int at) {
+        const int st = at & 1;
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(su32(&full[st])), "r"(kStage)
+                     : "memory");
+        bulk_load(As + (size_t)st * kStage, src + (size_t)at * (kAtom / 4), kAtom, &full[st]);
+        bulk_load(As + (size_t)st * kStage + kAtom, src + kDensePlane / 4 + (size_t)at * (kAtom / 4), kAtom, &full[st]);
+    };
+    if (tid == 0) {   // the first two atoms (constant data: before the predecessor completes)
+        load_atom(0);
+        load_atom(1);
     }
     asm volatile("griddepcontrol.wait;\n" ::: "memory");
 
@@ -563,23 +573,35 @@ __global__ void __launch_bounds__(kThreads, 1) k_dense_mma(DenseArgs a) {
         constexpr unsigned ID = idesc_tf32(128, NCOL);
         bool ok = true;
         const unsigned long long bd0 = sdesc(su32(Bs));
-        for (int p = 0; p < 2 && ok; ++p) {
-            if (!bar_wait(&full[p], 0u)) {
+        for (int at = 0; at < kDenseAtoms && ok; ++at) {
+            const int st = at & 1;
+            if (!bar_wait(&full[st], (unsigned)(at >> 1) & 1u)) {
                 ok = false;
                 break;
             }
             fence_after();
-            const unsigned long long ad0 = sdesc(su32(As + (size_t)p * kDensePlane));
-            const unsigned dacc = tmem + (unsigned)(p * NCOL);
 #pragma unroll
-            for (int at = 0; at < kDenseAtoms; ++at)
+            for (int p = 0; p < 2; ++p) {   // re part into accumulator 0, im part into accumulator 1
+                const unsigned long long ad0 = sdesc(su32(As + (size_t)st * kStage + (size_t)p * kAtom));
+                const unsigned dacc = tmem + (unsigned)(p * NCOL);
 #pragma unroll
                 for (int k8 = 0; k8 < 4; ++k8)
-                    mma_tf32(dacc, ad0 + (unsigned long long)(at * 1024 + 2 * k8),
-                             bd0 + (unsigned long long)(at * (BATOM >> 4) + 2 * k8), ID, (at | k8) ? 1u : 0u);
+                    mma_tf32(dacc, ad0 + 2ull * k8, bd0 + (unsigned long long)(at * (BATOM >> 4) + 2 * k8), ID,
+                             (at | k8) ? 1u : 0u);
+            }
+            mma_commit(&empty[st]);   // the stage is free once these MMAs have read it
         }
         if (!ok) atomicOr(failed, 1);
         mma_commit(done);
+    }
+    if (tid == 0) {   // refill: atoms 2 and 3 once the MMAs of atoms 0 and 1 are done
+        for (int at = 2; at < kDenseAtoms; ++at) {
+            if (!bar_wait(&empty[at & 1], 0u)) {
+                atomicOr(failed, 2);
+                break;
+            }
+            load_atom(at);
+        }
     }
     const int r = 32 * (warp & 3) + lane;
     const int half = warp >> 2;
