@@ -328,6 +328,7 @@ int ls_transpose64(ls_handle* h, const double2* a, double2* b);
 int ls_transpose64_b(ls_handle* h, const double2* a, double2* b, int nb);
 int ls_stencil_apply64(ls_handle* h, int dir, int mode, const double2* v, const double2* g, double2* y);
 int ls_stencil_apply_b(ls_handle* h, int dir, int withm, const double2* v, const double2* g, double2* y, int nb);
+int ls_stencil_refine_f32(ls_handle* h, int dir, const float2* v, const double2* g, float2* y, int nb);
 int ls_vec_dots(ls_handle* h, int nvec, const double2* V, size_t ld, const double2* w, double2* out_host);
 int ls_vec_update(ls_handle* h, int nvec, const double2* V, size_t ld, const double2* coef_dev, double2* w);
 int ls_vec_norm(ls_handle* h, const double2* w, double* out_host);

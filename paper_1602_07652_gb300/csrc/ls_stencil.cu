@@ -23,10 +23,12 @@ namespace {
 // arithmetic type) by loads that are all issued before the first store, so every
 // value of v and m is read from HBM about once.
 constexpr int kStX = 32, kStZ = 32, kStRows = 4;   // tile, rows per thread (threads 32 x 8)
-template <int MODE, typename R>  // 0: y = A v   1: y = C v   2: y = g - C v
+// VF, YF: element types of v and y (double2; float2 for the mixed Algorithm 2's fields,
+// which hold FP32 values: v is the FP32 sweep's result, y feeds the FP32 sweep).
+template <int MODE, typename R, typename VF = double2, typename YF = double2>  // 0: y = A v  1: y = C v  2: y = g - C v
 __global__ void __launch_bounds__(256) k_stencil(int n, const StencilTables* __restrict__ tab,
-                                                 const double* __restrict__ m, const double2* __restrict__ v,
-                                                 const double2* __restrict__ g, double2* __restrict__ y) {
+                                                 const double* __restrict__ m, const VF* __restrict__ v,
+                                                 const double2* __restrict__ g, YF* __restrict__ y) {
     using CR = cpx_t<R>;
     constexpr int HX = kStX + 2, HZ = kStZ + 2, HN = HX * HZ;
     __shared__ CR sa[81], sb[81];
@@ -45,13 +47,14 @@ __global__ void __launch_bounds__(256) k_stencil(int n, const StencilTables* __r
     }
     const int x0 = blockIdx.x * kStX - 1, z0 = blockIdx.y * kStZ - 1;
     constexpr int PER = (HN + 255) / 256;   // halo tile elements per thread
-    double2 vv[PER];
+    const VF vz = {};
+    VF vv[PER];
     double mv[PER];
 #pragma unroll
     for (int u = 0; u < PER; ++u) {
         const int e = tid + u * 256, hz = e / HX, hx = e % HX, x = x0 + hx, z = z0 + hz;
         const bool in = e < HN && x >= 0 && x < n && z >= 0 && z < n;
-        vv[u] = in ? __ldg(&v[(size_t)z * n + x]) : make_double2(0.0, 0.0);
+        vv[u] = in ? __ldg(&v[(size_t)z * n + x]) : vz;
         if (MODE >= 1) mv[u] = in ? __ldg(&m[(size_t)z * n + x]) : 0.0;
     }
 #pragma unroll
@@ -95,7 +98,7 @@ __global__ void __launch_bounds__(256) k_stencil(int n, const StencilTables* __r
         const size_t k = (size_t)j * n + i;
         double2 out = ccast<double2>(acc);
         if (MODE == 2) out = __ldg(&g[k]) - out;
-        y[k] = out;
+        y[k] = ccast<YF>(out);
     }
 }
 
@@ -266,6 +269,17 @@ int ls_stencil_apply64(ls_handle* h, int dir, int mode, const double2* v, const 
 int ls_stencil_apply_b(ls_handle* h, int dir, int mode, const double2* v, const double2* g, double2* y, int nb) {
     if (h->prec == LS_MIXED) return stencil_launch<float>(h, dir, mode, v, g, y, nb);
     return stencil_launch<double>(h, dir, mode, v, g, y, nb);
+}
+
+// Algorithm 2's refinement residual e = g - C u1 in mixed precision, u1 and e in FP32
+// storage (their values are FP32 either way); FP32 coefficients and sums.
+int ls_stencil_refine_f32(ls_handle* h, int dir, const float2* v, const double2* g, float2* y, int nb) {
+    const int n = h->n;
+    const dim3 grid((unsigned)((n + kStX - 1) / kStX), (unsigned)((n + kStZ - 1) / kStZ), nb);
+    const dim3 block(kStX, 256 / kStX);
+    const double* m = dir == 0 ? h->m64 : h->mT64;
+    LS_LAUNCH(h, (k_stencil<2, float, float2, float2>), grid, block, 0, n, h->dtabs + dir, m, v, g, y);
+    return LS_OK;
 }
 
 int ls_stencil_apply(ls_handle* h, int dir, int mode, const double2* v, const double2* g, double2* y) {

@@ -286,9 +286,9 @@ __global__ void k_l0_even(int q, int nblk, const cpx_t<T>* __restrict__ cw, cons
 // of the field's): strip row r, column i is g[i][l t - E + r], contiguous along r, so the
 // reads go straight to the strip layout without the shared-memory tile.
 constexpr int kGatherTile = 32;
-template <typename T, bool TR>
+template <typename T, bool TR, typename GF = double2>
 __global__ void __launch_bounds__(256) k_gather(StripGeom g, const cpx_t<T>* __restrict__ inj, int l,
-                                                const double2* __restrict__ gf, cpx_t<T>* __restrict__ rhs,
+                                                const GF* __restrict__ gf, cpx_t<T>* __restrict__ rhs,
                                                 cpx_t<T>* __restrict__ sol, const cpx_t<T>* __restrict__ above,
                                                 cpx_t<T>* __restrict__ trace_above, size_t SB, size_t TB) {
     using C = cpx_t<T>;
@@ -304,18 +304,19 @@ __global__ void __launch_bounds__(256) k_gather(StripGeom g, const cpx_t<T>* __r
         trace_above += b * TB;
     }
     const int tx = threadIdx.x, ty = threadIdx.y;
-    double2 v[kGatherTile / 8];
+    const GF z0 = {};
+    GF v[kGatherTile / 8];
     if constexpr (TR) {
 #pragma unroll
         for (int u = 0; u < kGatherTile / 8; ++u) {   // rows of Omega^l (E <= r < E + t), along r
             const int i = i0 + ty + 8 * u, r = r0 + tx;
-            v[u] = (r >= E && r < E + t && i < n) ? __ldg(&gf[(size_t)i * n + (l * t - E + r)]) : make_double2(0.0, 0.0);
+            v[u] = (r >= E && r < E + t && i < n) ? __ldg(&gf[(size_t)i * n + (l * t - E + r)]) : z0;
         }
     } else {
 #pragma unroll
         for (int u = 0; u < kGatherTile / 8; ++u) {   // rows of Omega^l (E <= r < E + t), along x
             const int r = r0 + ty + 8 * u, i = i0 + tx;
-            v[u] = (r >= E && r < E + t && i < n) ? __ldg(&gf[(size_t)(l * t - E + r) * n + i]) : make_double2(0.0, 0.0);
+            v[u] = (r >= E && r < E + t && i < n) ? __ldg(&gf[(size_t)(l * t - E + r) * n + i]) : z0;
         }
 #pragma unroll
         for (int u = 0; u < kGatherTile / 8; ++u) tile[ty + 8 * u][tx] = ccast<C>(v[u]);
@@ -381,24 +382,24 @@ __global__ void k_inject_up(StripGeom g, const cpx_t<T>* __restrict__ inj, int l
 }
 
 // v = rows 1..n of every layer's solution (concatenation); batch member b = blockIdx.y
-template <typename T>
+template <typename T, typename OF = double2>
 __global__ void k_scatter(StripGeom g, const cpx_t<T>* __restrict__ sol, size_t strip_stride, size_t SB,
-                          double2* __restrict__ v) {
+                          OF* __restrict__ v) {
     const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int n = g.n;
     if (e >= (size_t)n * n) return;
     const size_t b = blockIdx.y;
     const int z = (int)(e / n), i = (int)(e % n);
     const int l = z / g.t, r = z - l * g.t + g.E;
-    v[b * (size_t)n * n + e] = ccast<double2>(sol[b * SB + (size_t)l * strip_stride + (size_t)i * g.q + r]);
+    v[b * (size_t)n * n + e] = ccast<OF>(sol[b * SB + (size_t)l * strip_stride + (size_t)i * g.q + r]);
 }
 
 // The same for the other direction's field, added to a field of this one:
 // v[i][z] = u[i][z] + (row z of the layers' solutions)[i]  (the vertical sweep's result
 // transposed back and added to the horizontal one, Algorithm 2); along z, coalesced.
-template <typename T>
+template <typename T, typename AF = double2>
 __global__ void k_scatter_tadd(StripGeom g, const cpx_t<T>* __restrict__ sol, size_t strip_stride, size_t SB,
-                               const double2* __restrict__ u, double2* __restrict__ v) {
+                               const AF* __restrict__ u, double2* __restrict__ v) {
     const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int n = g.n;
     if (e >= (size_t)n * n) return;
@@ -406,7 +407,7 @@ __global__ void k_scatter_tadd(StripGeom g, const cpx_t<T>* __restrict__ sol, si
     const int i = (int)(e / n), z = (int)(e % n);
     const int l = z / g.t, r = z - l * g.t + g.E;
     const size_t o = b * (size_t)n * n + e;
-    v[o] = u[o] + ccast<double2>(sol[b * SB + (size_t)l * strip_stride + (size_t)i * g.q + r]);
+    v[o] = ccast<double2>(u[o]) + ccast<double2>(sol[b * SB + (size_t)l * strip_stride + (size_t)i * g.q + r]);
 }
 
 // natural strip layout (q rows x n, x fastest) <-> block layout (i*q + r)
@@ -543,11 +544,12 @@ int cr_solve(ls_handle* h, int dir, int l, cpx_t<T>* x, size_t SB, int nb) {
     return LS_EINVAL;
 }
 
-template <typename T>
 // tr: g and v are fields of the other direction's grid (read and written transposed);
-// add: v = add + the result (tr only).
-int sweep_impl(ls_handle* h, int dir, const double2* g, double2* v, int nb, bool tr = false,
-               const double2* add = nullptr) {
+// add: v = add + the result (tr only).  GF, OF, AF: element types of g, v and add
+// (double2; float2 for the mixed Algorithm 2's intermediate fields, which hold FP32
+// values either way).
+template <typename T, typename GF = double2, typename OF = double2, typename AF = double2>
+int sweep_impl(ls_handle* h, int dir, const GF* g, OF* v, int nb, bool tr = false, const AF* add = nullptr) {
     using C = cpx_t<T>;
     const int n = h->n, q = h->q, L = h->L;
     const size_t sstride = (size_t)n * q;
@@ -562,11 +564,11 @@ int sweep_impl(ls_handle* h, int dir, const double2* g, double2* v, int nb, bool
     const dim3 gb(kGatherTile, 8);
     for (int l = L - 1; l >= 0; --l) {  // downward sweep
         if (tr)
-            LS_LAUNCH(h, (k_gather<T, true>), gg, gb, 0, geo, static_cast<const C*>(F.cinj), l, g, rhs + l * sstride,
+            LS_LAUNCH(h, (k_gather<T, true, GF>), gg, gb, 0, geo, static_cast<const C*>(F.cinj), l, g, rhs + l * sstride,
                       sol + l * sstride, l < L - 1 ? sol + (l + 1) * sstride : (const C*)nullptr,
                       l < L - 1 ? trc + (size_t)(l + 1) * n : (C*)nullptr, SB, TB);
         else
-            LS_LAUNCH(h, (k_gather<T, false>), gg, gb, 0, geo, static_cast<const C*>(F.cinj), l, g, rhs + l * sstride,
+            LS_LAUNCH(h, (k_gather<T, false, GF>), gg, gb, 0, geo, static_cast<const C*>(F.cinj), l, g, rhs + l * sstride,
                       sol + l * sstride, l < L - 1 ? sol + (l + 1) * sstride : (const C*)nullptr,
                       l < L - 1 ? trc + (size_t)(l + 1) * n : (C*)nullptr, SB, TB);
         LS_TRY(cr_solve<T>(h, dir, l, sol + l * sstride, SB, nb));
@@ -580,10 +582,14 @@ int sweep_impl(ls_handle* h, int dir, const double2* g, double2* v, int nb, bool
         LS_TRY(cr_solve<T>(h, dir, l, sol + l * sstride, SB, nb));
     }
     const size_t N = (size_t)n * n;
-    if (tr && add)
-        LS_LAUNCH(h, k_scatter_tadd<T>, dim3((unsigned)((N + 255) / 256), nb), 256, 0, geo, sol, sstride, SB, add, v);
-    else
-        LS_LAUNCH(h, k_scatter<T>, dim3((unsigned)((N + 255) / 256), nb), 256, 0, geo, sol, sstride, SB, v);
+    if constexpr (sizeof(OF) == sizeof(double2)) {
+        if (tr && add) {
+            LS_LAUNCH(h, (k_scatter_tadd<T, AF>), dim3((unsigned)((N + 255) / 256), nb), 256, 0, geo, sol, sstride, SB,
+                      add, v);
+            return LS_OK;
+        }
+    }
+    LS_LAUNCH(h, (k_scatter<T, OF>), dim3((unsigned)((N + 255) / 256), nb), 256, 0, geo, sol, sstride, SB, v);
     return LS_OK;
 }
 
@@ -710,11 +716,21 @@ static int bd_direct(ls_handle* h, const double2* g, double2* v, int nb) {
     const size_t N = (size_t)h->n * h->n;
     double2* u1 = static_cast<double2*>(h->lanes[h->lane].vtmp) + 2 * N * nb;
     double2* e = u1 + N * nb;
+    if (h->prec == LS_MIXED) {
+        // u1 and e hold FP32 values (the FP32 sweep's result; the residual the FP32 sweep
+        // reads), so they are stored in FP32: the same numbers with half the traffic
+        if (nb < 1 || nb > ls_bd_cap(h)) return LS_EINVAL;
+        LS_TRY(ls_sweep_reserve(h, nb));
+        float2* u1f = reinterpret_cast<float2*>(u1);
+        float2* ef = reinterpret_cast<float2*>(e);
+        LS_TRY((sweep_impl<float, double2, float2, float2>(h, 0, g, u1f, nb)));
+        LS_TRY(ls_stencil_refine_f32(h, 0, u1f, g, ef, nb));   // e = g - C u1
+        return sweep_impl<float, float2, double2, float2>(h, 1, ef, v, nb, true, u1f);
+    }
     LS_TRY(ls_sweep_dir_b(h, 0, g, u1, nb));
     LS_TRY(ls_stencil_apply_b(h, 0, 2, u1, g, e, nb));   // e = g - C u1
     // vertical layers on e as it is stored (their grid is its transpose): the gather reads
     // it transposed, and the scatter writes v = u1 + the result, transposed back
-    if (h->prec == LS_MIXED) return sweep_impl<float>(h, 1, e, v, nb, true, u1);
     return sweep_impl<double>(h, 1, e, v, nb, true, u1);
 }
 
