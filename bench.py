@@ -532,7 +532,8 @@ def run_ours(args):
                # live shares of the timed region (CUDA events inside the library)
                "time_shares": {"algorithm2": sum(st["t_sweep_ms"] for st in stats) / ms,
                                "ls_apply_fp32": t_app / ms,
-                               "ls_apply_fp64_refinement": sum(st["t_apply64_ms"] for st in stats) / ms}}
+                               "ls_apply_fp64_refinement": sum(st["t_apply64_ms"] for st in stats) / ms,
+                               "stencils_inner_solve": sum(st["t_stencil_ms"] for st in stats) / ms}}
     s.close()
     if rank == 0 and world == 1 and not args.fp64 and not args.no_fp64_leg:
         # the plain FP64 GPU method on the same problem and tolerance, one right-hand side at

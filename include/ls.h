@@ -95,6 +95,9 @@ typedef struct {
     int n_sweep;             /* Algorithm 2 applications counted in t_sweep_ms               */
     long long kernel_launches; /* kernels this library launched during the call            */
     int learned_steps;     /* outer steps that used the attached network (ls_set_learned)   */
+    double t_stencil_ms;     /* device time of the 9-point stencil applies A v, C v of the inner
+                                solve (Algorithm 3), if timing                              */
+    int n_stencil;           /* stencil applies counted in t_stencil_ms                      */
 } ls_stats;
 
 typedef struct ls_handle ls_handle;

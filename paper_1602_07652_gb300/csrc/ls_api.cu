@@ -129,6 +129,9 @@ int ls_timing_collect(ls_handle* h) {
         } else if (h->tkind[k] == 2) {
             h->t_apply64_ms += ms;
             h->n_apply64++;
+        } else if (h->tkind[k] == 3) {
+            h->t_stencil_ms += ms;
+            h->n_stencil++;
         } else {
             h->t_sweep_ms += ms;
             h->n_sweep++;
@@ -289,8 +292,8 @@ int ls_solve_batch(ls_handle* h, int nrhs, const ls_c64* f, double tol, ls_c64* 
     ls_stats local{};
     ls_stats* s = st ? st : &local;
     std::memset(s, 0, sizeof(*s));
-    h->t_apply_ms = h->t_sweep_ms = h->t_apply64_ms = 0;
-    h->n_apply = h->n_sweep = h->n_apply64 = 0;
+    h->t_apply_ms = h->t_sweep_ms = h->t_apply64_ms = h->t_stencil_ms = 0;
+    h->n_apply = h->n_sweep = h->n_apply64 = h->n_stencil = 0;
     h->learned_steps = 0;
     const long long l0 = h->launches;
     const auto t0 = std::chrono::steady_clock::now();
@@ -309,6 +312,8 @@ int ls_solve_batch(ls_handle* h, int nrhs, const ls_c64* f, double tol, ls_c64* 
     s->n_sweep = h->n_sweep;
     s->kernel_launches = h->launches - l0;
     s->learned_steps = h->learned_steps;
+    s->t_stencil_ms = h->t_stencil_ms;
+    s->n_stencil = h->n_stencil;
     return rc;
 }
 

@@ -100,42 +100,32 @@ struct StepArgs {
     const float2* ce;
 };
 
-template <int MODE, int NB, int KA>
-__global__ void __launch_bounds__(kThreads, 2) k_cr_mma(StepArgs a) {
-    using MO = ModeOf<MODE>;
-    constexpr int NV = MO::NV;
-    constexpr int KP = 32 * KA;                   // padded K of one plane
-    constexpr int BROWS = 2 * NB;                 // rows of one vector's B atom: [X_re; X_im]
-    constexpr unsigned BATOM = BROWS * 128;       // bytes of one vector's B atom
-    constexpr int NCOL = 2 * NB;                  // columns of one accumulator
-    constexpr int TCOLS = 2 * NCOL;               // two accumulators: M_re B, M_im B (32, 64 or 128)
-    const int q = a.q;
-    const int BR = (q + 7) / 8 * 8;
-    const int kStages = a.stages;
-    const unsigned kPlane = (unsigned)KA * (unsigned)BR * 128u;
-    extern __shared__ unsigned char smem_raw[];
-    unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    unsigned char* As = base;
-    unsigned char* Bs = As + (size_t)kStages * kPlane;
-    auto* full = reinterpret_cast<unsigned long long*>(Bs + (size_t)NV * KA * BATOM);
-    auto* empty = full + kMaxStages;
-    auto* done = empty + kMaxStages;
-    unsigned* tslot = reinterpret_cast<unsigned*>(done + 1);
-    int* failed = reinterpret_cast<int*>(tslot + 1);
-
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int idx = blockIdx.x;
-    // The next step may be scheduled now (programmatic dependent launch): its CTAs set up
-    // and start streaming their factor planes, which no step writes, while this one runs.
-    asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
-    const size_t s = (size_t)1 << a.k;
-    const int j = (MODE == 1) ? 2 * idx : (MODE == 3 ? 0 : 2 * idx + 1);
-    const bool hw = j >= 1, he = j + 1 < a.nk;
-    // vector slot t: present?, its block, its sign, its matrix (index in the pool)
+// Block j of the step's level that CTA `idx` takes, and its vector slots t: present?,
+// block (in the strip), sign, factor matrix (index in the pool).
+struct StepGeom {
+    size_t s;        // 2^k: blocks between neighbours at this level
+    int j;
+    bool hw, he;     // west / east neighbour present
     bool pres[3];
     long long blk[3];
     float sgn[3];
     size_t mat[3];
+    int npl;         // factor planes to stream: present vectors x 2
+};
+template <int MODE>
+__device__ __forceinline__ StepGeom step_geom(const StepArgs& a, int idx) {
+    StepGeom g{};
+    const size_t s = (size_t)1 << a.k;
+    const int j = (MODE == 1) ? 2 * idx : (MODE == 3 ? 0 : 2 * idx + 1);
+    const bool hw = j >= 1, he = j + 1 < a.nk;
+    g.s = s;
+    g.j = j;
+    g.hw = hw;
+    g.he = he;
+    bool* pres = g.pres;
+    long long* blk = g.blk;
+    float* sgn = g.sgn;
+    size_t* mat = g.mat;
     if (MODE == 0 || MODE == 3 || MODE == 4) {
         pres[0] = true; blk[0] = (long long)j * s; sgn[0] = 1.f; mat[0] = a.mat0 + a.off_a + idx;
     }
@@ -148,53 +138,26 @@ __global__ void __launch_bounds__(kThreads, 2) k_cr_mma(StepArgs a) {
         pres[1] = true; blk[1] = (long long)(j - 1) * (long long)s; sgn[1] = -1.f; mat[1] = a.mat0 + a.off_b + idx;
         pres[2] = he; blk[2] = (long long)(j + 1) * s; sgn[2] = -1.f; mat[2] = a.mat0 + a.off_c + idx;
     }
-    int npl = 0;   // A planes to stream: present vectors x 2
+    g.npl = 0;
 #pragma unroll
-    for (int t = 0; t < NV; ++t) npl += pres[t] ? 2 : 0;
+    for (int t = 0; t < ModeOf<MODE>::NV; ++t) g.npl += pres[t] ? 2 : 0;
+    return g;
+}
 
-    if (tid == 0) {
-        *failed = 0;
-        for (int i = 0; i < kStages; ++i) {
-            bar_init(&full[i], 1);
-            bar_init(&empty[i], 1);
-        }
-        bar_init(done, 1);
-        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
-        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-    }
-    if (warp == 0) {   // TMEM accumulator: 128 lanes x TCOLS columns
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(su32(tslot)),
-                     "r"(TCOLS)
-                     : "memory");
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
-    }
-    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
-    __syncthreads();
-    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-    const unsigned tmem = *tslot;
-
-    // producer: the first min(npl, kStages) planes start streaming before B is built
-    auto plane_src = [&](int i) {   // i-th present plane: (vector slot, re/im)
-        int t = 0, r = i;
-        while (!pres[t] || r >= 2) {
-            if (pres[t]) r -= 2;
-            ++t;
-        }
-        return a.pool + (2 * mat[t] + r) * (size_t)KA * BR * 32;
-    };
-    if (tid == 0) {
-        for (int i = 0; i < npl && i < kStages; ++i) {
-            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(su32(&full[i])), "r"(kPlane)
-                         : "memory");
-            bulk_load(As + (size_t)i * kPlane, plane_src(i), kPlane, &full[i]);
-        }
-    }
-
-    // Vectors are read and written only after the previous kernel of the stream has
-    // completed and its writes are visible.
-    asm volatile("griddepcontrol.wait;\n" ::: "memory");
-
-    // B: per vector t, atom at, rows [0,NB) = X_re, [NB,2NB) = X_im (TF32, the step's sign folded in).
+// Operand B of the step for the geometry gm: per vector t, atom at, rows [0,NB) = X_re,
+// [NB,2NB) = X_im (TF32, the step's sign folded in), built by the kThreads threads tid.
+template <int MODE, int NB, int KA>
+__device__ __forceinline__ void build_b(const StepArgs& a, const StepGeom& gm, unsigned char* Bs, int tid) {
+    constexpr int NV = ModeOf<MODE>::NV;
+    constexpr int KP = 32 * KA;
+    constexpr unsigned BATOM = 2 * NB * 128;
+    const int q = a.q, warp = tid >> 5, lane = tid & 31;
+    const int j = gm.j;
+    const bool he = gm.he;
+    const size_t s = gm.s;
+    const bool* pres = gm.pres;
+    const long long* blk = gm.blk;
+    const float* sgn = gm.sgn;
     // Every load is issued (at a clamped, valid address) before any value is used, so their
     // latencies overlap; absent vectors, members and padding rows are zeroed afterwards.
     const int nbc = a.nb < 1 ? 0 : a.nb - 1;
@@ -314,6 +277,154 @@ __global__ void __launch_bounds__(kThreads, 2) k_cr_mma(StepArgs a) {
             }
         }
     }
+}
+
+// x_j before the step, for the steps that add (MODE 1, 4): rows r = 32 (warp % 4) + lane,
+// members half * NB/2 .. of warp half = warp / 4 (the epilogue's mapping)
+template <int MODE, int NB>
+__device__ __forceinline__ void load_old(const StepArgs& a, const StepGeom& gm, int warp, int lane, float2* old) {
+    constexpr int HB = NB / 2;
+    const int r = 32 * (warp & 3) + lane, half = warp >> 2;
+#pragma unroll
+    for (int c = 0; c < HB; ++c) {
+        const int b = half * HB + c;
+        old[c] = (ModeOf<MODE>::ADD && r < a.q && b < a.nb) ? a.x[(size_t)b * a.SB + (size_t)gm.j * gm.s * a.q + r]
+                                                            : make_float2(0.f, 0.f);
+    }
+}
+
+// Epilogue of a step: the two accumulators (tensor memory at tmem) -> x_j (+ old for the
+// steps that add), NaN if the step failed.  Warps 0-7: warp w reads TMEM lanes
+// 32 (w % 4) .. + 31 (rows r), its half w / 4 of the members.
+template <int MODE, int NB>
+__device__ __forceinline__ void store_step(const StepArgs& a, const StepGeom& gm, unsigned tmem, bool bad,
+                                           const float2* old, int warp, int lane) {
+    using MO = ModeOf<MODE>;
+    constexpr int NCOL = 2 * NB, HB = NB / 2;
+    const int q = a.q, j = gm.j;
+    const size_t s = gm.s;
+    const int r = 32 * (warp & 3) + lane;
+    const int half = warp >> 2;
+    // D_re = M_re X_re - M_im X_im = acc0[:, b] - acc1[:, NB + b],
+    // D_im = M_re X_im + M_im X_re = acc0[:, NB + b] + acc1[:, b]
+    float dre[HB], dim[HB];
+    const unsigned tl = tmem + ((unsigned)(32 * (warp & 3)) << 16);
+    if constexpr (HB % 8 == 0) {
+#pragma unroll
+        for (int c = 0; c < HB; c += 8) {
+            float rr[8], ri[8], ir[8], ii[8];
+            const unsigned col = (unsigned)(half * HB + c);
+            tmem_ld8(tl + col, rr);
+            tmem_ld8(tl + (unsigned)NB + col, ri);
+            tmem_ld8(tl + (unsigned)NCOL + col, ir);
+            tmem_ld8(tl + (unsigned)(NCOL + NB) + col, ii);
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+                dre[c + e] = rr[e] - ii[e];
+                dim[c + e] = ri[e] + ir[e];
+            }
+        }
+    } else {   // NB = 8: each half takes 4 members; read 8 and keep its 4
+        float rr[8], ri[8], ir[8], ii[8];
+        tmem_ld8(tl, rr);
+        tmem_ld8(tl + (unsigned)NB, ri);
+        tmem_ld8(tl + (unsigned)NCOL, ir);
+        tmem_ld8(tl + (unsigned)(NCOL + NB), ii);
+#pragma unroll
+        for (int c = 0; c < HB; ++c) {
+            dre[c] = rr[half * HB + c] - ii[half * HB + c];
+            dim[c] = ri[half * HB + c] + ir[half * HB + c];
+        }
+    }
+    if (r < q) {
+#pragma unroll
+        for (int c = 0; c < HB; ++c) {
+            const int b = half * HB + c;
+            if (b >= a.nb) continue;
+            float2* xj = a.x + (size_t)b * a.SB + (size_t)j * s * q + r;
+            float2 v = bad ? make_float2(__int_as_float(0x7fc00000), __int_as_float(0x7fc00000))
+                           : make_float2(dre[c], dim[c]);
+            if (MO::ADD && !bad) v = make_float2(old[c].x + v.x, old[c].y + v.y);
+            *xj = v;
+        }
+    }
+}
+
+template <int MODE, int NB, int KA>
+__global__ void __launch_bounds__(kThreads, 2) k_cr_mma(StepArgs a) {
+    using MO = ModeOf<MODE>;
+    constexpr int NV = MO::NV;
+    constexpr int BROWS = 2 * NB;                 // rows of one vector's B atom: [X_re; X_im]
+    constexpr unsigned BATOM = BROWS * 128;       // bytes of one vector's B atom
+    constexpr int NCOL = 2 * NB;                  // columns of one accumulator
+    constexpr int TCOLS = 2 * NCOL;               // two accumulators: M_re B, M_im B (32, 64 or 128)
+    const int q = a.q;
+    const int BR = (q + 7) / 8 * 8;
+    const int kStages = a.stages;
+    const unsigned kPlane = (unsigned)KA * (unsigned)BR * 128u;
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    unsigned char* As = base;
+    unsigned char* Bs = As + (size_t)kStages * kPlane;
+    auto* full = reinterpret_cast<unsigned long long*>(Bs + (size_t)NV * KA * BATOM);
+    auto* empty = full + kMaxStages;
+    auto* done = empty + kMaxStages;
+    unsigned* tslot = reinterpret_cast<unsigned*>(done + 1);
+    int* failed = reinterpret_cast<int*>(tslot + 1);
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int idx = blockIdx.x;
+    // The next step may be scheduled now (programmatic dependent launch): its CTAs set up
+    // and start streaming their factor planes, which no step writes, while this one runs.
+    asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
+    const StepGeom g = step_geom<MODE>(a, idx);
+    const bool* pres = g.pres;
+    const size_t* mat = g.mat;
+    const int npl = g.npl;
+
+    if (tid == 0) {
+        *failed = 0;
+        for (int i = 0; i < kStages; ++i) {
+            bar_init(&full[i], 1);
+            bar_init(&empty[i], 1);
+        }
+        bar_init(done, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+    }
+    if (warp == 0) {   // TMEM accumulator: 128 lanes x TCOLS columns
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(su32(tslot)),
+                     "r"(TCOLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    const unsigned tmem = *tslot;
+
+    // producer: the first min(npl, kStages) planes start streaming before B is built
+    auto plane_src = [&](int i) {   // i-th present plane: (vector slot, re/im)
+        int t = 0, r = i;
+        while (!pres[t] || r >= 2) {
+            if (pres[t]) r -= 2;
+            ++t;
+        }
+        return a.pool + (2 * mat[t] + r) * (size_t)KA * BR * 32;
+    };
+    if (tid == 0) {
+        for (int i = 0; i < npl && i < kStages; ++i) {
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(su32(&full[i])), "r"(kPlane)
+                         : "memory");
+            bulk_load(As + (size_t)i * kPlane, plane_src(i), kPlane, &full[i]);
+        }
+    }
+
+    // Vectors are read and written only after the previous kernel of the stream has
+    // completed and its writes are visible.
+    asm volatile("griddepcontrol.wait;\n" ::: "memory");
+
+    build_b<MODE, NB, KA>(a, g, Bs, tid);
     asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");   // B visible to the tensor cores
     __syncthreads();
 
@@ -374,62 +485,13 @@ __global__ void __launch_bounds__(kThreads, 2) k_cr_mma(StepArgs a) {
         }
     }
     // epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31 (rows r), columns split between w and w + 4
-    const int r = 32 * (warp & 3) + lane;
-    const int half = warp >> 2;   // 0: members [0, NB/2), 1: [NB/2, NB)
-    constexpr int HB = NB / 2;
-    float2 old[HB];   // x_j before the step (the steps that add), read while the products run
-#pragma unroll
-    for (int c = 0; c < HB; ++c) {
-        const int b = half * HB + c;
-        old[c] = (MO::ADD && r < q && b < a.nb) ? a.x[(size_t)b * a.SB + (size_t)j * s * q + r] : make_float2(0.f, 0.f);
-    }
+    float2 old[NB / 2];   // x_j before the step (the steps that add), read while the products run
+    load_old<MODE, NB>(a, g, warp, lane, old);
     const bool fin = bar_wait(done, 0);
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
     __syncthreads();
     const bool bad = !fin || *failed;
-    // D_re = M_re X_re - M_im X_im = acc0[:, b] - acc1[:, NB + b],
-    // D_im = M_re X_im + M_im X_re = acc0[:, NB + b] + acc1[:, b]
-    float dre[HB], dim[HB];
-    const unsigned tl = tmem + ((unsigned)(32 * (warp & 3)) << 16);
-    if constexpr (HB % 8 == 0) {
-#pragma unroll
-        for (int c = 0; c < HB; c += 8) {
-            float rr[8], ri[8], ir[8], ii[8];
-            const unsigned col = (unsigned)(half * HB + c);
-            tmem_ld8(tl + col, rr);
-            tmem_ld8(tl + (unsigned)NB + col, ri);
-            tmem_ld8(tl + (unsigned)NCOL + col, ir);
-            tmem_ld8(tl + (unsigned)(NCOL + NB) + col, ii);
-#pragma unroll
-            for (int e = 0; e < 8; ++e) {
-                dre[c + e] = rr[e] - ii[e];
-                dim[c + e] = ri[e] + ir[e];
-            }
-        }
-    } else {   // NB = 8: each half takes 4 members; read 8 and keep its 4
-        float rr[8], ri[8], ir[8], ii[8];
-        tmem_ld8(tl, rr);
-        tmem_ld8(tl + (unsigned)NB, ri);
-        tmem_ld8(tl + (unsigned)NCOL, ir);
-        tmem_ld8(tl + (unsigned)(NCOL + NB), ii);
-#pragma unroll
-        for (int c = 0; c < HB; ++c) {
-            dre[c] = rr[half * HB + c] - ii[half * HB + c];
-            dim[c] = ri[half * HB + c] + ir[half * HB + c];
-        }
-    }
-    if (r < q) {
-#pragma unroll
-        for (int c = 0; c < HB; ++c) {
-            const int b = half * HB + c;
-            if (b >= a.nb) continue;
-            float2* xj = a.x + (size_t)b * a.SB + (size_t)j * s * q + r;
-            float2 v = bad ? make_float2(__int_as_float(0x7fc00000), __int_as_float(0x7fc00000))
-                           : make_float2(dre[c], dim[c]);
-            if (MO::ADD && !bad) v = make_float2(old[c].x + v.x, old[c].y + v.y);
-            *xj = v;
-        }
-    }
+    store_step<MODE, NB>(a, g, tmem, bad, old, warp, lane);
     if (bad && tid == 0) atomicAdd(&g_cr_timeouts, 1u);
     asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
     __syncthreads();

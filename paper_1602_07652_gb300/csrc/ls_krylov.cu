@@ -84,7 +84,11 @@ int apply_op(ls_handle* h, Op op, const double2* x, double2* y) {
             LS_TRY(ls_apply_mx(h, x, y));
             return ls_timing_end(h, 0);
         }
-        default: return ls_stencil_apply(h, 0, 1, x, nullptr, y);
+        default: {
+            LS_TRY(ls_timing_begin(h));
+            LS_TRY(ls_stencil_apply(h, 0, 1, x, nullptr, y));
+            return ls_timing_end(h, 3);
+        }
     }
 }
 
@@ -142,7 +146,11 @@ int apply_pc_b(ls_handle* h, Pc pc, double2* v, double2* z, int nb, const unsign
     // Algorithm 3: z = GMRES(C, A v, Algorithm 2, inner_tol), all members at once
     Ctx* c = ctx_of(h);
     for (int b = 0; b < top; ++b)
-        if (on[b]) LS_TRY(ls_stencil_apply(h, 0, 0, v + b * N, nullptr, c->tmpA + b * N));
+        if (on[b]) {
+            LS_TRY(ls_timing_begin(h));
+            LS_TRY(ls_stencil_apply(h, 0, 0, v + b * N, nullptr, c->tmpA + b * N));
+            LS_TRY(ls_timing_end(h, 3));
+        }
     std::vector<double> tl(nb, h->opts.inner_tol);
     std::vector<Result> r(nb);
     LS_TRY(fgmres_b(h, c, c->inner, OP_C, PC_BD, c->tmpA, z, false, tl.data(), h->opts.inner_maxit, top, on,
