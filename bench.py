@@ -431,9 +431,17 @@ def run_ours(args):
     def theta(k):
         return direction(base, k, rank, world)
 
-    def step(k):  # B incident plane waves: right-hand sides on the device, one batched solve
+    rhs_events = []   # (start, end) of each timed step's right-hand-side convolutions
+
+    def step(k, timed=False):  # B incident plane waves: right-hand sides on the device, one batched solve
+        if timed:
+            ea, eb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            ea.record(s.stream)
         for b in range(B):
             s.ls_incident_rhs(theta(k * B + b), f[b])
+        if timed:
+            eb.record(s.stream)
+            rhs_events.append((ea, eb))
         _, st, _ = s.ls_solve_batch(f, wl["tol"], u)
         return st
 
@@ -454,7 +462,7 @@ def run_ours(args):
     ev0.record(stream)
     stats = []
     for k in range(args.steps):
-        stats.append(step(args.warmup + k))
+        stats.append(step(args.warmup + k, timed=True))
     ev1.record(stream)
     torch.cuda.synchronize()
     torch.cuda.nvtx.range_pop()
@@ -462,6 +470,7 @@ def run_ours(args):
     if world > 1:
         dist.barrier()
     ms = max_over_ranks(ev0.elapsed_time(ev1), world, "cuda")
+    t_rhs = sum(ea.elapsed_time(eb) for ea, eb in rhs_events)
     s.ls_set_timing(False)
     # end to end through the C ABI with host buffers: the same directions as the timed
     # steps, right-hand sides prepared in pinned host memory beforehand; each step copies
@@ -533,7 +542,9 @@ def run_ours(args):
                "time_shares": {"algorithm2": sum(st["t_sweep_ms"] for st in stats) / ms,
                                "ls_apply_fp32": t_app / ms,
                                "ls_apply_fp64_refinement": sum(st["t_apply64_ms"] for st in stats) / ms,
-                               "stencils_inner_solve": sum(st["t_stencil_ms"] for st in stats) / ms}}
+                               "stencils_inner_solve": sum(st["t_stencil_ms"] for st in stats) / ms,
+                               "arnoldi_orthogonalisation": sum(st["t_orth_ms"] for st in stats) / ms,
+                               "incident_rhs_fp64": t_rhs / ms}}
     s.close()
     if rank == 0 and world == 1 and not args.fp64 and not args.no_fp64_leg:
         # the plain FP64 GPU method on the same problem and tolerance, one right-hand side at

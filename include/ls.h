@@ -98,6 +98,9 @@ typedef struct {
     double t_stencil_ms;     /* device time of the 9-point stencil applies A v, C v of the inner
                                 solve (Algorithm 3), if timing                              */
     int n_stencil;           /* stencil applies counted in t_stencil_ms                      */
+    double t_orth_ms;        /* device time of the Arnoldi orthogonalisations (CGS2 dots and
+                                updates, both Krylov levels), if timing                     */
+    int n_orth;              /* Arnoldi steps counted in t_orth_ms                           */
 } ls_stats;
 
 typedef struct ls_handle ls_handle;

@@ -50,7 +50,8 @@ class Stats(ctypes.Structure):
                 ("t_apply64_ms", ctypes.c_double), ("n_apply64", ctypes.c_int),
                 ("t_sweep_ms", ctypes.c_double), ("n_sweep", ctypes.c_int),
                 ("kernel_launches", ctypes.c_longlong), ("learned_steps", ctypes.c_int),
-                ("t_stencil_ms", ctypes.c_double), ("n_stencil", ctypes.c_int)]
+                ("t_stencil_ms", ctypes.c_double), ("n_stencil", ctypes.c_int),
+                ("t_orth_ms", ctypes.c_double), ("n_orth", ctypes.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -132,6 +132,9 @@ int ls_timing_collect(ls_handle* h) {
         } else if (h->tkind[k] == 3) {
             h->t_stencil_ms += ms;
             h->n_stencil++;
+        } else if (h->tkind[k] == 4) {
+            h->t_orth_ms += ms;
+            h->n_orth++;
         } else {
             h->t_sweep_ms += ms;
             h->n_sweep++;
@@ -292,8 +295,8 @@ int ls_solve_batch(ls_handle* h, int nrhs, const ls_c64* f, double tol, ls_c64* 
     ls_stats local{};
     ls_stats* s = st ? st : &local;
     std::memset(s, 0, sizeof(*s));
-    h->t_apply_ms = h->t_sweep_ms = h->t_apply64_ms = h->t_stencil_ms = 0;
-    h->n_apply = h->n_sweep = h->n_apply64 = h->n_stencil = 0;
+    h->t_apply_ms = h->t_sweep_ms = h->t_apply64_ms = h->t_stencil_ms = h->t_orth_ms = 0;
+    h->n_apply = h->n_sweep = h->n_apply64 = h->n_stencil = h->n_orth = 0;
     h->learned_steps = 0;
     const long long l0 = h->launches;
     const auto t0 = std::chrono::steady_clock::now();
@@ -314,6 +317,8 @@ int ls_solve_batch(ls_handle* h, int nrhs, const ls_c64* f, double tol, ls_c64* 
     s->learned_steps = h->learned_steps;
     s->t_stencil_ms = h->t_stencil_ms;
     s->n_stencil = h->n_stencil;
+    s->t_orth_ms = h->t_orth_ms;
+    s->n_orth = h->n_orth;
     return rc;
 }
 

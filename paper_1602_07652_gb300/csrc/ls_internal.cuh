@@ -272,8 +272,8 @@ struct ls_handle {
                                // 1 for batches of 5 or more right-hand sides, 2 always
 
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
-    double t_apply_ms = 0, t_sweep_ms = 0, t_apply64_ms = 0, t_stencil_ms = 0;
-    int n_apply = 0, n_sweep = 0, n_apply64 = 0, n_stencil = 0;
+    double t_apply_ms = 0, t_sweep_ms = 0, t_apply64_ms = 0, t_stencil_ms = 0, t_orth_ms = 0;
+    int n_apply = 0, n_sweep = 0, n_apply64 = 0, n_stencil = 0, n_orth = 0;
     // timing without host synchronisation: event pairs recorded during a solve and
     // read once at its end (kind 0: FP32/mixed or FP64 apply, 1: Algorithm 2, 2: FP64 refinement apply)
     std::vector<cudaEvent_t> tev;   // 2 per interval

@@ -246,11 +246,13 @@ int fgmres_b(ls_handle* h, Ctx* c, KrylovSpace& S, Op op, Pc pc, const double2* 
                 double2* hd = S.hdev + i * HS;
                 LS_TRY(apply_op(h, op, Zb(j) + i * N, vn));
                 // CGS2 against V_0..V_j; coefficients stay on the device between the passes
+                LS_TRY(ls_timing_begin(h));
                 LS_TRY(ls_vec_dots_dev(h, j + 1, V(0, i), ldv, vn, hd));
                 LS_TRY(ls_vec_update(h, j + 1, V(0, i), ldv, hd, vn));
                 LS_TRY(ls_vec_dots_dev(h, j + 1, V(0, i), ldv, vn, hd + (m + 1)));
                 LS_TRY(ls_vec_update(h, j + 1, V(0, i), ldv, hd + (m + 1), vn));
                 LS_TRY(ls_vec_dots_dev(h, 1, vn, 0, vn, hd + 2 * (m + 1)));
+                LS_TRY(ls_timing_end(h, 4));
             }
             LS_CUDA(cudaMemcpyAsync(hh_all.data(), S.hdev, sizeof(double2) * HS * nb, cudaMemcpyDeviceToHost,
                                     h->stream));
