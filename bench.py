@@ -506,9 +506,9 @@ def run_ours(args):
         # algorithmic bytes of one LS-apply (three HBM passes over the n x P slab, P = 2n):
         # FP32: pass 1 reads u (8 n^2) and m (4 n^2) and writes the slab (16 n^2); pass 2
         # reads and writes it (32 n^2) and reads the Ghat quadrant (8 n^2); pass 3 reads it
-        # (16 n^2) and u (8 n^2) and writes y (8 n^2): 100 n^2.  FP64: 200 n^2.  The solve's
-        # mixed apply takes and returns FP64 fields (24 n^2 more moved); the method's bytes
-        # are the FP32 ones, so those are what the fraction is taken on.
+        # (16 n^2) and u (8 n^2) and writes y (8 n^2): 100 n^2.  FP64: 200 n^2.  The mixed
+        # solve's correction iteration keeps its Krylov vectors in FP32, so its applies
+        # take and return FP32 fields and move exactly these 100 n^2.
         bytes_apply = (200.0 if args.fp64 else 100.0) * n * n
         ach = bytes_apply / (t_app / n_app / 1e3) / 1e9 if n_app else None
         outer = statistics.mean(st["outer_iters"] for st in stats) / B  # per right-hand side
@@ -524,7 +524,7 @@ def run_ours(args):
                "roofline": {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
                             "frac": (ach / hbm) if ach else None, "traffic": None,
                             "kernel": "LS-apply (3 FFT passes), " + ("FP64" if args.fp64 else
-                                                                      "FP32 arithmetic, FP64 I/O"),
+                                                                      "FP32 arithmetic and I/O"),
                             "algorithmic_bytes": bytes_apply, "peak_source": src,
                             "launches": n_app, "avg_ms": t_app / n_app if n_app else None},
                "clocks": clk,

@@ -328,14 +328,27 @@ int ls_transpose64(ls_handle* h, const double2* a, double2* b);
 int ls_transpose64_b(ls_handle* h, const double2* a, double2* b, int nb);
 int ls_stencil_apply64(ls_handle* h, int dir, int mode, const double2* v, const double2* g, double2* y);
 int ls_stencil_apply_b(ls_handle* h, int dir, int withm, const double2* v, const double2* g, double2* y, int nb);
-int ls_stencil_refine_f32(ls_handle* h, int dir, const float2* v, const double2* g, float2* y, int nb);
+int ls_stencil_refine_f32(ls_handle* h, int dir, const float2* v, const float2* g, float2* y, int nb);
+int ls_stencil_apply_f32(ls_handle* h, int dir, int mode, const float2* v, float2* y);
+// Krylov vectors in FP64 (double2) or FP32 (float2); dot products summed in FP64
 int ls_vec_dots(ls_handle* h, int nvec, const double2* V, size_t ld, const double2* w, double2* out_host);
+int ls_vec_dots_dev(ls_handle* h, int nvec, const double2* V, size_t ld, const double2* w, double2* out_dev);
+int ls_vec_dots_dev(ls_handle* h, int nvec, const float2* V, size_t ld, const float2* w, double2* out_dev);
 int ls_vec_update(ls_handle* h, int nvec, const double2* V, size_t ld, const double2* coef_dev, double2* w);
+int ls_vec_update(ls_handle* h, int nvec, const float2* V, size_t ld, const double2* coef_dev, float2* w);
 int ls_vec_norm(ls_handle* h, const double2* w, double* out_host);
+int ls_vec_norm(ls_handle* h, const float2* w, double* out_host);
 int ls_vec_axpby(ls_handle* h, double2 a, const double2* x, double2 b, double2* y);  // y = a x + b y
+int ls_vec_axpby(ls_handle* h, double2 a, const float2* x, double2 b, float2* y);
+int ls_vec_axpby(ls_handle* h, double2 a, const float2* x, double2 b, double2* y);
 int ls_vec_copy(ls_handle* h, const double2* x, double2* y);
+int ls_vec_copy(ls_handle* h, const float2* x, float2* y);
+int ls_vec_copy(ls_handle* h, const double2* x, float2* y);   // rounded to FP32
+int ls_vec_copy(ls_handle* h, const float2* x, double2* y);   // widened
 int ls_vec_zero(ls_handle* h, double2* y);
+int ls_vec_zero(ls_handle* h, float2* y);
 int ls_vec_combine(ls_handle* h, int nvec, const double2* Z, size_t ld, const double2* coef_host, double2* x);
+int ls_vec_combine(ls_handle* h, int nvec, const float2* Z, size_t ld, const double2* coef_host, float2* x);
 
 // factorisation (ls_factor.cu)
 int ls_factor_all(ls_handle* h);
@@ -347,7 +360,10 @@ int ls_sweep_dir(ls_handle* h, int dir, const double2* g, double2* v);   // Algo
 int ls_sweep_dir_b(ls_handle* h, int dir, const double2* g, double2* v, int nb);
 int ls_sweep_reserve(ls_handle* h, int nb);
 int ls_bd_b(ls_handle* h, const double2* g, double2* v, int nb);         // Algorithm 2, nb right-hand sides
+int ls_bd_b(ls_handle* h, const float2* g, float2* v, int nb);           // the same on FP32 fields (LS_MIXED)
 int ls_bd_lanes(ls_handle* h, const double2* g, double2* v, int nb, int chunk,
+                const unsigned char* on = nullptr);
+int ls_bd_lanes(ls_handle* h, const float2* g, float2* v, int nb, int chunk,
                 const unsigned char* on = nullptr);  // chunks on concurrent lanes, idle chunks skipped
 void ls_lanes_free(ls_handle* h);
 int ls_bd(ls_handle* h, const double2* g, double2* v);                   // Algorithm 2

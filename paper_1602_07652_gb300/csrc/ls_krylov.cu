@@ -27,7 +27,6 @@
 
 #include "ls_internal.cuh"
 
-int ls_vec_dots_dev(ls_handle* h, int nvec, const double2* V, size_t ld, const double2* w, double2* out_dev);
 int ls_timing_begin(ls_handle* h);
 int ls_timing_end(ls_handle* h, int kind);
 
@@ -41,35 +40,62 @@ enum Pc { PC_NONE, PC_BD, PC_LS, PC_NET };
 // Vectors of a Krylov space for up to nbcap members: direction j of member b is
 // V + (j * nbcap + b) * N, so the members' j-th directions form one contiguous
 // block (what the batched preconditioner reads and writes).
+// VT: double2 (LS_FP64) or float2 (LS_MIXED: the FP32 correction solve and Algorithm 3).
+template <typename VT>
 struct KrylovSpace {
-    double2* V = nullptr;     // (m+1) blocks
-    double2* Z = nullptr;     // m blocks (preconditioned directions)
-    double2* w = nullptr;     // one block of work vectors
-    double2* r = nullptr;     // one block of residuals
+    VT* V = nullptr;          // (m+1) blocks
+    VT* Z = nullptr;          // m blocks (preconditioned directions)
+    VT* w = nullptr;          // one block of work vectors
+    VT* r = nullptr;          // one block of residuals
     double2* hdev = nullptr;  // per member: 2 (m+1) + 2 coefficients
     int m = 0;
 };
 
 struct Ctx {
     ls_handle* h;
-    KrylovSpace outer, inner;
-    double2* tmpA = nullptr;  // A r for Algorithm 3, one block
+    KrylovSpace<double2> outer, inner;      // LS_FP64
+    KrylovSpace<float2> outer32, inner32;   // LS_MIXED
+    double2* tmpA = nullptr;    // A r for Algorithm 3, one block (LS_FP64)
+    float2* tmpA32 = nullptr;   // the same in FP32 (LS_MIXED)
+    double2* dref = nullptr;    // LS_MIXED: the FP64 refinement residuals, one block
+    double2* stage64 = nullptr; // LS_MIXED: two FP64 fields (the learned step's input and output)
     int nbcap = 0;
 };
+template <typename VT> KrylovSpace<VT>& inner_space(Ctx* c);
+template <> KrylovSpace<double2>& inner_space<double2>(Ctx* c) { return c->inner; }
+template <> KrylovSpace<float2>& inner_space<float2>(Ctx* c) { return c->inner32; }
+double2* tmpA_of(Ctx* c, double2*) { return c->tmpA; }
+float2* tmpA_of(Ctx* c, float2*) { return c->tmpA32; }
 
 Ctx* ctx_of(ls_handle* h);
 
 size_t hstride(int m) { return 2 * (size_t)(m + 1) + 2; }
 
-int alloc_space(ls_handle* h, KrylovSpace& S, int m, int nbcap) {
+template <typename VT>
+int alloc_space(ls_handle* h, KrylovSpace<VT>& S, int m, int nbcap) {
     const size_t N = (size_t)h->n * h->n;
     S.m = m;
-    LS_CUDA(cudaMalloc(&S.V, sizeof(double2) * N * (m + 1) * nbcap));
-    LS_CUDA(cudaMalloc(&S.Z, sizeof(double2) * N * m * nbcap));
-    LS_CUDA(cudaMalloc(&S.w, sizeof(double2) * N * nbcap));
-    LS_CUDA(cudaMalloc(&S.r, sizeof(double2) * N * nbcap));
+    LS_CUDA(cudaMalloc(&S.V, sizeof(VT) * N * (m + 1) * nbcap));
+    LS_CUDA(cudaMalloc(&S.Z, sizeof(VT) * N * m * nbcap));
+    LS_CUDA(cudaMalloc(&S.w, sizeof(VT) * N * nbcap));
+    LS_CUDA(cudaMalloc(&S.r, sizeof(VT) * N * nbcap));
     LS_CUDA(cudaMalloc(&S.hdev, sizeof(double2) * hstride(m) * nbcap));
     return LS_OK;
+}
+
+// FP32 vectors (LS_MIXED): H with the FP32-I/O convolution, C with the FP32 stencil
+int apply_op(ls_handle* h, Op op, const float2* x, float2* y) {
+    if (op == OP_HMIX) {
+        LS_TRY(ls_timing_begin(h));
+        LS_TRY(ls_apply32(h, x, y));
+        return ls_timing_end(h, 0);
+    }
+    if (op == OP_C) {
+        LS_TRY(ls_timing_begin(h));
+        LS_TRY(ls_stencil_apply_f32(h, 0, 1, x, y));
+        return ls_timing_end(h, 3);
+    }
+    return LS_EINVAL;   // the FP64 apply takes FP64 vectors
 }
 
 int apply_op(ls_handle* h, Op op, const double2* x, double2* y) {
@@ -98,7 +124,8 @@ struct Result {
     bool converged = false;
 };
 
-int fgmres_b(ls_handle* h, Ctx* c, KrylovSpace& S, Op op, Pc pc, const double2* b, double2* x, bool x0,
+template <typename VT>
+int fgmres_b(ls_handle* h, Ctx* c, KrylovSpace<VT>& S, Op op, Pc pc, const VT* b, VT* x, bool x0,
              const double* tol, int maxit, int nb, const unsigned char* live, Result* res, ls_stats* st);
 
 // Right-hand sides per batched Algorithm 2 call: the autotuner's choice, else the
@@ -110,7 +137,37 @@ int bd_chunk(const ls_handle* h) {
 
 // z_b = M v_b for the members with on[b]; v and z are blocks of nb vectors.
 // Members that are off have their slot of v zeroed (their z is not used).
-int apply_pc_b(ls_handle* h, Pc pc, double2* v, double2* z, int nb, const unsigned char* on, ls_stats* st) {
+// The learned step on a member's field (the network takes FP64 fields): FP32 vectors go
+// through the two FP64 staging fields of the context.
+int net_apply(ls_handle* h, const double2* v, double2* z) {
+    return ls_net_apply_field(h->net, h->stream, h->n, h->n, v, h->m64, z);
+}
+int net_apply(ls_handle* h, const float2* v, float2* z) {
+    Ctx* c = ctx_of(h);
+    const size_t N = (size_t)h->n * h->n;
+    LS_TRY(ls_vec_copy(h, v, c->stage64));
+    LS_TRY(ls_net_apply_field(h->net, h->stream, h->n, h->n, c->stage64, h->m64, c->stage64 + N));
+    return ls_vec_copy(h, c->stage64 + N, z);
+}
+// Algorithm 1 (the Gauss-Seidel preconditioner option) on a chunk of members: FP64 fields
+// directly, FP32 ones through the upper half of the lane's FP64 scratch fields (the
+// horizontal sweep does not use them).
+int gs_chunk(ls_handle* h, const double2* v, double2* z, int cnt) { return ls_sweep_dir_b(h, 0, v, z, cnt); }
+int gs_chunk(ls_handle* h, const float2* v, float2* z, int cnt) {
+    const size_t N = (size_t)h->n * h->n;
+    LS_TRY(ls_sweep_reserve(h, cnt));
+    double2* in = static_cast<double2*>(h->lanes[h->lane].vtmp) + 2 * N * cnt;
+    double2* out = in + N * cnt;
+    for (int b = 0; b < cnt; ++b) LS_TRY(ls_vec_copy(h, v + b * N, in + b * N));
+    LS_TRY(ls_sweep_dir_b(h, 0, in, out, cnt));
+    for (int b = 0; b < cnt; ++b) LS_TRY(ls_vec_copy(h, out + b * N, z + b * N));
+    return LS_OK;
+}
+int stencil_A(ls_handle* h, const double2* v, double2* y) { return ls_stencil_apply(h, 0, 0, v, nullptr, y); }
+int stencil_A(ls_handle* h, const float2* v, float2* y) { return ls_stencil_apply_f32(h, 0, 0, v, y); }
+
+template <typename VT>
+int apply_pc_b(ls_handle* h, Pc pc, VT* v, VT* z, int nb, const unsigned char* on, ls_stats* st) {
     const size_t N = (size_t)h->n * h->n;
     int top = 0;
     for (int b = 0; b < nb; ++b)
@@ -123,7 +180,7 @@ int apply_pc_b(ls_handle* h, Pc pc, double2* v, double2* z, int nb, const unsign
     if (pc == PC_NET) {  // the learned step: z = s N(v / s, m)
         for (int b = 0; b < top; ++b)
             if (on[b]) {
-                LS_TRY(ls_net_apply_field(h->net, h->stream, h->n, h->n, v + b * N, h->m64, z + b * N));
+                LS_TRY(net_apply(h, v + b * N, z + b * N));
                 h->learned_steps++;
             }
         return LS_OK;
@@ -136,7 +193,7 @@ int apply_pc_b(ls_handle* h, Pc pc, double2* v, double2* z, int nb, const unsign
         if (h->opts.inner_precond == LS_PC_GS) {
             for (int b0 = 0; b0 < top; b0 += ch) {
                 const int cnt = top - b0 < ch ? top - b0 : ch;
-                LS_TRY(ls_sweep_dir_b(h, 0, v + b0 * N, z + b0 * N, cnt));
+                LS_TRY(gs_chunk(h, v + b0 * N, z + b0 * N, cnt));
             }
         } else {
             LS_TRY(ls_bd_lanes(h, v, z, top, ch, on));  // chunks run concurrently; idle ones are skipped
@@ -145,16 +202,17 @@ int apply_pc_b(ls_handle* h, Pc pc, double2* v, double2* z, int nb, const unsign
     }
     // Algorithm 3: z = GMRES(C, A v, Algorithm 2, inner_tol), all members at once
     Ctx* c = ctx_of(h);
+    VT* tA = tmpA_of(c, (VT*)nullptr);
     for (int b = 0; b < top; ++b)
         if (on[b]) {
             LS_TRY(ls_timing_begin(h));
-            LS_TRY(ls_stencil_apply(h, 0, 0, v + b * N, nullptr, c->tmpA + b * N));
+            LS_TRY(stencil_A(h, v + b * N, tA + b * N));
             LS_TRY(ls_timing_end(h, 3));
         }
     std::vector<double> tl(nb, h->opts.inner_tol);
     std::vector<Result> r(nb);
-    LS_TRY(fgmres_b(h, c, c->inner, OP_C, PC_BD, c->tmpA, z, false, tl.data(), h->opts.inner_maxit, top, on,
-                    r.data(), nullptr));
+    LS_TRY(fgmres_b(h, c, inner_space<VT>(c), OP_C, PC_BD, (const VT*)tA, z, false, tl.data(), h->opts.inner_maxit,
+                    top, on, r.data(), nullptr));
     if (st)
         for (int b = 0; b < top; ++b)
             if (on[b]) {
@@ -174,7 +232,8 @@ struct Member {
 
 // Flexible GMRES for members b < nb with live[b]: S.V, S.Z hold the members'
 // spaces; b, x are blocks of nb vectors (stride N).
-int fgmres_b(ls_handle* h, Ctx* c, KrylovSpace& S, Op op, Pc pc, const double2* b, double2* x, bool x0,
+template <typename VT>
+int fgmres_b(ls_handle* h, Ctx* c, KrylovSpace<VT>& S, Op op, Pc pc, const VT* b, VT* x, bool x0,
              const double* tol, int maxit, int nb, const unsigned char* live, Result* res, ls_stats* st) {
     const size_t N = (size_t)h->n * h->n;
     const size_t ldv = N * c->nbcap;  // distance between directions j and j+1 of a member
@@ -187,9 +246,9 @@ int fgmres_b(ls_handle* h, Ctx* c, KrylovSpace& S, Op op, Pc pc, const double2* 
         res[i] = Result{};
         if (!live[i]) continue;
         Member& e = M[i];
-        const double2* bi = b + i * N;
-        double2* xi = x + i * N;
-        double2* ri = S.r + i * N;
+        const VT* bi = b + i * N;
+        VT* xi = x + i * N;
+        VT* ri = S.r + i * N;
         LS_TRY(ls_vec_norm(h, bi, &e.nb));
         if (!std::isfinite(e.nb)) return LS_ENAN;
         if (e.nb == 0.0) {
@@ -242,7 +301,7 @@ int fgmres_b(ls_handle* h, Ctx* c, KrylovSpace& S, Op op, Pc pc, const double2* 
             LS_TRY(apply_pc_b(h, pcj, V(j, 0), Zb(j), nb, on.data(), st));
             for (int i = 0; i < nb; ++i) {
                 if (!on[i]) continue;
-                double2* vn = V(j + 1, i);
+                VT* vn = V(j + 1, i);
                 double2* hd = S.hdev + i * HS;
                 LS_TRY(apply_op(h, op, Zb(j) + i * N, vn));
                 // CGS2 against V_0..V_j; coefficients stay on the device between the passes
@@ -296,7 +355,7 @@ int fgmres_b(ls_handle* h, Ctx* c, KrylovSpace& S, Op op, Pc pc, const double2* 
                     e.cyc = false;
                     continue;
                 }
-                double2* vn = V(j + 1, i);
+                VT* vn = V(j + 1, i);
                 LS_TRY(ls_vec_axpby(h, make_double2(1.0 / hn, 0), vn, make_double2(0, 0), vn));
             }
         }
@@ -312,8 +371,8 @@ int fgmres_b(ls_handle* h, Ctx* c, KrylovSpace& S, Op op, Pc pc, const double2* 
             }
             std::vector<double2> yc(k);
             for (int r = 0; r < k; ++r) yc[r] = make_double2(e.y[r].real(), e.y[r].imag());
-            double2* xi = x + i * N;
-            double2* ri = S.r + i * N;
+            VT* xi = x + i * N;
+            VT* ri = S.r + i * N;
             LS_TRY(ls_vec_combine(h, k, Zb(0) + i * N, ldv, yc.data(), xi));
             LS_TRY(apply_op(h, op, xi, ri));
             LS_TRY(ls_vec_axpby(h, make_double2(1, 0), b + i * N, make_double2(-1, 0), ri));
@@ -337,15 +396,32 @@ int fgmres_b(ls_handle* h, Ctx* c, KrylovSpace& S, Op op, Pc pc, const double2* 
 // per-handle Krylov context
 namespace {
 Ctx* ctx_of(ls_handle* h) { return static_cast<Ctx*>(h->krylov); }
-void free_space(KrylovSpace& S) {
+template <typename VT>
+void free_space(KrylovSpace<VT>& S) {
     cudaFree(S.V);
     cudaFree(S.Z);
     cudaFree(S.w);
     cudaFree(S.r);
     cudaFree(S.hdev);
-    S = KrylovSpace{};
+    S = KrylovSpace<VT>{};
 }
-// Krylov spaces for nb members (grown on demand, never shrunk).
+void free_all(Ctx* c) {
+    free_space(c->outer);
+    free_space(c->inner);
+    free_space(c->outer32);
+    free_space(c->inner32);
+    cudaFree(c->tmpA);
+    cudaFree(c->tmpA32);
+    cudaFree(c->dref);
+    cudaFree(c->stage64);
+    c->tmpA = nullptr;
+    c->tmpA32 = nullptr;
+    c->dref = nullptr;
+    c->stage64 = nullptr;
+    c->nbcap = 0;
+}
+// Krylov spaces for nb members (grown on demand, never shrunk): FP64 vectors for
+// LS_FP64, FP32 ones (plus the FP64 refinement residuals) for LS_MIXED.
 int ctx_ensure(ls_handle* h, int nb) {
     Ctx* c = ctx_of(h);
     if (c && c->nbcap >= nb) return LS_OK;
@@ -354,15 +430,19 @@ int ctx_ensure(ls_handle* h, int nb) {
         c->h = h;
         h->krylov = c;
     }
-    free_space(c->outer);
-    free_space(c->inner);
-    cudaFree(c->tmpA);
-    c->tmpA = nullptr;
-    c->nbcap = 0;
+    free_all(c);
     const size_t N = (size_t)h->n * h->n;
-    LS_TRY(alloc_space(h, c->outer, h->opts.outer_restart, nb));
-    LS_TRY(alloc_space(h, c->inner, h->opts.inner_restart, nb));
-    LS_CUDA(cudaMalloc(&c->tmpA, sizeof(double2) * N * nb));
+    if (h->prec == LS_FP64) {
+        LS_TRY(alloc_space(h, c->outer, h->opts.outer_restart, nb));
+        LS_TRY(alloc_space(h, c->inner, h->opts.inner_restart, nb));
+        LS_CUDA(cudaMalloc(&c->tmpA, sizeof(double2) * N * nb));
+    } else {
+        LS_TRY(alloc_space(h, c->outer32, h->opts.outer_restart, nb));
+        LS_TRY(alloc_space(h, c->inner32, h->opts.inner_restart, nb));
+        LS_CUDA(cudaMalloc(&c->tmpA32, sizeof(float2) * N * nb));
+        LS_CUDA(cudaMalloc(&c->dref, sizeof(double2) * N * nb));
+        LS_CUDA(cudaMalloc(&c->stage64, sizeof(double2) * N * 2));
+    }
     c->nbcap = nb;
     return LS_OK;
 }
@@ -371,9 +451,7 @@ int ctx_ensure(ls_handle* h, int nb) {
 void ls_krylov_free(ls_handle* h) {
     Ctx* c = ctx_of(h);
     if (!c) return;
-    free_space(c->outer);
-    free_space(c->inner);
-    cudaFree(c->tmpA);
+    free_all(c);
     delete c;
     h->krylov = nullptr;
 }
@@ -383,7 +461,17 @@ int ls_inner_gmres(ls_handle* h, const double2* g, double tol, double2* v, int* 
     Ctx* c = ctx_of(h);
     Result r;
     const unsigned char live = 1;
-    LS_TRY(fgmres_b(h, c, c->inner, OP_C, PC_BD, g, v, false, &tol, h->opts.inner_maxit, 1, &live, &r, nullptr));
+    if (h->prec == LS_FP64) {
+        LS_TRY(fgmres_b(h, c, c->inner, OP_C, PC_BD, g, v, false, &tol, h->opts.inner_maxit, 1, &live, &r,
+                        nullptr));
+    } else {  // FP32 vectors: g rounded into the outer space's work block, the result widened into v
+        float2* g32 = c->outer32.w;
+        float2* v32 = c->inner32.w;
+        LS_TRY(ls_vec_copy(h, g, g32));
+        LS_TRY(fgmres_b(h, c, c->inner32, OP_C, PC_BD, (const float2*)g32, v32, false, &tol, h->opts.inner_maxit,
+                        1, &live, &r, nullptr));
+        LS_TRY(ls_vec_copy(h, (const float2*)v32, v));
+    }
     if (iters) *iters = r.iters;
     return r.converged ? LS_OK : LS_ENOCONV;
 }
@@ -430,11 +518,13 @@ int ls_outer_solve_b(ls_handle* h, int nb, const double2* f, double tol, double2
         }
         return all_conv ? LS_OK : LS_ENOCONV;
     }
-    // LS_MIXED: FP64 iterative refinement around the FP32-apply outer iteration.
-    // Blocks: outer.w holds the refinement right-hand sides and inner.w the
-    // corrections; flexible GMRES itself never touches either.
-    double2* d = c->outer.w;
-    double2* corr = c->inner.w;
+    // LS_MIXED: FP64 iterative refinement around the FP32 outer iteration. dref holds
+    // the FP64 residuals; outer32.w their FP32 roundings (the correction's right-hand
+    // sides) and inner32.w the FP32 corrections. Flexible GMRES itself never touches
+    // the w blocks of the space it runs in.
+    double2* d = c->dref;
+    float2* d32 = c->outer32.w;
+    float2* corr = c->inner32.w;
     if (!use_x0)
         for (int i = 0; i < nb; ++i)
             if (live[i]) LS_TRY(ls_vec_zero(h, u + i * N));
@@ -469,12 +559,15 @@ int ls_outer_solve_b(ls_handle* h, int nb, const double2* f, double tol, double2
             stol[i] = s;
         }
         if (!any) break;
-        LS_TRY(fgmres_b(h, c, c->outer, OP_HMIX, PC_LS, d, corr, false, stol.data(), h->opts.outer_maxit, nb,
-                        act.data(), r.data(), st));
+        for (int i = 0; i < nb; ++i)
+            if (act[i]) LS_TRY(ls_vec_copy(h, (const double2*)(d + i * N), d32 + i * N));
+        LS_TRY(fgmres_b(h, c, c->outer32, OP_HMIX, PC_LS, (const float2*)d32, corr, false, stol.data(),
+                        h->opts.outer_maxit, nb, act.data(), r.data(), st));
         for (int i = 0; i < nb; ++i) {
             if (!act[i]) continue;
             if (st) st->outer_iters += r[i].iters;
-            LS_TRY(ls_vec_axpby(h, make_double2(1, 0), corr + i * N, make_double2(1, 0), u + i * N));  // u += corr
+            LS_TRY(ls_vec_axpby(h, make_double2(1, 0), (const float2*)(corr + i * N), make_double2(1, 0),
+                                u + i * N));  // u += corr
             ++steps[i];
         }
     }

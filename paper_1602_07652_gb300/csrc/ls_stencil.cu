@@ -25,10 +25,10 @@ namespace {
 constexpr int kStX = 32, kStZ = 32, kStRows = 4;   // tile, rows per thread (threads 32 x 8)
 // VF, YF: element types of v and y (double2; float2 for the mixed Algorithm 2's fields,
 // which hold FP32 values: v is the FP32 sweep's result, y feeds the FP32 sweep).
-template <int MODE, typename R, typename VF = double2, typename YF = double2>  // 0: y = A v  1: y = C v  2: y = g - C v
+template <int MODE, typename R, typename VF = double2, typename YF = double2, typename GF = double2>  // 0: y = A v  1: y = C v  2: y = g - C v
 __global__ void __launch_bounds__(256) k_stencil(int n, const StencilTables* __restrict__ tab,
                                                  const double* __restrict__ m, const VF* __restrict__ v,
-                                                 const double2* __restrict__ g, YF* __restrict__ y) {
+                                                 const GF* __restrict__ g, YF* __restrict__ y) {
     using CR = cpx_t<R>;
     constexpr int HX = kStX + 2, HZ = kStZ + 2, HN = HX * HZ;
     __shared__ CR sa[81], sb[81];
@@ -97,7 +97,7 @@ __global__ void __launch_bounds__(256) k_stencil(int n, const StencilTables* __r
         }
         const size_t k = (size_t)j * n + i;
         double2 out = ccast<double2>(acc);
-        if (MODE == 2) out = __ldg(&g[k]) - out;
+        if (MODE == 2) out = ccast<double2>(__ldg(&g[k])) - out;
         y[k] = ccast<YF>(out);
     }
 }
@@ -135,16 +135,25 @@ __global__ void k_transpose_real(int n, const double* __restrict__ a, double* __
 constexpr int RED_BLOCKS = 608;   // 4 x 152 SMs
 constexpr int RED_THREADS = 256;
 
+// Vector kernels for FP64 (double2) and FP32 (float2) Krylov vectors.  FP32 vectors are
+// combined in FP32 (coefficients rounded once) and their dot products formed in FP32
+// per thread and summed in FP64 across threads and blocks, in a fixed order.
+template <typename VT> struct Acc;   // the per-thread dot accumulator of a vector type
+template <> struct Acc<double2> { using T = double2; };
+template <> struct Acc<float2> { using T = float2; };
+template <typename VT> __device__ __forceinline__ VT vt_of(double2 c) { return ccast<VT>(c); }
+
 // partial[b * nvec + i] = sum over block b's elements of conj(V_i) w   (i < nvec)
-__global__ void k_dots(size_t N, int nvec, const double2* __restrict__ V, size_t ld,
-                       const double2* __restrict__ w, double2* __restrict__ partial) {
+template <typename VT>
+__global__ void k_dots(size_t N, int nvec, const VT* __restrict__ V, size_t ld, const VT* __restrict__ w,
+                       double2* __restrict__ partial) {
     __shared__ double2 red[RED_THREADS];
     for (int i = 0; i < nvec; ++i) {
-        const double2* vi = V + (size_t)i * ld;
-        double2 acc = make_double2(0, 0);
+        const VT* vi = V + (size_t)i * ld;
+        VT acc = czero<VT>();
         for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < N; k += (size_t)gridDim.x * blockDim.x)
             acc = cconjmul_acc(__ldg(&vi[k]), __ldg(&w[k]), acc);
-        red[threadIdx.x] = acc;
+        red[threadIdx.x] = ccast<double2>(acc);
         __syncthreads();
         for (int s = blockDim.x / 2; s > 0; s >>= 1) {
             if (threadIdx.x < s) red[threadIdx.x] = red[threadIdx.x] + red[threadIdx.x + s];
@@ -173,13 +182,14 @@ __global__ void k_dots_final(int nblk, int nvec, const double2* __restrict__ par
 }
 
 // w -= sum_i coef[i] V_i
-__global__ void k_update(size_t N, int nvec, const double2* __restrict__ V, size_t ld,
-                         const double2* __restrict__ coef, double2* __restrict__ w) {
-    __shared__ double2 sc[128];
-    for (int i = threadIdx.x; i < nvec; i += blockDim.x) sc[i] = coef[i];
+template <typename VT>
+__global__ void k_update(size_t N, int nvec, const VT* __restrict__ V, size_t ld, const double2* __restrict__ coef,
+                         VT* __restrict__ w) {
+    __shared__ VT sc[128];
+    for (int i = threadIdx.x; i < nvec; i += blockDim.x) sc[i] = vt_of<VT>(coef[i]);
     __syncthreads();
     for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < N; k += (size_t)gridDim.x * blockDim.x) {
-        double2 acc = w[k];
+        VT acc = w[k];
         for (int i = 0; i < nvec; ++i) acc = cfms(sc[i], __ldg(&V[(size_t)i * ld + k]), acc);
         w[k] = acc;
     }
@@ -188,29 +198,35 @@ __global__ void k_update(size_t N, int nvec, const double2* __restrict__ V, size
 struct Coefs {
     double2 c[64];
 };
-// x += sum_i c_i Z_i
-__global__ void k_combine(size_t N, int nvec, const double2* __restrict__ Z, size_t ld, Coefs cf,
-                          double2* __restrict__ x) {
+// x += sum_i c_i Z_i  (Z of type ZT; x of type XT, summed in XT's precision)
+template <typename ZT, typename XT>
+__global__ void k_combine(size_t N, int nvec, const ZT* __restrict__ Z, size_t ld, Coefs cf, XT* __restrict__ x) {
     for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < N; k += (size_t)gridDim.x * blockDim.x) {
-        double2 acc = x[k];
-        for (int i = 0; i < nvec; ++i) acc = cfma(cf.c[i], __ldg(&Z[(size_t)i * ld + k]), acc);
+        XT acc = x[k];
+        for (int i = 0; i < nvec; ++i) acc = cfma(vt_of<XT>(cf.c[i]), ccast<XT>(__ldg(&Z[(size_t)i * ld + k])), acc);
         x[k] = acc;
     }
 }
 
-__global__ void k_axpby(size_t N, double2 a, const double2* __restrict__ x, double2 b, double2* __restrict__ y) {
+// y = a x + b y  (x of type XT, y of type YT, arithmetic in YT's precision)
+template <typename XT, typename YT>
+__global__ void k_axpby(size_t N, double2 a, const XT* __restrict__ x, double2 b, YT* __restrict__ y) {
+    const YT aa = vt_of<YT>(a), bb = vt_of<YT>(b);
     for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < N; k += (size_t)gridDim.x * blockDim.x)
-        y[k] = a * x[k] + b * y[k];
+        y[k] = aa * ccast<YT>(x[k]) + bb * y[k];
 }
 
-__global__ void k_copy(size_t N, const double2* __restrict__ x, double2* __restrict__ y) {
+// y = x, converting between the vector types
+template <typename XT, typename YT>
+__global__ void k_copy(size_t N, const XT* __restrict__ x, YT* __restrict__ y) {
     for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < N; k += (size_t)gridDim.x * blockDim.x)
-        y[k] = x[k];
+        y[k] = ccast<YT>(x[k]);
 }
 
-__global__ void k_zero(size_t N, double2* __restrict__ y) {
+template <typename VT>
+__global__ void k_zero(size_t N, VT* __restrict__ y) {
     for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < N; k += (size_t)gridDim.x * blockDim.x)
-        y[k] = make_double2(0, 0);
+        y[k] = czero<VT>();
 }
 
 // mismatches of the integer-pipe conversions against the hardware ones (NaN: NaN-ness only)
@@ -273,12 +289,26 @@ int ls_stencil_apply_b(ls_handle* h, int dir, int mode, const double2* v, const 
 
 // Algorithm 2's refinement residual e = g - C u1 in mixed precision, u1 and e in FP32
 // storage (their values are FP32 either way); FP32 coefficients and sums.
-int ls_stencil_refine_f32(ls_handle* h, int dir, const float2* v, const double2* g, float2* y, int nb) {
+int ls_stencil_refine_f32(ls_handle* h, int dir, const float2* v, const float2* g, float2* y, int nb) {
     const int n = h->n;
     const dim3 grid((unsigned)((n + kStX - 1) / kStX), (unsigned)((n + kStZ - 1) / kStZ), nb);
     const dim3 block(kStX, 256 / kStX);
     const double* m = dir == 0 ? h->m64 : h->mT64;
-    LS_LAUNCH(h, (k_stencil<2, float, float2, float2>), grid, block, 0, n, h->dtabs + dir, m, v, g, y);
+    LS_LAUNCH(h, (k_stencil<2, float, float2, float2, float2>), grid, block, 0, n, h->dtabs + dir, m, v, g, y);
+    return LS_OK;
+}
+
+// y = A v (mode 0) or C v (mode 1) with FP32 vectors and FP32 arithmetic (the mixed
+// precision inner solve's operator)
+int ls_stencil_apply_f32(ls_handle* h, int dir, int mode, const float2* v, float2* y) {
+    const int n = h->n;
+    const dim3 grid((unsigned)((n + kStX - 1) / kStX), (unsigned)((n + kStZ - 1) / kStZ), 1);
+    const dim3 block(kStX, 256 / kStX);
+    const double* m = dir == 0 ? h->m64 : h->mT64;
+    const StencilTables* tab = h->dtabs + dir;
+    const double2* none = nullptr;
+    if (mode == 0) LS_LAUNCH(h, (k_stencil<0, float, float2, float2>), grid, block, 0, n, tab, m, v, none, y);
+    else LS_LAUNCH(h, (k_stencil<1, float, float2, float2>), grid, block, 0, n, tab, m, v, none, y);
     return LS_OK;
 }
 
@@ -315,19 +345,21 @@ static int red_reserve(ls_handle* h, size_t cnt) {
 }
 
 // dots into device memory out_dev[0..nvec)
-int ls_vec_dots_dev(ls_handle* h, int nvec, const double2* V, size_t ld, const double2* w, double2* out_dev) {
+template <typename VT>
+int vec_dots_dev(ls_handle* h, int nvec, const VT* V, size_t ld, const VT* w, double2* out_dev) {
     const size_t N = (size_t)h->n * h->n;
     LS_TRY(red_reserve(h, (size_t)RED_BLOCKS * 64 + 256));
     double2* partial = reinterpret_cast<double2*>(h->red);
-    LS_LAUNCH(h, k_dots, RED_BLOCKS, RED_THREADS, 0, N, nvec, V, ld, w, partial);
+    LS_LAUNCH(h, k_dots<VT>, RED_BLOCKS, RED_THREADS, 0, N, nvec, V, ld, w, partial);
     LS_LAUNCH(h, k_dots_final, 1, RED_THREADS, 0, RED_BLOCKS, nvec, partial, out_dev);
     return LS_OK;
 }
 
-int ls_vec_dots(ls_handle* h, int nvec, const double2* V, size_t ld, const double2* w, double2* out_host) {
+template <typename VT>
+int vec_dots(ls_handle* h, int nvec, const VT* V, size_t ld, const VT* w, double2* out_host) {
     LS_TRY(red_reserve(h, (size_t)RED_BLOCKS * 64 + 256));
     double2* outd = reinterpret_cast<double2*>(h->red) + (size_t)RED_BLOCKS * 64;
-    LS_TRY(ls_vec_dots_dev(h, nvec, V, ld, w, outd));
+    LS_TRY(vec_dots_dev(h, nvec, V, ld, w, outd));
     LS_CUDA(cudaMemcpyAsync(h->red_host, outd, sizeof(double2) * nvec, cudaMemcpyDeviceToHost, h->stream));
     LS_CUDA(cudaStreamSynchronize(h->stream));
     const double2* hr = reinterpret_cast<const double2*>(h->red_host);
@@ -335,45 +367,96 @@ int ls_vec_dots(ls_handle* h, int nvec, const double2* V, size_t ld, const doubl
     return LS_OK;
 }
 
-int ls_vec_update(ls_handle* h, int nvec, const double2* V, size_t ld, const double2* coef_dev, double2* w) {
-    const size_t N = (size_t)h->n * h->n;
-    LS_LAUNCH(h, k_update, RED_BLOCKS, RED_THREADS, 0, N, nvec, V, ld, coef_dev, w);
-    return LS_OK;
-}
-
-int ls_vec_norm(ls_handle* h, const double2* w, double* out_host) {
+template <typename VT>
+int vec_norm(ls_handle* h, const VT* w, double* out_host) {
     double2 d;
-    LS_TRY(ls_vec_dots(h, 1, w, 0, w, &d));
+    LS_TRY(vec_dots(h, 1, w, 0, w, &d));
     // a NaN or Inf anywhere in w must surface as a non-finite norm
     *out_host = d.x >= 0 ? sqrt(d.x) : (d.x < 0 ? 0.0 : d.x);
     return LS_OK;
 }
 
-int ls_vec_combine(ls_handle* h, int nvec, const double2* Z, size_t ld, const double2* coef_host, double2* x) {
+template <typename ZT, typename XT>
+int vec_combine(ls_handle* h, int nvec, const ZT* Z, size_t ld, const double2* coef_host, XT* x) {
     const size_t N = (size_t)h->n * h->n;
     for (int base = 0; base < nvec; base += 64) {
         Coefs cf;
         const int cnt = nvec - base < 64 ? nvec - base : 64;
         for (int i = 0; i < cnt; ++i) cf.c[i] = coef_host[base + i];
-        LS_LAUNCH(h, k_combine, RED_BLOCKS, RED_THREADS, 0, N, cnt, Z + (size_t)base * ld, ld, cf, x);
+        LS_LAUNCH(h, (k_combine<ZT, XT>), RED_BLOCKS, RED_THREADS, 0, N, cnt, Z + (size_t)base * ld, ld, cf, x);
     }
     return LS_OK;
 }
 
+int ls_vec_dots_dev(ls_handle* h, int nvec, const double2* V, size_t ld, const double2* w, double2* out_dev) {
+    return vec_dots_dev(h, nvec, V, ld, w, out_dev);
+}
+int ls_vec_dots_dev(ls_handle* h, int nvec, const float2* V, size_t ld, const float2* w, double2* out_dev) {
+    return vec_dots_dev(h, nvec, V, ld, w, out_dev);
+}
+int ls_vec_dots(ls_handle* h, int nvec, const double2* V, size_t ld, const double2* w, double2* out_host) {
+    return vec_dots(h, nvec, V, ld, w, out_host);
+}
+int ls_vec_update(ls_handle* h, int nvec, const double2* V, size_t ld, const double2* coef_dev, double2* w) {
+    const size_t N = (size_t)h->n * h->n;
+    LS_LAUNCH(h, k_update<double2>, RED_BLOCKS, RED_THREADS, 0, N, nvec, V, ld, coef_dev, w);
+    return LS_OK;
+}
+int ls_vec_update(ls_handle* h, int nvec, const float2* V, size_t ld, const double2* coef_dev, float2* w) {
+    const size_t N = (size_t)h->n * h->n;
+    LS_LAUNCH(h, k_update<float2>, RED_BLOCKS, RED_THREADS, 0, N, nvec, V, ld, coef_dev, w);
+    return LS_OK;
+}
+int ls_vec_norm(ls_handle* h, const double2* w, double* out_host) { return vec_norm(h, w, out_host); }
+int ls_vec_norm(ls_handle* h, const float2* w, double* out_host) { return vec_norm(h, w, out_host); }
+int ls_vec_combine(ls_handle* h, int nvec, const double2* Z, size_t ld, const double2* coef_host, double2* x) {
+    return vec_combine(h, nvec, Z, ld, coef_host, x);
+}
+int ls_vec_combine(ls_handle* h, int nvec, const float2* Z, size_t ld, const double2* coef_host, float2* x) {
+    return vec_combine(h, nvec, Z, ld, coef_host, x);
+}
 int ls_vec_axpby(ls_handle* h, double2 a, const double2* x, double2 b, double2* y) {
     const size_t N = (size_t)h->n * h->n;
-    LS_LAUNCH(h, k_axpby, RED_BLOCKS, RED_THREADS, 0, N, a, x, b, y);
+    LS_LAUNCH(h, (k_axpby<double2, double2>), RED_BLOCKS, RED_THREADS, 0, N, a, x, b, y);
     return LS_OK;
 }
-
+int ls_vec_axpby(ls_handle* h, double2 a, const float2* x, double2 b, float2* y) {
+    const size_t N = (size_t)h->n * h->n;
+    LS_LAUNCH(h, (k_axpby<float2, float2>), RED_BLOCKS, RED_THREADS, 0, N, a, x, b, y);
+    return LS_OK;
+}
+int ls_vec_axpby(ls_handle* h, double2 a, const float2* x, double2 b, double2* y) {   // FP64 y += FP32 x
+    const size_t N = (size_t)h->n * h->n;
+    LS_LAUNCH(h, (k_axpby<float2, double2>), RED_BLOCKS, RED_THREADS, 0, N, a, x, b, y);
+    return LS_OK;
+}
 int ls_vec_copy(ls_handle* h, const double2* x, double2* y) {
     const size_t N = (size_t)h->n * h->n;
-    LS_LAUNCH(h, k_copy, RED_BLOCKS, RED_THREADS, 0, N, x, y);
+    LS_LAUNCH(h, (k_copy<double2, double2>), RED_BLOCKS, RED_THREADS, 0, N, x, y);
     return LS_OK;
 }
-
+int ls_vec_copy(ls_handle* h, const float2* x, float2* y) {
+    const size_t N = (size_t)h->n * h->n;
+    LS_LAUNCH(h, (k_copy<float2, float2>), RED_BLOCKS, RED_THREADS, 0, N, x, y);
+    return LS_OK;
+}
+int ls_vec_copy(ls_handle* h, const double2* x, float2* y) {   // rounded to FP32
+    const size_t N = (size_t)h->n * h->n;
+    LS_LAUNCH(h, (k_copy<double2, float2>), RED_BLOCKS, RED_THREADS, 0, N, x, y);
+    return LS_OK;
+}
+int ls_vec_copy(ls_handle* h, const float2* x, double2* y) {   // widened (exact)
+    const size_t N = (size_t)h->n * h->n;
+    LS_LAUNCH(h, (k_copy<float2, double2>), RED_BLOCKS, RED_THREADS, 0, N, x, y);
+    return LS_OK;
+}
 int ls_vec_zero(ls_handle* h, double2* y) {
     const size_t N = (size_t)h->n * h->n;
-    LS_LAUNCH(h, k_zero, RED_BLOCKS, RED_THREADS, 0, N, y);
+    LS_LAUNCH(h, k_zero<double2>, RED_BLOCKS, RED_THREADS, 0, N, y);
+    return LS_OK;
+}
+int ls_vec_zero(ls_handle* h, float2* y) {
+    const size_t N = (size_t)h->n * h->n;
+    LS_LAUNCH(h, k_zero<float2>, RED_BLOCKS, RED_THREADS, 0, N, y);
     return LS_OK;
 }

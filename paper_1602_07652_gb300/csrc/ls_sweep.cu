@@ -397,9 +397,9 @@ __global__ void k_scatter(StripGeom g, const cpx_t<T>* __restrict__ sol, size_t 
 // The same for the other direction's field, added to a field of this one:
 // v[i][z] = u[i][z] + (row z of the layers' solutions)[i]  (the vertical sweep's result
 // transposed back and added to the horizontal one, Algorithm 2); along z, coalesced.
-template <typename T, typename AF = double2>
+template <typename T, typename AF = double2, typename OF = double2>
 __global__ void k_scatter_tadd(StripGeom g, const cpx_t<T>* __restrict__ sol, size_t strip_stride, size_t SB,
-                               const AF* __restrict__ u, double2* __restrict__ v) {
+                               const AF* __restrict__ u, OF* __restrict__ v) {
     const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int n = g.n;
     if (e >= (size_t)n * n) return;
@@ -407,7 +407,7 @@ __global__ void k_scatter_tadd(StripGeom g, const cpx_t<T>* __restrict__ sol, si
     const int i = (int)(e / n), z = (int)(e % n);
     const int l = z / g.t, r = z - l * g.t + g.E;
     const size_t o = b * (size_t)n * n + e;
-    v[o] = ccast<double2>(u[o]) + ccast<double2>(sol[b * SB + (size_t)l * strip_stride + (size_t)i * g.q + r]);
+    v[o] = ccast<OF>(ccast<double2>(u[o]) + ccast<double2>(sol[b * SB + (size_t)l * strip_stride + (size_t)i * g.q + r]));
 }
 
 // natural strip layout (q rows x n, x fastest) <-> block layout (i*q + r)
@@ -582,12 +582,10 @@ int sweep_impl(ls_handle* h, int dir, const GF* g, OF* v, int nb, bool tr = fals
         LS_TRY(cr_solve<T>(h, dir, l, sol + l * sstride, SB, nb));
     }
     const size_t N = (size_t)n * n;
-    if constexpr (sizeof(OF) == sizeof(double2)) {
-        if (tr && add) {
-            LS_LAUNCH(h, (k_scatter_tadd<T, AF>), dim3((unsigned)((N + 255) / 256), nb), 256, 0, geo, sol, sstride, SB,
-                      add, v);
-            return LS_OK;
-        }
+    if (tr && add) {
+        LS_LAUNCH(h, (k_scatter_tadd<T, AF, OF>), dim3((unsigned)((N + 255) / 256), nb), 256, 0, geo, sol, sstride, SB,
+                  add, v);
+        return LS_OK;
     }
     LS_LAUNCH(h, (k_scatter<T, OF>), dim3((unsigned)((N + 255) / 256), nb), 256, 0, geo, sol, sstride, SB, v);
     return LS_OK;
@@ -712,21 +710,23 @@ int ls_sweep_dir(ls_handle* h, int dir, const double2* g, double2* v) { return l
 
 // Algorithm 2 for nb right-hand sides: v = u1 + u2, u1 = Alg. 1 horizontal (g),
 // u2 = Alg. 1 vertical (g - C u1).
+// Mixed precision: the fields g, v and the intermediate u1, e are FP32 (the values the FP32
+// sweeps read and produce), half the traffic of FP64 fields.
+static int bd_direct_mixed(ls_handle* h, const float2* g, float2* v, int nb) {
+    const size_t N = (size_t)h->n * h->n;
+    float2* u1f = reinterpret_cast<float2*>(static_cast<double2*>(h->lanes[h->lane].vtmp) + 2 * N * nb);
+    float2* ef = u1f + N * nb;
+    LS_TRY((sweep_impl<float, float2, float2, float2>(h, 0, g, u1f, nb)));
+    LS_TRY(ls_stencil_refine_f32(h, 0, u1f, g, ef, nb));   // e = g - C u1
+    // vertical layers on e as it is stored (their grid is its transpose): the gather reads
+    // it transposed, and the scatter writes v = u1 + the result, transposed back
+    return sweep_impl<float, float2, float2, float2>(h, 1, ef, v, nb, true, u1f);
+}
+
 static int bd_direct(ls_handle* h, const double2* g, double2* v, int nb) {
     const size_t N = (size_t)h->n * h->n;
     double2* u1 = static_cast<double2*>(h->lanes[h->lane].vtmp) + 2 * N * nb;
     double2* e = u1 + N * nb;
-    if (h->prec == LS_MIXED) {
-        // u1 and e hold FP32 values (the FP32 sweep's result; the residual the FP32 sweep
-        // reads), so they are stored in FP32: the same numbers with half the traffic
-        if (nb < 1 || nb > ls_bd_cap(h)) return LS_EINVAL;
-        LS_TRY(ls_sweep_reserve(h, nb));
-        float2* u1f = reinterpret_cast<float2*>(u1);
-        float2* ef = reinterpret_cast<float2*>(e);
-        LS_TRY((sweep_impl<float, double2, float2, float2>(h, 0, g, u1f, nb)));
-        LS_TRY(ls_stencil_refine_f32(h, 0, u1f, g, ef, nb));   // e = g - C u1
-        return sweep_impl<float, float2, double2, float2>(h, 1, ef, v, nb, true, u1f);
-    }
     LS_TRY(ls_sweep_dir_b(h, 0, g, u1, nb));
     LS_TRY(ls_stencil_apply_b(h, 0, 2, u1, g, e, nb));   // e = g - C u1
     // vertical layers on e as it is stored (their grid is its transpose): the gather reads
@@ -750,7 +750,11 @@ static int bd_capture(ls_handle* h, int nb) {
     cudaGraph_t graph = nullptr;
     cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
-        rc = bd_direct(h, h->lanes[h->lane].bd_in, h->lanes[h->lane].bd_out, nb);
+        if (h->prec == LS_MIXED)
+            rc = bd_direct_mixed(h, reinterpret_cast<const float2*>(h->lanes[h->lane].bd_in),
+                                 reinterpret_cast<float2*>(h->lanes[h->lane].bd_out), nb);
+        else
+            rc = bd_direct(h, h->lanes[h->lane].bd_in, h->lanes[h->lane].bd_out, nb);
         e = cudaStreamEndCapture(cap, &graph);
     }
     h->stream = saved;
@@ -775,13 +779,44 @@ static int bd_capture(ls_handle* h, int nb) {
     return LS_OK;
 }
 
-int ls_bd_b(ls_handle* h, const double2* g, double2* v, int nb) {
+// Algorithm 2 on FP32 fields (mixed precision): the captured graph reads and writes the
+// lane's staging buffers as FP32.
+int ls_bd_b(ls_handle* h, const float2* g, float2* v, int nb) {
+    if (h->prec != LS_MIXED) return LS_ESTATE;
     if (nb < 1 || nb > ls_bd_cap(h)) return LS_EINVAL;
     LS_TRY(ls_sweep_reserve(h, nb));
-    if (!h->opts.use_graphs) return bd_direct(h, g, v, nb);
+    if (!h->opts.use_graphs) return bd_direct_mixed(h, g, v, nb);
     ls_handle::SweepLane& W = h->lanes[h->lane];
     if (!W.exec[nb]) LS_TRY(bd_capture(h, nb));
     const size_t N = (size_t)h->n * h->n;
+    LS_CUDA(cudaMemcpyAsync(W.bd_in, g, sizeof(float2) * N * nb, cudaMemcpyDeviceToDevice, h->stream));
+    LS_CUDA(cudaGraphLaunch(W.exec[nb], h->stream));
+    h->launches += W.nodes[nb];
+    LS_CUDA(cudaMemcpyAsync(v, W.bd_out, sizeof(float2) * N * nb, cudaMemcpyDeviceToDevice, h->stream));
+    return LS_OK;
+}
+
+int ls_bd_b(ls_handle* h, const double2* g, double2* v, int nb) {
+    if (nb < 1 || nb > ls_bd_cap(h)) return LS_EINVAL;
+    LS_TRY(ls_sweep_reserve(h, nb));
+    ls_handle::SweepLane& W = h->lanes[h->lane];
+    const size_t N = (size_t)h->n * h->n;
+    if (h->prec == LS_MIXED) {   // through FP32 copies in the lane's staging buffers
+        float2* in = reinterpret_cast<float2*>(W.bd_in);
+        float2* out = reinterpret_cast<float2*>(W.bd_out);
+        for (int b = 0; b < nb; ++b) LS_TRY(ls_vec_copy(h, g + b * N, in + b * N));
+        if (!h->opts.use_graphs) {
+            LS_TRY(bd_direct_mixed(h, in, out, nb));
+        } else {
+            if (!W.exec[nb]) LS_TRY(bd_capture(h, nb));
+            LS_CUDA(cudaGraphLaunch(W.exec[nb], h->stream));
+            h->launches += W.nodes[nb];
+        }
+        for (int b = 0; b < nb; ++b) LS_TRY(ls_vec_copy(h, out + b * N, v + b * N));
+        return LS_OK;
+    }
+    if (!h->opts.use_graphs) return bd_direct(h, g, v, nb);
+    if (!W.exec[nb]) LS_TRY(bd_capture(h, nb));
     LS_CUDA(cudaMemcpyAsync(W.bd_in, g, sizeof(double2) * N * nb, cudaMemcpyDeviceToDevice, h->stream));
     LS_CUDA(cudaGraphLaunch(W.exec[nb], h->stream));
     h->launches += W.nodes[nb];
@@ -789,13 +824,8 @@ int ls_bd_b(ls_handle* h, const double2* g, double2* v, int nb) {
     return LS_OK;
 }
 
-// Algorithm 2 for nb right-hand sides in chunks of `chunk`: the k-th chunk that
-// holds a member with on[b] (all, if on is null) runs on lane k mod kLanes, each
-// lane with its own workspace and stream, so the chunks' chains of dependent
-// launches overlap on the GPU; chunks without such a member are skipped (their
-// outputs are left as they were).  Ordered after the work already on the
-// handle's stream; the handle's stream waits for all chunks.
-int ls_bd_lanes(ls_handle* h, const double2* g, double2* v, int nb, int chunk, const unsigned char* on) {
+template <typename FT>
+static int bd_lanes(ls_handle* h, const FT* g, FT* v, int nb, int chunk, const unsigned char* on) {
     if (chunk < 1) return LS_EINVAL;
     const size_t N = (size_t)h->n * h->n;
     const int nchunks = (nb + chunk - 1) / chunk;
@@ -839,6 +869,13 @@ int ls_bd_lanes(ls_handle* h, const double2* g, double2* v, int nb, int chunk, c
         cudaStreamWaitEvent(main, h->lanes[k].done, 0);
     }
     return rc;
+}
+
+int ls_bd_lanes(ls_handle* h, const double2* g, double2* v, int nb, int chunk, const unsigned char* on) {
+    return bd_lanes(h, g, v, nb, chunk, on);
+}
+int ls_bd_lanes(ls_handle* h, const float2* g, float2* v, int nb, int chunk, const unsigned char* on) {
+    return bd_lanes(h, g, v, nb, chunk, on);
 }
 
 int ls_bd(ls_handle* h, const double2* g, double2* v) { return ls_bd_b(h, g, v, 1); }
