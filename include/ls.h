@@ -137,6 +137,13 @@ int ls_apply_f32(ls_handle* h, const ls_c32* u, ls_c32* y);
  * (the apply LS_MIXED uses inside its refinement loop).  u, y: device, nz*nx; may alias. */
 int ls_apply_mixed(ls_handle* h, const ls_c64* u, ls_c64* y);
 
+/* ls_apply_double_float -- the same operator with FP64 input/output and double-float
+ * arithmetic inside (each real a pair hi + lo of FP32 numbers, about 48 significant bits,
+ * on the FP32 pipes; relative error a few 1e-13 against ls_apply).  LS_MIXED solves compute
+ * their refinement residuals f - H u this way (ls_set_double_float).  u, y: device, nz*nx;
+ * may alias. */
+int ls_apply_double_float(ls_handle* h, const ls_c64* u, ls_c64* y);
+
 /* ls_axpby -- y = a x + b y over the nz*nx grid (a = a_re + i a_im, b likewise), on
  * the handle's stream: the residual r = f - H u (ls_apply, then a = 1, b = -1 with
  * y = H u) and corrections e = u* - u of the outer iteration (Sec. 4) without
@@ -144,7 +151,9 @@ int ls_apply_mixed(ls_handle* h, const ls_c64* u, ls_c64* y);
 int ls_axpby(ls_handle* h, double a_re, double a_im, const ls_c64* x, double b_re, double b_im, ls_c64* y);
 
 /* ls_incident_rhs -- f = -w^2 G (m u_I) with u_I = exp(i w (x cos theta + z sin theta))
- * generated on the device (Sec. 2, f = -w^2 G D u_I).  f: device, nz*nx. */
+ * generated on the device (Sec. 2, f = -w^2 G D u_I).  FP64 output; the convolution runs
+ * in double-float arithmetic when ls_set_double_float is on (the LS_MIXED default), else
+ * in FP64.  f: device, nz*nx. */
 int ls_incident_rhs(ls_handle* h, double theta, ls_c64* f);
 
 /* ls_solve -- solve H u = f (Sec. 4): outer flexible GMRES preconditioned by
@@ -258,6 +267,14 @@ int ls_set_shapes(ls_handle* h, int fft_variant, int bd_chunk);
  * drops the captured sweep graphs on a change.  LS_ESTATE when on > 0 and the form is
  * not built (LS_FP64, before ls_factor, or q > 112); LS_EINVAL for other values. */
 int ls_set_tensor_steps(ls_handle* h, int on);
+
+/* ls_set_double_float -- on = 1: the FP64-accurate convolutions of a solve, the
+ * refinement residuals f - H u of LS_MIXED (Sec. 4's outer iteration around the FP32
+ * correction) and ls_incident_rhs, run in double-float arithmetic (ls_apply_double_float):
+ * GB300's FP64 pipe is about 1/64 of its FP32 rate, and a residual correct to a few 1e-13
+ * is far below any solve tolerance.  on = 0: FP64.  Default 1 for LS_MIXED handles, 0 for
+ * LS_FP64 ones.  ls_apply stays FP64 either way.  LS_EINVAL for other values of on. */
+int ls_set_double_float(ls_handle* h, int on);
 
 /* ls_set_reduced_inverse -- LS_MIXED, tensor-core local solves (Sec. 3.4; factors of
  * Sec. 4.1): the block-cyclic-reduction steps of the levels at and above the first level

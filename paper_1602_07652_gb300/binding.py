@@ -80,6 +80,7 @@ _SIGS = {
     "ls_axpby": (ctypes.c_int, [_P, ctypes.c_double, ctypes.c_double, _P, ctypes.c_double, ctypes.c_double, _P]),
     "ls_apply_f32": (ctypes.c_int, [_P, _P, _P]),
     "ls_apply_mixed": (ctypes.c_int, [_P, _P, _P]),
+    "ls_apply_double_float": (ctypes.c_int, [_P, _P, _P]),
     "ls_incident_rhs": (ctypes.c_int, [_P, ctypes.c_double, _P]),
     "ls_solve": (ctypes.c_int, [_P, _P, ctypes.c_double, _P, ctypes.c_int, ctypes.POINTER(Stats)]),
     "ls_solve_batch": (ctypes.c_int, [_P, ctypes.c_int, _P, ctypes.c_double, _P, ctypes.c_int,
@@ -92,6 +93,7 @@ _SIGS = {
     "ls_set_reduction": (ctypes.c_int, [_P, ctypes.c_int]),
     "ls_set_tensor_steps": (ctypes.c_int, [_P, ctypes.c_int]),
     "ls_set_reduced_inverse": (ctypes.c_int, [_P, ctypes.c_int]),
+    "ls_set_double_float": (ctypes.c_int, [_P, ctypes.c_int]),
     "ls_check_conversions": (ctypes.c_int, [_P, _P, ctypes.c_longlong, ctypes.POINTER(ctypes.c_ulonglong)]),
     "ls_device_timeouts": (ctypes.c_int, [ctypes.POINTER(ctypes.c_uint)]),
     "ls_test_tma_shortfall": (ctypes.c_int, [ctypes.c_uint]),
@@ -379,6 +381,12 @@ class Solver:
             "ls_apply_mixed")
         return y
 
+    def ls_apply_double_float(self, u, y=None):
+        y = torch.empty_like(u) if y is None else y
+        _ck(self._lib.ls_apply_double_float(self._h, _c128(u, self.N, "ls_apply_double_float"),
+                                            _c128(y, self.N, "ls_apply_double_float")), "ls_apply_double_float")
+        return y
+
     def ls_apply_f32(self, u, y=None):
         y = torch.empty_like(u) if y is None else y
         if u.dtype != torch.complex64 or y.dtype != torch.complex64:
@@ -425,6 +433,9 @@ class Solver:
 
     def ls_set_reduced_inverse(self, on):
         _ck(self._lib.ls_set_reduced_inverse(self._h, int(on)), "ls_set_reduced_inverse")
+
+    def ls_set_double_float(self, on):
+        _ck(self._lib.ls_set_double_float(self._h, int(on)), "ls_set_double_float")
 
     def ls_autotune(self, nrhs=1, reps=3):
         t = Tuning()

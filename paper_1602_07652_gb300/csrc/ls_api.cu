@@ -70,7 +70,7 @@ void release(ls_handle* h) {
         h->hostbufs = nullptr;
     }
     void* ptrs[] = {h->m64, h->m32, h->mT64, h->ghat64, h->ghat32, h->tw64, h->tw32, h->fftws, h->incx,
-                    h->incz, h->dtabs, h->red};
+                    h->incz, h->dtabs, h->red, h->mdf, h->ghatdf, h->twdf, h->incxdf, h->inczdf};
     for (void* p : ptrs) cudaFree(p);
     if (h->red_host) cudaFreeHost(h->red_host);
     if (h->ev0) cudaEventDestroy(h->ev0);
@@ -200,6 +200,7 @@ int ls_setup(const ls_grid* grid, double hstep, double omega, const double* m, c
     h->lp = lp;
     h->P = 1 << lp;
     h->prec = grid->precision;
+    h->dfloat = grid->precision == LS_MIXED ? 1 : 0;
     h->h = hstep;
     h->omega = omega;
     ls_default_opts(&h->opts);
@@ -286,7 +287,12 @@ int ls_apply_mixed(ls_handle* h, const ls_c64* u, ls_c64* y) {
 
 int ls_incident_rhs(ls_handle* h, double theta, ls_c64* f) {
     if (!h || !f || !std::isfinite(theta)) return LS_EINVAL;
-    return ls_rhs64(h, theta, reinterpret_cast<double2*>(f));
+    return ls_rhs(h, theta, reinterpret_cast<double2*>(f));
+}
+
+int ls_apply_double_float(ls_handle* h, const ls_c64* u, ls_c64* y) {
+    if (!h || !u || !y) return LS_EINVAL;
+    return ls_apply_df(h, reinterpret_cast<const double2*>(u), reinterpret_cast<double2*>(y));
 }
 
 int ls_solve_batch(ls_handle* h, int nrhs, const ls_c64* f, double tol, ls_c64* u, int use_x0, ls_stats* st) {
@@ -338,7 +344,7 @@ int ls_solve_plane_wave(ls_handle* h, double theta, double tol, ls_c64* u, ls_st
     HostBufs* b = nullptr;
     LS_TRY(host_reserve(h, 1, &b));
     const long long l0 = h->launches;
-    LS_TRY(ls_rhs64(h, theta, b->f));
+    LS_TRY(ls_rhs(h, theta, b->f));
     const long long extra = h->launches - l0;
     const int rc = ls_solve(h, reinterpret_cast<const ls_c64*>(b->f), tol, u, 0, st);
     if (st) st->kernel_launches += extra;

@@ -23,6 +23,7 @@
 #include <mutex>
 
 #include "ls_fft_common.cuh"
+#include "ls_dfloat.cuh"
 
 namespace {
 
@@ -40,7 +41,7 @@ __device__ __forceinline__ void stage_compute(C (&v)[E], int j, int TPC, int ls,
             const int sh = lp - ls - LR;
 #pragma unroll
             for (int r = 1; r < R; ++r) {
-                C w = __ldg(&tw[(k * r) << sh]);
+                C w = ldg_c(&tw[(k * r) << sh]);
                 if (DIR < 0) w.y = -w.y;
                 v[e * R + r] = v[e * R + r] * w;
             }
@@ -123,6 +124,19 @@ struct RowVec<double2, 2> {
     __device__ __forceinline__ static void store(double2* p, const double2 (&o)[2]) { p[0] = o[0]; p[1] = o[1]; }
 };
 
+template <>
+struct RowVec<cdfl, 2> {
+    __device__ __forceinline__ static void load(const cdfl* p, cdfl (&o)[2]) {
+        const float4 a = reinterpret_cast<const float4*>(p)[0], b = reinterpret_cast<const float4*>(p)[1];
+        o[0] = cdfl{dfl(a.x, a.y), dfl(a.z, a.w)};
+        o[1] = cdfl{dfl(b.x, b.y), dfl(b.z, b.w)};
+    }
+    __device__ __forceinline__ static void store(cdfl* p, const cdfl (&o)[2]) {
+        reinterpret_cast<float4*>(p)[0] = make_float4(o[0].x.hi, o[0].x.lo, o[0].y.hi, o[0].y.lo);
+        reinterpret_cast<float4*>(p)[1] = make_float4(o[1].x.hi, o[1].x.lo, o[1].y.hi, o[1].y.lo);
+    }
+};
+
 template <int R, int DIR, int E, int CW, typename C>
 __device__ __forceinline__ void stage_compute_vec(C (&v)[CW][E], int j, int TPC, int ls, int lp,
                                                   const C* __restrict__ tw) {
@@ -135,7 +149,7 @@ __device__ __forceinline__ void stage_compute_vec(C (&v)[CW][E], int j, int TPC,
             const int sh = lp - ls - LR;
 #pragma unroll
             for (int r = 1; r < R; ++r) {
-                C w = __ldg(&tw[(k * r) << sh]);
+                C w = ldg_c(&tw[(k * r) << sh]);
                 if (DIR < 0) w.y = -w.y;
 #pragma unroll
                 for (int c = 0; c < CW; ++c) v[c][e * R + r] = v[c][e * R + r] * w;
@@ -168,6 +182,19 @@ struct Halves<double2, 2> {  // half = 1 column = double2
     using H = double2;
     __device__ __forceinline__ static void split(const double2 (&r)[2], double2& a, double2& b) { a = r[0]; b = r[1]; }
     __device__ __forceinline__ static void join(const double2& a, const double2& b, double2 (&r)[2]) { r[0] = a; r[1] = b; }
+};
+
+template <>
+struct Halves<cdfl, 2> {  // half = 1 column = one double-float complex (16 bytes)
+    using H = float4;
+    __device__ __forceinline__ static void split(const cdfl (&r)[2], float4& a, float4& b) {
+        a = make_float4(r[0].x.hi, r[0].x.lo, r[0].y.hi, r[0].y.lo);
+        b = make_float4(r[1].x.hi, r[1].x.lo, r[1].y.hi, r[1].y.lo);
+    }
+    __device__ __forceinline__ static void join(const float4& a, const float4& b, cdfl (&r)[2]) {
+        r[0] = cdfl{dfl(a.x, a.y), dfl(a.z, a.w)};
+        r[1] = cdfl{dfl(b.x, b.y), dfl(b.z, b.w)};
+    }
 };
 
 template <int E, int DIR, int CW, typename C>
@@ -287,7 +314,7 @@ __global__ void __launch_bounds__(512) k_cols_vec(FftPlan pl, int nin, int nout,
             const int kz = j + e * TPC + (r << (lp - lrl));
             const int kzq = kz <= P / 2 ? kz : P - kz;
 #pragma unroll
-            for (int c = 0; c < CW; ++c) v[c][qq] = v[c][qq] * __ldg(&g[c][kzq]);
+            for (int c = 0; c < CW; ++c) v[c][qq] = v[c][qq] * ldg_c(&g[c][kzq]);
         }
         fft_core_vec<EV, -1, CW>(v, buf0, buf1, pl, j, TPC, tw);
 #pragma unroll
@@ -359,6 +386,34 @@ __global__ void k_incident_factors(int n, double wh, double cth, double sth, dou
     ez[i] = make_double2(c, s);
 }
 
+// double-float tables (ls_dfloat.cuh): cnt doubles, complex arrays as pairs of reals
+__global__ void k_to_dfl(size_t cnt, const double* __restrict__ a, dfl* __restrict__ b) {
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < cnt) b[i] = dfl_of(a[i]);
+}
+
+__global__ void k_incident_factors_df(int n, double wh, double cth, double sth, cdfl* ex, cdfl* ez) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double s, c;
+    sincos(wh * (double)(i + 1) * cth, &s, &c);
+    ex[i] = ccast<cdfl>(make_double2(c, s));
+    sincos(wh * (double)(i + 1) * sth, &s, &c);
+    ez[i] = ccast<cdfl>(make_double2(c, s));
+}
+
+// m u_I in double-float: the incident wave's factors and the medium as double-float tables
+struct SrcIncDf {
+    const dfl* m;
+    const cdfl* ex;
+    const cdfl* ez;
+    int n;
+    template <typename C>
+    __device__ __forceinline__ cdfl load(int z, int x) const {
+        return m[(size_t)z * n + x] * (ldg_c(&ex[x]) * ldg_c(&ez[z]));
+    }
+};
+
 __global__ void k_quad_to32(size_t cnt, const double2* a, float2* b) {
     const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < cnt) b[i] = ccast<float2>(a[i]);
@@ -394,6 +449,11 @@ int allow_smem(K kern, size_t bytes) {
     return LS_OK;
 }
 
+int to_dfl(ls_handle* h, const double* a, dfl* b, size_t cnt) {
+    LS_LAUNCH(h, k_to_dfl, (unsigned)((cnt + 255) / 256), 256, 0, cnt, a, b);
+    return LS_OK;
+}
+
 }  // namespace
 
 int ls_fft_init(ls_handle* h) {
@@ -408,6 +468,13 @@ int ls_fft_init(ls_handle* h) {
     LS_CUDA(cudaMalloc(&h->incx, sizeof(double2) * h->n));
     LS_CUDA(cudaMalloc(&h->incz, sizeof(double2) * h->n));
     LS_LAUNCH(h, k_twiddles, (P + 255) / 256, 256, 0, P, h->tw64, h->tw32);
+    const size_t N = (size_t)h->n * h->n;
+    LS_CUDA(cudaMalloc(&h->twdf, sizeof(cdfl) * P));
+    LS_CUDA(cudaMalloc(&h->mdf, sizeof(dfl) * N));
+    LS_CUDA(cudaMalloc(&h->incxdf, sizeof(cdfl) * h->n));
+    LS_CUDA(cudaMalloc(&h->inczdf, sizeof(cdfl) * h->n));
+    LS_TRY(to_dfl(h, reinterpret_cast<const double*>(h->tw64), reinterpret_cast<dfl*>(h->twdf), 2 * (size_t)P));
+    LS_TRY(to_dfl(h, h->m64, h->mdf, N));
     LS_TRY(allow_smem(k_cols_vec<double, EV, CW64, 0>, col_smem(P)));
     LS_TRY(allow_smem(k_cols_vec<double, EV, CW64, 1>, col_smem(P)));
     LS_TRY(allow_smem(k_cols_vec<float, EV, CW32, 0>, col_smem(P)));
@@ -416,6 +483,11 @@ int ls_fft_init(ls_handle* h) {
     LS_TRY(allow_smem(k_rows_fwd<double, E64, SrcGpad>, row_smem64(P)));
     LS_TRY(allow_smem(k_rows_inv<double, E64, DstApply<double2>>, row_smem64(P)));
     LS_TRY(allow_smem(k_rows_inv<double, E64, DstRhs>, row_smem64(P)));
+    LS_TRY(allow_smem(k_cols_vec<dfl, EV, CW64, 0>, col_smem(P)));
+    LS_TRY(allow_smem(k_rows_fwd<dfl, E64, SrcMU<dfl, double2>>, row_smem64(P)));
+    LS_TRY(allow_smem(k_rows_fwd<dfl, E64, SrcIncDf>, row_smem64(P)));
+    LS_TRY(allow_smem(k_rows_inv<dfl, E64, DstApply<double2>>, row_smem64(P)));
+    LS_TRY(allow_smem(k_rows_inv<dfl, E64, DstRhs>, row_smem64(P)));
     LS_TRY(allow_smem(k_rows_fwd<float, E32, SrcMU<float, float2>>, row_smem32(P)));
     LS_TRY(allow_smem(k_rows_fwd<float, E32, SrcMU<float, double2>>, row_smem32(P)));
     LS_TRY(allow_smem(k_rows_inv<float, E32, DstApply<float2>>, row_smem32(P)));
@@ -443,6 +515,13 @@ int ls_spectrum_build(ls_handle* h, const double2* gtab) {
         const size_t cnt = q1 * q1;
         k_quad_to32<<<(unsigned)((cnt + 255) / 256), 256, 0, h->stream>>>(cnt, h->ghat64, h->ghat32);
         h->launches++;
+        if (cudaMalloc(&h->ghatdf, sizeof(cdfl) * cnt) != cudaSuccess) {
+            rc = LS_ENOMEM;
+            break;
+        }
+        if ((rc = to_dfl(h, reinterpret_cast<const double*>(h->ghat64), reinterpret_cast<dfl*>(h->ghatdf),
+                         2 * cnt)) != LS_OK)
+            break;
         cudaError_t e = cudaPeekAtLastError();
         if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
         if (e != cudaSuccess) rc = ls_cuda_fail(e);
@@ -463,6 +542,21 @@ int ls_apply64(ls_handle* h, const double2* u, double2* y) {
     DstApply<double2> dst{u, y, n};
     LS_LAUNCH(h, (k_rows_inv<double, E64, DstApply<double2>>), n, P / E64, row_smem64(P),
               pl, n, X, dst, h->tw64);
+    return LS_OK;
+}
+
+// The FP64 apply's three passes in double-float arithmetic (ls_dfloat.cuh): FP64 I/O,
+// about 48 significant bits inside, on the FP32 pipes.
+int ls_apply_df(ls_handle* h, const double2* u, double2* y) {
+    const int n = h->n, P = h->P;
+    const FftPlan& pl = h->plan64;
+    cdfl* X = static_cast<cdfl*>(h->fftws);
+    SrcMU<dfl, double2> src{h->mdf, u, n};
+    LS_LAUNCH(h, (k_rows_fwd<dfl, E64, SrcMU<dfl, double2>>), n, P / E64, row_smem64(P), pl, n, src, X, h->twdf);
+    LS_LAUNCH(h, (k_cols_vec<dfl, EV, CW64, 0>), P / CW64, (P / EV), col_smem(P), h->planc64, n, n, X, h->ghatdf,
+              (cdfl*)nullptr, dfl(0.f, 0.f), h->twdf);
+    DstApply<double2> dst{u, y, n};
+    LS_LAUNCH(h, (k_rows_inv<dfl, E64, DstApply<double2>>), n, P / E64, row_smem64(P), pl, n, X, dst, h->twdf);
     return LS_OK;
 }
 
@@ -512,6 +606,26 @@ int ls_rhs64(ls_handle* h, double theta, double2* f) {
     DstRhs dst{f, n};
     LS_LAUNCH(h, (k_rows_inv<double, E64, DstRhs>), n, P / E64, row_smem64(P), pl, n, X, dst, h->tw64);
     return LS_OK;
+}
+
+// The incident right-hand side in double-float arithmetic (FP64 output)
+int ls_rhs_df(ls_handle* h, double theta, double2* f) {
+    const int n = h->n, P = h->P;
+    const FftPlan& pl = h->plan64;
+    cdfl* X = static_cast<cdfl*>(h->fftws);
+    LS_LAUNCH(h, k_incident_factors_df, (n + 255) / 256, 256, 0, n, h->omega * h->h, std::cos(theta),
+              std::sin(theta), h->incxdf, h->inczdf);
+    SrcIncDf src{h->mdf, h->incxdf, h->inczdf, n};
+    LS_LAUNCH(h, (k_rows_fwd<dfl, E64, SrcIncDf>), n, P / E64, row_smem64(P), pl, n, src, X, h->twdf);
+    LS_LAUNCH(h, (k_cols_vec<dfl, EV, CW64, 0>), P / CW64, (P / EV), col_smem(P), h->planc64, n, n, X, h->ghatdf,
+              (cdfl*)nullptr, dfl(0.f, 0.f), h->twdf);
+    DstRhs dst{f, n};
+    LS_LAUNCH(h, (k_rows_inv<dfl, E64, DstRhs>), n, P / E64, row_smem64(P), pl, n, X, dst, h->twdf);
+    return LS_OK;
+}
+
+int ls_rhs(ls_handle* h, double theta, double2* f) {
+    return h->dfloat ? ls_rhs_df(h, theta, f) : ls_rhs64(h, theta, f);
 }
 
 

@@ -211,6 +211,15 @@ struct ls_handle {
     float2* ghat32 = nullptr;
     double2* tw64 = nullptr;   // twiddles exp(-2 pi i m / P), m < P
     float2* tw32 = nullptr;
+    // double-float copies (ls_dfloat.cuh) of the medium, the spectral quadrant, the
+    // twiddles and the incident-wave factors: the FP64-accurate convolutions on the FP32 pipes
+    struct dfl* mdf = nullptr;
+    struct cdfl* ghatdf = nullptr;
+    struct cdfl* twdf = nullptr;
+    struct cdfl* incxdf = nullptr;
+    struct cdfl* inczdf = nullptr;
+    int dfloat = 0;            // 1 (LS_MIXED default): refinement residuals and incident
+                               // right-hand sides in double-float arithmetic
     FftPlan plan64{}, plan32{};    // row passes
     FftPlan planc64{}, planc32{};  // column pass
     void* fftws = nullptr;     // n*P complex (FP64 size)
@@ -312,6 +321,9 @@ int ls_spectrum_build(ls_handle* h, const double2* gtab);       // Ghat from the
 int ls_apply64(ls_handle* h, const double2* u, double2* y);     // y = H u (FP64)
 int ls_apply32(ls_handle* h, const float2* u, float2* y);       // y = H u (FP32)
 int ls_apply_mx(ls_handle* h, const double2* u, double2* y);    // FP64 I/O, FP32 arithmetic
+int ls_apply_df(ls_handle* h, const double2* u, double2* y);    // FP64 I/O, double-float arithmetic
+int ls_rhs_df(ls_handle* h, double theta, double2* f);          // incident right-hand side, double-float
+int ls_rhs(ls_handle* h, double theta, double2* f);             // ls_rhs_df if h->dfloat, else ls_rhs64
 bool ls_fft16_supported(const ls_handle* h);                     // radix-16 FP32 path: 256 <= P <= 4096
 int ls_fft16_init(ls_handle* h);
 int ls_apply32_fft16(ls_handle* h, const float2* u, float2* y, int shape);  // shape: fft_variant != 1

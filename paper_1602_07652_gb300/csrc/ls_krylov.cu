@@ -539,7 +539,8 @@ int ls_outer_solve_b(ls_handle* h, int nb, const double2* f, double tol, double2
                 LS_TRY(ls_vec_copy(h, f + i * N, di));
             } else {
                 LS_TRY(ls_timing_begin(h));
-                LS_TRY(ls_apply64(h, u + i * N, di));  // d = H u (FP64)
+                // d = H u: FP64-accurate (double-float arithmetic by default, else FP64)
+                LS_TRY(h->dfloat ? ls_apply_df(h, u + i * N, di) : ls_apply64(h, u + i * N, di));
                 LS_TRY(ls_timing_end(h, 2));
                 LS_TRY(ls_vec_axpby(h, make_double2(1, 0), f + i * N, make_double2(-1, 0), di));  // d = f - H u
             }

@@ -54,7 +54,7 @@ extern "C" int ls_autotune(ls_handle* h, int nrhs, int reps, ls_tuning* out) {
     LS_CUDA(cudaMalloc(&buf, sizeof(double2) * N * 2 * nrhs));
     int rc = LS_OK;
     do {
-        for (int b = 0; b < nrhs && rc == LS_OK; ++b) rc = ls_rhs64(h, 0.7 + 0.9 * b, buf + b * N);
+        for (int b = 0; b < nrhs && rc == LS_OK; ++b) rc = ls_rhs(h, 0.7 + 0.9 * b, buf + b * N);
         if (rc != LS_OK) break;
         // FFT tile shape (the variant the solve's FP32 / mixed apply uses)
         ApplyArg aa{buf, buf + nrhs * N};
@@ -157,6 +157,12 @@ extern "C" int ls_set_tensor_steps(ls_handle* h, int on) {
         if (h->bd_chunk > ls_bd_cap(h)) h->bd_chunk = 0;
         ls_bd_graph_free(h);
     }
+    return LS_OK;
+}
+
+extern "C" int ls_set_double_float(ls_handle* h, int on) {
+    if (!h || on < 0 || on > 1) return LS_EINVAL;
+    h->dfloat = on;
     return LS_OK;
 }
 

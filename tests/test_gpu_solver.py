@@ -52,6 +52,27 @@ def test_c1_configuration_matches_oracle(prec):
     s.close()
 
 
+@pytest.mark.parametrize("dfloat", [1, 0])
+def test_mixed_refinement_residual_forms(dfloat):
+    # LS_MIXED judges convergence on its refinement residual f - H u, computed in
+    # double-float arithmetic (default) or FP64; either way the FP64 residual of the
+    # returned field, taken here with ls_apply, meets the tolerance.
+    n, L, E = 96, 4, 6
+    w = inputs.omega_for_ppw(n, 8.0)
+    m = inputs.bump_medium(n, nbumps=8, seed=21)
+    s = binding.Solver(cuda(m), w, layers=L, ext=E, precision=binding.LS_MIXED)
+    s.ls_set_double_float(dfloat)
+    s.ls_factor()
+    f = s.ls_incident_rhs(0.8)
+    u, st, rc = s.ls_solve(f, 1e-10)
+    r = (f - s.ls_apply(u)).cpu().numpy()
+    true_res = float(np.linalg.norm(r) / np.linalg.norm(f.cpu().numpy()))
+    assert st["true_rel_residual"] <= 1e-10
+    assert true_res <= 1.01e-10
+    assert abs(true_res - st["true_rel_residual"]) <= 5e-12
+    s.close()
+
+
 def test_ragged_size_and_seeded_angle():
     n, L, E = 48, 3, 4
     w = inputs.omega_for_ppw(n, 8.0)
