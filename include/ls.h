@@ -84,12 +84,14 @@ typedef struct {
     int inner_iters_total;   /* inner GMRES iterations summed over all preconditioner calls */
     int inner_calls;         /* Algorithm 3 applications                                     */
     int refine_steps;        /* LS_MIXED refinement steps (1 = no correction needed)         */
-    double true_rel_residual;/* ||f - H u|| / ||f|| with an FP64 apply of H                 */
+    double true_rel_residual;/* ||f - H u|| / ||f|| with an FP64-accurate apply of H (LS_MIXED:
+                                the double-float one unless ls_set_double_float(h, 0))     */
     double t_solve_s;        /* wall time of the call                                        */
     double t_apply_ms;       /* device time of FP32-arithmetic LS-applies (LS_MIXED) or of all
                                 FP64 LS-applies (LS_FP64), if timing is enabled            */
     int n_apply;             /* LS-applies counted in t_apply_ms                             */
-    double t_apply64_ms;     /* LS_MIXED: device time of the FP64 refinement-residual applies */
+    double t_apply64_ms;     /* LS_MIXED: device time of the refinement-residual applies
+                                (double-float or FP64, ls_set_double_float)                */
     int n_apply64;           /* LS-applies counted in t_apply64_ms                           */
     double t_sweep_ms;       /* total device time of Algorithm 2 applications (if timing)   */
     int n_sweep;             /* Algorithm 2 applications counted in t_sweep_ms               */
@@ -101,6 +103,9 @@ typedef struct {
     double t_orth_ms;        /* device time of the Arnoldi orthogonalisations (CGS2 dots and
                                 updates, both Krylov levels), if timing                     */
     int n_orth;              /* Arnoldi steps counted in t_orth_ms                           */
+    long long sweep_fields;  /* fields the Algorithm 2 applications processed, summed: the
+                                members still iterating (ls_set_pack_members), else the
+                                batch up to the last one still iterating                    */
 } ls_stats;
 
 typedef struct ls_handle ls_handle;
@@ -267,6 +272,16 @@ int ls_set_shapes(ls_handle* h, int fft_variant, int bd_chunk);
  * drops the captured sweep graphs on a change.  LS_ESTATE when on > 0 and the form is
  * not built (LS_FP64, before ls_factor, or q > 112); LS_EINVAL for other values. */
 int ls_set_tensor_steps(ls_handle* h, int on);
+
+/* ls_set_pack_members -- on = 1 (default): before each batched Algorithm 2 application
+ * (Sec. 3.5) inside a lockstep batch, the members still iterating are moved into the
+ * leading slots and Algorithm 2 runs on that many fields only (the results are moved
+ * back); the members that have converged cost nothing.  on = 0: it runs on the batch up
+ * to the last member still iterating, the others' slots zeroed.  Results agree up to the
+ * rounding of the form the smaller batch takes (batches below 5 run the local solves on
+ * the CUDA cores in FP32 instead of TF32 on the tensor cores).  LS_EINVAL for other
+ * values of on. */
+int ls_set_pack_members(ls_handle* h, int on);
 
 /* ls_set_double_float -- on = 1: the FP64-accurate convolutions of a solve, the
  * refinement residuals f - H u of LS_MIXED (Sec. 4's outer iteration around the FP32

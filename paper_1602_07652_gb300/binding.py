@@ -51,7 +51,8 @@ class Stats(ctypes.Structure):
                 ("t_sweep_ms", ctypes.c_double), ("n_sweep", ctypes.c_int),
                 ("kernel_launches", ctypes.c_longlong), ("learned_steps", ctypes.c_int),
                 ("t_stencil_ms", ctypes.c_double), ("n_stencil", ctypes.c_int),
-                ("t_orth_ms", ctypes.c_double), ("n_orth", ctypes.c_int)]
+                ("t_orth_ms", ctypes.c_double), ("n_orth", ctypes.c_int),
+                ("sweep_fields", ctypes.c_longlong)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -94,6 +95,7 @@ _SIGS = {
     "ls_set_tensor_steps": (ctypes.c_int, [_P, ctypes.c_int]),
     "ls_set_reduced_inverse": (ctypes.c_int, [_P, ctypes.c_int]),
     "ls_set_double_float": (ctypes.c_int, [_P, ctypes.c_int]),
+    "ls_set_pack_members": (ctypes.c_int, [_P, ctypes.c_int]),
     "ls_check_conversions": (ctypes.c_int, [_P, _P, ctypes.c_longlong, ctypes.POINTER(ctypes.c_ulonglong)]),
     "ls_device_timeouts": (ctypes.c_int, [ctypes.POINTER(ctypes.c_uint)]),
     "ls_test_tma_shortfall": (ctypes.c_int, [ctypes.c_uint]),
@@ -433,6 +435,9 @@ class Solver:
 
     def ls_set_reduced_inverse(self, on):
         _ck(self._lib.ls_set_reduced_inverse(self._h, int(on)), "ls_set_reduced_inverse")
+
+    def ls_set_pack_members(self, on):
+        _ck(self._lib.ls_set_pack_members(self._h, int(on)), "ls_set_pack_members")
 
     def ls_set_double_float(self, on):
         _ck(self._lib.ls_set_double_float(self._h, int(on)), "ls_set_double_float")

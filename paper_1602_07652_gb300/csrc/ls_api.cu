@@ -304,6 +304,7 @@ int ls_solve_batch(ls_handle* h, int nrhs, const ls_c64* f, double tol, ls_c64* 
     h->t_apply_ms = h->t_sweep_ms = h->t_apply64_ms = h->t_stencil_ms = h->t_orth_ms = 0;
     h->n_apply = h->n_sweep = h->n_apply64 = h->n_stencil = h->n_orth = 0;
     h->learned_steps = 0;
+    h->sweep_fields = 0;
     const long long l0 = h->launches;
     const auto t0 = std::chrono::steady_clock::now();
     h->tused = 0;
@@ -325,6 +326,7 @@ int ls_solve_batch(ls_handle* h, int nrhs, const ls_c64* f, double tol, ls_c64* 
     s->n_stencil = h->n_stencil;
     s->t_orth_ms = h->t_orth_ms;
     s->n_orth = h->n_orth;
+    s->sweep_fields = h->sweep_fields;
     return rc;
 }
 

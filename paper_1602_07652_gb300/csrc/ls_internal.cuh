@@ -277,6 +277,8 @@ struct ls_handle {
     bool tc_ready = false;     // LS_MIXED: TF32 factor planes and tensor maps built (ls_cr_tc_prepare)
     int tc_sms = 0;            // SMs of the device (tensor-core steps: CTAs per SM by level size)
     int tc_dense = 1;          // tensor-core local solves: levels with <= 32 blocks as one dense product
+    int pack_members = 1;      // Algorithm 2 on the members still iterating only, packed (ls_krylov.cu)
+    long long sweep_fields = 0;  // fields Algorithm 2 processed during the current solve
     int cr_tc = 1;             // FP32 reduction steps on the tensor cores when tc_ready: 0 never,
                                // 1 for batches of 5 or more right-hand sides, 2 always
 

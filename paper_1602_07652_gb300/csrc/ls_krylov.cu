@@ -186,19 +186,47 @@ int apply_pc_b(ls_handle* h, Pc pc, VT* v, VT* z, int nb, const unsigned char* o
         return LS_OK;
     }
     if (pc == PC_BD) {
-        for (int b = 0; b < top; ++b)
-            if (!on[b]) LS_TRY(ls_vec_zero(h, v + b * N));
         const int ch = bd_chunk(h);
-        LS_TRY(ls_timing_begin(h));
         if (h->opts.inner_precond == LS_PC_GS) {
+            for (int b = 0; b < top; ++b)
+                if (!on[b]) LS_TRY(ls_vec_zero(h, v + b * N));
+            LS_TRY(ls_timing_begin(h));
             for (int b0 = 0; b0 < top; b0 += ch) {
                 const int cnt = top - b0 < ch ? top - b0 : ch;
                 LS_TRY(gs_chunk(h, v + b0 * N, z + b0 * N, cnt));
             }
-        } else {
-            LS_TRY(ls_bd_lanes(h, v, z, top, ch, on));  // chunks run concurrently; idle ones are skipped
+            h->sweep_fields += top;
+            return ls_timing_end(h, 1);
         }
-        return ls_timing_end(h, 1);
+        // Algorithm 2 costs what the batch it runs costs, whether a slot's member is still
+        // iterating or not: the members that are on move into the leading slots first.
+        // Slot k takes member act[k] >= k in increasing k (a slot is overwritten only
+        // after its own member has moved out), and the moves are undone in decreasing k,
+        // which restores every member's direction and puts its result in its own slot.
+        std::vector<int> act;
+        for (int b = 0; b < top; ++b)
+            if (on[b]) act.push_back(b);
+        const int cnt = h->pack_members ? (int)act.size() : top;
+        if (h->pack_members) {
+            for (int k = 0; k < cnt; ++k)
+                if (act[k] != k) LS_TRY(ls_vec_copy(h, (const VT*)(v + act[k] * N), v + k * N));
+        } else {
+            for (int b = 0; b < top; ++b)
+                if (!on[b]) LS_TRY(ls_vec_zero(h, v + b * N));
+        }
+        std::vector<unsigned char> all(cnt, 1);
+        LS_TRY(ls_timing_begin(h));
+        // chunks run concurrently; idle ones are skipped
+        LS_TRY(ls_bd_lanes(h, v, z, cnt, ch, h->pack_members ? all.data() : on));
+        LS_TRY(ls_timing_end(h, 1));
+        h->sweep_fields += cnt;
+        if (h->pack_members)
+            for (int k = cnt - 1; k >= 0; --k)
+                if (act[k] != k) {
+                    LS_TRY(ls_vec_copy(h, (const VT*)(v + k * N), v + act[k] * N));
+                    LS_TRY(ls_vec_copy(h, (const VT*)(z + k * N), z + act[k] * N));
+                }
+        return LS_OK;
     }
     // Algorithm 3: z = GMRES(C, A v, Algorithm 2, inner_tol), all members at once
     Ctx* c = ctx_of(h);

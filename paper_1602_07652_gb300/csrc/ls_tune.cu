@@ -160,6 +160,12 @@ extern "C" int ls_set_tensor_steps(ls_handle* h, int on) {
     return LS_OK;
 }
 
+extern "C" int ls_set_pack_members(ls_handle* h, int on) {
+    if (!h || on < 0 || on > 1) return LS_EINVAL;
+    h->pack_members = on;
+    return LS_OK;
+}
+
 extern "C" int ls_set_double_float(ls_handle* h, int on) {
     if (!h || on < 0 || on > 1) return LS_EINVAL;
     h->dfloat = on;

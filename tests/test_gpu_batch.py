@@ -126,6 +126,34 @@ def test_batched_solve_matches_single_solves_and_oracle(prec):
     s.close()
 
 
+def test_packed_members_match_unpacked_batch():
+    # Algorithm 2 on the members still iterating only (packed into the leading slots)
+    # versus on the whole batch up to the last member still iterating: the same
+    # converged fields, fewer fields through Algorithm 2.
+    n, L, E = 96, 4, 6
+    w = inputs.omega_for_ppw(n, 10.0)
+    m = inputs.bump_medium(n, nbumps=10, seed=5)
+    s = binding.Solver(cuda(m), w, layers=L, ext=E, precision=binding.LS_MIXED)
+    s.ls_factor()
+    thetas = [0.3 * k + 0.1 for k in range(12)]
+    f = torch.stack([s.ls_incident_rhs(t) for t in thetas]).contiguous()
+    tol = 1e-9
+    s.ls_set_pack_members(0)
+    u0, st0, rc0 = s.ls_solve_batch(f, tol)
+    s.ls_set_pack_members(1)
+    u1, st1, rc1 = s.ls_solve_batch(f, tol)
+    assert rc0 == 0 and rc1 == 0
+    assert st0["true_rel_residual"] <= tol and st1["true_rel_residual"] <= tol
+    print("fields through Algorithm 2: unpacked %d packed %d; outer %d / %d" % (
+        st0["sweep_fields"], st1["sweep_fields"], st0["outer_iters"], st1["outer_iters"]))
+    assert st1["sweep_fields"] <= st0["sweep_fields"]
+    for b in range(len(thetas)):
+        assert rel(u1[b], u0[b]) < 1e-7, (b, rel(u1[b], u0[b]))
+    with pytest.raises(binding.LSError):
+        s.ls_set_pack_members(3)
+    s.close()
+
+
 def test_batched_solve_with_a_zero_member_and_ragged_size():
     n, L, E = 48, 3, 4
     w = inputs.omega_for_ppw(n, 8.0)
