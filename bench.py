@@ -477,6 +477,7 @@ def run_ours(args):
         dist.barrier()
     ms = max_over_ranks(ev0.elapsed_time(ev1), world, "cuda")
     t_rhs = sum(ea.elapsed_time(eb) for ea, eb in rhs_events)
+    a2_hist = s.ls_get_sweep_histogram()   # the last timed step's Algorithm 2 batch sizes
     s.ls_set_timing(False)
     # end to end through the C ABI with host buffers: the same directions as the timed
     # steps, right-hand sides prepared in pinned host memory beforehand; each step copies
@@ -546,7 +547,8 @@ def run_ours(args):
                               "true_rel_residual_max": max(st["true_rel_residual"] for st in stats),
                               # fields per batched Algorithm 2 application (members still iterating)
                               "algorithm2_fields_per_application":
-                                  sum(st["sweep_fields"] for st in stats) / max(1, sum(st["n_sweep"] for st in stats))},
+                                  sum(st["sweep_fields"] for st in stats) / max(1, sum(st["n_sweep"] for st in stats)),
+                              "algorithm2_batch_sizes_last_step": {str(k): v for k, v in sorted(a2_hist.items())}},
                "sweep_ms_avg": (sum(st["t_sweep_ms"] for st in stats) / max(1, sum(st["n_sweep"] for st in stats))),
                # live shares of the timed region (CUDA events inside the library)
                "time_shares": {"algorithm2": sum(st["t_sweep_ms"] for st in stats) / ms,

@@ -273,6 +273,11 @@ int ls_set_shapes(ls_handle* h, int fft_variant, int bd_chunk);
  * not built (LS_FP64, before ls_factor, or q > 112); LS_EINVAL for other values. */
 int ls_set_tensor_steps(ls_handle* h, int on);
 
+/* ls_get_sweep_histogram -- counts[k] = how many batched Algorithm 2 applications of the
+ * last solve ran on k fields (k = 0 .. len - 1; entries past LS_MAX_BATCH are 0).
+ * LS_EINVAL for a null pointer or len < 1. */
+int ls_get_sweep_histogram(ls_handle* h, int* counts, int len);
+
 /* ls_set_pack_members -- on = 1 (default): before each batched Algorithm 2 application
  * (Sec. 3.5) inside a lockstep batch, the members still iterating are moved into the
  * leading slots and Algorithm 2 runs on that many fields only (the results are moved

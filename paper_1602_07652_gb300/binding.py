@@ -96,6 +96,7 @@ _SIGS = {
     "ls_set_reduced_inverse": (ctypes.c_int, [_P, ctypes.c_int]),
     "ls_set_double_float": (ctypes.c_int, [_P, ctypes.c_int]),
     "ls_set_pack_members": (ctypes.c_int, [_P, ctypes.c_int]),
+    "ls_get_sweep_histogram": (ctypes.c_int, [_P, _P, ctypes.c_int]),
     "ls_check_conversions": (ctypes.c_int, [_P, _P, ctypes.c_longlong, ctypes.POINTER(ctypes.c_ulonglong)]),
     "ls_device_timeouts": (ctypes.c_int, [ctypes.POINTER(ctypes.c_uint)]),
     "ls_test_tma_shortfall": (ctypes.c_int, [ctypes.c_uint]),
@@ -435,6 +436,12 @@ class Solver:
 
     def ls_set_reduced_inverse(self, on):
         _ck(self._lib.ls_set_reduced_inverse(self._h, int(on)), "ls_set_reduced_inverse")
+
+    def ls_get_sweep_histogram(self):
+        """{batch size: Algorithm 2 applications} of the last solve."""
+        counts = (ctypes.c_int * 65)()
+        _ck(self._lib.ls_get_sweep_histogram(self._h, counts, 65), "ls_get_sweep_histogram")
+        return {k: counts[k] for k in range(65) if counts[k]}
 
     def ls_set_pack_members(self, on):
         _ck(self._lib.ls_set_pack_members(self._h, int(on)), "ls_set_pack_members")

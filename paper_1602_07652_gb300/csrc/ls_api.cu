@@ -290,6 +290,12 @@ int ls_incident_rhs(ls_handle* h, double theta, ls_c64* f) {
     return ls_rhs(h, theta, reinterpret_cast<double2*>(f));
 }
 
+int ls_get_sweep_histogram(ls_handle* h, int* counts, int len) {
+    if (!h || !counts || len < 1) return LS_EINVAL;
+    for (int k = 0; k < len; ++k) counts[k] = k <= LS_MAX_BATCH ? h->sweep_hist[k] : 0;
+    return LS_OK;
+}
+
 int ls_apply_double_float(ls_handle* h, const ls_c64* u, ls_c64* y) {
     if (!h || !u || !y) return LS_EINVAL;
     return ls_apply_df(h, reinterpret_cast<const double2*>(u), reinterpret_cast<double2*>(y));
@@ -305,6 +311,7 @@ int ls_solve_batch(ls_handle* h, int nrhs, const ls_c64* f, double tol, ls_c64* 
     h->n_apply = h->n_sweep = h->n_apply64 = h->n_stencil = h->n_orth = 0;
     h->learned_steps = 0;
     h->sweep_fields = 0;
+    std::memset(h->sweep_hist, 0, sizeof(h->sweep_hist));
     const long long l0 = h->launches;
     const auto t0 = std::chrono::steady_clock::now();
     h->tused = 0;

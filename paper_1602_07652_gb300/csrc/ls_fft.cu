@@ -21,6 +21,7 @@
 // stored and read.
 #include <cmath>
 #include <mutex>
+#include <type_traits>
 
 #include "ls_fft_common.cuh"
 #include "ls_dfloat.cuh"
@@ -240,9 +241,14 @@ __device__ __forceinline__ void fft_core_vec(C (&v)[CW][E], typename Halves<C, C
 }
 
 // ---------------------------------------------------------------- kernels
+// Row passes: at most 512 threads (P <= 4096, E >= 8).  The double-float ones are held to
+// 64 registers so that two CTAs share an SM (their arithmetic is latency-bound at one).
+template <typename T> constexpr int rows_min_blocks() { return std::is_same<T, dfl>::value ? 2 : 1; }
+
 template <typename T, int E, class Src>
-__global__ void k_rows_fwd(FftPlan pl, int nin, Src src, cpx_t<T>* __restrict__ out,
-                           const cpx_t<T>* __restrict__ tw) {
+__global__ void __launch_bounds__(512, rows_min_blocks<T>()) k_rows_fwd(FftPlan pl, int nin, Src src,
+                                                                        cpx_t<T>* __restrict__ out,
+                                                                        const cpx_t<T>* __restrict__ tw) {
     using C = cpx_t<T>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* buf = reinterpret_cast<C*>(smem_raw);
@@ -342,8 +348,9 @@ __global__ void __launch_bounds__(512) k_cols_vec(FftPlan pl, int nin, int nout,
 }
 
 template <typename T, int E, class Dst>
-__global__ void k_rows_inv(FftPlan pl, int n, const cpx_t<T>* __restrict__ X, Dst dst,
-                           const cpx_t<T>* __restrict__ tw) {
+__global__ void __launch_bounds__(512, rows_min_blocks<T>()) k_rows_inv(FftPlan pl, int n,
+                                                                        const cpx_t<T>* __restrict__ X, Dst dst,
+                                                                        const cpx_t<T>* __restrict__ tw) {
     using C = cpx_t<T>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* buf = reinterpret_cast<C*>(smem_raw);

@@ -279,6 +279,7 @@ struct ls_handle {
     int tc_dense = 1;          // tensor-core local solves: levels with <= 32 blocks as one dense product
     int pack_members = 1;      // Algorithm 2 on the members still iterating only, packed (ls_krylov.cu)
     long long sweep_fields = 0;  // fields Algorithm 2 processed during the current solve
+    int sweep_hist[LS_MAX_BATCH + 1] = {};  // its applications by batch size, current solve
     int cr_tc = 1;             // FP32 reduction steps on the tensor cores when tc_ready: 0 never,
                                // 1 for batches of 5 or more right-hand sides, 2 always
 
@@ -350,6 +351,12 @@ int ls_vec_dots_dev(ls_handle* h, int nvec, const double2* V, size_t ld, const d
 int ls_vec_dots_dev(ls_handle* h, int nvec, const float2* V, size_t ld, const float2* w, double2* out_dev);
 int ls_vec_update(ls_handle* h, int nvec, const double2* V, size_t ld, const double2* coef_dev, double2* w);
 int ls_vec_update(ls_handle* h, int nvec, const float2* V, size_t ld, const double2* coef_dev, float2* w);
+// One fused pass of a Gram-Schmidt step against nvec directions (ls_stencil.cu):
+// mode 0: out = V^H w; 1: w -= V coef, then out = V^H w; 2: w -= V coef, then out[0] = w^H w.
+int ls_vec_orth(ls_handle* h, int mode, int nvec, const double2* V, size_t ld, const double2* coef_dev, double2* w,
+                double2* out_dev);
+int ls_vec_orth(ls_handle* h, int mode, int nvec, const float2* V, size_t ld, const double2* coef_dev, float2* w,
+                double2* out_dev);
 int ls_vec_norm(ls_handle* h, const double2* w, double* out_host);
 int ls_vec_norm(ls_handle* h, const float2* w, double* out_host);
 int ls_vec_axpby(ls_handle* h, double2 a, const double2* x, double2 b, double2* y);  // y = a x + b y

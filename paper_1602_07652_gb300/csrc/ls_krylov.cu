@@ -196,6 +196,7 @@ int apply_pc_b(ls_handle* h, Pc pc, VT* v, VT* z, int nb, const unsigned char* o
                 LS_TRY(gs_chunk(h, v + b0 * N, z + b0 * N, cnt));
             }
             h->sweep_fields += top;
+            h->sweep_hist[top < LS_MAX_BATCH ? top : LS_MAX_BATCH]++;
             return ls_timing_end(h, 1);
         }
         // Algorithm 2 costs what the batch it runs costs, whether a slot's member is still
@@ -220,6 +221,7 @@ int apply_pc_b(ls_handle* h, Pc pc, VT* v, VT* z, int nb, const unsigned char* o
         LS_TRY(ls_bd_lanes(h, v, z, cnt, ch, h->pack_members ? all.data() : on));
         LS_TRY(ls_timing_end(h, 1));
         h->sweep_fields += cnt;
+        h->sweep_hist[cnt < LS_MAX_BATCH ? cnt : LS_MAX_BATCH]++;
         if (h->pack_members)
             for (int k = cnt - 1; k >= 0; --k)
                 if (act[k] != k) {
@@ -332,13 +334,12 @@ int fgmres_b(ls_handle* h, Ctx* c, KrylovSpace<VT>& S, Op op, Pc pc, const VT* b
                 VT* vn = V(j + 1, i);
                 double2* hd = S.hdev + i * HS;
                 LS_TRY(apply_op(h, op, Zb(j) + i * N, vn));
-                // CGS2 against V_0..V_j; coefficients stay on the device between the passes
+                // CGS2 against V_0..V_j in three fused passes (dots; update and dots;
+                // update and norm); coefficients stay on the device between the passes
                 LS_TRY(ls_timing_begin(h));
-                LS_TRY(ls_vec_dots_dev(h, j + 1, V(0, i), ldv, vn, hd));
-                LS_TRY(ls_vec_update(h, j + 1, V(0, i), ldv, hd, vn));
-                LS_TRY(ls_vec_dots_dev(h, j + 1, V(0, i), ldv, vn, hd + (m + 1)));
-                LS_TRY(ls_vec_update(h, j + 1, V(0, i), ldv, hd + (m + 1), vn));
-                LS_TRY(ls_vec_dots_dev(h, 1, vn, 0, vn, hd + 2 * (m + 1)));
+                LS_TRY(ls_vec_orth(h, 0, j + 1, V(0, i), ldv, nullptr, vn, hd));
+                LS_TRY(ls_vec_orth(h, 1, j + 1, V(0, i), ldv, hd, vn, hd + (m + 1)));
+                LS_TRY(ls_vec_orth(h, 2, j + 1, V(0, i), ldv, hd + (m + 1), vn, hd + 2 * (m + 1)));
                 LS_TRY(ls_timing_end(h, 4));
             }
             LS_CUDA(cudaMemcpyAsync(hh_all.data(), S.hdev, sizeof(double2) * HS * nb, cudaMemcpyDeviceToHost,

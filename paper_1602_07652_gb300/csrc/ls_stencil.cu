@@ -195,6 +195,63 @@ __global__ void k_update(size_t N, int nvec, const VT* __restrict__ V, size_t ld
     }
 }
 
+// One pass of a classical Gram-Schmidt step against nvec <= G directions V_i (stride ld),
+// with everything that is local to an element fused into the pass:
+//   MODE 0: partial dots V_i^H w;
+//   MODE 1: w -= sum_i coef_i V_i, then the partial dots V_i^H w of the updated w;
+//   MODE 2: w -= sum_i coef_i V_i, then the partial ||w||^2.
+// Per element the operations and their order are those of k_update followed by k_dots,
+// and the partial sums are formed and stored as k_dots forms them, so the fused passes
+// give the same results as the separate kernels while reading each V_i and w once.
+template <typename VT, int G, int MODE>
+__global__ void __launch_bounds__(RED_THREADS) k_orth(size_t N, int nvec, const VT* __restrict__ V, size_t ld,
+                                                      const double2* __restrict__ coef, VT* __restrict__ w,
+                                                      double2* __restrict__ partial) {
+    constexpr int NO = MODE == 2 ? 1 : G;   // sums per thread
+    __shared__ VT sc[G];
+    __shared__ double2 red[RED_THREADS];
+    if (MODE > 0) {
+        for (int i = threadIdx.x; i < nvec; i += blockDim.x) sc[i] = vt_of<VT>(coef[i]);
+        __syncthreads();
+    }
+    VT acc[NO];
+#pragma unroll
+    for (int i = 0; i < NO; ++i) acc[i] = czero<VT>();
+    for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < N; k += (size_t)gridDim.x * blockDim.x) {
+        VT vk[G];
+#pragma unroll
+        for (int i = 0; i < G; ++i)
+            if (i < nvec) vk[i] = __ldg(&V[(size_t)i * ld + k]);
+        VT wk = w[k];
+        if (MODE > 0) {
+#pragma unroll
+            for (int i = 0; i < G; ++i)
+                if (i < nvec) wk = cfms(sc[i], vk[i], wk);
+            w[k] = wk;
+        }
+        if (MODE < 2) {
+#pragma unroll
+            for (int i = 0; i < G; ++i)
+                if (i < nvec) acc[i] = cconjmul_acc(vk[i], wk, acc[i]);
+        } else {
+            acc[0] = cconjmul_acc(wk, wk, acc[0]);
+        }
+    }
+    const int nout = MODE == 2 ? 1 : nvec;
+#pragma unroll
+    for (int i = 0; i < NO; ++i) {
+        if (i >= nout) break;
+        red[threadIdx.x] = ccast<double2>(acc[i]);
+        __syncthreads();
+        for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+            if (threadIdx.x < s) red[threadIdx.x] = red[threadIdx.x] + red[threadIdx.x + s];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) partial[(size_t)blockIdx.x * nout + i] = red[0];
+        __syncthreads();
+    }
+}
+
 struct Coefs {
     double2 c[64];
 };
@@ -386,6 +443,50 @@ int vec_combine(ls_handle* h, int nvec, const ZT* Z, size_t ld, const double2* c
         LS_LAUNCH(h, (k_combine<ZT, XT>), RED_BLOCKS, RED_THREADS, 0, N, cnt, Z + (size_t)base * ld, ld, cf, x);
     }
     return LS_OK;
+}
+
+// The fused pass with G the smallest of 2, 4, 8, 16 that holds nvec directions: the
+// registers (G values of V and G sums per thread) and so the resident warps that keep
+// loads in flight follow the step's own size.
+template <typename VT, int G>
+int orth_launch(ls_handle* h, int mode, int nvec, const VT* V, size_t ld, const double2* coef_dev, VT* w,
+                double2* partial) {
+    const size_t N = (size_t)h->n * h->n;
+    if (mode == 0) LS_LAUNCH(h, (k_orth<VT, G, 0>), RED_BLOCKS, RED_THREADS, 0, N, nvec, V, ld, coef_dev, w, partial);
+    else if (mode == 1) LS_LAUNCH(h, (k_orth<VT, G, 1>), RED_BLOCKS, RED_THREADS, 0, N, nvec, V, ld, coef_dev, w, partial);
+    else LS_LAUNCH(h, (k_orth<VT, G, 2>), RED_BLOCKS, RED_THREADS, 0, N, nvec, V, ld, coef_dev, w, partial);
+    return LS_OK;
+}
+
+template <typename VT>
+int vec_orth(ls_handle* h, int mode, int nvec, const VT* V, size_t ld, const double2* coef_dev, VT* w,
+             double2* out_dev) {
+    const size_t N = (size_t)h->n * h->n;
+    constexpr int GMAX = sizeof(VT) == 8 ? 16 : 8;
+    if (nvec < 1 || mode < 0 || mode > 2) return LS_EINVAL;
+    if (nvec > GMAX) {  // more directions than one pass holds: the separate kernels
+        if (mode == 0) return vec_dots_dev(h, nvec, V, ld, w, out_dev);
+        LS_LAUNCH(h, k_update<VT>, RED_BLOCKS, RED_THREADS, 0, N, nvec, V, ld, coef_dev, w);
+        if (mode == 1) return vec_dots_dev(h, nvec, V, ld, w, out_dev);
+        return vec_dots_dev(h, 1, (const VT*)w, 0, (const VT*)w, out_dev);
+    }
+    LS_TRY(red_reserve(h, (size_t)RED_BLOCKS * 64 + 256));
+    double2* partial = reinterpret_cast<double2*>(h->red);
+    if (nvec <= 2) LS_TRY((orth_launch<VT, 2>(h, mode, nvec, V, ld, coef_dev, w, partial)));
+    else if (nvec <= 4) LS_TRY((orth_launch<VT, 4>(h, mode, nvec, V, ld, coef_dev, w, partial)));
+    else if (nvec <= 8) LS_TRY((orth_launch<VT, 8>(h, mode, nvec, V, ld, coef_dev, w, partial)));
+    else if constexpr (GMAX >= 16) LS_TRY((orth_launch<VT, 16>(h, mode, nvec, V, ld, coef_dev, w, partial)));
+    LS_LAUNCH(h, k_dots_final, 1, RED_THREADS, 0, RED_BLOCKS, mode == 2 ? 1 : nvec, partial, out_dev);
+    return LS_OK;
+}
+
+int ls_vec_orth(ls_handle* h, int mode, int nvec, const double2* V, size_t ld, const double2* coef_dev, double2* w,
+                double2* out_dev) {
+    return vec_orth(h, mode, nvec, V, ld, coef_dev, w, out_dev);
+}
+int ls_vec_orth(ls_handle* h, int mode, int nvec, const float2* V, size_t ld, const double2* coef_dev, float2* w,
+                double2* out_dev) {
+    return vec_orth(h, mode, nvec, V, ld, coef_dev, w, out_dev);
 }
 
 int ls_vec_dots_dev(ls_handle* h, int nvec, const double2* V, size_t ld, const double2* w, double2* out_dev) {

@@ -140,8 +140,13 @@ def test_packed_members_match_unpacked_batch():
     tol = 1e-9
     s.ls_set_pack_members(0)
     u0, st0, rc0 = s.ls_solve_batch(f, tol)
+    h0 = s.ls_get_sweep_histogram()
     s.ls_set_pack_members(1)
     u1, st1, rc1 = s.ls_solve_batch(f, tol)
+    h1 = s.ls_get_sweep_histogram()
+    # the histogram of batch sizes accounts for every field through Algorithm 2
+    assert sum(k * v for k, v in h0.items()) == st0["sweep_fields"]
+    assert sum(k * v for k, v in h1.items()) == st1["sweep_fields"]
     assert rc0 == 0 and rc1 == 0
     assert st0["true_rel_residual"] <= tol and st1["true_rel_residual"] <= tol
     print("fields through Algorithm 2: unpacked %d packed %d; outer %d / %d" % (
