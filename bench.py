@@ -486,12 +486,14 @@ def run_ours(args):
     if args.e2e_steps is None:
         args.e2e_steps = args.steps
     if args.e2e_steps > 0:
-        f_hosts = []
+        f_hosts = []   # page-locked buffers from the library's own allocator (ls_host_alloc)
         for k in range(args.e2e_steps):
             for b in range(B):
                 s.ls_incident_rhs(theta((args.warmup + k) * B + b), f[b])
-            f_hosts.append(f.cpu().pin_memory())
-        u_host = torch.empty_like(f_hosts[0]).pin_memory()
+            fh = binding.host_empty(f.shape)
+            fh.copy_(f.cpu())
+            f_hosts.append(fh)
+        u_host = binding.host_empty(f.shape)
         s.ls_solve_batch_host(f_hosts[0], wl["tol"], u_host)
         torch.cuda.synchronize()
         t0 = time.perf_counter()

@@ -9,6 +9,7 @@ raises.
 from __future__ import annotations
 
 import ctypes
+import weakref
 import os
 
 import torch
@@ -97,6 +98,8 @@ _SIGS = {
     "ls_set_double_float": (ctypes.c_int, [_P, ctypes.c_int]),
     "ls_set_pack_members": (ctypes.c_int, [_P, ctypes.c_int]),
     "ls_get_sweep_histogram": (ctypes.c_int, [_P, _P, ctypes.c_int]),
+    "ls_host_alloc": (ctypes.c_int, [ctypes.c_size_t, ctypes.POINTER(_P)]),
+    "ls_host_free": (ctypes.c_int, [_P]),
     "ls_check_conversions": (ctypes.c_int, [_P, _P, ctypes.c_longlong, ctypes.POINTER(ctypes.c_ulonglong)]),
     "ls_device_timeouts": (ctypes.c_int, [ctypes.POINTER(ctypes.c_uint)]),
     "ls_test_tma_shortfall": (ctypes.c_int, [ctypes.c_uint]),
@@ -254,6 +257,18 @@ class Net:
         _ck(self._lib.ls_net_train_step(self._h, nb, H, W, _ptr(r), _ptr(m), _ptr(e), float(lr), ctypes.byref(loss)),
             "ls_net_train_step")
         return loss.value
+
+
+def host_empty(shape, dtype=torch.complex128) -> torch.Tensor:
+    """A CPU tensor in page-locked memory the library allocates (ls_host_alloc), for the
+    host-array entry points; the block is released when the last view of it is gone."""
+    lib = load_library()
+    nbytes = int(torch.Size(shape).numel()) * torch.empty((), dtype=dtype).element_size()
+    p = _P()
+    _ck(lib.ls_host_alloc(ctypes.c_size_t(nbytes), ctypes.byref(p)), "ls_host_alloc")
+    arr = (ctypes.c_byte * nbytes).from_address(p.value)
+    weakref.finalize(arr, lib.ls_host_free, _P(p.value))
+    return torch.frombuffer(arr, dtype=dtype).view(shape)
 
 
 def device_timeouts() -> int:

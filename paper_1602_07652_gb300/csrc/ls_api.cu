@@ -290,6 +290,23 @@ int ls_incident_rhs(ls_handle* h, double theta, ls_c64* f) {
     return ls_rhs(h, theta, reinterpret_cast<double2*>(f));
 }
 
+int ls_host_alloc(size_t bytes, void** out) {
+    if (!out) return LS_EINVAL;
+    *out = nullptr;
+    if (bytes == 0) return LS_EINVAL;
+    if (cudaHostAlloc(out, bytes, cudaHostAllocPortable) != cudaSuccess) {
+        *out = nullptr;
+        cudaGetLastError();   // the failure is reported by the return code
+        return LS_ENOMEM;
+    }
+    return LS_OK;
+}
+
+int ls_host_free(void* p) {
+    if (!p) return LS_OK;
+    return cudaFreeHost(p) == cudaSuccess ? LS_OK : LS_ECUDA;
+}
+
 int ls_get_sweep_histogram(ls_handle* h, int* counts, int len) {
     if (!h || !counts || len < 1) return LS_EINVAL;
     for (int k = 0; k < len; ++k) counts[k] = k <= LS_MAX_BATCH ? h->sweep_hist[k] : 0;

@@ -109,6 +109,14 @@ def test_host_buffers_match_device_solve():
     uh = torch.empty_like(fh).pin_memory()
     s.ls_solve_host(fh, 1e-9, uh)
     assert torch.equal(uh, u_dev.cpu())
+    # page-locked buffers from the library's own allocator
+    fl = binding.host_empty(fh.shape)
+    ul = binding.host_empty(fh.shape)
+    assert fl.dtype == torch.complex128 and fl.shape == fh.shape and not fl.is_cuda
+    fl.copy_(fh)
+    s.ls_solve_host(fl, 1e-9, ul)
+    assert torch.equal(ul, u_dev.cpu())
+    del fl, ul
     s.close()
 
 
