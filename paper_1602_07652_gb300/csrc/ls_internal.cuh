@@ -357,8 +357,15 @@ int ls_vec_orth(ls_handle* h, int mode, int nvec, const double2* V, size_t ld, c
                 double2* out_dev);
 int ls_vec_orth(ls_handle* h, int mode, int nvec, const float2* V, size_t ld, const double2* coef_dev, float2* w,
                 double2* out_dev);
-int ls_vec_norm(ls_handle* h, const double2* w, double* out_host);
-int ls_vec_norm(ls_handle* h, const float2* w, double* out_host);
+// The same passes for members members[0..cnt) of a lockstep batch in one launch (member m:
+// V and w at + m * mstride, coef at + m * cstride, out at + m * ostride); mode 3: out = w^H w.
+int ls_vec_orth_b(ls_handle* h, int mode, int nvec, const double2* V, size_t ld, size_t mstride, const double2* coef,
+                  size_t cstride, double2* w, const int* members, int cnt, double2* out, size_t ostride);
+int ls_vec_orth_b(ls_handle* h, int mode, int nvec, const float2* V, size_t ld, size_t mstride, const double2* coef,
+                  size_t cstride, float2* w, const int* members, int cnt, double2* out, size_t ostride);
+// out[m] = ||w + m * mstride|| for the listed members: one pass, one device->host read
+int ls_vec_norms_b(ls_handle* h, const double2* w, size_t mstride, const int* members, int cnt, double* out);
+int ls_vec_norms_b(ls_handle* h, const float2* w, size_t mstride, const int* members, int cnt, double* out);
 int ls_vec_axpby(ls_handle* h, double2 a, const double2* x, double2 b, double2* y);  // y = a x + b y
 int ls_vec_axpby(ls_handle* h, double2 a, const float2* x, double2 b, float2* y);
 int ls_vec_axpby(ls_handle* h, double2 a, const float2* x, double2 b, double2* y);

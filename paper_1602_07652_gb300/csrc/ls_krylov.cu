@@ -272,20 +272,26 @@ int fgmres_b(ls_handle* h, Ctx* c, KrylovSpace<VT>& S, Op op, Pc pc, const VT* b
     auto V = [&](int j, int mb) { return S.V + (size_t)j * ldv + mb * N; };
     auto Zb = [&](int j) { return S.Z + (size_t)j * ldv; };
     std::vector<Member> M(nb);
+    std::vector<double> nrm(nb, 0.0);   // norms of the members' vectors, by member
+    std::vector<int> lv, nz;            // live members; live members with b != 0
     for (int i = 0; i < nb; ++i) {
         res[i] = Result{};
-        if (!live[i]) continue;
+        if (live[i]) lv.push_back(i);
+    }
+    LS_TRY(ls_vec_norms_b(h, b, N, lv.data(), (int)lv.size(), nrm.data()));
+    for (int i : lv) {
         Member& e = M[i];
         const VT* bi = b + i * N;
         VT* xi = x + i * N;
         VT* ri = S.r + i * N;
-        LS_TRY(ls_vec_norm(h, bi, &e.nb));
+        e.nb = nrm[i];
         if (!std::isfinite(e.nb)) return LS_ENAN;
         if (e.nb == 0.0) {
             LS_TRY(ls_vec_zero(h, xi));
             res[i].converged = true;
             continue;
         }
+        nz.push_back(i);
         if (x0) {
             LS_TRY(apply_op(h, op, xi, ri));
             LS_TRY(ls_vec_axpby(h, make_double2(1, 0), bi, make_double2(-1, 0), ri));  // r = b - A x
@@ -293,7 +299,11 @@ int fgmres_b(ls_handle* h, Ctx* c, KrylovSpace<VT>& S, Op op, Pc pc, const VT* b
             LS_TRY(ls_vec_zero(h, xi));
             LS_TRY(ls_vec_copy(h, bi, ri));
         }
-        LS_TRY(ls_vec_norm(h, ri, &e.beta));
+    }
+    LS_TRY(ls_vec_norms_b(h, (const VT*)S.r, N, nz.data(), (int)nz.size(), nrm.data()));
+    for (int i : nz) {
+        Member& e = M[i];
+        e.beta = nrm[i];
         e.relres = e.beta / e.nb;
         if (!std::isfinite(e.relres)) return LS_ENAN;
         e.active = e.relres > tol[i] && e.total < maxit;
@@ -329,19 +339,22 @@ int fgmres_b(ls_handle* h, Ctx* c, KrylovSpace<VT>& S, Op op, Pc pc, const VT* b
             // with a network attached, the outer cycle's first direction is the learned step
             const Pc pcj = (pc == PC_LS && j == 0 && h->net) ? PC_NET : pc;
             LS_TRY(apply_pc_b(h, pcj, V(j, 0), Zb(j), nb, on.data(), st));
-            for (int i = 0; i < nb; ++i) {
-                if (!on[i]) continue;
-                VT* vn = V(j + 1, i);
-                double2* hd = S.hdev + i * HS;
-                LS_TRY(apply_op(h, op, Zb(j) + i * N, vn));
-                // CGS2 against V_0..V_j in three fused passes (dots; update and dots;
-                // update and norm); coefficients stay on the device between the passes
-                LS_TRY(ls_timing_begin(h));
-                LS_TRY(ls_vec_orth(h, 0, j + 1, V(0, i), ldv, nullptr, vn, hd));
-                LS_TRY(ls_vec_orth(h, 1, j + 1, V(0, i), ldv, hd, vn, hd + (m + 1)));
-                LS_TRY(ls_vec_orth(h, 2, j + 1, V(0, i), ldv, hd + (m + 1), vn, hd + 2 * (m + 1)));
-                LS_TRY(ls_timing_end(h, 4));
-            }
+            std::vector<int> ons;
+            for (int i = 0; i < nb; ++i)
+                if (on[i]) {
+                    ons.push_back(i);
+                    LS_TRY(apply_op(h, op, Zb(j) + i * N, V(j + 1, i)));
+                }
+            // CGS2 against V_0..V_j in three fused passes (dots; update and dots; update and
+            // norm), each one launch for all members; coefficients stay on the device
+            const int cnt = (int)ons.size();
+            LS_TRY(ls_timing_begin(h));
+            LS_TRY(ls_vec_orth_b(h, 0, j + 1, S.V, ldv, N, nullptr, 0, V(j + 1, 0), ons.data(), cnt, S.hdev, HS));
+            LS_TRY(ls_vec_orth_b(h, 1, j + 1, S.V, ldv, N, S.hdev, HS, V(j + 1, 0), ons.data(), cnt,
+                                 S.hdev + (m + 1), HS));
+            LS_TRY(ls_vec_orth_b(h, 2, j + 1, S.V, ldv, N, S.hdev + (m + 1), HS, V(j + 1, 0), ons.data(), cnt,
+                                 S.hdev + 2 * (m + 1), HS));
+            LS_TRY(ls_timing_end(h, 4));
             LS_CUDA(cudaMemcpyAsync(hh_all.data(), S.hdev, sizeof(double2) * HS * nb, cudaMemcpyDeviceToHost,
                                     h->stream));
             LS_CUDA(cudaStreamSynchronize(h->stream));
@@ -389,9 +402,11 @@ int fgmres_b(ls_handle* h, Ctx* c, KrylovSpace<VT>& S, Op op, Pc pc, const VT* b
             }
         }
         // end of the cycle: x += Z y for every member that iterated, then its true residual
+        std::vector<int> done;
         for (int i = 0; i < nb; ++i) {
             Member& e = M[i];
             if (!e.active) continue;
+            done.push_back(i);
             const int k = e.k;
             for (int r = k - 1; r >= 0; --r) {
                 cd s = e.gv[r];
@@ -405,7 +420,11 @@ int fgmres_b(ls_handle* h, Ctx* c, KrylovSpace<VT>& S, Op op, Pc pc, const VT* b
             LS_TRY(ls_vec_combine(h, k, Zb(0) + i * N, ldv, yc.data(), xi));
             LS_TRY(apply_op(h, op, xi, ri));
             LS_TRY(ls_vec_axpby(h, make_double2(1, 0), b + i * N, make_double2(-1, 0), ri));
-            LS_TRY(ls_vec_norm(h, ri, &e.beta));
+        }
+        LS_TRY(ls_vec_norms_b(h, (const VT*)S.r, N, done.data(), (int)done.size(), nrm.data()));
+        for (int i : done) {
+            Member& e = M[i];
+            e.beta = nrm[i];
             e.relres = e.beta / e.nb;
             if (!std::isfinite(e.relres)) return LS_ENAN;
             e.active = e.relres > tol[i] && e.total < maxit;
@@ -516,8 +535,10 @@ int ls_outer_solve_b(ls_handle* h, int nb, const double2* f, double tol, double2
     std::vector<unsigned char> live(nb, 0);
     std::vector<Result> r(nb);
     int nlive = 0;
+    std::vector<int> all(nb);
+    for (int i = 0; i < nb; ++i) all[i] = i;
+    LS_TRY(ls_vec_norms_b(h, f, N, all.data(), nb, nf.data()));
     for (int i = 0; i < nb; ++i) {
-        LS_TRY(ls_vec_norm(h, f + i * N, &nf[i]));
         if (!std::isfinite(nf[i])) return LS_ENAN;
         if (nf[i] == 0.0) LS_TRY(ls_vec_zero(h, u + i * N));
         else {
@@ -559,10 +580,13 @@ int ls_outer_solve_b(ls_handle* h, int nb, const double2* f, double tol, double2
             if (live[i]) LS_TRY(ls_vec_zero(h, u + i * N));
     std::vector<unsigned char> act(live);
     std::vector<int> steps(nb, 0);
+    std::vector<double> nr(nb, 0.0);
     for (;;) {
         bool any = false;
+        std::vector<int> cur;
         for (int i = 0; i < nb; ++i) {
             if (!act[i]) continue;
+            cur.push_back(i);
             double2* di = d + i * N;
             if (steps[i] == 0 && !use_x0) {  // u = 0: the residual is f itself
                 LS_TRY(ls_vec_copy(h, f + i * N, di));
@@ -573,9 +597,10 @@ int ls_outer_solve_b(ls_handle* h, int nb, const double2* f, double tol, double2
                 LS_TRY(ls_timing_end(h, 2));
                 LS_TRY(ls_vec_axpby(h, make_double2(1, 0), f + i * N, make_double2(-1, 0), di));  // d = f - H u
             }
-            double nr;
-            LS_TRY(ls_vec_norm(h, di, &nr));
-            relres[i] = nr / nf[i];
+        }
+        LS_TRY(ls_vec_norms_b(h, (const double2*)d, N, cur.data(), (int)cur.size(), nr.data()));
+        for (int i : cur) {
+            relres[i] = nr[i] / nf[i];
             if (!std::isfinite(relres[i])) return LS_ENAN;
             if (relres[i] <= tol || steps[i] >= h->opts.refine_maxit) {
                 act[i] = 0;

@@ -195,23 +195,38 @@ __global__ void k_update(size_t N, int nvec, const VT* __restrict__ V, size_t ld
     }
 }
 
+// Members of a lockstep batch that a batched vector kernel serves: grid row y works on
+// member idx[y], whose vectors start idx[y] * mstride after the block's base pointers.
+struct MemberList {
+    int idx[LS_MAX_BATCH];
+};
+
 // One pass of a classical Gram-Schmidt step against nvec <= G directions V_i (stride ld),
-// with everything that is local to an element fused into the pass:
+// for the members of a batch at once, with everything that is local to an element fused
+// into the pass:
 //   MODE 0: partial dots V_i^H w;
 //   MODE 1: w -= sum_i coef_i V_i, then the partial dots V_i^H w of the updated w;
-//   MODE 2: w -= sum_i coef_i V_i, then the partial ||w||^2.
-// Per element the operations and their order are those of k_update followed by k_dots,
-// and the partial sums are formed and stored as k_dots forms them, so the fused passes
-// give the same results as the separate kernels while reading each V_i and w once.
+//   MODE 2: w -= sum_i coef_i V_i, then the partial ||w||^2;
+//   MODE 3: the partial ||w||^2 (nvec = 0, w unchanged).
+// Grid row y serves member m = ml.idx[y] (its V, w at + m * mstride, its coefficients at
+// coef + m * cstride) with gridDim.x blocks; their partial sums go to
+// partial[(y * gridDim.x + b) * nout + i].  Per element the operations and their order are
+// those of an update followed by a dot pass, and each partial sum is formed as k_dots forms
+// it, so the fused passes give the results of separate kernels while reading each V_i and
+// w once.
 template <typename VT, int G, int MODE>
 __global__ void __launch_bounds__(RED_THREADS) k_orth(size_t N, int nvec, const VT* __restrict__ V, size_t ld,
-                                                      const double2* __restrict__ coef, VT* __restrict__ w,
+                                                      size_t mstride, const double2* __restrict__ coef,
+                                                      size_t cstride, VT* __restrict__ w, MemberList ml,
                                                       double2* __restrict__ partial) {
-    constexpr int NO = MODE == 2 ? 1 : G;   // sums per thread
+    constexpr int NO = MODE >= 2 ? 1 : G;   // sums per thread
     __shared__ VT sc[G];
     __shared__ double2 red[RED_THREADS];
-    if (MODE > 0) {
-        for (int i = threadIdx.x; i < nvec; i += blockDim.x) sc[i] = vt_of<VT>(coef[i]);
+    const size_t mo = (size_t)ml.idx[blockIdx.y] * mstride;
+    VT* wm = w + mo;
+    if (MODE == 1 || MODE == 2) {
+        const double2* cm = coef + (size_t)ml.idx[blockIdx.y] * cstride;
+        for (int i = threadIdx.x; i < nvec; i += blockDim.x) sc[i] = vt_of<VT>(cm[i]);
         __syncthreads();
     }
     VT acc[NO];
@@ -219,15 +234,17 @@ __global__ void __launch_bounds__(RED_THREADS) k_orth(size_t N, int nvec, const 
     for (int i = 0; i < NO; ++i) acc[i] = czero<VT>();
     for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < N; k += (size_t)gridDim.x * blockDim.x) {
         VT vk[G];
+        if (MODE < 3) {
 #pragma unroll
-        for (int i = 0; i < G; ++i)
-            if (i < nvec) vk[i] = __ldg(&V[(size_t)i * ld + k]);
-        VT wk = w[k];
-        if (MODE > 0) {
+            for (int i = 0; i < G; ++i)
+                if (i < nvec) vk[i] = __ldg(&V[mo + (size_t)i * ld + k]);
+        }
+        VT wk = wm[k];
+        if (MODE == 1 || MODE == 2) {
 #pragma unroll
             for (int i = 0; i < G; ++i)
                 if (i < nvec) wk = cfms(sc[i], vk[i], wk);
-            w[k] = wk;
+            wm[k] = wk;
         }
         if (MODE < 2) {
 #pragma unroll
@@ -237,7 +254,8 @@ __global__ void __launch_bounds__(RED_THREADS) k_orth(size_t N, int nvec, const 
             acc[0] = cconjmul_acc(wk, wk, acc[0]);
         }
     }
-    const int nout = MODE == 2 ? 1 : nvec;
+    const int nout = MODE >= 2 ? 1 : nvec;
+    double2* pp = partial + ((size_t)blockIdx.y * gridDim.x + blockIdx.x) * nout;
 #pragma unroll
     for (int i = 0; i < NO; ++i) {
         if (i >= nout) break;
@@ -247,7 +265,28 @@ __global__ void __launch_bounds__(RED_THREADS) k_orth(size_t N, int nvec, const 
             if (threadIdx.x < s) red[threadIdx.x] = red[threadIdx.x] + red[threadIdx.x + s];
             __syncthreads();
         }
-        if (threadIdx.x == 0) partial[(size_t)blockIdx.x * nout + i] = red[0];
+        if (threadIdx.x == 0) pp[i] = red[0];
+        __syncthreads();
+    }
+}
+
+// out[ml.idx[x] * ostride + i] = sum_b partial[(x * bpm + b) * nout + i]: block x sums the
+// partials of grid row x of k_orth (fixed order, as k_dots_final).
+__global__ void k_orth_final(int bpm, int nout, const double2* __restrict__ partial, MemberList ml,
+                             double2* __restrict__ out, size_t ostride) {
+    __shared__ double2 red[RED_THREADS];
+    const double2* p = partial + (size_t)blockIdx.x * bpm * nout;
+    double2* o = out + (size_t)ml.idx[blockIdx.x] * ostride;
+    for (int i = 0; i < nout; ++i) {
+        double2 acc = make_double2(0, 0);
+        for (int b = threadIdx.x; b < bpm; b += blockDim.x) acc = acc + p[(size_t)b * nout + i];
+        red[threadIdx.x] = acc;
+        __syncthreads();
+        for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+            if (threadIdx.x < s) red[threadIdx.x] = red[threadIdx.x] + red[threadIdx.x + s];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) o[i] = red[0];
         __syncthreads();
     }
 }
@@ -424,14 +463,6 @@ int vec_dots(ls_handle* h, int nvec, const VT* V, size_t ld, const VT* w, double
     return LS_OK;
 }
 
-template <typename VT>
-int vec_norm(ls_handle* h, const VT* w, double* out_host) {
-    double2 d;
-    LS_TRY(vec_dots(h, 1, w, 0, w, &d));
-    // a NaN or Inf anywhere in w must surface as a non-finite norm
-    *out_host = d.x >= 0 ? sqrt(d.x) : (d.x < 0 ? 0.0 : d.x);
-    return LS_OK;
-}
 
 template <typename ZT, typename XT>
 int vec_combine(ls_handle* h, int nvec, const ZT* Z, size_t ld, const double2* coef_host, XT* x) {
@@ -449,35 +480,94 @@ int vec_combine(ls_handle* h, int nvec, const ZT* Z, size_t ld, const double2* c
 // registers (G values of V and G sums per thread) and so the resident warps that keep
 // loads in flight follow the step's own size.
 template <typename VT, int G>
-int orth_launch(ls_handle* h, int mode, int nvec, const VT* V, size_t ld, const double2* coef_dev, VT* w,
-                double2* partial) {
+int orth_launch(ls_handle* h, int mode, dim3 grid, int nvec, const VT* V, size_t ld, size_t mstride,
+                const double2* coef, size_t cstride, VT* w, const MemberList& ml, double2* partial) {
     const size_t N = (size_t)h->n * h->n;
-    if (mode == 0) LS_LAUNCH(h, (k_orth<VT, G, 0>), RED_BLOCKS, RED_THREADS, 0, N, nvec, V, ld, coef_dev, w, partial);
-    else if (mode == 1) LS_LAUNCH(h, (k_orth<VT, G, 1>), RED_BLOCKS, RED_THREADS, 0, N, nvec, V, ld, coef_dev, w, partial);
-    else LS_LAUNCH(h, (k_orth<VT, G, 2>), RED_BLOCKS, RED_THREADS, 0, N, nvec, V, ld, coef_dev, w, partial);
+    switch (mode) {
+        case 0:
+            LS_LAUNCH(h, (k_orth<VT, G, 0>), grid, RED_THREADS, 0, N, nvec, V, ld, mstride, coef, cstride, w, ml, partial);
+            break;
+        case 1:
+            LS_LAUNCH(h, (k_orth<VT, G, 1>), grid, RED_THREADS, 0, N, nvec, V, ld, mstride, coef, cstride, w, ml, partial);
+            break;
+        case 2:
+            LS_LAUNCH(h, (k_orth<VT, G, 2>), grid, RED_THREADS, 0, N, nvec, V, ld, mstride, coef, cstride, w, ml, partial);
+            break;
+        default:
+            LS_LAUNCH(h, (k_orth<VT, G, 3>), grid, RED_THREADS, 0, N, 0, V, ld, mstride, coef, cstride, w, ml, partial);
+            break;
+    }
     return LS_OK;
 }
 
+// The pass of `mode` for members members[0..cnt) of a batch (member m: V + m * mstride,
+// w + m * mstride, coef + m * cstride, out + m * ostride); RED_BLOCKS blocks shared out
+// among them.  More directions than one pass holds: the separate kernels, member by member.
+template <typename VT>
+int vec_orth_b(ls_handle* h, int mode, int nvec, const VT* V, size_t ld, size_t mstride, const double2* coef,
+               size_t cstride, VT* w, const int* members, int cnt, double2* out, size_t ostride) {
+    const size_t N = (size_t)h->n * h->n;
+    constexpr int GMAX = sizeof(VT) == 8 ? 16 : 8;
+    if (mode < 0 || mode > 3 || cnt < 0 || cnt > LS_MAX_BATCH || (mode < 3 && nvec < 1)) return LS_EINVAL;
+    if (cnt == 0) return LS_OK;
+    if (mode < 3 && nvec > GMAX) {
+        for (int c = 0; c < cnt; ++c) {
+            const size_t mo = (size_t)members[c] * mstride;
+            double2* o = out + (size_t)members[c] * ostride;
+            if (mode == 0) {
+                LS_TRY(vec_dots_dev(h, nvec, V + mo, ld, (const VT*)(w + mo), o));
+                continue;
+            }
+            LS_LAUNCH(h, k_update<VT>, RED_BLOCKS, RED_THREADS, 0, N, nvec, V + mo, ld,
+                      coef + (size_t)members[c] * cstride, w + mo);
+            if (mode == 1) LS_TRY(vec_dots_dev(h, nvec, V + mo, ld, (const VT*)(w + mo), o));
+            else LS_TRY(vec_dots_dev(h, 1, (const VT*)(w + mo), 0, (const VT*)(w + mo), o));
+        }
+        return LS_OK;
+    }
+    MemberList ml;
+    for (int c = 0; c < cnt; ++c) ml.idx[c] = members[c];
+    const int bpm = RED_BLOCKS / cnt;   // >= 9: cnt <= LS_MAX_BATCH
+    const dim3 grid((unsigned)bpm, (unsigned)cnt);
+    LS_TRY(red_reserve(h, (size_t)RED_BLOCKS * 64 + 256));
+    double2* partial = reinterpret_cast<double2*>(h->red);
+    if (mode == 3 || nvec <= 2) LS_TRY((orth_launch<VT, 2>(h, mode, grid, nvec, V, ld, mstride, coef, cstride, w, ml, partial)));
+    else if (nvec <= 4) LS_TRY((orth_launch<VT, 4>(h, mode, grid, nvec, V, ld, mstride, coef, cstride, w, ml, partial)));
+    else if (nvec <= 8) LS_TRY((orth_launch<VT, 8>(h, mode, grid, nvec, V, ld, mstride, coef, cstride, w, ml, partial)));
+    else if constexpr (GMAX >= 16)
+        LS_TRY((orth_launch<VT, 16>(h, mode, grid, nvec, V, ld, mstride, coef, cstride, w, ml, partial)));
+    LS_LAUNCH(h, k_orth_final, (unsigned)cnt, RED_THREADS, 0, bpm, mode >= 2 ? 1 : nvec, partial, ml, out, ostride);
+    return LS_OK;
+}
+
+// ||w_m|| for the members members[0..cnt) (member m at w + m * mstride) into out[m]: one
+// pass over all of them and one device->host read.  A NaN or Inf in a member's vector
+// gives a non-finite norm.
+template <typename VT>
+int vec_norms_b(ls_handle* h, const VT* w, size_t mstride, const int* members, int cnt, double* out) {
+    if (cnt < 0 || cnt > LS_MAX_BATCH) return LS_EINVAL;
+    if (cnt == 0) return LS_OK;
+    LS_TRY(red_reserve(h, (size_t)RED_BLOCKS * 64 + 256));
+    double2* outd = reinterpret_cast<double2*>(h->red) + (size_t)RED_BLOCKS * 64;
+    int top = 0;
+    for (int c = 0; c < cnt; ++c) top = members[c] + 1 > top ? members[c] + 1 : top;
+    LS_TRY(vec_orth_b(h, 3, 0, (const VT*)nullptr, 0, mstride, nullptr, 0, const_cast<VT*>(w), members, cnt, outd, 1));
+    LS_CUDA(cudaMemcpyAsync(h->red_host, outd, sizeof(double2) * top, cudaMemcpyDeviceToHost, h->stream));
+    LS_CUDA(cudaStreamSynchronize(h->stream));
+    const double2* hr = reinterpret_cast<const double2*>(h->red_host);
+    for (int c = 0; c < cnt; ++c) {
+        const double d = hr[members[c]].x;
+        out[members[c]] = d >= 0 ? sqrt(d) : (d < 0 ? 0.0 : d);
+    }
+    return LS_OK;
+}
+
+// one member: the pass over directions V (stride ld) and w, results at out_dev
 template <typename VT>
 int vec_orth(ls_handle* h, int mode, int nvec, const VT* V, size_t ld, const double2* coef_dev, VT* w,
              double2* out_dev) {
-    const size_t N = (size_t)h->n * h->n;
-    constexpr int GMAX = sizeof(VT) == 8 ? 16 : 8;
-    if (nvec < 1 || mode < 0 || mode > 2) return LS_EINVAL;
-    if (nvec > GMAX) {  // more directions than one pass holds: the separate kernels
-        if (mode == 0) return vec_dots_dev(h, nvec, V, ld, w, out_dev);
-        LS_LAUNCH(h, k_update<VT>, RED_BLOCKS, RED_THREADS, 0, N, nvec, V, ld, coef_dev, w);
-        if (mode == 1) return vec_dots_dev(h, nvec, V, ld, w, out_dev);
-        return vec_dots_dev(h, 1, (const VT*)w, 0, (const VT*)w, out_dev);
-    }
-    LS_TRY(red_reserve(h, (size_t)RED_BLOCKS * 64 + 256));
-    double2* partial = reinterpret_cast<double2*>(h->red);
-    if (nvec <= 2) LS_TRY((orth_launch<VT, 2>(h, mode, nvec, V, ld, coef_dev, w, partial)));
-    else if (nvec <= 4) LS_TRY((orth_launch<VT, 4>(h, mode, nvec, V, ld, coef_dev, w, partial)));
-    else if (nvec <= 8) LS_TRY((orth_launch<VT, 8>(h, mode, nvec, V, ld, coef_dev, w, partial)));
-    else if constexpr (GMAX >= 16) LS_TRY((orth_launch<VT, 16>(h, mode, nvec, V, ld, coef_dev, w, partial)));
-    LS_LAUNCH(h, k_dots_final, 1, RED_THREADS, 0, RED_BLOCKS, mode == 2 ? 1 : nvec, partial, out_dev);
-    return LS_OK;
+    const int zero = 0;
+    return vec_orth_b(h, mode, nvec, V, ld, 0, coef_dev, 0, w, &zero, 1, out_dev, 0);
 }
 
 int ls_vec_orth(ls_handle* h, int mode, int nvec, const double2* V, size_t ld, const double2* coef_dev, double2* w,
@@ -487,6 +577,20 @@ int ls_vec_orth(ls_handle* h, int mode, int nvec, const double2* V, size_t ld, c
 int ls_vec_orth(ls_handle* h, int mode, int nvec, const float2* V, size_t ld, const double2* coef_dev, float2* w,
                 double2* out_dev) {
     return vec_orth(h, mode, nvec, V, ld, coef_dev, w, out_dev);
+}
+int ls_vec_orth_b(ls_handle* h, int mode, int nvec, const double2* V, size_t ld, size_t mstride, const double2* coef,
+                  size_t cstride, double2* w, const int* members, int cnt, double2* out, size_t ostride) {
+    return vec_orth_b(h, mode, nvec, V, ld, mstride, coef, cstride, w, members, cnt, out, ostride);
+}
+int ls_vec_orth_b(ls_handle* h, int mode, int nvec, const float2* V, size_t ld, size_t mstride, const double2* coef,
+                  size_t cstride, float2* w, const int* members, int cnt, double2* out, size_t ostride) {
+    return vec_orth_b(h, mode, nvec, V, ld, mstride, coef, cstride, w, members, cnt, out, ostride);
+}
+int ls_vec_norms_b(ls_handle* h, const double2* w, size_t mstride, const int* members, int cnt, double* out) {
+    return vec_norms_b(h, w, mstride, members, cnt, out);
+}
+int ls_vec_norms_b(ls_handle* h, const float2* w, size_t mstride, const int* members, int cnt, double* out) {
+    return vec_norms_b(h, w, mstride, members, cnt, out);
 }
 
 int ls_vec_dots_dev(ls_handle* h, int nvec, const double2* V, size_t ld, const double2* w, double2* out_dev) {
@@ -508,8 +612,6 @@ int ls_vec_update(ls_handle* h, int nvec, const float2* V, size_t ld, const doub
     LS_LAUNCH(h, k_update<float2>, RED_BLOCKS, RED_THREADS, 0, N, nvec, V, ld, coef_dev, w);
     return LS_OK;
 }
-int ls_vec_norm(ls_handle* h, const double2* w, double* out_host) { return vec_norm(h, w, out_host); }
-int ls_vec_norm(ls_handle* h, const float2* w, double* out_host) { return vec_norm(h, w, out_host); }
 int ls_vec_combine(ls_handle* h, int nvec, const double2* Z, size_t ld, const double2* coef_host, double2* x) {
     return vec_combine(h, nvec, Z, ld, coef_host, x);
 }
