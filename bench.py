@@ -47,6 +47,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true",
                     help="skip the timed oracle sample (the CPU baseline)")
     ap.add_argument("--no-fp64-leg", action="store_true", help="skip the plain FP64 GPU leg")
+    ap.add_argument("--refine-inner-tol", type=float, default=None,
+                    help="mixed precision: tolerance floor of each FP32 correction solve (library default 1e-6)")
     ap.add_argument("--no-pack", action="store_true",
                     help="run Algorithm 2 on the whole lockstep batch, converged members included")
     ap.add_argument("--no-tensor-steps", action="store_true",
@@ -412,6 +414,8 @@ def run_ours(args):
     # restart lengths above the iteration counts this workload needs (<= 6 outer, <= 6 inner
     # per call), so they never restart; they bound the Krylov memory of large batches
     o.outer_restart, o.inner_restart = 10, 10
+    if args.refine_inner_tol is not None:
+        o.refine_inner_tol = args.refine_inner_tol
     prec = binding.LS_FP64 if args.fp64 else binding.LS_MIXED
     if args.fp64 and args.batch > 4:
         raise SystemExit("--fp64 takes batches of at most 4")

@@ -254,6 +254,7 @@ int apply_pc_b(ls_handle* h, Pc pc, VT* v, VT* z, int nb, const unsigned char* o
 
 struct Member {
     double nb = 0, beta = 0, relres = 0;
+    double cyc0 = 0;      // true relative residual when the current cycle started
     int total = 0, k = 0;
     bool active = false;  // still iterating (not converged, under maxit)
     bool cyc = false;     // taking part in the current Arnoldi cycle
@@ -326,6 +327,7 @@ int fgmres_b(ls_handle* h, Ctx* c, KrylovSpace<VT>& S, Op op, Pc pc, const VT* b
             std::fill(e.gv.begin(), e.gv.end(), cd(0));
             std::fill(e.H.begin(), e.H.end(), cd(0));
             e.gv[0] = e.beta;
+            e.cyc0 = e.relres;
             e.k = 0;
         }
         if (!any) break;
@@ -428,6 +430,9 @@ int fgmres_b(ls_handle* h, Ctx* c, KrylovSpace<VT>& S, Op op, Pc pc, const VT* b
             e.relres = e.beta / e.nb;
             if (!std::isfinite(e.relres)) return LS_ENAN;
             e.active = e.relres > tol[i] && e.total < maxit;
+            // the FP32 correction of a mixed solve stops where FP32 stops gaining (a cycle
+            // that did not halve its true residual): the FP64 refinement takes it from there
+            if (op == OP_HMIX && e.relres > 0.5 * e.cyc0) e.active = false;
         }
     }
     for (int i = 0; i < nb; ++i) {
