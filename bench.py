@@ -584,7 +584,11 @@ def run_ours(args):
                                       "how": "sketch of the field (about 2 per cent accurate) and its values at %d "
                                              "seeded points vs the stored digest of the FP64 oracle's field "
                                              "solved to %g" % (len(dg["points"]), dg["tol"]),
-                                      "gpu": "mixed precision, batched, tol %g, first incident wave" % wl["tol"]}
+                                      "gpu": "mixed precision, batched, tol %g, first incident wave" % wl["tol"],
+                                      # at tol 1e-6 the error is what a 1e-6 residual leaves on this operator;
+                                      # the element-wise parity bar is taken at tol 1e-8 by the GPU tests
+                                      "parity_bar": "tests/test_gpu_fullsize.py: C3 refined to 1e-8, relative "
+                                                    "L2 <= 1e-6 and points <= 1e-5 of max |u| vs this digest"}
         if not args.no_cpu_baseline and dg is not None:
             try:
                 v, step_ms, desc = oracle_sample(wl, dg["at_tol_1e-6"], steps=3)
