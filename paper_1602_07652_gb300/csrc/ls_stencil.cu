@@ -211,9 +211,9 @@ struct MemberList {
 // Grid row y serves member m = ml.idx[y] (its V, w at + m * mstride, its coefficients at
 // coef + m * cstride) with gridDim.x blocks; their partial sums go to
 // partial[(y * gridDim.x + b) * nout + i].  Per element the operations and their order are
-// those of an update followed by a dot pass, and each partial sum is formed as k_dots forms
-// it, so the fused passes give the results of separate kernels while reading each V_i and
-// w once.
+// those of an update followed by a dot pass, so the fused passes give the results of
+// separate kernels up to the grouping of the partial sums, while reading each V_i and w
+// once.
 template <typename VT, int G, int MODE>
 __global__ void __launch_bounds__(RED_THREADS) k_orth(size_t N, int nvec, const VT* __restrict__ V, size_t ld,
                                                       size_t mstride, const double2* __restrict__ coef,
@@ -229,10 +229,28 @@ __global__ void __launch_bounds__(RED_THREADS) k_orth(size_t N, int nvec, const 
         for (int i = threadIdx.x; i < nvec; i += blockDim.x) sc[i] = vt_of<VT>(cm[i]);
         __syncthreads();
     }
+    // per-thread sums in VT over at most kFlush elements, then added into FP64 (with a batch
+    // a member gets fewer blocks, so a thread covers more elements than RED_BLOCKS would give)
+    constexpr int kFlush = 64;
     VT acc[NO];
+    double2 accd[NO];
 #pragma unroll
-    for (int i = 0; i < NO; ++i) acc[i] = czero<VT>();
+    for (int i = 0; i < NO; ++i) {
+        acc[i] = czero<VT>();
+        accd[i] = make_double2(0, 0);
+    }
+    int run = 0;
     for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < N; k += (size_t)gridDim.x * blockDim.x) {
+        if (run == kFlush) {
+#pragma unroll
+            for (int i = 0; i < NO; ++i)
+                if (MODE >= 2 || i < nvec) {
+                    accd[i] = accd[i] + ccast<double2>(acc[i]);
+                    acc[i] = czero<VT>();
+                }
+            run = 0;
+        }
+        ++run;
         VT vk[G];
         if (MODE < 3) {
 #pragma unroll
@@ -259,7 +277,7 @@ __global__ void __launch_bounds__(RED_THREADS) k_orth(size_t N, int nvec, const 
 #pragma unroll
     for (int i = 0; i < NO; ++i) {
         if (i >= nout) break;
-        red[threadIdx.x] = ccast<double2>(acc[i]);
+        red[threadIdx.x] = accd[i] + ccast<double2>(acc[i]);
         __syncthreads();
         for (int s = blockDim.x / 2; s > 0; s >>= 1) {
             if (threadIdx.x < s) red[threadIdx.x] = red[threadIdx.x] + red[threadIdx.x + s];
