@@ -346,19 +346,11 @@ int ls_stencil_apply_b(ls_handle* h, int dir, int withm, const double2* v, const
 int ls_stencil_refine_f32(ls_handle* h, int dir, const float2* v, const float2* g, float2* y, int nb);
 int ls_stencil_apply_f32(ls_handle* h, int dir, int mode, const float2* v, float2* y);
 // Krylov vectors in FP64 (double2) or FP32 (float2); dot products summed in FP64
-int ls_vec_dots(ls_handle* h, int nvec, const double2* V, size_t ld, const double2* w, double2* out_host);
-int ls_vec_dots_dev(ls_handle* h, int nvec, const double2* V, size_t ld, const double2* w, double2* out_dev);
-int ls_vec_dots_dev(ls_handle* h, int nvec, const float2* V, size_t ld, const float2* w, double2* out_dev);
-int ls_vec_update(ls_handle* h, int nvec, const double2* V, size_t ld, const double2* coef_dev, double2* w);
-int ls_vec_update(ls_handle* h, int nvec, const float2* V, size_t ld, const double2* coef_dev, float2* w);
-// One fused pass of a Gram-Schmidt step against nvec directions (ls_stencil.cu):
-// mode 0: out = V^H w; 1: w -= V coef, then out = V^H w; 2: w -= V coef, then out[0] = w^H w.
-int ls_vec_orth(ls_handle* h, int mode, int nvec, const double2* V, size_t ld, const double2* coef_dev, double2* w,
-                double2* out_dev);
-int ls_vec_orth(ls_handle* h, int mode, int nvec, const float2* V, size_t ld, const double2* coef_dev, float2* w,
-                double2* out_dev);
-// The same passes for members members[0..cnt) of a lockstep batch in one launch (member m:
-// V and w at + m * mstride, coef at + m * cstride, out at + m * ostride); mode 3: out = w^H w.
+// One fused pass of a Gram-Schmidt step against nvec directions (ls_stencil.cu) for
+// members members[0..cnt) of a lockstep batch in one launch (member m: V and w at
+// + m * mstride, coef at + m * cstride, out at + m * ostride):
+// mode 0: out = V^H w; 1: w -= V coef, then out = V^H w; 2: w -= V coef, then out[0] = w^H w;
+// mode 3: out[0] = w^H w.
 int ls_vec_orth_b(ls_handle* h, int mode, int nvec, const double2* V, size_t ld, size_t mstride, const double2* coef,
                   size_t cstride, double2* w, const int* members, int cnt, double2* out, size_t ostride);
 int ls_vec_orth_b(ls_handle* h, int mode, int nvec, const float2* V, size_t ld, size_t mstride, const double2* coef,

@@ -469,17 +469,6 @@ int vec_dots_dev(ls_handle* h, int nvec, const VT* V, size_t ld, const VT* w, do
     return LS_OK;
 }
 
-template <typename VT>
-int vec_dots(ls_handle* h, int nvec, const VT* V, size_t ld, const VT* w, double2* out_host) {
-    LS_TRY(red_reserve(h, (size_t)RED_BLOCKS * 64 + 256));
-    double2* outd = reinterpret_cast<double2*>(h->red) + (size_t)RED_BLOCKS * 64;
-    LS_TRY(vec_dots_dev(h, nvec, V, ld, w, outd));
-    LS_CUDA(cudaMemcpyAsync(h->red_host, outd, sizeof(double2) * nvec, cudaMemcpyDeviceToHost, h->stream));
-    LS_CUDA(cudaStreamSynchronize(h->stream));
-    const double2* hr = reinterpret_cast<const double2*>(h->red_host);
-    for (int i = 0; i < nvec; ++i) out_host[i] = hr[i];
-    return LS_OK;
-}
 
 
 template <typename ZT, typename XT>
@@ -580,22 +569,6 @@ int vec_norms_b(ls_handle* h, const VT* w, size_t mstride, const int* members, i
     return LS_OK;
 }
 
-// one member: the pass over directions V (stride ld) and w, results at out_dev
-template <typename VT>
-int vec_orth(ls_handle* h, int mode, int nvec, const VT* V, size_t ld, const double2* coef_dev, VT* w,
-             double2* out_dev) {
-    const int zero = 0;
-    return vec_orth_b(h, mode, nvec, V, ld, 0, coef_dev, 0, w, &zero, 1, out_dev, 0);
-}
-
-int ls_vec_orth(ls_handle* h, int mode, int nvec, const double2* V, size_t ld, const double2* coef_dev, double2* w,
-                double2* out_dev) {
-    return vec_orth(h, mode, nvec, V, ld, coef_dev, w, out_dev);
-}
-int ls_vec_orth(ls_handle* h, int mode, int nvec, const float2* V, size_t ld, const double2* coef_dev, float2* w,
-                double2* out_dev) {
-    return vec_orth(h, mode, nvec, V, ld, coef_dev, w, out_dev);
-}
 int ls_vec_orth_b(ls_handle* h, int mode, int nvec, const double2* V, size_t ld, size_t mstride, const double2* coef,
                   size_t cstride, double2* w, const int* members, int cnt, double2* out, size_t ostride) {
     return vec_orth_b(h, mode, nvec, V, ld, mstride, coef, cstride, w, members, cnt, out, ostride);
@@ -611,25 +584,6 @@ int ls_vec_norms_b(ls_handle* h, const float2* w, size_t mstride, const int* mem
     return vec_norms_b(h, w, mstride, members, cnt, out);
 }
 
-int ls_vec_dots_dev(ls_handle* h, int nvec, const double2* V, size_t ld, const double2* w, double2* out_dev) {
-    return vec_dots_dev(h, nvec, V, ld, w, out_dev);
-}
-int ls_vec_dots_dev(ls_handle* h, int nvec, const float2* V, size_t ld, const float2* w, double2* out_dev) {
-    return vec_dots_dev(h, nvec, V, ld, w, out_dev);
-}
-int ls_vec_dots(ls_handle* h, int nvec, const double2* V, size_t ld, const double2* w, double2* out_host) {
-    return vec_dots(h, nvec, V, ld, w, out_host);
-}
-int ls_vec_update(ls_handle* h, int nvec, const double2* V, size_t ld, const double2* coef_dev, double2* w) {
-    const size_t N = (size_t)h->n * h->n;
-    LS_LAUNCH(h, k_update<double2>, RED_BLOCKS, RED_THREADS, 0, N, nvec, V, ld, coef_dev, w);
-    return LS_OK;
-}
-int ls_vec_update(ls_handle* h, int nvec, const float2* V, size_t ld, const double2* coef_dev, float2* w) {
-    const size_t N = (size_t)h->n * h->n;
-    LS_LAUNCH(h, k_update<float2>, RED_BLOCKS, RED_THREADS, 0, N, nvec, V, ld, coef_dev, w);
-    return LS_OK;
-}
 int ls_vec_combine(ls_handle* h, int nvec, const double2* Z, size_t ld, const double2* coef_host, double2* x) {
     return vec_combine(h, nvec, Z, ld, coef_host, x);
 }
