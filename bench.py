@@ -48,7 +48,7 @@ def parse():
                     help="skip the timed oracle sample (the CPU baseline)")
     ap.add_argument("--no-fp64-leg", action="store_true", help="skip the plain FP64 GPU leg")
     ap.add_argument("--refine-inner-tol", type=float, default=None,
-                    help="mixed precision: tolerance floor of each FP32 correction solve (library default 1e-6)")
+                    help="mixed precision: tolerance floor of each FP32 correction solve (library default 1e-4)")
     ap.add_argument("--no-pack", action="store_true",
                     help="run Algorithm 2 on the whole lockstep batch, converged members included")
     ap.add_argument("--no-tensor-steps", action="store_true",

@@ -68,10 +68,13 @@ typedef struct {
                               the w^2-weighted coefficient (Sec. 3.3; default 10)            */
     int refine_maxit;      /* LS_MIXED: refinement steps cap (default 6)                    */
     double refine_inner_tol; /* LS_MIXED: floor of the relative tolerance of each FP32
-                                correction solve (default 1e-6: at solve tolerances >= 1e-6
-                                one correction usually suffices); a correction whose restart
-                                cycle does not halve its true residual stops there and the
-                                FP64 refinement takes another step                          */
+                                correction solve (default 1e-4: the last correction then
+                                over-solves, and at tol 1e-6 the field stays within 1e-6 of
+                                the converged one; 1e-6 usually needs one correction only,
+                                faster, with the field as close as a 1e-6 residual allows);
+                                a correction whose restart cycle does not halve its true
+                                residual stops there and the FP64 refinement takes another
+                                step                                                        */
     int use_graphs;        /* 1 (default): replay Algorithm 2 as a captured CUDA graph;
                               0: launch its kernels one by one (same arithmetic)            */
     int inner_precond;     /* preconditioner of the inner GMRES: LS_PC_BD (default,

@@ -155,7 +155,7 @@ void ls_default_opts(ls_opts* o) {
     o->outer_maxit = 200;
     o->shift = 10.0;
     o->refine_maxit = 6;
-    o->refine_inner_tol = 1e-6;
+    o->refine_inner_tol = 1e-4;
     o->use_graphs = 1;
     o->inner_precond = LS_PC_BD;
 }
